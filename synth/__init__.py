@@ -1,0 +1,8 @@
+"""Seeded synthetic inputs (water boxes with ions) for tests and benchmarks.
+
+Holds none of the multilevel summation arithmetic: it only places atoms and
+assigns charges.  Both the oracle side and the CUDA side take their inputs
+from here.
+"""
+from .water import (TIP3P, WORKLOADS, Workload, make_water_box, replica_sizes,  # noqa: F401
+                    workload, spatial_subsample)
