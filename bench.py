@@ -1,0 +1,351 @@
+"""Benchmark: MSM energy+force evaluations per second on the 1,066,628-atom
+periodic water box (216.8 A, 0.15 M NaCl; a = 12 A, h = 2.5 A, quintic C1
+basis, C2 Taylor smoothing), mixed precision, with the plain FP64 GPU path
+measured beside it and the FP64 CPU oracle as the reference arm.
+
+One step = one whole evaluation (binning, short-range pairs, anterpolation,
+restriction + lattice cutoff on every level, top level, prolongation,
+interpolation + energy) on inputs already resident in HBM.  The L2 cache is
+flushed (a 512 MB write) between timed steps, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank evaluates its own replica (the single-system
+path does not shard); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import WORKLOADS  # noqa: E402
+
+METRIC = "MSM energy+force evals/sec at 1.07M atoms (mixed precision; FP64 GPU path beside it)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+N_SM, FP32_LANES, FP64_FMA_PER_SM_CLK = 152, 128, 2
+
+
+def load_peaks():
+    if os.path.exists(PEAKS_FILE):
+        p = json.load(open(PEAKS_FILE))
+        return p, "measured"
+    return FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def work_model(plan, n, box, cutoff, order):
+    """Algorithmic work per evaluation ('Work and traffic model')."""
+    V = box ** 3
+    rho = n / V
+    pairs = n * (4.0 / 3.0) * math.pi * cutoff ** 3 * rho       # ordered pairs within a
+    W3 = (order + 1) ** 3
+    taps = plan_taps(plan)
+    pts = [d[0] * d[1] * d[2] for d in plan.dims]
+    lat_pts = sum(pts[:-1])
+    return {
+        "short_range": {"flop": 31.0 * pairs, "bytes": 36.0 * n, "units": "%.4g ordered pairs" % pairs},
+        "lattice_cutoff": {"flop": 2.0 * taps * lat_pts, "bytes": 12.0 * lat_pts,
+                           "units": "%d points x %d taps" % (lat_pts, taps)},
+        "anterpolation": {"flop": 3.0 * W3 * n, "bytes": 32.0 * n + 8.0 * pts[0]},
+        "interpolation": {"flop": 8.0 * W3 * n, "bytes": 68.0 * n + 4.0 * pts[0]},
+        "binning": {"flop": 0.0, "bytes": 32.0 * n + 4 * 8.0 * n * 2 + 64.0 * n},
+    }
+
+
+def plan_taps(plan):
+    h = plan.h_eff
+    a = plan.params.cutoff
+    E = [int(math.ceil(2 * a / h[d])) for d in range(3)]
+    cnt = 0
+    for dz in range(-E[2], E[2] + 1):
+        for dy in range(-E[1], E[1] + 1):
+            for dx in range(-E[0], E[0] + 1):
+                if (dx * h[0]) ** 2 + (dy * h[1]) ** 2 + (dz * h[2]) ** 2 < (2 * a) ** 2:
+                    cnt += 1
+    return cnt
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle as O
+    w = WORKLOADS[args.workload]
+    pos, q = w.make()
+    P = O.Params(box=(w.box,) * 3, periodic=w.periodic, cutoff=w.cutoff, spacing=w.spacing,
+                 levels=w.levels, order=w.order, split=w.split)
+    O.lib()
+    cores = os.cpu_count()
+    times = []
+    # each step is one whole evaluation; steps stop once 150 s are spent so the
+    # run ends within a few minutes whatever --steps asks
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        O.msm(P, pos, q)
+        times.append(time.perf_counter() - t0)
+        if sum(times) > 150.0:
+            break
+    v = len(times) / sum(times)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
+        "steps": len(times), "warmup": 0, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "atoms": w.n_atoms},
+        "cpu_baseline": {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d whole evaluation(s) of the %d-atom system" % (len(times), w.n_atoms)},
+        "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def cpu_baseline(w, budget_s=30.0):
+    """One whole oracle evaluation of the same system on the host cores."""
+    import oracle as O
+    pos, q = w.make()
+    P = O.Params(box=(w.box,) * 3, periodic=w.periodic, cutoff=w.cutoff, spacing=w.spacing,
+                 levels=w.levels, order=w.order, split=w.split)
+    O.lib()
+    t0 = time.perf_counter()
+    O.msm(P, pos, q)
+    t = time.perf_counter() - t0
+    return {"value": 1.0 / t, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "1 whole evaluation of the %d-atom system (%.1f s)" % (w.n_atoms, t)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="water1m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1402_7216_gb300 import MSM
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = WORKLOADS[args.workload]
+    pos_h, q_h = w.make()
+    n = len(q_h)
+    pos = torch.tensor(pos_h, device=dev)
+    q = torch.tensor(q_h, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def make(precision):
+        return MSM(box=w.box, periodic=w.periodic, cutoff=w.cutoff, spacing=w.spacing, levels=w.levels,
+                   order=w.order, splitting=w.split, precision=precision, max_atoms=n)
+
+    def timed(plan, steps, warmup, profile=False):
+        E = torch.empty((), dtype=torch.float64, device=dev)
+        phi = torch.empty(n, dtype=torch.float64, device=dev)
+        F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        for _ in range(warmup):
+            plan.eval(pos, q, out=(E, phi, F))
+        torch.cuda.synchronize()
+        plan.check_status()
+        plan.profile_read()
+        if profile:
+            plan.profile(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.fill_(1.0)                     # L2 flush, outside the timed events
+            a.record(stream)
+            plan.eval(pos, q, out=(E, phi, F))
+            b.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        plan.profile(False)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        prof = plan.profile_read()
+        plan.check_status()
+        return ms, prof, (E.item(), phi, F)
+
+    # mixed precision (the headline)
+    plan = make("mixed")
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, (stage_ms, launches, evals), (E_mix, phi_mix, F_mix) = timed(plan, args.steps, max(3, args.warmup), True)
+    clk = clocks.stop()
+    tot = sum(ms)
+    if world > 1:
+        t = torch.tensor([tot], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = t.item()
+    value = world * args.steps / (tot / 1e3)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    pos_pin = torch.tensor(pos_h).pin_memory()
+    q_pin = torch.tensor(q_h).pin_memory()
+    for _ in range(2):
+        plan.eval_host(pos_pin, q_pin)
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(max(3, args.steps // 3)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.eval_host(pos_pin, q_pin)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_tot = sum(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_tot], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_tot = t.item()
+    e2e_value = world * len(e2e_t) / e2e_tot
+
+    # plain FP64 GPU path at the same parameters, and the mixed path's error against it
+    fp64 = None
+    if not args.no_fp64:
+        plan64 = make("fp64")
+        ms64, prof64, (E64, phi64, F64) = timed(plan64, max(3, args.steps // 6), 2, True)
+        fp64 = {"value": len(ms64) / (sum(ms64) / 1e3), "unit": "evals/s",
+                "ms_per_step": sum(ms64) / len(ms64),
+                "stage_ms": {k: v / prof64[2] for k, v in prof64[0].items()}}
+        Fm, Fd = F_mix.double(), F64.double()
+        fp64["mixed_vs_fp64"] = {
+            "energy_rel": abs(E_mix - E64) / abs(E64),
+            "force_rel_rms": float(torch.sqrt(((Fm - Fd) ** 2).sum() / (Fd ** 2).sum())),
+            "phi_rel_rms": float(torch.sqrt(((phi_mix - phi64) ** 2).sum() / (phi64 ** 2).sum()))}
+        plan64.close()
+
+    if rank != 0:
+        return
+    peaks, peak_kind = load_peaks()
+    hbm = peaks.get("hbm_gbs", FALLBACK["hbm_gbs"])
+    sm_max = peaks.get("sm_max_mhz", FALLBACK["sm_max_mhz"])
+    fp32_peak = N_SM * FP32_LANES * 2 * sm_max * 1e6 / 1e12       # TFLOP/s, FMA = 2 flop
+    per_eval = {k: v / evals for k, v in stage_ms.items()}
+    model = work_model(plan, n, w.box, w.cutoff, w.order)
+    kernels = {}
+    for k, v in per_eval.items():
+        e = {"ms": v}
+        if k in model and v > 0:
+            e["gflop_s"] = model[k]["flop"] / (v * 1e-3) / 1e9
+            e["hbm_gb_s_algorithmic"] = model[k]["bytes"] / (v * 1e-3) / 1e9
+            e["frac_fp32_peak"] = e["gflop_s"] / (fp32_peak * 1e3)
+            e["frac_hbm_peak"] = e["hbm_gb_s_algorithmic"] / hbm
+        kernels[k] = e
+    dom = max(per_eval, key=per_eval.get)
+    if dom in ("short_range", "lattice_cutoff", "anterpolation", "interpolation"):
+        ach = model[dom]["flop"] / (per_eval[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": None,
+                "peak_source": "FP32 FMA peak: %d SMs x %d lanes x 2 flop x %.0f MHz (%s sm_max_mhz)"
+                               % (N_SM, FP32_LANES, sm_max, peak_kind),
+                "work_per_launch": model[dom].get("units")}
+    else:
+        ach = model.get(dom, {"bytes": 0})["bytes"] / (per_eval[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None}
+    out = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (pairs, grids) + f64 (top level, energy)",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "atoms": n, "box_A": w.box, "cutoff_A": w.cutoff,
+                   "spacing_A": w.spacing, "h_eff_A": plan.h_eff[0], "order": w.order,
+                   "splitting": w.split, "levels": plan.levels, "grid0": plan.dims[0],
+                   "precision": "mixed", "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 32 * n,
+                "d2h_bytes_per_step": 8, "api": "msm_eval_host (pinned host buffers)"},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernels_ms_per_eval": kernels,
+        "fp64_gpu_path": fp64,
+        "clocks": clk,
+        "energy": E_mix,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(out))
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/*
+ * msm.h -- C ABI of the GB300 multilevel summation (MSM) library.
+ *
+ * One call evaluates Coulomb electrostatics of N point charges by the
+ * multilevel summation method of the thesis proposal "Large-Scale Molecular
+ * Dynamics Simulations for Highly Parallel Infrastructures" (Pazurikova,
+ * 2014), Sec. "Multilevel Summation Method": the kernel 1/r is split as
+ * g* + g^0 + ... + g^{l-1} (Eq. msmgrid) with the Taylor smoothing gamma;
+ * the short-range part g* is summed over atom pairs within the cutoff a; the
+ * rest goes through anterpolation, restriction, a lattice cutoff per level,
+ * an all-pairs top level, prolongation and interpolation; the potential is
+ * U_i = k_c (u_i^short + u_i^long) and the forces are F_i = -dU/dr_i
+ * (Sec. "Simulation loop").
+ *
+ * Conventions shared by every entry point:
+ *   - Units are the caller's: positions in the unit of box/cutoff/spacing
+ *     (Angstrom in the tests), charges in e; energies come out in
+ *     coulomb_k * charge^2 / length.
+ *   - Device pointers are CUDA device addresses on the current device.
+ *     Arrays are dense, C order: pos and force are [n][3] (x, y, z of one
+ *     atom adjacent), q and phi are [n].
+ *   - The caller owns every input and output buffer; the plan owns its
+ *     workspace (sorted atoms, grids, tables) and frees it in msm_destroy.
+ *   - Evaluation calls are asynchronous on the given CUDA stream (NULL = the
+ *     legacy default stream) and never synchronise the host.  Errors that can
+ *     only be seen on the device (an atom outside an open box, a non-finite
+ *     input) are posted to a device status word that msm_status reads.
+ *   - A plan is not thread-safe: calls on one plan must be ordered (one
+ *     stream, or the caller's own synchronisation).
+ *   - Every function returns MSM_OK (0) or a negative MSM_ERR_* code.
+ */
+#ifndef MSM_GB300_H
+#define MSM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSM_OK 0
+#define MSM_ERR_INVALID_ARG (-1)        /* bad parameter, NULL pointer, n < 0 */
+#define MSM_ERR_UNSUPPORTED (-2)        /* valid but not built (e.g. box too small for the cell walk) */
+#define MSM_ERR_CUTOFF_GT_HALF_BOX (-3) /* periodic box with a > L/2 (minimum image fails) */
+#define MSM_ERR_ATOM_OUTSIDE_BOX (-4)   /* open box: an atom outside [0, L] (device-detected) */
+#define MSM_ERR_NONFINITE (-5)          /* NaN/Inf position or charge (device-detected) */
+#define MSM_ERR_OOM (-6)                /* device allocation failed */
+#define MSM_ERR_CUDA (-7)               /* a CUDA runtime call failed */
+#define MSM_ERR_TIMEOUT (-8)            /* a bounded device wait gave up */
+#define MSM_ERR_TOO_MANY_ATOMS (-9)     /* n > max_atoms of the plan */
+#define MSM_ERR_NO_FORWARD (-10)        /* backward called before a forward on this plan */
+
+#define MSM_FP64 0  /* every step in double precision */
+#define MSM_MIXED 1 /* pairs and grids in FP32 with compensated sums; top level and energy in FP64 */
+
+typedef struct msm_plan* msm_handle;
+
+/* Parameters of one MSM configuration (Sec. "Multilevel Summation Method"). */
+typedef struct {
+  double box[3];    /* box edges L_x, L_y, L_z; open boxes require 0 <= x <= L per coordinate */
+  int periodic;     /* 1: periodic in x, y and z; 0: open boundaries */
+  double cutoff;    /* a: cutoff of the short-range kernel g*; level k reaches 2^(k+1) a */
+  double spacing;   /* h: finest grid spacing (periodic: an upper bound, h_eff = L/M0 <= h) */
+  int levels;       /* l: number of grids; 0 picks it (top grid <= 8 points per dimension) */
+  int order;        /* p: interpolation degree, 3 (cubic, C1) or 5 (quintic, C1) */
+  int splitting;    /* m: Taylor smoothing order of gamma, 1 (C1), 2 (C2, printed), 3 (C3) */
+  int precision;    /* MSM_FP64 or MSM_MIXED */
+  double coulomb_k; /* prefactor k_c (1/(4 pi eps0) in caller units); 1.0 gives e^2/length */
+  int64_t max_atoms;/* capacity of the plan's workspace */
+} msm_params;
+
+/* Builds a plan: validates params, fixes the grid geometry, builds the
+ * level stencil and the top-level kernel (FP64, host) and allocates device
+ * workspace for max_atoms atoms on the current device.  Synchronous.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUTOFF_GT_HALF_BOX, OOM, CUDA. */
+int msm_create(const msm_params* params, msm_handle* out);
+
+/* Frees the plan and its device workspace (synchronises the device). */
+void msm_destroy(msm_handle h);
+
+/* Grid geometry of the plan: h_eff[3] (finest spacing per dimension), the
+ * level count, and for level k the point counts dims[3k..3k+2] and the first
+ * absolute index lo[3k..3k+2] (0 for periodic grids; grid point i of level k
+ * sits at i * 2^k * h_eff).  dims and lo may be NULL, else hold 3*levels ints. */
+int msm_query(msm_handle h, double h_eff[3], int* levels, int* dims, int* lo);
+
+/* One energy+force evaluation (the forward pass).
+ *   pos    [n][3] double, device; periodic positions may lie anywhere (they are
+ *          folded into the box), open ones must lie in [0, L].
+ *   q      [n] double, device.
+ *   energy [1] double, device: E = 1/2 sum_i q_i phi_i.
+ *   phi    [n] double, device or NULL: phi_i = dE/dq_i.
+ *   force  [n][3] double, device or NULL: F_i = -dE/dr_i.
+ * The plan keeps the sorted atoms and per-atom grid terms of this call for a
+ * following msm_eval_backward.  Errors: INVALID_ARG, TOO_MANY_ATOMS, CUDA;
+ * ATOM_OUTSIDE_BOX and NONFINITE later through msm_status. */
+int msm_eval(msm_handle h, int64_t n, const double* pos, const double* q, double* energy,
+             double* phi, double* force, void* cuda_stream);
+
+/* Adjoint of the last msm_eval on this plan: given the upstream gradient
+ * grad_energy = dL/dE ([1] double, device), writes grad_pos = dL/dr ([n][3])
+ * and grad_q = dL/dq ([n]); either output may be NULL.  The long-range part
+ * is evaluated by the transposed grid passes (interpolation^T =
+ * anterpolation, prolongation^T = restriction, the symmetric lattice and top
+ * kernels); the short-range part reuses the forward pair sums.  Positions
+ * and charges must be those of the last msm_eval.
+ * Errors: INVALID_ARG, NO_FORWARD, CUDA. */
+int msm_eval_backward(msm_handle h, const double* grad_energy, double* grad_pos, double* grad_q,
+                      void* cuda_stream);
+
+/* Same as msm_eval with HOST buffers: copies pos and q to the device, runs
+ * the evaluation on the stream, copies energy (and phi/force when non-NULL)
+ * back and synchronises the stream before returning.  Pinned host memory
+ * makes the copies asynchronous to the host thread; pageable memory works.
+ * Device-detected errors are returned directly. */
+int msm_eval_host(msm_handle h, int64_t n, const double* pos, const double* q, double* energy,
+                  double* phi, double* force, void* cuda_stream);
+
+/* Synchronises the plan's last stream and returns the first device-posted
+ * error since the previous msm_status call (or MSM_OK), then clears it. */
+int msm_status(msm_handle h);
+
+/* Copies one grid of the last evaluation to HOST memory, as doubles in the
+ * layout [dims_z][dims_y][dims_x] of msm_query: which = 0 the charges q^k,
+ * which = 1 the potential u^k (after prolongation; level l-1: top level).
+ * Synchronous.  For tests and diagnostics. */
+int msm_debug_grid(msm_handle h, int level, int which, double* host_out);
+
+/* Stages of one evaluation, in launch order (for msm_profile_read). */
+#define MSM_STAGE_BINNING 0       /* cell keys, radix sort, cell starts, gather */
+#define MSM_STAGE_SHORT_RANGE 1   /* g* pair sums */
+#define MSM_STAGE_ANTERPOLATION 2
+#define MSM_STAGE_RESTRICTION 3   /* all levels */
+#define MSM_STAGE_LATTICE 4       /* lattice cutoff, all levels */
+#define MSM_STAGE_TOP 5
+#define MSM_STAGE_PROLONGATION 6  /* all levels */
+#define MSM_STAGE_INTERPOLATION 7 /* interpolation, assembly, energy reduction */
+#define MSM_NSTAGES 8
+
+/* Diagnostics: enable != 0 makes every following msm_eval and
+ * msm_eval_backward record a CUDA event pair around each stage on its stream
+ * (events only, no synchronisation).  Disabling keeps what was recorded. */
+int msm_profile(msm_handle h, int enable);
+
+/* Synchronises the recorded events and returns, since the previous read:
+ * ms[MSM_NSTAGES] the summed device time of each stage (may be NULL),
+ * *launches the number of kernels and memset nodes the library enqueued and
+ * *evals the number of evaluations (either may be NULL); then resets. */
+int msm_profile_read(msm_handle h, double* ms, int64_t* launches, int64_t* evals);
+
+/* Name of a stage (e.g. "short_range"); "?" when out of range. */
+const char* msm_stage_name(int stage);
+
+/* Human-readable name of an MSM_ERR_* code. */
+const char* msm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSM_GB300_H */

@@ -1,0 +1,186 @@
+"""GB300-native multilevel summation (MSM) energy+force evaluation.
+
+Thin Python binding over the C ABI of ``include/msm.h``: every step of an
+evaluation runs in the CUDA kernels of ``libmsm_gb300.so``; PyTorch only
+provides device memory and the stream.  The method follows Sec. "Multilevel
+Summation Method" of the thesis proposal "Large-Scale Molecular Dynamics
+Simulations for Highly Parallel Infrastructures" (Pazurikova, 2014).
+
+    plan = MSM(box=(62.2,)*3, periodic=True, cutoff=10.0, spacing=2.0, order=3)
+    E, phi, F = plan.eval(pos, q)        # pos [N,3], q [N]: float64 CUDA tensors
+    E = MSMEnergy.apply(pos, q, plan)    # differentiable: dE/dpos = -F, dE/dq = phi
+"""
+import ctypes as C
+
+import torch
+
+from . import _capi
+from ._capi import MSMError, MSM_FP64, MSM_MIXED  # noqa: F401
+
+__all__ = ["MSM", "MSMEnergy", "MSMError", "MSM_FP64", "MSM_MIXED", "lib"]
+
+
+def lib():
+    return _capi.load()
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(None)
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+class MSM:
+    """One MSM configuration (plan) on the current CUDA device.
+
+    box: edges (L_x, L_y, L_z); periodic: bool; cutoff: a; spacing: h;
+    levels: l (0 = automatic); order: 3 cubic / 5 quintic; splitting: Taylor
+    order m of gamma (1, 2, 3); precision: "fp64" or "mixed"; coulomb_k:
+    prefactor; max_atoms: capacity of the workspace.
+    """
+
+    def __init__(self, box, periodic, cutoff, spacing, levels=0, order=3, splitting=2,
+                 precision="mixed", coulomb_k=1.0, max_atoms=1 << 20):
+        L = lib()
+        p = _capi.MSMParams()
+        b = box if hasattr(box, "__len__") else (box, box, box)
+        for d in range(3):
+            p.box[d] = float(b[d])
+        p.periodic = int(bool(periodic))
+        p.cutoff = float(cutoff)
+        p.spacing = float(spacing)
+        p.levels = int(levels)
+        p.order = int(order)
+        p.splitting = int(splitting)
+        p.precision = {"fp64": MSM_FP64, "mixed": MSM_MIXED}[precision]
+        p.coulomb_k = float(coulomb_k)
+        p.max_atoms = int(max_atoms)
+        self.params = p
+        self.precision = precision
+        self._h = C.c_void_p()
+        self._last_n = None
+        _capi.check(L.msm_create(C.byref(p), C.byref(self._h)), "msm_create")
+        heff = (C.c_double * 3)()
+        nl = C.c_int()
+        dims = (C.c_int * (3 * _capi.MAX_LEVELS))()
+        lo = (C.c_int * (3 * _capi.MAX_LEVELS))()
+        _capi.check(L.msm_query(self._h, heff, C.byref(nl), dims, lo), "msm_query")
+        self.h_eff = tuple(heff)
+        self.levels = nl.value
+        self.dims = [tuple(dims[3 * k:3 * k + 3]) for k in range(self.levels)]
+        self.lo = [tuple(lo[3 * k:3 * k + 3]) for k in range(self.levels)]
+
+    def close(self):
+        if self._h:
+            lib().msm_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _check_inputs(pos, q):
+        if not (pos.is_cuda and q.is_cuda):
+            raise ValueError("pos and q must be CUDA tensors")
+        if pos.dtype != torch.float64 or q.dtype != torch.float64:
+            raise ValueError("pos and q must be float64")
+        if pos.dim() != 2 or pos.shape[1] != 3 or q.shape != (pos.shape[0],):
+            raise ValueError("pos must be [N,3] and q [N]")
+        return pos.contiguous(), q.contiguous()
+
+    def eval(self, pos, q, want_phi=True, want_force=True, stream=None, out=None):
+        """Forward pass: returns (E [0-d], phi [N] or None, F [N,3] or None)."""
+        pos, q = self._check_inputs(pos, q)
+        n = pos.shape[0]
+        if out is None:
+            E = torch.empty((), dtype=torch.float64, device=pos.device)
+            phi = torch.empty(n, dtype=torch.float64, device=pos.device) if want_phi else None
+            F = torch.empty((n, 3), dtype=torch.float64, device=pos.device) if want_force else None
+        else:
+            E, phi, F = out
+        rc = lib().msm_eval(self._h, n, _ptr(pos), _ptr(q), _ptr(E), _ptr(phi), _ptr(F), _stream(stream))
+        _capi.check(rc, "msm_eval")
+        self._last_n = n
+        return E, phi, F
+
+    def backward(self, grad_E, want_pos=True, want_q=True, stream=None):
+        """Adjoint of the last eval: returns (dL/dpos [N,3], dL/dq [N])."""
+        n = self._last_n
+        if n is None:
+            raise MSMError(-10, "msm_eval_backward")
+        dev = grad_E.device
+        gp = torch.empty((n, 3), dtype=torch.float64, device=dev) if want_pos else None
+        gq = torch.empty(n, dtype=torch.float64, device=dev) if want_q else None
+        g = grad_E.to(torch.float64).reshape(()).contiguous()
+        rc = lib().msm_eval_backward(self._h, _ptr(g), _ptr(gp), _ptr(gq), _stream(stream))
+        _capi.check(rc, "msm_eval_backward")
+        return gp, gq
+
+    def eval_host(self, pos, q, want_phi=False, want_force=False, stream=None):
+        """End-to-end call with HOST (CPU) buffers: copies in, evaluates,
+        copies the energy (and phi/F when asked) out, synchronises."""
+        if pos.is_cuda or q.is_cuda:
+            raise ValueError("eval_host takes CPU tensors")
+        pos = pos.to(torch.float64).contiguous()
+        q = q.to(torch.float64).contiguous()
+        n = pos.shape[0]
+        E = torch.empty((), dtype=torch.float64, pin_memory=pos.is_pinned())
+        phi = torch.empty(n, dtype=torch.float64, pin_memory=pos.is_pinned()) if want_phi else None
+        F = torch.empty((n, 3), dtype=torch.float64, pin_memory=pos.is_pinned()) if want_force else None
+        rc = lib().msm_eval_host(self._h, n, _ptr(pos), _ptr(q), _ptr(E), _ptr(phi), _ptr(F),
+                                 _stream(stream))
+        _capi.check(rc, "msm_eval_host")
+        return E, phi, F
+
+    def profile(self, enable=True):
+        """Records per-stage CUDA events around every following evaluation."""
+        _capi.check(lib().msm_profile(self._h, int(bool(enable))), "msm_profile")
+
+    def profile_read(self):
+        """Returns ({stage: ms}, launches, evals) accumulated since the last read."""
+        ms = (C.c_double * _capi.NSTAGES)()
+        nl, ne = C.c_int64(), C.c_int64()
+        _capi.check(lib().msm_profile_read(self._h, ms, C.byref(nl), C.byref(ne)), "msm_profile_read")
+        names = [lib().msm_stage_name(i).decode() for i in range(_capi.NSTAGES)]
+        return dict(zip(names, list(ms))), nl.value, ne.value
+
+    def status(self):
+        return lib().msm_status(self._h)
+
+    def check_status(self):
+        _capi.check(self.status(), "device status")
+
+    def debug_grid(self, level, which):
+        """Copy of a grid of the last evaluation (which: 'q' or 'u'), as a
+        float64 CPU tensor [nz, ny, nx]."""
+        import numpy as np
+        nx, ny, nz = self.dims[level]
+        out = np.zeros((nz, ny, nx))
+        rc = lib().msm_debug_grid(self._h, int(level), {"q": 0, "u": 1}[which],
+                                  out.ctypes.data_as(C.POINTER(C.c_double)))
+        _capi.check(rc, "msm_debug_grid")
+        return out
+
+
+class MSMEnergy(torch.autograd.Function):
+    """E(pos, q) with a hand-written adjoint: backward runs the transposed
+    grid passes of the library (msm_eval_backward)."""
+
+    @staticmethod
+    def forward(ctx, pos, q, plan):
+        E, _, _ = plan.eval(pos.detach(), q.detach(), want_phi=False, want_force=False)
+        plan._last_n = pos.shape[0]
+        ctx.plan = plan
+        return E
+
+    @staticmethod
+    def backward(ctx, grad_E):
+        gp, gq = ctx.plan.backward(grad_E, want_pos=ctx.needs_input_grad[0],
+                                   want_q=ctx.needs_input_grad[1])
+        return gp, gq, None

@@ -1,0 +1,83 @@
+"""ctypes declarations of the C ABI in include/msm.h (argument marshalling only).
+
+The shared library is built in-tree (``paper_1402_7216_gb300/build.py``); if it
+is missing this module raises instead of falling back to anything else.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmsm_gb300.so")
+
+MSM_OK = 0
+ERRORS = {
+    -1: "MSM_ERR_INVALID_ARG", -2: "MSM_ERR_UNSUPPORTED", -3: "MSM_ERR_CUTOFF_GT_HALF_BOX",
+    -4: "MSM_ERR_ATOM_OUTSIDE_BOX", -5: "MSM_ERR_NONFINITE", -6: "MSM_ERR_OOM", -7: "MSM_ERR_CUDA",
+    -8: "MSM_ERR_TIMEOUT", -9: "MSM_ERR_TOO_MANY_ATOMS", -10: "MSM_ERR_NO_FORWARD",
+}
+MSM_FP64, MSM_MIXED = 0, 1
+MAX_LEVELS = 16
+
+
+class MSMParams(C.Structure):
+    _fields_ = [("box", C.c_double * 3), ("periodic", C.c_int), ("cutoff", C.c_double),
+                ("spacing", C.c_double), ("levels", C.c_int), ("order", C.c_int),
+                ("splitting", C.c_int), ("precision", C.c_int), ("coulomb_k", C.c_double),
+                ("max_atoms", C.c_int64)]
+
+
+class MSMError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s%s (%d)" % (what + ": " if what else "", ERRORS.get(code, "unknown"), code))
+
+
+_lib = None
+_D = C.POINTER(C.c_double)
+EXPORTS = ["msm_create", "msm_destroy", "msm_query", "msm_eval", "msm_eval_backward",
+           "msm_eval_host", "msm_status", "msm_debug_grid", "msm_profile", "msm_profile_read",
+           "msm_stage_name", "msm_strerror"]
+NSTAGES = 8
+
+
+def load(path=LIB_PATH):
+    """Loads the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libmsm_gb300.so is not built (run __graft_entry__.build() or "
+                          "python paper_1402_7216_gb300/build.py); there is no fallback")
+    L = C.CDLL(path)
+    vp = C.c_void_p
+    L.msm_create.argtypes = [C.POINTER(MSMParams), C.POINTER(vp)]
+    L.msm_create.restype = C.c_int
+    L.msm_destroy.argtypes = [vp]
+    L.msm_destroy.restype = None
+    L.msm_query.argtypes = [vp, _D, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.msm_query.restype = C.c_int
+    L.msm_eval.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp]
+    L.msm_eval.restype = C.c_int
+    L.msm_eval_backward.argtypes = [vp, vp, vp, vp, vp]
+    L.msm_eval_backward.restype = C.c_int
+    L.msm_eval_host.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp]
+    L.msm_eval_host.restype = C.c_int
+    L.msm_status.argtypes = [vp]
+    L.msm_status.restype = C.c_int
+    L.msm_debug_grid.argtypes = [vp, C.c_int, C.c_int, _D]
+    L.msm_debug_grid.restype = C.c_int
+    L.msm_profile.argtypes = [vp, C.c_int]
+    L.msm_profile.restype = C.c_int
+    L.msm_profile_read.argtypes = [vp, _D, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.msm_profile_read.restype = C.c_int
+    L.msm_stage_name.argtypes = [C.c_int]
+    L.msm_stage_name.restype = C.c_char_p
+    L.msm_strerror.argtypes = [C.c_int]
+    L.msm_strerror.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def check(code, what=""):
+    if code != MSM_OK:
+        raise MSMError(code, what)

@@ -1,0 +1,265 @@
+// capi.cu -- the extern "C" entry points declared in include/msm.h.
+// Each evaluation is a fixed sequence of kernel launches on the caller's
+// stream (no host synchronisation, no allocation), in the order of the
+// method: binning, short-range pairs, anterpolation, restriction and lattice
+// cutoff per level, top level, prolongation, interpolation and assembly.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "msm_internal.h"
+
+using namespace msm;
+
+struct msm_plan {
+  Plan p;
+};
+
+namespace {
+
+int decode_status(int bits) {
+  if (bits & kStatusNonfinite) return MSM_ERR_NONFINITE;
+  if (bits & kStatusOutside) return MSM_ERR_ATOM_OUTSIDE_BOX;
+  if (bits & kStatusTimeout) return MSM_ERR_TIMEOUT;
+  return MSM_OK;
+}
+
+// Runs one stage launcher; with profiling on, brackets it with an event pair
+// from the plan's pool (events only: no synchronisation).
+template <typename F>
+cudaError_t stage(Plan& P, int which, cudaStream_t st, F&& launch) {
+  if (!P.profiling) return launch();
+  if (P.nrec == P.recs.size()) {
+    Plan::StageRec r;
+    r.stage = which;
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess)
+      return cudaErrorMemoryAllocation;
+    P.recs.push_back(r);
+  }
+  Plan::StageRec& r = P.recs[P.nrec++];
+  r.stage = which;
+  cudaEventRecord(r.a, st);
+  cudaError_t e = launch();
+  cudaEventRecord(r.b, st);
+  return e;
+}
+
+// The grid sweep shared by the forward pass and its adjoint: starting from
+// the level-0 charges in q[0], fills q[1..l-1] by restriction, u[k] by the
+// lattice cutoff and the top level, then prolongates u down to level 0.
+cudaError_t grid_sweep(Plan& P, void* const* q, void* const* u, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  int l = P.levels;
+  for (int k = 0; k + 1 < l && e == cudaSuccess; ++k) {
+    e = stage(P, MSM_STAGE_RESTRICTION, st, [&] { return launch_restrict(P, k, q[k], q[k + 1], st); });
+    if (e == cudaSuccess)
+      e = stage(P, MSM_STAGE_LATTICE, st, [&] { return launch_lattice(P, k, q[k], u[k], st); });
+  }
+  if (e == cudaSuccess) e = stage(P, MSM_STAGE_TOP, st, [&] { return launch_top(P, q[l - 1], u[l - 1], st); });
+  for (int k = l - 2; k >= 0 && e == cudaSuccess; --k)
+    e = stage(P, MSM_STAGE_PROLONGATION, st, [&] { return launch_prolong(P, k, u[k + 1], u[k], st); });
+  return e;
+}
+
+int forward(Plan& P, int64_t n, const double* pos, const double* q, double* energy, double* phi,
+            double* force, cudaStream_t st) {
+  cudaError_t e = stage(P, MSM_STAGE_BINNING, st, [&] { return launch_binning(P, n, pos, q, st); });
+  if (e == cudaSuccess) e = stage(P, MSM_STAGE_SHORT_RANGE, st, [&] { return launch_short_range(P, n, st); });
+  if (e == cudaSuccess)
+    e = stage(P, MSM_STAGE_ANTERPOLATION, st,
+              [&] { return launch_anterpolate(P, n, P.d.gq[0], nullptr, 1.0, st); });
+  if (e == cudaSuccess) e = grid_sweep(P, P.d.gq, P.d.gu, st);
+  if (e == cudaSuccess)
+    e = stage(P, MSM_STAGE_INTERPOLATION, st,
+              [&] { return launch_interp_forward(P, n, energy, phi, force, st); });
+  if (e != cudaSuccess) return MSM_ERR_CUDA;
+  P.last_stream = st;
+  P.last_n = n;
+  P.evals += 1;
+  return MSM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int msm_create(const msm_params* params, msm_handle* out) {
+  if (!params || !out) return MSM_ERR_INVALID_ARG;
+  *out = nullptr;
+  msm_plan* h = new (std::nothrow) msm_plan();
+  if (!h) return MSM_ERR_OOM;
+  int rc = build_plan(params, &h->p);
+  if (rc != MSM_OK) {
+    free_plan(&h->p);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return MSM_OK;
+}
+
+void msm_destroy(msm_handle h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  for (auto& r : h->p.recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  free_plan(&h->p);
+  delete h;
+}
+
+int msm_query(msm_handle h, double h_eff[3], int* levels, int* dims, int* lo) {
+  if (!h) return MSM_ERR_INVALID_ARG;
+  const Plan& P = h->p;
+  if (h_eff)
+    for (int d = 0; d < 3; ++d) h_eff[d] = P.h[d];
+  if (levels) *levels = P.levels;
+  for (int k = 0; k < P.levels; ++k)
+    for (int d = 0; d < 3; ++d) {
+      if (dims) dims[3 * k + d] = P.n[k][d];
+      if (lo) lo[3 * k + d] = P.lo[k][d];
+    }
+  return MSM_OK;
+}
+
+int msm_eval(msm_handle h, int64_t n, const double* pos, const double* q, double* energy, double* phi,
+             double* force, void* stream) {
+  if (!h || n < 0 || !energy || (n > 0 && (!pos || !q))) return MSM_ERR_INVALID_ARG;
+  Plan& P = h->p;
+  if (n > P.cap) return MSM_ERR_TOO_MANY_ATOMS;
+  return forward(P, n, pos, q, energy, phi, force, (cudaStream_t)stream);
+}
+
+int msm_eval_backward(msm_handle h, const double* grad_energy, double* grad_pos, double* grad_q,
+                      void* stream) {
+  if (!h || !grad_energy) return MSM_ERR_INVALID_ARG;
+  Plan& P = h->p;
+  if (P.last_n < 0) return MSM_ERR_NO_FORWARD;
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t n = P.last_n;
+  // adjoint of u_long = A^T M A q with respect to its inputs: anterpolate the
+  // adjoint of u_long (1/2 dL/dE q_i), sweep the (symmetric) grid operator,
+  // and interpolate the result back to the atoms.
+  cudaError_t e = stage(P, MSM_STAGE_ANTERPOLATION, st,
+                        [&] { return launch_anterpolate(P, n, P.d.aq[0], grad_energy, 0.5, st); });
+  if (e == cudaSuccess) e = grid_sweep(P, P.d.aq, P.d.au, st);
+  if (e == cudaSuccess)
+    e = stage(P, MSM_STAGE_INTERPOLATION, st,
+              [&] { return launch_interp_backward(P, n, grad_energy, grad_pos, grad_q, st); });
+  if (e != cudaSuccess) return MSM_ERR_CUDA;
+  P.last_stream = st;
+  return MSM_OK;
+}
+
+int msm_eval_host(msm_handle h, int64_t n, const double* pos, const double* q, double* energy, double* phi,
+                  double* force, void* stream) {
+  if (!h || n < 0 || !energy || (n > 0 && (!pos || !q))) return MSM_ERR_INVALID_ARG;
+  Plan& P = h->p;
+  if (n > P.cap) return MSM_ERR_TOO_MANY_ATOMS;
+  DeviceBuffers& D = P.d;
+  if (!D.hpos) {  // staging buffers for the host-buffer entry point, made on first use
+    cudaError_t e = cudaMalloc((void**)&D.hpos, sizeof(double) * 3 * P.cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&D.hq, sizeof(double) * P.cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&D.hphi, sizeof(double) * P.cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&D.hforce, sizeof(double) * 3 * P.cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&D.henergy, sizeof(double));
+    if (e != cudaSuccess) return MSM_ERR_OOM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n > 0) {
+    if (cudaMemcpyAsync(D.hpos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(D.hq, q, sizeof(double) * n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return MSM_ERR_CUDA;
+  }
+  int rc = forward(P, n, D.hpos, D.hq, D.henergy, phi ? D.hphi : nullptr, force ? D.hforce : nullptr, st);
+  if (rc != MSM_OK) return rc;
+  if (cudaMemcpyAsync(energy, D.henergy, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return MSM_ERR_CUDA;
+  if (phi && n > 0 && cudaMemcpyAsync(phi, D.hphi, sizeof(double) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return MSM_ERR_CUDA;
+  if (force && n > 0 &&
+      cudaMemcpyAsync(force, D.hforce, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return MSM_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MSM_ERR_CUDA;
+  return msm_status(h);
+}
+
+int msm_status(msm_handle h) {
+  if (!h) return MSM_ERR_INVALID_ARG;
+  Plan& P = h->p;
+  if (cudaStreamSynchronize(P.last_stream) != cudaSuccess) return MSM_ERR_CUDA;
+  int bits = 0;
+  if (cudaMemcpy(&bits, P.d.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MSM_ERR_CUDA;
+  if (bits && cudaMemset(P.d.status, 0, sizeof(int)) != cudaSuccess) return MSM_ERR_CUDA;
+  return decode_status(bits);
+}
+
+int msm_debug_grid(msm_handle h, int level, int which, double* host_out) {
+  if (!h || !host_out || level < 0 || which < 0 || which > 1) return MSM_ERR_INVALID_ARG;
+  Plan& P = h->p;
+  if (level >= P.levels) return MSM_ERR_INVALID_ARG;
+  int64_t np = grid_points(P, level);
+  double* tmp = nullptr;
+  if (cudaMalloc((void**)&tmp, sizeof(double) * np) != cudaSuccess) return MSM_ERR_OOM;
+  cudaStream_t st = P.last_stream;
+  const void* src = which == 0 ? P.d.gq[level] : P.d.gu[level];
+  cudaError_t e = launch_grid_to_double(P, src, tmp, np, which == 0, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpy(host_out, tmp, sizeof(double) * np, cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  return e == cudaSuccess ? MSM_OK : MSM_ERR_CUDA;
+}
+
+int msm_profile(msm_handle h, int enable) {
+  if (!h) return MSM_ERR_INVALID_ARG;
+  h->p.profiling = enable != 0;
+  return MSM_OK;
+}
+
+int msm_profile_read(msm_handle h, double* ms, int64_t* launches, int64_t* evals) {
+  if (!h) return MSM_ERR_INVALID_ARG;
+  Plan& P = h->p;
+  double acc[MSM_NSTAGES] = {0};
+  for (size_t i = 0; i < P.nrec; ++i) {
+    Plan::StageRec& r = P.recs[i];
+    float t = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess)
+      return MSM_ERR_CUDA;
+    if (r.stage >= 0 && r.stage < MSM_NSTAGES) acc[r.stage] += t;
+  }
+  if (ms)
+    for (int s = 0; s < MSM_NSTAGES; ++s) ms[s] = acc[s];
+  if (launches) *launches = P.launches;
+  if (evals) *evals = P.evals;
+  P.nrec = 0;
+  P.launches = 0;
+  P.evals = 0;
+  return MSM_OK;
+}
+
+const char* msm_stage_name(int s) {
+  static const char* names[MSM_NSTAGES] = {"binning", "short_range", "anterpolation", "restriction",
+                                           "lattice_cutoff", "top_level", "prolongation",
+                                           "interpolation"};
+  return (s >= 0 && s < MSM_NSTAGES) ? names[s] : "?";
+}
+
+const char* msm_strerror(int code) {
+  switch (code) {
+    case MSM_OK: return "ok";
+    case MSM_ERR_INVALID_ARG: return "invalid argument";
+    case MSM_ERR_UNSUPPORTED: return "unsupported configuration";
+    case MSM_ERR_CUTOFF_GT_HALF_BOX: return "cutoff larger than half the periodic box";
+    case MSM_ERR_ATOM_OUTSIDE_BOX: return "atom outside the open box";
+    case MSM_ERR_NONFINITE: return "non-finite position or charge";
+    case MSM_ERR_OOM: return "device allocation failed";
+    case MSM_ERR_CUDA: return "CUDA error";
+    case MSM_ERR_TIMEOUT: return "bounded device wait gave up";
+    case MSM_ERR_TOO_MANY_ATOMS: return "more atoms than the plan's capacity";
+    case MSM_ERR_NO_FORWARD: return "backward before forward";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

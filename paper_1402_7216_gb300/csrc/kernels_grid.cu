@@ -1,0 +1,700 @@
+// kernels_grid.cu -- the long-range steps of MSM (Sec. "Multilevel Summation
+// Method"), in the order the thesis lists them:
+//   anterpolation   q^0_mu = sum_j phi^0_mu(r_j) q_j
+//   restriction     q^{k+1}_mu = sum_nu phi^{k+1}_mu(r^k_nu) q^k_nu
+//   lattice cutoff  u^{k,cutoff}_mu = sum_nu g^k(r^k_mu, r^k_nu) q^k_nu
+//   top level       u^{l-1}_mu = sum_nu g^{l-1}(r_mu, r_nu) q^{l-1}_nu (all pairs)
+//   prolongation    u^k_mu = u^{k,cutoff}_mu + sum_nu phi^{k+1}_nu(r^k_mu) u^{k+1}_nu
+//   interpolation   u_i^long = sum_mu phi^0_mu(r_i) u^0_mu (and its gradient)
+// with phi^k_mu = Phi(x)Phi(y)Phi(z) on spacing 2^k h, Phi the C1 cubic
+// (numerical Hermite) or C1 quintic interpolant.  Grids are dense arrays,
+// x fastest.  The adjoint (backward) pass reuses the same kernels: the
+// transpose of interpolation is anterpolation, the transpose of prolongation
+// is restriction, and the lattice and top kernels are symmetric.
+#include <cmath>
+
+#include "msm_internal.h"
+
+namespace msm {
+
+namespace {
+
+// ---- nodal basis Phi ----
+// Piece j of Phi covers |d| in [j, j+1]; it is written as a polynomial in the
+// local coordinate u = |d| - j in [0, 1], where every coefficient is small,
+// so FP32 evaluation keeps full relative accuracy (expanding in |d| instead
+// would cancel terms up to ~60 against weights of ~0.01).
+//   cubic   P0 = 1 - 5/2 u^2 + 3/2 u^3          P1 = -u (1 - u)^2 / 2
+//   quintic Q0 = (1 - u^2)(2 - u)(6 + 3u - 5u^2)/12
+//           Q1 = u (u - 1)(u - 2)(5u^2 + u - 8)/24
+//           Q2 = -(u + 1) u (u - 1)^2 (u - 2)/24
+template <typename T, int ORDER>
+struct Basis;
+
+template <typename T>
+struct Basis<T, 3> {
+  static constexpr int S = 2;
+  __device__ static T p(int j, T u) {
+    return j == 0 ? T(1) + u * u * (T(-2.5) + T(1.5) * u) : u * (T(-0.5) + u * (T(1) - T(0.5) * u));
+  }
+  __device__ static T dp(int j, T u) {
+    return j == 0 ? u * (T(-5) + T(4.5) * u) : T(-0.5) + u * (T(2) - T(1.5) * u);
+  }
+};
+
+template <typename T>
+struct Basis<T, 5> {
+  static constexpr int S = 3;
+  __device__ static T p(int j, T u) {
+    if (j == 0)
+      return T(1) + u * u * (T(-25.0 / 12) + u * (T(5.0 / 12) + u * (T(13.0 / 12) - T(5.0 / 12) * u)));
+    if (j == 1)
+      return u * (T(-16.0 / 24) + u * (T(26.0 / 24) + u * (T(-1.0 / 24) + u * (T(-14.0 / 24) + T(5.0 / 24) * u))));
+    return u * (T(2.0 / 24) + u * (T(-3.0 / 24) + u * (T(-1.0 / 24) + u * (T(3.0 / 24) - T(1.0 / 24) * u))));
+  }
+  __device__ static T dp(int j, T u) {
+    if (j == 0)
+      return u * (T(-50.0 / 12) + u * (T(15.0 / 12) + u * (T(52.0 / 12) - T(25.0 / 12) * u)));
+    if (j == 1)
+      return T(-16.0 / 24) + u * (T(52.0 / 24) + u * (T(-3.0 / 24) + u * (T(-56.0 / 24) + T(25.0 / 24) * u)));
+    return T(2.0 / 24) + u * (T(-6.0 / 24) + u * (T(-3.0 / 24) + u * (T(12.0 / 24) - T(5.0 / 24) * u)));
+  }
+};
+
+// Weights of the 2S support points base + s (s = 0..2S-1) for an atom at
+// fractional offset f in [0,1) past grid point base + S - 1.  The signed
+// distance to point s is d = f + S - 1 - s: piece S-1-s at u = f for s < S,
+// piece s-S at u = 1 - f beyond.
+template <typename T, int ORDER>
+__device__ __forceinline__ void weights(T f, T* w) {
+  constexpr int S = Basis<T, ORDER>::S;
+  const T g = T(1) - f;
+#pragma unroll
+  for (int s = 0; s < 2 * S; ++s)
+    w[s] = (s < S) ? Basis<T, ORDER>::p(S - 1 - s, f) : Basis<T, ORDER>::p(s - S, g);
+}
+
+// dPhi/dd at the same points (d > 0 for s < S, d < 0 beyond).
+template <typename T, int ORDER>
+__device__ __forceinline__ void dweights(T f, T* w) {
+  constexpr int S = Basis<T, ORDER>::S;
+  const T g = T(1) - f;
+#pragma unroll
+  for (int s = 0; s < 2 * S; ++s)
+    w[s] = (s < S) ? Basis<T, ORDER>::dp(S - 1 - s, f) : -Basis<T, ORDER>::dp(s - S, g);
+}
+
+struct GridDims {
+  int n[3];
+  int lo[3];
+  int periodic;
+};
+
+__device__ __forceinline__ int slot(int idx, int n, int lo, int periodic) {
+  if (periodic) {
+    int r = idx % n;
+    return r < 0 ? r + n : r;
+  }
+  return idx - lo;  // callers only pass indices inside the open grid
+}
+
+// ---- anterpolation: atom-centric scatter with float/double atomics ----
+template <typename T, int ORDER>
+__global__ void k_anterp(const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, int n,
+                         double* __restrict__ grid, GridDims G, const double* __restrict__ dscale,
+                         double factor) {
+  constexpr int W = 2 * Basis<T, ORDER>::S;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const R4<T> f = gfrac[i];
+  const int4 b = gbase[i];
+  double sc = factor * (dscale ? *dscale : 1.0);
+  const T qi = T(sc) * f.w;
+  T wx[W], wy[W], wz[W];
+  weights<T, ORDER>(f.x, wx);
+  weights<T, ORDER>(f.y, wy);
+  weights<T, ORDER>(f.z, wz);
+  int ix[W], iy[W], iz[W];
+#pragma unroll
+  for (int s = 0; s < W; ++s) {
+    ix[s] = slot(b.x + s, G.n[0], G.lo[0], G.periodic);
+    iy[s] = slot(b.y + s, G.n[1], G.lo[1], G.periodic);
+    iz[s] = slot(b.z + s, G.n[2], G.lo[2], G.periodic);
+  }
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    const T qz = qi * wz[c];
+#pragma unroll
+    for (int bb = 0; bb < W; ++bb) {
+      const T qyz = qz * wy[bb];
+      double* row = grid + ((size_t)iz[c] * G.n[1] + iy[bb]) * G.n[0];
+#pragma unroll
+      for (int a = 0; a < W; ++a) atomicAdd(row + ix[a], (double)(qyz * wx[a]));
+    }
+  }
+}
+
+// ---- restriction: one thread per coarse point, nonzero taps only ----
+// 1-D weights Phi(d/2): cubic d = 0, +-1, +-3 -> 1, 9/16, -1/16;
+// quintic d = 0, +-1, +-3, +-5 -> 1, 75/128, -25/256, 3/256.
+template <int ORDER>
+struct RWeights;
+template <>
+struct RWeights<3> {
+  static constexpr int N = 5;
+  __device__ static int d(int t) { return t == 0 ? 0 : (t == 1 ? 1 : (t == 2 ? -1 : (t == 3 ? 3 : -3))); }
+  __device__ static double w(int t) { return t == 0 ? 1.0 : (t <= 2 ? 9.0 / 16 : -1.0 / 16); }
+};
+template <>
+struct RWeights<5> {
+  static constexpr int N = 7;
+  __device__ static int d(int t) {
+    return t == 0 ? 0 : (t == 1 ? 1 : (t == 2 ? -1 : (t == 3 ? 3 : (t == 4 ? -3 : (t == 5 ? 5 : -5)))));
+  }
+  __device__ static double w(int t) {
+    return t == 0 ? 1.0 : (t <= 2 ? 75.0 / 128 : (t <= 4 ? -25.0 / 256 : 3.0 / 256));
+  }
+};
+
+template <typename T, int ORDER>
+__global__ void k_restrict(const T* __restrict__ fine, T* __restrict__ coarse, GridDims F, GridDims C) {
+  // instantiated with T = double: charge grids stay in FP64 in every precision mode
+  constexpr int N = RWeights<ORDER>::N;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t np = (int64_t)C.n[0] * C.n[1] * C.n[2];
+  if (t >= np) return;
+  int cx = (int)(t % C.n[0]), cy = (int)((t / C.n[0]) % C.n[1]), cz = (int)(t / ((int64_t)C.n[0] * C.n[1]));
+  int mu[3] = {C.lo[0] + cx, C.lo[1] + cy, C.lo[2] + cz};
+  int sx[N], sy[N], sz[N];
+  T w[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    w[k] = T(RWeights<ORDER>::w(k));
+    int d = RWeights<ORDER>::d(k);
+    int v[3] = {2 * mu[0] + d, 2 * mu[1] + d, 2 * mu[2] + d};
+    int s3[3];
+    for (int e = 0; e < 3; ++e) {
+      if (F.periodic) {
+        s3[e] = slot(v[e], F.n[e], 0, 1);
+      } else {
+        int s = v[e] - F.lo[e];
+        s3[e] = (s >= 0 && s < F.n[e]) ? s : -1;
+      }
+    }
+    sx[k] = s3[0];
+    sy[k] = s3[1];
+    sz[k] = s3[2];
+  }
+  T sum = 0;
+  for (int c = 0; c < N; ++c) {
+    if (sz[c] < 0) continue;
+    for (int b = 0; b < N; ++b) {
+      if (sy[b] < 0) continue;
+      const T* row = fine + ((size_t)sz[c] * F.n[1] + sy[b]) * F.n[0];
+      T part = 0;
+#pragma unroll
+      for (int a = 0; a < N; ++a)
+        if (sx[a] >= 0) part += w[a] * row[sx[a]];
+      sum += w[c] * w[b] * part;
+    }
+  }
+  coarse[t] = sum;
+}
+
+// ---- prolongation: fine point gathers the coarse points that reach it ----
+template <typename T, int ORDER>
+__global__ void k_prolong(const T* __restrict__ coarse, T* __restrict__ fine, GridDims F, GridDims C) {
+  constexpr int S = (ORDER + 1) / 2;
+  constexpr int MX = S * 2;  // at most 2S nonzero coarse neighbours per dimension (odd points)
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t np = (int64_t)F.n[0] * F.n[1] * F.n[2];
+  if (t >= np) return;
+  int f[3] = {(int)(t % F.n[0]), (int)((t / F.n[0]) % F.n[1]), (int)(t / ((int64_t)F.n[0] * F.n[1]))};
+  int cs[3][MX];
+  T cw[3][MX];
+  int cn[3];
+  for (int e = 0; e < 3; ++e) {
+    int nu = F.lo[e] + f[e];
+    cn[e] = 0;
+    // coarse mu with nu - 2 mu = d, d odd in [-(2S-1), 2S-1] or d = 0
+    for (int d = -(2 * S - 1); d <= 2 * S - 1; ++d) {
+      if (((nu - d) & 1) != 0) continue;
+      if (d != 0 && (d & 1) == 0) continue;  // Phi(+-1), Phi(+-2) vanish
+      int mu = (nu - d) / 2;
+      int s;
+      if (C.periodic) {
+        s = slot(mu, C.n[e], 0, 1);
+      } else {
+        s = mu - C.lo[e];
+        if (s < 0 || s >= C.n[e]) continue;
+      }
+      int ad = d < 0 ? -d : d;
+      double w = (ad == 0) ? 1.0
+                 : (ORDER == 3 ? (ad == 1 ? 9.0 / 16 : -1.0 / 16)
+                               : (ad == 1 ? 75.0 / 128 : (ad == 3 ? -25.0 / 256 : 3.0 / 256)));
+      cs[e][cn[e]] = s;
+      cw[e][cn[e]] = T(w);
+      ++cn[e];
+    }
+  }
+  T sum = 0;
+  for (int c = 0; c < cn[2]; ++c)
+    for (int b = 0; b < cn[1]; ++b) {
+      const T* row = coarse + ((size_t)cs[2][c] * C.n[1] + cs[1][b]) * C.n[0];
+      T part = 0;
+      for (int a = 0; a < cn[0]; ++a) part += cw[0][a] * row[cs[0][a]];
+      sum += cw[2][c] * cw[1][b] * part;
+    }
+  fine[t] += sum;
+}
+
+// ---- lattice cutoff: z-streaming shared-memory planes, register tiles ----
+// A block of 4 warps owns a 32 x 16 x 4 brick of outputs; warp w owns plane
+// z0 + w, and each lane 8 consecutive x outputs in rows y and y + 8.  The
+// input planes z0 - Ez .. z0 + 3 + Ez are staged in turn (a 2-D window with
+// halo Ex, Ey); for staged plane zi, warp w applies the stencil rows of
+// dz = zi - (z0 + w) as segments of 8 taps along x: 8 x 8 x 2 FMAs per
+// segment from 2 x 15 shared loads.  Per-plane partial sums are folded into
+// the totals with TwoSum in mixed precision.
+constexpr int LBX = 32, LBY = 16, LBZ = 4, LPX = 8;
+
+template <typename T>
+__device__ __forceinline__ void two_sum_add(T& s, T& c, T x) {
+  T t = s + x;
+  T bp = t - s;
+  c += (s - (t - bp)) + (x - bp);
+  s = t;
+}
+
+template <typename T, bool COMP>
+__global__ void __launch_bounds__(128) k_lattice(const double* __restrict__ q, T* __restrict__ u, GridDims G,
+                                                 const Segment<T>* __restrict__ seg,
+                                                 const int* __restrict__ seg_start, int Ex, int Ey, int Ez,
+                                                 T scale) {
+  extern __shared__ unsigned char smem_raw[];
+  T* plane = reinterpret_cast<T*>(smem_raw);
+  const int SXw = LBX + 2 * Ex + kSeg;   // staged width
+  const int SX = SXw | 1;                // odd row pitch: conflict-free rows
+  const int SY = LBY + 2 * Ey;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tx = lane & 3, ty = lane >> 2;
+  const int x0 = blockIdx.x * LBX, y0 = blockIdx.y * LBY, z0 = blockIdx.z * LBZ;
+  const int zo = z0 + warp;
+  T acc[2][LPX], cmp[2][LPX];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int j = 0; j < LPX; ++j) acc[r][j] = cmp[r][j] = T(0);
+
+  for (int zi = z0 - Ez; zi < z0 + LBZ + Ez; ++zi) {
+    __syncthreads();
+    // stage plane zi (wrapped or zero outside an open grid)
+    int gz;
+    bool zok;
+    if (G.periodic) {
+      gz = zi % G.n[2];
+      if (gz < 0) gz += G.n[2];
+      zok = true;
+    } else {
+      gz = zi;
+      zok = (zi >= 0 && zi < G.n[2]);
+    }
+    for (int e = tid; e < SY * SXw; e += 128) {
+      int xx = e % SXw, yy = e / SXw;
+      int gx = x0 - Ex + xx, gy = y0 - Ey + yy;
+      T v = T(0);
+      if (G.periodic) {
+        gx %= G.n[0];
+        if (gx < 0) gx += G.n[0];
+        gy %= G.n[1];
+        if (gy < 0) gy += G.n[1];
+        v = (T)q[((size_t)gz * G.n[1] + gy) * G.n[0] + gx];
+      } else if (zok && gx >= 0 && gx < G.n[0] && gy >= 0 && gy < G.n[1]) {
+        v = (T)q[((size_t)gz * G.n[1] + gy) * G.n[0] + gx];
+      }
+      plane[yy * SX + xx] = v;
+    }
+    __syncthreads();
+    const int dz = zi - zo;
+    if (dz < -Ez || dz > Ez || zo >= G.n[2]) continue;  // warp-uniform
+    T part[2][LPX];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int j = 0; j < LPX; ++j) part[r][j] = T(0);
+    const int s1 = seg_start[dz + Ez + 1];
+    for (int s = seg_start[dz + Ez]; s < s1; ++s) {
+      const Segment<T> sg = seg[s];
+      const int xb = tx * LPX + Ex + sg.dx0;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const T* row = plane + (ty + 8 * r + Ey + sg.dy) * SX + xb;
+        T win[LPX + kSeg - 1];
+#pragma unroll
+        for (int k = 0; k < LPX + kSeg - 1; ++k) win[k] = row[k];
+#pragma unroll
+        for (int k = 0; k < kSeg; ++k)
+#pragma unroll
+          for (int j = 0; j < LPX; ++j) part[r][j] += sg.g[k] * win[j + k];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int j = 0; j < LPX; ++j) {
+        if (COMP) two_sum_add(acc[r][j], cmp[r][j], part[r][j]);
+        else acc[r][j] += part[r][j];
+      }
+  }
+  if (zo >= G.n[2]) return;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    int y = y0 + ty + 8 * r;
+    if (y >= G.n[1]) continue;
+#pragma unroll
+    for (int j = 0; j < LPX; ++j) {
+      int x = x0 + tx * LPX + j;
+      if (x < G.n[0]) u[((size_t)zo * G.n[1] + y) * G.n[0] + x] = scale * (acc[r][j] + cmp[r][j]);
+    }
+  }
+}
+
+// ---- top level: all pairs of the coarsest grid, FP64 ----
+template <typename T>
+__global__ void k_top(const double* __restrict__ qt, T* __restrict__ ut, double* __restrict__ ut64,
+                      GridDims G, const double* __restrict__ K, int tx, int ty, int tz) {
+  int64_t np = (int64_t)G.n[0] * G.n[1] * G.n[2];
+  int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= np) return;
+  int mx = (int)(m % G.n[0]), my = (int)((m / G.n[0]) % G.n[1]), mz = (int)(m / ((int64_t)G.n[0] * G.n[1]));
+  double sum = 0.0;
+  for (int vz = 0; vz < G.n[2]; ++vz) {
+    int dz = G.periodic ? (mz - vz + G.n[2]) % G.n[2] : mz - vz + G.n[2] - 1;
+    for (int vy = 0; vy < G.n[1]; ++vy) {
+      int dy = G.periodic ? (my - vy + G.n[1]) % G.n[1] : my - vy + G.n[1] - 1;
+      const double* Krow = K + ((size_t)dz * ty + dy) * tx;
+      const double* qrow = qt + ((size_t)vz * G.n[1] + vy) * G.n[0];
+      for (int vx = 0; vx < G.n[0]; ++vx) {
+        int dx = G.periodic ? (mx - vx + G.n[0]) % G.n[0] : mx - vx + G.n[0] - 1;
+        sum += Krow[dx] * qrow[vx];
+      }
+    }
+  }
+  ut[m] = (T)sum;
+  ut64[m] = sum;
+  (void)tz;
+}
+
+// ---- interpolation at the atoms and assembly (forward) ----
+template <typename T, int ORDER>
+__device__ __forceinline__ void interp_atom(const R4<T>& f, const int4& b, const T* __restrict__ u0,
+                                            const GridDims& G, const T inv_h[3], T& p, T g[3]) {
+  constexpr int W = 2 * Basis<T, ORDER>::S;
+  T wx[W], wy[W], wz[W], dx[W], dy[W], dz[W];
+  weights<T, ORDER>(f.x, wx);
+  weights<T, ORDER>(f.y, wy);
+  weights<T, ORDER>(f.z, wz);
+  dweights<T, ORDER>(f.x, dx);
+  dweights<T, ORDER>(f.y, dy);
+  dweights<T, ORDER>(f.z, dz);
+  int ix[W], iy[W], iz[W];
+#pragma unroll
+  for (int s = 0; s < W; ++s) {
+    ix[s] = slot(b.x + s, G.n[0], G.lo[0], G.periodic);
+    iy[s] = slot(b.y + s, G.n[1], G.lo[1], G.periodic);
+    iz[s] = slot(b.z + s, G.n[2], G.lo[2], G.periodic);
+  }
+  T P = 0, Gx = 0, Gy = 0, Gz = 0;
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    T pz = 0, gxz = 0, gyz = 0;
+#pragma unroll
+    for (int bb = 0; bb < W; ++bb) {
+      const T* row = u0 + ((size_t)iz[c] * G.n[1] + iy[bb]) * G.n[0];
+      T sa = 0, sd = 0;
+#pragma unroll
+      for (int a = 0; a < W; ++a) {
+        T v = __ldg(row + ix[a]);
+        sa += wx[a] * v;
+        sd += dx[a] * v;
+      }
+      pz += wy[bb] * sa;
+      gxz += wy[bb] * sd;
+      gyz += dy[bb] * sa;
+    }
+    P += wz[c] * pz;
+    Gx += wz[c] * gxz;
+    Gy += wz[c] * gyz;
+    Gz += dz[c] * pz;
+  }
+  p = P;
+  g[0] = Gx * inv_h[0];
+  g[1] = Gy * inv_h[1];
+  g[2] = Gz * inv_h[2];
+}
+
+template <int BLOCK>
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[BLOCK / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = (lane < BLOCK / 32) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  return s;  // valid in thread 0
+}
+
+struct AssembleArgs {
+  double self_c;  // gamma(0)/a
+  double kc;      // Coulomb prefactor
+  double inv_h[3];
+};
+
+template <typename T, int ORDER>
+__global__ void __launch_bounds__(256) k_interp_fwd(
+    const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm, int n,
+    const T* __restrict__ u0, GridDims G, AssembleArgs A, const T* __restrict__ phis,
+    R4<T>* __restrict__ fs, R4<T>* __restrict__ glong, double* __restrict__ phi_out,
+    double* __restrict__ force_out, double* __restrict__ partial) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (i < n) {
+    const R4<T> f = gfrac[i];
+    const T ih[3] = {T(A.inv_h[0]), T(A.inv_h[1]), T(A.inv_h[2])};
+    T p, g[3];
+    interp_atom<T, ORDER>(f, gbase[i], u0, G, ih, p, g);
+    R4<T> s = fs[i];
+    const double qi = (double)f.w;
+    const double phi = A.kc * ((double)phis[i] + (double)p - qi * A.self_c);
+    const int o = perm[i];
+    if (phi_out) phi_out[o] = phi;
+    if (force_out) {
+      force_out[3 * (size_t)o + 0] = A.kc * ((double)s.x - qi * (double)g[0]);
+      force_out[3 * (size_t)o + 1] = A.kc * ((double)s.y - qi * (double)g[1]);
+      force_out[3 * (size_t)o + 2] = A.kc * ((double)s.z - qi * (double)g[2]);
+    }
+    s.w = p;
+    fs[i] = s;
+    glong[i] = R4<T>{g[0], g[1], g[2], T(0)};
+    e = qi * phi;
+  }
+  double bsum = block_sum<256>(e);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bsum;
+}
+
+__global__ void __launch_bounds__(1024) k_energy_final(const double* __restrict__ partial, int nb,
+                                                       double* __restrict__ energy) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 1024) v += partial[i];
+  double s = block_sum<1024>(v);
+  if (threadIdx.x == 0) *energy = 0.5 * s;
+}
+
+// adjoint assembly: av0 = M (anterpolated 1/2 gE q) on the grid
+template <typename T, int ORDER>
+__global__ void __launch_bounds__(256) k_interp_bwd(
+    const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm, int n,
+    const T* __restrict__ av0, GridDims G, AssembleArgs A, const T* __restrict__ phis,
+    const R4<T>* __restrict__ fs, const R4<T>* __restrict__ glong, const double* __restrict__ gE,
+    double* __restrict__ grad_pos, double* __restrict__ grad_q) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const R4<T> f = gfrac[i];
+  const T ih[3] = {T(A.inv_h[0]), T(A.inv_h[1]), T(A.inv_h[2])};
+  T v, gv[3];
+  interp_atom<T, ORDER>(f, gbase[i], av0, G, ih, v, gv);
+  const R4<T> s = fs[i];
+  const R4<T> gl = glong[i];
+  const double g = *gE, qi = (double)f.w;
+  const int o = perm[i];
+  if (grad_q)
+    grad_q[o] = A.kc * (g * ((double)phis[i] - qi * A.self_c) + 0.5 * g * (double)s.w + (double)v);
+  if (grad_pos) {
+    grad_pos[3 * (size_t)o + 0] = A.kc * (-g * (double)s.x + 0.5 * g * qi * (double)gl.x + qi * (double)gv[0]);
+    grad_pos[3 * (size_t)o + 1] = A.kc * (-g * (double)s.y + 0.5 * g * qi * (double)gl.y + qi * (double)gv[1]);
+    grad_pos[3 * (size_t)o + 2] = A.kc * (-g * (double)s.z + 0.5 * g * qi * (double)gl.z + qi * (double)gv[2]);
+  }
+}
+
+template <typename T>
+__global__ void k_to_double(const T* __restrict__ src, double* __restrict__ dst, int64_t count) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) dst[i] = (double)src[i];
+}
+
+GridDims dims_of(const Plan& P, int k) {
+  GridDims G;
+  for (int d = 0; d < 3; ++d) {
+    G.n[d] = P.n[k][d];
+    G.lo[d] = P.lo[k][d];
+  }
+  G.periodic = P.P.periodic;
+  return G;
+}
+
+AssembleArgs assemble_args(const Plan& P) {
+  AssembleArgs A;
+  A.self_c = P.gamma0 / P.P.cutoff;
+  A.kc = P.P.coulomb_k;
+  for (int d = 0; d < 3; ++d) A.inv_h[d] = 1.0 / P.h[d];
+  return A;
+}
+
+unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+cudaError_t launch_anterpolate(Plan& P, int64_t n, void* grid0, const double* dscale, double factor,
+                               cudaStream_t st) {
+  size_t bytes = sizeof(double) * (size_t)grid_points(P, 0);
+  cudaMemsetAsync(grid0, 0, bytes, st);
+  P.launches += 1 + (n > 0 ? 1 : 0);
+  if (n <= 0) return cudaGetLastError();
+  GridDims G = dims_of(P, 0);
+  unsigned nb = blocks_for(n, 256);
+  if (P.fp64) {
+    if (P.P.order == 3)
+      k_anterp<double, 3><<<nb, 256, 0, st>>>((const R4<double>*)P.d.gfrac, P.d.gbase, (int)n,
+                                              (double*)grid0, G, dscale, factor);
+    else
+      k_anterp<double, 5><<<nb, 256, 0, st>>>((const R4<double>*)P.d.gfrac, P.d.gbase, (int)n,
+                                              (double*)grid0, G, dscale, factor);
+  } else {
+    if (P.P.order == 3)
+      k_anterp<float, 3><<<nb, 256, 0, st>>>((const R4<float>*)P.d.gfrac, P.d.gbase, (int)n,
+                                             (double*)grid0, G, dscale, factor);
+    else
+      k_anterp<float, 5><<<nb, 256, 0, st>>>((const R4<float>*)P.d.gfrac, P.d.gbase, (int)n,
+                                             (double*)grid0, G, dscale, factor);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(Plan& P, int k, const void* fine, void* coarse, cudaStream_t st) {
+  P.launches += 1;
+  GridDims F = dims_of(P, k), C = dims_of(P, k + 1);
+  unsigned nb = blocks_for(grid_points(P, k + 1), 128);
+  if (P.P.order == 3) k_restrict<double, 3><<<nb, 128, 0, st>>>((const double*)fine, (double*)coarse, F, C);
+  else k_restrict<double, 5><<<nb, 128, 0, st>>>((const double*)fine, (double*)coarse, F, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(Plan& P, int k, const void* coarse, void* fine, cudaStream_t st) {
+  P.launches += 1;
+  GridDims F = dims_of(P, k), C = dims_of(P, k + 1);
+  unsigned nb = blocks_for(grid_points(P, k), 128);
+  if (P.fp64) {
+    if (P.P.order == 3) k_prolong<double, 3><<<nb, 128, 0, st>>>((const double*)coarse, (double*)fine, F, C);
+    else k_prolong<double, 5><<<nb, 128, 0, st>>>((const double*)coarse, (double*)fine, F, C);
+  } else {
+    if (P.P.order == 3) k_prolong<float, 3><<<nb, 128, 0, st>>>((const float*)coarse, (float*)fine, F, C);
+    else k_prolong<float, 5><<<nb, 128, 0, st>>>((const float*)coarse, (float*)fine, F, C);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lattice(Plan& P, int k, const void* qk, void* uk, cudaStream_t st) {
+  P.launches += 1;
+  GridDims G = dims_of(P, k);
+  dim3 grid(blocks_for(G.n[0], LBX), blocks_for(G.n[1], LBY), blocks_for(G.n[2], LBZ));
+  int SX = (LBX + 2 * P.E[0] + kSeg) | 1, SY = LBY + 2 * P.E[1];
+  double scale = std::ldexp(1.0, -k);
+  if (P.fp64) {
+    size_t sm = sizeof(double) * SX * SY;
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(k_lattice<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_set = true;
+    }
+    k_lattice<double, false><<<grid, 128, sm, st>>>((const double*)qk, (double*)uk, G,
+                                                    (const Segment<double>*)P.d.seg, P.d.seg_start, P.E[0],
+                                                    P.E[1], P.E[2], scale);
+  } else {
+    size_t sm = sizeof(float) * SX * SY;
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(k_lattice<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_set = true;
+    }
+    k_lattice<float, true><<<grid, 128, sm, st>>>((const double*)qk, (float*)uk, G,
+                                                  (const Segment<float>*)P.d.seg, P.d.seg_start, P.E[0],
+                                                  P.E[1], P.E[2], (float)scale);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_top(Plan& P, const void* qt, void* ut, cudaStream_t st) {
+  P.launches += 1;
+  int top = P.levels - 1;
+  GridDims G = dims_of(P, top);
+  unsigned nb = blocks_for(grid_points(P, top), 64);
+  if (P.fp64)
+    k_top<double><<<nb, 64, 0, st>>>((const double*)qt, (double*)ut, P.d.topu, G, P.d.topK,
+                                     P.top_table_dims[0], P.top_table_dims[1], P.top_table_dims[2]);
+  else
+    k_top<float><<<nb, 64, 0, st>>>((const double*)qt, (float*)ut, P.d.topu, G, P.d.topK,
+                                    P.top_table_dims[0], P.top_table_dims[1], P.top_table_dims[2]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, double* phi, double* force,
+                                  cudaStream_t st) {
+  GridDims G = dims_of(P, 0);
+  AssembleArgs A = assemble_args(P);
+  unsigned nb = blocks_for(n, 256);
+  if (n > 0) {
+#define MSM_FWD(T, O)                                                                                  \
+  k_interp_fwd<T, O><<<nb, 256, 0, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.idx[0], (int)n,      \
+                                         (const T*)P.d.gu[0], G, A, (const T*)P.d.phis, (R4<T>*)P.d.fs, \
+                                         (R4<T>*)P.d.glong, phi, force, P.d.partial)
+    if (P.fp64) {
+      if (P.P.order == 3) MSM_FWD(double, 3);
+      else MSM_FWD(double, 5);
+    } else {
+      if (P.P.order == 3) MSM_FWD(float, 3);
+      else MSM_FWD(float, 5);
+    }
+#undef MSM_FWD
+  }
+  k_energy_final<<<1, 1024, 0, st>>>(P.d.partial, n > 0 ? (int)nb : 0, energy);
+  P.launches += 1 + (n > 0 ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, double* grad_pos, double* grad_q,
+                                   cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  GridDims G = dims_of(P, 0);
+  AssembleArgs A = assemble_args(P);
+  unsigned nb = blocks_for(n, 256);
+  P.launches += 1;
+#define MSM_BWD(T, O)                                                                                 \
+  k_interp_bwd<T, O><<<nb, 256, 0, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.idx[0], (int)n,     \
+                                         (const T*)P.d.au[0], G, A, (const T*)P.d.phis,               \
+                                         (const R4<T>*)P.d.fs, (const R4<T>*)P.d.glong, gE, grad_pos, \
+                                         grad_q)
+  if (P.fp64) {
+    if (P.P.order == 3) MSM_BWD(double, 3);
+    else MSM_BWD(double, 5);
+  } else {
+    if (P.P.order == 3) MSM_BWD(float, 3);
+    else MSM_BWD(float, 5);
+  }
+#undef MSM_BWD
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grid_to_double(Plan& P, const void* src, double* dst, int64_t count, bool is_double,
+                                  cudaStream_t st) {
+  unsigned nb = blocks_for(count, 256);
+  if (count <= 0) return cudaSuccess;
+  if (P.fp64 || is_double) k_to_double<double><<<nb, 256, 0, st>>>((const double*)src, dst, count);
+  else k_to_double<float><<<nb, 256, 0, st>>>((const float*)src, dst, count);
+  return cudaGetLastError();
+}
+
+}  // namespace msm

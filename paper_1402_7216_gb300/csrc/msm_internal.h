@@ -1,0 +1,148 @@
+// msm_internal.h -- plan layout and kernel launchers of the GB300 MSM library.
+// Not part of the public ABI (include/msm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/msm.h"
+
+namespace msm {
+
+constexpr int kMaxLevels = 16;
+constexpr int kSeg = 8;           // taps per stencil segment (x direction)
+constexpr int kMaxCellOffsets = 125;
+
+// Status bits posted by kernels (atomicOr) and decoded by msm_status.
+constexpr int kStatusOutside = 1;
+constexpr int kStatusNonfinite = 2;
+constexpr int kStatusTimeout = 4;
+
+template <typename T>
+struct alignas(4 * sizeof(T)) R4 {
+  T x, y, z, w;
+};
+
+// One x-run of the level stencil: taps (dx0 + j, dy, dz), j = 0..kSeg-1,
+// with coefficients g[j] (zero past the end of the run).
+template <typename T>
+struct Segment {
+  int dy, dx0;
+  T g[kSeg];
+};
+
+// Per-precision device tables and buffers.
+struct DeviceBuffers {
+  // binning / sorting
+  int* keys[2] = {nullptr, nullptr};
+  int* idx[2] = {nullptr, nullptr};
+  int* hist = nullptr;
+  int* cell_start = nullptr;   // [ncell + 1]
+  // sorted atoms (type T = float or double, selected by precision)
+  void* atoms = nullptr;       // R4<T>[cap]: cell-local x, y, z and q
+  void* gfrac = nullptr;       // R4<T>[cap]: fractional grid offsets (0..1) and q
+  int4* gbase = nullptr;       // [cap]: first level-0 index of the basis support per dim
+  // per-atom results in sorted order
+  void* phis = nullptr;        // T[cap]  short-range potential
+  void* fs = nullptr;          // R4<T>[cap] short-range force (x, y, z) and long-range potential (w)
+  void* glong = nullptr;       // R4<T>[cap] long-range gradient (x, y, z), spare (w)
+  // grids, one per level: charges q^k in FP64, potentials u^k in T
+  void* gq[kMaxLevels] = {};
+  void* gu[kMaxLevels] = {};
+  // adjoint grids
+  void* aq[kMaxLevels] = {};
+  void* au[kMaxLevels] = {};
+  // top level (always FP64)
+  double* topK = nullptr;      // periodic: [M^3] circulant; open: [(2M-1)^3] Toeplitz
+  double* topq = nullptr;
+  double* topu = nullptr;
+  // level stencil
+  void* seg = nullptr;         // Segment<T>[nseg]
+  int* seg_start = nullptr;    // [2*Ez+2]: segments of plane dz live in [start[dz+Ez], start[dz+Ez+1])
+  // neighbour cell offsets (x, y, z) of the pair kernel
+  int4* cell_off = nullptr;    // [noff]
+  // reductions and status
+  double* partial = nullptr;   // per-block energy partials
+  double* scalars = nullptr;   // [8] scratch scalars (0: backward scale)
+  int* status = nullptr;
+  // host-path staging (msm_eval_host)
+  double* hpos = nullptr;
+  double* hq = nullptr;
+  double* hphi = nullptr;
+  double* hforce = nullptr;
+  double* henergy = nullptr;
+};
+
+struct Plan {
+  msm_params P;
+  bool fp64 = false;
+  int S = 2, W = 4;            // basis half support, taps per dimension
+  int levels = 1;
+  double h[3];                 // finest spacing
+  int lo[kMaxLevels][3];
+  int n[kMaxLevels][3];
+  // short-range cells
+  int nc[3];
+  double cw[3];
+  int ncell = 1;
+  int key_passes = 1;
+  int noff = 0;
+  // smoothing constants
+  double gamma0 = 0.0;         // gamma(0)
+  // level stencil
+  int E[3] = {0, 0, 0};        // largest |dx|, |dy|, |dz| of a tap
+  int nseg = 0;
+  double stencil_taps = 0.0;   // number of taps (for work accounting)
+  // top level
+  int top_table_dims[3];
+  // workspace
+  int64_t cap = 0;
+  int nblk_hist = 0;
+  int nblk_partial = 0;
+  DeviceBuffers d;
+  // state
+  cudaStream_t last_stream = nullptr;
+  int64_t last_n = -1;
+  int host_status = 0;
+  // diagnostics: stage event pairs (pool reused across reads), launch count
+  struct StageRec {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  bool profiling = false;
+  std::vector<StageRec> recs;
+  size_t nrec = 0;
+  int64_t launches = 0;
+  int64_t evals = 0;
+};
+
+// ---- host helpers (plan.cpp) ----
+int build_plan(const msm_params* p, Plan* plan);
+void free_plan(Plan* plan);
+int64_t grid_points(const Plan& P, int k);
+
+// ---- launchers (.cu files); all asynchronous on stream ----
+// binning: keys, stable radix sort by cell, cell_start, gather of sorted atoms
+cudaError_t launch_binning(Plan& P, int64_t n, const double* pos, const double* q, cudaStream_t s);
+// short-range pair sums (phis, fs.xyz)
+cudaError_t launch_short_range(Plan& P, int64_t n, cudaStream_t s);
+// grid passes: anterpolation (charges q_i * scale, scale from device or 1)
+cudaError_t launch_anterpolate(Plan& P, int64_t n, void* grid0, const double* dscale, double factor,
+                               cudaStream_t s);
+cudaError_t launch_restrict(Plan& P, int k, const void* fine, void* coarse, cudaStream_t s);
+cudaError_t launch_lattice(Plan& P, int k, const void* qk, void* uk, cudaStream_t s);
+cudaError_t launch_top(Plan& P, const void* qt, void* ut, cudaStream_t s);
+cudaError_t launch_prolong(Plan& P, int k, const void* coarse, void* fine, cudaStream_t s);
+// interpolation of u^0 at the atoms and assembly of E, phi, F (forward)
+cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, double* phi, double* force,
+                                  cudaStream_t s);
+// adjoint: interpolation of the adjoint grid and assembly of dL/dq, dL/dr
+cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, double* grad_pos,
+                                   double* grad_q, cudaStream_t s);
+// grid copy to double (debug)
+cudaError_t launch_grid_to_double(Plan& P, const void* src, double* dst, int64_t count, bool is_double,
+                                  cudaStream_t s);
+
+}  // namespace msm

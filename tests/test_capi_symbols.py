@@ -1,0 +1,65 @@
+"""CPU checks of the C ABI boundary: the CUDA library builds, loads and exports
+every entry point include/msm.h declares (no compute calls: no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "msm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(msm_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def library():
+    from paper_1402_7216_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ["msm_create", "msm_destroy", "msm_eval", "msm_eval_backward", "msm_eval_host",
+              "msm_status", "msm_query", "msm_strerror"]:
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(library):
+    for s in declared_symbols():
+        assert hasattr(library, s), s
+
+
+def test_binding_names_match_header():
+    from paper_1402_7216_gb300 import _capi
+    assert sorted(_capi.EXPORTS) == sorted(declared_symbols())
+
+
+def test_strerror_is_pure_host(library):
+    library.msm_strerror.restype = ctypes.c_char_p
+    assert library.msm_strerror(0) == b"ok"
+    assert b"capacity" in library.msm_strerror(-9)
+    assert library.msm_strerror(12345) == b"unknown error"
+
+
+def test_create_rejects_bad_parameters_without_a_gpu(library):
+    # parameter validation happens before any device call
+    from paper_1402_7216_gb300 import _capi
+    L = _capi.load()
+    h = ctypes.c_void_p()
+    p = _capi.MSMParams()
+    for d in range(3):
+        p.box[d] = 30.0
+    p.periodic, p.cutoff, p.spacing, p.order, p.splitting = 1, 10.0, 2.0, 4, 2
+    p.precision, p.coulomb_k, p.max_atoms = 1, 1.0, 100
+    assert L.msm_create(ctypes.byref(p), ctypes.byref(h)) == -1        # order 4
+    p.order = 3
+    p.cutoff = 16.0
+    assert L.msm_create(ctypes.byref(p), ctypes.byref(h)) == -3        # a > L/2
+    p.cutoff = 13.0
+    assert L.msm_create(ctypes.byref(p), ctypes.byref(h)) == -2        # fewer than 5 cells
+    assert L.msm_create(None, ctypes.byref(h)) == -1

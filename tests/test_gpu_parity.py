@@ -1,0 +1,269 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (per comparison, stated here once):
+  FP64 path  : energy rel 1e-10, force rel-RMS 1e-9, potential rel-RMS 1e-9.
+               Both sides run the same algorithm in double precision; only the
+               summation order (and, periodic, two independent Ewald builds of
+               the top-level kernel) differ.
+  mixed path : energy rel 1e-6, force rel-RMS 1e-5, potential rel-RMS 1e-6
+               (the accuracy targets for FP32 pair and grid sums with
+               compensated accumulation against the FP64 oracle).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from conftest import rel_rms
+from synth import make_water_box, spatial_subsample, WORKLOADS
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": dict(E=1e-10, F=1e-9, phi=1e-9), "mixed": dict(E=1e-6, F=1e-5, phi=1e-6)}
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_7216_gb300 import lib
+    lib()
+    return torch.device("cuda:0")
+
+
+def plan_for(cfg, precision, n, **kw):
+    from paper_1402_7216_gb300 import MSM
+    return MSM(box=cfg["box"], periodic=cfg["periodic"], cutoff=cfg["cutoff"], spacing=cfg["spacing"],
+               levels=cfg.get("levels", 0), order=cfg["order"], splitting=cfg["split"],
+               precision=precision, max_atoms=max(n, 1), **kw)
+
+
+def oparams(cfg):
+    b = cfg["box"]
+    return O.Params(box=(b, b, b) if np.isscalar(b) else tuple(b), periodic=cfg["periodic"],
+                    cutoff=cfg["cutoff"], spacing=cfg["spacing"], levels=cfg.get("levels", 0),
+                    order=cfg["order"], split=cfg["split"])
+
+
+def gpu_eval(plan, pos, q, dev):
+    E, phi, F = plan.eval(torch.tensor(pos, device=dev), torch.tensor(q, device=dev))
+    torch.cuda.synchronize()
+    plan.check_status()
+    return E.item(), phi.cpu().numpy(), F.cpu().numpy()
+
+
+def assert_close(got, ref, precision, what=""):
+    E, phi, F = got
+    t = TOL[precision]
+    if "E" in ref:
+        assert abs(E - ref["E"]) <= t["E"] * abs(ref["E"]), (what, E, ref["E"])
+    assert rel_rms(F, ref["F"]) <= t["F"], (what, rel_rms(F, ref["F"]))
+    assert rel_rms(phi, ref["phi"]) <= t["phi"], (what, rel_rms(phi, ref["phi"]))
+
+
+SMALL = [
+    dict(name="per-cubic-C2", box=24.0, periodic=True, cutoff=8.0, spacing=1.5, order=3, split=2),
+    dict(name="per-quintic-C2", box=24.0, periodic=True, cutoff=8.0, spacing=2.0, order=5, split=2),
+    dict(name="per-cubic-C1-l2", box=24.0, periodic=True, cutoff=6.0, spacing=2.0, order=3, split=1, levels=2),
+    dict(name="per-quintic-C3-l1", box=24.0, periodic=True, cutoff=6.0, spacing=2.0, order=5, split=3, levels=1),
+    dict(name="open-cubic-C2", box=24.0, periodic=False, cutoff=8.0, spacing=2.0, order=3, split=2),
+    dict(name="open-quintic-C1", box=24.0, periodic=False, cutoff=7.0, spacing=1.7, order=5, split=1),
+    dict(name="open-cubic-C3-l1", box=24.0, periodic=False, cutoff=6.0, spacing=2.0, order=3, split=3, levels=1),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("cfg", SMALL, ids=[c["name"] for c in SMALL])
+def test_small_systems_match_oracle(cfg, precision, dev):
+    pos, q = make_water_box(cfg["box"], 420, 3, 2, seed=21, periodic=cfg["periodic"])
+    ref = O.msm(oparams(cfg), pos, q)
+    plan = plan_for(cfg, precision, len(q))
+    assert plan.levels == ref["geometry"].levels
+    assert_close(gpu_eval(plan, pos, q, dev), ref, precision, cfg["name"])
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_staged_grids_match_oracle_fp64(periodic, dev):
+    cfg = dict(box=24.0, periodic=periodic, cutoff=6.0, spacing=1.5, order=5, split=2, levels=3)
+    pos, q = make_water_box(24.0, 300, 1, 1, seed=22, periodic=periodic)
+    ref = O.msm(oparams(cfg), pos, q, keep_grids=True)
+    plan = plan_for(cfg, "fp64", len(q))
+    gpu_eval(plan, pos, q, dev)
+    G = ref["geometry"]
+    for k in range(G.levels):
+        assert plan.dims[k] == G.n[k] and plan.lo[k] == G.lo[k]
+        for which, grids in [("q", ref["q_grids"]), ("u", ref["u_grids"])]:
+            g = plan.debug_grid(k, which)
+            r = grids[k]
+            scale = np.abs(r).max()
+            assert np.abs(g - r).max() <= 1e-11 * scale, (k, which, np.abs(g - r).max(), scale)
+
+
+def test_water3k_open_fp64_and_mixed(dev):
+    w = WORKLOADS["water3k_open"]
+    pos, q = w.make()
+    cfg = dict(box=w.box, periodic=False, cutoff=w.cutoff, spacing=w.spacing, order=w.order, split=w.split)
+    ref = O.msm(oparams(cfg), pos, q)
+    direct = O.direct_sum(pos, q)
+    for precision in ["fp64", "mixed"]:
+        got = gpu_eval(plan_for(cfg, precision, len(q)), pos, q, dev)
+        assert_close(got, ref, precision, precision)
+        # and the method's error against the exact Coulomb sum stays in the paper's band
+        assert rel_rms(got[2], direct["F"]) < 0.05
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_water23k_periodic(precision, dev):
+    w = WORKLOADS["water23k"]
+    pos, q = w.make()
+    cfg = dict(box=w.box, periodic=True, cutoff=w.cutoff, spacing=w.spacing, order=w.order, split=w.split)
+    ref = O.msm(oparams(cfg), pos, q)
+    plan = plan_for(cfg, precision, len(q))
+    assert plan.dims[0] == (32, 32, 32) and plan.levels == 3
+    assert_close(gpu_eval(plan, pos, q, dev), ref, precision)
+
+
+def test_edge_cases(dev):
+    cfg = dict(box=20.0, periodic=True, cutoff=6.0, spacing=2.0, order=3, split=2)
+    # no atoms
+    plan = plan_for(cfg, "mixed", 16)
+    E, _, _ = plan.eval(torch.zeros((0, 3), dtype=torch.float64, device=dev),
+                        torch.zeros(0, dtype=torch.float64, device=dev))
+    assert E.item() == 0.0
+    # one atom, two atoms, atoms exactly on grid points and on the periodic boundary
+    for pos in [np.array([[3.3, 4.4, 5.5]]),
+                np.array([[2.0, 4.0, 6.0], [18.0, 0.0, 20.0 - 1e-12]]),
+                np.array([[0.0, 0.0, 0.0], [2.0, 2.0, 2.0], [10.0, 12.0, 2.0], [19.999999, 8.0, 4.0]])]:
+        q = np.resize(np.array([1.0, -0.5, 0.25, -0.75]), len(pos))
+        ref = O.msm(oparams(cfg), pos, q)
+        for precision in ["fp64", "mixed"]:
+            got = gpu_eval(plan_for(cfg, precision, len(q)), pos, q, dev)
+            tol = TOL[precision]
+            # few atoms: the forces are tiny differences (e.g. a lone atom's grid
+            # self force), so they are compared on the scale of a unit-charge
+            # interaction at one grid spacing, 1/h^2
+            fscale = 1.0 / cfg["spacing"] ** 2
+            assert abs(got[0] - ref["E"]) <= tol["E"] * (abs(ref["E"]) + 1.0)
+            np.testing.assert_allclose(got[2], ref["F"], rtol=0, atol=tol["F"] * fscale)
+    # open box: atoms on the faces x = 0 and x = L
+    ocfg = dict(box=20.0, periodic=False, cutoff=6.0, spacing=2.0, order=5, split=2)
+    pos = np.array([[0.0, 0.0, 0.0], [20.0, 20.0, 20.0], [20.0, 0.0, 10.0], [4.0, 6.0, 8.0]])
+    q = np.array([1.0, -1.0, 0.5, -0.5])
+    ref = O.msm(oparams(ocfg), pos, q)
+    got = gpu_eval(plan_for(ocfg, "fp64", 4), pos, q, dev)
+    assert abs(got[0] - ref["E"]) <= 1e-10 * abs(ref["E"])
+    # sparse and dense cells: a cluster far denser than water (many > 32-atom cells) plus empty space
+    rng = np.random.default_rng(3)
+    pos = np.vstack([rng.uniform(2.0, 6.0, (700, 3)), rng.uniform(0.0, 20.0, (37, 3))])
+    q = rng.uniform(-1, 1, len(pos))
+    ref = O.msm(oparams(cfg), pos, q)
+    for precision in ["fp64", "mixed"]:
+        got = gpu_eval(plan_for(cfg, precision, len(q)), pos, q, dev)
+        assert abs(got[0] - ref["E"]) <= 10 * TOL[precision]["E"] * abs(ref["E"])
+        assert rel_rms(got[2], ref["F"]) <= 10 * TOL[precision]["F"]
+
+
+def test_device_errors_are_reported(dev):
+    from paper_1402_7216_gb300 import MSMError
+    ocfg = dict(box=20.0, periodic=False, cutoff=6.0, spacing=2.0, order=3, split=2)
+    plan = plan_for(ocfg, "mixed", 8)
+    pos = torch.tensor([[1.0, 2.0, 3.0], [25.0, 1.0, 1.0]], dtype=torch.float64, device=dev)
+    q = torch.tensor([1.0, -1.0], dtype=torch.float64, device=dev)
+    plan.eval(pos, q)
+    assert plan.status() == -4                         # atom outside the open box
+    assert plan.status() == 0                          # cleared after reading
+    pos[1, 0] = float("nan")
+    plan.eval(pos, q)
+    assert plan.status() == -5                         # non-finite input
+    with pytest.raises(MSMError) as e:
+        plan.eval(torch.zeros((9, 3), dtype=torch.float64, device=dev),
+                  torch.zeros(9, dtype=torch.float64, device=dev))
+    assert e.value.code == -9                          # more atoms than the plan holds
+    fresh = plan_for(ocfg, "mixed", 8)
+    with pytest.raises(MSMError):
+        fresh.backward(torch.ones((), dtype=torch.float64, device=dev))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_backward_adjoint_matches_forward_outputs(precision, dev):
+    from paper_1402_7216_gb300 import MSMEnergy
+    cfg = dict(box=24.0, periodic=True, cutoff=8.0, spacing=2.0, order=5, split=2)
+    pos, q = make_water_box(24.0, 400, 2, 2, seed=23, periodic=True)
+    plan = plan_for(cfg, precision, len(q))
+    E, phi, F = plan.eval(torch.tensor(pos, device=dev), torch.tensor(q, device=dev))
+    tp = torch.tensor(pos, device=dev, requires_grad=True)
+    tq = torch.tensor(q, device=dev, requires_grad=True)
+    E2 = MSMEnergy.apply(tp, tq, plan)
+    (3.0 * E2).backward()
+    t = TOL[precision]
+    assert abs(E2.item() - E.item()) <= 1e-9 * abs(E.item())      # repeat of the same forward
+    assert rel_rms(tp.grad.cpu().numpy(), -3.0 * F.cpu().numpy()) <= t["F"]
+    assert rel_rms(tq.grad.cpu().numpy(), 3.0 * phi.cpu().numpy()) <= t["phi"]
+    ref = O.msm(oparams(cfg), pos, q)
+    assert rel_rms(-tp.grad.cpu().numpy() / 3.0, ref["F"]) <= t["F"]
+
+
+def test_backward_finite_differences_water23k_fp64(dev):
+    """Central differences (step 1e-4 A) of the FP64 GPU energy on 64 random
+    atoms against the adjoint gradient."""
+    from paper_1402_7216_gb300 import MSMEnergy
+    w = WORKLOADS["water23k"]
+    pos, q = w.make()
+    cfg = dict(box=w.box, periodic=True, cutoff=w.cutoff, spacing=w.spacing, order=w.order, split=w.split)
+    plan = plan_for(cfg, "fp64", len(q))
+    tp = torch.tensor(pos, device=dev, requires_grad=True)
+    tq = torch.tensor(q, device=dev)
+    MSMEnergy.apply(tp, tq, plan).backward()
+    grad = tp.grad.cpu().numpy()
+    rng = np.random.default_rng(24)
+    step = 1e-4
+    base = torch.tensor(pos, device=dev)
+    for i in rng.choice(len(q), 64, replace=False):
+        d = int(rng.integers(3))
+        pp, pm = base.clone(), base.clone()
+        pp[i, d] += step
+        pm[i, d] -= step
+        Ep = plan.eval(pp, tq, want_phi=False, want_force=False)[0].item()
+        Em = plan.eval(pm, tq, want_phi=False, want_force=False)[0].item()
+        fd = (Ep - Em) / (2 * step)
+        assert abs(fd - grad[i, d]) <= 1e-6 + 1e-6 * abs(grad[i, d]), (i, d, fd, grad[i, d])
+
+
+def test_host_entry_point_matches_device(dev):
+    cfg = dict(box=24.0, periodic=True, cutoff=8.0, spacing=2.0, order=3, split=2)
+    pos, q = make_water_box(24.0, 400, 0, 0, seed=25, periodic=True)
+    plan = plan_for(cfg, "mixed", len(q))
+    Ed, phid, Fd = gpu_eval(plan, pos, q, dev)
+    Eh, phih, Fh = plan.eval_host(torch.tensor(pos).pin_memory(), torch.tensor(q).pin_memory(),
+                                  want_phi=True, want_force=True)
+    # same inputs, same kernels; only the order of floating-point atomics differs
+    assert abs(Eh.item() - Ed) <= 1e-9 * abs(Ed)
+    assert rel_rms(Fh.numpy(), Fd) <= 1e-9
+
+
+def test_repeatable(dev):
+    cfg = dict(box=24.0, periodic=True, cutoff=8.0, spacing=2.0, order=5, split=2)
+    pos, q = make_water_box(24.0, 400, 2, 2, seed=26, periodic=True)
+    for precision, tol in [("fp64", 1e-13), ("mixed", 1e-6)]:
+        plan = plan_for(cfg, precision, len(q))
+        a = gpu_eval(plan, pos, q, dev)
+        b = gpu_eval(plan, pos, q, dev)
+        assert abs(a[0] - b[0]) <= tol * abs(a[0])
+        assert rel_rms(a[2], b[2]) <= tol
+
+
+def test_water1m_mixed_on_subsample(dev):
+    """The benchmark workload (1,066,628 atoms, quintic, a = 12, h = 2.5) in the
+    benchmark's launch configuration: mixed precision against the oracle on a
+    4,096-atom spatial subsample, and its energy against the FP64 GPU path."""
+    w = WORKLOADS["water1m"]
+    pos, q = w.make()
+    cfg = dict(box=w.box, periodic=True, cutoff=w.cutoff, spacing=w.spacing, order=w.order, split=w.split)
+    sub = spatial_subsample(pos, (w.box,) * 3, 4096, seed=1)
+    ref = O.msm(oparams(cfg), pos, q, targets=sub)
+    got = gpu_eval(plan_for(cfg, "mixed", len(q)), pos, q, dev)
+    assert rel_rms(got[2][sub], ref["F"]) <= TOL["mixed"]["F"]
+    assert rel_rms(got[1][sub], ref["phi"]) <= TOL["mixed"]["phi"]
+    got64 = gpu_eval(plan_for(cfg, "fp64", len(q)), pos, q, dev)
+    assert rel_rms(got64[2][sub], ref["F"]) <= TOL["fp64"]["F"]
+    assert abs(got[0] - got64[0]) <= TOL["mixed"]["E"] * abs(got64[0])
