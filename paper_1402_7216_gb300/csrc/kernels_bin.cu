@@ -18,8 +18,9 @@ namespace {
 constexpr int kChunk = 4096;   // atoms per radix block
 constexpr int kThreads = 256;  // = radix size
 
-__device__ __forceinline__ double fold(double x, double L) {
-  double y = x - L * floor(x / L);
+// Folds x into [0, L) (multiplying by the reciprocal: FP64 division is slow).
+__device__ __forceinline__ double fold(double x, double L, double inv_L) {
+  double y = x - L * floor(x * inv_L);
   if (y >= L) y -= L;
   if (y < 0.0) y += L;
   return y;
@@ -27,7 +28,9 @@ __device__ __forceinline__ double fold(double x, double L) {
 
 struct BinArgs {
   double box[3];
+  double inv_box[3];
   double cw[3];
+  double inv_cw[3];
   double inv_h[3];
   int nc[3];
   int fmax[3];  // open grids: largest floor(x/h) the level-0 grid covers
@@ -47,12 +50,12 @@ __global__ void k_keys(const double* __restrict__ pos, const double* __restrict_
   for (int d = 0; d < 3; ++d) {
     double v = x[d];
     if (A.periodic) {
-      v = isfinite(v) ? fold(v, A.box[d]) : 0.0;
+      v = isfinite(v) ? fold(v, A.box[d], A.inv_box[d]) : 0.0;
     } else if (!(v >= 0.0 && v <= A.box[d])) {
       bad |= kStatusOutside;
       v = 0.0;
     }
-    int ci = (int)floor(v / A.cw[d]);
+    int ci = (int)floor(v * A.inv_cw[d]);
     c[d] = ci < 0 ? 0 : (ci >= A.nc[d] ? A.nc[d] - 1 : ci);
   }
   if (bad) atomicOr(status, bad);
@@ -165,7 +168,7 @@ __global__ void k_gather(const double* __restrict__ pos, const double* __restric
   int bs[3];
   for (int d = 0; d < 3; ++d) {
     double v = pos[3 * (size_t)i + d];
-    if (A.periodic) v = isfinite(v) ? fold(v, A.box[d]) : 0.0;
+    if (A.periodic) v = isfinite(v) ? fold(v, A.box[d], A.inv_box[d]) : 0.0;
     else v = fmin(fmax(v, 0.0), A.box[d]);
     loc[d] = (T)(v - c[d] * A.cw[d]);
     double t = v * A.inv_h[d];
@@ -187,7 +190,9 @@ cudaError_t launch_binning(Plan& P, int64_t n64, const double* pos, const double
   BinArgs A;
   for (int d = 0; d < 3; ++d) {
     A.box[d] = P.P.box[d];
+    A.inv_box[d] = 1.0 / P.P.box[d];
     A.cw[d] = P.cw[d];
+    A.inv_cw[d] = 1.0 / P.cw[d];
     A.inv_h[d] = 1.0 / P.h[d];
     A.nc[d] = P.nc[d];
     A.fmax[d] = P.n[0][d] - 2 * P.S;

@@ -98,165 +98,196 @@ __device__ __forceinline__ int slot(int idx, int n, int lo, int periodic) {
   return idx - lo;  // callers only pass indices inside the open grid
 }
 
-// ---- anterpolation: atom-centric scatter with float/double atomics ----
-template <typename T, int ORDER>
-__global__ void k_anterp(const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, int n,
-                         double* __restrict__ grid, GridDims G, const double* __restrict__ dscale,
-                         double factor) {
-  constexpr int W = 2 * Basis<T, ORDER>::S;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const R4<T> f = gfrac[i];
-  const int4 b = gbase[i];
-  double sc = factor * (dscale ? *dscale : 1.0);
-  const T qi = T(sc) * f.w;
-  T wx[W], wy[W], wz[W];
-  weights<T, ORDER>(f.x, wx);
-  weights<T, ORDER>(f.y, wy);
-  weights<T, ORDER>(f.z, wz);
-  int ix[W], iy[W], iz[W];
-#pragma unroll
-  for (int s = 0; s < W; ++s) {
-    ix[s] = slot(b.x + s, G.n[0], G.lo[0], G.periodic);
-    iy[s] = slot(b.y + s, G.n[1], G.lo[1], G.periodic);
-    iz[s] = slot(b.z + s, G.n[2], G.lo[2], G.periodic);
+// ---- anterpolation: per-block shared-memory patches ----
+// A block owns B x B x B short-range cells; the level-0 points their atoms
+// can reach form a patch of at most PD^3 points held in shared memory.  Each
+// atom adds its (2S)^3 weighted charges into the patch (shared-memory
+// atomics); the block then adds the patch into the global FP64 grid, so
+// global atomics only meet where neighbouring patches overlap.
+struct AnterpArgs {
+  int nc[3];        // short-range cells per dimension
+  int B;            // cells per block side
+  int pd;           // patch points per dimension
+  double cw_h[3];   // cell width in units of h
+};
+
+template <typename T, typename ACC, int ORDER>
+__global__ void __launch_bounds__(256) k_anterp_patch(const R4<T>* __restrict__ gfrac,
+                                                      const int4* __restrict__ gbase,
+                                                      const int* __restrict__ cell_start, AnterpArgs A,
+                                                      GridDims G, double* __restrict__ grid,
+                                                      const double* __restrict__ dscale, double factor) {
+  constexpr int S = Basis<T, ORDER>::S, W = 2 * S;
+  extern __shared__ unsigned char smem_raw[];
+  ACC* patch = reinterpret_cast<ACC*>(smem_raw);
+  __shared__ int pref[65], cellid[64], ncs;
+  const int PD = A.pd, np = PD * PD * PD, tid = threadIdx.x;
+  const int c0[3] = {(int)blockIdx.x * A.B, (int)blockIdx.y * A.B, (int)blockIdx.z * A.B};
+  int lo[3];
+  for (int d = 0; d < 3; ++d) lo[d] = (int)floor(c0[d] * A.cw_h[d]) - S - 1;
+  for (int e = tid; e < np; e += blockDim.x) patch[e] = ACC(0);
+  if (tid == 0) {
+    int run = 0, k = 0;
+    for (int bz = 0; bz < A.B; ++bz)
+      for (int by = 0; by < A.B; ++by)
+        for (int bx = 0; bx < A.B; ++bx) {
+          int x = c0[0] + bx, y = c0[1] + by, z = c0[2] + bz;
+          if (x >= A.nc[0] || y >= A.nc[1] || z >= A.nc[2]) continue;
+          int c = (z * A.nc[1] + y) * A.nc[0] + x;
+          cellid[k] = c;
+          pref[k] = run;
+          run += cell_start[c + 1] - cell_start[c];
+          ++k;
+        }
+    pref[k] = run;
+    ncs = k;
   }
-#pragma unroll
-  for (int c = 0; c < W; ++c) {
-    const T qz = qi * wz[c];
-#pragma unroll
-    for (int bb = 0; bb < W; ++bb) {
-      const T qyz = qz * wy[bb];
-      double* row = grid + ((size_t)iz[c] * G.n[1] + iy[bb]) * G.n[0];
-#pragma unroll
-      for (int a = 0; a < W; ++a) atomicAdd(row + ix[a], (double)(qyz * wx[a]));
+  __syncthreads();
+  const int nk = ncs, total = pref[nk];
+  const double sc = factor * (dscale ? *dscale : 1.0);
+  for (int kk = tid; kk < total; kk += blockDim.x) {
+    int a0 = 0, a1 = nk;  // last cell with pref <= kk
+    while (a1 - a0 > 1) {
+      int m = (a0 + a1) >> 1;
+      if (pref[m] <= kk) a0 = m;
+      else a1 = m;
     }
+    const int i = cell_start[cellid[a0]] + (kk - pref[a0]);
+    const R4<T> f = gfrac[i];
+    const int4 b = gbase[i];
+    const T qi = T(sc) * f.w;
+    T wx[W], wy[W], wz[W];
+    weights<T, ORDER>(f.x, wx);
+    weights<T, ORDER>(f.y, wy);
+    weights<T, ORDER>(f.z, wz);
+    const int px = b.x - lo[0], py = b.y - lo[1], pz = b.z - lo[2];
+    if (px >= 0 && py >= 0 && pz >= 0 && px + W <= PD && py + W <= PD && pz + W <= PD) {
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const T qz = qi * wz[c];
+#pragma unroll
+        for (int bb = 0; bb < W; ++bb) {
+          const T qyz = qz * wy[bb];
+          ACC* row = patch + ((pz + c) * PD + py + bb) * PD + px;
+#pragma unroll
+          for (int a = 0; a < W; ++a) atomicAdd(row + a, ACC(qyz * wx[a]));
+        }
+      }
+    } else {  // outside the patch (cannot happen for atoms inside their cells): straight to the grid
+      for (int c = 0; c < W; ++c)
+        for (int bb = 0; bb < W; ++bb)
+          for (int a = 0; a < W; ++a) {
+            int sx = slot(b.x + a, G.n[0], G.lo[0], G.periodic), sy = slot(b.y + bb, G.n[1], G.lo[1], G.periodic),
+                sz = slot(b.z + c, G.n[2], G.lo[2], G.periodic);
+            atomicAdd(grid + ((size_t)sz * G.n[1] + sy) * G.n[0] + sx, (double)(qi * wz[c] * wy[bb] * wx[a]));
+          }
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < np; e += blockDim.x) {
+    const ACC v = patch[e];
+    if (v == ACC(0)) continue;
+    int ix = lo[0] + e % PD, iy = lo[1] + (e / PD) % PD, iz = lo[2] + e / (PD * PD);
+    if (!G.periodic && (ix < G.lo[0] || iy < G.lo[1] || iz < G.lo[2] || ix >= G.lo[0] + G.n[0] ||
+                        iy >= G.lo[1] + G.n[1] || iz >= G.lo[2] + G.n[2]))
+      continue;
+    int sx = slot(ix, G.n[0], G.lo[0], G.periodic), sy = slot(iy, G.n[1], G.lo[1], G.periodic),
+        sz = slot(iz, G.n[2], G.lo[2], G.periodic);
+    atomicAdd(grid + ((size_t)sz * G.n[1] + sy) * G.n[0] + sx, (double)v);
   }
 }
 
-// ---- restriction: one thread per coarse point, nonzero taps only ----
-// 1-D weights Phi(d/2): cubic d = 0, +-1, +-3 -> 1, 9/16, -1/16;
-// quintic d = 0, +-1, +-3, +-5 -> 1, 75/128, -25/256, 3/256.
+// ---- restriction and prolongation: separable 1-D passes ----
+// phi^{k+1}_mu(r^k_nu) = prod_d Phi((nu_d - 2 mu_d)/2), so restriction is
+// three 1-D filters (x, then y, then z) and prolongation, its transpose, the
+// same filters in reverse order.  1-D weights Phi(d/2): cubic d = 0, +-1,
+// +-3 -> 1, 9/16, -1/16; quintic d = 0, +-1, +-3, +-5 -> 1, 75/128, -25/256,
+// 3/256 (Phi vanishes at the other integers).
 template <int ORDER>
-struct RWeights;
-template <>
-struct RWeights<3> {
-  static constexpr int N = 5;
-  __device__ static int d(int t) { return t == 0 ? 0 : (t == 1 ? 1 : (t == 2 ? -1 : (t == 3 ? 3 : -3))); }
-  __device__ static double w(int t) { return t == 0 ? 1.0 : (t <= 2 ? 9.0 / 16 : -1.0 / 16); }
-};
-template <>
-struct RWeights<5> {
-  static constexpr int N = 7;
-  __device__ static int d(int t) {
-    return t == 0 ? 0 : (t == 1 ? 1 : (t == 2 ? -1 : (t == 3 ? 3 : (t == 4 ? -3 : (t == 5 ? 5 : -5)))));
-  }
-  __device__ static double w(int t) {
-    return t == 0 ? 1.0 : (t <= 2 ? 75.0 / 128 : (t <= 4 ? -25.0 / 256 : 3.0 / 256));
-  }
-};
-
-template <typename T, int ORDER>
-__global__ void k_restrict(const T* __restrict__ fine, T* __restrict__ coarse, GridDims F, GridDims C) {
-  // instantiated with T = double: charge grids stay in FP64 in every precision mode
-  constexpr int N = RWeights<ORDER>::N;
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t np = (int64_t)C.n[0] * C.n[1] * C.n[2];
-  if (t >= np) return;
-  int cx = (int)(t % C.n[0]), cy = (int)((t / C.n[0]) % C.n[1]), cz = (int)(t / ((int64_t)C.n[0] * C.n[1]));
-  int mu[3] = {C.lo[0] + cx, C.lo[1] + cy, C.lo[2] + cz};
-  int sx[N], sy[N], sz[N];
-  T w[N];
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    w[k] = T(RWeights<ORDER>::w(k));
-    int d = RWeights<ORDER>::d(k);
-    int v[3] = {2 * mu[0] + d, 2 * mu[1] + d, 2 * mu[2] + d};
-    int s3[3];
-    for (int e = 0; e < 3; ++e) {
-      if (F.periodic) {
-        s3[e] = slot(v[e], F.n[e], 0, 1);
-      } else {
-        int s = v[e] - F.lo[e];
-        s3[e] = (s >= 0 && s < F.n[e]) ? s : -1;
-      }
-    }
-    sx[k] = s3[0];
-    sy[k] = s3[1];
-    sz[k] = s3[2];
-  }
-  T sum = 0;
-  for (int c = 0; c < N; ++c) {
-    if (sz[c] < 0) continue;
-    for (int b = 0; b < N; ++b) {
-      if (sy[b] < 0) continue;
-      const T* row = fine + ((size_t)sz[c] * F.n[1] + sy[b]) * F.n[0];
-      T part = 0;
-#pragma unroll
-      for (int a = 0; a < N; ++a)
-        if (sx[a] >= 0) part += w[a] * row[sx[a]];
-      sum += w[c] * w[b] * part;
-    }
-  }
-  coarse[t] = sum;
+__device__ __forceinline__ double rweight(int ad) {
+  if (ad == 0) return 1.0;
+  if (ORDER == 3) return ad == 1 ? 9.0 / 16 : -1.0 / 16;
+  return ad == 1 ? 75.0 / 128 : (ad == 3 ? -25.0 / 256 : 3.0 / 256);
 }
 
-// ---- prolongation: fine point gathers the coarse points that reach it ----
+struct AxisArgs {
+  int nin[3], nout[3];  // array dims (x, y, z) of input and output
+  int axis;             // 0, 1, 2
+  int lo_in, lo_out;    // first absolute index along the axis
+  int periodic;
+};
+
+// restriction along one axis: out[.., c, ..] = sum_d w(d) in[.., 2(lo_out + c) + d - lo_in, ..]
 template <typename T, int ORDER>
-__global__ void k_prolong(const T* __restrict__ coarse, T* __restrict__ fine, GridDims F, GridDims C) {
-  constexpr int S = (ORDER + 1) / 2;
-  constexpr int MX = S * 2;  // at most 2S nonzero coarse neighbours per dimension (odd points)
+__global__ void k_restrict_axis(const T* __restrict__ in, T* __restrict__ out, AxisArgs A) {
+  constexpr int R = ORDER;  // taps reach |d| <= 2S - 1 = ORDER
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t np = (int64_t)F.n[0] * F.n[1] * F.n[2];
+  int64_t np = (int64_t)A.nout[0] * A.nout[1] * A.nout[2];
   if (t >= np) return;
-  int f[3] = {(int)(t % F.n[0]), (int)((t / F.n[0]) % F.n[1]), (int)(t / ((int64_t)F.n[0] * F.n[1]))};
-  int cs[3][MX];
-  T cw[3][MX];
-  int cn[3];
-  for (int e = 0; e < 3; ++e) {
-    int nu = F.lo[e] + f[e];
-    cn[e] = 0;
-    // coarse mu with nu - 2 mu = d, d odd in [-(2S-1), 2S-1] or d = 0
-    for (int d = -(2 * S - 1); d <= 2 * S - 1; ++d) {
-      if (((nu - d) & 1) != 0) continue;
-      if (d != 0 && (d & 1) == 0) continue;  // Phi(+-1), Phi(+-2) vanish
-      int mu = (nu - d) / 2;
-      int s;
-      if (C.periodic) {
-        s = slot(mu, C.n[e], 0, 1);
-      } else {
-        s = mu - C.lo[e];
-        if (s < 0 || s >= C.n[e]) continue;
-      }
-      int ad = d < 0 ? -d : d;
-      double w = (ad == 0) ? 1.0
-                 : (ORDER == 3 ? (ad == 1 ? 9.0 / 16 : -1.0 / 16)
-                               : (ad == 1 ? 75.0 / 128 : (ad == 3 ? -25.0 / 256 : 3.0 / 256)));
-      cs[e][cn[e]] = s;
-      cw[e][cn[e]] = T(w);
-      ++cn[e];
-    }
-  }
+  int c[3] = {(int)(t % A.nout[0]), (int)((t / A.nout[0]) % A.nout[1]), (int)(t / ((int64_t)A.nout[0] * A.nout[1]))};
+  int64_t stride = A.axis == 0 ? 1 : (A.axis == 1 ? (int64_t)A.nin[0] : (int64_t)A.nin[0] * A.nin[1]);
+  int cc = c[A.axis];
+  c[A.axis] = 0;
+  const T* base = in + ((int64_t)c[2] * A.nin[1] + c[1]) * A.nin[0] + c[0];
+  int n = A.nin[A.axis];
+  int nu0 = 2 * (A.lo_out + cc);
   T sum = 0;
-  for (int c = 0; c < cn[2]; ++c)
-    for (int b = 0; b < cn[1]; ++b) {
-      const T* row = coarse + ((size_t)cs[2][c] * C.n[1] + cs[1][b]) * C.n[0];
-      T part = 0;
-      for (int a = 0; a < cn[0]; ++a) part += cw[0][a] * row[cs[0][a]];
-      sum += cw[2][c] * cw[1][b] * part;
+#pragma unroll
+  for (int d = -R; d <= R; ++d) {
+    if (d != 0 && (d & 1) == 0) continue;
+    int s = nu0 + d - A.lo_in;
+    if (A.periodic) {
+      s %= n;
+      if (s < 0) s += n;
+    } else if (s < 0 || s >= n) {
+      continue;
     }
-  fine[t] += sum;
+    sum += T(rweight<ORDER>(d < 0 ? -d : d)) * base[s * stride];
+  }
+  out[t] = sum;
+}
+
+// prolongation along one axis: out[.., f, ..] (+)= sum_mu w(nu - 2 mu) in[.., mu - lo_in, ..]
+template <typename T, int ORDER>
+__global__ void k_prolong_axis(const T* __restrict__ in, T* __restrict__ out, AxisArgs A, int accumulate) {
+  constexpr int R = ORDER;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t np = (int64_t)A.nout[0] * A.nout[1] * A.nout[2];
+  if (t >= np) return;
+  int c[3] = {(int)(t % A.nout[0]), (int)((t / A.nout[0]) % A.nout[1]), (int)(t / ((int64_t)A.nout[0] * A.nout[1]))};
+  int64_t stride = A.axis == 0 ? 1 : (A.axis == 1 ? (int64_t)A.nin[0] : (int64_t)A.nin[0] * A.nin[1]);
+  int f = c[A.axis];
+  c[A.axis] = 0;
+  const T* base = in + ((int64_t)c[2] * A.nin[1] + c[1]) * A.nin[0] + c[0];
+  int n = A.nin[A.axis];
+  int nu = A.lo_out + f;
+  T sum = 0;
+#pragma unroll
+  for (int d = -R; d <= R; ++d) {  // nu - 2 mu = d, d = 0 or odd
+    if (d != 0 && (d & 1) == 0) continue;
+    if (((nu - d) & 1) != 0) continue;
+    int s = (nu - d) / 2 - A.lo_in;
+    if (A.periodic) {
+      s %= n;
+      if (s < 0) s += n;
+    } else if (s < 0 || s >= n) {
+      continue;
+    }
+    sum += T(rweight<ORDER>(d < 0 ? -d : d)) * base[s * stride];
+  }
+  out[t] = accumulate ? out[t] + sum : sum;
 }
 
 // ---- lattice cutoff: z-streaming shared-memory planes, register tiles ----
-// A block of 4 warps owns a 32 x 16 x 4 brick of outputs; warp w owns plane
-// z0 + w, and each lane 8 consecutive x outputs in rows y and y + 8.  The
-// input planes z0 - Ez .. z0 + 3 + Ez are staged in turn (a 2-D window with
-// halo Ex, Ey); for staged plane zi, warp w applies the stencil rows of
-// dz = zi - (z0 + w) as segments of 8 taps along x: 8 x 8 x 2 FMAs per
-// segment from 2 x 15 shared loads.  Per-plane partial sums are folded into
-// the totals with TwoSum in mixed precision.
-constexpr int LBX = 32, LBY = 16, LBZ = 4, LPX = 8;
+// A block of 4 warps owns a 32 x 8 x 4 brick of outputs; warp w owns plane
+// z0 + w, and each lane 8 consecutive x outputs of one row.  The input
+// planes z0 - Ez .. z0 + 3 + Ez are staged in turn (a 2-D window with halo
+// Ex, Ey, converted from the FP64 charge grid); for staged plane zi, warp w
+// applies the stencil rows of dz = zi - (z0 + w) as segments of 8 taps along
+// x: 64 FMAs per segment from 15 shared loads.  The odd row pitch keeps the
+// 32 lanes on 32 banks.  Per-plane partial sums are folded into the totals
+// with TwoSum in mixed precision.
+constexpr int LBX = 32, LBY = 8, LBZ = 4, LPX = 8;
 
 template <typename T>
 __device__ __forceinline__ void two_sum_add(T& s, T& c, T x) {
@@ -280,15 +311,12 @@ __global__ void __launch_bounds__(128) k_lattice(const double* __restrict__ q, T
   const int tx = lane & 3, ty = lane >> 2;
   const int x0 = blockIdx.x * LBX, y0 = blockIdx.y * LBY, z0 = blockIdx.z * LBZ;
   const int zo = z0 + warp;
-  T acc[2][LPX], cmp[2][LPX];
+  T acc[LPX], cmp[LPX];
 #pragma unroll
-  for (int r = 0; r < 2; ++r)
-#pragma unroll
-    for (int j = 0; j < LPX; ++j) acc[r][j] = cmp[r][j] = T(0);
+  for (int j = 0; j < LPX; ++j) acc[j] = cmp[j] = T(0);
 
   for (int zi = z0 - Ez; zi < z0 + LBZ + Ez; ++zi) {
     __syncthreads();
-    // stage plane zi (wrapped or zero outside an open grid)
     int gz;
     bool zok;
     if (G.periodic) {
@@ -317,46 +345,84 @@ __global__ void __launch_bounds__(128) k_lattice(const double* __restrict__ q, T
     __syncthreads();
     const int dz = zi - zo;
     if (dz < -Ez || dz > Ez || zo >= G.n[2]) continue;  // warp-uniform
-    T part[2][LPX];
+    T part[LPX];
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-      for (int j = 0; j < LPX; ++j) part[r][j] = T(0);
+    for (int j = 0; j < LPX; ++j) part[j] = T(0);
     const int s1 = seg_start[dz + Ez + 1];
     for (int s = seg_start[dz + Ez]; s < s1; ++s) {
       const Segment<T> sg = seg[s];
-      const int xb = tx * LPX + Ex + sg.dx0;
+      const T* row = plane + (ty + Ey + sg.dy) * SX + tx * LPX + Ex + sg.dx0;
+      T win[LPX + kSeg - 1];
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const T* row = plane + (ty + 8 * r + Ey + sg.dy) * SX + xb;
-        T win[LPX + kSeg - 1];
+      for (int k = 0; k < LPX + kSeg - 1; ++k) win[k] = row[k];
 #pragma unroll
-        for (int k = 0; k < LPX + kSeg - 1; ++k) win[k] = row[k];
+      for (int k = 0; k < kSeg; ++k)
 #pragma unroll
-        for (int k = 0; k < kSeg; ++k)
-#pragma unroll
-          for (int j = 0; j < LPX; ++j) part[r][j] += sg.g[k] * win[j + k];
-      }
+        for (int j = 0; j < LPX; ++j) part[j] += sg.g[k] * win[j + k];
     }
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-      for (int j = 0; j < LPX; ++j) {
-        if (COMP) two_sum_add(acc[r][j], cmp[r][j], part[r][j]);
-        else acc[r][j] += part[r][j];
-      }
-  }
-  if (zo >= G.n[2]) return;
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    int y = y0 + ty + 8 * r;
-    if (y >= G.n[1]) continue;
 #pragma unroll
     for (int j = 0; j < LPX; ++j) {
-      int x = x0 + tx * LPX + j;
-      if (x < G.n[0]) u[((size_t)zo * G.n[1] + y) * G.n[0] + x] = scale * (acc[r][j] + cmp[r][j]);
+      if (COMP) two_sum_add(acc[j], cmp[j], part[j]);
+      else acc[j] += part[j];
     }
   }
+  if (zo >= G.n[2]) return;
+  const int y = y0 + ty;
+  if (y >= G.n[1]) return;
+#pragma unroll
+  for (int j = 0; j < LPX; ++j) {
+    int x = x0 + tx * LPX + j;
+    if (x < G.n[0]) u[((size_t)zo * G.n[1] + y) * G.n[0] + x] = scale * (acc[j] + cmp[j]);
+  }
+}
+
+// Coarse levels have too few points to fill the GPU with bricks: one thread
+// per (output point, stencil plane dz), reading the charges straight from
+// global memory, adding its plane's share into the zeroed output.
+template <typename T>
+__global__ void __launch_bounds__(128) k_lattice_small(const double* __restrict__ q, T* __restrict__ u,
+                                                       GridDims G, const Segment<T>* __restrict__ seg,
+                                                       const int* __restrict__ seg_start, int Ez, T scale) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t np = (int64_t)G.n[0] * G.n[1] * G.n[2];
+  if (p >= np) return;
+  const int dz = (int)blockIdx.y - Ez;
+  const int x = (int)(p % G.n[0]), y = (int)((p / G.n[0]) % G.n[1]), z = (int)(p / ((int64_t)G.n[0] * G.n[1]));
+  int zz = z + dz;
+  if (G.periodic) {
+    zz %= G.n[2];
+    if (zz < 0) zz += G.n[2];
+  } else if (zz < 0 || zz >= G.n[2]) {
+    return;
+  }
+  T sum = 0;
+  const int s1 = seg_start[dz + Ez + 1];
+  for (int s = seg_start[dz + Ez]; s < s1; ++s) {
+    const Segment<T> sg = seg[s];
+    int yy = y + sg.dy;
+    if (G.periodic) {
+      yy %= G.n[1];
+      if (yy < 0) yy += G.n[1];
+    } else if (yy < 0 || yy >= G.n[1]) {
+      continue;
+    }
+    const double* row = q + ((size_t)zz * G.n[1] + yy) * G.n[0];
+    int xx = x + sg.dx0;
+    if (G.periodic) {  // wrap once, then step with a compare
+      xx %= G.n[0];
+      if (xx < 0) xx += G.n[0];
+#pragma unroll
+      for (int k = 0; k < kSeg; ++k) {
+        sum += sg.g[k] * (T)row[xx];
+        if (++xx == G.n[0]) xx = 0;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kSeg; ++k, ++xx)
+        if (xx >= 0 && xx < G.n[0]) sum += sg.g[k] * (T)row[xx];
+    }
+  }
+  atomicAdd(u + p, scale * sum);
 }
 
 // ---- top level: all pairs of the coarsest grid, FP64 ----
@@ -548,82 +614,127 @@ unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
 
+template <typename T, typename ACC, int ORDER>
+void anterp_t(Plan& P, void* grid0, const double* dscale, double factor, cudaStream_t st) {
+  AnterpArgs A;
+  for (int d = 0; d < 3; ++d) {
+    A.nc[d] = P.nc[d];
+    A.cw_h[d] = P.cw[d] / P.h[d];
+  }
+  A.B = P.ablk;
+  A.pd = P.apd;
+  dim3 grid(blocks_for(P.nc[0], A.B), blocks_for(P.nc[1], A.B), blocks_for(P.nc[2], A.B));
+  size_t sm = sizeof(ACC) * (size_t)A.pd * A.pd * A.pd;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_anterp_patch<T, ACC, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_anterp_patch<T, ACC, ORDER><<<grid, 256, sm, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.cell_start, A,
+                                                     dims_of(P, 0), (double*)grid0, dscale, factor);
+}
+
 cudaError_t launch_anterpolate(Plan& P, int64_t n, void* grid0, const double* dscale, double factor,
                                cudaStream_t st) {
   size_t bytes = sizeof(double) * (size_t)grid_points(P, 0);
   cudaMemsetAsync(grid0, 0, bytes, st);
   P.launches += 1 + (n > 0 ? 1 : 0);
   if (n <= 0) return cudaGetLastError();
-  GridDims G = dims_of(P, 0);
-  unsigned nb = blocks_for(n, 256);
   if (P.fp64) {
-    if (P.P.order == 3)
-      k_anterp<double, 3><<<nb, 256, 0, st>>>((const R4<double>*)P.d.gfrac, P.d.gbase, (int)n,
-                                              (double*)grid0, G, dscale, factor);
-    else
-      k_anterp<double, 5><<<nb, 256, 0, st>>>((const R4<double>*)P.d.gfrac, P.d.gbase, (int)n,
-                                              (double*)grid0, G, dscale, factor);
+    if (P.P.order == 3) anterp_t<double, double, 3>(P, grid0, dscale, factor, st);
+    else anterp_t<double, double, 5>(P, grid0, dscale, factor, st);
   } else {
-    if (P.P.order == 3)
-      k_anterp<float, 3><<<nb, 256, 0, st>>>((const R4<float>*)P.d.gfrac, P.d.gbase, (int)n,
-                                             (double*)grid0, G, dscale, factor);
-    else
-      k_anterp<float, 5><<<nb, 256, 0, st>>>((const R4<float>*)P.d.gfrac, P.d.gbase, (int)n,
-                                             (double*)grid0, G, dscale, factor);
+    if (P.P.order == 3) anterp_t<float, float, 3>(P, grid0, dscale, factor, st);
+    else anterp_t<float, float, 5>(P, grid0, dscale, factor, st);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_restrict(Plan& P, int k, const void* fine, void* coarse, cudaStream_t st) {
-  P.launches += 1;
-  GridDims F = dims_of(P, k), C = dims_of(P, k + 1);
-  unsigned nb = blocks_for(grid_points(P, k + 1), 128);
-  if (P.P.order == 3) k_restrict<double, 3><<<nb, 128, 0, st>>>((const double*)fine, (double*)coarse, F, C);
-  else k_restrict<double, 5><<<nb, 128, 0, st>>>((const double*)fine, (double*)coarse, F, C);
+  P.launches += 3;
+  const int* nf = P.n[k];
+  const int* nc = P.n[k + 1];
+  double* t1 = (double*)P.d.tmp[0];
+  double* t2 = (double*)P.d.tmp[1];
+  const double* src[3] = {(const double*)fine, t1, t2};
+  double* dst[3] = {t1, t2, (double*)coarse};
+  int cur[3] = {nf[0], nf[1], nf[2]};
+  for (int ax = 0; ax < 3; ++ax) {
+    AxisArgs A;
+    for (int d = 0; d < 3; ++d) A.nin[d] = cur[d];
+    cur[ax] = nc[ax];
+    for (int d = 0; d < 3; ++d) A.nout[d] = cur[d];
+    A.axis = ax;
+    A.lo_in = P.lo[k][ax];
+    A.lo_out = P.lo[k + 1][ax];
+    A.periodic = P.P.periodic;
+    unsigned nb = blocks_for((int64_t)cur[0] * cur[1] * cur[2], 256);
+    if (P.P.order == 3) k_restrict_axis<double, 3><<<nb, 256, 0, st>>>(src[ax], dst[ax], A);
+    else k_restrict_axis<double, 5><<<nb, 256, 0, st>>>(src[ax], dst[ax], A);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_prolong(Plan& P, int k, const void* coarse, void* fine, cudaStream_t st) {
-  P.launches += 1;
-  GridDims F = dims_of(P, k), C = dims_of(P, k + 1);
-  unsigned nb = blocks_for(grid_points(P, k), 128);
-  if (P.fp64) {
-    if (P.P.order == 3) k_prolong<double, 3><<<nb, 128, 0, st>>>((const double*)coarse, (double*)fine, F, C);
-    else k_prolong<double, 5><<<nb, 128, 0, st>>>((const double*)coarse, (double*)fine, F, C);
-  } else {
-    if (P.P.order == 3) k_prolong<float, 3><<<nb, 128, 0, st>>>((const float*)coarse, (float*)fine, F, C);
-    else k_prolong<float, 5><<<nb, 128, 0, st>>>((const float*)coarse, (float*)fine, F, C);
+template <typename T>
+void prolong_t(Plan& P, int k, const T* coarse, T* fine, cudaStream_t st) {
+  const int* nf = P.n[k];
+  const int* nc = P.n[k + 1];
+  T* s1 = (T*)P.d.tmp[0];
+  T* s2 = (T*)P.d.tmp[1];
+  const T* src[3] = {coarse, s1, s2};
+  T* dst[3] = {s1, s2, fine};
+  int cur[3] = {nc[0], nc[1], nc[2]};
+  for (int i = 0; i < 3; ++i) {
+    int ax = 2 - i;  // z, then y, then x
+    AxisArgs A;
+    for (int d = 0; d < 3; ++d) A.nin[d] = cur[d];
+    cur[ax] = nf[ax];
+    for (int d = 0; d < 3; ++d) A.nout[d] = cur[d];
+    A.axis = ax;
+    A.lo_in = P.lo[k + 1][ax];
+    A.lo_out = P.lo[k][ax];
+    A.periodic = P.P.periodic;
+    unsigned nb = blocks_for((int64_t)cur[0] * cur[1] * cur[2], 256);
+    int acc = (i == 2) ? 1 : 0;  // the last pass adds onto u^{k,cutoff}
+    if (P.P.order == 3) k_prolong_axis<T, 3><<<nb, 256, 0, st>>>(src[i], dst[i], A, acc);
+    else k_prolong_axis<T, 5><<<nb, 256, 0, st>>>(src[i], dst[i], A, acc);
   }
+}
+
+cudaError_t launch_prolong(Plan& P, int k, const void* coarse, void* fine, cudaStream_t st) {
+  P.launches += 3;
+  if (P.fp64) prolong_t<double>(P, k, (const double*)coarse, (double*)fine, st);
+  else prolong_t<float>(P, k, (const float*)coarse, (float*)fine, st);
   return cudaGetLastError();
+}
+
+template <typename T, bool COMP>
+void lattice_t(Plan& P, int k, const double* qk, T* uk, cudaStream_t st) {
+  GridDims G = dims_of(P, k);
+  dim3 grid(blocks_for(G.n[0], LBX), blocks_for(G.n[1], LBY), blocks_for(G.n[2], LBZ));
+  T scale = (T)std::ldexp(1.0, -k);
+  if ((int64_t)grid.x * grid.y * grid.z < 2 * 152) {  // coarse level: split the stencil planes instead
+    cudaMemsetAsync(uk, 0, sizeof(T) * (size_t)grid_points(P, k), st);
+    dim3 g2(blocks_for(grid_points(P, k), 128), 2 * P.E[2] + 1);
+    k_lattice_small<T><<<g2, 128, 0, st>>>(qk, uk, G, (const Segment<T>*)P.d.seg, P.d.seg_start, P.E[2], scale);
+    P.launches += 1;
+    return;
+  }
+  int SX = (LBX + 2 * P.E[0] + kSeg) | 1, SY = LBY + 2 * P.E[1];
+  size_t sm = sizeof(T) * SX * SY;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_lattice<T, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_lattice<T, COMP><<<grid, 128, sm, st>>>(qk, uk, G, (const Segment<T>*)P.d.seg, P.d.seg_start, P.E[0], P.E[1],
+                                           P.E[2], scale);
 }
 
 cudaError_t launch_lattice(Plan& P, int k, const void* qk, void* uk, cudaStream_t st) {
   P.launches += 1;
-  GridDims G = dims_of(P, k);
-  dim3 grid(blocks_for(G.n[0], LBX), blocks_for(G.n[1], LBY), blocks_for(G.n[2], LBZ));
-  int SX = (LBX + 2 * P.E[0] + kSeg) | 1, SY = LBY + 2 * P.E[1];
-  double scale = std::ldexp(1.0, -k);
-  if (P.fp64) {
-    size_t sm = sizeof(double) * SX * SY;
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaFuncSetAttribute(k_lattice<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_set = true;
-    }
-    k_lattice<double, false><<<grid, 128, sm, st>>>((const double*)qk, (double*)uk, G,
-                                                    (const Segment<double>*)P.d.seg, P.d.seg_start, P.E[0],
-                                                    P.E[1], P.E[2], scale);
-  } else {
-    size_t sm = sizeof(float) * SX * SY;
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaFuncSetAttribute(k_lattice<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_set = true;
-    }
-    k_lattice<float, true><<<grid, 128, sm, st>>>((const double*)qk, (float*)uk, G,
-                                                  (const Segment<float>*)P.d.seg, P.d.seg_start, P.E[0],
-                                                  P.E[1], P.E[2], (float)scale);
-  }
+  if (P.fp64) lattice_t<double, false>(P, k, (const double*)qk, (double*)uk, st);
+  else lattice_t<float, true>(P, k, (const double*)qk, (float*)uk, st);
   return cudaGetLastError();
 }
 

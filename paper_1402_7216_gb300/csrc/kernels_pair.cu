@@ -5,13 +5,14 @@
 //
 // One warp owns one cell of the sort-binned atoms (cells at least a/2 wide):
 // its lanes hold up to 32 target atoms and walk the neighbour cells within
-// reach (offsets whose closest points are nearer than a).  Source atoms of a
-// neighbour cell are staged in the warp's shared memory (shifted into the
-// target cell's frame, so every difference is between small cell-local
-// coordinates) and broadcast to the lanes.  Each pair costs one rsqrt and
-// ~20 FP32 operations; rejected pairs are masked, not branched.  Mixed
-// precision sums each staged chunk in FP32 and folds the chunk sums into the
-// running totals with an error-free TwoSum (compensated accumulation).
+// reach (offsets whose closest points are nearer than a).  Source atoms are
+// shifted into the target cell's frame (every difference is between small
+// cell-local coordinates), culled against the bounding box of the targets,
+// and queued in the warp's shared memory; full queues are broadcast to the
+// lanes in unrolled batches.  Each pair costs one rsqrt and ~20 FP32
+// operations; rejected pairs are masked, not branched.  Mixed precision sums
+// each batch in FP32 and folds the batch sums into the running totals with an
+// error-free TwoSum (compensated accumulation).
 #include "msm_internal.h"
 
 namespace msm {
@@ -39,9 +40,6 @@ struct Smooth<T, 3> {
   __device__ static T gs(T s) { return T(-2.1875) + s * (T(2.625) - T(0.9375) * s); }
 };
 
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-
 // error-free transformation s + x = t + err; the error goes to the compensation term
 template <typename T>
 __device__ __forceinline__ void two_sum_add(T& s, T& c, T x) {
@@ -53,33 +51,98 @@ __device__ __forceinline__ void two_sum_add(T& s, T& c, T x) {
 
 struct PairArgs {
   int nc[3];
-  double cw[3];
   int periodic;
   int noff;
   double a;
 };
 
 constexpr int kWarps = 4;
+constexpr int kBatch = 32;       // pairs per lane per batch (one queue drain)
+constexpr unsigned kFull = 0xffffffffu;
 
+__device__ __forceinline__ float fast_rsqrt(float x) {  // one MUFU.RSQ; inputs are >= a^2/... never denormal
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ T far_away() { return T(1e18); }
+
+// One batch: the lane's target atom against the kBatch queued sources.
+template <typename T, int M, bool COMP>
+__device__ __forceinline__ void pair_batch(const R4<T>* __restrict__ Q, const R4<T>& ai, T a2, T inv_a,
+                                           T inv_a2, T two_inv_a3, T& phi, T& fx, T& fy, T& fz, T& cphi,
+                                           T& cfx, T& cfy, T& cfz) {
+  T pphi = 0, px = 0, py = 0, pz = 0;
+#pragma unroll 8
+  for (int jj = 0; jj < kBatch; ++jj) {
+    const R4<T> b = Q[jj];
+    const T dx = ai.x - b.x, dy = ai.y - b.y, dz = ai.z - b.z;
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    const bool ok = (r2 < a2) && (r2 > T(0));   // inside the cutoff, not the atom itself
+    const T r2s = ok ? r2 : a2;
+    const T qj = ok ? b.w : T(0);
+    const T rinv = fast_rsqrt(r2s);
+    const T s = r2s * inv_a2;
+    pphi += qj * (rinv - Smooth<T, M>::g(s) * inv_a);
+    const T f = qj * (-(rinv * rinv * rinv) - two_inv_a3 * Smooth<T, M>::gs(s));
+    px += f * dx;
+    py += f * dy;
+    pz += f * dz;
+  }
+  if (COMP) {
+    two_sum_add(phi, cphi, pphi);
+    two_sum_add(fx, cfx, px);
+    two_sum_add(fy, cfy, py);
+    two_sum_add(fz, cfz, pz);
+  } else {
+    phi += pphi;
+    fx += px;
+    fy += py;
+    fz += pz;
+  }
+}
+
+// One warp per cell.  For every neighbour cell in reach, the warp stages 32
+// source atoms at a time (shifted into the target cell's frame), drops those
+// farther than a from the bounding box of its target atoms, and appends the
+// rest to a per-warp queue in shared memory; each full queue of kBatch
+// sources is one fully unrolled batch of pair evaluations.
 template <typename T, int M, bool COMP>
 __global__ void __launch_bounds__(32 * kWarps) k_short_range(
     const R4<T>* __restrict__ atoms, const int* __restrict__ cell_start,
-    const int4* __restrict__ offs, PairArgs A, int ncell, T* __restrict__ phis,
-    R4<T>* __restrict__ fs) {
-  __shared__ R4<T> sj[kWarps][32];
+    const int4* __restrict__ offs, const R4<T>* __restrict__ shifts, PairArgs A, int ncell,
+    T* __restrict__ phis, R4<T>* __restrict__ fs) {
+  __shared__ R4<T> queue[kWarps][2 * kBatch];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  R4<T>* Q = queue[warp];
   const int cell = blockIdx.x * kWarps + warp;
   if (cell >= ncell) return;  // warp-uniform
   const int cx = cell % A.nc[0], cy = (cell / A.nc[0]) % A.nc[1], cz = cell / (A.nc[0] * A.nc[1]);
   const T a2 = T(A.a * A.a), inv_a = T(1.0 / A.a), inv_a2 = T(1.0 / (A.a * A.a));
   const T two_inv_a3 = T(2.0 / (A.a * A.a * A.a));
+  const R4<T> dummy = {far_away<T>(), far_away<T>(), far_away<T>(), T(0)};
   const int i0 = cell_start[cell], i1 = cell_start[cell + 1];
   for (int ib = i0; ib < i1; ib += 32) {
     const int i = ib + lane;
     const bool iv = i < i1;
     R4<T> ai = iv ? atoms[i] : R4<T>{T(0), T(0), T(0), T(0)};
-    T phi = 0, fx = 0, fy = 0, fz = 0;
-    T cphi = 0, cfx = 0, cfy = 0, cfz = 0;
+    // bounding box of this chunk's target atoms
+    T lx = iv ? ai.x : far_away<T>(), ly = iv ? ai.y : far_away<T>(), lz = iv ? ai.z : far_away<T>();
+    T hx = iv ? ai.x : -far_away<T>(), hy = iv ? ai.y : -far_away<T>(), hz = iv ? ai.z : -far_away<T>();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lx = min(lx, __shfl_xor_sync(kFull, lx, o));
+      ly = min(ly, __shfl_xor_sync(kFull, ly, o));
+      lz = min(lz, __shfl_xor_sync(kFull, lz, o));
+      hx = max(hx, __shfl_xor_sync(kFull, hx, o));
+      hy = max(hy, __shfl_xor_sync(kFull, hy, o));
+      hz = max(hz, __shfl_xor_sync(kFull, hz, o));
+    }
+    T phi = 0, fx = 0, fy = 0, fz = 0, cphi = 0, cfx = 0, cfy = 0, cfz = 0;
+    int qn = 0;  // queued sources (warp-uniform)
     for (int o = 0; o < A.noff; ++o) {
       const int4 off = offs[o];
       int nx = cx + off.x, ny = cy + off.y, nz = cz + off.z;
@@ -91,48 +154,39 @@ __global__ void __launch_bounds__(32 * kWarps) k_short_range(
         continue;
       }
       const int nb = (nz * A.nc[1] + ny) * A.nc[0] + nx;
-      const T sx = T(off.x * A.cw[0]), sy = T(off.y * A.cw[1]), sz = T(off.z * A.cw[2]);
+      const R4<T> sh = shifts[o];
       const int j0 = cell_start[nb], j1 = cell_start[nb + 1];
       for (int jb = j0; jb < j1; jb += 32) {
         const int j = jb + lane;
+        R4<T> aj = dummy;
         if (j < j1) {
-          R4<T> aj = atoms[j];
-          aj.x += sx;
-          aj.y += sy;
-          aj.z += sz;
-          sj[warp][lane] = aj;
+          aj = atoms[j];
+          aj.x += sh.x;
+          aj.y += sh.y;
+          aj.z += sh.z;
         }
+        const T ex = max(max(lx - aj.x, aj.x - hx), T(0));
+        const T ey = max(max(ly - aj.y, aj.y - hy), T(0));
+        const T ez = max(max(lz - aj.z, aj.z - hz), T(0));
+        const bool keep = (j < j1) && (ex * ex + ey * ey + ez * ez < a2);
+        const unsigned bal = __ballot_sync(kFull, keep);
+        if (keep) Q[qn + __popc(bal & ((1u << lane) - 1u))] = aj;
+        qn += __popc(bal);
         __syncwarp();
-        const int cnt = min(32, j1 - jb);
-        T pphi = 0, px = 0, py = 0, pz = 0;
-        for (int jj = 0; jj < cnt; ++jj) {
-          const R4<T> b = sj[warp][jj];
-          const T dx = ai.x - b.x, dy = ai.y - b.y, dz = ai.z - b.z;
-          const T r2 = dx * dx + dy * dy + dz * dz;
-          const bool ok = (r2 < a2) && (r2 > T(0));
-          const T r2s = ok ? r2 : a2;
-          const T rinv = rsq(r2s);
-          const T s = r2s * inv_a2;
-          const T qj = ok ? b.w : T(0);
-          pphi += qj * (rinv - Smooth<T, M>::g(s) * inv_a);
-          const T f = qj * (-(rinv * rinv * rinv) - two_inv_a3 * Smooth<T, M>::gs(s));
-          px += f * dx;
-          py += f * dy;
-          pz += f * dz;
+        if (qn >= kBatch) {
+          pair_batch<T, M, COMP>(Q, ai, a2, inv_a, inv_a2, two_inv_a3, phi, fx, fy, fz, cphi, cfx, cfy, cfz);
+          __syncwarp();
+          if (lane < qn - kBatch) Q[lane] = Q[kBatch + lane];
+          qn -= kBatch;
+          __syncwarp();
         }
-        if (COMP) {
-          two_sum_add(phi, cphi, pphi);
-          two_sum_add(fx, cfx, px);
-          two_sum_add(fy, cfy, py);
-          two_sum_add(fz, cfz, pz);
-        } else {
-          phi += pphi;
-          fx += px;
-          fy += py;
-          fz += pz;
-        }
-        __syncwarp();
       }
+    }
+    if (qn > 0) {  // last partial batch, padded with far-away zero charges
+      if (lane >= qn) Q[lane] = dummy;
+      __syncwarp();
+      pair_batch<T, M, COMP>(Q, ai, a2, inv_a, inv_a2, two_inv_a3, phi, fx, fy, fz, cphi, cfx, cfy, cfz);
+      __syncwarp();
     }
     if (iv) {
       phis[i] = phi + cphi;
@@ -145,28 +199,26 @@ __global__ void __launch_bounds__(32 * kWarps) k_short_range(
 template <typename T, bool COMP>
 void launch_t(Plan& P, cudaStream_t st) {
   PairArgs A;
-  for (int d = 0; d < 3; ++d) {
-    A.nc[d] = P.nc[d];
-    A.cw[d] = P.cw[d];
-  }
+  for (int d = 0; d < 3; ++d) A.nc[d] = P.nc[d];
   A.periodic = P.P.periodic;
   A.noff = P.noff;
   A.a = P.P.cutoff;
   int blocks = (P.ncell + kWarps - 1) / kWarps;
   auto* at = (const R4<T>*)P.d.atoms;
+  auto* sh = (const R4<T>*)P.d.cell_shift;
   auto* ph = (T*)P.d.phis;
   auto* fs = (R4<T>*)P.d.fs;
   switch (P.P.splitting) {
     case 1:
-      k_short_range<T, 1, COMP><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, A,
+      k_short_range<T, 1, COMP><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A,
                                                                P.ncell, ph, fs);
       break;
     case 2:
-      k_short_range<T, 2, COMP><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, A,
+      k_short_range<T, 2, COMP><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A,
                                                                P.ncell, ph, fs);
       break;
     default:
-      k_short_range<T, 3, COMP><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, A,
+      k_short_range<T, 3, COMP><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A,
                                                                P.ncell, ph, fs);
       break;
   }

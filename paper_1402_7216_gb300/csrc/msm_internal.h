@@ -54,6 +54,8 @@ struct DeviceBuffers {
   // adjoint grids
   void* aq[kMaxLevels] = {};
   void* au[kMaxLevels] = {};
+  // separable restriction / prolongation temporaries (each as large as level 0, in doubles)
+  void* tmp[2] = {nullptr, nullptr};
   // top level (always FP64)
   double* topK = nullptr;      // periodic: [M^3] circulant; open: [(2M-1)^3] Toeplitz
   double* topq = nullptr;
@@ -63,6 +65,7 @@ struct DeviceBuffers {
   int* seg_start = nullptr;    // [2*Ez+2]: segments of plane dz live in [start[dz+Ez], start[dz+Ez+1])
   // neighbour cell offsets (x, y, z) of the pair kernel
   int4* cell_off = nullptr;    // [noff]
+  void* cell_shift = nullptr;  // R4<T>[noff]: offset times cell width, in the plan's precision
   // reductions and status
   double* partial = nullptr;   // per-block energy partials
   double* scalars = nullptr;   // [8] scratch scalars (0: backward scale)
@@ -89,6 +92,8 @@ struct Plan {
   int ncell = 1;
   int key_passes = 1;
   int noff = 0;
+  // anterpolation patches: blocks of ablk^3 cells, patches of apd^3 points
+  int ablk = 1, apd = 1;
   // smoothing constants
   double gamma0 = 0.0;         // gamma(0)
   // level stencil

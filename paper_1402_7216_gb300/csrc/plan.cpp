@@ -251,6 +251,21 @@ int build_plan(const msm_params* pp, Plan* P) {
         offs.push_back(make_int4(ox, oy, oz, 0));
       }
   P->noff = (int)offs.size();
+  // anterpolation patch: B^3 cells reach at most floor(B cw/h) + 2S + 5
+  // points per dimension (with margin for rounding); keep it in shared memory
+  {
+    int cap = P->fp64 ? 24 : 32;
+    int B = 4, pd = 0;
+    for (; B >= 1; --B) {
+      pd = 0;
+      for (int d = 0; d < 3; ++d)
+        pd = std::max(pd, (int)std::floor(B * P->cw[d] / P->h[d]) + 2 * P->S + 5);
+      if (pd <= cap) break;
+    }
+    if (B < 1) return MSM_ERR_UNSUPPORTED;  // cells wider than a patch can hold
+    P->ablk = B;
+    P->apd = pd;
+  }
 
   // level stencil G0(n) = g^0(|h o n|) on the level-0 lattice; level k uses
   // 2^-k G0 because g^k(2^k r) = 2^-k g^0(r).
@@ -352,6 +367,14 @@ int build_plan(const msm_params* pp, Plan* P) {
     M(&D.aq[k], sizeof(double) * np);
     M(&D.au[k], T * np);
   }
+  // temporaries of the separable passes: the largest level pair, per dimension
+  size_t tsize = (size_t)grid_points(*P, 0);
+  for (int k = 0; k + 1 < P->levels; ++k) {
+    size_t t = 1;
+    for (int d = 0; d < 3; ++d) t *= (size_t)std::max(P->n[k][d], P->n[k + 1][d]);
+    tsize = std::max(tsize, t);
+  }
+  for (int i = 0; i < 2; ++i) M(&D.tmp[i], sizeof(double) * tsize);
   size_t ntop = (size_t)grid_points(*P, top);
   M((void**)&D.topq, sizeof(double) * ntop);
   M((void**)&D.topu, sizeof(double) * ntop);
@@ -362,6 +385,16 @@ int build_plan(const msm_params* pp, Plan* P) {
   if (cudaMemset(D.status, 0, sizeof(int)) != cudaSuccess) return MSM_ERR_CUDA;
   if (upload((void**)&D.topK, K) != cudaSuccess) return MSM_ERR_OOM;
   if (upload((void**)&D.cell_off, offs) != cudaSuccess) return MSM_ERR_OOM;
+  if (P->fp64) {
+    std::vector<R4<double>> sh;
+    for (auto& o : offs) sh.push_back({o.x * P->cw[0], o.y * P->cw[1], o.z * P->cw[2], 0.0});
+    if (upload(&D.cell_shift, sh) != cudaSuccess) return MSM_ERR_OOM;
+  } else {
+    std::vector<R4<float>> sh;
+    for (auto& o : offs)
+      sh.push_back({(float)(o.x * P->cw[0]), (float)(o.y * P->cw[1]), (float)(o.z * P->cw[2]), 0.f});
+    if (upload(&D.cell_shift, sh) != cudaSuccess) return MSM_ERR_OOM;
+  }
   std::vector<int> start;
   if (P->fp64) {
     std::vector<Segment<double>> segs;
@@ -381,11 +414,13 @@ int build_plan(const msm_params* pp, Plan* P) {
 void free_plan(Plan* P) {
   DeviceBuffers& D = P->d;
   void* ptrs[] = {D.keys[0], D.keys[1], D.idx[0], D.idx[1], D.hist, D.cell_start, D.atoms,
-                  D.gfrac, D.gbase, D.phis, D.fs, D.glong, D.topK, D.topq, D.topu, D.seg,
+                  D.gfrac, D.gbase, D.phis, D.fs, D.glong, D.topK, D.topq, D.topu, D.seg, D.cell_shift,
                   D.seg_start, D.cell_off, D.partial, D.scalars, D.status, D.hpos, D.hq,
                   D.hphi, D.hforce, D.henergy};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (int i = 0; i < 2; ++i)
+    if (D.tmp[i]) cudaFree(D.tmp[i]);
   for (int k = 0; k < kMaxLevels; ++k) {
     if (D.gq[k]) cudaFree(D.gq[k]);
     if (D.gu[k]) cudaFree(D.gu[k]);

@@ -236,9 +236,10 @@ def test_host_entry_point_matches_device(dev):
     Ed, phid, Fd = gpu_eval(plan, pos, q, dev)
     Eh, phih, Fh = plan.eval_host(torch.tensor(pos).pin_memory(), torch.tensor(q).pin_memory(),
                                   want_phi=True, want_force=True)
-    # same inputs, same kernels; only the order of floating-point atomics differs
-    assert abs(Eh.item() - Ed) <= 1e-9 * abs(Ed)
-    assert rel_rms(Fh.numpy(), Fd) <= 1e-9
+    # same inputs, same kernels; only the order of the FP32 shared-memory
+    # atomics of the anterpolation differs between the two runs
+    assert abs(Eh.item() - Ed) <= 1e-7 * abs(Ed)
+    assert rel_rms(Fh.numpy(), Fd) <= 1e-7
 
 
 def test_repeatable(dev):
