@@ -151,6 +151,25 @@ int msm_profile_read(msm_handle h, double* ms, int64_t* launches, int64_t* evals
 /* Name of a stage (e.g. "short_range"); "?" when out of range. */
 const char* msm_stage_name(int stage);
 
+/* Energy E = 1/2 sum_i q_i phi_i from per-atom charges q[n] and potentials
+ * phi[n] (double, device), written to energy[1] (double, device), computed in
+ * FP64 with a fixed two-pass reduction -- the same reduction msm_eval ends
+ * with, for callers that must not allocate device memory (an engine whose
+ * pool owns all device memory, or a step loop that cannot afford cudaMalloc,
+ * which may synchronise the device).  The paper has no counterpart.
+ *   - Allocates nothing: its scratch (one partial sum per 256 atoms) is a
+ *     file-scope device array of 65,536 doubles (512 KiB) that every GPU
+ *     loading the library holds until the process exits; n is therefore
+ *     limited to 16,777,216 atoms, larger n returns MSM_ERR_TOO_MANY_ATOMS.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one array: calls that overlap on the GPU (on
+ *     different streams, or from several threads) race.  Each call writes
+ *     every partial it reads, so nothing has to be cleared between calls.
+ *   - Asynchronous on cuda_stream; no plan is needed.
+ * Errors: INVALID_ARG, TOO_MANY_ATOMS, CUDA. */
+int msm_energy_noalloc(int64_t n, const double* q, const double* phi, double* energy, void* cuda_stream);
+
 /* Human-readable name of an MSM_ERR_* code. */
 const char* msm_strerror(int code);
 

@@ -36,7 +36,7 @@ _lib = None
 _D = C.POINTER(C.c_double)
 EXPORTS = ["msm_create", "msm_destroy", "msm_query", "msm_eval", "msm_eval_backward",
            "msm_eval_host", "msm_status", "msm_debug_grid", "msm_profile", "msm_profile_read",
-           "msm_stage_name", "msm_strerror"]
+           "msm_stage_name", "msm_energy_noalloc", "msm_strerror"]
 NSTAGES = 8
 
 
@@ -72,6 +72,8 @@ def load(path=LIB_PATH):
     L.msm_profile_read.restype = C.c_int
     L.msm_stage_name.argtypes = [C.c_int]
     L.msm_stage_name.restype = C.c_char_p
+    L.msm_energy_noalloc.argtypes = [C.c_int64, vp, vp, vp, vp]
+    L.msm_energy_noalloc.restype = C.c_int
     L.msm_strerror.argtypes = [C.c_int]
     L.msm_strerror.restype = C.c_char_p
     _lib = L
