@@ -75,27 +75,42 @@ __global__ void __launch_bounds__(kThreads) k_hist(const int* __restrict__ keys,
   hist[t * nblk + b] = h[t];
 }
 
-// Exclusive scan of `total` ints in place, one block of 1024 threads.
+// Exclusive scan of `total` ints in place, one block of 1024 threads walking
+// the array in coalesced tiles of 1024 (warp-shuffle scan inside a tile, a
+// running carry between tiles).
 __global__ void __launch_bounds__(1024) k_scan(int* __restrict__ data, int total) {
-  __shared__ int sums[1024];
-  int t = threadIdx.x;
-  int per = (total + 1023) / 1024;
-  int beg = min(total, t * per), end = min(total, beg + per);
-  int s = 0;
-  for (int i = beg; i < end; ++i) s += data[i];
-  sums[t] = s;
+  __shared__ int wsum[32];
+  __shared__ int carry_s;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t == 0) carry_s = 0;
   __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {  // Hillis-Steele inclusive scan
-    int v = (t >= off) ? sums[t - off] : 0;
+  for (int base = 0; base < total; base += 1024) {
+    const int i = base + t;
+    const int v = (i < total) ? data[i] : 0;
+    int x = v;  // inclusive warp scan
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    sums[t] += v;
+    if (warp == 0) {
+      int w = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      wsum[lane] = w;  // inclusive over warps
+    }
     __syncthreads();
-  }
-  int run = sums[t] - s;
-  for (int i = beg; i < end; ++i) {
-    int v = data[i];
-    data[i] = run;
-    run += v;
+    const int carry = carry_s;
+    const int excl = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - v;
+    if (i < total) data[i] = excl;
+    __syncthreads();
+    if (t == 1023) carry_s = excl + v;
+    __syncthreads();
   }
 }
 

@@ -12,6 +12,7 @@
 // transpose of interpolation is anterpolation, the transpose of prolongation
 // is restriction, and the lattice and top kernels are symmetric.
 #include <cmath>
+#include <type_traits>
 
 #include "msm_internal.h"
 
@@ -111,6 +112,56 @@ struct AnterpArgs {
   double cw_h[3];   // cell width in units of h
 };
 
+// One thread per atom, and the lanes of a warp take atoms from different
+// cells of the block: the block's atoms are listed rank-major (the first atom
+// of every cell, then the second of every cell, ...), so consecutive threads
+// work on different cells.  Atoms of one cell share most of their support,
+// so this keeps the shared-memory atomics of one warp instruction on
+// different points, and no lane idles while others finish a fuller cell.
+constexpr int kAnterpMaxAtoms = 4096;  // atoms per block listed in shared memory
+
+__device__ __forceinline__ int block_cells(const AnterpArgs& A, const int* __restrict__ cell_start, const int* c0,
+                                           int* cstart, int* ccount) {
+  int k = 0;
+  for (int bz = 0; bz < A.B; ++bz)
+    for (int by = 0; by < A.B; ++by)
+      for (int bx = 0; bx < A.B; ++bx) {
+        int x = c0[0] + bx, y = c0[1] + by, z = c0[2] + bz;
+        if (x >= A.nc[0] || y >= A.nc[1] || z >= A.nc[2]) continue;
+        int c = (z * A.nc[1] + y) * A.nc[0] + x;
+        cstart[k] = cell_start[c];
+        ccount[k] = cell_start[c + 1] - cell_start[c];
+        ++k;
+      }
+  return k;
+}
+
+// Rank-major list of the block's atoms (warp 0 builds it); returns the count,
+// or -1 when the block holds more atoms than the list can take.
+__device__ __forceinline__ int build_rank_list(int nk, const int* cstart, const int* ccount, int* list,
+                                               int* maxc_s) {
+  const int lane = threadIdx.x & 31;
+  int total = 0;
+  if (threadIdx.x < 32) {
+    int mx = 0;
+    for (int c = lane; c < nk; c += 32) mx = max(mx, ccount[c]);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int r = 0; r < mx; ++r)
+      for (int cb = 0; cb < nk; cb += 32) {
+        const int c = cb + lane;
+        const bool has = c < nk && ccount[c] > r;
+        const unsigned bal = __ballot_sync(0xffffffffu, has);
+        const int p = total + __popc(bal & ((1u << lane) - 1u));
+        if (has && p < kAnterpMaxAtoms) list[p] = cstart[c] + r;
+        total += __popc(bal);
+      }
+    if (lane == 0) *maxc_s = total;
+  }
+  __syncthreads();
+  total = *maxc_s;
+  return total > kAnterpMaxAtoms ? -1 : total;
+}
+
 template <typename T, typename ACC, int ORDER>
 __global__ void __launch_bounds__(256) k_anterp_patch(const R4<T>* __restrict__ gfrac,
                                                       const int4* __restrict__ gbase,
@@ -120,47 +171,30 @@ __global__ void __launch_bounds__(256) k_anterp_patch(const R4<T>* __restrict__ 
   constexpr int S = Basis<T, ORDER>::S, W = 2 * S;
   extern __shared__ unsigned char smem_raw[];
   ACC* patch = reinterpret_cast<ACC*>(smem_raw);
-  __shared__ int pref[65], cellid[64], ncs;
+  __shared__ int cstart[64], ccount[64], list[kAnterpMaxAtoms], tot_s;
   const int PD = A.pd, np = PD * PD * PD, tid = threadIdx.x;
   const int c0[3] = {(int)blockIdx.x * A.B, (int)blockIdx.y * A.B, (int)blockIdx.z * A.B};
-  int lo[3];
-  for (int d = 0; d < 3; ++d) lo[d] = (int)floor(c0[d] * A.cw_h[d]) - S - 1;
+  const int lo0 = (int)floor(c0[0] * A.cw_h[0]) - S - 1;
+  const int lo1 = (int)floor(c0[1] * A.cw_h[1]) - S - 1;
+  const int lo2 = (int)floor(c0[2] * A.cw_h[2]) - S - 1;
   for (int e = tid; e < np; e += blockDim.x) patch[e] = ACC(0);
-  if (tid == 0) {
-    int run = 0, k = 0;
-    for (int bz = 0; bz < A.B; ++bz)
-      for (int by = 0; by < A.B; ++by)
-        for (int bx = 0; bx < A.B; ++bx) {
-          int x = c0[0] + bx, y = c0[1] + by, z = c0[2] + bz;
-          if (x >= A.nc[0] || y >= A.nc[1] || z >= A.nc[2]) continue;
-          int c = (z * A.nc[1] + y) * A.nc[0] + x;
-          cellid[k] = c;
-          pref[k] = run;
-          run += cell_start[c + 1] - cell_start[c];
-          ++k;
-        }
-    pref[k] = run;
-    ncs = k;
-  }
+  __shared__ int nk_s;
+  if (tid == 0) nk_s = block_cells(A, cell_start, c0, cstart, ccount);
   __syncthreads();
-  const int nk = ncs, total = pref[nk];
-  const double sc = factor * (dscale ? *dscale : 1.0);
-  for (int kk = tid; kk < total; kk += blockDim.x) {
-    int a0 = 0, a1 = nk;  // last cell with pref <= kk
-    while (a1 - a0 > 1) {
-      int m = (a0 + a1) >> 1;
-      if (pref[m] <= kk) a0 = m;
-      else a1 = m;
-    }
-    const int i = cell_start[cellid[a0]] + (kk - pref[a0]);
+  const int nk = nk_s;
+  int total = build_rank_list(nk, cstart, ccount, list, &tot_s);
+  const T sc_all = T(factor * (dscale ? *dscale : 1.0));
+  const int count = total >= 0 ? total : 0;
+  for (int kk = tid; kk < count; kk += blockDim.x) {
+    const int i = list[kk];
     const R4<T> f = gfrac[i];
     const int4 b = gbase[i];
-    const T qi = T(sc) * f.w;
+    const T qi = sc_all * f.w;
     T wx[W], wy[W], wz[W];
     weights<T, ORDER>(f.x, wx);
     weights<T, ORDER>(f.y, wy);
     weights<T, ORDER>(f.z, wz);
-    const int px = b.x - lo[0], py = b.y - lo[1], pz = b.z - lo[2];
+    const int px = b.x - lo0, py = b.y - lo1, pz = b.z - lo2;
     if (px >= 0 && py >= 0 && pz >= 0 && px + W <= PD && py + W <= PD && pz + W <= PD) {
 #pragma unroll
       for (int c = 0; c < W; ++c) {
@@ -183,11 +217,31 @@ __global__ void __launch_bounds__(256) k_anterp_patch(const R4<T>* __restrict__ 
           }
     }
   }
+  if (total < 0) {  // more atoms than the list holds: one thread per atom, straight to the grid
+    for (int c = 0; c < nk; ++c)
+      for (int m = tid; m < ccount[c]; m += blockDim.x) {
+        const int i = cstart[c] + m;
+        const R4<T> f = gfrac[i];
+        const int4 b = gbase[i];
+        const T qi = sc_all * f.w;
+        T wx[W], wy[W], wz[W];
+        weights<T, ORDER>(f.x, wx);
+        weights<T, ORDER>(f.y, wy);
+        weights<T, ORDER>(f.z, wz);
+        for (int cc = 0; cc < W; ++cc)
+          for (int bb = 0; bb < W; ++bb)
+            for (int a = 0; a < W; ++a) {
+              int sx = slot(b.x + a, G.n[0], G.lo[0], G.periodic), sy = slot(b.y + bb, G.n[1], G.lo[1], G.periodic),
+                  sz = slot(b.z + cc, G.n[2], G.lo[2], G.periodic);
+              atomicAdd(grid + ((size_t)sz * G.n[1] + sy) * G.n[0] + sx, (double)(qi * wz[cc] * wy[bb] * wx[a]));
+            }
+      }
+  }
   __syncthreads();
   for (int e = tid; e < np; e += blockDim.x) {
     const ACC v = patch[e];
     if (v == ACC(0)) continue;
-    int ix = lo[0] + e % PD, iy = lo[1] + (e / PD) % PD, iz = lo[2] + e / (PD * PD);
+    int ix = lo0 + e % PD, iy = lo1 + (e / PD) % PD, iz = lo2 + e / (PD * PD);
     if (!G.periodic && (ix < G.lo[0] || iy < G.lo[1] || iz < G.lo[2] || ix >= G.lo[0] + G.n[0] ||
                         iy >= G.lo[1] + G.n[1] || iz >= G.lo[2] + G.n[2]))
       continue;
@@ -279,15 +333,19 @@ __global__ void k_prolong_axis(const T* __restrict__ in, T* __restrict__ out, Ax
 }
 
 // ---- lattice cutoff: z-streaming shared-memory planes, register tiles ----
-// A block of 4 warps owns a 32 x 8 x 4 brick of outputs; warp w owns plane
-// z0 + w, and each lane 8 consecutive x outputs of one row.  The input
-// planes z0 - Ez .. z0 + 3 + Ez are staged in turn (a 2-D window with halo
-// Ex, Ey, converted from the FP64 charge grid); for staged plane zi, warp w
-// applies the stencil rows of dz = zi - (z0 + w) as segments of 8 taps along
-// x: 64 FMAs per segment from 15 shared loads.  The odd row pitch keeps the
-// 32 lanes on 32 banks.  Per-plane partial sums are folded into the totals
-// with TwoSum in mixed precision.
-constexpr int LBX = 32, LBY = 8, LBZ = 4, LPX = 8;
+// A block of 4 warps owns a brick of outputs 32 (x) x LBY (y) x 4 (z); warp w
+// owns plane z0 + w.  The input planes are staged one at a time in shared
+// memory (a 2-D window with halo Ex, Ey; odd row pitch so the lanes of a warp
+// sit on distinct banks); for staged plane zi, warp w applies the stencil rows
+// of dz = zi - (z0 + w) as segments of 8 taps along x on register tiles of
+// 8 consecutive x outputs per lane.  Coarse levels with few bricks split the
+// input planes over several blocks (nsplit) that add their partial sums into
+// the zeroed output; per-plane partial sums are folded into the totals with
+// TwoSum in mixed precision.
+//   FP64: one row per lane (LBY = 8), scalar FMA.
+//   FP32: two rows per lane (LBY = 16) packed into float2, one FFMA2 per two
+//         outputs, coefficients stored pre-duplicated as float2 pairs.
+constexpr int LBX = 32, LBZ = 4, LPX = 8;
 
 template <typename T>
 __device__ __forceinline__ void two_sum_add(T& s, T& c, T x) {
@@ -297,57 +355,69 @@ __device__ __forceinline__ void two_sum_add(T& s, T& c, T x) {
   s = t;
 }
 
+// Stages plane zi of q into plane[] (rows SY, staged width SXw, pitch SX).
+template <typename T>
+__device__ __forceinline__ void stage_plane(T* plane, const T* __restrict__ q, const GridDims& G, int zi, int x0,
+                                            int y0, int Ex, int Ey, int SXw, int SX, int SY) {
+  int gz;
+  bool zok;
+  if (G.periodic) {
+    gz = zi % G.n[2];
+    if (gz < 0) gz += G.n[2];
+    zok = true;
+  } else {
+    gz = zi;
+    zok = (zi >= 0 && zi < G.n[2]);
+  }
+  for (int e = threadIdx.x; e < SY * SXw; e += blockDim.x) {
+    int xx = e % SXw, yy = e / SXw;
+    int gx = x0 - Ex + xx, gy = y0 - Ey + yy;
+    T v = T(0);
+    if (G.periodic) {
+      gx %= G.n[0];
+      if (gx < 0) gx += G.n[0];
+      gy %= G.n[1];
+      if (gy < 0) gy += G.n[1];
+      v = q[((size_t)gz * G.n[1] + gy) * G.n[0] + gx];
+    } else if (zok && gx >= 0 && gx < G.n[0] && gy >= 0 && gy < G.n[1]) {
+      v = q[((size_t)gz * G.n[1] + gy) * G.n[0] + gx];
+    }
+    plane[yy * SX + xx] = v;
+  }
+}
+
+struct LatticeArgs {
+  int Ex, Ey, Ez;
+  int nsplit;  // blocks sharing one brick's input planes
+  int nbz;     // bricks along z
+};
+
 template <typename T, bool COMP>
-__global__ void __launch_bounds__(128) k_lattice(const double* __restrict__ q, T* __restrict__ u, GridDims G,
+__global__ void __launch_bounds__(128) k_lattice(const T* __restrict__ q, T* __restrict__ u, GridDims G,
                                                  const Segment<T>* __restrict__ seg,
-                                                 const int* __restrict__ seg_start, int Ex, int Ey, int Ez,
-                                                 T scale) {
+                                                 const int* __restrict__ seg_start, LatticeArgs L, T scale) {
+  constexpr int LBY = 8;
   extern __shared__ unsigned char smem_raw[];
   T* plane = reinterpret_cast<T*>(smem_raw);
-  const int SXw = LBX + 2 * Ex + kSeg;   // staged width
-  const int SX = SXw | 1;                // odd row pitch: conflict-free rows
-  const int SY = LBY + 2 * Ey;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tx = lane & 3, ty = lane >> 2;
-  const int x0 = blockIdx.x * LBX, y0 = blockIdx.y * LBY, z0 = blockIdx.z * LBZ;
-  const int zo = z0 + warp;
+  const int Ex = L.Ex, Ey = L.Ey, Ez = L.Ez;
+  const int SXw = LBX + 2 * Ex + kSeg, SX = SXw | 1, SY = LBY + 2 * Ey;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tx = lane & 3, ty = lane >> 2;
+  const int bz = blockIdx.z % L.nbz, part = blockIdx.z / L.nbz;
+  const int x0 = blockIdx.x * LBX, y0 = blockIdx.y * LBY, z0 = bz * LBZ, zo = z0 + warp;
+  const int nplanes = LBZ + 2 * Ez, per = (nplanes + L.nsplit - 1) / L.nsplit;
+  const int zbeg = z0 - Ez + part * per, zend = min(z0 - Ez + nplanes, zbeg + per);
   T acc[LPX], cmp[LPX];
 #pragma unroll
   for (int j = 0; j < LPX; ++j) acc[j] = cmp[j] = T(0);
-
-  for (int zi = z0 - Ez; zi < z0 + LBZ + Ez; ++zi) {
+  for (int zi = zbeg; zi < zend; ++zi) {
     __syncthreads();
-    int gz;
-    bool zok;
-    if (G.periodic) {
-      gz = zi % G.n[2];
-      if (gz < 0) gz += G.n[2];
-      zok = true;
-    } else {
-      gz = zi;
-      zok = (zi >= 0 && zi < G.n[2]);
-    }
-    for (int e = tid; e < SY * SXw; e += 128) {
-      int xx = e % SXw, yy = e / SXw;
-      int gx = x0 - Ex + xx, gy = y0 - Ey + yy;
-      T v = T(0);
-      if (G.periodic) {
-        gx %= G.n[0];
-        if (gx < 0) gx += G.n[0];
-        gy %= G.n[1];
-        if (gy < 0) gy += G.n[1];
-        v = (T)q[((size_t)gz * G.n[1] + gy) * G.n[0] + gx];
-      } else if (zok && gx >= 0 && gx < G.n[0] && gy >= 0 && gy < G.n[1]) {
-        v = (T)q[((size_t)gz * G.n[1] + gy) * G.n[0] + gx];
-      }
-      plane[yy * SX + xx] = v;
-    }
+    stage_plane(plane, q, G, zi, x0, y0, Ex, Ey, SXw, SX, SY);
     __syncthreads();
     const int dz = zi - zo;
     if (dz < -Ez || dz > Ez || zo >= G.n[2]) continue;  // warp-uniform
-    T part[LPX];
+    T part_[LPX];
 #pragma unroll
-    for (int j = 0; j < LPX; ++j) part[j] = T(0);
+    for (int j = 0; j < LPX; ++j) part_[j] = T(0);
     const int s1 = seg_start[dz + Ez + 1];
     for (int s = seg_start[dz + Ez]; s < s1; ++s) {
       const Segment<T> sg = seg[s];
@@ -358,12 +428,12 @@ __global__ void __launch_bounds__(128) k_lattice(const double* __restrict__ q, T
 #pragma unroll
       for (int k = 0; k < kSeg; ++k)
 #pragma unroll
-        for (int j = 0; j < LPX; ++j) part[j] += sg.g[k] * win[j + k];
+        for (int j = 0; j < LPX; ++j) part_[j] += sg.g[k] * win[j + k];
     }
 #pragma unroll
     for (int j = 0; j < LPX; ++j) {
-      if (COMP) two_sum_add(acc[j], cmp[j], part[j]);
-      else acc[j] += part[j];
+      if (COMP) two_sum_add(acc[j], cmp[j], part_[j]);
+      else acc[j] += part_[j];
     }
   }
   if (zo >= G.n[2]) return;
@@ -372,57 +442,73 @@ __global__ void __launch_bounds__(128) k_lattice(const double* __restrict__ q, T
 #pragma unroll
   for (int j = 0; j < LPX; ++j) {
     int x = x0 + tx * LPX + j;
-    if (x < G.n[0]) u[((size_t)zo * G.n[1] + y) * G.n[0] + x] = scale * (acc[j] + cmp[j]);
+    if (x >= G.n[0]) continue;
+    T v = scale * (acc[j] + cmp[j]);
+    if (L.nsplit > 1) atomicAdd(u + ((size_t)zo * G.n[1] + y) * G.n[0] + x, v);
+    else u[((size_t)zo * G.n[1] + y) * G.n[0] + x] = v;
   }
 }
 
-// Coarse levels have too few points to fill the GPU with bricks: one thread
-// per (output point, stencil plane dz), reading the charges straight from
-// global memory, adding its plane's share into the zeroed output.
-template <typename T>
-__global__ void __launch_bounds__(128) k_lattice_small(const double* __restrict__ q, T* __restrict__ u,
-                                                       GridDims G, const Segment<T>* __restrict__ seg,
-                                                       const int* __restrict__ seg_start, int Ez, T scale) {
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t np = (int64_t)G.n[0] * G.n[1] * G.n[2];
-  if (p >= np) return;
-  const int dz = (int)blockIdx.y - Ez;
-  const int x = (int)(p % G.n[0]), y = (int)((p / G.n[0]) % G.n[1]), z = (int)(p / ((int64_t)G.n[0] * G.n[1]));
-  int zz = z + dz;
-  if (G.periodic) {
-    zz %= G.n[2];
-    if (zz < 0) zz += G.n[2];
-  } else if (zz < 0 || zz >= G.n[2]) {
-    return;
-  }
-  T sum = 0;
-  const int s1 = seg_start[dz + Ez + 1];
-  for (int s = seg_start[dz + Ez]; s < s1; ++s) {
-    const Segment<T> sg = seg[s];
-    int yy = y + sg.dy;
-    if (G.periodic) {
-      yy %= G.n[1];
-      if (yy < 0) yy += G.n[1];
-    } else if (yy < 0 || yy >= G.n[1]) {
-      continue;
-    }
-    const double* row = q + ((size_t)zz * G.n[1] + yy) * G.n[0];
-    int xx = x + sg.dx0;
-    if (G.periodic) {  // wrap once, then step with a compare
-      xx %= G.n[0];
-      if (xx < 0) xx += G.n[0];
+__device__ __forceinline__ void two_sum_add2(float2& s, float2& c, float2 x) {
+  two_sum_add(s.x, c.x, x.x);
+  two_sum_add(s.y, c.y, x.y);
+}
+
+__global__ void __launch_bounds__(128) k_lattice_f2(const float* __restrict__ q, float* __restrict__ u, GridDims G,
+                                                    const Segment2* __restrict__ seg,
+                                                    const int* __restrict__ seg_start, LatticeArgs L, float scale) {
+  constexpr int LBY = 16;
+  extern __shared__ unsigned char smem_raw[];
+  float* plane = reinterpret_cast<float*>(smem_raw);
+  const int Ex = L.Ex, Ey = L.Ey, Ez = L.Ez;
+  const int SXw = LBX + 2 * Ex + kSeg, SX = SXw | 1, SY = LBY + 2 * Ey;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tx = lane & 3, ty = lane >> 2;
+  const int bz = blockIdx.z % L.nbz, part = blockIdx.z / L.nbz;
+  const int x0 = blockIdx.x * LBX, y0 = blockIdx.y * LBY, z0 = bz * LBZ, zo = z0 + warp;
+  const int nplanes = LBZ + 2 * Ez, per = (nplanes + L.nsplit - 1) / L.nsplit;
+  const int zbeg = z0 - Ez + part * per, zend = min(z0 - Ez + nplanes, zbeg + per);
+  float2 acc[LPX], cmp[LPX];  // (row ty, row ty + 8) of the 8 x outputs
 #pragma unroll
-      for (int k = 0; k < kSeg; ++k) {
-        sum += sg.g[k] * (T)row[xx];
-        if (++xx == G.n[0]) xx = 0;
-      }
-    } else {
+  for (int j = 0; j < LPX; ++j) acc[j] = cmp[j] = make_float2(0.f, 0.f);
+  for (int zi = zbeg; zi < zend; ++zi) {
+    __syncthreads();
+    stage_plane(plane, q, G, zi, x0, y0, Ex, Ey, SXw, SX, SY);
+    __syncthreads();
+    const int dz = zi - zo;
+    if (dz < -Ez || dz > Ez || zo >= G.n[2]) continue;  // warp-uniform
+    float2 part_[LPX];
 #pragma unroll
-      for (int k = 0; k < kSeg; ++k, ++xx)
-        if (xx >= 0 && xx < G.n[0]) sum += sg.g[k] * (T)row[xx];
+    for (int j = 0; j < LPX; ++j) part_[j] = make_float2(0.f, 0.f);
+    const int s1 = seg_start[dz + Ez + 1];
+    for (int s = seg_start[dz + Ez]; s < s1; ++s) {
+      const Segment2 sg = seg[s];
+      const float* r0 = plane + (ty + Ey + sg.dy) * SX + tx * LPX + Ex + sg.dx0;
+      const float* r1 = r0 + 8 * SX;
+      float2 win[LPX + kSeg - 1];
+#pragma unroll
+      for (int k = 0; k < LPX + kSeg - 1; ++k) win[k] = make_float2(r0[k], r1[k]);
+#pragma unroll
+      for (int k = 0; k < kSeg; ++k)
+#pragma unroll
+        for (int j = 0; j < LPX; ++j) part_[j] = __ffma2_rn(sg.g[k], win[j + k], part_[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < LPX; ++j) two_sum_add2(acc[j], cmp[j], part_[j]);
+  }
+  if (zo >= G.n[2]) return;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int y = y0 + ty + 8 * r;
+    if (y >= G.n[1]) continue;
+#pragma unroll
+    for (int j = 0; j < LPX; ++j) {
+      int x = x0 + tx * LPX + j;
+      if (x >= G.n[0]) continue;
+      float v = scale * (r == 0 ? acc[j].x + cmp[j].x : acc[j].y + cmp[j].y);
+      if (L.nsplit > 1) atomicAdd(u + ((size_t)zo * G.n[1] + y) * G.n[0] + x, v);
+      else u[((size_t)zo * G.n[1] + y) * G.n[0] + x] = v;
     }
   }
-  atomicAdd(u + p, scale * sum);
 }
 
 // ---- top level: all pairs of the coarsest grid, FP64 ----
@@ -520,19 +606,116 @@ struct AssembleArgs {
   double inv_h[3];
 };
 
+// Interpolation through the same per-block patches: a block stages the u^0
+// points its atoms can reach (PD^3, wrapped) in shared memory, then each
+// thread gathers its atoms' (2S)^3 taps from there.
+template <typename T, int ORDER>
+__device__ __forceinline__ void interp_patch_atom(const R4<T>& f, const int4& b, const T* __restrict__ patch, int PD,
+                                                  int lo0, int lo1, int lo2, const T* __restrict__ u0,
+                                                  const GridDims& G, const T ih[3], T& p, T g[3]) {
+  constexpr int W = 2 * Basis<T, ORDER>::S;
+  const int px = b.x - lo0, py = b.y - lo1, pz = b.z - lo2;
+  if (px >= 0 && py >= 0 && pz >= 0 && px + W <= PD && py + W <= PD && pz + W <= PD) {
+    T wx[W], wy[W], wz[W], dx[W], dy[W], dz[W];
+    weights<T, ORDER>(f.x, wx);
+    weights<T, ORDER>(f.y, wy);
+    weights<T, ORDER>(f.z, wz);
+    dweights<T, ORDER>(f.x, dx);
+    dweights<T, ORDER>(f.y, dy);
+    dweights<T, ORDER>(f.z, dz);
+    T P = 0, Gx = 0, Gy = 0, Gz = 0;
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      T pzv = 0, gxz = 0, gyz = 0;
+#pragma unroll
+      for (int bb = 0; bb < W; ++bb) {
+        const T* row = patch + ((pz + c) * PD + py + bb) * PD + px;
+        T sa = 0, sd = 0;
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+          T v = row[a];
+          sa += wx[a] * v;
+          sd += dx[a] * v;
+        }
+        pzv += wy[bb] * sa;
+        gxz += wy[bb] * sd;
+        gyz += dy[bb] * sa;
+      }
+      P += wz[c] * pzv;
+      Gx += wz[c] * gxz;
+      Gy += wz[c] * gyz;
+      Gz += dz[c] * pzv;
+    }
+    p = P;
+    g[0] = Gx * ih[0];
+    g[1] = Gy * ih[1];
+    g[2] = Gz * ih[2];
+  } else {
+    interp_atom<T, ORDER>(f, b, u0, G, ih, p, g);
+  }
+}
+
+// Stages the patch of u^0 for the block at cell block c0; returns the atom
+// count of the block's rank-major list (-1 when it does not fit).
+template <typename T>
+__device__ __forceinline__ int stage_interp_block(const AnterpArgs& A, const int* __restrict__ cell_start,
+                                                  const T* __restrict__ u0, const GridDims& G, T* patch, int lo0,
+                                                  int lo1, int lo2, int* cstart, int* ccount, int* list, int* nk_s,
+                                                  int* tot_s) {
+  const int PD = A.pd, np = PD * PD * PD;
+  const int c0[3] = {(int)blockIdx.x * A.B, (int)blockIdx.y * A.B, (int)blockIdx.z * A.B};
+  for (int e = threadIdx.x; e < np; e += blockDim.x) {
+    int ix = lo0 + e % PD, iy = lo1 + (e / PD) % PD, iz = lo2 + e / (PD * PD);
+    T v = T(0);
+    if (G.periodic) {
+      v = u0[((size_t)slot(iz, G.n[2], 0, 1) * G.n[1] + slot(iy, G.n[1], 0, 1)) * G.n[0] + slot(ix, G.n[0], 0, 1)];
+    } else if (ix >= G.lo[0] && iy >= G.lo[1] && iz >= G.lo[2] && ix < G.lo[0] + G.n[0] && iy < G.lo[1] + G.n[1] &&
+               iz < G.lo[2] + G.n[2]) {
+      v = u0[((size_t)(iz - G.lo[2]) * G.n[1] + (iy - G.lo[1])) * G.n[0] + (ix - G.lo[0])];
+    }
+    patch[e] = v;
+  }
+  if (threadIdx.x == 0) *nk_s = block_cells(A, cell_start, c0, cstart, ccount);
+  __syncthreads();
+  return build_rank_list(*nk_s, cstart, ccount, list, tot_s);
+}
+
 template <typename T, int ORDER>
 __global__ void __launch_bounds__(256) k_interp_fwd(
-    const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm, int n,
-    const T* __restrict__ u0, GridDims G, AssembleArgs A, const T* __restrict__ phis,
-    R4<T>* __restrict__ fs, R4<T>* __restrict__ glong, double* __restrict__ phi_out,
+    const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm,
+    const int* __restrict__ cell_start, AnterpArgs AA, const T* __restrict__ u0, GridDims G, AssembleArgs A,
+    const T* __restrict__ phis, R4<T>* __restrict__ fs, R4<T>* __restrict__ glong, double* __restrict__ phi_out,
     double* __restrict__ force_out, double* __restrict__ partial) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int S = Basis<T, ORDER>::S;
+  extern __shared__ unsigned char smem_raw[];
+  T* patch = reinterpret_cast<T*>(smem_raw);
+  __shared__ int cstart[64], ccount[64], list[kAnterpMaxAtoms], nk_s, tot_s;
+  const int c0[3] = {(int)blockIdx.x * AA.B, (int)blockIdx.y * AA.B, (int)blockIdx.z * AA.B};
+  const int lo0 = (int)floor(c0[0] * AA.cw_h[0]) - S - 1;
+  const int lo1 = (int)floor(c0[1] * AA.cw_h[1]) - S - 1;
+  const int lo2 = (int)floor(c0[2] * AA.cw_h[2]) - S - 1;
+  const int total = stage_interp_block<T>(AA, cell_start, u0, G, patch, lo0, lo1, lo2, cstart, ccount, list, &nk_s,
+                                          &tot_s);
+  const T ih[3] = {T(A.inv_h[0]), T(A.inv_h[1]), T(A.inv_h[2])};
   double e = 0.0;
-  if (i < n) {
+  const int nk = nk_s;
+  // atoms from the list, or (over-full block) walked cell by cell
+  const int nlist = total >= 0 ? total : 0;
+  int walk_c = 0, walk_m = threadIdx.x;
+  for (int kk = threadIdx.x;; kk += blockDim.x) {
+    int i;
+    if (total >= 0) {
+      if (kk >= nlist) break;
+      i = list[kk];
+    } else {
+      while (walk_c < nk && walk_m >= ccount[walk_c]) walk_m -= ccount[walk_c++];
+      if (walk_c >= nk) break;
+      i = cstart[walk_c] + walk_m;
+      walk_m += blockDim.x;
+    }
     const R4<T> f = gfrac[i];
-    const T ih[3] = {T(A.inv_h[0]), T(A.inv_h[1]), T(A.inv_h[2])};
     T p, g[3];
-    interp_atom<T, ORDER>(f, gbase[i], u0, G, ih, p, g);
+    interp_patch_atom<T, ORDER>(f, gbase[i], patch, AA.pd, lo0, lo1, lo2, u0, G, ih, p, g);
     R4<T> s = fs[i];
     const double qi = (double)f.w;
     const double phi = A.kc * ((double)phis[i] + (double)p - qi * A.self_c);
@@ -546,10 +729,10 @@ __global__ void __launch_bounds__(256) k_interp_fwd(
     s.w = p;
     fs[i] = s;
     glong[i] = R4<T>{g[0], g[1], g[2], T(0)};
-    e = qi * phi;
+    e += qi * phi;
   }
   double bsum = block_sum<256>(e);
-  if (threadIdx.x == 0) partial[blockIdx.x] = bsum;
+  if (threadIdx.x == 0) partial[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = bsum;
 }
 
 __global__ void __launch_bounds__(1024) k_energy_final(const double* __restrict__ partial, int nb,
@@ -563,26 +746,49 @@ __global__ void __launch_bounds__(1024) k_energy_final(const double* __restrict_
 // adjoint assembly: av0 = M (anterpolated 1/2 gE q) on the grid
 template <typename T, int ORDER>
 __global__ void __launch_bounds__(256) k_interp_bwd(
-    const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm, int n,
-    const T* __restrict__ av0, GridDims G, AssembleArgs A, const T* __restrict__ phis,
-    const R4<T>* __restrict__ fs, const R4<T>* __restrict__ glong, const double* __restrict__ gE,
-    double* __restrict__ grad_pos, double* __restrict__ grad_q) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const R4<T> f = gfrac[i];
+    const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm,
+    const int* __restrict__ cell_start, AnterpArgs AA, const T* __restrict__ av0, GridDims G, AssembleArgs A,
+    const T* __restrict__ phis, const R4<T>* __restrict__ fs, const R4<T>* __restrict__ glong,
+    const double* __restrict__ gE, double* __restrict__ grad_pos, double* __restrict__ grad_q) {
+  constexpr int S = Basis<T, ORDER>::S;
+  extern __shared__ unsigned char smem_raw[];
+  T* patch = reinterpret_cast<T*>(smem_raw);
+  __shared__ int cstart[64], ccount[64], list[kAnterpMaxAtoms], nk_s, tot_s;
+  const int c0[3] = {(int)blockIdx.x * AA.B, (int)blockIdx.y * AA.B, (int)blockIdx.z * AA.B};
+  const int lo0 = (int)floor(c0[0] * AA.cw_h[0]) - S - 1;
+  const int lo1 = (int)floor(c0[1] * AA.cw_h[1]) - S - 1;
+  const int lo2 = (int)floor(c0[2] * AA.cw_h[2]) - S - 1;
+  const int total = stage_interp_block<T>(AA, cell_start, av0, G, patch, lo0, lo1, lo2, cstart, ccount, list, &nk_s,
+                                          &tot_s);
   const T ih[3] = {T(A.inv_h[0]), T(A.inv_h[1]), T(A.inv_h[2])};
-  T v, gv[3];
-  interp_atom<T, ORDER>(f, gbase[i], av0, G, ih, v, gv);
-  const R4<T> s = fs[i];
-  const R4<T> gl = glong[i];
-  const double g = *gE, qi = (double)f.w;
-  const int o = perm[i];
-  if (grad_q)
-    grad_q[o] = A.kc * (g * ((double)phis[i] - qi * A.self_c) + 0.5 * g * (double)s.w + (double)v);
-  if (grad_pos) {
-    grad_pos[3 * (size_t)o + 0] = A.kc * (-g * (double)s.x + 0.5 * g * qi * (double)gl.x + qi * (double)gv[0]);
-    grad_pos[3 * (size_t)o + 1] = A.kc * (-g * (double)s.y + 0.5 * g * qi * (double)gl.y + qi * (double)gv[1]);
-    grad_pos[3 * (size_t)o + 2] = A.kc * (-g * (double)s.z + 0.5 * g * qi * (double)gl.z + qi * (double)gv[2]);
+  const double gg = *gE;
+  const int nk = nk_s, nlist = total >= 0 ? total : 0;
+  int walk_c = 0, walk_m = threadIdx.x;
+  for (int kk = threadIdx.x;; kk += blockDim.x) {
+    int i;
+    if (total >= 0) {
+      if (kk >= nlist) break;
+      i = list[kk];
+    } else {
+      while (walk_c < nk && walk_m >= ccount[walk_c]) walk_m -= ccount[walk_c++];
+      if (walk_c >= nk) break;
+      i = cstart[walk_c] + walk_m;
+      walk_m += blockDim.x;
+    }
+    const R4<T> f = gfrac[i];
+    T v, gv[3];
+    interp_patch_atom<T, ORDER>(f, gbase[i], patch, AA.pd, lo0, lo1, lo2, av0, G, ih, v, gv);
+    const R4<T> s = fs[i];
+    const R4<T> gl = glong[i];
+    const double qi = (double)f.w;
+    const int o = perm[i];
+    if (grad_q)
+      grad_q[o] = A.kc * (gg * ((double)phis[i] - qi * A.self_c) + 0.5 * gg * (double)s.w + (double)v);
+    if (grad_pos) {
+      grad_pos[3 * (size_t)o + 0] = A.kc * (-gg * (double)s.x + 0.5 * gg * qi * (double)gl.x + qi * (double)gv[0]);
+      grad_pos[3 * (size_t)o + 1] = A.kc * (-gg * (double)s.y + 0.5 * gg * qi * (double)gl.y + qi * (double)gv[1]);
+      grad_pos[3 * (size_t)o + 2] = A.kc * (-gg * (double)s.z + 0.5 * gg * qi * (double)gl.z + qi * (double)gv[2]);
+    }
   }
 }
 
@@ -708,33 +914,53 @@ cudaError_t launch_prolong(Plan& P, int k, const void* coarse, void* fine, cudaS
   return cudaGetLastError();
 }
 
-template <typename T, bool COMP>
-void lattice_t(Plan& P, int k, const double* qk, T* uk, cudaStream_t st) {
+__global__ void k_f64_to_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t count) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) dst[i] = (float)src[i];
+}
+
+// Lattice cutoff of level k from the FP64 charges qk.  Mixed precision first
+// converts the level's charges to FP32 once (on GB300 the conversion runs on
+// the slow FP64 pipe, so it must not sit in the per-tap loop).
+template <typename T>
+void lattice_t(Plan& P, int k, const double* qk64, T* uk, cudaStream_t st) {
   GridDims G = dims_of(P, k);
-  dim3 grid(blocks_for(G.n[0], LBX), blocks_for(G.n[1], LBY), blocks_for(G.n[2], LBZ));
-  T scale = (T)std::ldexp(1.0, -k);
-  if ((int64_t)grid.x * grid.y * grid.z < 2 * 152) {  // coarse level: split the stencil planes instead
-    cudaMemsetAsync(uk, 0, sizeof(T) * (size_t)grid_points(P, k), st);
-    dim3 g2(blocks_for(grid_points(P, k), 128), 2 * P.E[2] + 1);
-    k_lattice_small<T><<<g2, 128, 0, st>>>(qk, uk, G, (const Segment<T>*)P.d.seg, P.d.seg_start, P.E[2], scale);
+  const bool f32 = !std::is_same<T, double>::value;
+  const T* qk = (const T*)qk64;
+  if (f32) {
+    float* qf = (float*)P.d.tmp[0];  // free between the restriction and the prolongation passes
+    k_f64_to_f32<<<blocks_for(grid_points(P, k), 256), 256, 0, st>>>(qk64, qf, grid_points(P, k));
     P.launches += 1;
-    return;
+    qk = (const T*)qf;
   }
+  const int LBY = f32 ? 16 : 8;
+  LatticeArgs L;
+  L.Ex = P.E[0];
+  L.Ey = P.E[1];
+  L.Ez = P.E[2];
+  L.nbz = (int)blocks_for(G.n[2], LBZ);
+  int64_t bricks = (int64_t)blocks_for(G.n[0], LBX) * blocks_for(G.n[1], LBY) * L.nbz;
+  L.nsplit = (int)std::min<int64_t>(LBZ + 2 * L.Ez, std::max<int64_t>(1, (4 * 152 + bricks - 1) / bricks));
+  if (L.nsplit > 1) {
+    cudaMemsetAsync(uk, 0, sizeof(T) * (size_t)grid_points(P, k), st);
+    P.launches += 1;
+  }
+  dim3 grid(blocks_for(G.n[0], LBX), blocks_for(G.n[1], LBY), L.nbz * L.nsplit);
   int SX = (LBX + 2 * P.E[0] + kSeg) | 1, SY = LBY + 2 * P.E[1];
   size_t sm = sizeof(T) * SX * SY;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_lattice<T, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
+  T scale = (T)std::ldexp(1.0, -k);
+  if (f32) {
+    k_lattice_f2<<<grid, 128, sm, st>>>((const float*)qk, (float*)uk, G, (const Segment2*)P.d.seg2, P.d.seg_start,
+                                        L, (float)scale);
+  } else {
+    k_lattice<T, false><<<grid, 128, sm, st>>>(qk, uk, G, (const Segment<T>*)P.d.seg, P.d.seg_start, L, scale);
   }
-  k_lattice<T, COMP><<<grid, 128, sm, st>>>(qk, uk, G, (const Segment<T>*)P.d.seg, P.d.seg_start, P.E[0], P.E[1],
-                                           P.E[2], scale);
 }
 
 cudaError_t launch_lattice(Plan& P, int k, const void* qk, void* uk, cudaStream_t st) {
   P.launches += 1;
-  if (P.fp64) lattice_t<double, false>(P, k, (const double*)qk, (double*)uk, st);
-  else lattice_t<float, true>(P, k, (const double*)qk, (float*)uk, st);
+  if (P.fp64) lattice_t<double>(P, k, (const double*)qk, (double*)uk, st);
+  else lattice_t<float>(P, k, (const double*)qk, (float*)uk, st);
   return cudaGetLastError();
 }
 
@@ -752,26 +978,45 @@ cudaError_t launch_top(Plan& P, const void* qt, void* ut, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+AnterpArgs patch_args(const Plan& P) {
+  AnterpArgs A;
+  for (int d = 0; d < 3; ++d) {
+    A.nc[d] = P.nc[d];
+    A.cw_h[d] = P.cw[d] / P.h[d];
+  }
+  A.B = P.ablk;
+  A.pd = P.apd;
+  return A;
+}
+
 cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, double* phi, double* force,
                                   cudaStream_t st) {
   GridDims G = dims_of(P, 0);
   AssembleArgs A = assemble_args(P);
-  unsigned nb = blocks_for(n, 256);
+  AnterpArgs AA = patch_args(P);
+  dim3 grid(blocks_for(P.nc[0], AA.B), blocks_for(P.nc[1], AA.B), blocks_for(P.nc[2], AA.B));
+  int nb = (int)(grid.x * grid.y * grid.z);
   if (n > 0) {
-#define MSM_FWD(T, O)                                                                                  \
-  k_interp_fwd<T, O><<<nb, 256, 0, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.idx[0], (int)n,      \
-                                         (const T*)P.d.gu[0], G, A, (const T*)P.d.phis, (R4<T>*)P.d.fs, \
-                                         (R4<T>*)P.d.glong, phi, force, P.d.partial)
+    size_t sm = (P.fp64 ? 8 : 4) * (size_t)AA.pd * AA.pd * AA.pd;
+#define MSM_FWD(T, O)                                                                                            \
+  {                                                                                                              \
+    static bool attr = false;                                                                                    \
+    if (!attr) {                                                                                                 \
+      cudaFuncSetAttribute(k_interp_fwd<T, O>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);         \
+      attr = true;                                                                                               \
+    }                                                                                                            \
+    k_interp_fwd<T, O><<<grid, 256, sm, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.idx[0], P.d.cell_start, AA, \
+                                              (const T*)P.d.gu[0], G, A, (const T*)P.d.phis, (R4<T>*)P.d.fs,    \
+                                              (R4<T>*)P.d.glong, phi, force, P.d.partial);                      \
+  }
     if (P.fp64) {
-      if (P.P.order == 3) MSM_FWD(double, 3);
-      else MSM_FWD(double, 5);
+      if (P.P.order == 3) MSM_FWD(double, 3) else MSM_FWD(double, 5)
     } else {
-      if (P.P.order == 3) MSM_FWD(float, 3);
-      else MSM_FWD(float, 5);
+      if (P.P.order == 3) MSM_FWD(float, 3) else MSM_FWD(float, 5)
     }
 #undef MSM_FWD
   }
-  k_energy_final<<<1, 1024, 0, st>>>(P.d.partial, n > 0 ? (int)nb : 0, energy);
+  k_energy_final<<<1, 1024, 0, st>>>(P.d.partial, n > 0 ? nb : 0, energy);
   P.launches += 1 + (n > 0 ? 1 : 0);
   return cudaGetLastError();
 }
@@ -781,19 +1026,25 @@ cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, double*
   if (n <= 0) return cudaSuccess;
   GridDims G = dims_of(P, 0);
   AssembleArgs A = assemble_args(P);
-  unsigned nb = blocks_for(n, 256);
+  AnterpArgs AA = patch_args(P);
+  dim3 grid(blocks_for(P.nc[0], AA.B), blocks_for(P.nc[1], AA.B), blocks_for(P.nc[2], AA.B));
+  size_t sm = (P.fp64 ? 8 : 4) * (size_t)AA.pd * AA.pd * AA.pd;
   P.launches += 1;
-#define MSM_BWD(T, O)                                                                                 \
-  k_interp_bwd<T, O><<<nb, 256, 0, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.idx[0], (int)n,     \
-                                         (const T*)P.d.au[0], G, A, (const T*)P.d.phis,               \
-                                         (const R4<T>*)P.d.fs, (const R4<T>*)P.d.glong, gE, grad_pos, \
-                                         grad_q)
+#define MSM_BWD(T, O)                                                                                             \
+  {                                                                                                               \
+    static bool attr = false;                                                                                     \
+    if (!attr) {                                                                                                  \
+      cudaFuncSetAttribute(k_interp_bwd<T, O>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);          \
+      attr = true;                                                                                                \
+    }                                                                                                             \
+    k_interp_bwd<T, O><<<grid, 256, sm, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.idx[0], P.d.cell_start, AA,  \
+                                              (const T*)P.d.au[0], G, A, (const T*)P.d.phis,                     \
+                                              (const R4<T>*)P.d.fs, (const R4<T>*)P.d.glong, gE, grad_pos, grad_q); \
+  }
   if (P.fp64) {
-    if (P.P.order == 3) MSM_BWD(double, 3);
-    else MSM_BWD(double, 5);
+    if (P.P.order == 3) MSM_BWD(double, 3) else MSM_BWD(double, 5)
   } else {
-    if (P.P.order == 3) MSM_BWD(float, 3);
-    else MSM_BWD(float, 5);
+    if (P.P.order == 3) MSM_BWD(float, 3) else MSM_BWD(float, 5)
   }
 #undef MSM_BWD
   return cudaGetLastError();

@@ -13,6 +13,8 @@
 // operations; rejected pairs are masked, not branched.  Mixed precision sums
 // each batch in FP32 and folds the batch sums into the running totals with an
 // error-free TwoSum (compensated accumulation).
+#include <cmath>
+
 #include "msm_internal.h"
 
 namespace msm {
@@ -196,6 +198,256 @@ __global__ void __launch_bounds__(32 * kWarps) k_short_range(
   }
 }
 
+// ---- mixed precision: packed FP32x2 arithmetic (two sources per instruction) ----
+// The queue is stored as four FP32 arrays (x, y, z, q), so sources j and j+1
+// load as one float2 each and feed FFMA2/FMUL2/FADD2 directly.  With
+// d = r_j - r_i, f' = q_j (1/r^3 + 2 gamma_s(s)/a^3) and
+// F_i = -q_i sum_j f' d, which needs no negations in the loop.  The home cell
+// (the only one that holds the target itself) goes through the scalar batch
+// with the self test; every other cell skips that test.  Far-away padding
+// sits at 1e6 so that the unmasked polynomial stays finite.
+template <int M>
+struct SmoothF2;
+template <>
+struct SmoothF2<1> {
+  __device__ static float2 g(float2 s) { return __ffma2_rn(s, make_float2(-0.5f, -0.5f), make_float2(1.5f, 1.5f)); }
+  __device__ static float2 gs(float2) { return make_float2(-0.5f, -0.5f); }
+};
+template <>
+struct SmoothF2<2> {
+  __device__ static float2 g(float2 s) {
+    float2 t = __ffma2_rn(s, make_float2(0.375f, 0.375f), make_float2(-1.25f, -1.25f));
+    return __ffma2_rn(t, s, make_float2(1.875f, 1.875f));
+  }
+  __device__ static float2 gs(float2 s) {
+    return __ffma2_rn(s, make_float2(0.75f, 0.75f), make_float2(-1.25f, -1.25f));
+  }
+};
+template <>
+struct SmoothF2<3> {
+  __device__ static float2 g(float2 s) {
+    float2 t = __ffma2_rn(s, make_float2(-0.3125f, -0.3125f), make_float2(1.3125f, 1.3125f));
+    t = __ffma2_rn(t, s, make_float2(-2.1875f, -2.1875f));
+    return __ffma2_rn(t, s, make_float2(2.1875f, 2.1875f));
+  }
+  __device__ static float2 gs(float2 s) {
+    float2 t = __ffma2_rn(s, make_float2(-0.9375f, -0.9375f), make_float2(2.625f, 2.625f));
+    return __ffma2_rn(t, s, make_float2(-2.1875f, -2.1875f));
+  }
+};
+
+struct QueueF {
+  float x[2 * kBatch], y[2 * kBatch], z[2 * kBatch], q[2 * kBatch];
+};
+
+// gamma(r/a)/a and (2/a^3) dgamma/ds written straight as polynomials in r^2
+// (host-scaled coefficients, duplicated into float2 pairs):
+//   pot = 1/r - sum_k G[k] r2^k,   f' = 1/r^3 + sum_k D[k] r2^k.
+struct PairCoef {
+  float2 G[4];
+  float2 D[3];
+};
+
+template <int M>
+__device__ __forceinline__ float2 poly_g(const PairCoef& C, float2 r2) {
+  float2 t = C.G[M];
+#pragma unroll
+  for (int k = M - 1; k >= 0; --k) t = __ffma2_rn(t, r2, C.G[k]);
+  return t;
+}
+template <int M>
+__device__ __forceinline__ float2 poly_d(const PairCoef& C, float2 r2) {
+  float2 t = C.D[M - 1];
+#pragma unroll
+  for (int k = M - 2; k >= 0; --k) t = __ffma2_rn(t, r2, C.D[k]);
+  return t;
+}
+
+template <int M>
+__device__ __forceinline__ void pair_batch_f2(const QueueF& Q, float2 nax, float2 nay, float2 naz, float a2,
+                                              const PairCoef& C, float& phi, float& px, float& py, float& pz,
+                                              float& cphi, float& cpx, float& cpy, float& cpz) {
+  float2 sphi = make_float2(0.f, 0.f), sx = sphi, sy = sphi, sz = sphi;
+#pragma unroll 4
+  for (int jj = 0; jj < kBatch; jj += 2) {
+    const float2 bx = *reinterpret_cast<const float2*>(&Q.x[jj]);
+    const float2 by = *reinterpret_cast<const float2*>(&Q.y[jj]);
+    const float2 bz = *reinterpret_cast<const float2*>(&Q.z[jj]);
+    const float2 bq = *reinterpret_cast<const float2*>(&Q.q[jj]);
+    const float2 dx = __fadd2_rn(bx, nax), dy = __fadd2_rn(by, nay), dz = __fadd2_rn(bz, naz);
+    float2 r2 = __fmul2_rn(dx, dx);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dz, dz, r2);
+    const float2 qj = make_float2(r2.x < a2 ? bq.x : 0.f, r2.y < a2 ? bq.y : 0.f);
+    const float2 rinv = make_float2(fast_rsqrt(r2.x), fast_rsqrt(r2.y));
+    const float2 pot = __fadd2_rn(rinv, poly_g<M>(C, r2));   // G holds -gamma coefficients
+    sphi = __ffma2_rn(qj, pot, sphi);
+    const float2 rinv3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
+    const float2 fp = __fmul2_rn(__fadd2_rn(rinv3, poly_d<M>(C, r2)), qj);
+    sx = __ffma2_rn(fp, dx, sx);
+    sy = __ffma2_rn(fp, dy, sy);
+    sz = __ffma2_rn(fp, dz, sz);
+  }
+  two_sum_add(phi, cphi, sphi.x + sphi.y);
+  two_sum_add(px, cpx, sx.x + sx.y);
+  two_sum_add(py, cpy, sy.x + sy.y);
+  two_sum_add(pz, cpz, sz.x + sz.y);
+}
+
+// Rows of neighbour cells: for each (dy, dz) the cells cx+xlo..cx+xhi of one x
+// row are contiguous in the sorted atom array (cells are numbered x fastest),
+// so a whole row is staged as one or two contiguous atom ranges (two when the
+// row wraps around a periodic box) instead of cell by cell.  The x offset of
+// a source atom's cell follows from comparing its index with the cell starts
+// of the row.
+template <int M>
+__global__ void __launch_bounds__(32 * kWarps, 7) k_short_range_f2(
+    const R4<float>* __restrict__ atoms, const int* __restrict__ cell_start,
+    const int4* __restrict__ rows, int nrows, PairArgs A, PairCoef C, float cwx, float cwy, float cwz, int ncell,
+    float* __restrict__ phis, R4<float>* __restrict__ fs) {
+  __shared__ QueueF queue[kWarps];
+  __shared__ R4<float> home[kWarps][kBatch];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  QueueF& Q = queue[warp];
+  const int cell = blockIdx.x * kWarps + warp;
+  if (cell >= ncell) return;  // warp-uniform
+  const int ncx = A.nc[0], ncy = A.nc[1], ncz = A.nc[2];
+  const int cx = cell % ncx, cy = (cell / ncx) % ncy, cz = cell / (ncx * ncy);
+  const float a2 = (float)(A.a * A.a), inv_a = (float)(1.0 / A.a), inv_a2s = (float)(1.0 / (A.a * A.a));
+  const float two_inv_a3 = (float)(2.0 / (A.a * A.a * A.a));
+  const float FAR = 1e6f;
+  const int i0 = cell_start[cell], i1 = cell_start[cell + 1];
+  for (int ib = i0; ib < i1; ib += 32) {
+    const int i = ib + lane;
+    const bool iv = i < i1;
+    const R4<float> ai = iv ? atoms[i] : R4<float>{0.f, 0.f, 0.f, 0.f};
+    float lx = iv ? ai.x : FAR, ly = iv ? ai.y : FAR, lz = iv ? ai.z : FAR;
+    float hx = iv ? ai.x : -FAR, hy = iv ? ai.y : -FAR, hz = iv ? ai.z : -FAR;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lx = fminf(lx, __shfl_xor_sync(kFull, lx, o));
+      ly = fminf(ly, __shfl_xor_sync(kFull, ly, o));
+      lz = fminf(lz, __shfl_xor_sync(kFull, lz, o));
+      hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, o));
+      hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, o));
+      hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, o));
+    }
+    const float2 nax = make_float2(-ai.x, -ai.x), nay = make_float2(-ai.y, -ai.y), naz = make_float2(-ai.z, -ai.z);
+    float phi = 0.f, px = 0.f, py = 0.f, pz = 0.f, cphi = 0.f, cpx = 0.f, cpy = 0.f, cpz = 0.f;
+    // home cell: scalar batches with the self test
+    for (int jb = i0; jb < i1; jb += 32) {
+      const int j = jb + lane;
+      home[warp][lane] = (j < i1) ? atoms[j] : R4<float>{FAR, FAR, FAR, 0.f};
+      __syncwarp();
+      float hphi = 0.f, hx_ = 0.f, hy_ = 0.f, hz_ = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+      pair_batch<float, M, true>(home[warp], ai, a2, inv_a, inv_a2s, two_inv_a3, hphi, hx_, hy_, hz_, c0, c1, c2,
+                                 c3);
+      two_sum_add(phi, cphi, hphi + c0);
+      two_sum_add(px, cpx, hx_ + c1);
+      two_sum_add(py, cpy, hy_ + c2);
+      two_sum_add(pz, cpz, hz_ + c3);
+      __syncwarp();
+    }
+    int qn = 0;  // queued sources (warp-uniform)
+    for (int r = 0; r < nrows; ++r) {
+      const int4 row = rows[r];  // (dy, dz, xlo, xhi): x offsets xlo..xhi of this row
+      int ny = cy + row.x, nz = cz + row.y;
+      if (A.periodic) {
+        ny += (ny < 0) ? ncy : ((ny >= ncy) ? -ncy : 0);
+        nz += (nz < 0) ? ncz : ((nz >= ncz) ? -ncz : 0);
+      } else if (ny < 0 || nz < 0 || ny >= ncy || nz >= ncz) {
+        continue;
+      }
+      const int rbase = (nz * ncy + ny) * ncx;
+      const float sy = row.x * cwy, sz = row.y * cwz;
+      // one or two contiguous segments [ox0, ox1] of x offsets
+      for (int seg = 0; seg < 2; ++seg) {
+        int ox0, ox1;
+        if (A.periodic) {
+          int xa = cx + row.z, xb = cx + row.w;  // may leave [0, ncx) by at most R
+          if (xa < 0) {
+            if (seg == 0) { ox0 = row.z; ox1 = -cx - 1; } else { ox0 = -cx; ox1 = row.w; }
+          } else if (xb >= ncx) {
+            if (seg == 0) { ox0 = row.z; ox1 = ncx - 1 - cx; } else { ox0 = ncx - cx; ox1 = row.w; }
+          } else {
+            if (seg == 1) break;
+            ox0 = row.z; ox1 = row.w;
+          }
+          if (ox0 > ox1) continue;  // this side of the wrap is empty
+        } else {
+          if (seg == 1) break;
+          ox0 = max(row.z, -cx);
+          ox1 = min(row.w, ncx - 1 - cx);
+          if (ox0 > ox1) break;
+        }
+        int x0 = cx + ox0, x1 = cx + ox1;
+        if (A.periodic) {
+          x0 += (x0 < 0) ? ncx : ((x0 >= ncx) ? -ncx : 0);
+          x1 += (x1 < 0) ? ncx : ((x1 >= ncx) ? -ncx : 0);
+        }
+        const int j0 = cell_start[rbase + x0], j1 = cell_start[rbase + x1 + 1];
+        // cell starts of the segment's interior cells, to find each source's x offset
+        int bnd[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) bnd[t] = (x0 + 1 + t <= x1) ? cell_start[rbase + x0 + 1 + t] : 0x7fffffff;
+        for (int jb = j0; jb < j1; jb += 32) {
+          const int j = jb + lane;
+          R4<float> aj = {FAR, FAR, FAR, 0.f};
+          if (j < j1) {
+            aj = atoms[j];
+            int ox = ox0 + (j >= bnd[0]) + (j >= bnd[1]) + (j >= bnd[2]) + (j >= bnd[3]);
+            aj.x += ox * cwx;
+            aj.y += sy;
+            aj.z += sz;
+          }
+          const float ex = fmaxf(fmaxf(lx - aj.x, aj.x - hx), 0.f);
+          const float ey = fmaxf(fmaxf(ly - aj.y, aj.y - hy), 0.f);
+          const float ez = fmaxf(fmaxf(lz - aj.z, aj.z - hz), 0.f);
+          const bool keep = (j < j1) && (ex * ex + ey * ey + ez * ez < a2);
+          const unsigned bal = __ballot_sync(kFull, keep);
+          if (keep) {
+            const int p = qn + __popc(bal & ((1u << lane) - 1u));
+            Q.x[p] = aj.x;
+            Q.y[p] = aj.y;
+            Q.z[p] = aj.z;
+            Q.q[p] = aj.w;
+          }
+          qn += __popc(bal);
+          __syncwarp();
+          if (qn >= kBatch) {
+            pair_batch_f2<M>(Q, nax, nay, naz, a2, C, phi, px, py, pz, cphi, cpx, cpy, cpz);
+            __syncwarp();
+            if (lane < qn - kBatch) {
+              Q.x[lane] = Q.x[kBatch + lane];
+              Q.y[lane] = Q.y[kBatch + lane];
+              Q.z[lane] = Q.z[kBatch + lane];
+              Q.q[lane] = Q.q[kBatch + lane];
+            }
+            qn -= kBatch;
+            __syncwarp();
+          }
+        }
+      }
+    }
+    if (qn > 0) {  // last partial batch, padded with far-away zero charges
+      if (lane >= qn) {
+        Q.x[lane] = FAR;
+        Q.y[lane] = FAR;
+        Q.z[lane] = FAR;
+        Q.q[lane] = 0.f;
+      }
+      __syncwarp();
+      pair_batch_f2<M>(Q, nax, nay, naz, a2, C, phi, px, py, pz, cphi, cpx, cpy, cpz);
+      __syncwarp();
+    }
+    if (iv) {
+      phis[i] = phi + cphi;
+      const float qi = ai.w;
+      fs[i] = R4<float>{-qi * (px + cpx), -qi * (py + cpy), -qi * (pz + cpz), 0.f};
+    }
+  }
+}
+
 template <typename T, bool COMP>
 void launch_t(Plan& P, cudaStream_t st) {
   PairArgs A;
@@ -226,10 +478,48 @@ void launch_t(Plan& P, cudaStream_t st) {
 
 }  // namespace
 
+void launch_f2(Plan& P, cudaStream_t st) {
+  PairArgs A;
+  for (int d = 0; d < 3; ++d) A.nc[d] = P.nc[d];
+  A.periodic = P.P.periodic;
+  A.noff = P.noff;
+  A.a = P.P.cutoff;
+  int blocks = (P.ncell + kWarps - 1) / kWarps;
+  auto* at = (const R4<float>*)P.d.atoms;
+  auto* sh = (const R4<float>*)P.d.cell_shift;
+  auto* ph = (float*)P.d.phis;
+  auto* fs = (R4<float>*)P.d.fs;
+  // gamma coefficients c_k (Taylor series of s^(-1/2) about s = 1, truncated at m)
+  static const double c[4][4] = {{0, 0, 0, 0}, {1.5, -0.5, 0, 0}, {1.875, -1.25, 0.375, 0},
+                                 {2.1875, -2.1875, 1.3125, -0.3125}};
+  const int m = P.P.splitting;
+  const double a = P.P.cutoff;
+  PairCoef C;
+  for (int k = 0; k < 4; ++k) {
+    float g = (k <= m) ? (float)(-c[m][k] / std::pow(a, 2 * k + 1)) : 0.f;
+    C.G[k] = make_float2(g, g);
+  }
+  for (int k = 0; k < 3; ++k) {
+    float d = (k + 1 <= m) ? (float)(2.0 * (k + 1) * c[m][k + 1] / std::pow(a, 2 * k + 3)) : 0.f;
+    C.D[k] = make_float2(d, d);
+  }
+  const float cwx = (float)P.cw[0], cwy = (float)P.cw[1], cwz = (float)P.cw[2];
+  (void)sh;
+  if (m == 1)
+    k_short_range_f2<1><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_rows, P.nrows, A, C, cwx, cwy,
+                                                        cwz, P.ncell, ph, fs);
+  else if (m == 2)
+    k_short_range_f2<2><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_rows, P.nrows, A, C, cwx, cwy,
+                                                        cwz, P.ncell, ph, fs);
+  else
+    k_short_range_f2<3><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_rows, P.nrows, A, C, cwx, cwy,
+                                                        cwz, P.ncell, ph, fs);
+}
+
 cudaError_t launch_short_range(Plan& P, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (P.fp64) launch_t<double, false>(P, st);
-  else launch_t<float, true>(P, st);
+  else launch_f2(P, st);
   P.launches += 1;
   return cudaGetLastError();
 }

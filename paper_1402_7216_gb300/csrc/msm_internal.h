@@ -33,6 +33,12 @@ struct Segment {
   T g[kSeg];
 };
 
+// The same run with each coefficient duplicated, for packed FP32x2 FMAs.
+struct Segment2 {
+  int dy, dx0;
+  float2 g[kSeg];
+};
+
 // Per-precision device tables and buffers.
 struct DeviceBuffers {
   // binning / sorting
@@ -62,10 +68,12 @@ struct DeviceBuffers {
   double* topu = nullptr;
   // level stencil
   void* seg = nullptr;         // Segment<T>[nseg]
+  void* seg2 = nullptr;        // Segment2[nseg] (mixed precision only)
   int* seg_start = nullptr;    // [2*Ez+2]: segments of plane dz live in [start[dz+Ez], start[dz+Ez+1])
   // neighbour cell offsets (x, y, z) of the pair kernel
   int4* cell_off = nullptr;    // [noff]
   void* cell_shift = nullptr;  // R4<T>[noff]: offset times cell width, in the plan's precision
+  int4* cell_rows = nullptr;   // [nrows]: (dy, dz, xlo, xhi) rows of neighbour cell offsets
   // reductions and status
   double* partial = nullptr;   // per-block energy partials
   double* scalars = nullptr;   // [8] scratch scalars (0: backward scale)
@@ -92,6 +100,7 @@ struct Plan {
   int ncell = 1;
   int key_passes = 1;
   int noff = 0;
+  int nrows = 0;
   // anterpolation patches: blocks of ablk^3 cells, patches of apd^3 points
   int ablk = 1, apd = 1;
   // smoothing constants

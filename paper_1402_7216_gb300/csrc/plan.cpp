@@ -251,6 +251,25 @@ int build_plan(const msm_params* pp, Plan* P) {
         offs.push_back(make_int4(ox, oy, oz, 0));
       }
   P->noff = (int)offs.size();
+  // the same offsets grouped by (dy, dz) into contiguous x runs (cells are numbered x fastest)
+  std::vector<int4> rowv;
+  for (int oz = -2; oz <= 2; ++oz)
+    for (int oy = -2; oy <= 2; ++oy) {
+      int xlo = 99, xhi = -99;
+      for (auto& o : offs)
+        if (o.y == oy && o.z == oz) {
+          xlo = std::min(xlo, o.x);
+          xhi = std::max(xhi, o.x);
+        }
+      if (xlo > xhi) continue;
+      if (oy == 0 && oz == 0) {  // the home cell (offset 0) is evaluated separately, with the self test
+        if (xlo <= -1) rowv.push_back(make_int4(oy, oz, xlo, -1));
+        if (xhi >= 1) rowv.push_back(make_int4(oy, oz, 1, xhi));
+      } else {
+        rowv.push_back(make_int4(oy, oz, xlo, xhi));
+      }
+    }
+  P->nrows = (int)rowv.size();
   // anterpolation patch: B^3 cells reach at most floor(B cw/h) + 2S + 5
   // points per dimension (with margin for rounding); keep it in shared memory
   {
@@ -343,7 +362,11 @@ int build_plan(const msm_params* pp, Plan* P) {
   P->cap = cap;
   const int kChunk = 4096;  // atoms per radix-sort block
   P->nblk_hist = (int)((cap + kChunk - 1) / kChunk);
-  P->nblk_partial = (int)((cap + 255) / 256) + 1;  // one energy partial per interpolation block
+  {  // one energy partial per interpolation block (blocks of ablk^3 cells)
+    int64_t nb = 1;
+    for (int d = 0; d < 3; ++d) nb *= (P->nc[d] + P->ablk - 1) / P->ablk;
+    P->nblk_partial = (int)std::max<int64_t>(nb, 1);
+  }
   cudaError_t e = cudaSuccess;
   auto M = [&](void** ptr, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(ptr, bytes ? bytes : 16);
@@ -385,6 +408,7 @@ int build_plan(const msm_params* pp, Plan* P) {
   if (cudaMemset(D.status, 0, sizeof(int)) != cudaSuccess) return MSM_ERR_CUDA;
   if (upload((void**)&D.topK, K) != cudaSuccess) return MSM_ERR_OOM;
   if (upload((void**)&D.cell_off, offs) != cudaSuccess) return MSM_ERR_OOM;
+  if (upload((void**)&D.cell_rows, rowv) != cudaSuccess) return MSM_ERR_OOM;
   if (P->fp64) {
     std::vector<R4<double>> sh;
     for (auto& o : offs) sh.push_back({o.x * P->cw[0], o.y * P->cw[1], o.z * P->cw[2], 0.0});
@@ -406,6 +430,13 @@ int build_plan(const msm_params* pp, Plan* P) {
     build_segments<float>(*P, G, P->E, segs, start);
     P->nseg = (int)segs.size();
     if (upload(&D.seg, segs) != cudaSuccess) return MSM_ERR_OOM;
+    std::vector<Segment2> segs2(segs.size());
+    for (size_t i = 0; i < segs.size(); ++i) {
+      segs2[i].dy = segs[i].dy;
+      segs2[i].dx0 = segs[i].dx0;
+      for (int j = 0; j < kSeg; ++j) segs2[i].g[j] = make_float2(segs[i].g[j], segs[i].g[j]);
+    }
+    if (upload(&D.seg2, segs2) != cudaSuccess) return MSM_ERR_OOM;
   }
   if (upload((void**)&D.seg_start, start) != cudaSuccess) return MSM_ERR_OOM;
   return MSM_OK;
@@ -414,7 +445,7 @@ int build_plan(const msm_params* pp, Plan* P) {
 void free_plan(Plan* P) {
   DeviceBuffers& D = P->d;
   void* ptrs[] = {D.keys[0], D.keys[1], D.idx[0], D.idx[1], D.hist, D.cell_start, D.atoms,
-                  D.gfrac, D.gbase, D.phis, D.fs, D.glong, D.topK, D.topq, D.topu, D.seg, D.cell_shift,
+                  D.gfrac, D.gbase, D.phis, D.fs, D.glong, D.topK, D.topq, D.topu, D.seg, D.seg2, D.cell_shift, D.cell_rows,
                   D.seg_start, D.cell_off, D.partial, D.scalars, D.status, D.hpos, D.hq,
                   D.hphi, D.hforce, D.henergy};
   for (void* p : ptrs)
