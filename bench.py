@@ -115,6 +115,22 @@ def work_model(plan, n, box, cutoff, order):
     }
 
 
+def recorded_traffic():
+    """DRAM bytes per launch from the committed ncu capture (profiles/roofline_traffic.json),
+    for each stage whose kernel source is unchanged since the capture; None otherwise."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(path):
+        return {}
+    rec = json.load(open(path))
+    out = {}
+    for stage, k in rec.get("kernels", {}).items():
+        src = os.path.join(ROOT, k["source"])
+        if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest() == k["sha256"]:
+            out[stage] = k["dram_bytes_per_launch"]
+    return out
+
+
 def plan_taps(plan):
     h = plan.h_eff
     a = plan.params.cutoff
@@ -308,18 +324,22 @@ def main():
             e["frac_fp32_peak"] = e["gflop_s"] / (fp32_peak * 1e3)
             e["frac_hbm_peak"] = e["hbm_gb_s_algorithmic"] / hbm
         kernels[k] = e
+    traffic = recorded_traffic()
+    for k, e in kernels.items():
+        if k in traffic:
+            e["dram_bytes_ncu"] = traffic[k]
     dom = max(per_eval, key=per_eval.get)
     if dom in ("short_range", "lattice_cutoff", "anterpolation", "interpolation"):
         ach = model[dom]["flop"] / (per_eval[dom] * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": None,
+                "frac": ach / fp32_peak, "traffic": traffic.get(dom),
                 "peak_source": "FP32 FMA peak: %d SMs x %d lanes x 2 flop x %.0f MHz (%s sm_max_mhz)"
                                % (N_SM, FP32_LANES, sm_max, peak_kind),
                 "work_per_launch": model[dom].get("units")}
     else:
         ach = model.get(dom, {"bytes": 0})["bytes"] / (per_eval[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None}
+                "frac": ach / hbm, "traffic": traffic.get(dom)}
     out = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": tot / args.steps, "higher_is_better": True,
