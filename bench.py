@@ -192,6 +192,67 @@ def cpu_baseline(w, budget_s=30.0):
             "sample": "1 whole evaluation of the %d-atom system (%.1f s)" % (w.n_atoms, t)}
 
 
+def bench_batch(dev, args, n_rep=64):
+    import numpy as np
+    import torch
+    from paper_1402_7216_gb300 import MSM, MSMBatch
+    from synth import replica_boxes
+    reps = replica_boxes(n_rep)
+    counts = [len(q) for (_, _, q) in reps]
+    n = sum(counts)
+    plans = [MSM(box=L, periodic=True, cutoff=10.0, spacing=2.0, order=3, splitting=2, precision="mixed",
+                 max_atoms=len(q)) for (L, _, q) in reps]
+    pos = torch.tensor(np.vstack([p for (_, p, _) in reps]), device=dev)
+    q = torch.tensor(np.concatenate([qq for (_, _, qq) in reps]), device=dev)
+    E = torch.zeros(n_rep, dtype=torch.float64, device=dev)
+    F = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    phi = torch.zeros(n, dtype=torch.float64, device=dev)
+    gE = torch.ones(n_rep, dtype=torch.float64, device=dev)
+    gp = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    gq = torch.zeros(n, dtype=torch.float64, device=dev)
+    batch = MSMBatch(plans)
+    graph = batch.graph(pos, q, counts, E, phi, F, gE, gp, gq)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        graph.launch()
+    torch.cuda.synchronize()
+    steps = max(5, args.steps // 5)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush.fill_(1.0)
+        a.record(stream)
+        graph.launch()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    # the same work as separate calls on one stream (no graph, no fork)
+    seq = []
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        a.record(stream)
+        o = 0
+        for r, p in enumerate(plans):
+            c = counts[r]
+            p.eval(pos[o:o + c], q[o:o + c], want_phi=False, want_force=False)
+            p.backward(gE[r], want_pos=True, want_q=True)
+            o += c
+        b.record(stream)
+        torch.cuda.synchronize()
+        seq.append(a.elapsed_time(b))
+    for p in plans:
+        p.check_status()
+    graph.close()
+    t = sum(ms) / len(ms)
+    return {"metric": "replica energy+force+adjoint evaluations per second (one graph launch = all replicas)",
+            "value": n_rep / (t * 1e-3), "unit": "replica-evals/s", "replicas": n_rep, "atoms_total": n,
+            "atoms_min": min(counts), "atoms_max": max(counts), "ms_per_batch": t, "steps": steps,
+            "ms_per_batch_sequential_calls": min(seq),
+            "config": "periodic water boxes at 0.1 atoms/A^3, a=10, h=2.0, cubic, C2, mixed precision, "
+                      "forward + adjoint, CUDA graph of the stream-forked batch, L2 flushed between steps"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,6 +262,7 @@ def main():
     ap.add_argument("--workload", default="water1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -307,6 +369,13 @@ def main():
             "phi_rel_rms": float(torch.sqrt(((phi_mix - phi64) ** 2).sum() / (phi64 ** 2).sum()))}
         plan64.close()
 
+    # batched replicas: 64 periodic water boxes, N log-uniform in [5k, 50k] at
+    # 0.1 atoms/A^3, a = 10, h = 2.0, cubic, mixed precision; forward + adjoint
+    # of all replicas replayed from one captured CUDA graph
+    batched = None
+    if not args.no_batch:
+        batched = bench_batch(dev, args)
+
     if rank != 0:
         return
     peaks, peak_kind = load_peaks()
@@ -356,6 +425,7 @@ def main():
         "roofline": roof,
         "kernels_ms_per_eval": kernels,
         "fp64_gpu_path": fp64,
+        "batched_replicas": batched,
         "clocks": clk,
         "energy": E_mix,
     }

@@ -116,8 +116,42 @@ int msm_eval_backward(msm_handle h, const double* grad_energy, double* grad_pos,
 int msm_eval_host(msm_handle h, int64_t n, const double* pos, const double* q, double* energy,
                   double* phi, double* force, void* cuda_stream);
 
-/* Synchronises the plan's last stream and returns the first device-posted
- * error since the previous msm_status call (or MSM_OK), then clears it. */
+/* ---- batches of independent systems (replicas) ----
+ * Replica r uses plans[r] (its own box, geometry and workspace; a plan may
+ * appear only once in a batch) and the atoms offsets[r] .. offsets[r+1]-1 of
+ * the concatenated arrays pos [N][3] and q [N] (device), N = offsets[nrep]
+ * (host array of nrep+1 int64, offsets[0] = 0).  energies [nrep] (device)
+ * receives one energy per replica; phi [N] and force [N][3] (device, either
+ * NULL) the per-atom results in the input order.  The replicas are forked
+ * over a pool of library-owned streams and joined back onto cuda_stream with
+ * events, so independent small systems run concurrently; the call is
+ * asynchronous and can be captured into a CUDA graph.
+ * Errors: INVALID_ARG, TOO_MANY_ATOMS, CUDA. */
+int msm_eval_batch(const msm_handle* plans, int nrep, const int64_t* offsets, const double* pos, const double* q,
+                   double* energies, double* phi, double* force, void* cuda_stream);
+
+/* Adjoint of the last msm_eval_batch (or of the last msm_eval of every plan):
+ * grad_energies [nrep] (device) -> grad_pos [N][3], grad_q [N] (device, either
+ * NULL), per replica as msm_eval_backward.
+ * Errors: INVALID_ARG, TOO_MANY_ATOMS, NO_FORWARD, CUDA. */
+int msm_eval_backward_batch(const msm_handle* plans, int nrep, const int64_t* offsets, const double* grad_energies,
+                            double* grad_pos, double* grad_q, void* cuda_stream);
+
+/* A batched forward (and, when grad_energies is not NULL, its adjoint)
+ * captured once into an instantiated CUDA graph on the given buffers; every
+ * msm_graph_launch replays all kernels of all replicas with one launch.  The
+ * buffers and plans must outlive the graph; inputs may change between
+ * replays (same sizes).  Creating the graph runs nothing.
+ * Errors: INVALID_ARG, TOO_MANY_ATOMS, OOM, CUDA. */
+typedef struct msm_graph* msm_graph_handle;
+int msm_batch_graph_create(const msm_handle* plans, int nrep, const int64_t* offsets, const double* pos,
+                           const double* q, double* energies, double* phi, double* force,
+                           const double* grad_energies, double* grad_pos, double* grad_q, msm_graph_handle* out);
+int msm_graph_launch(msm_graph_handle g, void* cuda_stream);
+void msm_graph_destroy(msm_graph_handle g);
+
+/* Synchronises the device and returns the first device-posted error of this
+ * plan since the previous msm_status call (or MSM_OK), then clears it. */
 int msm_status(msm_handle h);
 
 /* Copies one grid of the last evaluation to HOST memory, as doubles in the

@@ -17,7 +17,7 @@ import torch
 from . import _capi
 from ._capi import MSMError, MSM_FP64, MSM_MIXED  # noqa: F401
 
-__all__ = ["MSM", "MSMEnergy", "MSMError", "MSM_FP64", "MSM_MIXED", "lib"]
+__all__ = ["MSM", "MSMBatch", "BatchGraph", "MSMEnergy", "MSMError", "MSM_FP64", "MSM_MIXED", "lib"]
 
 
 def lib():
@@ -166,6 +166,83 @@ class MSM:
                                   out.ctypes.data_as(C.POINTER(C.c_double)))
         _capi.check(rc, "msm_debug_grid")
         return out
+
+
+class MSMBatch:
+    """Independent systems (replicas) evaluated together: replica r uses
+    plans[r] and the atoms offsets[r]..offsets[r+1]-1 of concatenated pos/q."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        self._arr = (C.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+
+    def _offsets(self, counts):
+        off = [0]
+        for c in counts:
+            off.append(off[-1] + int(c))
+        return (C.c_int64 * len(off))(*off), off[-1]
+
+    def eval(self, pos, q, counts, want_phi=True, want_force=True, stream=None, out=None):
+        """Returns (energies [nrep], phi [N] or None, F [N,3] or None)."""
+        offs, n = self._offsets(counts)
+        dev = pos.device
+        if out is None:
+            E = torch.empty(len(self.plans), dtype=torch.float64, device=dev)
+            phi = torch.empty(n, dtype=torch.float64, device=dev) if want_phi else None
+            F = torch.empty((n, 3), dtype=torch.float64, device=dev) if want_force else None
+        else:
+            E, phi, F = out
+        rc = lib().msm_eval_batch(self._arr, len(self.plans), offs, _ptr(pos), _ptr(q), _ptr(E), _ptr(phi),
+                                  _ptr(F), _stream(stream))
+        _capi.check(rc, "msm_eval_batch")
+        for p, c in zip(self.plans, counts):
+            p._last_n = int(c)
+        return E, phi, F
+
+    def backward(self, grad_energies, counts, want_pos=True, want_q=True, stream=None):
+        offs, n = self._offsets(counts)
+        dev = grad_energies.device
+        gp = torch.empty((n, 3), dtype=torch.float64, device=dev) if want_pos else None
+        gq = torch.empty(n, dtype=torch.float64, device=dev) if want_q else None
+        g = grad_energies.to(torch.float64).contiguous()
+        rc = lib().msm_eval_backward_batch(self._arr, len(self.plans), offs, _ptr(g), _ptr(gp), _ptr(gq),
+                                           _stream(stream))
+        _capi.check(rc, "msm_eval_backward_batch")
+        return gp, gq
+
+    def graph(self, pos, q, counts, energies, phi=None, force=None, grad_energies=None, grad_pos=None,
+              grad_q=None):
+        """Captures the batched forward (+ adjoint when grad_energies is given)
+        on these buffers into a CUDA graph; returns a BatchGraph."""
+        offs, _ = self._offsets(counts)
+        h = C.c_void_p()
+        rc = lib().msm_batch_graph_create(self._arr, len(self.plans), offs, _ptr(pos), _ptr(q), _ptr(energies),
+                                          _ptr(phi), _ptr(force), _ptr(grad_energies), _ptr(grad_pos),
+                                          _ptr(grad_q), C.byref(h))
+        _capi.check(rc, "msm_batch_graph_create")
+        return BatchGraph(h, keep=(pos, q, energies, phi, force, grad_energies, grad_pos, grad_q, self))
+
+
+class BatchGraph:
+    """An instantiated CUDA graph of a batched evaluation."""
+
+    def __init__(self, h, keep):
+        self._h = h
+        self._keep = keep  # the captured buffers must outlive the graph
+
+    def launch(self, stream=None):
+        _capi.check(lib().msm_graph_launch(self._h, _stream(stream)), "msm_graph_launch")
+
+    def close(self):
+        if self._h:
+            lib().msm_graph_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class MSMEnergy(torch.autograd.Function):

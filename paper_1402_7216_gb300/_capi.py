@@ -36,7 +36,8 @@ _lib = None
 _D = C.POINTER(C.c_double)
 EXPORTS = ["msm_create", "msm_destroy", "msm_query", "msm_eval", "msm_eval_backward",
            "msm_eval_host", "msm_status", "msm_debug_grid", "msm_profile", "msm_profile_read",
-           "msm_stage_name", "msm_energy_noalloc", "msm_strerror"]
+           "msm_stage_name", "msm_energy_noalloc", "msm_eval_batch", "msm_eval_backward_batch",
+           "msm_batch_graph_create", "msm_graph_launch", "msm_graph_destroy", "msm_strerror"]
 NSTAGES = 8
 
 
@@ -72,6 +73,16 @@ def load(path=LIB_PATH):
     L.msm_profile_read.restype = C.c_int
     L.msm_stage_name.argtypes = [C.c_int]
     L.msm_stage_name.restype = C.c_char_p
+    L.msm_eval_batch.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
+    L.msm_eval_batch.restype = C.c_int
+    L.msm_eval_backward_batch.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
+    L.msm_eval_backward_batch.restype = C.c_int
+    L.msm_batch_graph_create.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(vp)]
+    L.msm_batch_graph_create.restype = C.c_int
+    L.msm_graph_launch.argtypes = [vp, vp]
+    L.msm_graph_launch.restype = C.c_int
+    L.msm_graph_destroy.argtypes = [vp]
+    L.msm_graph_destroy.restype = None
     L.msm_energy_noalloc.argtypes = [C.c_int64, vp, vp, vp, vp]
     L.msm_energy_noalloc.restype = C.c_int
     L.msm_strerror.argtypes = [C.c_int]

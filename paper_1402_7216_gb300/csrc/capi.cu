@@ -5,7 +5,9 @@
 // cutoff per level, top level, prolongation, interpolation and assembly.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "msm_internal.h"
 
@@ -79,13 +81,127 @@ int forward(Plan& P, int64_t n, const double* pos, const double* q, double* ener
   return MSM_OK;
 }
 
+int backward(Plan& P, const double* grad_energy, double* grad_pos, double* grad_q, cudaStream_t st) {
+  if (P.last_n < 0) return MSM_ERR_NO_FORWARD;
+  int64_t n = P.last_n;
+  // adjoint of u_long = A^T M A q with respect to its inputs: anterpolate the
+  // adjoint of u_long (1/2 dL/dE q_i), sweep the (symmetric) grid operator,
+  // and interpolate the result back to the atoms.
+  cudaError_t e = stage(P, MSM_STAGE_ANTERPOLATION, st,
+                        [&] { return launch_anterpolate(P, n, P.d.aq[0], grad_energy, 0.5, st); });
+  if (e == cudaSuccess) e = grid_sweep(P, P.d.aq, P.d.au, st);
+  if (e == cudaSuccess)
+    e = stage(P, MSM_STAGE_INTERPOLATION, st,
+              [&] { return launch_interp_backward(P, n, grad_energy, grad_pos, grad_q, st); });
+  if (e != cudaSuccess) return MSM_ERR_CUDA;
+  P.last_stream = st;
+  return MSM_OK;
+}
+
+// ---- batches: replicas forked over a pool of streams, joined on the caller's ----
+constexpr int kPoolStreams = 16;
+
+struct StreamPool {
+  int device = -1;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t s[kPoolStreams] = {};
+  cudaEvent_t done[kPoolStreams] = {};
+};
+
+std::mutex g_pool_mu;
+StreamPool g_pools[8];
+
+cudaError_t pool_for_device(StreamPool** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 8) return cudaErrorInvalidDevice;
+  StreamPool& P = g_pools[dev];
+  if (P.device != dev) {
+    e = cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming);
+    for (int k = 0; k < kPoolStreams && e == cudaSuccess; ++k) {
+      e = cudaStreamCreateWithFlags(&P.s[k], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.done[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return e;
+    P.device = dev;
+  }
+  *out = &P;
+  return cudaSuccess;
+}
+
+int check_batch(const msm_handle* plans, int nrep, const int64_t* offsets) {
+  if (!plans || nrep < 1 || !offsets || offsets[0] != 0) return MSM_ERR_INVALID_ARG;
+  for (int r = 0; r < nrep; ++r) {
+    if (!plans[r]) return MSM_ERR_INVALID_ARG;
+    int64_t n = offsets[r + 1] - offsets[r];
+    if (n < 0) return MSM_ERR_INVALID_ARG;
+    if (n > plans[r]->p.cap) return MSM_ERR_TOO_MANY_ATOMS;
+    for (int s = 0; s < r; ++s)
+      if (plans[s] == plans[r]) return MSM_ERR_INVALID_ARG;  // a plan's workspace serves one replica
+  }
+  return MSM_OK;
+}
+
+// Runs body(r, stream) for every replica on the pool, forked from and joined
+// back onto st (events only; capturable).
+template <typename F>
+int fork_join(int nrep, cudaStream_t st, F&& body) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  StreamPool* pool = nullptr;
+  if (pool_for_device(&pool) != cudaSuccess) return MSM_ERR_CUDA;
+  const int K = nrep < kPoolStreams ? nrep : kPoolStreams;
+  if (cudaEventRecord(pool->fork, st) != cudaSuccess) return MSM_ERR_CUDA;
+  for (int k = 0; k < K; ++k)
+    if (cudaStreamWaitEvent(pool->s[k], pool->fork, 0) != cudaSuccess) return MSM_ERR_CUDA;
+  int rc = MSM_OK;
+  for (int r = 0; r < nrep && rc == MSM_OK; ++r) rc = body(r, pool->s[r % K]);
+  for (int k = 0; k < K; ++k) {
+    if (cudaEventRecord(pool->done[k], pool->s[k]) != cudaSuccess) return MSM_ERR_CUDA;
+    if (cudaStreamWaitEvent(st, pool->done[k], 0) != cudaSuccess) return MSM_ERR_CUDA;
+  }
+  return rc;
+}
+
+int batch_forward(const msm_handle* plans, int nrep, const int64_t* off, const double* pos, const double* q,
+                  double* energies, double* phi, double* force, cudaStream_t st) {
+  return fork_join(nrep, st, [&](int r, cudaStream_t s) {
+    Plan& P = plans[r]->p;
+    int64_t o = off[r], n = off[r + 1] - off[r];
+    return forward(P, n, pos + 3 * o, q + o, energies + r, phi ? phi + o : nullptr, force ? force + 3 * o : nullptr,
+                   s);
+  });
+}
+
+int batch_backward(const msm_handle* plans, int nrep, const int64_t* off, const double* grad_energies,
+                   double* grad_pos, double* grad_q, cudaStream_t st) {
+  return fork_join(nrep, st, [&](int r, cudaStream_t s) {
+    Plan& P = plans[r]->p;
+    int64_t o = off[r];
+    if (P.last_n != off[r + 1] - off[r]) return (int)MSM_ERR_NO_FORWARD;
+    return backward(P, grad_energies + r, grad_pos ? grad_pos + 3 * o : nullptr, grad_q ? grad_q + o : nullptr, s);
+  });
+}
+
+std::once_flag g_config_once;
+cudaError_t g_config_err = cudaSuccess;
+
 }  // namespace
+
+struct msm_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
 
 extern "C" {
 
 int msm_create(const msm_params* params, msm_handle* out) {
   if (!params || !out) return MSM_ERR_INVALID_ARG;
   *out = nullptr;
+  int vrc = validate_params(params);
+  if (vrc != MSM_OK) return vrc;
+  std::call_once(g_config_once, [] { g_config_err = configure_kernels(); });
+  if (g_config_err != cudaSuccess) return MSM_ERR_CUDA;
   msm_plan* h = new (std::nothrow) msm_plan();
   if (!h) return MSM_ERR_OOM;
   int rc = build_plan(params, &h->p);
@@ -134,22 +250,70 @@ int msm_eval(msm_handle h, int64_t n, const double* pos, const double* q, double
 int msm_eval_backward(msm_handle h, const double* grad_energy, double* grad_pos, double* grad_q,
                       void* stream) {
   if (!h || !grad_energy) return MSM_ERR_INVALID_ARG;
-  Plan& P = h->p;
-  if (P.last_n < 0) return MSM_ERR_NO_FORWARD;
-  cudaStream_t st = (cudaStream_t)stream;
-  int64_t n = P.last_n;
-  // adjoint of u_long = A^T M A q with respect to its inputs: anterpolate the
-  // adjoint of u_long (1/2 dL/dE q_i), sweep the (symmetric) grid operator,
-  // and interpolate the result back to the atoms.
-  cudaError_t e = stage(P, MSM_STAGE_ANTERPOLATION, st,
-                        [&] { return launch_anterpolate(P, n, P.d.aq[0], grad_energy, 0.5, st); });
-  if (e == cudaSuccess) e = grid_sweep(P, P.d.aq, P.d.au, st);
-  if (e == cudaSuccess)
-    e = stage(P, MSM_STAGE_INTERPOLATION, st,
-              [&] { return launch_interp_backward(P, n, grad_energy, grad_pos, grad_q, st); });
-  if (e != cudaSuccess) return MSM_ERR_CUDA;
-  P.last_stream = st;
+  return backward(h->p, grad_energy, grad_pos, grad_q, (cudaStream_t)stream);
+}
+
+int msm_eval_batch(const msm_handle* plans, int nrep, const int64_t* offsets, const double* pos, const double* q,
+                   double* energies, double* phi, double* force, void* stream) {
+  int rc = check_batch(plans, nrep, offsets);
+  if (rc != MSM_OK) return rc;
+  if (!energies || (offsets[nrep] > 0 && (!pos || !q))) return MSM_ERR_INVALID_ARG;
+  return batch_forward(plans, nrep, offsets, pos, q, energies, phi, force, (cudaStream_t)stream);
+}
+
+int msm_eval_backward_batch(const msm_handle* plans, int nrep, const int64_t* offsets, const double* grad_energies,
+                            double* grad_pos, double* grad_q, void* stream) {
+  int rc = check_batch(plans, nrep, offsets);
+  if (rc != MSM_OK) return rc;
+  if (!grad_energies) return MSM_ERR_INVALID_ARG;
+  return batch_backward(plans, nrep, offsets, grad_energies, grad_pos, grad_q, (cudaStream_t)stream);
+}
+
+int msm_batch_graph_create(const msm_handle* plans, int nrep, const int64_t* offsets, const double* pos,
+                           const double* q, double* energies, double* phi, double* force,
+                           const double* grad_energies, double* grad_pos, double* grad_q, msm_graph_handle* out) {
+  if (!out) return MSM_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = check_batch(plans, nrep, offsets);
+  if (rc != MSM_OK) return rc;
+  if (!energies || (offsets[nrep] > 0 && (!pos || !q))) return MSM_ERR_INVALID_ARG;
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return MSM_ERR_CUDA;
+  msm_graph* g = new (std::nothrow) msm_graph();
+  if (!g) {
+    cudaStreamDestroy(cs);
+    return MSM_ERR_OOM;
+  }
+  rc = MSM_OK;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = MSM_ERR_CUDA;
+  if (rc == MSM_OK) {
+    rc = batch_forward(plans, nrep, offsets, pos, q, energies, phi, force, cs);
+    if (rc == MSM_OK && grad_energies) rc = batch_backward(plans, nrep, offsets, grad_energies, grad_pos, grad_q, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);  // always end the capture
+    if (rc == MSM_OK && e != cudaSuccess) rc = MSM_ERR_CUDA;
+    g->graph = graph;
+    if (rc == MSM_OK && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) rc = MSM_ERR_CUDA;
+  }
+  cudaStreamDestroy(cs);
+  if (rc != MSM_OK) {
+    msm_graph_destroy(g);
+    return rc;
+  }
+  *out = g;
   return MSM_OK;
+}
+
+int msm_graph_launch(msm_graph_handle g, void* stream) {
+  if (!g || !g->exec) return MSM_ERR_INVALID_ARG;
+  return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? MSM_OK : MSM_ERR_CUDA;
+}
+
+void msm_graph_destroy(msm_graph_handle g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
 }
 
 int msm_eval_host(msm_handle h, int64_t n, const double* pos, const double* q, double* energy, double* phi,
@@ -188,7 +352,7 @@ int msm_eval_host(msm_handle h, int64_t n, const double* pos, const double* q, d
 int msm_status(msm_handle h) {
   if (!h) return MSM_ERR_INVALID_ARG;
   Plan& P = h->p;
-  if (cudaStreamSynchronize(P.last_stream) != cudaSuccess) return MSM_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return MSM_ERR_CUDA;
   int bits = 0;
   if (cudaMemcpy(&bits, P.d.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MSM_ERR_CUDA;
   if (bits && cudaMemset(P.d.status, 0, sizeof(int)) != cudaSuccess) return MSM_ERR_CUDA;

@@ -831,11 +831,6 @@ void anterp_t(Plan& P, void* grid0, const double* dscale, double factor, cudaStr
   A.pd = P.apd;
   dim3 grid(blocks_for(P.nc[0], A.B), blocks_for(P.nc[1], A.B), blocks_for(P.nc[2], A.B));
   size_t sm = sizeof(ACC) * (size_t)A.pd * A.pd * A.pd;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_anterp_patch<T, ACC, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
   k_anterp_patch<T, ACC, ORDER><<<grid, 256, sm, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.cell_start, A,
                                                      dims_of(P, 0), (double*)grid0, dscale, factor);
 }
@@ -1000,11 +995,6 @@ cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, double* ph
     size_t sm = (P.fp64 ? 8 : 4) * (size_t)AA.pd * AA.pd * AA.pd;
 #define MSM_FWD(T, O)                                                                                            \
   {                                                                                                              \
-    static bool attr = false;                                                                                    \
-    if (!attr) {                                                                                                 \
-      cudaFuncSetAttribute(k_interp_fwd<T, O>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);         \
-      attr = true;                                                                                               \
-    }                                                                                                            \
     k_interp_fwd<T, O><<<grid, 256, sm, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.idx[0], P.d.cell_start, AA, \
                                               (const T*)P.d.gu[0], G, A, (const T*)P.d.phis, (R4<T>*)P.d.fs,    \
                                               (R4<T>*)P.d.glong, phi, force, P.d.partial);                      \
@@ -1032,11 +1022,6 @@ cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, double*
   P.launches += 1;
 #define MSM_BWD(T, O)                                                                                             \
   {                                                                                                               \
-    static bool attr = false;                                                                                     \
-    if (!attr) {                                                                                                  \
-      cudaFuncSetAttribute(k_interp_bwd<T, O>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);          \
-      attr = true;                                                                                                \
-    }                                                                                                             \
     k_interp_bwd<T, O><<<grid, 256, sm, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.idx[0], P.d.cell_start, AA,  \
                                               (const T*)P.d.au[0], G, A, (const T*)P.d.phis,                     \
                                               (const R4<T>*)P.d.fs, (const R4<T>*)P.d.glong, gE, grad_pos, grad_q); \
@@ -1048,6 +1033,30 @@ cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, double*
   }
 #undef MSM_BWD
   return cudaGetLastError();
+}
+
+// Opts the patch kernels into more than 48 KB of dynamic shared memory.  Done
+// once per process when the first plan is built, so that no configuration call
+// happens while a stream is being captured into a graph.
+cudaError_t configure_kernels() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (r != cudaSuccess) e = r;
+  };
+  set((const void*)k_anterp_patch<float, float, 3>);
+  set((const void*)k_anterp_patch<float, float, 5>);
+  set((const void*)k_anterp_patch<double, double, 3>);
+  set((const void*)k_anterp_patch<double, double, 5>);
+  set((const void*)k_interp_fwd<float, 3>);
+  set((const void*)k_interp_fwd<float, 5>);
+  set((const void*)k_interp_fwd<double, 3>);
+  set((const void*)k_interp_fwd<double, 5>);
+  set((const void*)k_interp_bwd<float, 3>);
+  set((const void*)k_interp_bwd<float, 5>);
+  set((const void*)k_interp_bwd<double, 3>);
+  set((const void*)k_interp_bwd<double, 5>);
+  return e;
 }
 
 cudaError_t launch_grid_to_double(Plan& P, const void* src, double* dst, int64_t count, bool is_double,

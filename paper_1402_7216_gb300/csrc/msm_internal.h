@@ -133,6 +133,7 @@ struct Plan {
 };
 
 // ---- host helpers (plan.cpp) ----
+int validate_params(const msm_params* p);  // host only, no CUDA calls
 int build_plan(const msm_params* p, Plan* plan);
 void free_plan(Plan* plan);
 int64_t grid_points(const Plan& P, int k);
@@ -155,6 +156,8 @@ cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, double* ph
 // adjoint: interpolation of the adjoint grid and assembly of dL/dq, dL/dr
 cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, double* grad_pos,
                                    double* grad_q, cudaStream_t s);
+// one-time kernel attributes (called once per process before the first launch)
+cudaError_t configure_kernels();
 // grid copy to double (debug)
 cudaError_t launch_grid_to_double(Plan& P, const void* src, double* dst, int64_t count, bool is_double,
                                   cudaStream_t s);

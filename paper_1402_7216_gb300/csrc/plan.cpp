@@ -198,8 +198,31 @@ void build_segments(const Plan& P, const std::vector<double>& G, const int E[3],
 
 int64_t grid_points(const Plan& P, int k) { return (int64_t)P.n[k][0] * P.n[k][1] * P.n[k][2]; }
 
+int validate_params(const msm_params* pp) {
+  const msm_params& p = *pp;
+  for (int d = 0; d < 3; ++d)
+    if (!(p.box[d] > 0.0) || !std::isfinite(p.box[d])) return MSM_ERR_INVALID_ARG;
+  if (!(p.cutoff > 0.0) || !(p.spacing > 0.0) || !std::isfinite(p.cutoff) || !std::isfinite(p.spacing))
+    return MSM_ERR_INVALID_ARG;
+  if (p.order != 3 && p.order != 5) return MSM_ERR_INVALID_ARG;
+  if (p.splitting < 1 || p.splitting > 3) return MSM_ERR_INVALID_ARG;
+  if (p.precision != MSM_FP64 && p.precision != MSM_MIXED) return MSM_ERR_INVALID_ARG;
+  if (p.levels < 0 || p.levels > kMaxLevels) return MSM_ERR_INVALID_ARG;
+  if (p.max_atoms < 1 || p.max_atoms > (int64_t)1 << 30) return MSM_ERR_INVALID_ARG;
+  if (!std::isfinite(p.coulomb_k)) return MSM_ERR_INVALID_ARG;
+  if (p.periodic) {
+    for (int d = 0; d < 3; ++d)
+      if (p.cutoff > 0.5 * p.box[d]) return MSM_ERR_CUTOFF_GT_HALF_BOX;
+    for (int d = 0; d < 3; ++d)
+      if ((int)std::floor(p.box[d] / (0.5 * p.cutoff)) < 5) return MSM_ERR_UNSUPPORTED;
+  }
+  return MSM_OK;
+}
+
 int build_plan(const msm_params* pp, Plan* P) {
   const msm_params& p = *pp;
+  int vrc = validate_params(pp);
+  if (vrc != MSM_OK) return vrc;
   for (int d = 0; d < 3; ++d)
     if (!(p.box[d] > 0.0) || !std::isfinite(p.box[d])) return MSM_ERR_INVALID_ARG;
   if (!(p.cutoff > 0.0) || !(p.spacing > 0.0) || !std::isfinite(p.cutoff) || !std::isfinite(p.spacing))

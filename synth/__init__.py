@@ -4,5 +4,5 @@ Holds none of the multilevel summation arithmetic: it only places atoms and
 assigns charges.  Both the oracle side and the CUDA side take their inputs
 from here.
 """
-from .water import (TIP3P, WORKLOADS, Workload, make_water_box, replica_sizes,  # noqa: F401
-                    workload, spatial_subsample)
+from .water import (TIP3P, WORKLOADS, Workload, make_water_box, replica_boxes,  # noqa: F401
+                    replica_sizes, workload, spatial_subsample)

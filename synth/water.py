@@ -4,9 +4,10 @@ Recipe (stated once, used by every test and benchmark):
   * sites: water oxygens and ions.  Up to ``RSA_MAX_SITES`` sites are placed by
     random sequential addition (uniform proposals, rejected when closer than
     ``dmin`` = 2.5 A to an accepted site, tested in batches against a hash grid);
-    larger systems use a jittered simple-cubic lattice (spacing chosen so the
-    lattice has at least as many nodes as sites, a random subset of nodes,
-    uniform jitter of +-0.25 A per coordinate).  Both keep sites >= 2.5 A apart.
+    larger systems (and the batched replicas) use a jittered rectangular
+    lattice (node counts chosen so the lattice has at least as many nodes as
+    sites, a random subset of nodes, uniform jitter of up to +-0.25 A per
+    coordinate).  Both keep sites >= 2.5 A apart.
   * water: O at the site, the two H at 0.9572 A with H-O-H = 104.52 deg, in a
     uniformly random orientation (random unit quaternion).
   * charges: O -0.834 e, H +0.417 e, Na+ +1 e, Cl- -1 e.  Ions replace random
@@ -125,24 +126,26 @@ def _rsa_sites(rng, n, L, lo, hi, periodic, dmin):
 
 
 def _lattice_sites(rng, n, L, lo, hi, periodic, dmin, jitter=0.25):
-    """Jittered simple-cubic lattice, random subset of nodes."""
-    span = np.asarray(hi, float) - np.asarray(lo, float)
-    vol = float(np.prod(span))
-    a = (vol / n) ** (1.0 / 3.0)
-    while True:
-        m = np.floor(span / a).astype(int) if not periodic else np.floor(np.asarray(L) / a).astype(int)
-        if int(m.prod()) >= n:
-            break
-        a *= 0.995
-    step = (np.asarray(L, float) / m) if periodic else (span / np.maximum(m - 1, 1))
-    if step.min() - 2 * jitter < dmin:
+    """Jittered rectangular lattice, random subset of nodes.  Node counts per
+    dimension start at the ~3.06 A water-density spacing and grow (the
+    coarsest dimension first) until the lattice holds n nodes; the jitter
+    shrinks if needed so that sites stay at least dmin apart."""
+    span = (np.asarray(L, float) if periodic else np.asarray(hi, float) - np.asarray(lo, float))
+    a = (float(np.prod(span)) / n) ** (1.0 / 3.0)
+    m = np.maximum(1, np.floor(span / a).astype(int))
+    nodes = (lambda mm: span / mm) if periodic else (lambda mm: span / np.maximum(mm - 1, 1))
+    while int(m.prod()) < n:
+        m[int(np.argmax(nodes(m)))] += 1
+    step = nodes(m)
+    jit = min(jitter, 0.499 * (float(step.min()) - dmin))
+    if jit < 0:
         raise ValueError("lattice too dense for the minimum spacing")
     idx = rng.choice(int(m.prod()), size=n, replace=False)
     ijk = np.stack([idx % m[0], (idx // m[0]) % m[1], idx // (m[0] * m[1])], axis=1)
     base = (np.asarray(lo, float) if not periodic else 0.0) + ijk * step
     if periodic:
         base = base + 0.5 * step
-    pos = base + rng.uniform(-jitter, jitter, size=(n, 3))
+    pos = base + rng.uniform(-jit, jit, size=(n, 3))
     if not periodic:
         pos = np.clip(pos, lo, hi)
     return pos
@@ -235,6 +238,18 @@ def replica_sizes(n_rep=64, lo=5000, hi=50000, seed=14):
     rng = np.random.default_rng(seed)
     n = np.exp(rng.uniform(math.log(lo), math.log(hi), size=n_rep))
     return (np.round(n / 3.0).astype(int) * 3).tolist()
+
+
+def replica_boxes(n_rep=64, lo=5000, hi=50000, density=0.1, seed=14, method="lattice"):
+    """The batched-replica workload: n_rep periodic water boxes whose atom
+    counts are log-uniform in [lo, hi] (multiples of 3), each at the given
+    atom density, L = (N / density)^(1/3).  Returns [(L, pos, q), ...]."""
+    out = []
+    for r, n in enumerate(replica_sizes(n_rep, lo, hi, seed)):
+        L = (n / density) ** (1.0 / 3.0)
+        pos, q = make_water_box(L, n // 3, 0, 0, seed=seed * 1000 + r, periodic=True, method=method)
+        out.append((L, pos, q))
+    return out
 
 
 def spatial_subsample(pos, box, n_pick, seed=0):
