@@ -449,52 +449,93 @@ __global__ void __launch_bounds__(128) k_lattice(const T* __restrict__ q, T* __r
   }
 }
 
-__device__ __forceinline__ void two_sum_add2(float2& s, float2& c, float2 x) {
-  two_sum_add(s.x, c.x, x.x);
-  two_sum_add(s.y, c.y, x.y);
+// Asynchronous staging of one plane (cp.async: global -> shared without
+// registers); points outside an open grid are zero-filled (source size 0).
+__device__ __forceinline__ void stage_plane_async(float* plane, const float* __restrict__ q, const GridDims& G,
+                                                  int zi, int x0, int y0, int Ex, int Ey, int SXw, int SX, int SY) {
+  int gz;
+  bool zok;
+  if (G.periodic) {
+    gz = zi % G.n[2];
+    if (gz < 0) gz += G.n[2];
+    zok = true;
+  } else {
+    gz = zi;
+    zok = (zi >= 0 && zi < G.n[2]);
+  }
+  for (int e = threadIdx.x; e < SY * SXw; e += blockDim.x) {
+    int xx = e % SXw, yy = e / SXw;
+    int gx = x0 - Ex + xx, gy = y0 - Ey + yy;
+    bool ok;
+    if (G.periodic) {
+      gx %= G.n[0];
+      if (gx < 0) gx += G.n[0];
+      gy %= G.n[1];
+      if (gy < 0) gy += G.n[1];
+      ok = true;
+    } else {
+      ok = zok && gx >= 0 && gx < G.n[0] && gy >= 0 && gy < G.n[1];
+    }
+    const float* src = ok ? q + ((size_t)gz * G.n[1] + gy) * G.n[0] + gx : q;
+    unsigned dst = (unsigned)__cvta_generic_to_shared(plane + yy * SX + xx);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0));
+  }
 }
 
+// FP32: two rows per lane packed into float2 (one FFMA2 per two outputs),
+// coefficients pre-duplicated as float2 pairs, the next input plane staged by
+// cp.async while the current one is applied (double buffer).  Each plane's
+// partial sums are added into the totals (blocked summation over planes).
 __global__ void __launch_bounds__(128) k_lattice_f2(const float* __restrict__ q, float* __restrict__ u, GridDims G,
                                                     const Segment2* __restrict__ seg,
                                                     const int* __restrict__ seg_start, LatticeArgs L, float scale) {
   constexpr int LBY = 16;
   extern __shared__ unsigned char smem_raw[];
-  float* plane = reinterpret_cast<float*>(smem_raw);
   const int Ex = L.Ex, Ey = L.Ey, Ez = L.Ez;
   const int SXw = LBX + 2 * Ex + kSeg, SX = SXw | 1, SY = LBY + 2 * Ey;
+  float* buf0 = reinterpret_cast<float*>(smem_raw);
+  float* buf1 = buf0 + SX * SY;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tx = lane & 3, ty = lane >> 2;
   const int bz = blockIdx.z % L.nbz, part = blockIdx.z / L.nbz;
   const int x0 = blockIdx.x * LBX, y0 = blockIdx.y * LBY, z0 = bz * LBZ, zo = z0 + warp;
   const int nplanes = LBZ + 2 * Ez, per = (nplanes + L.nsplit - 1) / L.nsplit;
   const int zbeg = z0 - Ez + part * per, zend = min(z0 - Ez + nplanes, zbeg + per);
-  float2 acc[LPX], cmp[LPX];  // (row ty, row ty + 8) of the 8 x outputs
+  float2 acc[LPX];  // (row ty, row ty + 8) of the 8 x outputs
 #pragma unroll
-  for (int j = 0; j < LPX; ++j) acc[j] = cmp[j] = make_float2(0.f, 0.f);
+  for (int j = 0; j < LPX; ++j) acc[j] = make_float2(0.f, 0.f);
+  if (zbeg < zend) stage_plane_async(buf0, q, G, zbeg, x0, y0, Ex, Ey, SXw, SX, SY);
+  asm volatile("cp.async.commit_group;\n" ::);
   for (int zi = zbeg; zi < zend; ++zi) {
-    __syncthreads();
-    stage_plane(plane, q, G, zi, x0, y0, Ex, Ey, SXw, SX, SY);
-    __syncthreads();
+    float* cur = ((zi - zbeg) & 1) ? buf1 : buf0;
+    float* nxt = ((zi - zbeg) & 1) ? buf0 : buf1;
+    if (zi + 1 < zend) stage_plane_async(nxt, q, G, zi + 1, x0, y0, Ex, Ey, SXw, SX, SY);
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 1;\n" ::);  // plane zi has landed (this thread's copies)
+    __syncthreads();                               // ... and everyone else's
     const int dz = zi - zo;
-    if (dz < -Ez || dz > Ez || zo >= G.n[2]) continue;  // warp-uniform
-    float2 part_[LPX];
+    if (dz >= -Ez && dz <= Ez && zo < G.n[2]) {  // warp-uniform
+      float2 part_[LPX];
 #pragma unroll
-    for (int j = 0; j < LPX; ++j) part_[j] = make_float2(0.f, 0.f);
-    const int s1 = seg_start[dz + Ez + 1];
-    for (int s = seg_start[dz + Ez]; s < s1; ++s) {
-      const Segment2 sg = seg[s];
-      const float* r0 = plane + (ty + Ey + sg.dy) * SX + tx * LPX + Ex + sg.dx0;
-      const float* r1 = r0 + 8 * SX;
-      float2 win[LPX + kSeg - 1];
+      for (int j = 0; j < LPX; ++j) part_[j] = make_float2(0.f, 0.f);
+      const int s1 = seg_start[dz + Ez + 1];
+      for (int s = seg_start[dz + Ez]; s < s1; ++s) {
+        const Segment2 sg = seg[s];
+        const float* r0 = cur + (ty + Ey + sg.dy) * SX + tx * LPX + Ex + sg.dx0;
+        const float* r1 = r0 + 8 * SX;
+        float2 win[LPX + kSeg - 1];
 #pragma unroll
-      for (int k = 0; k < LPX + kSeg - 1; ++k) win[k] = make_float2(r0[k], r1[k]);
+        for (int k = 0; k < LPX + kSeg - 1; ++k) win[k] = make_float2(r0[k], r1[k]);
 #pragma unroll
-      for (int k = 0; k < kSeg; ++k)
+        for (int k = 0; k < kSeg; ++k)
 #pragma unroll
-        for (int j = 0; j < LPX; ++j) part_[j] = __ffma2_rn(sg.g[k], win[j + k], part_[j]);
+          for (int j = 0; j < LPX; ++j) part_[j] = __ffma2_rn(sg.g[k], win[j + k], part_[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < LPX; ++j) acc[j] = __fadd2_rn(acc[j], part_[j]);
     }
-#pragma unroll
-    for (int j = 0; j < LPX; ++j) two_sum_add2(acc[j], cmp[j], part_[j]);
+    __syncthreads();  // the buffer just read is restaged two planes from now
   }
+  asm volatile("cp.async.wait_group 0;\n" ::);
   if (zo >= G.n[2]) return;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
@@ -504,7 +545,7 @@ __global__ void __launch_bounds__(128) k_lattice_f2(const float* __restrict__ q,
     for (int j = 0; j < LPX; ++j) {
       int x = x0 + tx * LPX + j;
       if (x >= G.n[0]) continue;
-      float v = scale * (r == 0 ? acc[j].x + cmp[j].x : acc[j].y + cmp[j].y);
+      float v = scale * (r == 0 ? acc[j].x : acc[j].y);
       if (L.nsplit > 1) atomicAdd(u + ((size_t)zo * G.n[1] + y) * G.n[0] + x, v);
       else u[((size_t)zo * G.n[1] + y) * G.n[0] + x] = v;
     }
@@ -942,7 +983,7 @@ void lattice_t(Plan& P, int k, const double* qk64, T* uk, cudaStream_t st) {
   }
   dim3 grid(blocks_for(G.n[0], LBX), blocks_for(G.n[1], LBY), L.nbz * L.nsplit);
   int SX = (LBX + 2 * P.E[0] + kSeg) | 1, SY = LBY + 2 * P.E[1];
-  size_t sm = sizeof(T) * SX * SY;
+  size_t sm = sizeof(T) * SX * SY * (f32 ? 2 : 1);  // FP32 double-buffers its planes
   T scale = (T)std::ldexp(1.0, -k);
   if (f32) {
     k_lattice_f2<<<grid, 128, sm, st>>>((const float*)qk, (float*)uk, G, (const Segment2*)P.d.seg2, P.d.seg_start,

@@ -245,9 +245,16 @@ int build_plan(const msm_params* pp, Plan* P) {
   if (rc != MSM_OK) return rc;
   P->gamma0 = smooth(p.splitting, 0.0);
 
-  // short-range cells: width >= a/2, neighbours within two cells
+  // short-range cells: width >= a/2 (neighbours within two cells), widened
+  // toward ~26 atoms per cell at the plan's capacity density so that the 32
+  // lanes of a warp stay busy (the bounding-box culling absorbs the larger
+  // candidate volume)
+  double vol = p.box[0] * p.box[1] * p.box[2];
+  double wfill = std::cbrt(26.0 * vol / (double)p.max_atoms);
+  double wmin = std::max(0.5 * p.cutoff, std::min(wfill, 0.75 * p.cutoff));
   for (int d = 0; d < 3; ++d) {
-    int c = (int)std::floor(p.box[d] / (0.5 * p.cutoff));
+    int c = (int)std::floor(p.box[d] / wmin);
+    if (p.periodic && c < 5) c = (int)std::floor(p.box[d] / (0.5 * p.cutoff));
     if (c < 1) c = 1;
     if (p.periodic && c < 5) return MSM_ERR_UNSUPPORTED;  // the 5-cell walk would alias images
     if (c > 1024) c = 1024;
