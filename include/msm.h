@@ -69,11 +69,32 @@ typedef struct {
   int64_t max_atoms;/* capacity of the plan's workspace */
 } msm_params;
 
+/* Tile shapes of a plan (0 in a field keeps its default).  They change
+ * speed, never results beyond floating-point summation order.
+ *   cell_fill     target atoms per short-range cell at the plan's capacity
+ *                 density (default 26; cells stay between a/2 and 3a/4 wide)
+ *   patch_cells   short-range cells per side of the shared-memory patch blocks
+ *                 of anterpolation and interpolation (default: the largest of
+ *                 4, 3, 2, 1 whose patch fits)
+ *   lattice_waves blocks per SM the lattice cutoff aims for when it splits the
+ *                 stencil planes of a small level over several blocks (default 4)
+ * Ranges: cell_fill 0..256, patch_cells 0..4, lattice_waves 0..64; anything
+ * else is INVALID_ARG (checked on the host before any device call). */
+typedef struct {
+  int cell_fill;
+  int patch_cells;
+  int lattice_waves;
+} msm_tuning;
+
 /* Builds a plan: validates params, fixes the grid geometry, builds the
  * level stencil and the top-level kernel (FP64, host) and allocates device
  * workspace for max_atoms atoms on the current device.  Synchronous.
  * Errors: INVALID_ARG, UNSUPPORTED, CUTOFF_GT_HALF_BOX, OOM, CUDA. */
 int msm_create(const msm_params* params, msm_handle* out);
+
+/* msm_create with explicit tile shapes (tuning may be NULL: defaults).
+ * Errors as msm_create; INVALID_ARG for negative or out-of-range fields. */
+int msm_create_tuned(const msm_params* params, const msm_tuning* tuning, msm_handle* out);
 
 /* Frees the plan and its device workspace (synchronises the device). */
 void msm_destroy(msm_handle h);

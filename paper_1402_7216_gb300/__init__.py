@@ -39,11 +39,12 @@ class MSM:
     box: edges (L_x, L_y, L_z); periodic: bool; cutoff: a; spacing: h;
     levels: l (0 = automatic); order: 3 cubic / 5 quintic; splitting: Taylor
     order m of gamma (1, 2, 3); precision: "fp64" or "mixed"; coulomb_k:
-    prefactor; max_atoms: capacity of the workspace.
+    prefactor; max_atoms: capacity of the workspace; tuning: optional tile
+    shapes {"cell_fill", "patch_cells", "lattice_waves"} (see autotune.py).
     """
 
     def __init__(self, box, periodic, cutoff, spacing, levels=0, order=3, splitting=2,
-                 precision="mixed", coulomb_k=1.0, max_atoms=1 << 20):
+                 precision="mixed", coulomb_k=1.0, max_atoms=1 << 20, tuning=None):
         L = lib()
         p = _capi.MSMParams()
         b = box if hasattr(box, "__len__") else (box, box, box)
@@ -62,7 +63,10 @@ class MSM:
         self.precision = precision
         self._h = C.c_void_p()
         self._last_n = None
-        _capi.check(L.msm_create(C.byref(p), C.byref(self._h)), "msm_create")
+        self.tuning = dict(tuning or {})
+        t = _capi.MSMTuning(int(self.tuning.get("cell_fill", 0)), int(self.tuning.get("patch_cells", 0)),
+                            int(self.tuning.get("lattice_waves", 0)))
+        _capi.check(L.msm_create_tuned(C.byref(p), C.byref(t), C.byref(self._h)), "msm_create_tuned")
         heff = (C.c_double * 3)()
         nl = C.c_int()
         dims = (C.c_int * (3 * _capi.MAX_LEVELS))()

@@ -26,6 +26,10 @@ class MSMParams(C.Structure):
                 ("max_atoms", C.c_int64)]
 
 
+class MSMTuning(C.Structure):
+    _fields_ = [("cell_fill", C.c_int), ("patch_cells", C.c_int), ("lattice_waves", C.c_int)]
+
+
 class MSMError(RuntimeError):
     def __init__(self, code, what=""):
         self.code = code
@@ -34,7 +38,7 @@ class MSMError(RuntimeError):
 
 _lib = None
 _D = C.POINTER(C.c_double)
-EXPORTS = ["msm_create", "msm_destroy", "msm_query", "msm_eval", "msm_eval_backward",
+EXPORTS = ["msm_create", "msm_create_tuned", "msm_destroy", "msm_query", "msm_eval", "msm_eval_backward",
            "msm_eval_host", "msm_status", "msm_debug_grid", "msm_profile", "msm_profile_read",
            "msm_stage_name", "msm_energy_noalloc", "msm_eval_batch", "msm_eval_backward_batch",
            "msm_batch_graph_create", "msm_graph_launch", "msm_graph_destroy", "msm_strerror"]
@@ -53,6 +57,8 @@ def load(path=LIB_PATH):
     vp = C.c_void_p
     L.msm_create.argtypes = [C.POINTER(MSMParams), C.POINTER(vp)]
     L.msm_create.restype = C.c_int
+    L.msm_create_tuned.argtypes = [C.POINTER(MSMParams), C.POINTER(MSMTuning), C.POINTER(vp)]
+    L.msm_create_tuned.restype = C.c_int
     L.msm_destroy.argtypes = [vp]
     L.msm_destroy.restype = None
     L.msm_query.argtypes = [vp, _D, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]

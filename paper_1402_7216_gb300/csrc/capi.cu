@@ -195,16 +195,19 @@ struct msm_graph {
 
 extern "C" {
 
-int msm_create(const msm_params* params, msm_handle* out) {
+int msm_create(const msm_params* params, msm_handle* out) { return msm_create_tuned(params, nullptr, out); }
+
+int msm_create_tuned(const msm_params* params, const msm_tuning* tuning, msm_handle* out) {
   if (!params || !out) return MSM_ERR_INVALID_ARG;
   *out = nullptr;
   int vrc = validate_params(params);
+  if (vrc == MSM_OK) vrc = validate_tuning(tuning);
   if (vrc != MSM_OK) return vrc;
   std::call_once(g_config_once, [] { g_config_err = configure_kernels(); });
   if (g_config_err != cudaSuccess) return MSM_ERR_CUDA;
   msm_plan* h = new (std::nothrow) msm_plan();
   if (!h) return MSM_ERR_OOM;
-  int rc = build_plan(params, &h->p);
+  int rc = build_plan(params, tuning, &h->p);
   if (rc != MSM_OK) {
     free_plan(&h->p);
     delete h;

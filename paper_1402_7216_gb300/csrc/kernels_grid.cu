@@ -976,7 +976,8 @@ void lattice_t(Plan& P, int k, const double* qk64, T* uk, cudaStream_t st) {
   L.Ez = P.E[2];
   L.nbz = (int)blocks_for(G.n[2], LBZ);
   int64_t bricks = (int64_t)blocks_for(G.n[0], LBX) * blocks_for(G.n[1], LBY) * L.nbz;
-  L.nsplit = (int)std::min<int64_t>(LBZ + 2 * L.Ez, std::max<int64_t>(1, (4 * 152 + bricks - 1) / bricks));
+  const int64_t target = (int64_t)P.lattice_waves * 152;
+  L.nsplit = (int)std::min<int64_t>(LBZ + 2 * L.Ez, std::max<int64_t>(1, (target + bricks - 1) / bricks));
   if (L.nsplit > 1) {
     cudaMemsetAsync(uk, 0, sizeof(T) * (size_t)grid_points(P, k), st);
     P.launches += 1;

@@ -103,6 +103,8 @@ struct Plan {
   int nrows = 0;
   // anterpolation patches: blocks of ablk^3 cells, patches of apd^3 points
   int ablk = 1, apd = 1;
+  // lattice: blocks per SM to aim for when splitting a small level's planes
+  int lattice_waves = 4;
   // smoothing constants
   double gamma0 = 0.0;         // gamma(0)
   // level stencil
@@ -134,7 +136,8 @@ struct Plan {
 
 // ---- host helpers (plan.cpp) ----
 int validate_params(const msm_params* p);  // host only, no CUDA calls
-int build_plan(const msm_params* p, Plan* plan);
+int validate_tuning(const msm_tuning* t);  // host only, no CUDA calls
+int build_plan(const msm_params* p, const msm_tuning* t, Plan* plan);
 void free_plan(Plan* plan);
 int64_t grid_points(const Plan& P, int k);
 

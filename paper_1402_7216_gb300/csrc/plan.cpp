@@ -219,10 +219,24 @@ int validate_params(const msm_params* pp) {
   return MSM_OK;
 }
 
-int build_plan(const msm_params* pp, Plan* P) {
+int validate_tuning(const msm_tuning* t) {
+  if (!t) return MSM_OK;
+  if (t->cell_fill < 0 || t->cell_fill > 256 || t->patch_cells < 0 || t->patch_cells > 4 || t->lattice_waves < 0 ||
+      t->lattice_waves > 64)
+    return MSM_ERR_INVALID_ARG;
+  return MSM_OK;
+}
+
+int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   const msm_params& p = *pp;
   int vrc = validate_params(pp);
   if (vrc != MSM_OK) return vrc;
+  int trc = validate_tuning(tune);
+  if (trc != MSM_OK) return trc;
+  msm_tuning TU = {0, 0, 0};
+  if (tune) TU = *tune;
+  const double fill = TU.cell_fill > 0 ? TU.cell_fill : 26.0;
+  P->lattice_waves = TU.lattice_waves > 0 ? TU.lattice_waves : 4;
   for (int d = 0; d < 3; ++d)
     if (!(p.box[d] > 0.0) || !std::isfinite(p.box[d])) return MSM_ERR_INVALID_ARG;
   if (!(p.cutoff > 0.0) || !(p.spacing > 0.0) || !std::isfinite(p.cutoff) || !std::isfinite(p.spacing))
@@ -246,11 +260,11 @@ int build_plan(const msm_params* pp, Plan* P) {
   P->gamma0 = smooth(p.splitting, 0.0);
 
   // short-range cells: width >= a/2 (neighbours within two cells), widened
-  // toward ~26 atoms per cell at the plan's capacity density so that the 32
+  // toward ~26 atoms per cell (tunable) at the plan's capacity density so that the 32
   // lanes of a warp stay busy (the bounding-box culling absorbs the larger
   // candidate volume)
   double vol = p.box[0] * p.box[1] * p.box[2];
-  double wfill = std::cbrt(26.0 * vol / (double)p.max_atoms);
+  double wfill = std::cbrt(fill * vol / (double)p.max_atoms);
   double wmin = std::max(0.5 * p.cutoff, std::min(wfill, 0.75 * p.cutoff));
   for (int d = 0; d < 3; ++d) {
     int c = (int)std::floor(p.box[d] / wmin);
@@ -304,7 +318,7 @@ int build_plan(const msm_params* pp, Plan* P) {
   // points per dimension (with margin for rounding); keep it in shared memory
   {
     int cap = P->fp64 ? 24 : 32;
-    int B = 4, pd = 0;
+    int B = TU.patch_cells > 0 ? TU.patch_cells : 4, pd = 0;
     for (; B >= 1; --B) {
       pd = 0;
       for (int d = 0; d < 3; ++d)

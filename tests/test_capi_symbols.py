@@ -63,3 +63,21 @@ def test_create_rejects_bad_parameters_without_a_gpu(library):
     p.cutoff = 13.0
     assert L.msm_create(ctypes.byref(p), ctypes.byref(h)) == -2        # fewer than 5 cells
     assert L.msm_create(None, ctypes.byref(h)) == -1
+
+
+def test_create_tuned_rejects_bad_tuning_without_a_gpu(library):
+    # the tuning ranges are checked on the host before any device call
+    from paper_1402_7216_gb300 import _capi
+    L = _capi.load()
+    h = ctypes.c_void_p()
+    p = _capi.MSMParams()
+    for d in range(3):
+        p.box[d] = 30.0
+    p.periodic, p.cutoff, p.spacing, p.order, p.splitting = 1, 9.0, 2.0, 3, 2
+    p.precision, p.coulomb_k, p.max_atoms = 1, 1.0, 100
+    for bad in [(-1, 0, 0), (257, 0, 0), (0, 5, 0), (0, -2, 0), (0, 0, 65), (0, 0, -1)]:
+        t = _capi.MSMTuning(*bad)
+        assert L.msm_create_tuned(ctypes.byref(p), ctypes.byref(t), ctypes.byref(h)) == -1, bad
+    p.order = 4  # bad params are still reported with a valid tuning
+    t = _capi.MSMTuning(26, 4, 4)
+    assert L.msm_create_tuned(ctypes.byref(p), ctypes.byref(t), ctypes.byref(h)) == -1
