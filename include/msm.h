@@ -129,6 +129,24 @@ int msm_eval(msm_handle h, int64_t n, const double* pos, const double* q, double
 int msm_eval_backward(msm_handle h, const double* grad_energy, double* grad_pos, double* grad_q,
                       void* cuda_stream);
 
+/* msm_eval with FP32 positions, charges and per-atom outputs (device):
+ *   pos [n][3] float, q [n] float, phi [n] float or NULL, force [n][3] float
+ *   or NULL; energy stays [1] double.
+ * The plan's precision decides the arithmetic exactly as for msm_eval; FP32
+ * inputs only skip the FP64 reads, and on a mixed plan the results match
+ * msm_eval on the same (float-representable) inputs to FP32 rounding.
+ * Errors as msm_eval.  (Interface from the same input/output definition,
+ * Sec. "Multilevel Summation Method": charges q_i and positions r_i in, the
+ * potential and the forces F_i = -dU/dr_i out.) */
+int msm_eval_f32io(msm_handle h, int64_t n, const float* pos, const float* q, double* energy,
+                   float* phi, float* force, void* cuda_stream);
+
+/* msm_eval_backward with FP32 outputs grad_pos [n][3] and grad_q [n]
+ * (grad_energy stays [1] double).  Follows either msm_eval or
+ * msm_eval_f32io.  Errors as msm_eval_backward. */
+int msm_eval_backward_f32io(msm_handle h, const double* grad_energy, float* grad_pos, float* grad_q,
+                            void* cuda_stream);
+
 /* Same as msm_eval with HOST buffers: copies pos and q to the device, runs
  * the evaluation on the stream, copies energy (and phi/force when non-NULL)
  * back and synchronises the stream before returning.  Pinned host memory

@@ -92,38 +92,53 @@ class MSM:
     def _check_inputs(pos, q):
         if not (pos.is_cuda and q.is_cuda):
             raise ValueError("pos and q must be CUDA tensors")
-        if pos.dtype != torch.float64 or q.dtype != torch.float64:
-            raise ValueError("pos and q must be float64")
+        if pos.dtype != q.dtype or pos.dtype not in (torch.float64, torch.float32):
+            raise ValueError("pos and q must both be float64 (msm_eval) or both float32 (msm_eval_f32io)")
         if pos.dim() != 2 or pos.shape[1] != 3 or q.shape != (pos.shape[0],):
             raise ValueError("pos must be [N,3] and q [N]")
         return pos.contiguous(), q.contiguous()
 
     def eval(self, pos, q, want_phi=True, want_force=True, stream=None, out=None):
-        """Forward pass: returns (E [0-d], phi [N] or None, F [N,3] or None)."""
+        """Forward pass: returns (E [0-d] float64, phi [N] or None, F [N,3] or
+        None).  float64 inputs go through msm_eval, float32 inputs through
+        msm_eval_f32io (phi and F then come back as float32)."""
         pos, q = self._check_inputs(pos, q)
         n = pos.shape[0]
+        io = pos.dtype
         if out is None:
             E = torch.empty((), dtype=torch.float64, device=pos.device)
-            phi = torch.empty(n, dtype=torch.float64, device=pos.device) if want_phi else None
-            F = torch.empty((n, 3), dtype=torch.float64, device=pos.device) if want_force else None
+            phi = torch.empty(n, dtype=io, device=pos.device) if want_phi else None
+            F = torch.empty((n, 3), dtype=io, device=pos.device) if want_force else None
         else:
             E, phi, F = out
-        rc = lib().msm_eval(self._h, n, _ptr(pos), _ptr(q), _ptr(E), _ptr(phi), _ptr(F), _stream(stream))
-        _capi.check(rc, "msm_eval")
+        fn = lib().msm_eval if io == torch.float64 else lib().msm_eval_f32io
+        rc = fn(self._h, n, _ptr(pos), _ptr(q), _ptr(E), _ptr(phi), _ptr(F), _stream(stream))
+        _capi.check(rc, "msm_eval" if io == torch.float64 else "msm_eval_f32io")
         self._last_n = n
+        self._last_io = io
         return E, phi, F
 
-    def backward(self, grad_E, want_pos=True, want_q=True, stream=None):
-        """Adjoint of the last eval: returns (dL/dpos [N,3], dL/dq [N])."""
+    def eval_f32io(self, pos, q, want_phi=True, want_force=True, stream=None, out=None):
+        """msm_eval_f32io: eval with float32 positions, charges and outputs."""
+        if pos.dtype != torch.float32 or q.dtype != torch.float32:
+            raise ValueError("eval_f32io takes float32 pos and q")
+        return self.eval(pos, q, want_phi, want_force, stream, out)
+
+    def backward(self, grad_E, want_pos=True, want_q=True, stream=None, dtype=None):
+        """Adjoint of the last eval: returns (dL/dpos [N,3], dL/dq [N]) in the
+        last eval's input type (or `dtype`: float64 -> msm_eval_backward,
+        float32 -> msm_eval_backward_f32io)."""
         n = self._last_n
         if n is None:
             raise MSMError(-10, "msm_eval_backward")
+        io = dtype or getattr(self, "_last_io", torch.float64)
         dev = grad_E.device
-        gp = torch.empty((n, 3), dtype=torch.float64, device=dev) if want_pos else None
-        gq = torch.empty(n, dtype=torch.float64, device=dev) if want_q else None
+        gp = torch.empty((n, 3), dtype=io, device=dev) if want_pos else None
+        gq = torch.empty(n, dtype=io, device=dev) if want_q else None
         g = grad_E.to(torch.float64).reshape(()).contiguous()
-        rc = lib().msm_eval_backward(self._h, _ptr(g), _ptr(gp), _ptr(gq), _stream(stream))
-        _capi.check(rc, "msm_eval_backward")
+        fn = lib().msm_eval_backward if io == torch.float64 else lib().msm_eval_backward_f32io
+        rc = fn(self._h, _ptr(g), _ptr(gp), _ptr(gq), _stream(stream))
+        _capi.check(rc, "msm_eval_backward" if io == torch.float64 else "msm_eval_backward_f32io")
         return gp, gq
 
     def eval_host(self, pos, q, want_phi=False, want_force=False, stream=None):

@@ -39,6 +39,7 @@ class MSMError(RuntimeError):
 _lib = None
 _D = C.POINTER(C.c_double)
 EXPORTS = ["msm_create", "msm_create_tuned", "msm_destroy", "msm_query", "msm_eval", "msm_eval_backward",
+           "msm_eval_f32io", "msm_eval_backward_f32io",
            "msm_eval_host", "msm_status", "msm_debug_grid", "msm_profile", "msm_profile_read",
            "msm_stage_name", "msm_energy_noalloc", "msm_eval_batch", "msm_eval_backward_batch",
            "msm_batch_graph_create", "msm_graph_launch", "msm_graph_destroy", "msm_strerror"]
@@ -67,6 +68,10 @@ def load(path=LIB_PATH):
     L.msm_eval.restype = C.c_int
     L.msm_eval_backward.argtypes = [vp, vp, vp, vp, vp]
     L.msm_eval_backward.restype = C.c_int
+    L.msm_eval_f32io.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp]
+    L.msm_eval_f32io.restype = C.c_int
+    L.msm_eval_backward_f32io.argtypes = [vp, vp, vp, vp, vp]
+    L.msm_eval_backward_f32io.restype = C.c_int
     L.msm_eval_host.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp]
     L.msm_eval_host.restype = C.c_int
     L.msm_status.argtypes = [vp]

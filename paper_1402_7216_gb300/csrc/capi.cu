@@ -63,8 +63,9 @@ cudaError_t grid_sweep(Plan& P, void* const* q, void* const* u, cudaStream_t st)
   return e;
 }
 
-int forward(Plan& P, int64_t n, const double* pos, const double* q, double* energy, double* phi,
-            double* force, cudaStream_t st) {
+// IO = the caller's type of positions, charges and per-atom outputs
+template <typename IO>
+int forward(Plan& P, int64_t n, const IO* pos, const IO* q, double* energy, IO* phi, IO* force, cudaStream_t st) {
   cudaError_t e = stage(P, MSM_STAGE_BINNING, st, [&] { return launch_binning(P, n, pos, q, st); });
   if (e == cudaSuccess) e = stage(P, MSM_STAGE_SHORT_RANGE, st, [&] { return launch_short_range(P, n, st); });
   if (e == cudaSuccess)
@@ -81,7 +82,8 @@ int forward(Plan& P, int64_t n, const double* pos, const double* q, double* ener
   return MSM_OK;
 }
 
-int backward(Plan& P, const double* grad_energy, double* grad_pos, double* grad_q, cudaStream_t st) {
+template <typename IO>
+int backward(Plan& P, const double* grad_energy, IO* grad_pos, IO* grad_q, cudaStream_t st) {
   if (P.last_n < 0) return MSM_ERR_NO_FORWARD;
   int64_t n = P.last_n;
   // adjoint of u_long = A^T M A q with respect to its inputs: anterpolate the
@@ -252,6 +254,20 @@ int msm_eval(msm_handle h, int64_t n, const double* pos, const double* q, double
 
 int msm_eval_backward(msm_handle h, const double* grad_energy, double* grad_pos, double* grad_q,
                       void* stream) {
+  if (!h || !grad_energy) return MSM_ERR_INVALID_ARG;
+  return backward(h->p, grad_energy, grad_pos, grad_q, (cudaStream_t)stream);
+}
+
+int msm_eval_f32io(msm_handle h, int64_t n, const float* pos, const float* q, double* energy, float* phi,
+                   float* force, void* stream) {
+  if (!h || n < 0 || !energy || (n > 0 && (!pos || !q))) return MSM_ERR_INVALID_ARG;
+  Plan& P = h->p;
+  if (n > P.cap) return MSM_ERR_TOO_MANY_ATOMS;
+  return forward(P, n, pos, q, energy, phi, force, (cudaStream_t)stream);
+}
+
+int msm_eval_backward_f32io(msm_handle h, const double* grad_energy, float* grad_pos, float* grad_q,
+                            void* stream) {
   if (!h || !grad_energy) return MSM_ERR_INVALID_ARG;
   return backward(h->p, grad_energy, grad_pos, grad_q, (cudaStream_t)stream);
 }

@@ -1,13 +1,33 @@
-// kernels_bin.cu -- atom binning by sort (link cells, Sec. "Short-range
-// interactions": atoms are binned into cells so that each atom only examines
-// nearby cells).  The cell key of every atom is sorted by a stable LSD radix
-// sort (8-bit digits, per-block histograms, one scan, stable scatter ranked
-// with warp match), so the binning takes no scatter atomics on global memory
-// and the order inside a cell is the input order (deterministic).
-// The gather then writes the sorted atoms in the layouts the later passes
-// read: cell-local coordinates for the pair sums, and fractional level-0 grid
-// coordinates plus the first support index for the grid passes.
+// kernels_bin.cu -- atom binning (link cells, Sec. "Short-range interactions":
+// atoms are binned into cells so that each atom only examines nearby cells).
+//
+// A counting sort over cells in four launches:
+//   k_bin_count    cell key of every atom; its rank inside the cell from one
+//                  warp-aggregated atomic per (warp, cell)
+//   k_cell_sums    per-chunk sums of the cell counts
+//   k_cell_scan    exclusive scan -> cell_start; resets the counts to zero
+//                  for the next evaluation
+//   k_bin_scatter  writes each atom's sorted records at cell_start + rank:
+//                  cell-local coordinates for the pair sums, fractional
+//                  level-0 grid coordinates and the first support index for
+//                  the grid passes, and the permutation back to input order.
+// The order inside a cell is the order in which the atomics were served, so
+// it may change from one evaluation to the next; every later pass either
+// accumulates in whatever order the atoms come or goes through the
+// permutation, so only the rounding of sums depends on it.
+//
+// Precision.  The FP64 plan folds and bins in FP64.  The mixed plan takes no
+// FP64 arithmetic at all (this GPU issues FP64 at 1/64 of the FP32 rate): an
+// FP64 coordinate is split with integer operations into hi + lo (two floats,
+// 24 + 29 significant bits), cell and grid origins are FP32 pairs whose
+// leading part times any index is exact, and the differences that matter,
+// hi - k*c_hi, are exact by Sterbenz' lemma.  The cell-local coordinate and
+// the fractional grid coordinate therefore carry a single FP32 rounding, as
+// if they had been computed in FP64 and rounded.  FP32 inputs (hi = x, lo = 0)
+// take the same path.  Positions outside [0, L) of a periodic box are folded
+// in FP64 first (rare).
 #include <cmath>
+#include <cstring>
 
 #include "msm_internal.h"
 
@@ -15,8 +35,7 @@ namespace msm {
 
 namespace {
 
-constexpr int kChunk = 4096;   // atoms per radix block
-constexpr int kThreads = 256;  // = radix size
+constexpr int kScanChunk = 4096;  // cells per block of the cell scan (1024 threads x 4)
 
 // Folds x into [0, L) (multiplying by the reciprocal: FP64 division is slow).
 __device__ __forceinline__ double fold(double x, double L, double inv_L) {
@@ -27,225 +46,344 @@ __device__ __forceinline__ double fold(double x, double L, double inv_L) {
 }
 
 struct BinArgs {
-  double box[3];
-  double inv_box[3];
-  double cw[3];
-  double inv_cw[3];
-  double inv_h[3];
+  // FP64 plan
+  double box[3], inv_box[3], cw[3], inv_cw[3], h[3], inv_h[3];
+  // mixed plan: c = c_hi + c_lo with k * c_hi exact for every index k in use
+  float cw_hi[3], cw_lo[3], cwf[3], inv_cwf[3];
+  float h_hi[3], h_lo[3], hf[3], inv_hf[3];
+  long long box_bits[3];  // bit pattern of L as a double (inside test for FP64 inputs)
+  int box_bits32[3];      // ... of float(L) (FP32 inputs)
   int nc[3];
   int fmax[3];  // open grids: largest floor(x/h) the level-0 grid covers
   int periodic;
   int S;
 };
 
-__global__ void k_keys(const double* __restrict__ pos, const double* __restrict__ q, int n,
-                       BinArgs A, int* __restrict__ keys, int* __restrict__ idx,
-                       int* __restrict__ status) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double x[3] = {pos[3 * (size_t)i], pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2]};
-  int bad = 0;
-  if (!isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2]) || !isfinite(q[i])) bad |= kStatusNonfinite;
-  int c[3];
-  for (int d = 0; d < 3; ++d) {
-    double v = x[d];
-    if (A.periodic) {
-      v = isfinite(v) ? fold(v, A.box[d], A.inv_box[d]) : 0.0;
-    } else if (!(v >= 0.0 && v <= A.box[d])) {
-      bad |= kStatusOutside;
-      v = 0.0;
+// Splits a finite y >= 0 into hi + lo with integer operations only: hi keeps
+// the leading 24 significant bits (truncated), lo the next 29 (so hi + lo
+// equals y to 2^-48 relative).  y < 2^-126 maps to 0.
+__device__ __forceinline__ void split_nonneg(double y, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(y);
+  const int e = (int)(b >> 52);  // biased exponent (the sign bit is 0)
+  if (e < 897) {
+    hi = 0.f;
+    lo = 0.f;
+    return;
+  }
+  hi = __int_as_float(((e - 896) << 23) | (int)((unsigned)(b >> 29) & 0x7fffffu));
+  const unsigned ml = (unsigned)b & 0x1fffffffu;
+  lo = (e >= 949) ? __fmul_rn(__uint2float_rn(ml), __int_as_float((e - 948) << 23)) : 0.f;
+}
+__device__ __forceinline__ void split_nonneg(float y, float& hi, float& lo) {
+  hi = (y > 0.f) ? y : 0.f;  // -0 -> 0
+  lo = 0.f;
+}
+
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned long long)__double_as_longlong(x) >> 52 & 0x7ff) != 0x7ff;
+}
+__device__ __forceinline__ bool finite_bits(float x) { return ((unsigned)__float_as_int(x) >> 23 & 0xff) != 0xff; }
+
+// 0 <= x < L (periodic, strict) or 0 <= x <= L (open), decided on the bit
+// pattern: non-negative IEEE values order like their bit patterns.  A false
+// "outside" for x == float(L) < L only sends the atom through the fold.
+__device__ __forceinline__ bool inside_bits(double x, const BinArgs& A, int d, bool closed) {
+  long long b = __double_as_longlong(x);
+  if (b == (long long)0x8000000000000000ull) b = 0;  // -0
+  return b >= 0 && (closed ? b <= A.box_bits[d] : b < A.box_bits[d]);
+}
+__device__ __forceinline__ bool inside_bits(float x, const BinArgs& A, int d, bool closed) {
+  int b = __float_as_int(x);
+  if (b == (int)0x80000000u) b = 0;
+  return b >= 0 && (closed ? b <= A.box_bits32[d] : b < A.box_bits32[d]);
+}
+
+// x - k * c for x = hi + lo, c = c_hi + c_lo: k * c_hi is exact and so is
+// hi - k * c_hi (Sterbenz), so the result is rounded once.
+__device__ __forceinline__ float offset_from(float hi, float lo, int k, float c_hi, float c_lo) {
+  const float kf = (float)k;
+  return __fadd_rn(__fsub_rn(hi, __fmul_rn(kf, c_hi)), __fsub_rn(lo, __fmul_rn(kf, c_lo)));
+}
+
+// One coordinate on the mixed plan: the folded coordinate as hi + lo
+// (status bits to `bad`), its cell index, and its level-0 floor index and
+// fraction.  Every step uses explicitly rounded intrinsics, so the count and
+// scatter kernels reach the same decisions.
+template <typename IO>
+__device__ __forceinline__ void prep_mixed(IO x, const BinArgs& A, int d, int& bad, float& hi, float& lo) {
+  if (!finite_bits(x)) {
+    bad |= kStatusNonfinite;
+    hi = lo = 0.f;
+  } else if (inside_bits(x, A, d, !A.periodic)) {
+    split_nonneg(x, hi, lo);
+  } else if (A.periodic) {
+    split_nonneg(fold((double)x, A.box[d], A.inv_box[d]), hi, lo);
+  } else {
+    bad |= kStatusOutside;
+    hi = lo = 0.f;
+  }
+}
+
+__device__ __forceinline__ int cell_mixed(float hi, float lo, const BinArgs& A, int d) {
+  const int nc = A.nc[d];
+  int k = min((int)__fmul_rz(hi, A.inv_cwf[d]), nc - 1);
+  const float loc = offset_from(hi, lo, k, A.cw_hi[d], A.cw_lo[d]);
+  if (loc < 0.f && k > 0) --k;
+  else if (loc >= A.cwf[d] && k < nc - 1) ++k;
+  return k;
+}
+
+__device__ __forceinline__ void grid_mixed(float hi, float lo, const BinArgs& A, int d, int& b, float& fr) {
+  b = (int)__fmul_rz(hi, A.inv_hf[d]);
+  if (!A.periodic) b = min(b, A.fmax[d]);
+  float dist = offset_from(hi, lo, b, A.h_hi[d], A.h_lo[d]);
+  if (dist < 0.f && b > 0) {
+    --b;
+    dist = offset_from(hi, lo, b, A.h_hi[d], A.h_lo[d]);
+  } else if (dist >= A.hf[d] && (A.periodic || b < A.fmax[d])) {
+    ++b;
+    dist = offset_from(hi, lo, b, A.h_hi[d], A.h_lo[d]);
+  }
+  fr = __fmul_rn(dist, A.inv_hf[d]);
+}
+
+// The same on the FP64 plan (FP64 arithmetic throughout).
+template <typename IO>
+__device__ __forceinline__ double prep_fp64(IO xin, const BinArgs& A, int d, int& bad) {
+  const double v = (double)xin;
+  if (!finite_bits(xin)) {
+    bad |= kStatusNonfinite;
+    return 0.0;
+  }
+  if (A.periodic) return fold(v, A.box[d], A.inv_box[d]);
+  if (!(v >= 0.0 && v <= A.box[d])) {
+    bad |= kStatusOutside;
+    return 0.0;
+  }
+  return v;
+}
+
+__device__ __forceinline__ int cell_fp64(double v, const BinArgs& A, int d) {
+  const int ci = (int)floor(__dmul_rn(v, A.inv_cw[d]));
+  return ci < 0 ? 0 : (ci >= A.nc[d] ? A.nc[d] - 1 : ci);
+}
+
+__device__ __forceinline__ void grid_fp64(double v, const BinArgs& A, int d, int& b, double& fr) {
+  const double t = v * A.inv_h[d];
+  double fl = floor(t);
+  if (!A.periodic && fl > (double)A.fmax[d]) fl = (double)A.fmax[d];  // x = L rounding up
+  b = (int)fl;
+  fr = t - fl;
+}
+
+template <typename IO, bool FP64>
+__global__ void __launch_bounds__(256) k_bin_count(const IO* __restrict__ pos, const IO* __restrict__ q, int n,
+                                                   BinArgs A, int* __restrict__ count, int* __restrict__ key_out,
+                                                   int* __restrict__ rank_out, int* __restrict__ status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool valid = i < n;
+  int key = -1, bad = 0;
+  if (valid) {
+    int c[3];
+    for (int d = 0; d < 3; ++d) {
+      const IO x = pos[3 * (size_t)i + d];
+      if (FP64) {
+        c[d] = cell_fp64(prep_fp64(x, A, d, bad), A, d);
+      } else {
+        float hi, lo;
+        prep_mixed(x, A, d, bad, hi, lo);
+        c[d] = cell_mixed(hi, lo, A, d);
+      }
     }
-    int ci = (int)floor(v * A.inv_cw[d]);
-    c[d] = ci < 0 ? 0 : (ci >= A.nc[d] ? A.nc[d] - 1 : ci);
+    if (!finite_bits(q[i])) bad |= kStatusNonfinite;
+    key = (c[2] * A.nc[1] + c[1]) * A.nc[0] + c[0];
   }
   if (bad) atomicOr(status, bad);
-  keys[i] = (c[2] * A.nc[1] + c[1]) * A.nc[0] + c[0];
-  idx[i] = i;
+  // one atomic per distinct cell in the warp
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (valid && lane == leader) base = atomicAdd(&count[key], __popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (valid) {
+    key_out[i] = key;
+    rank_out[i] = base + __popc(peers & ((1u << lane) - 1u));
+  }
 }
 
-__global__ void __launch_bounds__(kThreads) k_hist(const int* __restrict__ keys, int n, int shift,
-                                                   int* __restrict__ hist, int nblk) {
-  __shared__ int h[256];
-  int t = threadIdx.x, b = blockIdx.x;
-  h[t] = 0;
+template <int NT>
+__device__ __forceinline__ int block_reduce_sum(int v, int* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
   __syncthreads();
-  int end = min(n, (b + 1) * kChunk);
-  for (int i = b * kChunk + t; i < end; i += kThreads) atomicAdd(&h[(keys[i] >> shift) & 255], 1);
+  v = (lane < NT / 32) ? red[lane] : 0;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
-  hist[t * nblk + b] = h[t];
+  return v;
 }
 
-// Exclusive scan of `total` ints in place, one block of 1024 threads walking
-// the array in coalesced tiles of 1024 (warp-shuffle scan inside a tile, a
-// running carry between tiles).
-__global__ void __launch_bounds__(1024) k_scan(int* __restrict__ data, int total) {
-  __shared__ int wsum[32];
-  __shared__ int carry_s;
+__global__ void __launch_bounds__(1024) k_cell_sums(const int* __restrict__ count, int ncell, int* __restrict__ sums) {
+  __shared__ int red[32];
+  const int c0 = blockIdx.x * kScanChunk + 4 * threadIdx.x;
+  int v = 0;
+  for (int t = 0; t < 4; ++t) v += (c0 + t < ncell) ? count[c0 + t] : 0;
+  v = block_reduce_sum<1024>(v, red);
+  if (threadIdx.x == 0) sums[blockIdx.x] = v;
+}
+
+// cell_start[c] = sum of count[0..c); count[c] = 0 afterwards.
+__global__ void __launch_bounds__(1024) k_cell_scan(int* __restrict__ count, int ncell,
+                                                    const int* __restrict__ sums, int* __restrict__ cell_start) {
+  __shared__ int red[32], wsum[32];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  if (t == 0) carry_s = 0;
+  // this block's offset: the sums of the chunks before it
+  int pre = 0;
+  for (int b = t; b < (int)blockIdx.x; b += 1024) pre += sums[b];
+  pre = block_reduce_sum<1024>(pre, red);
+  const int c0 = blockIdx.x * kScanChunk + 4 * t;
+  int v[4], tot = 0;
+  for (int k = 0; k < 4; ++k) {
+    v[k] = (c0 + k < ncell) ? count[c0 + k] : 0;
+    tot += v[k];
+  }
+  int x = tot;  // inclusive warp scan of the thread totals
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
   __syncthreads();
-  for (int base = 0; base < total; base += 1024) {
-    const int i = base + t;
-    const int v = (i < total) ? data[i] : 0;
-    int x = v;  // inclusive warp scan
-#pragma unroll
+  if (warp == 0) {
+    int w = wsum[lane];
     for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
     }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      int w = wsum[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
-      }
-      wsum[lane] = w;  // inclusive over warps
-    }
-    __syncthreads();
-    const int carry = carry_s;
-    const int excl = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - v;
-    if (i < total) data[i] = excl;
-    __syncthreads();
-    if (t == 1023) carry_s = excl + v;
-    __syncthreads();
+    wsum[lane] = w;
   }
+  __syncthreads();
+  int run = pre + (warp > 0 ? wsum[warp - 1] : 0) + x - tot;
+  for (int k = 0; k < 4; ++k) {
+    const int c = c0 + k;
+    if (c < ncell) {
+      cell_start[c] = run;
+      count[c] = 0;
+    }
+    run += v[k];
+  }
+  if (c0 <= ncell - 1 && ncell - 1 < c0 + 4) cell_start[ncell] = run;  // end marker, by the last cell's thread
 }
 
-// Stable scatter: inside a block, items are ranked in index order (warp
-// match for ranks inside a warp, a per-digit prefix over the warps), on top of
-// the block's scanned digit offset.
-__global__ void __launch_bounds__(kThreads) k_scatter(const int* __restrict__ kin,
-                                                      const int* __restrict__ iin,
-                                                      int* __restrict__ kout, int* __restrict__ iout,
-                                                      const int* __restrict__ hist, int n, int shift,
-                                                      int nblk) {
-  __shared__ int s_off[256];
-  __shared__ int s_w[kThreads / 32][256];
-  int t = threadIdx.x, lane = t & 31, warp = t >> 5, b = blockIdx.x;
-  s_off[t] = hist[t * nblk + b];
-  int base = b * kChunk;
-  for (int sub = 0; sub < kChunk && base + sub < n; sub += kThreads) {
-    for (int e = t; e < (kThreads / 32) * 256; e += kThreads) (&s_w[0][0])[e] = 0;
-    __syncthreads();
-    int i = base + sub + t;
-    bool valid = i < n;
-    int key = valid ? kin[i] : 0;
-    int digit = valid ? ((key >> shift) & 255) : 256;
-    unsigned peers = __match_any_sync(0xffffffffu, digit);
-    int rank = __popc(peers & ((1u << lane) - 1u));
-    if (valid && lane == __ffs(peers) - 1) s_w[warp][digit] = __popc(peers);
-    __syncthreads();
-    {
-      int run = s_off[t];
-      for (int w = 0; w < kThreads / 32; ++w) {
-        int c = s_w[w][t];
-        s_w[w][t] = run;
-        run += c;
-      }
-      s_off[t] = run;
+template <typename IO, bool FP64>
+__global__ void __launch_bounds__(256) k_bin_scatter(const IO* __restrict__ pos, const IO* __restrict__ q, int n,
+                                                     BinArgs A, const int* __restrict__ key_in,
+                                                     const int* __restrict__ rank_in,
+                                                     const int* __restrict__ cell_start, void* __restrict__ atoms_v,
+                                                     void* __restrict__ gfrac_v, int4* __restrict__ gbase,
+                                                     int* __restrict__ perm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int key = key_in[i];
+  const int s = cell_start[key] + rank_in[i];
+  const int kc[3] = {key % A.nc[0], (key / A.nc[0]) % A.nc[1], key / (A.nc[0] * A.nc[1])};
+  int bad = 0, bs[3];
+  if (FP64) {
+    double loc[3], fr[3];
+    for (int d = 0; d < 3; ++d) {
+      const double v = prep_fp64(pos[3 * (size_t)i + d], A, d, bad);
+      loc[d] = v - kc[d] * A.cw[d];
+      grid_fp64(v, A, d, bs[d], fr[d]);
     }
-    __syncthreads();
-    if (valid) {
-      int p = s_w[warp][digit] + rank;
-      kout[p] = key;
-      iout[p] = iin[i];
+    const double qi = finite_bits(q[i]) ? (double)q[i] : 0.0;
+    reinterpret_cast<R4<double>*>(atoms_v)[s] = R4<double>{loc[0], loc[1], loc[2], qi};
+    reinterpret_cast<R4<double>*>(gfrac_v)[s] = R4<double>{fr[0], fr[1], fr[2], qi};
+  } else {
+    float loc[3], fr[3];
+    for (int d = 0; d < 3; ++d) {
+      float hi, lo;
+      prep_mixed(pos[3 * (size_t)i + d], A, d, bad, hi, lo);
+      loc[d] = offset_from(hi, lo, kc[d], A.cw_hi[d], A.cw_lo[d]);
+      grid_mixed(hi, lo, A, d, bs[d], fr[d]);
     }
-    __syncthreads();
+    const float qi = finite_bits(q[i]) ? (float)q[i] : 0.f;
+    reinterpret_cast<R4<float>*>(atoms_v)[s] = R4<float>{loc[0], loc[1], loc[2], qi};
+    reinterpret_cast<R4<float>*>(gfrac_v)[s] = R4<float>{fr[0], fr[1], fr[2], qi};
   }
+  gbase[s] = make_int4(bs[0] - (A.S - 1), bs[1] - (A.S - 1), bs[2] - (A.S - 1), 0);
+  perm[s] = i;
 }
 
-__global__ void k_cell_start(const int* __restrict__ keys, int n, int ncell, int* __restrict__ cs) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c > ncell) return;
-  int lo = 0, hi = n;  // first position with key >= c
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (keys[mid] < c) lo = mid + 1;
-    else hi = mid;
-  }
-  cs[c] = lo;
+// Veltkamp-style split c = hi + lo with hi holding `hb` significant bits.
+void split_const(double c, int hb, float& hi, float& lo) {
+  int ex = 0;
+  const double f = std::frexp(c, &ex);  // c = f * 2^ex, f in [0.5, 1)
+  const double h = std::ldexp(std::floor(std::ldexp(f, hb)), ex - hb);
+  hi = (float)h;
+  lo = (float)(c - h);
 }
 
-template <typename T>
-__global__ void k_gather(const double* __restrict__ pos, const double* __restrict__ q, int n,
-                         BinArgs A, const int* __restrict__ keys, const int* __restrict__ idx,
-                         R4<T>* __restrict__ atoms, R4<T>* __restrict__ gfrac,
-                         int4* __restrict__ gbase) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  int i = idx[s], key = keys[s];
-  int c[3] = {key % A.nc[0], (key / A.nc[0]) % A.nc[1], key / (A.nc[0] * A.nc[1])};
-  double qi = q[i];
-  T loc[3], fr[3];
-  int bs[3];
-  for (int d = 0; d < 3; ++d) {
-    double v = pos[3 * (size_t)i + d];
-    if (A.periodic) v = isfinite(v) ? fold(v, A.box[d], A.inv_box[d]) : 0.0;
-    else v = fmin(fmax(v, 0.0), A.box[d]);
-    loc[d] = (T)(v - c[d] * A.cw[d]);
-    double t = v * A.inv_h[d];
-    double fl = floor(t);
-    if (!A.periodic && fl > (double)A.fmax[d]) fl = (double)A.fmax[d];  // x = L rounding up
-    fr[d] = (T)(t - fl);
-    bs[d] = (int)fl - (A.S - 1);
-  }
-  atoms[s] = R4<T>{loc[0], loc[1], loc[2], (T)qi};
-  gfrac[s] = R4<T>{fr[0], fr[1], fr[2], (T)qi};
-  gbase[s] = make_int4(bs[0], bs[1], bs[2], 0);
+int bits_for(int kmax) {
+  int b = 1;
+  while ((1 << b) <= kmax) ++b;
+  return b;
 }
 
 }  // namespace
 
-cudaError_t launch_binning(Plan& P, int64_t n64, const double* pos, const double* q, cudaStream_t st) {
-  int n = (int)n64;
+template <typename IO>
+cudaError_t launch_binning(Plan& P, int64_t n64, const IO* pos, const IO* q, cudaStream_t st) {
+  const int n = (int)n64;
   DeviceBuffers& D = P.d;
   BinArgs A;
   for (int d = 0; d < 3; ++d) {
-    A.box[d] = P.P.box[d];
-    A.inv_box[d] = 1.0 / P.P.box[d];
+    const double L = P.P.box[d];
+    A.box[d] = L;
+    A.inv_box[d] = 1.0 / L;
     A.cw[d] = P.cw[d];
     A.inv_cw[d] = 1.0 / P.cw[d];
+    A.h[d] = P.h[d];
     A.inv_h[d] = 1.0 / P.h[d];
     A.nc[d] = P.nc[d];
     A.fmax[d] = P.n[0][d] - 2 * P.S;
+    // leading parts short enough that index * leading part is exact in FP32
+    split_const(P.cw[d], 24 - bits_for(P.nc[d] + 1), A.cw_hi[d], A.cw_lo[d]);
+    split_const(P.h[d], 24 - bits_for(P.n[0][d] + 2), A.h_hi[d], A.h_lo[d]);
+    A.cwf[d] = (float)P.cw[d];
+    A.inv_cwf[d] = (float)(1.0 / P.cw[d]);
+    A.hf[d] = (float)P.h[d];
+    A.inv_hf[d] = (float)(1.0 / P.h[d]);
+    double Ld = L;
+    float Lf = (float)L;
+    std::memcpy(&A.box_bits[d], &Ld, 8);
+    std::memcpy(&A.box_bits32[d], &Lf, 4);
   }
   A.periodic = P.P.periodic;
   A.S = P.S;
-  if (n > 0) {
-    k_keys<<<(n + 255) / 256, 256, 0, st>>>(pos, q, n, A, D.keys[0], D.idx[0], D.status);
-    int nblk = (n + kChunk - 1) / kChunk;
-    int cur = 0;
-    for (int pass = 0; pass < P.key_passes; ++pass) {
-      int shift = 8 * pass;
-      k_hist<<<nblk, kThreads, 0, st>>>(D.keys[cur], n, shift, D.hist, nblk);
-      k_scan<<<1, 1024, 0, st>>>(D.hist, 256 * nblk);
-      k_scatter<<<nblk, kThreads, 0, st>>>(D.keys[cur], D.idx[cur], D.keys[cur ^ 1], D.idx[cur ^ 1],
-                                           D.hist, n, shift, nblk);
-      cur ^= 1;
-    }
-    P.launches += 1 + 3 * P.key_passes;
-    if (cur != 0) {  // keep the sorted result in slot 0
-      P.launches += 2;
-      cudaMemcpyAsync(D.keys[0], D.keys[1], sizeof(int) * n, cudaMemcpyDeviceToDevice, st);
-      cudaMemcpyAsync(D.idx[0], D.idx[1], sizeof(int) * n, cudaMemcpyDeviceToDevice, st);
-    }
-  }
-  k_cell_start<<<(P.ncell + 1 + 255) / 256, 256, 0, st>>>(D.keys[0], n, P.ncell, D.cell_start);
-  P.launches += 1 + (n > 0 ? 1 : 0);
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  const unsigned nsc = (unsigned)((P.ncell + kScanChunk - 1) / kScanChunk);
   if (n > 0) {
     if (P.fp64)
-      k_gather<double><<<(n + 255) / 256, 256, 0, st>>>(pos, q, n, A, D.keys[0], D.idx[0],
-                                                        (R4<double>*)D.atoms, (R4<double>*)D.gfrac,
-                                                        D.gbase);
+      k_bin_count<IO, true><<<nb, 256, 0, st>>>(pos, q, n, A, D.count, D.key, D.rank, D.status);
     else
-      k_gather<float><<<(n + 255) / 256, 256, 0, st>>>(pos, q, n, A, D.keys[0], D.idx[0],
-                                                       (R4<float>*)D.atoms, (R4<float>*)D.gfrac,
-                                                       D.gbase);
+      k_bin_count<IO, false><<<nb, 256, 0, st>>>(pos, q, n, A, D.count, D.key, D.rank, D.status);
   }
+  k_cell_sums<<<nsc, 1024, 0, st>>>(D.count, P.ncell, D.csum);
+  k_cell_scan<<<nsc, 1024, 0, st>>>(D.count, P.ncell, D.csum, D.cell_start);
+  if (n > 0) {
+    if (P.fp64)
+      k_bin_scatter<IO, true><<<nb, 256, 0, st>>>(pos, q, n, A, D.key, D.rank, D.cell_start, D.atoms, D.gfrac,
+                                                  D.gbase, D.perm);
+    else
+      k_bin_scatter<IO, false><<<nb, 256, 0, st>>>(pos, q, n, A, D.key, D.rank, D.cell_start, D.atoms, D.gfrac,
+                                                   D.gbase, D.perm);
+  }
+  P.launches += 2 + (n > 0 ? 2 : 0);
   return cudaGetLastError();
 }
+
+template cudaError_t launch_binning<double>(Plan&, int64_t, const double*, const double*, cudaStream_t);
+template cudaError_t launch_binning<float>(Plan&, int64_t, const float*, const float*, cudaStream_t);
 
 }  // namespace msm

@@ -645,6 +645,67 @@ struct AssembleArgs {
   double self_c;  // gamma(0)/a
   double kc;      // Coulomb prefactor
   double inv_h[3];
+  float self_cf, kcf;  // the same in FP32 (mixed plans assemble in FP32)
+};
+
+// Per-atom assembly of phi_i, F_i (forward) and of dL/dq_i, dL/dr_i
+// (adjoint).  The mixed plan works in FP32 and converts once per output (FP64
+// operations, conversions included, issue at 1/64 of the FP32 rate here); the
+// FP64 plan works in FP64.
+template <typename T>
+struct Assemble;
+template <>
+struct Assemble<float> {
+  template <typename OUT>
+  __device__ static double forward(const AssembleArgs& A, float q, float phis, float p, const R4<float>& s,
+                                   const float g[3], int o, OUT* phi_out, OUT* force_out) {
+    const float phi = A.kcf * ((phis + p) - q * A.self_cf);
+    if (phi_out) phi_out[o] = (OUT)phi;
+    if (force_out) {
+      force_out[3 * (size_t)o + 0] = (OUT)(A.kcf * (s.x - q * g[0]));
+      force_out[3 * (size_t)o + 1] = (OUT)(A.kcf * (s.y - q * g[1]));
+      force_out[3 * (size_t)o + 2] = (OUT)(A.kcf * (s.z - q * g[2]));
+    }
+    return (double)(q * phi);
+  }
+  template <typename OUT>
+  __device__ static void backward(const AssembleArgs& A, float gg, float q, float phis, const R4<float>& s,
+                                  const R4<float>& gl, float v, const float gv[3], int o, OUT* grad_pos,
+                                  OUT* grad_q) {
+    const float hg = 0.5f * gg;
+    if (grad_q) grad_q[o] = (OUT)(A.kcf * (gg * (phis - q * A.self_cf) + hg * s.w + v));
+    if (grad_pos) {
+      grad_pos[3 * (size_t)o + 0] = (OUT)(A.kcf * (-gg * s.x + hg * q * gl.x + q * gv[0]));
+      grad_pos[3 * (size_t)o + 1] = (OUT)(A.kcf * (-gg * s.y + hg * q * gl.y + q * gv[1]));
+      grad_pos[3 * (size_t)o + 2] = (OUT)(A.kcf * (-gg * s.z + hg * q * gl.z + q * gv[2]));
+    }
+  }
+};
+template <>
+struct Assemble<double> {
+  template <typename OUT>
+  __device__ static double forward(const AssembleArgs& A, double q, double phis, double p, const R4<double>& s,
+                                   const double g[3], int o, OUT* phi_out, OUT* force_out) {
+    const double phi = A.kc * (phis + p - q * A.self_c);
+    if (phi_out) phi_out[o] = (OUT)phi;
+    if (force_out) {
+      force_out[3 * (size_t)o + 0] = (OUT)(A.kc * (s.x - q * g[0]));
+      force_out[3 * (size_t)o + 1] = (OUT)(A.kc * (s.y - q * g[1]));
+      force_out[3 * (size_t)o + 2] = (OUT)(A.kc * (s.z - q * g[2]));
+    }
+    return q * phi;
+  }
+  template <typename OUT>
+  __device__ static void backward(const AssembleArgs& A, double gg, double q, double phis, const R4<double>& s,
+                                  const R4<double>& gl, double v, const double gv[3], int o, OUT* grad_pos,
+                                  OUT* grad_q) {
+    if (grad_q) grad_q[o] = (OUT)(A.kc * (gg * (phis - q * A.self_c) + 0.5 * gg * s.w + v));
+    if (grad_pos) {
+      grad_pos[3 * (size_t)o + 0] = (OUT)(A.kc * (-gg * s.x + 0.5 * gg * q * gl.x + q * gv[0]));
+      grad_pos[3 * (size_t)o + 1] = (OUT)(A.kc * (-gg * s.y + 0.5 * gg * q * gl.y + q * gv[1]));
+      grad_pos[3 * (size_t)o + 2] = (OUT)(A.kc * (-gg * s.z + 0.5 * gg * q * gl.z + q * gv[2]));
+    }
+  }
 };
 
 // Interpolation through the same per-block patches: a block stages the u^0
@@ -721,12 +782,12 @@ __device__ __forceinline__ int stage_interp_block(const AnterpArgs& A, const int
   return build_rank_list(*nk_s, cstart, ccount, list, tot_s);
 }
 
-template <typename T, int ORDER>
+template <typename T, int ORDER, typename OUT>
 __global__ void __launch_bounds__(256) k_interp_fwd(
     const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm,
     const int* __restrict__ cell_start, AnterpArgs AA, const T* __restrict__ u0, GridDims G, AssembleArgs A,
-    const T* __restrict__ phis, R4<T>* __restrict__ fs, R4<T>* __restrict__ glong, double* __restrict__ phi_out,
-    double* __restrict__ force_out, double* __restrict__ partial) {
+    const T* __restrict__ phis, R4<T>* __restrict__ fs, R4<T>* __restrict__ glong, OUT* __restrict__ phi_out,
+    OUT* __restrict__ force_out, double* __restrict__ partial) {
   constexpr int S = Basis<T, ORDER>::S;
   extern __shared__ unsigned char smem_raw[];
   T* patch = reinterpret_cast<T*>(smem_raw);
@@ -758,19 +819,10 @@ __global__ void __launch_bounds__(256) k_interp_fwd(
     T p, g[3];
     interp_patch_atom<T, ORDER>(f, gbase[i], patch, AA.pd, lo0, lo1, lo2, u0, G, ih, p, g);
     R4<T> s = fs[i];
-    const double qi = (double)f.w;
-    const double phi = A.kc * ((double)phis[i] + (double)p - qi * A.self_c);
-    const int o = perm[i];
-    if (phi_out) phi_out[o] = phi;
-    if (force_out) {
-      force_out[3 * (size_t)o + 0] = A.kc * ((double)s.x - qi * (double)g[0]);
-      force_out[3 * (size_t)o + 1] = A.kc * ((double)s.y - qi * (double)g[1]);
-      force_out[3 * (size_t)o + 2] = A.kc * ((double)s.z - qi * (double)g[2]);
-    }
+    e += Assemble<T>::forward(A, f.w, phis[i], p, s, g, perm[i], phi_out, force_out);
     s.w = p;
     fs[i] = s;
     glong[i] = R4<T>{g[0], g[1], g[2], T(0)};
-    e += qi * phi;
   }
   double bsum = block_sum<256>(e);
   if (threadIdx.x == 0) partial[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = bsum;
@@ -785,12 +837,12 @@ __global__ void __launch_bounds__(1024) k_energy_final(const double* __restrict_
 }
 
 // adjoint assembly: av0 = M (anterpolated 1/2 gE q) on the grid
-template <typename T, int ORDER>
+template <typename T, int ORDER, typename OUT>
 __global__ void __launch_bounds__(256) k_interp_bwd(
     const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm,
     const int* __restrict__ cell_start, AnterpArgs AA, const T* __restrict__ av0, GridDims G, AssembleArgs A,
     const T* __restrict__ phis, const R4<T>* __restrict__ fs, const R4<T>* __restrict__ glong,
-    const double* __restrict__ gE, double* __restrict__ grad_pos, double* __restrict__ grad_q) {
+    const double* __restrict__ gE, OUT* __restrict__ grad_pos, OUT* __restrict__ grad_q) {
   constexpr int S = Basis<T, ORDER>::S;
   extern __shared__ unsigned char smem_raw[];
   T* patch = reinterpret_cast<T*>(smem_raw);
@@ -802,7 +854,7 @@ __global__ void __launch_bounds__(256) k_interp_bwd(
   const int total = stage_interp_block<T>(AA, cell_start, av0, G, patch, lo0, lo1, lo2, cstart, ccount, list, &nk_s,
                                           &tot_s);
   const T ih[3] = {T(A.inv_h[0]), T(A.inv_h[1]), T(A.inv_h[2])};
-  const double gg = *gE;
+  const T gg = (T)*gE;
   const int nk = nk_s, nlist = total >= 0 ? total : 0;
   int walk_c = 0, walk_m = threadIdx.x;
   for (int kk = threadIdx.x;; kk += blockDim.x) {
@@ -819,17 +871,7 @@ __global__ void __launch_bounds__(256) k_interp_bwd(
     const R4<T> f = gfrac[i];
     T v, gv[3];
     interp_patch_atom<T, ORDER>(f, gbase[i], patch, AA.pd, lo0, lo1, lo2, av0, G, ih, v, gv);
-    const R4<T> s = fs[i];
-    const R4<T> gl = glong[i];
-    const double qi = (double)f.w;
-    const int o = perm[i];
-    if (grad_q)
-      grad_q[o] = A.kc * (gg * ((double)phis[i] - qi * A.self_c) + 0.5 * gg * (double)s.w + (double)v);
-    if (grad_pos) {
-      grad_pos[3 * (size_t)o + 0] = A.kc * (-gg * (double)s.x + 0.5 * gg * qi * (double)gl.x + qi * (double)gv[0]);
-      grad_pos[3 * (size_t)o + 1] = A.kc * (-gg * (double)s.y + 0.5 * gg * qi * (double)gl.y + qi * (double)gv[1]);
-      grad_pos[3 * (size_t)o + 2] = A.kc * (-gg * (double)s.z + 0.5 * gg * qi * (double)gl.z + qi * (double)gv[2]);
-    }
+    Assemble<T>::backward(A, gg, f.w, phis[i], fs[i], glong[i], v, gv, perm[i], grad_pos, grad_q);
   }
 }
 
@@ -854,6 +896,8 @@ AssembleArgs assemble_args(const Plan& P) {
   A.self_c = P.gamma0 / P.P.cutoff;
   A.kc = P.P.coulomb_k;
   for (int d = 0; d < 3; ++d) A.inv_h[d] = 1.0 / P.h[d];
+  A.self_cf = (float)A.self_c;
+  A.kcf = (float)A.kc;
   return A;
 }
 
@@ -1026,8 +1070,8 @@ AnterpArgs patch_args(const Plan& P) {
   return A;
 }
 
-cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, double* phi, double* force,
-                                  cudaStream_t st) {
+template <typename OUT>
+cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, OUT* phi, OUT* force, cudaStream_t st) {
   GridDims G = dims_of(P, 0);
   AssembleArgs A = assemble_args(P);
   AnterpArgs AA = patch_args(P);
@@ -1037,7 +1081,7 @@ cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, double* ph
     size_t sm = (P.fp64 ? 8 : 4) * (size_t)AA.pd * AA.pd * AA.pd;
 #define MSM_FWD(T, O)                                                                                            \
   {                                                                                                              \
-    k_interp_fwd<T, O><<<grid, 256, sm, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.idx[0], P.d.cell_start, AA, \
+    k_interp_fwd<T, O, OUT><<<grid, 256, sm, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.perm, P.d.cell_start, AA, \
                                               (const T*)P.d.gu[0], G, A, (const T*)P.d.phis, (R4<T>*)P.d.fs,    \
                                               (R4<T>*)P.d.glong, phi, force, P.d.partial);                      \
   }
@@ -1053,7 +1097,8 @@ cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, double* ph
   return cudaGetLastError();
 }
 
-cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, double* grad_pos, double* grad_q,
+template <typename OUT>
+cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, OUT* grad_pos, OUT* grad_q,
                                    cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   GridDims G = dims_of(P, 0);
@@ -1064,7 +1109,7 @@ cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, double*
   P.launches += 1;
 #define MSM_BWD(T, O)                                                                                             \
   {                                                                                                               \
-    k_interp_bwd<T, O><<<grid, 256, sm, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.idx[0], P.d.cell_start, AA,  \
+    k_interp_bwd<T, O, OUT><<<grid, 256, sm, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.perm, P.d.cell_start, AA,  \
                                               (const T*)P.d.au[0], G, A, (const T*)P.d.phis,                     \
                                               (const R4<T>*)P.d.fs, (const R4<T>*)P.d.glong, gE, grad_pos, grad_q); \
   }
@@ -1090,16 +1135,29 @@ cudaError_t configure_kernels() {
   set((const void*)k_anterp_patch<float, float, 5>);
   set((const void*)k_anterp_patch<double, double, 3>);
   set((const void*)k_anterp_patch<double, double, 5>);
-  set((const void*)k_interp_fwd<float, 3>);
-  set((const void*)k_interp_fwd<float, 5>);
-  set((const void*)k_interp_fwd<double, 3>);
-  set((const void*)k_interp_fwd<double, 5>);
-  set((const void*)k_interp_bwd<float, 3>);
-  set((const void*)k_interp_bwd<float, 5>);
-  set((const void*)k_interp_bwd<double, 3>);
-  set((const void*)k_interp_bwd<double, 5>);
+  set((const void*)k_interp_fwd<float, 3, double>);
+  set((const void*)k_interp_fwd<float, 3, float>);
+  set((const void*)k_interp_fwd<float, 5, double>);
+  set((const void*)k_interp_fwd<float, 5, float>);
+  set((const void*)k_interp_fwd<double, 3, double>);
+  set((const void*)k_interp_fwd<double, 3, float>);
+  set((const void*)k_interp_fwd<double, 5, double>);
+  set((const void*)k_interp_fwd<double, 5, float>);
+  set((const void*)k_interp_bwd<float, 3, double>);
+  set((const void*)k_interp_bwd<float, 3, float>);
+  set((const void*)k_interp_bwd<float, 5, double>);
+  set((const void*)k_interp_bwd<float, 5, float>);
+  set((const void*)k_interp_bwd<double, 3, double>);
+  set((const void*)k_interp_bwd<double, 3, float>);
+  set((const void*)k_interp_bwd<double, 5, double>);
+  set((const void*)k_interp_bwd<double, 5, float>);
   return e;
 }
+
+template cudaError_t launch_interp_forward<double>(Plan&, int64_t, double*, double*, double*, cudaStream_t);
+template cudaError_t launch_interp_forward<float>(Plan&, int64_t, double*, float*, float*, cudaStream_t);
+template cudaError_t launch_interp_backward<double>(Plan&, int64_t, const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_interp_backward<float>(Plan&, int64_t, const double*, float*, float*, cudaStream_t);
 
 cudaError_t launch_grid_to_double(Plan& P, const void* src, double* dst, int64_t count, bool is_double,
                                   cudaStream_t st) {

@@ -51,12 +51,47 @@ __device__ __forceinline__ void two_sum_add(T& s, T& c, T x) {
   s = t;
 }
 
+// Cutoff constants are precomputed on the host in both precisions: a divide
+// in FP64 on every thread would cost dozens of FP64-pipe operations.
 struct PairArgs {
   int nc[3];
   int periodic;
   int noff;
-  double a;
+  double a2, inv_a, inv_a2, two_inv_a3;
+  float a2f, inv_af, inv_a2f, two_inv_a3f;
 };
+
+template <typename T>
+struct CutoffConsts;
+template <>
+struct CutoffConsts<double> {
+  __device__ static void get(const PairArgs& A, double& a2, double& ia, double& ia2, double& t3) {
+    a2 = A.a2; ia = A.inv_a; ia2 = A.inv_a2; t3 = A.two_inv_a3;
+  }
+};
+template <>
+struct CutoffConsts<float> {
+  __device__ static void get(const PairArgs& A, float& a2, float& ia, float& ia2, float& t3) {
+    a2 = A.a2f; ia = A.inv_af; ia2 = A.inv_a2f; t3 = A.two_inv_a3f;
+  }
+};
+
+PairArgs pair_args(const Plan& P) {
+  PairArgs A;
+  for (int d = 0; d < 3; ++d) A.nc[d] = P.nc[d];
+  A.periodic = P.P.periodic;
+  A.noff = P.noff;
+  const double a = P.P.cutoff;
+  A.a2 = a * a;
+  A.inv_a = 1.0 / a;
+  A.inv_a2 = 1.0 / (a * a);
+  A.two_inv_a3 = 2.0 / (a * a * a);
+  A.a2f = (float)A.a2;
+  A.inv_af = (float)A.inv_a;
+  A.inv_a2f = (float)A.inv_a2;
+  A.two_inv_a3f = (float)A.two_inv_a3;
+  return A;
+}
 
 constexpr int kWarps = 4;
 constexpr int kBatch = 32;       // pairs per lane per batch (one queue drain)
@@ -123,8 +158,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_short_range(
   const int cell = blockIdx.x * kWarps + warp;
   if (cell >= ncell) return;  // warp-uniform
   const int cx = cell % A.nc[0], cy = (cell / A.nc[0]) % A.nc[1], cz = cell / (A.nc[0] * A.nc[1]);
-  const T a2 = T(A.a * A.a), inv_a = T(1.0 / A.a), inv_a2 = T(1.0 / (A.a * A.a));
-  const T two_inv_a3 = T(2.0 / (A.a * A.a * A.a));
+  T a2, inv_a, inv_a2, two_inv_a3;
+  CutoffConsts<T>::get(A, a2, inv_a, inv_a2, two_inv_a3);
   const R4<T> dummy = {far_away<T>(), far_away<T>(), far_away<T>(), T(0)};
   const int i0 = cell_start[cell], i1 = cell_start[cell + 1];
   for (int ib = i0; ib < i1; ib += 32) {
@@ -282,8 +317,7 @@ __device__ __forceinline__ void pair_batch_f2(const QueueF& Q, float2 nax, float
     const float2 rinv = make_float2(fast_rsqrt(r2.x), fast_rsqrt(r2.y));
     const float2 pot = __fadd2_rn(rinv, poly_g<M>(C, r2));   // G holds -gamma coefficients
     sphi = __ffma2_rn(qj, pot, sphi);
-    const float2 rinv3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
-    const float2 fp = __fmul2_rn(__fadd2_rn(rinv3, poly_d<M>(C, r2)), qj);
+    const float2 fp = __fmul2_rn(__ffma2_rn(__fmul2_rn(rinv, rinv), rinv, poly_d<M>(C, r2)), qj);
     sx = __ffma2_rn(fp, dx, sx);
     sy = __ffma2_rn(fp, dy, sy);
     sz = __ffma2_rn(fp, dz, sz);
@@ -313,8 +347,7 @@ __global__ void __launch_bounds__(32 * kWarps, 7) k_short_range_f2(
   if (cell >= ncell) return;  // warp-uniform
   const int ncx = A.nc[0], ncy = A.nc[1], ncz = A.nc[2];
   const int cx = cell % ncx, cy = (cell / ncx) % ncy, cz = cell / (ncx * ncy);
-  const float a2 = (float)(A.a * A.a), inv_a = (float)(1.0 / A.a), inv_a2s = (float)(1.0 / (A.a * A.a));
-  const float two_inv_a3 = (float)(2.0 / (A.a * A.a * A.a));
+  const float a2 = A.a2f, inv_a = A.inv_af, inv_a2s = A.inv_a2f, two_inv_a3 = A.two_inv_a3f;
   const float FAR = 1e6f;
   const int i0 = cell_start[cell], i1 = cell_start[cell + 1];
   for (int ib = i0; ib < i1; ib += 32) {
@@ -450,11 +483,7 @@ __global__ void __launch_bounds__(32 * kWarps, 7) k_short_range_f2(
 
 template <typename T, bool COMP>
 void launch_t(Plan& P, cudaStream_t st) {
-  PairArgs A;
-  for (int d = 0; d < 3; ++d) A.nc[d] = P.nc[d];
-  A.periodic = P.P.periodic;
-  A.noff = P.noff;
-  A.a = P.P.cutoff;
+  PairArgs A = pair_args(P);
   int blocks = (P.ncell + kWarps - 1) / kWarps;
   auto* at = (const R4<T>*)P.d.atoms;
   auto* sh = (const R4<T>*)P.d.cell_shift;
@@ -479,11 +508,7 @@ void launch_t(Plan& P, cudaStream_t st) {
 }  // namespace
 
 void launch_f2(Plan& P, cudaStream_t st) {
-  PairArgs A;
-  for (int d = 0; d < 3; ++d) A.nc[d] = P.nc[d];
-  A.periodic = P.P.periodic;
-  A.noff = P.noff;
-  A.a = P.P.cutoff;
+  PairArgs A = pair_args(P);
   int blocks = (P.ncell + kWarps - 1) / kWarps;
   auto* at = (const R4<float>*)P.d.atoms;
   auto* sh = (const R4<float>*)P.d.cell_shift;

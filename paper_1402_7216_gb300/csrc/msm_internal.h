@@ -42,9 +42,11 @@ struct Segment2 {
 // Per-precision device tables and buffers.
 struct DeviceBuffers {
   // binning / sorting
-  int* keys[2] = {nullptr, nullptr};
-  int* idx[2] = {nullptr, nullptr};
-  int* hist = nullptr;
+  int* key = nullptr;          // [cap]  cell of each atom (input order)
+  int* rank = nullptr;         // [cap]  its place inside the cell
+  int* perm = nullptr;         // [cap]  sorted slot -> input index
+  int* count = nullptr;        // [ncell] atoms per cell (zero between evaluations)
+  int* csum = nullptr;         // [ncell / 4096 + 1] per-chunk sums of count
   int* cell_start = nullptr;   // [ncell + 1]
   // sorted atoms (type T = float or double, selected by precision)
   void* atoms = nullptr;       // R4<T>[cap]: cell-local x, y, z and q
@@ -98,7 +100,6 @@ struct Plan {
   int nc[3];
   double cw[3];
   int ncell = 1;
-  int key_passes = 1;
   int noff = 0;
   int nrows = 0;
   // anterpolation patches: blocks of ablk^3 cells, patches of apd^3 points
@@ -115,7 +116,6 @@ struct Plan {
   int top_table_dims[3];
   // workspace
   int64_t cap = 0;
-  int nblk_hist = 0;
   int nblk_partial = 0;
   DeviceBuffers d;
   // state
@@ -143,7 +143,8 @@ int64_t grid_points(const Plan& P, int k);
 
 // ---- launchers (.cu files); all asynchronous on stream ----
 // binning: keys, stable radix sort by cell, cell_start, gather of sorted atoms
-cudaError_t launch_binning(Plan& P, int64_t n, const double* pos, const double* q, cudaStream_t s);
+template <typename IO>  // IO = double or float (caller's position and charge type)
+cudaError_t launch_binning(Plan& P, int64_t n, const IO* pos, const IO* q, cudaStream_t s);
 // short-range pair sums (phis, fs.xyz)
 cudaError_t launch_short_range(Plan& P, int64_t n, cudaStream_t s);
 // grid passes: anterpolation (charges q_i * scale, scale from device or 1)
@@ -154,11 +155,12 @@ cudaError_t launch_lattice(Plan& P, int k, const void* qk, void* uk, cudaStream_
 cudaError_t launch_top(Plan& P, const void* qt, void* ut, cudaStream_t s);
 cudaError_t launch_prolong(Plan& P, int k, const void* coarse, void* fine, cudaStream_t s);
 // interpolation of u^0 at the atoms and assembly of E, phi, F (forward)
-cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, double* phi, double* force,
-                                  cudaStream_t s);
+template <typename OUT>  // OUT = caller's output type (double or float)
+cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, OUT* phi, OUT* force, cudaStream_t s);
 // adjoint: interpolation of the adjoint grid and assembly of dL/dq, dL/dr
-cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, double* grad_pos,
-                                   double* grad_q, cudaStream_t s);
+template <typename OUT>
+cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, OUT* grad_pos, OUT* grad_q,
+                                   cudaStream_t s);
 // one-time kernel attributes (called once per process before the first launch)
 cudaError_t configure_kernels();
 // grid copy to double (debug)

@@ -276,11 +276,6 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
     P->cw[d] = p.box[d] / c;
   }
   P->ncell = P->nc[0] * P->nc[1] * P->nc[2];
-  {
-    int bits = 1;
-    while ((1 << bits) < P->ncell) ++bits;
-    P->key_passes = (bits + 7) / 8;
-  }
   std::vector<int4> offs;
   for (int oz = -2; oz <= 2; ++oz)
     for (int oy = -2; oy <= 2; ++oy)
@@ -404,8 +399,6 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   size_t T = P->fp64 ? sizeof(double) : sizeof(float);
   int64_t cap = p.max_atoms;
   P->cap = cap;
-  const int kChunk = 4096;  // atoms per radix-sort block
-  P->nblk_hist = (int)((cap + kChunk - 1) / kChunk);
   {  // one energy partial per interpolation block (blocks of ablk^3 cells)
     int64_t nb = 1;
     for (int d = 0; d < 3; ++d) nb *= (P->nc[d] + P->ablk - 1) / P->ablk;
@@ -415,11 +408,12 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   auto M = [&](void** ptr, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(ptr, bytes ? bytes : 16);
   };
-  for (int i = 0; i < 2; ++i) {
-    M((void**)&D.keys[i], sizeof(int) * cap);
-    M((void**)&D.idx[i], sizeof(int) * cap);
-  }
-  M((void**)&D.hist, sizeof(int) * 256 * (size_t)P->nblk_hist);
+  M((void**)&D.key, sizeof(int) * cap);
+  M((void**)&D.rank, sizeof(int) * cap);
+  M((void**)&D.perm, sizeof(int) * cap);
+  M((void**)&D.count, sizeof(int) * (size_t)P->ncell);
+  M((void**)&D.csum, sizeof(int) * (size_t)(P->ncell / 4096 + 1));
+  if (e == cudaSuccess) e = cudaMemset(D.count, 0, sizeof(int) * (size_t)P->ncell);  // kept zero between evaluations
   M((void**)&D.cell_start, sizeof(int) * (P->ncell + 1));
   M(&D.atoms, 4 * T * cap);
   M(&D.gfrac, 4 * T * cap);
@@ -488,7 +482,7 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
 
 void free_plan(Plan* P) {
   DeviceBuffers& D = P->d;
-  void* ptrs[] = {D.keys[0], D.keys[1], D.idx[0], D.idx[1], D.hist, D.cell_start, D.atoms,
+  void* ptrs[] = {D.key, D.rank, D.perm, D.count, D.csum, D.cell_start, D.atoms,
                   D.gfrac, D.gbase, D.phis, D.fs, D.glong, D.topK, D.topq, D.topu, D.seg, D.seg2, D.cell_shift, D.cell_rows,
                   D.seg_start, D.cell_off, D.partial, D.scalars, D.status, D.hpos, D.hq,
                   D.hphi, D.hforce, D.henergy};

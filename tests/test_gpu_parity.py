@@ -196,7 +196,10 @@ def test_backward_adjoint_matches_forward_outputs(precision, dev):
     E2 = MSMEnergy.apply(tp, tq, plan)
     (3.0 * E2).backward()
     t = TOL[precision]
-    assert abs(E2.item() - E.item()) <= 1e-9 * abs(E.item())      # repeat of the same forward
+    # repeat of the same forward: the order inside a cell follows the binning
+    # atomics, so FP32 sums may round differently from run to run
+    rep = 1e-12 if precision == "fp64" else 1e-7
+    assert abs(E2.item() - E.item()) <= rep * abs(E.item())
     assert rel_rms(tp.grad.cpu().numpy(), -3.0 * F.cpu().numpy()) <= t["F"]
     assert rel_rms(tq.grad.cpu().numpy(), 3.0 * phi.cpu().numpy()) <= t["phi"]
     ref = O.msm(oparams(cfg), pos, q)
@@ -236,8 +239,8 @@ def test_host_entry_point_matches_device(dev):
     Ed, phid, Fd = gpu_eval(plan, pos, q, dev)
     Eh, phih, Fh = plan.eval_host(torch.tensor(pos).pin_memory(), torch.tensor(q).pin_memory(),
                                   want_phi=True, want_force=True)
-    # same inputs, same kernels; only the order of the FP32 shared-memory
-    # atomics of the anterpolation differs between the two runs
+    # same inputs, same kernels; only the order of atomic additions (cell
+    # order of the binning, anterpolation sums) differs between the two runs
     assert abs(Eh.item() - Ed) <= 1e-7 * abs(Ed)
     assert rel_rms(Fh.numpy(), Fd) <= 1e-7
 
