@@ -13,6 +13,7 @@
 // operations; rejected pairs are masked, not branched.  Mixed precision sums
 // each batch in FP32 and folds the batch sums into the running totals with an
 // error-free TwoSum (compensated accumulation).
+#include <climits>
 #include <cmath>
 
 #include "msm_internal.h"
@@ -234,44 +235,14 @@ __global__ void __launch_bounds__(32 * kWarps) k_short_range(
 }
 
 // ---- mixed precision: packed FP32x2 arithmetic (two sources per instruction) ----
-// The queue is stored as four FP32 arrays (x, y, z, q), so sources j and j+1
-// load as one float2 each and feed FFMA2/FMUL2/FADD2 directly.  With
+// The queue is stored as four FP32 arrays (x, y, z, q), so sources j..j+3
+// load as one float4 per array and feed FFMA2/FMUL2/FADD2 as two pairs.  With
 // d = r_j - r_i, f' = q_j (1/r^3 + 2 gamma_s(s)/a^3) and
 // F_i = -q_i sum_j f' d, which needs no negations in the loop.  The home cell
 // (the only one that holds the target itself) goes through the scalar batch
 // with the self test; every other cell skips that test.  Far-away padding
 // sits at 1e6 so that the unmasked polynomial stays finite.
-template <int M>
-struct SmoothF2;
-template <>
-struct SmoothF2<1> {
-  __device__ static float2 g(float2 s) { return __ffma2_rn(s, make_float2(-0.5f, -0.5f), make_float2(1.5f, 1.5f)); }
-  __device__ static float2 gs(float2) { return make_float2(-0.5f, -0.5f); }
-};
-template <>
-struct SmoothF2<2> {
-  __device__ static float2 g(float2 s) {
-    float2 t = __ffma2_rn(s, make_float2(0.375f, 0.375f), make_float2(-1.25f, -1.25f));
-    return __ffma2_rn(t, s, make_float2(1.875f, 1.875f));
-  }
-  __device__ static float2 gs(float2 s) {
-    return __ffma2_rn(s, make_float2(0.75f, 0.75f), make_float2(-1.25f, -1.25f));
-  }
-};
-template <>
-struct SmoothF2<3> {
-  __device__ static float2 g(float2 s) {
-    float2 t = __ffma2_rn(s, make_float2(-0.3125f, -0.3125f), make_float2(1.3125f, 1.3125f));
-    t = __ffma2_rn(t, s, make_float2(-2.1875f, -2.1875f));
-    return __ffma2_rn(t, s, make_float2(2.1875f, 2.1875f));
-  }
-  __device__ static float2 gs(float2 s) {
-    float2 t = __ffma2_rn(s, make_float2(-0.9375f, -0.9375f), make_float2(2.625f, 2.625f));
-    return __ffma2_rn(t, s, make_float2(-2.1875f, -2.1875f));
-  }
-};
-
-struct QueueF {
+struct alignas(16) QueueF {
   float x[2 * kBatch], y[2 * kBatch], z[2 * kBatch], q[2 * kBatch];
 };
 
@@ -303,24 +274,32 @@ __device__ __forceinline__ void pair_batch_f2(const QueueF& Q, float2 nax, float
                                               const PairCoef& C, float& phi, float& px, float& py, float& pz,
                                               float& cphi, float& cpx, float& cpy, float& cpz) {
   float2 sphi = make_float2(0.f, 0.f), sx = sphi, sy = sphi, sz = sphi;
-#pragma unroll 4
-  for (int jj = 0; jj < kBatch; jj += 2) {
-    const float2 bx = *reinterpret_cast<const float2*>(&Q.x[jj]);
-    const float2 by = *reinterpret_cast<const float2*>(&Q.y[jj]);
-    const float2 bz = *reinterpret_cast<const float2*>(&Q.z[jj]);
-    const float2 bq = *reinterpret_cast<const float2*>(&Q.q[jj]);
-    const float2 dx = __fadd2_rn(bx, nax), dy = __fadd2_rn(by, nay), dz = __fadd2_rn(bz, naz);
-    float2 r2 = __fmul2_rn(dx, dx);
-    r2 = __ffma2_rn(dy, dy, r2);
-    r2 = __ffma2_rn(dz, dz, r2);
-    const float2 qj = make_float2(r2.x < a2 ? bq.x : 0.f, r2.y < a2 ? bq.y : 0.f);
-    const float2 rinv = make_float2(fast_rsqrt(r2.x), fast_rsqrt(r2.y));
-    const float2 pot = __fadd2_rn(rinv, poly_g<M>(C, r2));   // G holds -gamma coefficients
-    sphi = __ffma2_rn(qj, pot, sphi);
-    const float2 fp = __fmul2_rn(__ffma2_rn(__fmul2_rn(rinv, rinv), rinv, poly_d<M>(C, r2)), qj);
-    sx = __ffma2_rn(fp, dx, sx);
-    sy = __ffma2_rn(fp, dy, sy);
-    sz = __ffma2_rn(fp, dz, sz);
+  // sources jj..jj+3 load as one float4 per coordinate (two packed halves)
+#pragma unroll
+  for (int jj = 0; jj < kBatch; jj += 4) {
+    const float4 x4 = *reinterpret_cast<const float4*>(&Q.x[jj]);
+    const float4 y4 = *reinterpret_cast<const float4*>(&Q.y[jj]);
+    const float4 z4 = *reinterpret_cast<const float4*>(&Q.z[jj]);
+    const float4 q4 = *reinterpret_cast<const float4*>(&Q.q[jj]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float2 bx = h ? make_float2(x4.z, x4.w) : make_float2(x4.x, x4.y);
+      const float2 by = h ? make_float2(y4.z, y4.w) : make_float2(y4.x, y4.y);
+      const float2 bz = h ? make_float2(z4.z, z4.w) : make_float2(z4.x, z4.y);
+      const float2 bq = h ? make_float2(q4.z, q4.w) : make_float2(q4.x, q4.y);
+      const float2 dx = __fadd2_rn(bx, nax), dy = __fadd2_rn(by, nay), dz = __fadd2_rn(bz, naz);
+      float2 r2 = __fmul2_rn(dx, dx);
+      r2 = __ffma2_rn(dy, dy, r2);
+      r2 = __ffma2_rn(dz, dz, r2);
+      const float2 qj = make_float2(r2.x < a2 ? bq.x : 0.f, r2.y < a2 ? bq.y : 0.f);
+      const float2 rinv = make_float2(fast_rsqrt(r2.x), fast_rsqrt(r2.y));
+      const float2 pot = __fadd2_rn(rinv, poly_g<M>(C, r2));  // G holds -gamma coefficients
+      sphi = __ffma2_rn(qj, pot, sphi);
+      const float2 fp = __fmul2_rn(__ffma2_rn(__fmul2_rn(rinv, rinv), rinv, poly_d<M>(C, r2)), qj);
+      sx = __ffma2_rn(fp, dx, sx);
+      sy = __ffma2_rn(fp, dy, sy);
+      sz = __ffma2_rn(fp, dz, sz);
+    }
   }
   two_sum_add(phi, cphi, sphi.x + sphi.y);
   two_sum_add(px, cpx, sx.x + sx.y);
@@ -330,19 +309,33 @@ __device__ __forceinline__ void pair_batch_f2(const QueueF& Q, float2 nax, float
 
 // Rows of neighbour cells: for each (dy, dz) the cells cx+xlo..cx+xhi of one x
 // row are contiguous in the sorted atom array (cells are numbered x fastest),
-// so a whole row is staged as one or two contiguous atom ranges (two when the
-// row wraps around a periodic box) instead of cell by cell.  The x offset of
-// a source atom's cell follows from comparing its index with the cell starts
-// of the row.
+// so a whole row is one or two contiguous atom ranges ("segments"; two when
+// the row wraps around a periodic box).  At the start of a cell the lanes
+// build the cell's segment table together, one row per lane (all cell-start
+// loads in flight at once), and a warp scan lays the segments end to end
+// into one flat source index space.  The warp then walks that space in full
+// chunks of 32 sources, loading the next chunk's atoms before it works on the
+// current one.  The x offset of a source's cell follows from comparing its
+// index with the cell starts inside its segment.
+constexpr int kMaxRows = 32;  // rows per cell: cells at least a/2 wide give at most 26
+
+struct SegTable {
+  int4 rec[2 * kMaxRows + 1];   // (first atom, flat start, x offset of the first cell, -); sentinel at the end
+  int4 bnd[2 * kMaxRows];       // first atom of the segment's 2nd..5th cell (INT_MAX where absent)
+  float2 shift[2 * kMaxRows];   // (y, z) shift of the row
+};
+
 template <int M>
-__global__ void __launch_bounds__(32 * kWarps, 7) k_short_range_f2(
+__global__ void __launch_bounds__(32 * kWarps, 6) k_short_range_f2(
     const R4<float>* __restrict__ atoms, const int* __restrict__ cell_start,
     const int4* __restrict__ rows, int nrows, PairArgs A, PairCoef C, float cwx, float cwy, float cwz, int ncell,
     float* __restrict__ phis, R4<float>* __restrict__ fs) {
   __shared__ QueueF queue[kWarps];
   __shared__ R4<float> home[kWarps][kBatch];
+  __shared__ SegTable tables[kWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   QueueF& Q = queue[warp];
+  SegTable& T = tables[warp];
   const int cell = blockIdx.x * kWarps + warp;
   if (cell >= ncell) return;  // warp-uniform
   const int ncx = A.nc[0], ncy = A.nc[1], ncz = A.nc[2];
@@ -350,6 +343,80 @@ __global__ void __launch_bounds__(32 * kWarps, 7) k_short_range_f2(
   const float a2 = A.a2f, inv_a = A.inv_af, inv_a2s = A.inv_a2f, two_inv_a3 = A.two_inv_a3f;
   const float FAR = 1e6f;
   const int i0 = cell_start[cell], i1 = cell_start[cell + 1];
+
+  // ---- segment table of this cell (lane r: row r) ----
+  int len[2] = {0, 0}, j0s[2] = {0, 0}, ox0s[2] = {0, 0};
+  int4 bnds[2] = {make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX), make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX)};
+  float2 sh = make_float2(0.f, 0.f);
+  if (lane < nrows) {
+    const int4 row = rows[lane];  // (dy, dz, xlo, xhi): x offsets xlo..xhi of this row
+    int ny = cy + row.x, nz = cz + row.y;
+    bool inside = true;
+    if (A.periodic) {
+      ny += (ny < 0) ? ncy : ((ny >= ncy) ? -ncy : 0);
+      nz += (nz < 0) ? ncz : ((nz >= ncz) ? -ncz : 0);
+    } else if (ny < 0 || nz < 0 || ny >= ncy || nz >= ncz) {
+      inside = false;
+    }
+    const int rbase = (nz * ncy + ny) * ncx;
+    sh = make_float2(row.x * cwy, row.y * cwz);
+#pragma unroll
+    for (int seg = 0; seg < 2; ++seg) {
+      int ox0 = 0, ox1 = -1;  // empty unless set below
+      if (!inside) {
+      } else if (A.periodic) {
+        const int xa = cx + row.z, xb = cx + row.w;  // may leave [0, ncx) by at most 2
+        if (xa < 0) {
+          if (seg == 0) { ox0 = row.z; ox1 = -cx - 1; } else { ox0 = -cx; ox1 = row.w; }
+        } else if (xb >= ncx) {
+          if (seg == 0) { ox0 = row.z; ox1 = ncx - 1 - cx; } else { ox0 = ncx - cx; ox1 = row.w; }
+        } else if (seg == 0) {
+          ox0 = row.z; ox1 = row.w;
+        }
+      } else if (seg == 0) {
+        ox0 = max(row.z, -cx);
+        ox1 = min(row.w, ncx - 1 - cx);
+      }
+      if (ox0 <= ox1) {
+        int x0 = cx + ox0, x1 = cx + ox1;
+        if (A.periodic) {
+          x0 += (x0 < 0) ? ncx : ((x0 >= ncx) ? -ncx : 0);
+          x1 += (x1 < 0) ? ncx : ((x1 >= ncx) ? -ncx : 0);
+        }
+        const int j0 = cell_start[rbase + x0], j1 = cell_start[rbase + x1 + 1];
+        int bb[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) bb[t] = (x0 + 1 + t <= x1) ? cell_start[rbase + x0 + 1 + t] : INT_MAX;
+        len[seg] = j1 - j0;
+        j0s[seg] = j0;
+        ox0s[seg] = ox0;
+        bnds[seg] = make_int4(bb[0], bb[1], bb[2], bb[3]);
+      }
+    }
+  }
+  int total;
+  {
+    const int mine = len[0] + len[1];
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    total = __shfl_sync(kFull, incl, 31);
+    const int start = incl - mine;
+    if (lane < nrows) {
+#pragma unroll
+      for (int seg = 0; seg < 2; ++seg) {
+        T.rec[2 * lane + seg] = make_int4(j0s[seg], seg ? start + len[0] : start, ox0s[seg], 0);
+        T.bnd[2 * lane + seg] = bnds[seg];
+        T.shift[2 * lane + seg] = sh;
+      }
+    }
+    if (lane == 0) T.rec[2 * nrows] = make_int4(0, INT_MAX, 0, 0);
+    __syncwarp();
+  }
+
   for (int ib = i0; ib < i1; ib += 32) {
     const int i = ib + lane;
     const bool iv = i < i1;
@@ -381,85 +448,64 @@ __global__ void __launch_bounds__(32 * kWarps, 7) k_short_range_f2(
       two_sum_add(pz, cpz, hz_ + c3);
       __syncwarp();
     }
+    // ---- the neighbour rows: flat source index t in [0, total), 32 per step ----
+    int seg = 0;  // this lane's segment cursor (t only grows)
+    // source t: its atom index and cell x offset (t < total)
+    auto locate = [&](int t, int& j, int& ox, float2& shv) {
+      while (T.rec[seg + 1].y <= t) ++seg;
+      const int4 r = T.rec[seg];
+      const int4 b = T.bnd[seg];
+      j = r.x + (t - r.y);
+      ox = r.z + (j >= b.x) + (j >= b.y) + (j >= b.z) + (j >= b.w);
+      shv = T.shift[seg];
+    };
+    R4<float> an = {FAR, FAR, FAR, 0.f};
+    int oxn = 0;
+    float2 shn = make_float2(0.f, 0.f);
+    if (lane < total) {
+      int j;
+      locate(lane, j, oxn, shn);
+      an = atoms[j];
+    }
     int qn = 0;  // queued sources (warp-uniform)
-    for (int r = 0; r < nrows; ++r) {
-      const int4 row = rows[r];  // (dy, dz, xlo, xhi): x offsets xlo..xhi of this row
-      int ny = cy + row.x, nz = cz + row.y;
-      if (A.periodic) {
-        ny += (ny < 0) ? ncy : ((ny >= ncy) ? -ncy : 0);
-        nz += (nz < 0) ? ncz : ((nz >= ncz) ? -ncz : 0);
-      } else if (ny < 0 || nz < 0 || ny >= ncy || nz >= ncz) {
-        continue;
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const bool valid = t0 + lane < total;
+      R4<float> aj = an;
+      const int ox = oxn;
+      const float2 shv = shn;
+      if (t0 + 32 + lane < total) {  // next chunk's load goes out before this chunk's work
+        int j;
+        locate(t0 + 32 + lane, j, oxn, shn);
+        an = atoms[j];
       }
-      const int rbase = (nz * ncy + ny) * ncx;
-      const float sy = row.x * cwy, sz = row.y * cwz;
-      // one or two contiguous segments [ox0, ox1] of x offsets
-      for (int seg = 0; seg < 2; ++seg) {
-        int ox0, ox1;
-        if (A.periodic) {
-          int xa = cx + row.z, xb = cx + row.w;  // may leave [0, ncx) by at most R
-          if (xa < 0) {
-            if (seg == 0) { ox0 = row.z; ox1 = -cx - 1; } else { ox0 = -cx; ox1 = row.w; }
-          } else if (xb >= ncx) {
-            if (seg == 0) { ox0 = row.z; ox1 = ncx - 1 - cx; } else { ox0 = ncx - cx; ox1 = row.w; }
-          } else {
-            if (seg == 1) break;
-            ox0 = row.z; ox1 = row.w;
-          }
-          if (ox0 > ox1) continue;  // this side of the wrap is empty
-        } else {
-          if (seg == 1) break;
-          ox0 = max(row.z, -cx);
-          ox1 = min(row.w, ncx - 1 - cx);
-          if (ox0 > ox1) break;
+      aj.x += ox * cwx;
+      aj.y += shv.x;
+      aj.z += shv.y;
+      const float ex = fmaxf(fmaxf(lx - aj.x, aj.x - hx), 0.f);
+      const float ey = fmaxf(fmaxf(ly - aj.y, aj.y - hy), 0.f);
+      const float ez = fmaxf(fmaxf(lz - aj.z, aj.z - hz), 0.f);
+      const bool keep = valid && (ex * ex + ey * ey + ez * ez < a2);
+      const unsigned bal = __ballot_sync(kFull, keep);
+      if (keep) {
+        const int p = qn + __popc(bal & ((1u << lane) - 1u));
+        Q.x[p] = aj.x;
+        Q.y[p] = aj.y;
+        Q.z[p] = aj.z;
+        Q.q[p] = aj.w;
+      }
+      qn += __popc(bal);
+      __syncwarp();
+      if (qn >= kBatch) {
+        pair_batch_f2<M>(Q, nax, nay, naz, a2, C, phi, px, py, pz, cphi, cpx, cpy, cpz);
+        __syncwarp();
+        if (lane < qn - kBatch) {
+          Q.x[lane] = Q.x[kBatch + lane];
+          Q.y[lane] = Q.y[kBatch + lane];
+          Q.z[lane] = Q.z[kBatch + lane];
+          Q.q[lane] = Q.q[kBatch + lane];
         }
-        int x0 = cx + ox0, x1 = cx + ox1;
-        if (A.periodic) {
-          x0 += (x0 < 0) ? ncx : ((x0 >= ncx) ? -ncx : 0);
-          x1 += (x1 < 0) ? ncx : ((x1 >= ncx) ? -ncx : 0);
-        }
-        const int j0 = cell_start[rbase + x0], j1 = cell_start[rbase + x1 + 1];
-        // cell starts of the segment's interior cells, to find each source's x offset
-        int bnd[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) bnd[t] = (x0 + 1 + t <= x1) ? cell_start[rbase + x0 + 1 + t] : 0x7fffffff;
-        for (int jb = j0; jb < j1; jb += 32) {
-          const int j = jb + lane;
-          R4<float> aj = {FAR, FAR, FAR, 0.f};
-          if (j < j1) {
-            aj = atoms[j];
-            int ox = ox0 + (j >= bnd[0]) + (j >= bnd[1]) + (j >= bnd[2]) + (j >= bnd[3]);
-            aj.x += ox * cwx;
-            aj.y += sy;
-            aj.z += sz;
-          }
-          const float ex = fmaxf(fmaxf(lx - aj.x, aj.x - hx), 0.f);
-          const float ey = fmaxf(fmaxf(ly - aj.y, aj.y - hy), 0.f);
-          const float ez = fmaxf(fmaxf(lz - aj.z, aj.z - hz), 0.f);
-          const bool keep = (j < j1) && (ex * ex + ey * ey + ez * ez < a2);
-          const unsigned bal = __ballot_sync(kFull, keep);
-          if (keep) {
-            const int p = qn + __popc(bal & ((1u << lane) - 1u));
-            Q.x[p] = aj.x;
-            Q.y[p] = aj.y;
-            Q.z[p] = aj.z;
-            Q.q[p] = aj.w;
-          }
-          qn += __popc(bal);
-          __syncwarp();
-          if (qn >= kBatch) {
-            pair_batch_f2<M>(Q, nax, nay, naz, a2, C, phi, px, py, pz, cphi, cpx, cpy, cpz);
-            __syncwarp();
-            if (lane < qn - kBatch) {
-              Q.x[lane] = Q.x[kBatch + lane];
-              Q.y[lane] = Q.y[kBatch + lane];
-              Q.z[lane] = Q.z[kBatch + lane];
-              Q.q[lane] = Q.q[kBatch + lane];
-            }
-            qn -= kBatch;
-            __syncwarp();
-          }
-        }
+        qn -= kBatch;
+        __syncwarp();
       }
     }
     if (qn > 0) {  // last partial batch, padded with far-away zero charges
@@ -511,7 +557,6 @@ void launch_f2(Plan& P, cudaStream_t st) {
   PairArgs A = pair_args(P);
   int blocks = (P.ncell + kWarps - 1) / kWarps;
   auto* at = (const R4<float>*)P.d.atoms;
-  auto* sh = (const R4<float>*)P.d.cell_shift;
   auto* ph = (float*)P.d.phis;
   auto* fs = (R4<float>*)P.d.fs;
   // gamma coefficients c_k (Taylor series of s^(-1/2) about s = 1, truncated at m)
@@ -529,7 +574,6 @@ void launch_f2(Plan& P, cudaStream_t st) {
     C.D[k] = make_float2(d, d);
   }
   const float cwx = (float)P.cw[0], cwy = (float)P.cw[1], cwz = (float)P.cw[2];
-  (void)sh;
   if (m == 1)
     k_short_range_f2<1><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_rows, P.nrows, A, C, cwx, cwy,
                                                         cwz, P.ncell, ph, fs);

@@ -309,6 +309,10 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
       }
     }
   P->nrows = (int)rowv.size();
+  // the packed pair kernel builds its row table one row per lane; with cells
+  // at least a/2 wide there are at most 5 x 5 (dy, dz) rows plus the split
+  // home row
+  if (P->nrows > 32) return MSM_ERR_UNSUPPORTED;
   // anterpolation patch: B^3 cells reach at most floor(B cw/h) + 2S + 5
   // points per dimension (with margin for rounding); keep it in shared memory
   {
