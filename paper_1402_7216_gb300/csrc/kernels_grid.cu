@@ -251,6 +251,197 @@ __global__ void __launch_bounds__(256) k_anterp_patch(const R4<T>* __restrict__ 
   }
 }
 
+// ---- mixed precision: exact fixed-point patch sums ----
+// Shared-memory FP32 atomic adds return through a compare-and-swap round
+// trip, while 32-bit integer reductions are fire-and-forget.  So the mixed
+// plan accumulates each patch point as two integer sums: a contribution
+// c = q_j w (|w| <= 1) becomes t = c 2^12, a coarse part round(t) and a
+// residual round((t - round(t)) 2^19), each added with an integer reduction.
+// The patch sums are then exact, independent of order, at a resolution of
+// 2^-31.  Integer sums wrap modulo 2^32, so only the final sums must fit:
+// the coarse sum stays below 2^31 while |q_j| * (atoms of the block) <= 2^18
+// for every atom in the patch, and the residuals (|.| <= 2^18, one per atom)
+// of at most kAnterpMaxAtoms = 2^12 atoms stay below 2^30.  An atom with a
+// larger charge (or |q_j| >= 2^10) goes straight to the FP64 grid.  The device-side scale (the
+// adjoint's upstream gradient) multiplies the patch sums when they are
+// flushed, so the fixed-point resolution is relative to the charges alone.
+constexpr float kFxMagic = 12582912.0f;  // 1.5 * 2^23: adding it rounds |x| < 2^22 to an integer
+constexpr float kFxCoarse = 4096.0f;     // 2^12
+constexpr float kFxFine = 524288.0f;     // 2^19
+
+__device__ __forceinline__ void fx_split(float t, int& hi, int& lo) {
+  const float m = __fadd_rn(t, kFxMagic);
+  hi = __float_as_int(m) - __float_as_int(kFxMagic);
+  const float r = __fsub_rn(t, __fsub_rn(m, kFxMagic));  // t - round(t), exact
+  lo = __float_as_int(__fmaf_rn(r, kFxFine, kFxMagic)) - __float_as_int(kFxMagic);
+}
+
+// Bank-ordered atom list.  Every tap of an atom sits at a fixed offset from
+// the patch index of its first support point, so two lanes whose atoms' first
+// points share a shared-memory bank (index mod 32) collide on every one of
+// their (2S)^3 reductions.  The block therefore buckets its atoms by that
+// bank and lays the list out in rounds of 32 slots, slot L of round r holding
+// the r-th atom of bucket L: the 32 lanes of a warp instruction then touch 32
+// different banks.  Buckets fuller than the round count R = ceil(total/32)
+// spill into the empty slots of the others (those lanes share a bank with one
+// other lane).  Integer sums do not depend on the order, so neither the
+// bucket ranks nor the spill order affect the result.  Returns the slot count
+// 32 R (unfilled slots hold -1); scratch (at least total + 32 R ints) is the
+// not yet zeroed patch, else the list stays as it is.
+__device__ __forceinline__ int bank_order(int* list, int total, const int4* __restrict__ gbase, int lo0, int lo1,
+                                          int lo2, int PD, int* scratch, int nscratch) {
+  __shared__ int bcnt[32], bempty[33], ovf;
+  const int R = (total + 31) >> 5, nslot = R << 5;
+  if (total == 0 || nscratch < total + nslot) return total;  // block-uniform
+  const int tid = threadIdx.x;
+  if (tid < 32) bcnt[tid] = 0;
+  if (tid == 0) ovf = 0;
+  __syncthreads();
+  for (int kk = tid; kk < total; kk += blockDim.x) {
+    const int4 b = gbase[list[kk]];
+    const int key = (((b.z - lo2) * PD + (b.y - lo1)) * PD + (b.x - lo0)) & 31;
+    scratch[kk] = key | (atomicAdd(&bcnt[key], 1) << 5);
+  }
+  __syncthreads();
+  if (tid < 32) {  // empty slots of bucket L: rounds bcnt[L] .. R-1; exclusive prefix over L
+    const int e = max(0, R - bcnt[tid]);
+    int incl = e;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (tid >= o) incl += y;
+    }
+    bempty[tid] = incl - e;
+    if (tid == 31) bempty[32] = incl;
+  }
+  int* slots = scratch + total;
+  for (int e = tid; e < nslot; e += blockDim.x) slots[e] = -1;
+  __syncthreads();
+  for (int kk = tid; kk < total; kk += blockDim.x) {
+    const int key = scratch[kk] & 31, r = scratch[kk] >> 5;
+    int slot;
+    if (r < R) {
+      slot = (r << 5) | key;
+    } else {
+      const int o = atomicAdd(&ovf, 1);  // o < total empty slots, since 32 R >= total
+      int L = 0;
+      while (bempty[L + 1] <= o) ++L;
+      slot = ((bcnt[L] + (o - bempty[L])) << 5) | L;
+    }
+    slots[slot] = list[kk];
+  }
+  __syncthreads();
+  for (int e = tid; e < nslot; e += blockDim.x) list[e] = slots[e];
+  __syncthreads();
+  return nslot;
+}
+
+// One atom's (2S)^3 weighted charges straight into the FP64 grid (global
+// atomics); kept out of line so that the patch loop holds its weights in
+// registers.
+template <int ORDER>
+__device__ __noinline__ void anterp_atom_global(const R4<float> f, const int4 b, const GridDims G,
+                                                double* __restrict__ grid, double sc) {
+  constexpr int W = 2 * Basis<float, ORDER>::S;
+  float wx[W], wy[W], wz[W];
+  weights<float, ORDER>(f.x, wx);
+  weights<float, ORDER>(f.y, wy);
+  weights<float, ORDER>(f.z, wz);
+  const double qd = sc * (double)f.w;
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    const int sz = slot(b.z + c, G.n[2], G.lo[2], G.periodic);
+#pragma unroll
+    for (int bb = 0; bb < W; ++bb) {
+      const int sy = slot(b.y + bb, G.n[1], G.lo[1], G.periodic);
+      double* row = grid + ((size_t)sz * G.n[1] + sy) * G.n[0];
+#pragma unroll
+      for (int a = 0; a < W; ++a)
+        atomicAdd(row + slot(b.x + a, G.n[0], G.lo[0], G.periodic), qd * (double)(wz[c] * wy[bb] * wx[a]));
+    }
+  }
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(256) k_anterp_fx(const R4<float>* __restrict__ gfrac,
+                                                   const int4* __restrict__ gbase,
+                                                   const int* __restrict__ cell_start, AnterpArgs A, GridDims G,
+                                                   double* __restrict__ grid, const double* __restrict__ dscale,
+                                                   double factor) {
+  constexpr int S = Basis<float, ORDER>::S, W = 2 * S;
+  extern __shared__ unsigned char smem_raw[];
+  const int PD = A.pd, np = PD * PD * PD, tid = threadIdx.x;
+  int* phi_ = reinterpret_cast<int*>(smem_raw);  // coarse sums
+  int* plo = phi_ + np;                          // residual sums
+  __shared__ int cstart[64], ccount[64], list[kAnterpMaxAtoms + 32], tot_s, nk_s;  // + one round of slots
+  const int c0[3] = {(int)blockIdx.x * A.B, (int)blockIdx.y * A.B, (int)blockIdx.z * A.B};
+  const int lo0 = (int)floor(c0[0] * A.cw_h[0]) - S - 1;
+  const int lo1 = (int)floor(c0[1] * A.cw_h[1]) - S - 1;
+  const int lo2 = (int)floor(c0[2] * A.cw_h[2]) - S - 1;
+  if (tid == 0) nk_s = block_cells(A, cell_start, c0, cstart, ccount);
+  __syncthreads();
+  const int nk = nk_s;
+  const int total = build_rank_list(nk, cstart, ccount, list, &tot_s);
+  const double sc = factor * (dscale ? *dscale : 1.0);
+  // |q_j| <= 2^18 / (atoms in the patch) bounds the coarse sums; |q_j| < 2^10
+  // keeps |t| < 2^22, where the magic-number rounding of fx_split is exact
+  const float qmax = fminf(262144.0f / (float)max(total, 1), 1023.0f);
+  const int count = total >= 0 ? bank_order(list, total, gbase, lo0, lo1, lo2, PD, phi_, 2 * np) : 0;
+  for (int e = tid; e < 2 * np; e += blockDim.x) phi_[e] = 0;
+  __syncthreads();
+  for (int kk = tid; kk < count; kk += blockDim.x) {
+    const int i = list[kk];
+    if (i < 0) continue;  // unfilled slot of the bank-ordered list
+    const R4<float> f = gfrac[i];
+    const int4 b = gbase[i];
+    float wx[W], wy[W], wz[W];
+    weights<float, ORDER>(f.x, wx);
+    weights<float, ORDER>(f.y, wy);
+    weights<float, ORDER>(f.z, wz);
+    const int px = b.x - lo0, py = b.y - lo1, pz = b.z - lo2;
+    if (fabsf(f.w) < qmax && px >= 0 && py >= 0 && pz >= 0 && px + W <= PD && py + W <= PD && pz + W <= PD) {
+      const float qs = f.w * kFxCoarse;
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const float qz = qs * wz[c];
+#pragma unroll
+        for (int bb = 0; bb < W; ++bb) {
+          const float qyz = qz * wy[bb];
+          const int off = ((pz + c) * PD + py + bb) * PD + px;
+#pragma unroll
+          for (int a = 0; a < W; ++a) {
+            int h, l;
+            fx_split(qyz * wx[a], h, l);
+            atomicAdd(phi_ + off + a, h);
+            atomicAdd(plo + off + a, l);
+          }
+        }
+      }
+    } else {  // large charge, or outside the patch: straight to the FP64 grid
+      anterp_atom_global<ORDER>(f, b, G, grid, sc);
+    }
+  }
+  if (total < 0) {  // more atoms than the list holds: one thread per atom, straight to the grid
+    for (int c = 0; c < nk; ++c)
+      for (int m = tid; m < ccount[c]; m += blockDim.x) {
+        const int i = cstart[c] + m;
+        anterp_atom_global<ORDER>(gfrac[i], gbase[i], G, grid, sc);
+      }
+  }
+  __syncthreads();
+  const double ch = sc * (1.0 / 4096.0), cl = sc * (1.0 / 2147483648.0);  // 2^-12, 2^-31
+  for (int e = tid; e < np; e += blockDim.x) {
+    const int h = phi_[e], l = plo[e];
+    if ((h | l) == 0) continue;
+    int ix = lo0 + e % PD, iy = lo1 + (e / PD) % PD, iz = lo2 + e / (PD * PD);
+    if (!G.periodic && (ix < G.lo[0] || iy < G.lo[1] || iz < G.lo[2] || ix >= G.lo[0] + G.n[0] ||
+                        iy >= G.lo[1] + G.n[1] || iz >= G.lo[2] + G.n[2]))
+      continue;
+    int sx = slot(ix, G.n[0], G.lo[0], G.periodic), sy = slot(iy, G.n[1], G.lo[1], G.periodic),
+        sz = slot(iz, G.n[2], G.lo[2], G.periodic);
+    atomicAdd(grid + ((size_t)sz * G.n[1] + sy) * G.n[0] + sx, (double)h * ch + (double)l * cl);
+  }
+}
+
 // ---- restriction and prolongation: separable 1-D passes ----
 // phi^{k+1}_mu(r^k_nu) = prod_d Phi((nu_d - 2 mu_d)/2), so restriction is
 // three 1-D filters (x, then y, then z) and prolongation, its transpose, the
@@ -905,6 +1096,17 @@ unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
 
+AnterpArgs patch_args(const Plan& P) {
+  AnterpArgs A;
+  for (int d = 0; d < 3; ++d) {
+    A.nc[d] = P.nc[d];
+    A.cw_h[d] = P.cw[d] / P.h[d];
+  }
+  A.B = P.ablk;
+  A.pd = P.apd;
+  return A;
+}
+
 template <typename T, typename ACC, int ORDER>
 void anterp_t(Plan& P, void* grid0, const double* dscale, double factor, cudaStream_t st) {
   AnterpArgs A;
@@ -920,6 +1122,15 @@ void anterp_t(Plan& P, void* grid0, const double* dscale, double factor, cudaStr
                                                      dims_of(P, 0), (double*)grid0, dscale, factor);
 }
 
+template <int ORDER>
+void anterp_fx(Plan& P, void* grid0, const double* dscale, double factor, cudaStream_t st) {
+  AnterpArgs A = patch_args(P);
+  dim3 grid(blocks_for(P.nc[0], A.B), blocks_for(P.nc[1], A.B), blocks_for(P.nc[2], A.B));
+  size_t sm = 2 * sizeof(int) * (size_t)A.pd * A.pd * A.pd;  // coarse and residual sums
+  k_anterp_fx<ORDER><<<grid, 256, sm, st>>>((const R4<float>*)P.d.gfrac, P.d.gbase, P.d.cell_start, A,
+                                            dims_of(P, 0), (double*)grid0, dscale, factor);
+}
+
 cudaError_t launch_anterpolate(Plan& P, int64_t n, void* grid0, const double* dscale, double factor,
                                cudaStream_t st) {
   size_t bytes = sizeof(double) * (size_t)grid_points(P, 0);
@@ -930,8 +1141,8 @@ cudaError_t launch_anterpolate(Plan& P, int64_t n, void* grid0, const double* ds
     if (P.P.order == 3) anterp_t<double, double, 3>(P, grid0, dscale, factor, st);
     else anterp_t<double, double, 5>(P, grid0, dscale, factor, st);
   } else {
-    if (P.P.order == 3) anterp_t<float, float, 3>(P, grid0, dscale, factor, st);
-    else anterp_t<float, float, 5>(P, grid0, dscale, factor, st);
+    if (P.P.order == 3) anterp_fx<3>(P, grid0, dscale, factor, st);
+    else anterp_fx<5>(P, grid0, dscale, factor, st);
   }
   return cudaGetLastError();
 }
@@ -1059,16 +1270,6 @@ cudaError_t launch_top(Plan& P, const void* qt, void* ut, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-AnterpArgs patch_args(const Plan& P) {
-  AnterpArgs A;
-  for (int d = 0; d < 3; ++d) {
-    A.nc[d] = P.nc[d];
-    A.cw_h[d] = P.cw[d] / P.h[d];
-  }
-  A.B = P.ablk;
-  A.pd = P.apd;
-  return A;
-}
 
 template <typename OUT>
 cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, OUT* phi, OUT* force, cudaStream_t st) {
@@ -1131,8 +1332,8 @@ cudaError_t configure_kernels() {
     cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (r != cudaSuccess) e = r;
   };
-  set((const void*)k_anterp_patch<float, float, 3>);
-  set((const void*)k_anterp_patch<float, float, 5>);
+  set((const void*)k_anterp_fx<3>);
+  set((const void*)k_anterp_fx<5>);
   set((const void*)k_anterp_patch<double, double, 3>);
   set((const void*)k_anterp_patch<double, double, 5>);
   set((const void*)k_interp_fwd<float, 3, double>);

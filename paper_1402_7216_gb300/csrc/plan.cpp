@@ -315,8 +315,9 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   if (P->nrows > 32) return MSM_ERR_UNSUPPORTED;
   // anterpolation patch: B^3 cells reach at most floor(B cw/h) + 2S + 5
   // points per dimension (with margin for rounding); keep it in shared memory
+  // (FP64 sums, or two 32-bit integer sums per point on the mixed path)
   {
-    int cap = P->fp64 ? 24 : 32;
+    int cap = P->fp64 ? 24 : 29;
     int B = TU.patch_cells > 0 ? TU.patch_cells : 4, pd = 0;
     for (; B >= 1; --B) {
       pd = 0;

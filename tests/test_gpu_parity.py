@@ -271,3 +271,17 @@ def test_water1m_mixed_on_subsample(dev):
     got64 = gpu_eval(plan_for(cfg, "fp64", len(q)), pos, q, dev)
     assert rel_rms(got64[2][sub], ref["F"]) <= TOL["fp64"]["F"]
     assert abs(got[0] - got64[0]) <= TOL["mixed"]["E"] * abs(got64[0])
+
+
+def test_anterpolation_large_and_mixed_charges(dev):
+    """The mixed path sums patch charges in fixed point and routes large
+    charges (|q| >= 2^10, or |q| * atoms-per-patch > 2^18) straight to the FP64
+    grid; both routes, in one system, must match the oracle."""
+    cfg = dict(box=24.0, periodic=True, cutoff=8.0, spacing=2.0, order=5, split=2)
+    pos, q = make_water_box(24.0, 420, 3, 2, seed=23, periodic=True)
+    rng = np.random.default_rng(23)
+    scale = rng.choice([1.0, 300.0, 2500.0], size=len(q) // 3 + 1).repeat(3)[: len(q)]
+    q = q * scale
+    ref = O.msm(oparams(cfg), pos, q)
+    for precision in ["fp64", "mixed"]:
+        assert_close(gpu_eval(plan_for(cfg, precision, len(q)), pos, q, dev), ref, precision, precision)
