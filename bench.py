@@ -334,6 +334,12 @@ def main():
         tot = t.item()
     value = world * args.steps / (tot / 1e3)
 
+    # the same evaluation with every stage in turn on one stream (no overlap):
+    # per-kernel times without the concurrent grid passes, for context
+    plan.set_overlap(False)
+    ms_iso, (stage_iso, _, evals_iso), _ = timed(plan, max(3, args.steps // 4), 2, True)
+    plan.set_overlap(True)
+
     # end to end through the host-buffer entry point (pinned host memory)
     pos_pin = torch.tensor(pos_h).pin_memory()
     q_pin = torch.tensor(q_h).pin_memory()
@@ -397,18 +403,23 @@ def main():
     for k, e in kernels.items():
         if k in traffic:
             e["dram_bytes_ncu"] = traffic[k]
-    dom = max(per_eval, key=per_eval.get)
-    if dom in ("short_range", "lattice_cutoff", "anterpolation", "interpolation"):
-        ach = model[dom]["flop"] / (per_eval[dom] * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": traffic.get(dom),
-                "peak_source": "FP32 FMA peak: %d SMs x %d lanes x 2 flop x %.0f MHz (%s sm_max_mhz)"
-                               % (N_SM, FP32_LANES, sm_max, peak_kind),
-                "work_per_launch": model[dom].get("units")}
-    else:
-        ach = model.get(dom, {"bytes": 0})["bytes"] / (per_eval[dom] * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": traffic.get(dom)}
+    per_iso = {k: v / evals_iso for k, v in stage_iso.items()}
+
+    def roofline(stage_times, note):
+        dom = max(stage_times, key=stage_times.get)
+        if dom in ("short_range", "lattice_cutoff", "anterpolation", "interpolation"):
+            ach = model[dom]["flop"] / (stage_times[dom] * 1e-3) / 1e12
+            return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": ach / fp32_peak, "traffic": traffic.get(dom),
+                    "peak_source": "FP32 FMA peak: %d SMs x %d lanes x 2 flop x %.0f MHz (%s sm_max_mhz)"
+                                   % (N_SM, FP32_LANES, sm_max, peak_kind),
+                    "work_per_launch": model[dom].get("units"), "timing": note}
+        ach = model.get(dom, {"bytes": 0})["bytes"] / (stage_times[dom] * 1e-3) / 1e9
+        return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": traffic.get(dom), "timing": note}
+    roof = roofline(per_eval, "live: CUDA events on the kernel's stream in the timed region, where the grid "
+                              "passes run concurrently on the plan's side stream")
+    roof_iso = roofline(per_iso, "isolated: the same evaluation with every stage in turn on one stream")
     out = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": tot / args.steps, "higher_is_better": True,
@@ -423,7 +434,10 @@ def main():
                 "d2h_bytes_per_step": 8, "api": "msm_eval_host (pinned host buffers)"},
         "gpu_launches": launches,
         "roofline": roof,
+        "roofline_isolated": roof_iso,
         "kernels_ms_per_eval": kernels,
+        "kernels_ms_isolated": {k: round(v, 5) for k, v in per_iso.items()},
+        "ms_per_step_serial": sum(ms_iso) / len(ms_iso),
         "fp64_gpu_path": fp64,
         "batched_replicas": batched,
         "clocks": clk,

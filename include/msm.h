@@ -22,7 +22,10 @@
  *   - The caller owns every input and output buffer; the plan owns its
  *     workspace (sorted atoms, grids, tables) and frees it in msm_destroy.
  *   - Evaluation calls are asynchronous on the given CUDA stream (NULL = the
- *     legacy default stream) and never synchronise the host.  Errors that can
+ *     legacy default stream) and never synchronise the host.  msm_eval may
+ *     fork part of its work onto a plan-owned stream and joins it back onto
+ *     the given stream before returning control of the results (events
+ *     only; see msm_set_overlap).  Errors that can
  *     only be seen on the device (an atom outside an open box, a non-finite
  *     input) are posted to a device status word that msm_status reads.
  *   - A plan is not thread-safe: calls on one plan must be ordered (one
@@ -209,6 +212,18 @@ int msm_debug_grid(msm_handle h, int level, int which, double* host_out);
 #define MSM_STAGE_PROLONGATION 6  /* all levels */
 #define MSM_STAGE_INTERPOLATION 7 /* interpolation, assembly, energy reduction */
 #define MSM_NSTAGES 8
+
+/* Concurrency of the forward pass (on by default): after binning, the grid
+ * passes (anterpolation through prolongation) run on a stream the plan owns,
+ * created at the device's highest priority, concurrently with the short-range
+ * pair sums on the caller's stream; the caller's stream waits (event) for the
+ * grid before interpolation.  Fork and join are event waits, so a stream
+ * capture of the caller's stream takes both branches.  enable = 0 runs every
+ * stage on the caller's stream, one after another (stage timings then
+ * measure each kernel alone).  Results agree either way up to the rounding
+ * order of the atomic sums (the same as between two runs).
+ * Errors: INVALID_ARG. */
+int msm_set_overlap(msm_handle h, int enable);
 
 /* Diagnostics: enable != 0 makes every following msm_eval and
  * msm_eval_backward record a CUDA event pair around each stage on its stream

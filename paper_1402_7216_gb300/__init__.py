@@ -157,6 +157,11 @@ class MSM:
         _capi.check(rc, "msm_eval_host")
         return E, phi, F
 
+    def set_overlap(self, enable=True):
+        """Runs the grid passes concurrently with the pair sums (default) or,
+        with enable=False, every stage in turn on the caller's stream."""
+        _capi.check(lib().msm_set_overlap(self._h, int(bool(enable))), "msm_set_overlap")
+
     def profile(self, enable=True):
         """Records per-stage CUDA events around every following evaluation."""
         _capi.check(lib().msm_profile(self._h, int(bool(enable))), "msm_profile")

@@ -40,7 +40,7 @@ _lib = None
 _D = C.POINTER(C.c_double)
 EXPORTS = ["msm_create", "msm_create_tuned", "msm_destroy", "msm_query", "msm_eval", "msm_eval_backward",
            "msm_eval_f32io", "msm_eval_backward_f32io",
-           "msm_eval_host", "msm_status", "msm_debug_grid", "msm_profile", "msm_profile_read",
+           "msm_eval_host", "msm_status", "msm_debug_grid", "msm_set_overlap", "msm_profile", "msm_profile_read",
            "msm_stage_name", "msm_energy_noalloc", "msm_eval_batch", "msm_eval_backward_batch",
            "msm_batch_graph_create", "msm_graph_launch", "msm_graph_destroy", "msm_strerror"]
 NSTAGES = 8
@@ -78,6 +78,8 @@ def load(path=LIB_PATH):
     L.msm_status.restype = C.c_int
     L.msm_debug_grid.argtypes = [vp, C.c_int, C.c_int, _D]
     L.msm_debug_grid.restype = C.c_int
+    L.msm_set_overlap.argtypes = [vp, C.c_int]
+    L.msm_set_overlap.restype = C.c_int
     L.msm_profile.argtypes = [vp, C.c_int]
     L.msm_profile.restype = C.c_int
     L.msm_profile_read.argtypes = [vp, _D, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]

@@ -1,8 +1,9 @@
 // capi.cu -- the extern "C" entry points declared in include/msm.h.
-// Each evaluation is a fixed sequence of kernel launches on the caller's
-// stream (no host synchronisation, no allocation), in the order of the
-// method: binning, short-range pairs, anterpolation, restriction and lattice
-// cutoff per level, top level, prolongation, interpolation and assembly.
+// Each evaluation is a fixed sequence of kernel launches (no host
+// synchronisation, no allocation), in the order of the method: binning,
+// short-range pairs, anterpolation, restriction and lattice cutoff per level,
+// top level, prolongation, interpolation and assembly.  The grid passes may
+// run on a plan-owned stream forked from and joined back onto the caller's.
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -64,14 +65,31 @@ cudaError_t grid_sweep(Plan& P, void* const* q, void* const* u, cudaStream_t st)
 }
 
 // IO = the caller's type of positions, charges and per-atom outputs
+// After binning, the pair sums and the grid passes (anterpolation through
+// prolongation) depend only on the binned atoms, so with overlap on they run
+// concurrently: the grid passes on the plan's high-priority side stream (its
+// chain of small, latency-bound launches gets the SMs first), the pair sums on
+// the caller's stream filling the rest; the caller's stream waits for the grid
+// before interpolation.  Fork and join are event waits, so a stream capture of
+// st takes the side stream in and the graph gets two parallel branches.
 template <typename IO>
 int forward(Plan& P, int64_t n, const IO* pos, const IO* q, double* energy, IO* phi, IO* force, cudaStream_t st) {
   cudaError_t e = stage(P, MSM_STAGE_BINNING, st, [&] { return launch_binning(P, n, pos, q, st); });
-  if (e == cudaSuccess) e = stage(P, MSM_STAGE_SHORT_RANGE, st, [&] { return launch_short_range(P, n, st); });
+  cudaStream_t gs = st;
+  if (e == cudaSuccess && P.overlap) {
+    gs = P.side;
+    e = cudaEventRecord(P.ev_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(gs, P.ev_fork, 0);
+  }
   if (e == cudaSuccess)
-    e = stage(P, MSM_STAGE_ANTERPOLATION, st,
-              [&] { return launch_anterpolate(P, n, P.d.gq[0], nullptr, 1.0, st); });
-  if (e == cudaSuccess) e = grid_sweep(P, P.d.gq, P.d.gu, st);
+    e = stage(P, MSM_STAGE_ANTERPOLATION, gs,
+              [&] { return launch_anterpolate(P, n, P.d.gq[0], nullptr, 1.0, gs); });
+  if (e == cudaSuccess) e = stage(P, MSM_STAGE_SHORT_RANGE, st, [&] { return launch_short_range(P, n, st); });
+  if (e == cudaSuccess) e = grid_sweep(P, P.d.gq, P.d.gu, gs);
+  if (e == cudaSuccess && gs != st) {
+    e = cudaEventRecord(P.ev_join, gs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P.ev_join, 0);
+  }
   if (e == cudaSuccess)
     e = stage(P, MSM_STAGE_INTERPOLATION, st,
               [&] { return launch_interp_forward(P, n, energy, phi, force, st); });
@@ -392,6 +410,12 @@ int msm_debug_grid(msm_handle h, int level, int which, double* host_out) {
   if (e == cudaSuccess) e = cudaMemcpy(host_out, tmp, sizeof(double) * np, cudaMemcpyDeviceToHost);
   cudaFree(tmp);
   return e == cudaSuccess ? MSM_OK : MSM_ERR_CUDA;
+}
+
+int msm_set_overlap(msm_handle h, int enable) {
+  if (!h) return MSM_ERR_INVALID_ARG;
+  h->p.overlap = enable != 0;
+  return MSM_OK;
 }
 
 int msm_profile(msm_handle h, int enable) {

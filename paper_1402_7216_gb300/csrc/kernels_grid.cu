@@ -335,28 +335,29 @@ __device__ __forceinline__ int bank_order(int* list, int total, const int4* __re
   return nslot;
 }
 
-// One atom's (2S)^3 weighted charges straight into the FP64 grid (global
-// atomics); kept out of line so that the patch loop holds its weights in
-// registers.
+// One atom's (2S)^3 weighted charges straight into the fixed-point grid
+// (global 64-bit integer reductions, 2^-31 units, computed in FP64); kept out
+// of line so that the patch loop holds its weights in registers.
 template <int ORDER>
 __device__ __noinline__ void anterp_atom_global(const R4<float> f, const int4 b, const GridDims G,
-                                                double* __restrict__ grid, double sc) {
+                                                unsigned long long* __restrict__ gfx) {
   constexpr int W = 2 * Basis<float, ORDER>::S;
   float wx[W], wy[W], wz[W];
   weights<float, ORDER>(f.x, wx);
   weights<float, ORDER>(f.y, wy);
   weights<float, ORDER>(f.z, wz);
-  const double qd = sc * (double)f.w;
+  const double qd = 2147483648.0 * (double)f.w;  // 2^31 q
 #pragma unroll
   for (int c = 0; c < W; ++c) {
     const int sz = slot(b.z + c, G.n[2], G.lo[2], G.periodic);
 #pragma unroll
     for (int bb = 0; bb < W; ++bb) {
       const int sy = slot(b.y + bb, G.n[1], G.lo[1], G.periodic);
-      double* row = grid + ((size_t)sz * G.n[1] + sy) * G.n[0];
+      unsigned long long* row = gfx + ((size_t)sz * G.n[1] + sy) * G.n[0];
 #pragma unroll
       for (int a = 0; a < W; ++a)
-        atomicAdd(row + slot(b.x + a, G.n[0], G.lo[0], G.periodic), qd * (double)(wz[c] * wy[bb] * wx[a]));
+        atomicAdd(row + slot(b.x + a, G.n[0], G.lo[0], G.periodic),
+                  (unsigned long long)__double2ll_rn(qd * (double)(wz[c] * wy[bb] * wx[a])));
     }
   }
 }
@@ -365,8 +366,7 @@ template <int ORDER>
 __global__ void __launch_bounds__(256) k_anterp_fx(const R4<float>* __restrict__ gfrac,
                                                    const int4* __restrict__ gbase,
                                                    const int* __restrict__ cell_start, AnterpArgs A, GridDims G,
-                                                   double* __restrict__ grid, const double* __restrict__ dscale,
-                                                   double factor) {
+                                                   unsigned long long* __restrict__ gfx) {
   constexpr int S = Basis<float, ORDER>::S, W = 2 * S;
   extern __shared__ unsigned char smem_raw[];
   const int PD = A.pd, np = PD * PD * PD, tid = threadIdx.x;
@@ -381,7 +381,6 @@ __global__ void __launch_bounds__(256) k_anterp_fx(const R4<float>* __restrict__
   __syncthreads();
   const int nk = nk_s;
   const int total = build_rank_list(nk, cstart, ccount, list, &tot_s);
-  const double sc = factor * (dscale ? *dscale : 1.0);
   // |q_j| <= 2^18 / (atoms in the patch) bounds the coarse sums; |q_j| < 2^10
   // keeps |t| < 2^22, where the magic-number rounding of fx_split is exact
   const float qmax = fminf(262144.0f / (float)max(total, 1), 1023.0f);
@@ -416,19 +415,20 @@ __global__ void __launch_bounds__(256) k_anterp_fx(const R4<float>* __restrict__
           }
         }
       }
-    } else {  // large charge, or outside the patch: straight to the FP64 grid
-      anterp_atom_global<ORDER>(f, b, G, grid, sc);
+    } else {  // large charge, or outside the patch: straight to the global grid
+      anterp_atom_global<ORDER>(f, b, G, gfx);
     }
   }
   if (total < 0) {  // more atoms than the list holds: one thread per atom, straight to the grid
     for (int c = 0; c < nk; ++c)
       for (int m = tid; m < ccount[c]; m += blockDim.x) {
         const int i = cstart[c] + m;
-        anterp_atom_global<ORDER>(gfrac[i], gbase[i], G, grid, sc);
+        anterp_atom_global<ORDER>(gfrac[i], gbase[i], G, gfx);
       }
   }
   __syncthreads();
-  const double ch = sc * (1.0 / 4096.0), cl = sc * (1.0 / 2147483648.0);  // 2^-12, 2^-31
+  // flush: the point's value in 2^-31 units, h 2^19 + l, added to the global
+  // fixed-point grid with an integer reduction (no FP64 arithmetic)
   for (int e = tid; e < np; e += blockDim.x) {
     const int h = phi_[e], l = plo[e];
     if ((h | l) == 0) continue;
@@ -438,8 +438,19 @@ __global__ void __launch_bounds__(256) k_anterp_fx(const R4<float>* __restrict__
       continue;
     int sx = slot(ix, G.n[0], G.lo[0], G.periodic), sy = slot(iy, G.n[1], G.lo[1], G.periodic),
         sz = slot(iz, G.n[2], G.lo[2], G.periodic);
-    atomicAdd(grid + ((size_t)sz * G.n[1] + sy) * G.n[0] + sx, (double)h * ch + (double)l * cl);
+    atomicAdd(gfx + ((size_t)sz * G.n[1] + sy) * G.n[0] + sx,
+              (unsigned long long)((long long)h * 524288LL + (long long)l));
   }
+}
+
+// Fixed-point level-0 charges (2^-31 units) to the FP64 grid, times the
+// device-side scale: one conversion per grid point.
+__global__ void k_fx_to_f64(const unsigned long long* __restrict__ gfx, double* __restrict__ q0, int64_t count,
+                            const double* __restrict__ dscale, double factor) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double sc = factor * (dscale ? *dscale : 1.0) * (1.0 / 2147483648.0);
+  q0[i] = (double)(long long)gfx[i] * sc;
 }
 
 // ---- restriction and prolongation: separable 1-D passes ----
@@ -1122,28 +1133,39 @@ void anterp_t(Plan& P, void* grid0, const double* dscale, double factor, cudaStr
                                                      dims_of(P, 0), (double*)grid0, dscale, factor);
 }
 
+// Mixed precision: patch sums into the fixed-point grid (in the restriction
+// temporary tmp[0], free until the first restriction pass), then one
+// conversion to the FP64 level-0 grid that applies the scale.
 template <int ORDER>
-void anterp_fx(Plan& P, void* grid0, const double* dscale, double factor, cudaStream_t st) {
-  AnterpArgs A = patch_args(P);
-  dim3 grid(blocks_for(P.nc[0], A.B), blocks_for(P.nc[1], A.B), blocks_for(P.nc[2], A.B));
-  size_t sm = 2 * sizeof(int) * (size_t)A.pd * A.pd * A.pd;  // coarse and residual sums
-  k_anterp_fx<ORDER><<<grid, 256, sm, st>>>((const R4<float>*)P.d.gfrac, P.d.gbase, P.d.cell_start, A,
-                                            dims_of(P, 0), (double*)grid0, dscale, factor);
+void anterp_fx(Plan& P, int64_t n, void* grid0, const double* dscale, double factor, cudaStream_t st) {
+  const int64_t np = grid_points(P, 0);
+  auto* gfx = (unsigned long long*)P.d.tmp[0];
+  cudaMemsetAsync(gfx, 0, sizeof(unsigned long long) * (size_t)np, st);
+  P.launches += 2;
+  if (n > 0) {
+    AnterpArgs A = patch_args(P);
+    dim3 grid(blocks_for(P.nc[0], A.B), blocks_for(P.nc[1], A.B), blocks_for(P.nc[2], A.B));
+    size_t sm = 2 * sizeof(int) * (size_t)A.pd * A.pd * A.pd;  // coarse and residual sums
+    k_anterp_fx<ORDER><<<grid, 256, sm, st>>>((const R4<float>*)P.d.gfrac, P.d.gbase, P.d.cell_start, A,
+                                              dims_of(P, 0), gfx);
+    P.launches += 1;
+  }
+  k_fx_to_f64<<<blocks_for(np, 256), 256, 0, st>>>(gfx, (double*)grid0, np, dscale, factor);
 }
 
 cudaError_t launch_anterpolate(Plan& P, int64_t n, void* grid0, const double* dscale, double factor,
                                cudaStream_t st) {
+  if (!P.fp64) {
+    if (P.P.order == 3) anterp_fx<3>(P, n, grid0, dscale, factor, st);
+    else anterp_fx<5>(P, n, grid0, dscale, factor, st);
+    return cudaGetLastError();
+  }
   size_t bytes = sizeof(double) * (size_t)grid_points(P, 0);
   cudaMemsetAsync(grid0, 0, bytes, st);
   P.launches += 1 + (n > 0 ? 1 : 0);
   if (n <= 0) return cudaGetLastError();
-  if (P.fp64) {
-    if (P.P.order == 3) anterp_t<double, double, 3>(P, grid0, dscale, factor, st);
-    else anterp_t<double, double, 5>(P, grid0, dscale, factor, st);
-  } else {
-    if (P.P.order == 3) anterp_fx<3>(P, grid0, dscale, factor, st);
-    else anterp_fx<5>(P, grid0, dscale, factor, st);
-  }
+  if (P.P.order == 3) anterp_t<double, double, 3>(P, grid0, dscale, factor, st);
+  else anterp_t<double, double, 5>(P, grid0, dscale, factor, st);
   return cudaGetLastError();
 }
 

@@ -118,6 +118,12 @@ struct Plan {
   int64_t cap = 0;
   int nblk_partial = 0;
   DeviceBuffers d;
+  // concurrency: the grid passes of a forward evaluation run on `side` (a
+  // plan-owned stream of the highest priority) while the pair sums run on the
+  // caller's stream; fork and join are event waits
+  bool overlap = true;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // state
   cudaStream_t last_stream = nullptr;
   int64_t last_n = -1;

@@ -482,6 +482,12 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
     if (upload(&D.seg2, segs2) != cudaSuccess) return MSM_ERR_OOM;
   }
   if (upload((void**)&D.seg_start, start) != cudaSuccess) return MSM_ERR_OOM;
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&P->side, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return MSM_ERR_CUDA;
   return MSM_OK;
 }
 
@@ -502,6 +508,11 @@ void free_plan(Plan* P) {
     if (D.au[k]) cudaFree(D.au[k]);
   }
   D = DeviceBuffers();
+  if (P->side) cudaStreamDestroy(P->side);
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  if (P->ev_join) cudaEventDestroy(P->ev_join);
+  P->side = nullptr;
+  P->ev_fork = P->ev_join = nullptr;
 }
 
 }  // namespace msm

@@ -285,3 +285,22 @@ def test_anterpolation_large_and_mixed_charges(dev):
     ref = O.msm(oparams(cfg), pos, q)
     for precision in ["fp64", "mixed"]:
         assert_close(gpu_eval(plan_for(cfg, precision, len(q)), pos, q, dev), ref, precision, precision)
+
+
+def test_overlap_on_and_off_agree(dev):
+    """The forward pass with the grid passes on the plan's side stream
+    (concurrent with the pair sums) and with every stage in turn on the
+    caller's stream: same results up to the rounding order of atomic sums,
+    and both match the oracle."""
+    cfg = dict(box=30.0, periodic=True, cutoff=9.0, spacing=2.0, order=5, split=2)
+    pos, q = make_water_box(30.0, 850, 3, 3, seed=27, periodic=True)
+    ref = O.msm(oparams(cfg), pos, q)
+    for precision, tol in [("fp64", 1e-13), ("mixed", 1e-6)]:
+        plan = plan_for(cfg, precision, len(q))
+        plan.set_overlap(False)
+        a = gpu_eval(plan, pos, q, dev)
+        plan.set_overlap(True)
+        b = gpu_eval(plan, pos, q, dev)
+        assert abs(a[0] - b[0]) <= tol * abs(a[0])
+        assert rel_rms(a[2], b[2]) <= tol and rel_rms(a[1], b[1]) <= tol
+        assert_close(b, ref, precision, precision)
