@@ -959,15 +959,24 @@ __device__ __forceinline__ void interp_patch_atom(const R4<T>& f, const int4& b,
   }
 }
 
-// Stages the patch of u^0 for the block at cell block c0; returns the atom
-// count of the block's rank-major list (-1 when it does not fit).
+// Lists the block's atoms (rank-major, then bank-ordered with the patch as
+// scratch: the gathers of one warp instruction then read 32 different banks)
+// and stages the patch of u^0 for the block at cell block c0.  Returns the
+// slot count of the list (unfilled slots hold -1), or -1 when the block holds
+// more atoms than the list takes.
 template <typename T>
 __device__ __forceinline__ int stage_interp_block(const AnterpArgs& A, const int* __restrict__ cell_start,
-                                                  const T* __restrict__ u0, const GridDims& G, T* patch, int lo0,
-                                                  int lo1, int lo2, int* cstart, int* ccount, int* list, int* nk_s,
-                                                  int* tot_s) {
+                                                  const int4* __restrict__ gbase, const T* __restrict__ u0,
+                                                  const GridDims& G, T* patch, int lo0, int lo1, int lo2, int* cstart,
+                                                  int* ccount, int* list, int* nk_s, int* tot_s) {
   const int PD = A.pd, np = PD * PD * PD;
   const int c0[3] = {(int)blockIdx.x * A.B, (int)blockIdx.y * A.B, (int)blockIdx.z * A.B};
+  if (threadIdx.x == 0) *nk_s = block_cells(A, cell_start, c0, cstart, ccount);
+  __syncthreads();
+  int total = build_rank_list(*nk_s, cstart, ccount, list, tot_s);
+  if (total >= 0)
+    total = bank_order(list, total, gbase, lo0, lo1, lo2, PD, reinterpret_cast<int*>(patch),
+                       np * (int)(sizeof(T) / sizeof(int)));
   for (int e = threadIdx.x; e < np; e += blockDim.x) {
     int ix = lo0 + e % PD, iy = lo1 + (e / PD) % PD, iz = lo2 + e / (PD * PD);
     T v = T(0);
@@ -979,9 +988,8 @@ __device__ __forceinline__ int stage_interp_block(const AnterpArgs& A, const int
     }
     patch[e] = v;
   }
-  if (threadIdx.x == 0) *nk_s = block_cells(A, cell_start, c0, cstart, ccount);
   __syncthreads();
-  return build_rank_list(*nk_s, cstart, ccount, list, tot_s);
+  return total;
 }
 
 template <typename T, int ORDER, typename OUT>
@@ -993,13 +1001,13 @@ __global__ void __launch_bounds__(256) k_interp_fwd(
   constexpr int S = Basis<T, ORDER>::S;
   extern __shared__ unsigned char smem_raw[];
   T* patch = reinterpret_cast<T*>(smem_raw);
-  __shared__ int cstart[64], ccount[64], list[kAnterpMaxAtoms], nk_s, tot_s;
+  __shared__ int cstart[64], ccount[64], list[kAnterpMaxAtoms + 32], nk_s, tot_s;  // + one round of slots
   const int c0[3] = {(int)blockIdx.x * AA.B, (int)blockIdx.y * AA.B, (int)blockIdx.z * AA.B};
   const int lo0 = (int)floor(c0[0] * AA.cw_h[0]) - S - 1;
   const int lo1 = (int)floor(c0[1] * AA.cw_h[1]) - S - 1;
   const int lo2 = (int)floor(c0[2] * AA.cw_h[2]) - S - 1;
-  const int total = stage_interp_block<T>(AA, cell_start, u0, G, patch, lo0, lo1, lo2, cstart, ccount, list, &nk_s,
-                                          &tot_s);
+  const int total = stage_interp_block<T>(AA, cell_start, gbase, u0, G, patch, lo0, lo1, lo2, cstart, ccount, list,
+                                          &nk_s, &tot_s);
   const T ih[3] = {T(A.inv_h[0]), T(A.inv_h[1]), T(A.inv_h[2])};
   double e = 0.0;
   const int nk = nk_s;
@@ -1011,6 +1019,7 @@ __global__ void __launch_bounds__(256) k_interp_fwd(
     if (total >= 0) {
       if (kk >= nlist) break;
       i = list[kk];
+      if (i < 0) continue;  // unfilled slot of the bank-ordered list
     } else {
       while (walk_c < nk && walk_m >= ccount[walk_c]) walk_m -= ccount[walk_c++];
       if (walk_c >= nk) break;
@@ -1048,13 +1057,13 @@ __global__ void __launch_bounds__(256) k_interp_bwd(
   constexpr int S = Basis<T, ORDER>::S;
   extern __shared__ unsigned char smem_raw[];
   T* patch = reinterpret_cast<T*>(smem_raw);
-  __shared__ int cstart[64], ccount[64], list[kAnterpMaxAtoms], nk_s, tot_s;
+  __shared__ int cstart[64], ccount[64], list[kAnterpMaxAtoms + 32], nk_s, tot_s;  // + one round of slots
   const int c0[3] = {(int)blockIdx.x * AA.B, (int)blockIdx.y * AA.B, (int)blockIdx.z * AA.B};
   const int lo0 = (int)floor(c0[0] * AA.cw_h[0]) - S - 1;
   const int lo1 = (int)floor(c0[1] * AA.cw_h[1]) - S - 1;
   const int lo2 = (int)floor(c0[2] * AA.cw_h[2]) - S - 1;
-  const int total = stage_interp_block<T>(AA, cell_start, av0, G, patch, lo0, lo1, lo2, cstart, ccount, list, &nk_s,
-                                          &tot_s);
+  const int total = stage_interp_block<T>(AA, cell_start, gbase, av0, G, patch, lo0, lo1, lo2, cstart, ccount,
+                                          list, &nk_s, &tot_s);
   const T ih[3] = {T(A.inv_h[0]), T(A.inv_h[1]), T(A.inv_h[2])};
   const T gg = (T)*gE;
   const int nk = nk_s, nlist = total >= 0 ? total : 0;
@@ -1064,6 +1073,7 @@ __global__ void __launch_bounds__(256) k_interp_bwd(
     if (total >= 0) {
       if (kk >= nlist) break;
       i = list[kk];
+      if (i < 0) continue;  // unfilled slot of the bank-ordered list
     } else {
       while (walk_c < nk && walk_m >= ccount[walk_c]) walk_m -= ccount[walk_c++];
       if (walk_c >= nk) break;
