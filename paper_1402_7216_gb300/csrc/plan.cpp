@@ -235,7 +235,7 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   if (trc != MSM_OK) return trc;
   msm_tuning TU = {0, 0, 0};
   if (tune) TU = *tune;
-  const double fill = TU.cell_fill > 0 ? TU.cell_fill : 26.0;
+  const double fill = TU.cell_fill > 0 ? TU.cell_fill : 24.0;
   P->lattice_waves = TU.lattice_waves > 0 ? TU.lattice_waves : 4;
   for (int d = 0; d < 3; ++d)
     if (!(p.box[d] > 0.0) || !std::isfinite(p.box[d])) return MSM_ERR_INVALID_ARG;
@@ -260,7 +260,7 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   P->gamma0 = smooth(p.splitting, 0.0);
 
   // short-range cells: width >= a/2 (neighbours within two cells), widened
-  // toward ~26 atoms per cell (tunable) at the plan's capacity density so that the 32
+  // toward ~24 atoms per cell (tunable) at the plan's capacity density so that the 32
   // lanes of a warp stay busy (the bounding-box culling absorbs the larger
   // candidate volume)
   double vol = p.box[0] * p.box[1] * p.box[2];
