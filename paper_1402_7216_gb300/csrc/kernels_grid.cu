@@ -651,10 +651,32 @@ __global__ void __launch_bounds__(128) k_lattice(const T* __restrict__ q, T* __r
   }
 }
 
+// Window offsets of a block, computed once (the periodic wrap costs integer
+// divisions): col[xx] = grid x index of window column xx (-1 outside an open
+// grid), row[yy] = (grid y index) * n_x (-1 outside).
+__device__ __forceinline__ void window_offsets(const GridDims& G, int x0, int y0, int Ex, int Ey, int SXw, int SY,
+                                               int* col, int* row) {
+  for (int t = threadIdx.x; t < SXw + SY; t += blockDim.x) {
+    const bool isx = t < SXw;
+    const int d = isx ? 0 : 1, n = G.n[d];
+    int g = isx ? x0 - Ex + t : y0 - Ey + (t - SXw);
+    if (G.periodic) {
+      g %= n;
+      if (g < 0) g += n;
+    } else if (g < 0 || g >= n) {
+      g = -1;
+    }
+    if (isx) col[t] = g;
+    else row[t - SXw] = g < 0 ? -1 : g * G.n[0];
+  }
+}
+
 // Asynchronous staging of one plane (cp.async: global -> shared without
 // registers); points outside an open grid are zero-filled (source size 0).
+// Each thread walks the window with a fixed stride of blockDim.x elements,
+// stepping its (row, column) incrementally.
 __device__ __forceinline__ void stage_plane_async(float* plane, const float* __restrict__ q, const GridDims& G,
-                                                  int zi, int x0, int y0, int Ex, int Ey, int SXw, int SX, int SY) {
+                                                  int zi, const int* col, const int* row, int SXw, int SX, int SY) {
   int gz;
   bool zok;
   if (G.periodic) {
@@ -665,22 +687,21 @@ __device__ __forceinline__ void stage_plane_async(float* plane, const float* __r
     gz = zi;
     zok = (zi >= 0 && zi < G.n[2]);
   }
-  for (int e = threadIdx.x; e < SY * SXw; e += blockDim.x) {
-    int xx = e % SXw, yy = e / SXw;
-    int gx = x0 - Ex + xx, gy = y0 - Ey + yy;
-    bool ok;
-    if (G.periodic) {
-      gx %= G.n[0];
-      if (gx < 0) gx += G.n[0];
-      gy %= G.n[1];
-      if (gy < 0) gy += G.n[1];
-      ok = true;
-    } else {
-      ok = zok && gx >= 0 && gx < G.n[0] && gy >= 0 && gy < G.n[1];
-    }
-    const float* src = ok ? q + ((size_t)gz * G.n[1] + gy) * G.n[0] + gx : q;
+  const float* qz = q + (size_t)(zok ? gz : 0) * G.n[1] * G.n[0];
+  const int step = blockDim.x, dyy = step / SXw, dxx = step - dyy * SXw;
+  int xx = threadIdx.x % SXw, yy = threadIdx.x / SXw;
+  for (; yy < SY; ) {
+    const int gx = col[xx], go = row[yy];
+    const bool ok = zok && gx >= 0 && go >= 0;
+    const float* src = ok ? qz + go + gx : q;
     unsigned dst = (unsigned)__cvta_generic_to_shared(plane + yy * SX + xx);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0));
+    xx += dxx;
+    yy += dyy;
+    if (xx >= SXw) {
+      xx -= SXw;
+      ++yy;
+    }
   }
 }
 
@@ -697,6 +718,8 @@ __global__ void __launch_bounds__(128) k_lattice_f2(const float* __restrict__ q,
   const int SXw = LBX + 2 * Ex + kSeg, SX = SXw | 1, SY = LBY + 2 * Ey;
   float* buf0 = reinterpret_cast<float*>(smem_raw);
   float* buf1 = buf0 + SX * SY;
+  int* col = reinterpret_cast<int*>(buf1 + SX * SY);  // window offsets (SXw + SY ints)
+  int* row = col + SXw;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tx = lane & 3, ty = lane >> 2;
   const int bz = blockIdx.z % L.nbz, part = blockIdx.z / L.nbz;
   const int x0 = blockIdx.x * LBX, y0 = blockIdx.y * LBY, z0 = bz * LBZ, zo = z0 + warp;
@@ -705,12 +728,14 @@ __global__ void __launch_bounds__(128) k_lattice_f2(const float* __restrict__ q,
   float2 acc[LPX];  // (row ty, row ty + 8) of the 8 x outputs
 #pragma unroll
   for (int j = 0; j < LPX; ++j) acc[j] = make_float2(0.f, 0.f);
-  if (zbeg < zend) stage_plane_async(buf0, q, G, zbeg, x0, y0, Ex, Ey, SXw, SX, SY);
+  window_offsets(G, x0, y0, Ex, Ey, SXw, SY, col, row);
+  __syncthreads();
+  if (zbeg < zend) stage_plane_async(buf0, q, G, zbeg, col, row, SXw, SX, SY);
   asm volatile("cp.async.commit_group;\n" ::);
   for (int zi = zbeg; zi < zend; ++zi) {
     float* cur = ((zi - zbeg) & 1) ? buf1 : buf0;
     float* nxt = ((zi - zbeg) & 1) ? buf0 : buf1;
-    if (zi + 1 < zend) stage_plane_async(nxt, q, G, zi + 1, x0, y0, Ex, Ey, SXw, SX, SY);
+    if (zi + 1 < zend) stage_plane_async(nxt, q, G, zi + 1, col, row, SXw, SX, SY);
     asm volatile("cp.async.commit_group;\n" ::);
     asm volatile("cp.async.wait_group 1;\n" ::);  // plane zi has landed (this thread's copies)
     __syncthreads();                               // ... and everyone else's
@@ -1271,7 +1296,8 @@ void lattice_t(Plan& P, int k, const double* qk64, T* uk, cudaStream_t st) {
   }
   dim3 grid(blocks_for(G.n[0], LBX), blocks_for(G.n[1], LBY), L.nbz * L.nsplit);
   int SX = (LBX + 2 * P.E[0] + kSeg) | 1, SY = LBY + 2 * P.E[1];
-  size_t sm = sizeof(T) * SX * SY * (f32 ? 2 : 1);  // FP32 double-buffers its planes
+  // FP32 double-buffers its planes and keeps the window offsets (SXw + SY ints)
+  size_t sm = f32 ? sizeof(float) * 2 * SX * SY + sizeof(int) * (LBX + 2 * P.E[0] + kSeg + SY) : sizeof(T) * SX * SY;
   T scale = (T)std::ldexp(1.0, -k);
   if (f32) {
     k_lattice_f2<<<grid, 128, sm, st>>>((const float*)qk, (float*)uk, G, (const Segment2*)P.d.seg2, P.d.seg_start,
@@ -1364,6 +1390,7 @@ cudaError_t configure_kernels() {
     cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (r != cudaSuccess) e = r;
   };
+  set((const void*)k_lattice_f2);
   set((const void*)k_anterp_fx<3>);
   set((const void*)k_anterp_fx<5>);
   set((const void*)k_anterp_patch<double, double, 3>);
