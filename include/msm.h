@@ -80,7 +80,7 @@ typedef struct {
  *                 of anterpolation and interpolation (default: the largest of
  *                 4, 3, 2, 1 whose patch fits)
  *   lattice_waves blocks per SM the lattice cutoff aims for when it splits the
- *                 stencil planes of a small level over several blocks (default 4)
+ *                 stencil planes of a small level over several blocks (default 8)
  * Ranges: cell_fill 0..256, patch_cells 0..4, lattice_waves 0..64; anything
  * else is INVALID_ARG (checked on the host before any device call). */
 typedef struct {

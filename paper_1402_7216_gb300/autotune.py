@@ -17,7 +17,7 @@ import torch
 
 from . import MSM
 
-SEARCH = [("cell_fill", [20, 24, 28, 32]), ("patch_cells", [2, 3, 4]), ("lattice_waves", [2, 4, 8])]
+SEARCH = [("cell_fill", [20, 24, 28, 32]), ("patch_cells", [2, 3, 4]), ("lattice_waves", [4, 8, 16])]
 
 
 def cache_path():

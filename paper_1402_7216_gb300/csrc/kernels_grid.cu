@@ -548,6 +548,8 @@ __global__ void k_prolong_axis(const T* __restrict__ in, T* __restrict__ out, Ax
 //   FP32: two rows per lane (LBY = 16) packed into float2, one FFMA2 per two
 //         outputs, coefficients stored pre-duplicated as float2 pairs.
 constexpr int LBX = 32, LBZ = 4, LPX = 8;
+constexpr int kLatticeLP = 8;   // x outputs per lane of the FP32 lattice kernel (8 or 16)
+constexpr int kLatticeZ = 4;    // warps (output planes) per block of the FP32 lattice kernel
 
 template <typename T>
 __device__ __forceinline__ void two_sum_add(T& s, T& c, T x) {
@@ -705,14 +707,20 @@ __device__ __forceinline__ void stage_plane_async(float* plane, const float* __r
   }
 }
 
-// FP32: two rows per lane packed into float2 (one FFMA2 per two outputs),
-// coefficients pre-duplicated as float2 pairs, the next input plane staged by
-// cp.async while the current one is applied (double buffer).  Each plane's
-// partial sums are added into the totals (blocked summation over planes).
-__global__ void __launch_bounds__(128) k_lattice_f2(const float* __restrict__ q, float* __restrict__ u, GridDims G,
+// FP32: each lane owns LP consecutive x outputs of two rows TYN apart, packed
+// into float2 (one FFMA2 per two outputs); a warp covers 32 (x) x 2 TYN (y)
+// of one plane (TYN = 32 LP / 32 rows of lanes).  Coefficients are stored
+// pre-duplicated as float2 pairs; the next input plane is staged by cp.async
+// while the current one is applied (double buffer).  A segment of 8 taps is
+// applied as a sliding window: input column k feeds the outputs j = k - t of
+// every tap t, so one pair of shared loads serves up to 8 FFMA2 (LP + 7 loads
+// per 8 LP FFMA2).  Each plane's partial sums are added into the totals
+// (blocked summation over planes).
+template <int LP>
+__global__ void __launch_bounds__(32 * kLatticeZ) k_lattice_f2(const float* __restrict__ q, float* __restrict__ u, GridDims G,
                                                     const Segment2* __restrict__ seg,
                                                     const int* __restrict__ seg_start, LatticeArgs L, float scale) {
-  constexpr int LBY = 16;
+  constexpr int TXN = LBX / LP, TYN = 32 / TXN, LBY = 2 * TYN;
   extern __shared__ unsigned char smem_raw[];
   const int Ex = L.Ex, Ey = L.Ey, Ez = L.Ez;
   const int SXw = LBX + 2 * Ex + kSeg, SX = SXw | 1, SY = LBY + 2 * Ey;
@@ -720,14 +728,14 @@ __global__ void __launch_bounds__(128) k_lattice_f2(const float* __restrict__ q,
   float* buf1 = buf0 + SX * SY;
   int* col = reinterpret_cast<int*>(buf1 + SX * SY);  // window offsets (SXw + SY ints)
   int* row = col + SXw;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tx = lane & 3, ty = lane >> 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tx = lane % TXN, ty = lane / TXN;
   const int bz = blockIdx.z % L.nbz, part = blockIdx.z / L.nbz;
-  const int x0 = blockIdx.x * LBX, y0 = blockIdx.y * LBY, z0 = bz * LBZ, zo = z0 + warp;
-  const int nplanes = LBZ + 2 * Ez, per = (nplanes + L.nsplit - 1) / L.nsplit;
+  const int x0 = blockIdx.x * LBX, y0 = blockIdx.y * LBY, z0 = bz * kLatticeZ, zo = z0 + warp;
+  const int nplanes = kLatticeZ + 2 * Ez, per = (nplanes + L.nsplit - 1) / L.nsplit;
   const int zbeg = z0 - Ez + part * per, zend = min(z0 - Ez + nplanes, zbeg + per);
-  float2 acc[LPX];  // (row ty, row ty + 8) of the 8 x outputs
+  float2 acc[LP];  // (row ty, row ty + TYN) of the LP x outputs
 #pragma unroll
-  for (int j = 0; j < LPX; ++j) acc[j] = make_float2(0.f, 0.f);
+  for (int j = 0; j < LP; ++j) acc[j] = make_float2(0.f, 0.f);
   window_offsets(G, x0, y0, Ex, Ey, SXw, SY, col, row);
   __syncthreads();
   if (zbeg < zend) stage_plane_async(buf0, q, G, zbeg, col, row, SXw, SX, SY);
@@ -741,24 +749,24 @@ __global__ void __launch_bounds__(128) k_lattice_f2(const float* __restrict__ q,
     __syncthreads();                               // ... and everyone else's
     const int dz = zi - zo;
     if (dz >= -Ez && dz <= Ez && zo < G.n[2]) {  // warp-uniform
-      float2 part_[LPX];
+      float2 part_[LP];
 #pragma unroll
-      for (int j = 0; j < LPX; ++j) part_[j] = make_float2(0.f, 0.f);
+      for (int j = 0; j < LP; ++j) part_[j] = make_float2(0.f, 0.f);
       const int s1 = seg_start[dz + Ez + 1];
       for (int s = seg_start[dz + Ez]; s < s1; ++s) {
         const Segment2 sg = seg[s];
-        const float* r0 = cur + (ty + Ey + sg.dy) * SX + tx * LPX + Ex + sg.dx0;
-        const float* r1 = r0 + 8 * SX;
-        float2 win[LPX + kSeg - 1];
+        const float* r0 = cur + (ty + Ey + sg.dy) * SX + tx * LP + Ex + sg.dx0;
+        const float* r1 = r0 + TYN * SX;
 #pragma unroll
-        for (int k = 0; k < LPX + kSeg - 1; ++k) win[k] = make_float2(r0[k], r1[k]);
+        for (int k = 0; k < LP + kSeg - 1; ++k) {
+          const float2 w = make_float2(r0[k], r1[k]);
 #pragma unroll
-        for (int k = 0; k < kSeg; ++k)
-#pragma unroll
-          for (int j = 0; j < LPX; ++j) part_[j] = __ffma2_rn(sg.g[k], win[j + k], part_[j]);
+          for (int t = 0; t < kSeg; ++t)
+            if (k - t >= 0 && k - t < LP) part_[k - t] = __ffma2_rn(sg.g[t], w, part_[k - t]);
+        }
       }
 #pragma unroll
-      for (int j = 0; j < LPX; ++j) acc[j] = __fadd2_rn(acc[j], part_[j]);
+      for (int j = 0; j < LP; ++j) acc[j] = __fadd2_rn(acc[j], part_[j]);
     }
     __syncthreads();  // the buffer just read is restaged two planes from now
   }
@@ -766,11 +774,11 @@ __global__ void __launch_bounds__(128) k_lattice_f2(const float* __restrict__ q,
   if (zo >= G.n[2]) return;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
-    const int y = y0 + ty + 8 * r;
+    const int y = y0 + ty + TYN * r;
     if (y >= G.n[1]) continue;
 #pragma unroll
-    for (int j = 0; j < LPX; ++j) {
-      int x = x0 + tx * LPX + j;
+    for (int j = 0; j < LP; ++j) {
+      int x = x0 + tx * LP + j;
       if (x >= G.n[0]) continue;
       float v = scale * (r == 0 ? acc[j].x : acc[j].y);
       if (L.nsplit > 1) atomicAdd(u + ((size_t)zo * G.n[1] + y) * G.n[0] + x, v);
@@ -1281,15 +1289,16 @@ void lattice_t(Plan& P, int k, const double* qk64, T* uk, cudaStream_t st) {
     P.launches += 1;
     qk = (const T*)qf;
   }
-  const int LBY = f32 ? 16 : 8;
+  const int LBY = f32 ? 2 * (32 / (LBX / kLatticeLP)) : 8;
   LatticeArgs L;
   L.Ex = P.E[0];
   L.Ey = P.E[1];
   L.Ez = P.E[2];
-  L.nbz = (int)blocks_for(G.n[2], LBZ);
+  const int LBZb = f32 ? kLatticeZ : LBZ;  // output planes (warps) per block
+  L.nbz = (int)blocks_for(G.n[2], LBZb);
   int64_t bricks = (int64_t)blocks_for(G.n[0], LBX) * blocks_for(G.n[1], LBY) * L.nbz;
-  const int64_t target = (int64_t)P.lattice_waves * 152;
-  L.nsplit = (int)std::min<int64_t>(LBZ + 2 * L.Ez, std::max<int64_t>(1, (target + bricks - 1) / bricks));
+  const int64_t target = (int64_t)P.lattice_waves * 152 * 4 / LBZb;
+  L.nsplit = (int)std::min<int64_t>(LBZb + 2 * L.Ez, std::max<int64_t>(1, (target + bricks - 1) / bricks));
   if (L.nsplit > 1) {
     cudaMemsetAsync(uk, 0, sizeof(T) * (size_t)grid_points(P, k), st);
     P.launches += 1;
@@ -1300,7 +1309,7 @@ void lattice_t(Plan& P, int k, const double* qk64, T* uk, cudaStream_t st) {
   size_t sm = f32 ? sizeof(float) * 2 * SX * SY + sizeof(int) * (LBX + 2 * P.E[0] + kSeg + SY) : sizeof(T) * SX * SY;
   T scale = (T)std::ldexp(1.0, -k);
   if (f32) {
-    k_lattice_f2<<<grid, 128, sm, st>>>((const float*)qk, (float*)uk, G, (const Segment2*)P.d.seg2, P.d.seg_start,
+    k_lattice_f2<kLatticeLP><<<grid, 32 * kLatticeZ, sm, st>>>((const float*)qk, (float*)uk, G, (const Segment2*)P.d.seg2, P.d.seg_start,
                                         L, (float)scale);
   } else {
     k_lattice<T, false><<<grid, 128, sm, st>>>(qk, uk, G, (const Segment<T>*)P.d.seg, P.d.seg_start, L, scale);
@@ -1390,7 +1399,7 @@ cudaError_t configure_kernels() {
     cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (r != cudaSuccess) e = r;
   };
-  set((const void*)k_lattice_f2);
+  set((const void*)k_lattice_f2<kLatticeLP>);
   set((const void*)k_anterp_fx<3>);
   set((const void*)k_anterp_fx<5>);
   set((const void*)k_anterp_patch<double, double, 3>);

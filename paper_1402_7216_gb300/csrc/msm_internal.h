@@ -105,7 +105,7 @@ struct Plan {
   // anterpolation patches: blocks of ablk^3 cells, patches of apd^3 points
   int ablk = 1, apd = 1;
   // lattice: blocks per SM to aim for when splitting a small level's planes
-  int lattice_waves = 4;
+  int lattice_waves = 8;
   // smoothing constants
   double gamma0 = 0.0;         // gamma(0)
   // level stencil

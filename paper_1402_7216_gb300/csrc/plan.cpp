@@ -236,7 +236,7 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   msm_tuning TU = {0, 0, 0};
   if (tune) TU = *tune;
   const double fill = TU.cell_fill > 0 ? TU.cell_fill : 24.0;
-  P->lattice_waves = TU.lattice_waves > 0 ? TU.lattice_waves : 4;
+  P->lattice_waves = TU.lattice_waves > 0 ? TU.lattice_waves : 8;
   for (int d = 0; d < 3; ++d)
     if (!(p.box[d] > 0.0) || !std::isfinite(p.box[d])) return MSM_ERR_INVALID_ARG;
   if (!(p.cutoff > 0.0) || !(p.spacing > 0.0) || !std::isfinite(p.cutoff) || !std::isfinite(p.spacing))
