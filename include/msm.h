@@ -181,10 +181,15 @@ int msm_eval_backward_batch(const msm_handle* plans, int nrep, const int64_t* of
 
 /* A batched forward (and, when grad_energies is not NULL, its adjoint)
  * captured once into an instantiated CUDA graph on the given buffers; every
- * msm_graph_launch replays all kernels of all replicas with one launch.  The
+ * msm_graph_launch replays all kernels of all replicas with one launch.  When
+ * every plan is MSM_MIXED with one interpolation order and one splitting,
+ * each stage is a single kernel launch over all replicas (a block finds its
+ * replica in a table of per-replica arguments built here), the pair sums of
+ * all replicas running concurrently with their grid passes; otherwise the
+ * replicas' own launch sequences are forked over library streams.  The
  * buffers and plans must outlive the graph; inputs may change between
- * replays (same sizes).  Creating the graph runs nothing.
- * Errors: INVALID_ARG, TOO_MANY_ATOMS, OOM, CUDA. */
+ * replays (same sizes).  Creating the graph uploads the tables (synchronous)
+ * and runs no kernel.  Errors: INVALID_ARG, TOO_MANY_ATOMS, OOM, CUDA. */
 typedef struct msm_graph* msm_graph_handle;
 int msm_batch_graph_create(const msm_handle* plans, int nrep, const int64_t* offsets, const double* pos,
                            const double* q, double* energies, double* phi, double* force,

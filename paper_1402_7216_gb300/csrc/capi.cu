@@ -211,7 +211,78 @@ cudaError_t g_config_err = cudaSuccess;
 struct msm_graph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // batched form: the argument tables of the batched stages and the stream
+  // that carries the grid passes during the capture
+  BinBatch* bin = nullptr;
+  PairBatch* pair = nullptr;
+  GridBatch* grid = nullptr;
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
+
+namespace {
+
+// The batched form needs one kernel family for every replica: mixed
+// precision, one interpolation order, one splitting.
+bool batchable(const msm_handle* plans, int nrep) {
+  for (int r = 0; r < nrep; ++r) {
+    const Plan& P = plans[r]->p;
+    if (P.fp64 || P.P.order != plans[0]->p.P.order || P.P.splitting != plans[0]->p.P.splitting) return false;
+  }
+  return true;
+}
+
+// Builds the argument tables of the batched stages (synchronous; allocates).
+int batch_tables(msm_graph* g, const msm_handle* plans, int nrep, const int64_t* off, const double* pos,
+                 const double* q, double* energies, double* phi, double* force, const double* grad_energies,
+                 double* grad_pos, double* grad_q) {
+  std::vector<BatchRep> reps;
+  for (int r = 0; r < nrep; ++r) {
+    const int64_t o = off[r];
+    BatchRep b;
+    b.plan = &plans[r]->p;
+    b.n = off[r + 1] - o;
+    b.pos = pos + 3 * o;
+    b.q = q + o;
+    b.energy = energies + r;
+    b.phi = phi ? phi + o : nullptr;
+    b.force = force ? force + 3 * o : nullptr;
+    b.grad_energy = grad_energies ? grad_energies + r : nullptr;
+    b.grad_pos = grad_pos ? grad_pos + 3 * o : nullptr;
+    b.grad_q = grad_q ? grad_q + o : nullptr;
+    reps.push_back(b);
+  }
+  int least = 0, greatest = 0;
+  if (bin_batch_build(reps, &g->bin) != cudaSuccess || pair_batch_build(reps, &g->pair) != cudaSuccess ||
+      grid_batch_build(reps, grad_energies != nullptr, &g->grid) != cudaSuccess ||
+      cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&g->side, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->join, cudaEventDisableTiming) != cudaSuccess)
+    return MSM_ERR_CUDA;
+  for (int r = 0; r < nrep; ++r) plans[r]->p.last_n = off[r + 1] - off[r];
+  return MSM_OK;
+}
+
+// The batched forward (and adjoint) on cs: binning of every replica, then the
+// pair sums of every replica on cs concurrently with the grid passes of every
+// replica on the high-priority side stream, then interpolation; each stage is
+// one launch over all replicas.
+int batch_fused(msm_graph* g, cudaStream_t cs, bool backward) {
+  cudaError_t e = bin_batch_launch(g->bin, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(g->fork, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(g->side, g->fork, 0);
+  if (e == cudaSuccess) e = grid_batch_sweep(g->grid, false, g->side);
+  if (e == cudaSuccess) e = cudaEventRecord(g->join, g->side);
+  if (e == cudaSuccess) e = pair_batch_launch(g->pair, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, g->join, 0);
+  if (e == cudaSuccess) e = grid_batch_interp(g->grid, false, cs);
+  if (e == cudaSuccess && backward) e = grid_batch_sweep(g->grid, true, cs);
+  if (e == cudaSuccess && backward) e = grid_batch_interp(g->grid, true, cs);
+  return e == cudaSuccess ? MSM_OK : MSM_ERR_CUDA;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -321,11 +392,18 @@ int msm_batch_graph_create(const msm_handle* plans, int nrep, const int64_t* off
     cudaStreamDestroy(cs);
     return MSM_ERR_OOM;
   }
-  rc = MSM_OK;
-  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = MSM_ERR_CUDA;
+  const bool fused = batchable(plans, nrep);
+  rc = fused ? batch_tables(g, plans, nrep, offsets, pos, q, energies, phi, force, grad_energies, grad_pos, grad_q)
+             : MSM_OK;
+  if (rc == MSM_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = MSM_ERR_CUDA;
   if (rc == MSM_OK) {
-    rc = batch_forward(plans, nrep, offsets, pos, q, energies, phi, force, cs);
-    if (rc == MSM_OK && grad_energies) rc = batch_backward(plans, nrep, offsets, grad_energies, grad_pos, grad_q, cs);
+    if (fused) {
+      rc = batch_fused(g, cs, grad_energies != nullptr);
+    } else {
+      rc = batch_forward(plans, nrep, offsets, pos, q, energies, phi, force, cs);
+      if (rc == MSM_OK && grad_energies)
+        rc = batch_backward(plans, nrep, offsets, grad_energies, grad_pos, grad_q, cs);
+    }
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &graph);  // always end the capture
     if (rc == MSM_OK && e != cudaSuccess) rc = MSM_ERR_CUDA;
@@ -350,6 +428,13 @@ void msm_graph_destroy(msm_graph_handle g) {
   if (!g) return;
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->bin || g->pair || g->grid) cudaDeviceSynchronize();  // the tables may be in use by a launched graph
+  bin_batch_free(g->bin);
+  pair_batch_free(g->pair);
+  grid_batch_free(g->grid);
+  if (g->side) cudaStreamDestroy(g->side);
+  if (g->fork) cudaEventDestroy(g->fork);
+  if (g->join) cudaEventDestroy(g->join);
   delete g;
 }
 

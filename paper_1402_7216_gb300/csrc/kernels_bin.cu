@@ -28,6 +28,7 @@
 // in FP64 first (rare).
 #include <cmath>
 #include <cstring>
+#include <new>
 
 #include "msm_internal.h"
 
@@ -176,11 +177,29 @@ __device__ __forceinline__ void grid_fp64(double v, const BinArgs& A, int d, int
   fr = t - fl;
 }
 
+// Arguments of the count and scatter kernels (one replica).
+template <typename IO>
+struct BinKArgs {
+  const IO* pos;
+  const IO* q;
+  int n;
+  BinArgs A;
+  int* count;
+  int* key;
+  int* rank;
+  int* status;
+  const int* cell_start;
+  void* atoms;
+  void* gfrac;
+  int4* gbase;
+  int* perm;
+};
+
 template <typename IO, bool FP64>
-__global__ void __launch_bounds__(256) k_bin_count(const IO* __restrict__ pos, const IO* __restrict__ q, int n,
-                                                   BinArgs A, int* __restrict__ count, int* __restrict__ key_out,
-                                                   int* __restrict__ rank_out, int* __restrict__ status) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void bin_count_body(const IO* __restrict__ pos, const IO* __restrict__ q, int n,
+                                               const BinArgs& A, int* __restrict__ count, int* __restrict__ key_out,
+                                               int* __restrict__ rank_out, int* __restrict__ status, int blk) {
+  const int i = blk * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const bool valid = i < n;
   int key = -1, bad = 0;
@@ -212,6 +231,21 @@ __global__ void __launch_bounds__(256) k_bin_count(const IO* __restrict__ pos, c
   }
 }
 
+template <typename IO, bool FP64>
+__global__ void __launch_bounds__(256) k_bin_count(const IO* __restrict__ pos, const IO* __restrict__ q, int n,
+                                                   BinArgs A, int* __restrict__ count, int* __restrict__ key_out,
+                                                   int* __restrict__ rank_out, int* __restrict__ status) {
+  bin_count_body<IO, FP64>(pos, q, n, A, count, key_out, rank_out, status, blockIdx.x);
+}
+
+template <typename IO, bool FP64>
+__global__ void __launch_bounds__(256) kb_bin_count(const BinKArgs<IO>* __restrict__ tab, const int* __restrict__ first,
+                                                    int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  const BinKArgs<IO>& a = tab[r];
+  bin_count_body<IO, FP64>(a.pos, a.q, a.n, a.A, a.count, a.key, a.rank, a.status, blockIdx.x - first[r]);
+}
+
 template <int NT>
 __device__ __forceinline__ int block_reduce_sum(int v, int* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -224,25 +258,43 @@ __device__ __forceinline__ int block_reduce_sum(int v, int* red) {
   return v;
 }
 
-__global__ void __launch_bounds__(1024) k_cell_sums(const int* __restrict__ count, int ncell, int* __restrict__ sums) {
+struct ScanKArgs {
+  int* count;
+  int ncell;
+  int* sums;
+  int* cell_start;
+};
+
+__device__ __forceinline__ void cell_sums_body(const int* __restrict__ count, int ncell, int* __restrict__ sums,
+                                               int blk) {
   __shared__ int red[32];
-  const int c0 = blockIdx.x * kScanChunk + 4 * threadIdx.x;
+  const int c0 = blk * kScanChunk + 4 * threadIdx.x;
   int v = 0;
   for (int t = 0; t < 4; ++t) v += (c0 + t < ncell) ? count[c0 + t] : 0;
   v = block_reduce_sum<1024>(v, red);
-  if (threadIdx.x == 0) sums[blockIdx.x] = v;
+  if (threadIdx.x == 0) sums[blk] = v;
+}
+
+__global__ void __launch_bounds__(1024) k_cell_sums(const int* __restrict__ count, int ncell, int* __restrict__ sums) {
+  cell_sums_body(count, ncell, sums, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(1024) kb_cell_sums(const ScanKArgs* __restrict__ tab, const int* __restrict__ first,
+                                                     int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  cell_sums_body(tab[r].count, tab[r].ncell, tab[r].sums, blockIdx.x - first[r]);
 }
 
 // cell_start[c] = sum of count[0..c); count[c] = 0 afterwards.
-__global__ void __launch_bounds__(1024) k_cell_scan(int* __restrict__ count, int ncell,
-                                                    const int* __restrict__ sums, int* __restrict__ cell_start) {
+__device__ __forceinline__ void cell_scan_body(int* __restrict__ count, int ncell, const int* __restrict__ sums,
+                                               int* __restrict__ cell_start, int blk) {
   __shared__ int red[32], wsum[32];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   // this block's offset: the sums of the chunks before it
   int pre = 0;
-  for (int b = t; b < (int)blockIdx.x; b += 1024) pre += sums[b];
+  for (int b = t; b < blk; b += 1024) pre += sums[b];
   pre = block_reduce_sum<1024>(pre, red);
-  const int c0 = blockIdx.x * kScanChunk + 4 * t;
+  const int c0 = blk * kScanChunk + 4 * t;
   int v[4], tot = 0;
   for (int k = 0; k < 4; ++k) {
     v[k] = (c0 + k < ncell) ? count[c0 + k] : 0;
@@ -276,14 +328,24 @@ __global__ void __launch_bounds__(1024) k_cell_scan(int* __restrict__ count, int
   if (c0 <= ncell - 1 && ncell - 1 < c0 + 4) cell_start[ncell] = run;  // end marker, by the last cell's thread
 }
 
+__global__ void __launch_bounds__(1024) k_cell_scan(int* __restrict__ count, int ncell,
+                                                    const int* __restrict__ sums, int* __restrict__ cell_start) {
+  cell_scan_body(count, ncell, sums, cell_start, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(1024) kb_cell_scan(const ScanKArgs* __restrict__ tab, const int* __restrict__ first,
+                                                     int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  cell_scan_body(tab[r].count, tab[r].ncell, tab[r].sums, tab[r].cell_start, blockIdx.x - first[r]);
+}
+
 template <typename IO, bool FP64>
-__global__ void __launch_bounds__(256) k_bin_scatter(const IO* __restrict__ pos, const IO* __restrict__ q, int n,
-                                                     BinArgs A, const int* __restrict__ key_in,
-                                                     const int* __restrict__ rank_in,
-                                                     const int* __restrict__ cell_start, void* __restrict__ atoms_v,
-                                                     void* __restrict__ gfrac_v, int4* __restrict__ gbase,
-                                                     int* __restrict__ perm) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void bin_scatter_body(const IO* __restrict__ pos, const IO* __restrict__ q, int n,
+                                                 const BinArgs& A, const int* __restrict__ key_in,
+                                                 const int* __restrict__ rank_in, const int* __restrict__ cell_start,
+                                                 void* __restrict__ atoms_v, void* __restrict__ gfrac_v,
+                                                 int4* __restrict__ gbase, int* __restrict__ perm, int blk) {
+  const int i = blk * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int key = key_in[i];
   const int s = cell_start[key] + rank_in[i];
@@ -315,6 +377,25 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const IO* __restrict__ pos,
   perm[s] = i;
 }
 
+template <typename IO, bool FP64>
+__global__ void __launch_bounds__(256) k_bin_scatter(const IO* __restrict__ pos, const IO* __restrict__ q, int n,
+                                                     BinArgs A, const int* __restrict__ key_in,
+                                                     const int* __restrict__ rank_in,
+                                                     const int* __restrict__ cell_start, void* __restrict__ atoms_v,
+                                                     void* __restrict__ gfrac_v, int4* __restrict__ gbase,
+                                                     int* __restrict__ perm) {
+  bin_scatter_body<IO, FP64>(pos, q, n, A, key_in, rank_in, cell_start, atoms_v, gfrac_v, gbase, perm, blockIdx.x);
+}
+
+template <typename IO, bool FP64>
+__global__ void __launch_bounds__(256) kb_bin_scatter(const BinKArgs<IO>* __restrict__ tab,
+                                                      const int* __restrict__ first, int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  const BinKArgs<IO>& a = tab[r];
+  bin_scatter_body<IO, FP64>(a.pos, a.q, a.n, a.A, a.key, a.rank, a.cell_start, a.atoms, a.gfrac, a.gbase, a.perm,
+                             blockIdx.x - first[r]);
+}
+
 // Veltkamp-style split c = hi + lo with hi holding `hb` significant bits.
 void split_const(double c, int hb, float& hi, float& lo) {
   int ex = 0;
@@ -330,12 +411,7 @@ int bits_for(int kmax) {
   return b;
 }
 
-}  // namespace
-
-template <typename IO>
-cudaError_t launch_binning(Plan& P, int64_t n64, const IO* pos, const IO* q, cudaStream_t st) {
-  const int n = (int)n64;
-  DeviceBuffers& D = P.d;
+BinArgs bin_args(const Plan& P) {
   BinArgs A;
   for (int d = 0; d < 3; ++d) {
     const double L = P.P.box[d];
@@ -361,6 +437,16 @@ cudaError_t launch_binning(Plan& P, int64_t n64, const IO* pos, const IO* q, cud
   }
   A.periodic = P.P.periodic;
   A.S = P.S;
+  return A;
+}
+
+}  // namespace
+
+template <typename IO>
+cudaError_t launch_binning(Plan& P, int64_t n64, const IO* pos, const IO* q, cudaStream_t st) {
+  const int n = (int)n64;
+  DeviceBuffers& D = P.d;
+  const BinArgs A = bin_args(P);
   const unsigned nb = (unsigned)((n + 255) / 256);
   const unsigned nsc = (unsigned)((P.ncell + kScanChunk - 1) / kScanChunk);
   if (n > 0) {
@@ -381,6 +467,67 @@ cudaError_t launch_binning(Plan& P, int64_t n64, const IO* pos, const IO* q, cud
   }
   P.launches += 2 + (n > 0 ? 2 : 0);
   return cudaGetLastError();
+}
+
+struct BinBatch {
+  BatchTable<BinKArgs<double>> atoms;  // count and scatter: 256 atoms per block
+  BatchTable<ScanKArgs> scan;          // cell sums and scan: kScanChunk cells per block
+};
+
+cudaError_t bin_batch_build(const std::vector<BatchRep>& reps, BinBatch** out) {
+  *out = nullptr;
+  BinBatch* b = new (std::nothrow) BinBatch();
+  if (!b) return cudaErrorMemoryAllocation;
+  std::vector<BinKArgs<double>> ka;
+  std::vector<ScanKArgs> sa;
+  std::vector<int> kb, sb;
+  for (const BatchRep& r : reps) {
+    Plan& P = *r.plan;
+    DeviceBuffers& D = P.d;
+    BinKArgs<double> a;
+    a.pos = r.pos;
+    a.q = r.q;
+    a.n = (int)r.n;
+    a.A = bin_args(P);
+    a.count = D.count;
+    a.key = D.key;
+    a.rank = D.rank;
+    a.status = D.status;
+    a.cell_start = D.cell_start;
+    a.atoms = D.atoms;
+    a.gfrac = D.gfrac;
+    a.gbase = D.gbase;
+    a.perm = D.perm;
+    ka.push_back(a);
+    kb.push_back((int)((r.n + 255) / 256));
+    sa.push_back(ScanKArgs{D.count, P.ncell, D.csum, D.cell_start});
+    sb.push_back((P.ncell + kScanChunk - 1) / kScanChunk);
+  }
+  cudaError_t e = make_table(b->atoms, ka, kb);
+  if (e == cudaSuccess) e = make_table(b->scan, sa, sb);
+  if (e != cudaSuccess) {
+    bin_batch_free(b);
+    return e;
+  }
+  *out = b;
+  return cudaSuccess;
+}
+
+cudaError_t bin_batch_launch(BinBatch* b, cudaStream_t st) {
+  if (b->atoms.total > 0)
+    kb_bin_count<double, false><<<b->atoms.total, 256, 0, st>>>(b->atoms.args, b->atoms.first, b->atoms.nrep);
+  kb_cell_sums<<<b->scan.total, 1024, 0, st>>>(b->scan.args, b->scan.first, b->scan.nrep);
+  kb_cell_scan<<<b->scan.total, 1024, 0, st>>>(b->scan.args, b->scan.first, b->scan.nrep);
+  if (b->atoms.total > 0)
+    kb_bin_scatter<double, false><<<b->atoms.total, 256, 0, st>>>(b->atoms.args, b->atoms.first, b->atoms.nrep);
+  return cudaGetLastError();
+}
+
+void bin_batch_free(BinBatch* b) {
+  if (!b) return;
+  b->atoms.release();
+  b->scan.release();
+  delete b;
 }
 
 template cudaError_t launch_binning<double>(Plan&, int64_t, const double*, const double*, cudaStream_t);

@@ -11,7 +11,9 @@
 // x fastest.  The adjoint (backward) pass reuses the same kernels: the
 // transpose of interpolation is anterpolation, the transpose of prolongation
 // is restriction, and the lattice and top kernels are symmetric.
+#include <algorithm>
 #include <cmath>
+#include <new>
 #include <type_traits>
 
 #include "msm_internal.h"
@@ -363,17 +365,17 @@ __device__ __noinline__ void anterp_atom_global(const R4<float> f, const int4 b,
 }
 
 template <int ORDER>
-__global__ void __launch_bounds__(256) k_anterp_fx(const R4<float>* __restrict__ gfrac,
-                                                   const int4* __restrict__ gbase,
-                                                   const int* __restrict__ cell_start, AnterpArgs A, GridDims G,
-                                                   unsigned long long* __restrict__ gfx) {
+__device__ __forceinline__ void anterp_fx_body(const R4<float>* __restrict__ gfrac, const int4* __restrict__ gbase,
+                                               const int* __restrict__ cell_start, const AnterpArgs& A,
+                                               const GridDims& G, unsigned long long* __restrict__ gfx, int bx, int by,
+                                               int bz) {
   constexpr int S = Basis<float, ORDER>::S, W = 2 * S;
   extern __shared__ unsigned char smem_raw[];
   const int PD = A.pd, np = PD * PD * PD, tid = threadIdx.x;
   int* phi_ = reinterpret_cast<int*>(smem_raw);  // coarse sums
   int* plo = phi_ + np;                          // residual sums
   __shared__ int cstart[64], ccount[64], list[kAnterpMaxAtoms + 32], tot_s, nk_s;  // + one round of slots
-  const int c0[3] = {(int)blockIdx.x * A.B, (int)blockIdx.y * A.B, (int)blockIdx.z * A.B};
+  const int c0[3] = {bx * A.B, by * A.B, bz * A.B};
   const int lo0 = (int)floor(c0[0] * A.cw_h[0]) - S - 1;
   const int lo1 = (int)floor(c0[1] * A.cw_h[1]) - S - 1;
   const int lo2 = (int)floor(c0[2] * A.cw_h[2]) - S - 1;
@@ -443,14 +445,26 @@ __global__ void __launch_bounds__(256) k_anterp_fx(const R4<float>* __restrict__
   }
 }
 
+template <int ORDER>
+__global__ void __launch_bounds__(256) k_anterp_fx(const R4<float>* __restrict__ gfrac, const int4* __restrict__ gbase,
+                                                   const int* __restrict__ cell_start, AnterpArgs A, GridDims G,
+                                                   unsigned long long* __restrict__ gfx) {
+  anterp_fx_body<ORDER>(gfrac, gbase, cell_start, A, G, gfx, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // Fixed-point level-0 charges (2^-31 units) to the FP64 grid, times the
 // device-side scale: one conversion per grid point.
-__global__ void k_fx_to_f64(const unsigned long long* __restrict__ gfx, double* __restrict__ q0, int64_t count,
-                            const double* __restrict__ dscale, double factor) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void fx_to_f64_body(const unsigned long long* __restrict__ gfx, double* __restrict__ q0,
+                                               int64_t count, const double* __restrict__ dscale, double factor,
+                                               int64_t i) {
   if (i >= count) return;
   const double sc = factor * (dscale ? *dscale : 1.0) * (1.0 / 2147483648.0);
   q0[i] = (double)(long long)gfx[i] * sc;
+}
+
+__global__ void k_fx_to_f64(const unsigned long long* __restrict__ gfx, double* __restrict__ q0, int64_t count,
+                            const double* __restrict__ dscale, double factor) {
+  fx_to_f64_body(gfx, q0, count, dscale, factor, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---- restriction and prolongation: separable 1-D passes ----
@@ -475,9 +489,9 @@ struct AxisArgs {
 
 // restriction along one axis: out[.., c, ..] = sum_d w(d) in[.., 2(lo_out + c) + d - lo_in, ..]
 template <typename T, int ORDER>
-__global__ void k_restrict_axis(const T* __restrict__ in, T* __restrict__ out, AxisArgs A) {
+__device__ __forceinline__ void restrict_axis_body(const T* __restrict__ in, T* __restrict__ out, const AxisArgs& A,
+                                                   int64_t t) {
   constexpr int R = ORDER;  // taps reach |d| <= 2S - 1 = ORDER
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t np = (int64_t)A.nout[0] * A.nout[1] * A.nout[2];
   if (t >= np) return;
   int c[3] = {(int)(t % A.nout[0]), (int)((t / A.nout[0]) % A.nout[1]), (int)(t / ((int64_t)A.nout[0] * A.nout[1]))};
@@ -503,11 +517,16 @@ __global__ void k_restrict_axis(const T* __restrict__ in, T* __restrict__ out, A
   out[t] = sum;
 }
 
+template <typename T, int ORDER>
+__global__ void k_restrict_axis(const T* __restrict__ in, T* __restrict__ out, AxisArgs A) {
+  restrict_axis_body<T, ORDER>(in, out, A, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // prolongation along one axis: out[.., f, ..] (+)= sum_mu w(nu - 2 mu) in[.., mu - lo_in, ..]
 template <typename T, int ORDER>
-__global__ void k_prolong_axis(const T* __restrict__ in, T* __restrict__ out, AxisArgs A, int accumulate) {
+__device__ __forceinline__ void prolong_axis_body(const T* __restrict__ in, T* __restrict__ out, const AxisArgs& A,
+                                                  int accumulate, int64_t t) {
   constexpr int R = ORDER;
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t np = (int64_t)A.nout[0] * A.nout[1] * A.nout[2];
   if (t >= np) return;
   int c[3] = {(int)(t % A.nout[0]), (int)((t / A.nout[0]) % A.nout[1]), (int)(t / ((int64_t)A.nout[0] * A.nout[1]))};
@@ -532,6 +551,11 @@ __global__ void k_prolong_axis(const T* __restrict__ in, T* __restrict__ out, Ax
     sum += T(rweight<ORDER>(d < 0 ? -d : d)) * base[s * stride];
   }
   out[t] = accumulate ? out[t] + sum : sum;
+}
+
+template <typename T, int ORDER>
+__global__ void k_prolong_axis(const T* __restrict__ in, T* __restrict__ out, AxisArgs A, int accumulate) {
+  prolong_axis_body<T, ORDER>(in, out, A, accumulate, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---- lattice cutoff: z-streaming shared-memory planes, register tiles ----
@@ -717,9 +741,9 @@ __device__ __forceinline__ void stage_plane_async(float* plane, const float* __r
 // per 8 LP FFMA2).  Each plane's partial sums are added into the totals
 // (blocked summation over planes).
 template <int LP>
-__global__ void __launch_bounds__(32 * kLatticeZ) k_lattice_f2(const float* __restrict__ q, float* __restrict__ u, GridDims G,
-                                                    const Segment2* __restrict__ seg,
-                                                    const int* __restrict__ seg_start, LatticeArgs L, float scale) {
+__device__ __forceinline__ void lattice_f2_body(const float* __restrict__ q, float* __restrict__ u, const GridDims G,
+                                                const Segment2* __restrict__ seg, const int* __restrict__ seg_start,
+                                                const LatticeArgs L, float scale, int bx, int by, int bzs) {
   constexpr int TXN = LBX / LP, TYN = 32 / TXN, LBY = 2 * TYN;
   extern __shared__ unsigned char smem_raw[];
   const int Ex = L.Ex, Ey = L.Ey, Ez = L.Ez;
@@ -729,8 +753,8 @@ __global__ void __launch_bounds__(32 * kLatticeZ) k_lattice_f2(const float* __re
   int* col = reinterpret_cast<int*>(buf1 + SX * SY);  // window offsets (SXw + SY ints)
   int* row = col + SXw;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tx = lane % TXN, ty = lane / TXN;
-  const int bz = blockIdx.z % L.nbz, part = blockIdx.z / L.nbz;
-  const int x0 = blockIdx.x * LBX, y0 = blockIdx.y * LBY, z0 = bz * kLatticeZ, zo = z0 + warp;
+  const int bz = bzs % L.nbz, part = bzs / L.nbz;
+  const int x0 = bx * LBX, y0 = by * LBY, z0 = bz * kLatticeZ, zo = z0 + warp;
   const int nplanes = kLatticeZ + 2 * Ez, per = (nplanes + L.nsplit - 1) / L.nsplit;
   const int zbeg = z0 - Ez + part * per, zend = min(z0 - Ez + nplanes, zbeg + per);
   float2 acc[LP];  // (row ty, row ty + TYN) of the LP x outputs
@@ -787,29 +811,56 @@ __global__ void __launch_bounds__(32 * kLatticeZ) k_lattice_f2(const float* __re
   }
 }
 
+template <int LP>
+__global__ void __launch_bounds__(32 * kLatticeZ, 7) k_lattice_f2(const float* __restrict__ q, float* __restrict__ u,
+                                                               GridDims G, const Segment2* __restrict__ seg,
+                                                               const int* __restrict__ seg_start, LatticeArgs L,
+                                                               float scale) {
+  lattice_f2_body<LP>(q, u, G, seg, seg_start, L, scale, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // ---- top level: all pairs of the coarsest grid, FP64 ----
+// One warp per output point: the lanes split the sum over the points of the
+// coarsest grid and combine their FP64 partial sums with shuffles.
 template <typename T>
-__global__ void k_top(const double* __restrict__ qt, T* __restrict__ ut, double* __restrict__ ut64,
-                      GridDims G, const double* __restrict__ K, int tx, int ty, int tz) {
-  int64_t np = (int64_t)G.n[0] * G.n[1] * G.n[2];
-  int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= np) return;
-  int mx = (int)(m % G.n[0]), my = (int)((m / G.n[0]) % G.n[1]), mz = (int)(m / ((int64_t)G.n[0] * G.n[1]));
+__device__ __forceinline__ void top_body(const double* __restrict__ qt, T* __restrict__ ut, double* __restrict__ ut64,
+                                         const GridDims& G, const double* __restrict__ K, int tx, int ty,
+                                         int64_t m) {
+  const int lane = threadIdx.x & 31;
+  const int n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
+  const int np = n0 * n1 * n2;
+  if (m >= np) return;  // warp-uniform
+  const int mx = (int)(m % n0), my = (int)((m / n0) % n1), mz = (int)(m / ((int64_t)n0 * n1));
   double sum = 0.0;
-  for (int vz = 0; vz < G.n[2]; ++vz) {
-    int dz = G.periodic ? (mz - vz + G.n[2]) % G.n[2] : mz - vz + G.n[2] - 1;
-    for (int vy = 0; vy < G.n[1]; ++vy) {
-      int dy = G.periodic ? (my - vy + G.n[1]) % G.n[1] : my - vy + G.n[1] - 1;
-      const double* Krow = K + ((size_t)dz * ty + dy) * tx;
-      const double* qrow = qt + ((size_t)vz * G.n[1] + vy) * G.n[0];
-      for (int vx = 0; vx < G.n[0]; ++vx) {
-        int dx = G.periodic ? (mx - vx + G.n[0]) % G.n[0] : mx - vx + G.n[0] - 1;
-        sum += Krow[dx] * qrow[vx];
-      }
+  for (int v = lane; v < np; v += 32) {
+    const int vx = v % n0, vy = (v / n0) % n1, vz = v / (n0 * n1);
+    int dx = mx - vx, dy = my - vy, dz = mz - vz;
+    if (G.periodic) {
+      dx += dx < 0 ? n0 : 0;
+      dy += dy < 0 ? n1 : 0;
+      dz += dz < 0 ? n2 : 0;
+    } else {
+      dx += n0 - 1;
+      dy += n1 - 1;
+      dz += n2 - 1;
     }
+    sum += K[((size_t)dz * ty + dy) * tx + dx] * qt[v];
   }
-  ut[m] = (T)sum;
-  ut64[m] = sum;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) {
+    ut[m] = (T)sum;
+    ut64[m] = sum;
+  }
+}
+
+constexpr int kTopWarps = 4;  // output points per block of the top-level kernel
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kTopWarps) k_top(const double* __restrict__ qt, T* __restrict__ ut,
+                                                        double* __restrict__ ut64, GridDims G,
+                                                        const double* __restrict__ K, int tx, int ty, int tz) {
+  top_body<T>(qt, ut, ut64, G, K, tx, ty, (int64_t)blockIdx.x * kTopWarps + (threadIdx.x >> 5));
   (void)tz;
 }
 
@@ -1001,9 +1052,10 @@ template <typename T>
 __device__ __forceinline__ int stage_interp_block(const AnterpArgs& A, const int* __restrict__ cell_start,
                                                   const int4* __restrict__ gbase, const T* __restrict__ u0,
                                                   const GridDims& G, T* patch, int lo0, int lo1, int lo2, int* cstart,
-                                                  int* ccount, int* list, int* nk_s, int* tot_s) {
+                                                  int* ccount, int* list, int* nk_s, int* tot_s, int bx, int by,
+                                                  int bz) {
   const int PD = A.pd, np = PD * PD * PD;
-  const int c0[3] = {(int)blockIdx.x * A.B, (int)blockIdx.y * A.B, (int)blockIdx.z * A.B};
+  const int c0[3] = {bx * A.B, by * A.B, bz * A.B};
   if (threadIdx.x == 0) *nk_s = block_cells(A, cell_start, c0, cstart, ccount);
   __syncthreads();
   int total = build_rank_list(*nk_s, cstart, ccount, list, tot_s);
@@ -1025,22 +1077,48 @@ __device__ __forceinline__ int stage_interp_block(const AnterpArgs& A, const int
   return total;
 }
 
+// Arguments of the interpolation kernels (one system): the forward kernel
+// writes phi_out, force_out, fs.w, glong and the per-block energy partials;
+// the adjoint kernel reads fs and glong and writes grad_pos, grad_q.
+template <typename T, typename OUT>
+struct InterpKArgs {
+  const R4<T>* gfrac;
+  const int4* gbase;
+  const int* perm;
+  const int* cell_start;
+  AnterpArgs AA;
+  const T* u0;  // u^0 (forward) or the adjoint grid (backward)
+  GridDims G;
+  AssembleArgs A;
+  const T* phis;
+  R4<T>* fs;
+  R4<T>* glong;
+  OUT* phi_out;
+  OUT* force_out;
+  double* partial;
+  const double* gE;
+  OUT* grad_pos;
+  OUT* grad_q;
+  int nbx, nby;  // blocks along x and y
+};
+
 template <typename T, int ORDER, typename OUT>
-__global__ void __launch_bounds__(256) k_interp_fwd(
+__device__ __forceinline__ void interp_fwd_body(
     const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm,
-    const int* __restrict__ cell_start, AnterpArgs AA, const T* __restrict__ u0, GridDims G, AssembleArgs A,
-    const T* __restrict__ phis, R4<T>* __restrict__ fs, R4<T>* __restrict__ glong, OUT* __restrict__ phi_out,
-    OUT* __restrict__ force_out, double* __restrict__ partial) {
+    const int* __restrict__ cell_start, const AnterpArgs& AA, const T* __restrict__ u0, const GridDims& G,
+    const AssembleArgs& A, const T* __restrict__ phis, R4<T>* __restrict__ fs, R4<T>* __restrict__ glong,
+    OUT* __restrict__ phi_out, OUT* __restrict__ force_out, double* __restrict__ partial, int bx, int by, int bz,
+    int lin) {
   constexpr int S = Basis<T, ORDER>::S;
   extern __shared__ unsigned char smem_raw[];
   T* patch = reinterpret_cast<T*>(smem_raw);
   __shared__ int cstart[64], ccount[64], list[kAnterpMaxAtoms + 32], nk_s, tot_s;  // + one round of slots
-  const int c0[3] = {(int)blockIdx.x * AA.B, (int)blockIdx.y * AA.B, (int)blockIdx.z * AA.B};
+  const int c0[3] = {bx * AA.B, by * AA.B, bz * AA.B};
   const int lo0 = (int)floor(c0[0] * AA.cw_h[0]) - S - 1;
   const int lo1 = (int)floor(c0[1] * AA.cw_h[1]) - S - 1;
   const int lo2 = (int)floor(c0[2] * AA.cw_h[2]) - S - 1;
   const int total = stage_interp_block<T>(AA, cell_start, gbase, u0, G, patch, lo0, lo1, lo2, cstart, ccount, list,
-                                          &nk_s, &tot_s);
+                                          &nk_s, &tot_s, bx, by, bz);
   const T ih[3] = {T(A.inv_h[0]), T(A.inv_h[1]), T(A.inv_h[2])};
   double e = 0.0;
   const int nk = nk_s;
@@ -1069,34 +1147,57 @@ __global__ void __launch_bounds__(256) k_interp_fwd(
     glong[i] = R4<T>{g[0], g[1], g[2], T(0)};
   }
   double bsum = block_sum<256>(e);
-  if (threadIdx.x == 0) partial[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = bsum;
+  if (threadIdx.x == 0) partial[lin] = bsum;
 }
 
-__global__ void __launch_bounds__(1024) k_energy_final(const double* __restrict__ partial, int nb,
-                                                       double* __restrict__ energy) {
+template <typename T, int ORDER, typename OUT>
+__device__ __forceinline__ void interp_fwd_call(const InterpKArgs<T, OUT>& K, int bx, int by, int bz, int lin) {
+  interp_fwd_body<T, ORDER, OUT>(K.gfrac, K.gbase, K.perm, K.cell_start, K.AA, K.u0, K.G, K.A, K.phis, K.fs, K.glong,
+                                 K.phi_out, K.force_out, K.partial, bx, by, bz, lin);
+}
+
+template <typename T, int ORDER, typename OUT>
+__global__ void __launch_bounds__(256) k_interp_fwd(
+    const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm,
+    const int* __restrict__ cell_start, AnterpArgs AA, const T* __restrict__ u0, GridDims G, AssembleArgs A,
+    const T* __restrict__ phis, R4<T>* __restrict__ fs, R4<T>* __restrict__ glong, OUT* __restrict__ phi_out,
+    OUT* __restrict__ force_out, double* __restrict__ partial) {
+  interp_fwd_body<T, ORDER, OUT>(gfrac, gbase, perm, cell_start, AA, u0, G, A, phis, fs, glong, phi_out, force_out,
+                                 partial, blockIdx.x, blockIdx.y, blockIdx.z,
+                                 (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+}
+
+__device__ __forceinline__ void energy_final_body(const double* __restrict__ partial, int nb,
+                                                  double* __restrict__ energy) {
   double v = 0.0;
   for (int i = threadIdx.x; i < nb; i += 1024) v += partial[i];
   double s = block_sum<1024>(v);
   if (threadIdx.x == 0) *energy = 0.5 * s;
 }
 
+__global__ void __launch_bounds__(1024) k_energy_final(const double* __restrict__ partial, int nb,
+                                                       double* __restrict__ energy) {
+  energy_final_body(partial, nb, energy);
+}
+
 // adjoint assembly: av0 = M (anterpolated 1/2 gE q) on the grid
 template <typename T, int ORDER, typename OUT>
-__global__ void __launch_bounds__(256) k_interp_bwd(
+__device__ __forceinline__ void interp_bwd_body(
     const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm,
-    const int* __restrict__ cell_start, AnterpArgs AA, const T* __restrict__ av0, GridDims G, AssembleArgs A,
-    const T* __restrict__ phis, const R4<T>* __restrict__ fs, const R4<T>* __restrict__ glong,
-    const double* __restrict__ gE, OUT* __restrict__ grad_pos, OUT* __restrict__ grad_q) {
+    const int* __restrict__ cell_start, const AnterpArgs& AA, const T* __restrict__ av0, const GridDims& G,
+    const AssembleArgs& A, const T* __restrict__ phis, const R4<T>* __restrict__ fs,
+    const R4<T>* __restrict__ glong, const double* __restrict__ gE, OUT* __restrict__ grad_pos,
+    OUT* __restrict__ grad_q, int bx, int by, int bz) {
   constexpr int S = Basis<T, ORDER>::S;
   extern __shared__ unsigned char smem_raw[];
   T* patch = reinterpret_cast<T*>(smem_raw);
   __shared__ int cstart[64], ccount[64], list[kAnterpMaxAtoms + 32], nk_s, tot_s;  // + one round of slots
-  const int c0[3] = {(int)blockIdx.x * AA.B, (int)blockIdx.y * AA.B, (int)blockIdx.z * AA.B};
+  const int c0[3] = {bx * AA.B, by * AA.B, bz * AA.B};
   const int lo0 = (int)floor(c0[0] * AA.cw_h[0]) - S - 1;
   const int lo1 = (int)floor(c0[1] * AA.cw_h[1]) - S - 1;
   const int lo2 = (int)floor(c0[2] * AA.cw_h[2]) - S - 1;
   const int total = stage_interp_block<T>(AA, cell_start, gbase, av0, G, patch, lo0, lo1, lo2, cstart, ccount,
-                                          list, &nk_s, &tot_s);
+                                          list, &nk_s, &tot_s, bx, by, bz);
   const T ih[3] = {T(A.inv_h[0]), T(A.inv_h[1]), T(A.inv_h[2])};
   const T gg = (T)*gE;
   const int nk = nk_s, nlist = total >= 0 ? total : 0;
@@ -1118,6 +1219,22 @@ __global__ void __launch_bounds__(256) k_interp_bwd(
     interp_patch_atom<T, ORDER>(f, gbase[i], patch, AA.pd, lo0, lo1, lo2, av0, G, ih, v, gv);
     Assemble<T>::backward(A, gg, f.w, phis[i], fs[i], glong[i], v, gv, perm[i], grad_pos, grad_q);
   }
+}
+
+template <typename T, int ORDER, typename OUT>
+__device__ __forceinline__ void interp_bwd_call(const InterpKArgs<T, OUT>& K, int bx, int by, int bz) {
+  interp_bwd_body<T, ORDER, OUT>(K.gfrac, K.gbase, K.perm, K.cell_start, K.AA, K.u0, K.G, K.A, K.phis, K.fs, K.glong,
+                                 K.gE, K.grad_pos, K.grad_q, bx, by, bz);
+}
+
+template <typename T, int ORDER, typename OUT>
+__global__ void __launch_bounds__(256) k_interp_bwd(
+    const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm,
+    const int* __restrict__ cell_start, AnterpArgs AA, const T* __restrict__ av0, GridDims G, AssembleArgs A,
+    const T* __restrict__ phis, const R4<T>* __restrict__ fs, const R4<T>* __restrict__ glong,
+    const double* __restrict__ gE, OUT* __restrict__ grad_pos, OUT* __restrict__ grad_q) {
+  interp_bwd_body<T, ORDER, OUT>(gfrac, gbase, perm, cell_start, AA, av0, G, A, phis, fs, glong, gE, grad_pos, grad_q,
+                                 blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <typename T>
@@ -1270,9 +1387,13 @@ cudaError_t launch_prolong(Plan& P, int k, const void* coarse, void* fine, cudaS
   return cudaGetLastError();
 }
 
-__global__ void k_f64_to_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t count) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void f64_to_f32_body(const double* __restrict__ src, float* __restrict__ dst,
+                                                int64_t count, int64_t i) {
   if (i < count) dst[i] = (float)src[i];
+}
+
+__global__ void k_f64_to_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t count) {
+  f64_to_f32_body(src, dst, count, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Lattice cutoff of level k from the FP64 charges qk.  Mixed precision first
@@ -1327,38 +1448,66 @@ cudaError_t launch_top(Plan& P, const void* qt, void* ut, cudaStream_t st) {
   P.launches += 1;
   int top = P.levels - 1;
   GridDims G = dims_of(P, top);
-  unsigned nb = blocks_for(grid_points(P, top), 64);
+  unsigned nb = blocks_for(grid_points(P, top), kTopWarps);
   if (P.fp64)
-    k_top<double><<<nb, 64, 0, st>>>((const double*)qt, (double*)ut, P.d.topu, G, P.d.topK,
+    k_top<double><<<nb, 32 * kTopWarps, 0, st>>>((const double*)qt, (double*)ut, P.d.topu, G, P.d.topK,
                                      P.top_table_dims[0], P.top_table_dims[1], P.top_table_dims[2]);
   else
-    k_top<float><<<nb, 64, 0, st>>>((const double*)qt, (float*)ut, P.d.topu, G, P.d.topK,
+    k_top<float><<<nb, 32 * kTopWarps, 0, st>>>((const double*)qt, (float*)ut, P.d.topu, G, P.d.topK,
                                     P.top_table_dims[0], P.top_table_dims[1], P.top_table_dims[2]);
   return cudaGetLastError();
 }
 
 
+#define INTERP_FWD_ARGS(K)                                                                                   \
+  K.gfrac, K.gbase, K.perm, K.cell_start, K.AA, K.u0, K.G, K.A, K.phis, K.fs, K.glong, K.phi_out, K.force_out, \
+      K.partial
+#define INTERP_BWD_ARGS(K) \
+  K.gfrac, K.gbase, K.perm, K.cell_start, K.AA, K.u0, K.G, K.A, K.phis, K.fs, K.glong, K.gE, K.grad_pos, K.grad_q
+
+// Interpolation arguments of plan P (forward: grid u^0; backward: the adjoint grid).
+template <typename T, typename OUT>
+InterpKArgs<T, OUT> interp_kargs(Plan& P, bool backward, OUT* phi, OUT* force, const double* gE, OUT* grad_pos,
+                                 OUT* grad_q, double* partial) {
+  InterpKArgs<T, OUT> K;
+  K.gfrac = (const R4<T>*)P.d.gfrac;
+  K.gbase = P.d.gbase;
+  K.perm = P.d.perm;
+  K.cell_start = P.d.cell_start;
+  K.AA = patch_args(P);
+  K.u0 = (const T*)(backward ? P.d.au[0] : P.d.gu[0]);
+  K.G = dims_of(P, 0);
+  K.A = assemble_args(P);
+  K.phis = (const T*)P.d.phis;
+  K.fs = (R4<T>*)P.d.fs;
+  K.glong = (R4<T>*)P.d.glong;
+  K.phi_out = phi;
+  K.force_out = force;
+  K.partial = partial;
+  K.gE = gE;
+  K.grad_pos = grad_pos;
+  K.grad_q = grad_q;
+  K.nbx = (int)blocks_for(P.nc[0], K.AA.B);
+  K.nby = (int)blocks_for(P.nc[1], K.AA.B);
+  return K;
+}
+
 template <typename OUT>
 cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, OUT* phi, OUT* force, cudaStream_t st) {
-  GridDims G = dims_of(P, 0);
-  AssembleArgs A = assemble_args(P);
   AnterpArgs AA = patch_args(P);
   dim3 grid(blocks_for(P.nc[0], AA.B), blocks_for(P.nc[1], AA.B), blocks_for(P.nc[2], AA.B));
   int nb = (int)(grid.x * grid.y * grid.z);
   if (n > 0) {
     size_t sm = (P.fp64 ? 8 : 4) * (size_t)AA.pd * AA.pd * AA.pd;
-#define MSM_FWD(T, O)                                                                                            \
-  {                                                                                                              \
-    k_interp_fwd<T, O, OUT><<<grid, 256, sm, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.perm, P.d.cell_start, AA, \
-                                              (const T*)P.d.gu[0], G, A, (const T*)P.d.phis, (R4<T>*)P.d.fs,    \
-                                              (R4<T>*)P.d.glong, phi, force, P.d.partial);                      \
-  }
     if (P.fp64) {
-      if (P.P.order == 3) MSM_FWD(double, 3) else MSM_FWD(double, 5)
+      auto K = interp_kargs<double, OUT>(P, false, phi, force, nullptr, nullptr, nullptr, P.d.partial);
+      if (P.P.order == 3) k_interp_fwd<double, 3, OUT><<<grid, 256, sm, st>>>(INTERP_FWD_ARGS(K));
+      else k_interp_fwd<double, 5, OUT><<<grid, 256, sm, st>>>(INTERP_FWD_ARGS(K));
     } else {
-      if (P.P.order == 3) MSM_FWD(float, 3) else MSM_FWD(float, 5)
+      auto K = interp_kargs<float, OUT>(P, false, phi, force, nullptr, nullptr, nullptr, P.d.partial);
+      if (P.P.order == 3) k_interp_fwd<float, 3, OUT><<<grid, 256, sm, st>>>(INTERP_FWD_ARGS(K));
+      else k_interp_fwd<float, 5, OUT><<<grid, 256, sm, st>>>(INTERP_FWD_ARGS(K));
     }
-#undef MSM_FWD
   }
   k_energy_final<<<1, 1024, 0, st>>>(P.d.partial, n > 0 ? nb : 0, energy);
   P.launches += 1 + (n > 0 ? 1 : 0);
@@ -1369,24 +1518,484 @@ template <typename OUT>
 cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, OUT* grad_pos, OUT* grad_q,
                                    cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  GridDims G = dims_of(P, 0);
-  AssembleArgs A = assemble_args(P);
   AnterpArgs AA = patch_args(P);
   dim3 grid(blocks_for(P.nc[0], AA.B), blocks_for(P.nc[1], AA.B), blocks_for(P.nc[2], AA.B));
   size_t sm = (P.fp64 ? 8 : 4) * (size_t)AA.pd * AA.pd * AA.pd;
   P.launches += 1;
-#define MSM_BWD(T, O)                                                                                             \
-  {                                                                                                               \
-    k_interp_bwd<T, O, OUT><<<grid, 256, sm, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.perm, P.d.cell_start, AA,  \
-                                              (const T*)P.d.au[0], G, A, (const T*)P.d.phis,                     \
-                                              (const R4<T>*)P.d.fs, (const R4<T>*)P.d.glong, gE, grad_pos, grad_q); \
-  }
   if (P.fp64) {
-    if (P.P.order == 3) MSM_BWD(double, 3) else MSM_BWD(double, 5)
+    auto K = interp_kargs<double, OUT>(P, true, nullptr, nullptr, gE, grad_pos, grad_q, nullptr);
+    if (P.P.order == 3) k_interp_bwd<double, 3, OUT><<<grid, 256, sm, st>>>(INTERP_BWD_ARGS(K));
+    else k_interp_bwd<double, 5, OUT><<<grid, 256, sm, st>>>(INTERP_BWD_ARGS(K));
   } else {
-    if (P.P.order == 3) MSM_BWD(float, 3) else MSM_BWD(float, 5)
+    auto K = interp_kargs<float, OUT>(P, true, nullptr, nullptr, gE, grad_pos, grad_q, nullptr);
+    if (P.P.order == 3) k_interp_bwd<float, 3, OUT><<<grid, 256, sm, st>>>(INTERP_BWD_ARGS(K));
+    else k_interp_bwd<float, 5, OUT><<<grid, 256, sm, st>>>(INTERP_BWD_ARGS(K));
   }
-#undef MSM_BWD
+  return cudaGetLastError();
+}
+
+
+template cudaError_t launch_interp_forward<double>(Plan&, int64_t, double*, double*, double*, cudaStream_t);
+template cudaError_t launch_interp_forward<float>(Plan&, int64_t, double*, float*, float*, cudaStream_t);
+template cudaError_t launch_interp_backward<double>(Plan&, int64_t, const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_interp_backward<float>(Plan&, int64_t, const double*, float*, float*, cudaStream_t);
+
+cudaError_t launch_grid_to_double(Plan& P, const void* src, double* dst, int64_t count, bool is_double,
+                                  cudaStream_t st) {
+  unsigned nb = blocks_for(count, 256);
+  if (count <= 0) return cudaSuccess;
+  if (P.fp64 || is_double) k_to_double<double><<<nb, 256, 0, st>>>((const double*)src, dst, count);
+  else k_to_double<float><<<nb, 256, 0, st>>>((const float*)src, dst, count);
+  return cudaGetLastError();
+}
+
+
+// ---- batches: every grid pass as one launch over all replicas ----
+namespace {
+
+constexpr int kEw = 256;  // threads per block of the batched elementwise kernels
+
+struct ZeroKArgs {
+  unsigned* p;
+  int64_t words;
+};
+struct FxKArgs {
+  const unsigned long long* gfx;
+  double* q0;
+  int64_t count;
+  const double* dscale;
+  double factor;
+};
+template <typename T>
+struct AxisKArgs {
+  const T* in;
+  T* out;
+  AxisArgs A;
+  int acc;
+};
+struct ConvKArgs {
+  const double* src;
+  float* dst;
+  int64_t count;
+};
+struct AntKArgs {
+  const R4<float>* gfrac;
+  const int4* gbase;
+  const int* cell_start;
+  AnterpArgs A;
+  GridDims G;
+  unsigned long long* gfx;
+  int nbx, nby;
+};
+struct LatKArgs {
+  const float* q;
+  float* u;
+  GridDims G;
+  const Segment2* seg;
+  const int* seg_start;
+  LatticeArgs L;
+  float scale;
+  int nbx, nby;
+};
+struct TopKArgs {
+  const double* qt;
+  float* ut;
+  double* ut64;
+  GridDims G;
+  const double* K;
+  int tx, ty;
+};
+struct EnergyKArgs {
+  const double* partial;
+  int nb;
+  double* energy;
+};
+
+__device__ __forceinline__ int64_t ew_index(const int* __restrict__ first, int r) {
+  return (int64_t)(blockIdx.x - first[r]) * kEw + threadIdx.x;
+}
+
+__global__ void __launch_bounds__(kEw) kb_zero(const ZeroKArgs* __restrict__ tab, const int* __restrict__ first,
+                                               int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  const int64_t i = ew_index(first, r);
+  if (i < tab[r].words) tab[r].p[i] = 0u;
+}
+
+__global__ void __launch_bounds__(kEw) kb_fx_to_f64(const FxKArgs* __restrict__ tab, const int* __restrict__ first,
+                                                    int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  const FxKArgs& a = tab[r];
+  fx_to_f64_body(a.gfx, a.q0, a.count, a.dscale, a.factor, ew_index(first, r));
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(kEw) kb_restrict_axis(const AxisKArgs<double>* __restrict__ tab,
+                                                        const int* __restrict__ first, int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  const AxisKArgs<double>& a = tab[r];
+  restrict_axis_body<double, ORDER>(a.in, a.out, a.A, ew_index(first, r));
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(kEw) kb_prolong_axis(const AxisKArgs<float>* __restrict__ tab,
+                                                       const int* __restrict__ first, int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  const AxisKArgs<float>& a = tab[r];
+  prolong_axis_body<float, ORDER>(a.in, a.out, a.A, a.acc, ew_index(first, r));
+}
+
+__global__ void __launch_bounds__(kEw) kb_f64_to_f32(const ConvKArgs* __restrict__ tab, const int* __restrict__ first,
+                                                     int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  f64_to_f32_body(tab[r].src, tab[r].dst, tab[r].count, ew_index(first, r));
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(256, 2) kb_anterp_fx(const AntKArgs* __restrict__ tab, const int* __restrict__ first,
+                                                    int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  const AntKArgs& a = tab[r];
+  const int b = blockIdx.x - first[r];
+  anterp_fx_body<ORDER>(a.gfrac, a.gbase, a.cell_start, a.A, a.G, a.gfx, b % a.nbx, (b / a.nbx) % a.nby,
+                        b / (a.nbx * a.nby));
+}
+
+__global__ void __launch_bounds__(32 * kLatticeZ) kb_lattice_f2(const LatKArgs* __restrict__ tab,
+                                                                   const int* __restrict__ first, int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  const LatKArgs& a = tab[r];
+  const int b = blockIdx.x - first[r];
+  lattice_f2_body<kLatticeLP>(a.q, a.u, a.G, a.seg, a.seg_start, a.L, a.scale, b % a.nbx, (b / a.nbx) % a.nby,
+                              b / (a.nbx * a.nby));
+}
+
+__global__ void __launch_bounds__(32 * kTopWarps) kb_top(const TopKArgs* __restrict__ tab,
+                                                         const int* __restrict__ first, int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  const TopKArgs& a = tab[r];
+  top_body<float>(a.qt, a.ut, a.ut64, a.G, a.K, a.tx, a.ty,
+                  (int64_t)(blockIdx.x - first[r]) * kTopWarps + (threadIdx.x >> 5));
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(256, 2) kb_interp_fwd(const InterpKArgs<float, double>* __restrict__ tab,
+                                                     const int* __restrict__ first, int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  const InterpKArgs<float, double>& K = tab[r];
+  const int b = blockIdx.x - first[r];
+  interp_fwd_call<float, ORDER, double>(K, b % K.nbx, (b / K.nbx) % K.nby, b / (K.nbx * K.nby), b);
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(256, 2) kb_interp_bwd(const InterpKArgs<float, double>* __restrict__ tab,
+                                                     const int* __restrict__ first, int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  const InterpKArgs<float, double>& K = tab[r];
+  const int b = blockIdx.x - first[r];
+  interp_bwd_call<float, ORDER, double>(K, b % K.nbx, (b / K.nbx) % K.nby, b / (K.nbx * K.nby));
+}
+
+__global__ void __launch_bounds__(1024) kb_energy_final(const EnergyKArgs* __restrict__ tab,
+                                                        const int* __restrict__ first, int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  energy_final_body(tab[r].partial, tab[r].nb, tab[r].energy);
+}
+
+int ew_blocks(int64_t count) { return (int)((count + kEw - 1) / kEw); }
+
+}  // namespace
+
+struct GridBatch {
+  int order = 3;
+  int maxlev = 1;
+  bool has_backward = false;
+  BatchTable<ZeroKArgs> zero_fx;
+  BatchTable<AntKArgs> anterp;
+  BatchTable<FxKArgs> fx[2];
+  std::vector<BatchTable<AxisKArgs<double>>> restr[2];  // [dir][3 k + axis]
+  BatchTable<ConvKArgs> conv[2];
+  BatchTable<ZeroKArgs> zero_u[2];
+  BatchTable<LatKArgs> lattice[2];
+  BatchTable<TopKArgs> top[2];
+  std::vector<BatchTable<AxisKArgs<float>>> prol[2];  // [dir][3 k + pass]
+  BatchTable<InterpKArgs<float, double>> interp[2];
+  BatchTable<EnergyKArgs> energy;
+};
+
+void grid_batch_free(GridBatch* b) {
+  if (!b) return;
+  b->zero_fx.release();
+  b->anterp.release();
+  for (int d = 0; d < 2; ++d) {
+    b->fx[d].release();
+    for (auto& t : b->restr[d]) t.release();
+    b->conv[d].release();
+    b->zero_u[d].release();
+    b->lattice[d].release();
+    b->top[d].release();
+    for (auto& t : b->prol[d]) t.release();
+    b->interp[d].release();
+  }
+  b->energy.release();
+  delete b;
+}
+
+cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, GridBatch** out) {
+  *out = nullptr;
+  GridBatch* B = new (std::nothrow) GridBatch();
+  if (!B) return cudaErrorMemoryAllocation;
+  const int R = (int)reps.size();
+  B->order = reps.empty() ? 3 : reps[0].plan->P.order;
+  B->has_backward = backward;
+  for (const BatchRep& r : reps) B->maxlev = std::max(B->maxlev, r.plan->levels);
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  {  // anterpolation into the fixed-point grids (tmp[0]); the same kernels for both directions
+    std::vector<ZeroKArgs> za;
+    std::vector<AntKArgs> aa;
+    std::vector<int> zb, ab;
+    size_t sm = 0;
+    for (const BatchRep& r : reps) {
+      Plan& P = *r.plan;
+      const int64_t np = grid_points(P, 0);
+      za.push_back(ZeroKArgs{(unsigned*)P.d.tmp[0], 2 * np});
+      zb.push_back(ew_blocks(2 * np));
+      AntKArgs a;
+      a.gfrac = (const R4<float>*)P.d.gfrac;
+      a.gbase = P.d.gbase;
+      a.cell_start = P.d.cell_start;
+      a.A = patch_args(P);
+      a.G = dims_of(P, 0);
+      a.gfx = (unsigned long long*)P.d.tmp[0];
+      a.nbx = (int)blocks_for(P.nc[0], a.A.B);
+      a.nby = (int)blocks_for(P.nc[1], a.A.B);
+      aa.push_back(a);
+      ab.push_back(r.n > 0 ? a.nbx * a.nby * (int)blocks_for(P.nc[2], a.A.B) : 0);
+      sm = std::max(sm, 2 * sizeof(int) * (size_t)a.A.pd * a.A.pd * a.A.pd);
+    }
+    chk(make_table(B->zero_fx, za, zb));
+    chk(make_table(B->anterp, aa, ab, sm));
+  }
+  for (int dir = 0; dir < (backward ? 2 : 1); ++dir) {
+    std::vector<FxKArgs> fa;
+    std::vector<int> fb;
+    for (const BatchRep& r : reps) {
+      Plan& P = *r.plan;
+      const int64_t np = grid_points(P, 0);
+      fa.push_back(FxKArgs{(const unsigned long long*)P.d.tmp[0], (double*)(dir ? P.d.aq[0] : P.d.gq[0]), np,
+                           dir ? r.grad_energy : nullptr, dir ? 0.5 : 1.0});
+      fb.push_back(ew_blocks(np));
+    }
+    chk(make_table(B->fx[dir], fa, fb));
+    // restriction k -> k+1: three axis passes (fine -> tmp[0] -> tmp[1] -> coarse), FP64
+    B->restr[dir].resize(3 * std::max(B->maxlev - 1, 0));
+    for (int k = 0; k + 1 < B->maxlev; ++k)
+      for (int ax = 0; ax < 3; ++ax) {
+        std::vector<AxisKArgs<double>> ra;
+        std::vector<int> rb;
+        for (const BatchRep& r : reps) {
+          Plan& P = *r.plan;
+          AxisKArgs<double> a{};
+          int nb = 0;
+          if (k + 1 < P.levels) {
+            void* const* q = dir ? P.d.aq : P.d.gq;
+            const double* src[3] = {(const double*)q[k], (const double*)P.d.tmp[0], (const double*)P.d.tmp[1]};
+            double* dst[3] = {(double*)P.d.tmp[0], (double*)P.d.tmp[1], (double*)q[k + 1]};
+            int cur[3] = {P.n[k][0], P.n[k][1], P.n[k][2]};
+            for (int a2 = 0; a2 < ax; ++a2) cur[a2] = P.n[k + 1][a2];
+            for (int d = 0; d < 3; ++d) a.A.nin[d] = cur[d];
+            cur[ax] = P.n[k + 1][ax];
+            for (int d = 0; d < 3; ++d) a.A.nout[d] = cur[d];
+            a.A.axis = ax;
+            a.A.lo_in = P.lo[k][ax];
+            a.A.lo_out = P.lo[k + 1][ax];
+            a.A.periodic = P.P.periodic;
+            a.in = src[ax];
+            a.out = dst[ax];
+            a.acc = 0;
+            nb = ew_blocks((int64_t)cur[0] * cur[1] * cur[2]);
+          }
+          ra.push_back(a);
+          rb.push_back(nb);
+        }
+        chk(make_table(B->restr[dir][3 * k + ax], ra, rb));
+      }
+    // lattice cutoff of every level below the top, all in one launch: FP32
+    // copies of the charges at offsets of tmp[0], the outputs zeroed where
+    // several blocks add into them
+    {
+      std::vector<ConvKArgs> ca;
+      std::vector<ZeroKArgs> za;
+      std::vector<LatKArgs> la;
+      std::vector<int> cb, zb, lb;
+      size_t sm = 0;
+      for (const BatchRep& r : reps) {
+        Plan& P = *r.plan;
+        void* const* q = dir ? P.d.aq : P.d.gq;
+        void* const* u = dir ? P.d.au : P.d.gu;
+        int64_t off = 0;
+        for (int k = 0; k + 1 < P.levels; ++k) {
+          const int64_t np = grid_points(P, k);
+          float* qf = (float*)P.d.tmp[0] + off;
+          off += np;
+          ca.push_back(ConvKArgs{(const double*)q[k], qf, np});
+          cb.push_back(ew_blocks(np));
+          GridDims G = dims_of(P, k);
+          const int LBY = 2 * (32 / (LBX / kLatticeLP));
+          LatKArgs a;
+          a.q = qf;
+          a.u = (float*)u[k];
+          a.G = G;
+          a.seg = (const Segment2*)P.d.seg2;
+          a.seg_start = P.d.seg_start;
+          a.L.Ex = P.E[0];
+          a.L.Ey = P.E[1];
+          a.L.Ez = P.E[2];
+          a.L.nbz = (int)blocks_for(G.n[2], kLatticeZ);
+          a.nbx = (int)blocks_for(G.n[0], LBX);
+          a.nby = (int)blocks_for(G.n[1], LBY);
+          a.L.nsplit = 1;  // set below, once the bricks of every replica and level are known
+          a.scale = (float)std::ldexp(1.0, -k);
+          la.push_back(a);
+          lb.push_back(a.nbx * a.nby * a.L.nbz);
+          za.push_back(ZeroKArgs{(unsigned*)u[k], np});
+          zb.push_back(0);
+          const int SX = (LBX + 2 * P.E[0] + kSeg) | 1, SY = LBY + 2 * P.E[1];
+          sm = std::max(sm, sizeof(float) * 2 * SX * SY + sizeof(int) * (LBX + 2 * P.E[0] + kSeg + SY));
+        }
+      }
+      // one launch holds the bricks of every replica and level, so the input
+      // planes are split over several blocks only while the whole launch
+      // falls short of lattice_waves blocks per SM
+      int64_t bricks = 0;
+      for (int b : lb) bricks += b;
+      const int64_t target = (int64_t)reps[0].plan->lattice_waves * 152 * 4 / kLatticeZ;
+      const int nsplit = (int)std::max<int64_t>(1, (target + bricks - 1) / std::max<int64_t>(bricks, 1));
+      for (size_t i = 0; i < la.size(); ++i) {
+        la[i].L.nsplit = std::min(nsplit, kLatticeZ + 2 * la[i].L.Ez);
+        lb[i] *= la[i].L.nsplit;
+        if (la[i].L.nsplit > 1) zb[i] = ew_blocks(za[i].words);
+        else za[i].words = 0;
+      }
+      chk(make_table(B->conv[dir], ca, cb));
+      chk(make_table(B->zero_u[dir], za, zb));
+      chk(make_table(B->lattice[dir], la, lb, sm));
+    }
+    {  // top level of every replica
+      std::vector<TopKArgs> ta;
+      std::vector<int> tb;
+      for (const BatchRep& r : reps) {
+        Plan& P = *r.plan;
+        const int top = P.levels - 1;
+        void* const* q = dir ? P.d.aq : P.d.gq;
+        void* const* u = dir ? P.d.au : P.d.gu;
+        ta.push_back(TopKArgs{(const double*)q[top], (float*)u[top], P.d.topu, dims_of(P, top), P.d.topK,
+                              P.top_table_dims[0], P.top_table_dims[1]});
+        tb.push_back((int)blocks_for(grid_points(P, top), kTopWarps));
+      }
+      chk(make_table(B->top[dir], ta, tb));
+    }
+    // prolongation k+1 -> k: three passes (coarse -> tmp[0] -> tmp[1] -> fine, the last one adding), FP32
+    B->prol[dir].resize(3 * std::max(B->maxlev - 1, 0));
+    for (int k = B->maxlev - 2; k >= 0; --k)
+      for (int i = 0; i < 3; ++i) {
+        std::vector<AxisKArgs<float>> pa;
+        std::vector<int> pb;
+        for (const BatchRep& r : reps) {
+          Plan& P = *r.plan;
+          AxisKArgs<float> a{};
+          int nb = 0;
+          if (k + 1 < P.levels) {
+            void* const* u = dir ? P.d.au : P.d.gu;
+            const float* src[3] = {(const float*)u[k + 1], (const float*)P.d.tmp[0], (const float*)P.d.tmp[1]};
+            float* dst[3] = {(float*)P.d.tmp[0], (float*)P.d.tmp[1], (float*)u[k]};
+            int cur[3] = {P.n[k + 1][0], P.n[k + 1][1], P.n[k + 1][2]};
+            for (int j = 0; j < i; ++j) cur[2 - j] = P.n[k][2 - j];
+            const int ax = 2 - i;  // z, then y, then x
+            for (int d = 0; d < 3; ++d) a.A.nin[d] = cur[d];
+            cur[ax] = P.n[k][ax];
+            for (int d = 0; d < 3; ++d) a.A.nout[d] = cur[d];
+            a.A.axis = ax;
+            a.A.lo_in = P.lo[k + 1][ax];
+            a.A.lo_out = P.lo[k][ax];
+            a.A.periodic = P.P.periodic;
+            a.in = src[i];
+            a.out = dst[i];
+            a.acc = (i == 2) ? 1 : 0;
+            nb = ew_blocks((int64_t)cur[0] * cur[1] * cur[2]);
+          }
+          pa.push_back(a);
+          pb.push_back(nb);
+        }
+        chk(make_table(B->prol[dir][3 * k + i], pa, pb));
+      }
+    {  // interpolation and assembly
+      std::vector<InterpKArgs<float, double>> ia;
+      std::vector<int> ib;
+      std::vector<EnergyKArgs> ea;
+      std::vector<int> eb;
+      size_t sm = 0;
+      for (const BatchRep& r : reps) {
+        Plan& P = *r.plan;
+        auto K = dir ? interp_kargs<float, double>(P, true, nullptr, nullptr, r.grad_energy, r.grad_pos, r.grad_q, nullptr)
+                     : interp_kargs<float, double>(P, false, r.phi, r.force, nullptr, nullptr, nullptr, P.d.partial);
+        const int nb = K.nbx * K.nby * (int)blocks_for(P.nc[2], K.AA.B);
+        ia.push_back(K);
+        ib.push_back(r.n > 0 ? nb : 0);
+        sm = std::max(sm, sizeof(float) * (size_t)K.AA.pd * K.AA.pd * K.AA.pd);
+        ea.push_back(EnergyKArgs{P.d.partial, r.n > 0 ? nb : 0, r.energy});
+        eb.push_back(1);
+      }
+      chk(make_table(B->interp[dir], ia, ib, sm));
+      if (dir == 0) chk(make_table(B->energy, ea, eb));
+    }
+  }
+  (void)R;
+  if (e != cudaSuccess) {
+    grid_batch_free(B);
+    return e;
+  }
+  *out = B;
+  return cudaSuccess;
+}
+
+template <typename A, typename K>
+void launch_table(const BatchTable<A>& t, K kernel, int threads, cudaStream_t st) {
+  if (t.total > 0) kernel<<<t.total, threads, t.smem, st>>>(t.args, t.first, t.nrep);
+}
+
+cudaError_t grid_batch_sweep(GridBatch* B, bool backward, cudaStream_t st) {
+  const int d = backward ? 1 : 0;
+  if (backward && !B->has_backward) return cudaErrorInvalidValue;
+  const bool o3 = B->order == 3;
+  launch_table(B->zero_fx, kb_zero, kEw, st);
+  launch_table(B->anterp, o3 ? kb_anterp_fx<3> : kb_anterp_fx<5>, 256, st);
+  launch_table(B->fx[d], kb_fx_to_f64, kEw, st);
+  for (int k = 0; k + 1 < B->maxlev; ++k)
+    for (int ax = 0; ax < 3; ++ax)
+      launch_table(B->restr[d][3 * k + ax], o3 ? kb_restrict_axis<3> : kb_restrict_axis<5>, kEw, st);
+  launch_table(B->conv[d], kb_f64_to_f32, kEw, st);
+  launch_table(B->zero_u[d], kb_zero, kEw, st);
+  launch_table(B->lattice[d], kb_lattice_f2, 32 * kLatticeZ, st);
+  launch_table(B->top[d], kb_top, 32 * kTopWarps, st);
+  for (int k = B->maxlev - 2; k >= 0; --k)
+    for (int i = 0; i < 3; ++i)
+      launch_table(B->prol[d][3 * k + i], o3 ? kb_prolong_axis<3> : kb_prolong_axis<5>, kEw, st);
+  return cudaGetLastError();
+}
+
+cudaError_t grid_batch_interp(GridBatch* B, bool backward, cudaStream_t st) {
+  const bool o3 = B->order == 3;
+  if (backward) {
+    if (!B->has_backward) return cudaErrorInvalidValue;
+    launch_table(B->interp[1], o3 ? kb_interp_bwd<3> : kb_interp_bwd<5>, 256, st);
+  } else {
+    launch_table(B->interp[0], o3 ? kb_interp_fwd<3> : kb_interp_fwd<5>, 256, st);
+    launch_table(B->energy, kb_energy_final, 1024, st);
+  }
   return cudaGetLastError();
 }
 
@@ -1400,6 +2009,13 @@ cudaError_t configure_kernels() {
     if (r != cudaSuccess) e = r;
   };
   set((const void*)k_lattice_f2<kLatticeLP>);
+  set((const void*)kb_lattice_f2);
+  set((const void*)kb_anterp_fx<3>);
+  set((const void*)kb_anterp_fx<5>);
+  set((const void*)kb_interp_fwd<3>);
+  set((const void*)kb_interp_fwd<5>);
+  set((const void*)kb_interp_bwd<3>);
+  set((const void*)kb_interp_bwd<5>);
   set((const void*)k_anterp_fx<3>);
   set((const void*)k_anterp_fx<5>);
   set((const void*)k_anterp_patch<double, double, 3>);
@@ -1421,20 +2037,6 @@ cudaError_t configure_kernels() {
   set((const void*)k_interp_bwd<double, 5, double>);
   set((const void*)k_interp_bwd<double, 5, float>);
   return e;
-}
-
-template cudaError_t launch_interp_forward<double>(Plan&, int64_t, double*, double*, double*, cudaStream_t);
-template cudaError_t launch_interp_forward<float>(Plan&, int64_t, double*, float*, float*, cudaStream_t);
-template cudaError_t launch_interp_backward<double>(Plan&, int64_t, const double*, double*, double*, cudaStream_t);
-template cudaError_t launch_interp_backward<float>(Plan&, int64_t, const double*, float*, float*, cudaStream_t);
-
-cudaError_t launch_grid_to_double(Plan& P, const void* src, double* dst, int64_t count, bool is_double,
-                                  cudaStream_t st) {
-  unsigned nb = blocks_for(count, 256);
-  if (count <= 0) return cudaSuccess;
-  if (P.fp64 || is_double) k_to_double<double><<<nb, 256, 0, st>>>((const double*)src, dst, count);
-  else k_to_double<float><<<nb, 256, 0, st>>>((const float*)src, dst, count);
-  return cudaGetLastError();
 }
 
 }  // namespace msm

@@ -15,6 +15,7 @@
 // error-free TwoSum (compensated accumulation).
 #include <climits>
 #include <cmath>
+#include <new>
 
 #include "msm_internal.h"
 
@@ -331,18 +332,38 @@ struct SegTable {
   float2 shift[2 * kMaxRows];   // (y, z) shift of the row
 };
 
+// Arguments of the packed pair kernel (one system).
+struct PairKArgs {
+  const R4<float>* atoms;
+  const int* cell_start;
+  const int4* rows;
+  int nrows;
+  PairArgs A;
+  PairCoef C;
+  float cwx, cwy, cwz;
+  int ncell;
+  float* phis;
+  R4<float>* fs;
+};
+
 template <int M>
-__global__ void __launch_bounds__(32 * kWarps, 6) k_short_range_f2(
-    const R4<float>* __restrict__ atoms, const int* __restrict__ cell_start,
-    const int4* __restrict__ rows, int nrows, PairArgs A, PairCoef C, float cwx, float cwy, float cwz, int ncell,
-    float* __restrict__ phis, R4<float>* __restrict__ fs) {
+__device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk) {
+  const R4<float>* __restrict__ atoms = K.atoms;
+  const int* __restrict__ cell_start = K.cell_start;
+  const int4* __restrict__ rows = K.rows;
+  const int nrows = K.nrows, ncell = K.ncell;
+  const PairArgs& A = K.A;
+  const PairCoef C = K.C;
+  const float cwx = K.cwx, cwy = K.cwy, cwz = K.cwz;
+  float* __restrict__ phis = K.phis;
+  R4<float>* __restrict__ fs = K.fs;
   __shared__ QueueF queue[kWarps];
   __shared__ R4<float> home[kWarps][kBatch];
   __shared__ SegTable tables[kWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   QueueF& Q = queue[warp];
   SegTable& T = tables[warp];
-  const int cell = blockIdx.x * kWarps + warp;
+  const int cell = blk * kWarps + warp;
   if (cell >= ncell) return;  // warp-uniform
   const int ncx = A.nc[0], ncy = A.nc[1], ncz = A.nc[2];
   const int cx = cell % ncx, cy = (cell / ncx) % ncy, cz = cell / (ncx * ncy);
@@ -533,6 +554,18 @@ __global__ void __launch_bounds__(32 * kWarps, 6) k_short_range_f2(
   }
 }
 
+template <int M>
+__global__ void __launch_bounds__(32 * kWarps, 6) k_short_range_f2(PairKArgs a) {
+  short_range_f2_body<M>(a, blockIdx.x);
+}
+
+template <int M>
+__global__ void __launch_bounds__(32 * kWarps, 6) kb_short_range_f2(const PairKArgs* __restrict__ tab,
+                                                                   const int* __restrict__ first, int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  short_range_f2_body<M>(tab[r], blockIdx.x - first[r]);
+}
+
 template <typename T, bool COMP>
 void launch_t(Plan& P, cudaStream_t st) {
   PairArgs A = pair_args(P);
@@ -559,36 +592,41 @@ void launch_t(Plan& P, cudaStream_t st) {
 
 }  // namespace
 
-void launch_f2(Plan& P, cudaStream_t st) {
-  PairArgs A = pair_args(P);
-  int blocks = (P.ncell + kWarps - 1) / kWarps;
-  auto* at = (const R4<float>*)P.d.atoms;
-  auto* ph = (float*)P.d.phis;
-  auto* fs = (R4<float>*)P.d.fs;
+PairKArgs pair_kargs(const Plan& P) {
+  PairKArgs K;
+  K.A = pair_args(P);
+  K.atoms = (const R4<float>*)P.d.atoms;
+  K.cell_start = P.d.cell_start;
+  K.rows = P.d.cell_rows;
+  K.nrows = P.nrows;
+  K.ncell = P.ncell;
+  K.phis = (float*)P.d.phis;
+  K.fs = (R4<float>*)P.d.fs;
   // gamma coefficients c_k (Taylor series of s^(-1/2) about s = 1, truncated at m)
   static const double c[4][4] = {{0, 0, 0, 0}, {1.5, -0.5, 0, 0}, {1.875, -1.25, 0.375, 0},
                                  {2.1875, -2.1875, 1.3125, -0.3125}};
   const int m = P.P.splitting;
   const double a = P.P.cutoff;
-  PairCoef C;
   for (int k = 0; k < 4; ++k) {
     float g = (k <= m) ? (float)(-c[m][k] / std::pow(a, 2 * k + 1)) : 0.f;
-    C.G[k] = make_float2(g, g);
+    K.C.G[k] = make_float2(g, g);
   }
   for (int k = 0; k < 3; ++k) {
     float d = (k + 1 <= m) ? (float)(2.0 * (k + 1) * c[m][k + 1] / std::pow(a, 2 * k + 3)) : 0.f;
-    C.D[k] = make_float2(d, d);
+    K.C.D[k] = make_float2(d, d);
   }
-  const float cwx = (float)P.cw[0], cwy = (float)P.cw[1], cwz = (float)P.cw[2];
-  if (m == 1)
-    k_short_range_f2<1><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_rows, P.nrows, A, C, cwx, cwy,
-                                                        cwz, P.ncell, ph, fs);
-  else if (m == 2)
-    k_short_range_f2<2><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_rows, P.nrows, A, C, cwx, cwy,
-                                                        cwz, P.ncell, ph, fs);
-  else
-    k_short_range_f2<3><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_rows, P.nrows, A, C, cwx, cwy,
-                                                        cwz, P.ncell, ph, fs);
+  K.cwx = (float)P.cw[0];
+  K.cwy = (float)P.cw[1];
+  K.cwz = (float)P.cw[2];
+  return K;
+}
+
+void launch_f2(Plan& P, cudaStream_t st) {
+  const PairKArgs K = pair_kargs(P);
+  const int blocks = (P.ncell + kWarps - 1) / kWarps;
+  if (P.P.splitting == 1) k_short_range_f2<1><<<blocks, 32 * kWarps, 0, st>>>(K);
+  else if (P.P.splitting == 2) k_short_range_f2<2><<<blocks, 32 * kWarps, 0, st>>>(K);
+  else k_short_range_f2<3><<<blocks, 32 * kWarps, 0, st>>>(K);
 }
 
 cudaError_t launch_short_range(Plan& P, int64_t n, cudaStream_t st) {
@@ -597,6 +635,46 @@ cudaError_t launch_short_range(Plan& P, int64_t n, cudaStream_t st) {
   else launch_f2(P, st);
   P.launches += 1;
   return cudaGetLastError();
+}
+
+struct PairBatch {
+  BatchTable<PairKArgs> cells;  // kWarps cells per block
+  int splitting = 2;
+};
+
+cudaError_t pair_batch_build(const std::vector<BatchRep>& reps, PairBatch** out) {
+  *out = nullptr;
+  PairBatch* b = new (std::nothrow) PairBatch();
+  if (!b) return cudaErrorMemoryAllocation;
+  std::vector<PairKArgs> ka;
+  std::vector<int> kb;
+  for (const BatchRep& r : reps) {
+    ka.push_back(pair_kargs(*r.plan));
+    kb.push_back(r.n > 0 ? (r.plan->ncell + kWarps - 1) / kWarps : 0);
+    b->splitting = r.plan->P.splitting;
+  }
+  cudaError_t e = make_table(b->cells, ka, kb);
+  if (e != cudaSuccess) {
+    pair_batch_free(b);
+    return e;
+  }
+  *out = b;
+  return cudaSuccess;
+}
+
+cudaError_t pair_batch_launch(PairBatch* b, cudaStream_t st) {
+  const int nb = b->cells.total;
+  if (nb == 0) return cudaSuccess;
+  if (b->splitting == 1) kb_short_range_f2<1><<<nb, 32 * kWarps, 0, st>>>(b->cells.args, b->cells.first, b->cells.nrep);
+  else if (b->splitting == 2) kb_short_range_f2<2><<<nb, 32 * kWarps, 0, st>>>(b->cells.args, b->cells.first, b->cells.nrep);
+  else kb_short_range_f2<3><<<nb, 32 * kWarps, 0, st>>>(b->cells.args, b->cells.first, b->cells.nrep);
+  return cudaGetLastError();
+}
+
+void pair_batch_free(PairBatch* b) {
+  if (!b) return;
+  b->cells.release();
+  delete b;
 }
 
 }  // namespace msm

@@ -140,6 +140,91 @@ struct Plan {
   int64_t evals = 0;
 };
 
+// ---- batches of independent systems (one launch per stage over all replicas) ----
+// A batched launch numbers the blocks of all replicas consecutively; first[r]
+// is the first block of replica r (first[nrep] = total) and every block finds
+// its replica by binary search and reads that replica's kernel arguments from
+// a table in device memory.
+#ifdef __CUDACC__
+__device__ __forceinline__ int batch_rep(const int* __restrict__ first, int nrep, int b) {
+  int lo = 0, hi = nrep - 1;  // largest r with first[r] <= b (replicas without blocks are skipped)
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(first + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+#endif
+
+// A table of per-replica kernel arguments and block offsets in device memory.
+template <typename A>
+struct BatchTable {
+  A* args = nullptr;
+  int* first = nullptr;
+  int nrep = 0;
+  int total = 0;       // blocks over all replicas
+  size_t smem = 0;     // dynamic shared memory per block (the largest over the replicas)
+  void release() {
+    if (args) cudaFree(args);
+    if (first) cudaFree(first);
+    args = nullptr;
+    first = nullptr;
+  }
+};
+
+// Uploads per-replica arguments and block counts (synchronous; batch set-up only).
+template <typename A>
+cudaError_t make_table(BatchTable<A>& t, const std::vector<A>& args, const std::vector<int>& blocks, size_t smem = 0) {
+  t.release();
+  t.nrep = (int)args.size();
+  std::vector<int> first(args.size() + 1, 0);
+  for (size_t r = 0; r < args.size(); ++r) first[r + 1] = first[r] + blocks[r];
+  t.total = first.back();
+  t.smem = smem;
+  cudaError_t e = cudaMalloc((void**)&t.args, sizeof(A) * (args.empty() ? 1 : args.size()));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t.first, sizeof(int) * first.size());
+  if (e == cudaSuccess && !args.empty()) e = cudaMemcpy(t.args, args.data(), sizeof(A) * args.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(t.first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+// One replica of a batch: its plan and its slices of the caller's arrays
+// (device pointers; outputs may be NULL where the batch entry point allows).
+struct BatchRep {
+  Plan* plan;
+  int64_t n;
+  const double* pos;
+  const double* q;
+  double* energy;
+  double* phi;
+  double* force;
+  const double* grad_energy;
+  double* grad_pos;
+  double* grad_q;
+};
+
+// Batched stages, each a set of launches over all replicas on one stream.
+// build() uploads the tables (synchronous, allocates); launch() only
+// enqueues kernels.  The replicas must be mixed-precision plans of one
+// interpolation order and one splitting.
+struct BinBatch;
+struct PairBatch;
+struct GridBatch;
+cudaError_t bin_batch_build(const std::vector<BatchRep>& reps, BinBatch** out);
+cudaError_t bin_batch_launch(BinBatch* b, cudaStream_t st);
+void bin_batch_free(BinBatch* b);
+cudaError_t pair_batch_build(const std::vector<BatchRep>& reps, PairBatch** out);
+cudaError_t pair_batch_launch(PairBatch* b, cudaStream_t st);
+void pair_batch_free(PairBatch* b);
+// The grid passes: anterpolation and the sweep through the levels, then
+// interpolation with assembly (forward: phi, F and the energies; backward,
+// built only when every replica has grad_energy: dL/dq and dL/dr).
+cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, GridBatch** out);
+cudaError_t grid_batch_sweep(GridBatch* b, bool backward, cudaStream_t st);
+cudaError_t grid_batch_interp(GridBatch* b, bool backward, cudaStream_t st);
+void grid_batch_free(GridBatch* b);
+
 // ---- host helpers (plan.cpp) ----
 int validate_params(const msm_params* p);  // host only, no CUDA calls
 int validate_tuning(const msm_tuning* t);  // host only, no CUDA calls

@@ -267,7 +267,8 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   double wfill = std::cbrt(fill * vol / (double)p.max_atoms);
   double wmin = std::max(0.5 * p.cutoff, std::min(wfill, 0.75 * p.cutoff));
   for (int d = 0; d < 3; ++d) {
-    int c = (int)std::floor(p.box[d] / wmin);
+    // the cell count nearest to the target width, but cells at least a/2 wide
+    int c = std::min((int)std::lround(p.box[d] / wmin), (int)std::floor(p.box[d] / (0.5 * p.cutoff)));
     if (p.periodic && c < 5) c = (int)std::floor(p.box[d] / (0.5 * p.cutoff));
     if (c < 1) c = 1;
     if (p.periodic && c < 5) return MSM_ERR_UNSUPPORTED;  // the 5-cell walk would alias images

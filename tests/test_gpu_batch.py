@@ -81,26 +81,60 @@ def test_batch_graph_replays(dev):
     pos = torch.tensor(np.vstack([p for (_, p, _) in reps]), device=dev)
     q = torch.tensor(np.concatenate([qq for (_, _, qq) in reps]), device=dev)
     E = torch.zeros(len(reps), dtype=torch.float64, device=dev)
+    phi = torch.zeros(n, dtype=torch.float64, device=dev)
     F = torch.zeros((n, 3), dtype=torch.float64, device=dev)
-    gE = torch.ones(len(reps), dtype=torch.float64, device=dev)
+    gE = torch.linspace(0.5, 2.0, len(reps), dtype=torch.float64, device=dev)
     gp = torch.zeros((n, 3), dtype=torch.float64, device=dev)
     gq = torch.zeros(n, dtype=torch.float64, device=dev)
     batch = MSMBatch(plans)
-    g = batch.graph(pos, q, counts, E, None, F, gE, gp, gq)
+    # mixed plans of one order and splitting: every stage one launch over all replicas
+    g = batch.graph(pos, q, counts, E, phi, F, gE, gp, gq)
     torch.cuda.synchronize()
     assert E.abs().sum().item() == 0.0                  # capturing runs nothing
     direct = MSMBatch(make_plans(reps, "mixed"))
-    E2, _, F2 = direct.eval(pos, q, counts)
+    E2, phi2, F2 = direct.eval(pos, q, counts)
+    gscale = torch.cat([gE[r].expand(c) for r, c in enumerate(counts)])
     for _ in range(2):
         g.launch()
         torch.cuda.synchronize()
         assert torch.allclose(E, E2, rtol=1e-6, atol=0)
         assert rel_rms(F.cpu().numpy(), F2.cpu().numpy()) <= 1e-5
-        assert rel_rms(gp.cpu().numpy(), -F2.cpu().numpy()) <= 1e-5
+        assert rel_rms(phi.cpu().numpy(), phi2.cpu().numpy()) <= 1e-6
+        assert rel_rms(gp.cpu().numpy(), (-gscale[:, None] * F2).cpu().numpy()) <= 1e-5
+        assert rel_rms(gq.cpu().numpy(), (gscale * phi2).cpu().numpy()) <= 1e-5
+        for p in plans:
+            p.check_status()
+    # one replica of the graph against the oracle
+    L, p3, q3 = reps[3]
+    ref = O.msm(O.Params(box=(L,) * 3, periodic=True, cutoff=6.0, spacing=1.5, order=3, split=2), p3, q3)
+    s = sum(counts[:3])
+    assert abs(E[3].item() - ref["E"]) <= 1e-6 * abs(ref["E"])
+    assert rel_rms(F[s:s + counts[3]].cpu().numpy(), ref["F"]) <= 1e-5
     # new inputs in the same buffers are picked up by the next replay
     pos.add_(0.37)
     g.launch()
     E3, _, _ = direct.eval(pos, q, counts)
     torch.cuda.synchronize()
     assert torch.allclose(E, E3, rtol=1e-6, atol=0)
+    g.close()
+
+
+def test_batch_graph_fallback_fp64(dev):
+    """FP64 plans (or plans of different orders) are not batched kernel by
+    kernel; their graph forks the replicas' own launch sequences instead."""
+    from paper_1402_7216_gb300 import MSMBatch
+    reps = replicas(seed=42, sizes=(900, 1500, 600))
+    plans = make_plans(reps, "fp64")
+    counts = [len(q) for (_, _, q) in reps]
+    n = sum(counts)
+    pos = torch.tensor(np.vstack([p for (_, p, _) in reps]), device=dev)
+    q = torch.tensor(np.concatenate([qq for (_, _, qq) in reps]), device=dev)
+    E = torch.zeros(len(reps), dtype=torch.float64, device=dev)
+    F = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    g = MSMBatch(plans).graph(pos, q, counts, E, None, F)
+    g.launch()
+    E2, _, F2 = MSMBatch(make_plans(reps, "fp64")).eval(pos, q, counts)
+    torch.cuda.synchronize()
+    assert torch.allclose(E, E2, rtol=1e-12, atol=0)
+    assert rel_rms(F.cpu().numpy(), F2.cpu().numpy()) <= 1e-12
     g.close()
