@@ -618,6 +618,7 @@ struct LatticeArgs {
   int Ex, Ey, Ez;
   int nsplit;  // blocks sharing one brick's input planes
   int nbz;     // bricks along z
+  int txn, tyn;  // FP32 kernel: lanes along x (LP outputs each) and along y (two rows each) of a warp's tile
 };
 
 template <typename T, bool COMP>
@@ -740,21 +741,24 @@ __device__ __forceinline__ void stage_plane_async(float* plane, const float* __r
 // every tap t, so one pair of shared loads serves up to 8 FFMA2 (LP + 7 loads
 // per 8 LP FFMA2).  Each plane's partial sums are added into the totals
 // (blocked summation over planes).
-template <int LP>
+// TXC, TYC: the warp tile fixed at compile time (the common 32 x 16 tile),
+// or 0 to take it from L (other shapes, batches of uneven grids).
+template <int LP, int TXC, int TYC>
 __device__ __forceinline__ void lattice_f2_body(const float* __restrict__ q, float* __restrict__ u, const GridDims G,
                                                 const Segment2* __restrict__ seg, const int* __restrict__ seg_start,
                                                 const LatticeArgs L, float scale, int bx, int by, int bzs) {
-  constexpr int TXN = LBX / LP, TYN = 32 / TXN, LBY = 2 * TYN;
+  const int TXN = TXC ? TXC : L.txn, TYN = TYC ? TYC : L.tyn, TW = LP * TXN, LBY = 2 * TYN;  // tile: TW (x) by LBY (y)
   extern __shared__ unsigned char smem_raw[];
   const int Ex = L.Ex, Ey = L.Ey, Ez = L.Ez;
-  const int SXw = LBX + 2 * Ex + kSeg, SX = SXw | 1, SY = LBY + 2 * Ey;
+  const int SXw = TW + 2 * Ex + kSeg, SX = SXw | 1, SY = LBY + 2 * Ey;
   float* buf0 = reinterpret_cast<float*>(smem_raw);
   float* buf1 = buf0 + SX * SY;
   int* col = reinterpret_cast<int*>(buf1 + SX * SY);  // window offsets (SXw + SY ints)
   int* row = col + SXw;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tx = lane % TXN, ty = lane / TXN;
+  const bool active = (TXC * TYC == 32) || ty < TYN;  // lanes past TXN * TYN only help with staging
   const int bz = bzs % L.nbz, part = bzs / L.nbz;
-  const int x0 = bx * LBX, y0 = by * LBY, z0 = bz * kLatticeZ, zo = z0 + warp;
+  const int x0 = bx * TW, y0 = by * LBY, z0 = bz * kLatticeZ, zo = z0 + warp;
   const int nplanes = kLatticeZ + 2 * Ez, per = (nplanes + L.nsplit - 1) / L.nsplit;
   const int zbeg = z0 - Ez + part * per, zend = min(z0 - Ez + nplanes, zbeg + per);
   float2 acc[LP];  // (row ty, row ty + TYN) of the LP x outputs
@@ -772,7 +776,7 @@ __device__ __forceinline__ void lattice_f2_body(const float* __restrict__ q, flo
     asm volatile("cp.async.wait_group 1;\n" ::);  // plane zi has landed (this thread's copies)
     __syncthreads();                               // ... and everyone else's
     const int dz = zi - zo;
-    if (dz >= -Ez && dz <= Ez && zo < G.n[2]) {  // warp-uniform
+    if (active && dz >= -Ez && dz <= Ez && zo < G.n[2]) {
       float2 part_[LP];
 #pragma unroll
       for (int j = 0; j < LP; ++j) part_[j] = make_float2(0.f, 0.f);
@@ -795,7 +799,7 @@ __device__ __forceinline__ void lattice_f2_body(const float* __restrict__ q, flo
     __syncthreads();  // the buffer just read is restaged two planes from now
   }
   asm volatile("cp.async.wait_group 0;\n" ::);
-  if (zo >= G.n[2]) return;
+  if (zo >= G.n[2] || !active) return;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int y = y0 + ty + TYN * r;
@@ -811,12 +815,12 @@ __device__ __forceinline__ void lattice_f2_body(const float* __restrict__ q, flo
   }
 }
 
-template <int LP>
+template <int LP, int TXC, int TYC>
 __global__ void __launch_bounds__(32 * kLatticeZ, 7) k_lattice_f2(const float* __restrict__ q, float* __restrict__ u,
                                                                GridDims G, const Segment2* __restrict__ seg,
                                                                const int* __restrict__ seg_start, LatticeArgs L,
                                                                float scale) {
-  lattice_f2_body<LP>(q, u, G, seg, seg_start, L, scale, blockIdx.x, blockIdx.y, blockIdx.z);
+  lattice_f2_body<LP, TXC, TYC>(q, u, G, seg, seg_start, L, scale, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---- top level: all pairs of the coarsest grid, FP64 ----
@@ -1396,6 +1400,34 @@ __global__ void k_f64_to_f32(const double* __restrict__ src, float* __restrict__
   f64_to_f32_body(src, dst, count, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// Warp tile of the FP32 lattice kernel for an n0 x n1 plane: txn lanes of
+// kLatticeLP x outputs by tyn lanes of two rows (txn * tyn <= 32).  Every
+// tile costs one warp's pass over the stencil whatever its idle lanes, plus
+// the staging of its input window; the cost counts both (a warp's stencil
+// pass at a plane is ~14,000 instructions, staging ~1/3 instruction per
+// window element), so ragged small grids get tiles that fit them.
+static void lattice_tile(int n0, int n1, const int E[3], int& txn, int& tyn) {
+  double best = -1.0;
+  txn = 4;
+  tyn = 8;
+  for (int a = 1; a <= 32; ++a)
+    for (int b = 1; a * b <= 32; ++b) {
+      const double tiles = (double)((n0 + kLatticeLP * a - 1) / (kLatticeLP * a)) * ((n1 + 2 * b - 1) / (2 * b));
+      const double window = (double)(kLatticeLP * a + 2 * E[0] + kSeg) * (2 * b + 2 * E[1]);
+      const double cost = tiles * (14000.0 + window / 3.0);
+      if (best < 0 || cost < best) {
+        best = cost;
+        txn = a;
+        tyn = b;
+      }
+    }
+}
+
+static size_t lattice_smem(int txn, int tyn, const int E[3]) {
+  const int SXw = kLatticeLP * txn + 2 * E[0] + kSeg, SX = SXw | 1, SY = 2 * tyn + 2 * E[1];
+  return sizeof(float) * 2 * SX * SY + sizeof(int) * (SXw + SY);
+}
+
 // Lattice cutoff of level k from the FP64 charges qk.  Mixed precision first
 // converts the level's charges to FP32 once (on GB300 the conversion runs on
 // the slow FP64 pipe, so it must not sit in the per-tap loop).
@@ -1410,28 +1442,36 @@ void lattice_t(Plan& P, int k, const double* qk64, T* uk, cudaStream_t st) {
     P.launches += 1;
     qk = (const T*)qf;
   }
-  const int LBY = f32 ? 2 * (32 / (LBX / kLatticeLP)) : 8;
   LatticeArgs L;
   L.Ex = P.E[0];
   L.Ey = P.E[1];
   L.Ez = P.E[2];
+  L.txn = 4;  // one system: the 32 x 16 tile, fixed at compile time, on every level (the runtime-tile
+  L.tyn = 8;  // kernel is slower per tap than the saving on ragged coarse levels)
+  const int TW = f32 ? kLatticeLP * L.txn : LBX, LBY = f32 ? 2 * L.tyn : 8;
   const int LBZb = f32 ? kLatticeZ : LBZ;  // output planes (warps) per block
   L.nbz = (int)blocks_for(G.n[2], LBZb);
-  int64_t bricks = (int64_t)blocks_for(G.n[0], LBX) * blocks_for(G.n[1], LBY) * L.nbz;
+  int64_t bricks = (int64_t)blocks_for(G.n[0], TW) * blocks_for(G.n[1], LBY) * L.nbz;
   const int64_t target = (int64_t)P.lattice_waves * 152 * 4 / LBZb;
   L.nsplit = (int)std::min<int64_t>(LBZb + 2 * L.Ez, std::max<int64_t>(1, (target + bricks - 1) / bricks));
   if (L.nsplit > 1) {
     cudaMemsetAsync(uk, 0, sizeof(T) * (size_t)grid_points(P, k), st);
     P.launches += 1;
   }
-  dim3 grid(blocks_for(G.n[0], LBX), blocks_for(G.n[1], LBY), L.nbz * L.nsplit);
+  dim3 grid(blocks_for(G.n[0], TW), blocks_for(G.n[1], LBY), L.nbz * L.nsplit);
   int SX = (LBX + 2 * P.E[0] + kSeg) | 1, SY = LBY + 2 * P.E[1];
   // FP32 double-buffers its planes and keeps the window offsets (SXw + SY ints)
-  size_t sm = f32 ? sizeof(float) * 2 * SX * SY + sizeof(int) * (LBX + 2 * P.E[0] + kSeg + SY) : sizeof(T) * SX * SY;
+  size_t sm = f32 ? lattice_smem(L.txn, L.tyn, P.E) : sizeof(T) * SX * SY;
   T scale = (T)std::ldexp(1.0, -k);
   if (f32) {
-    k_lattice_f2<kLatticeLP><<<grid, 32 * kLatticeZ, sm, st>>>((const float*)qk, (float*)uk, G, (const Segment2*)P.d.seg2, P.d.seg_start,
-                                        L, (float)scale);
+    if (L.txn == 4 && L.tyn == 8)
+      k_lattice_f2<kLatticeLP, 4, 8><<<grid, 32 * kLatticeZ, sm, st>>>((const float*)qk, (float*)uk, G,
+                                                                      (const Segment2*)P.d.seg2, P.d.seg_start, L,
+                                                                      (float)scale);
+    else
+      k_lattice_f2<kLatticeLP, 0, 0><<<grid, 32 * kLatticeZ, sm, st>>>((const float*)qk, (float*)uk, G,
+                                                                      (const Segment2*)P.d.seg2, P.d.seg_start, L,
+                                                                      (float)scale);
   } else {
     k_lattice<T, false><<<grid, 128, sm, st>>>(qk, uk, G, (const Segment<T>*)P.d.seg, P.d.seg_start, L, scale);
   }
@@ -1666,8 +1706,8 @@ __global__ void __launch_bounds__(32 * kLatticeZ) kb_lattice_f2(const LatKArgs* 
   const int r = batch_rep(first, nrep, blockIdx.x);
   const LatKArgs& a = tab[r];
   const int b = blockIdx.x - first[r];
-  lattice_f2_body<kLatticeLP>(a.q, a.u, a.G, a.seg, a.seg_start, a.L, a.scale, b % a.nbx, (b / a.nbx) % a.nby,
-                              b / (a.nbx * a.nby));
+  lattice_f2_body<kLatticeLP, 0, 0>(a.q, a.u, a.G, a.seg, a.seg_start, a.L, a.scale, b % a.nbx, (b / a.nbx) % a.nby,
+                                    b / (a.nbx * a.nby));
 }
 
 __global__ void __launch_bounds__(32 * kTopWarps) kb_top(const TopKArgs* __restrict__ tab,
@@ -1844,8 +1884,9 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
           ca.push_back(ConvKArgs{(const double*)q[k], qf, np});
           cb.push_back(ew_blocks(np));
           GridDims G = dims_of(P, k);
-          const int LBY = 2 * (32 / (LBX / kLatticeLP));
           LatKArgs a;
+          lattice_tile(G.n[0], G.n[1], P.E, a.L.txn, a.L.tyn);
+          const int TW = kLatticeLP * a.L.txn, LBY = 2 * a.L.tyn;
           a.q = qf;
           a.u = (float*)u[k];
           a.G = G;
@@ -1855,7 +1896,7 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
           a.L.Ey = P.E[1];
           a.L.Ez = P.E[2];
           a.L.nbz = (int)blocks_for(G.n[2], kLatticeZ);
-          a.nbx = (int)blocks_for(G.n[0], LBX);
+          a.nbx = (int)blocks_for(G.n[0], TW);
           a.nby = (int)blocks_for(G.n[1], LBY);
           a.L.nsplit = 1;  // set below, once the bricks of every replica and level are known
           a.scale = (float)std::ldexp(1.0, -k);
@@ -1863,8 +1904,7 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
           lb.push_back(a.nbx * a.nby * a.L.nbz);
           za.push_back(ZeroKArgs{(unsigned*)u[k], np});
           zb.push_back(0);
-          const int SX = (LBX + 2 * P.E[0] + kSeg) | 1, SY = LBY + 2 * P.E[1];
-          sm = std::max(sm, sizeof(float) * 2 * SX * SY + sizeof(int) * (LBX + 2 * P.E[0] + kSeg + SY));
+          sm = std::max(sm, lattice_smem(a.L.txn, a.L.tyn, P.E));
         }
       }
       // one launch holds the bricks of every replica and level, so the input
@@ -2008,7 +2048,8 @@ cudaError_t configure_kernels() {
     cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (r != cudaSuccess) e = r;
   };
-  set((const void*)k_lattice_f2<kLatticeLP>);
+  set((const void*)k_lattice_f2<kLatticeLP, 4, 8>);
+  set((const void*)k_lattice_f2<kLatticeLP, 0, 0>);
   set((const void*)kb_lattice_f2);
   set((const void*)kb_anterp_fx<3>);
   set((const void*)kb_anterp_fx<5>);
