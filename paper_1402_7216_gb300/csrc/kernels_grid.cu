@@ -1161,7 +1161,7 @@ __device__ __forceinline__ void interp_fwd_call(const InterpKArgs<T, OUT>& K, in
 }
 
 template <typename T, int ORDER, typename OUT>
-__global__ void __launch_bounds__(256) k_interp_fwd(
+__global__ void __launch_bounds__(256, 3) k_interp_fwd(
     const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm,
     const int* __restrict__ cell_start, AnterpArgs AA, const T* __restrict__ u0, GridDims G, AssembleArgs A,
     const T* __restrict__ phis, R4<T>* __restrict__ fs, R4<T>* __restrict__ glong, OUT* __restrict__ phi_out,
