@@ -34,9 +34,9 @@ struct Segment {
 };
 
 // The same run with each coefficient duplicated, for packed FP32x2 FMAs.
-struct Segment2 {
+struct alignas(16) Segment2 {
+  float2 g[kSeg];  // first, so that it loads as four 16-byte words
   int dy, dx0;
-  float2 g[kSeg];
 };
 
 // Per-precision device tables and buffers.
