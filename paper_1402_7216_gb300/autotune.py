@@ -111,3 +111,82 @@ def tuned_plan(pos, q, box, periodic, cutoff, spacing, **kw):
     tuning, _ = autotune(pos, q, box, periodic, cutoff, spacing, **kw2)
     return MSM(box=box, periodic=periodic, cutoff=cutoff, spacing=spacing, max_atoms=int(q.shape[0]),
                tuning=tuning, **kw2)
+
+
+# Batches: one tuning shared by every replica, timed on the captured batch
+# graph (forward + adjoint), the form msm_batch_graph_create runs.
+SEARCH_BATCH = [("lattice_waves", [8, 16]), ("patch_cells", [3, 4]), ("cell_fill", [20, 24])]
+
+
+def time_graph(graph, reps=5, warmup=2):
+    """Median CUDA-event time (ms) of one replay of a batch graph."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        graph.launch()
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        graph.launch()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    ms.sort()
+    return ms[len(ms) // 2]
+
+
+def batch_key(boxes, counts, cutoff, spacing, order, splitting, precision):
+    import hashlib
+    h = hashlib.sha1(repr((list(map(float, boxes)), list(map(int, counts)))).encode()).hexdigest()[:16]
+    return "batch|%s|a=%.4f|h=%.4f|p=%d|m=%d|%s" % (h, cutoff, spacing, order, splitting, precision)
+
+
+def autotune_batch(boxes, pos, q, counts, cutoff, spacing, order=3, splitting=2, precision="mixed", reps=5,
+                   use_cache=True, search=SEARCH_BATCH):
+    """Returns (tuning dict, {candidate: ms}) for a batch of periodic boxes
+    (edges `boxes`, atoms `counts`, concatenated `pos`, `q` on the device),
+    timing the batch graph with the adjoint; cached like autotune()."""
+    from . import MSMBatch
+    key = batch_key(boxes, counts, cutoff, spacing, order, splitting, precision)
+    path = cache_path()
+    if use_cache:
+        hit = _load(path).get(key)
+        if hit:
+            return dict(hit["tuning"]), {"cached": hit.get("ms")}
+    n, nrep = int(q.shape[0]), len(counts)
+    dev = q.device
+    E = torch.zeros(nrep, dtype=torch.float64, device=dev)
+    F = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    gE = torch.ones(nrep, dtype=torch.float64, device=dev)
+    gp = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    best, times = {}, {}
+
+    def run(t):
+        plans = [MSM(box=L, periodic=True, cutoff=cutoff, spacing=spacing, order=order, splitting=splitting,
+                     precision=precision, max_atoms=int(c), tuning=t) for L, c in zip(boxes, counts)]
+        g = MSMBatch(plans).graph(pos, q, counts, E, None, F, gE, gp, None)
+        try:
+            return time_graph(g, reps)
+        finally:
+            g.close()
+            for p in plans:
+                p.close()
+
+    best_ms = run(best)
+    times["default"] = best_ms
+    for field, values in search:
+        for v in values:
+            cand = dict(best)
+            cand[field] = v
+            label = ",".join("%s=%d" % kv for kv in sorted(cand.items()))
+            if label in times:
+                continue
+            ms = run(cand)
+            times[label] = ms
+            if ms < best_ms * 0.98:
+                best, best_ms = cand, ms
+    if use_cache:
+        data = _load(path)
+        data[key] = {"tuning": best, "ms": best_ms}
+        _store(path, data)
+    return best, times

@@ -45,3 +45,40 @@ def test_tuning_fields_are_checked():
     from paper_1402_7216_gb300 import MSM, MSMError
     with pytest.raises(MSMError):
         MSM(box=30.0, periodic=True, cutoff=9.0, spacing=2.0, max_atoms=100, tuning={"patch_cells": 7})
+
+
+def test_autotune_batch_search_and_cache(tmp_path, monkeypatch):
+    """The batch tuner times the captured batch graph per candidate, returns
+    a candidate of its search space, and answers the second request from
+    the cache; a batch built with the chosen tuning gives the same results."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_7216_gb300 import MSM, MSMBatch
+    from paper_1402_7216_gb300 import autotune as AT
+    monkeypatch.setenv("MSM_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    dev = torch.device("cuda:0")
+    boxes, ps, qs = [], [], []
+    for i, nw in enumerate([500, 900, 700]):
+        L = (3 * nw / 0.1) ** (1.0 / 3.0)
+        p, qq = make_water_box(L, nw, 0, 0, seed=60 + i, periodic=True)
+        boxes.append(L)
+        ps.append(p)
+        qs.append(qq)
+    counts = [len(qq) for qq in qs]
+    pos = torch.tensor(np.vstack(ps), device=dev)
+    q = torch.tensor(np.concatenate(qs), device=dev)
+    kw = dict(cutoff=6.0, spacing=1.5, order=3, splitting=2)
+    tuning, times = AT.autotune_batch(boxes, pos, q, counts, reps=2, **kw)
+    space = dict(AT.SEARCH_BATCH)
+    for k, v in tuning.items():
+        assert v in space[k]
+    assert "default" in times and len(times) > 2
+    t2, times2 = AT.autotune_batch(boxes, pos, q, counts, reps=2, **kw)
+    assert t2 == tuning and "cached" in times2
+    mk = lambda t: [MSM(box=L, periodic=True, precision="mixed", max_atoms=c, tuning=t, **kw)
+                    for L, c in zip(boxes, counts)]
+    E0, _, F0 = MSMBatch(mk(None)).eval(pos, q, counts)
+    E1, _, F1 = MSMBatch(mk(tuning)).eval(pos, q, counts)
+    torch.cuda.synchronize()
+    assert torch.allclose(E0, E1, rtol=1e-6, atol=0)
+    assert rel_rms(F1.cpu().numpy(), F0.cpu().numpy()) <= 1e-5
