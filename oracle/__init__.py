@@ -92,6 +92,7 @@ def lib():
             "orc_short_range_brute": (C.c_int, [P, C.c_int64, _D, _D, C.c_int64, _I64, _D, _D]),
             "orc_short_range_cells": (C.c_int, [P, C.c_int64, _D, _D, _D, _D]),
             "orc_direct_sum": (C.c_double, [C.c_int64, _D, _D, C.c_int64, _I64, _D, _D]),
+            "orc_cutoff_sum": (C.c_double, [P, C.c_int64, _D, _D, C.c_int64, _I64, _D, _D]),
             "orc_ewald_sum": (C.c_double, [_D, C.c_double, C.c_int64, _D, _D, _D, _D]),
             "orc_ewald_psi_reg": (C.c_double, [_D, C.c_double, _D]),
             "orc_self_coefficient": (C.c_double, [P]),
@@ -319,6 +320,22 @@ def direct_sum(pos, q, targets=None, coulomb_k=1.0):
     out = {"phi": coulomb_k * phi, "F": coulomb_k * F}
     if t is None:
         out["E"] = coulomb_k * E
+    return out
+
+
+def cutoff_sum(P: Params, pos, q, targets=None):
+    """The cutoff method (the parareal section's simplest coarse propagator
+    G): the Coulomb law over pairs within the cutoff P.cutoff only (minimum
+    image when periodic), E = 1/2 sum q_i phi_i."""
+    pos, q = _f64(pos, (-1, 3)), _f64(q)
+    t, nt, tp = _targets(targets)
+    cnt = nt if t is not None else len(q)
+    phi, F = np.zeros(cnt), np.zeros((cnt, 3))
+    E = lib().orc_cutoff_sum(C.byref(P._c()), len(q), _dp(pos), _dp(q), nt, tp, _dp(phi), _dp(F))
+    kc = P.coulomb_k
+    out = {"phi": kc * phi, "F": kc * F}
+    if t is None:
+        out["E"] = kc * E
     return out
 
 

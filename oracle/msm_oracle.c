@@ -809,6 +809,39 @@ double orc_direct_sum(int64_t n, const double* pos, const double* q, int64_t nt,
   return E;
 }
 
+/* Cutoff method (the simplest coarse propagator G of the parareal section:  */
+/* the Coulomb law summed only over atoms within a constant cutoff a, all    */
+/* farther pairs neglected): phi_i = sum_{j!=i, r_ij<a} q_j/r_ij, F_i =       */
+/* q_i sum_{j!=i, r_ij<a} q_j (r_i - r_j)/r_ij^3 (the gradient inside the     */
+/* cutoff), E = 1/2 sum_i q_i phi_i.  Minimum image when periodic (a <= L/2). */
+/* Brute force over every pair.                                              */
+double orc_cutoff_sum(const orc_params* P, int64_t n, const double* pos, const double* q, int64_t nt,
+                      const int64_t* targets, double* phi, double* F) {
+  int64_t cnt = targets ? nt : n;
+  double a = P->cutoff;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t t = 0; t < cnt; ++t) {
+    int64_t i = targets ? targets[t] : t;
+    double p = 0.0, f[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double d[3] = {pos[3 * i] - pos[3 * j], pos[3 * i + 1] - pos[3 * j + 1],
+                     pos[3 * i + 2] - pos[3 * j + 2]};
+      min_image(P, d);
+      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      if (r >= a) continue;
+      p += q[j] / r;
+      for (int c = 0; c < 3; ++c) f[c] += q[i] * q[j] * d[c] / (r * r * r);
+    }
+    phi[t] = p;
+    for (int c = 0; c < 3; ++c) F[3 * t + c] = f[c];
+  }
+  double E = 0.0;
+  if (!targets)
+    for (int64_t i = 0; i < n; ++i) E += 0.5 * q[i] * phi[i];
+  return E;
+}
+
 /* Self term (reading): the grid part of u_i contains atom i's own charge     */
 /* through the smooth kernel, whose value at r = 0 is gamma(0)/a; that       */
 /* constant is removed from phi_i.  Exposed for the assembly step.           */

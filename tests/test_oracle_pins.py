@@ -429,3 +429,64 @@ def test_single_level_top_only(oracle):
     R = oracle.msm(P, pos, q)
     assert R["geometry"].levels == 1
     assert rel_rms(R["F"], D["F"]) < 0.01
+
+
+# ---- the cutoff method (the parareal section's coarse propagator G) ----
+
+def test_cutoff_sum_two_charges_closed_form(oracle):
+    """Two charges: inside the cutoff E = q1 q2 / r and F = +-q1 q2 d / r^3
+    (like charges repel); beyond it nothing, with open and periodic boxes
+    (minimum image across the boundary)."""
+    for periodic, pos in [(False, [[2.0, 3.0, 4.0], [5.0, 7.0, 4.0]]),    # r = 5
+                          (True, [[0.5, 10.0, 10.0], [19.5 - 4.0, 10.0, 10.0]])]:  # image r = 5
+        P = oracle.Params(box=(20.0,) * 3, periodic=periodic, cutoff=6.0, spacing=2.0)
+        q = np.array([0.8, -1.3])
+        out = oracle.cutoff_sum(P, np.array(pos), q)
+        assert out["E"] == pytest.approx(0.8 * -1.3 / 5.0, rel=1e-14)
+        d = np.array(pos[0]) - np.array(pos[1])
+        if periodic:
+            d -= 20.0 * np.round(d / 20.0)
+        f0 = 0.8 * -1.3 * d / 125.0
+        np.testing.assert_allclose(out["F"][0], f0, rtol=1e-13, atol=1e-16)
+        np.testing.assert_allclose(out["F"][1], -f0, rtol=1e-13, atol=1e-16)
+        P4 = oracle.Params(box=(20.0,) * 3, periodic=periodic, cutoff=4.9, spacing=2.0)
+        far = oracle.cutoff_sum(P4, np.array(pos), q)
+        assert far["E"] == 0.0 and np.all(far["F"] == 0.0)
+
+
+def test_cutoff_sum_equals_direct_sum_when_nothing_is_cut(oracle):
+    """An open box with a cutoff beyond its diagonal: the cutoff method is the
+    plain Coulomb sum (an independent routine, no minimum image, no cutoff)."""
+    pos, q = make_water_box(14.0, 60, 1, 1, seed=71, periodic=False)
+    P = oracle.Params(box=(14.0,) * 3, periodic=False, cutoff=30.0, spacing=2.0)
+    a, b = oracle.cutoff_sum(P, pos, q), oracle.direct_sum(pos, q)
+    assert a["E"] == pytest.approx(b["E"], rel=1e-13)
+    np.testing.assert_allclose(a["F"], b["F"], rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(a["phi"], b["phi"], rtol=1e-12, atol=1e-13)
+
+
+def test_cutoff_sum_forces_are_the_energy_gradient_and_scale(oracle):
+    """Central finite differences of E give -F (no pair within the step of
+    the cutoff edge); E(alpha q) = alpha^2 E."""
+    pos, q = make_water_box(16.0, 80, 1, 1, seed=72, periodic=True)
+    P = oracle.Params(box=(16.0,) * 3, periodic=True, cutoff=6.5, spacing=2.0)
+    ref = oracle.cutoff_sum(P, pos, q)
+    h = 1e-5
+    rng = np.random.default_rng(72)
+    checked = 0
+    for i in rng.choice(len(q), 12, replace=False):
+        d = pos - pos[i]
+        d -= 16.0 * np.round(d / 16.0)
+        r = np.sqrt((d ** 2).sum(1))
+        r[i] = 0.0
+        if np.any(np.abs(r[r > 0] - 6.5) < 1e-3):
+            continue
+        for c in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, c] += h
+            pm[i, c] -= h
+            fd = -(oracle.cutoff_sum(P, pp, q)["E"] - oracle.cutoff_sum(P, pm, q)["E"]) / (2 * h)
+            assert fd == pytest.approx(ref["F"][i, c], rel=1e-6, abs=1e-8)
+        checked += 1
+    assert checked >= 6
+    assert oracle.cutoff_sum(P, pos, 1.7 * q)["E"] == pytest.approx(1.7 ** 2 * ref["E"], rel=1e-13)
