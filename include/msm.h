@@ -121,6 +121,18 @@ int msm_query(msm_handle h, double h_eff[3], int* levels, int* dims, int* lo);
 int msm_eval(msm_handle h, int64_t n, const double* pos, const double* q, double* energy,
              double* phi, double* force, void* cuda_stream);
 
+/* The cutoff method (the simplest coarse propagator G of the parareal
+ * section, paragraph "Cutoff Method": the Coulomb law summed only over atoms
+ * within a constant cutoff, farther pairs neglected), on this plan's box,
+ * cutoff a, precision and coulomb_k:
+ *   phi_i = k_c sum_{j != i, r_ij < a} q_j / r_ij (minimum image when
+ *   periodic), F_i = -dE/dr_i inside the cutoff, E = 1/2 sum_i q_i phi_i.
+ * Arguments, layouts and errors as msm_eval; uses the plan's binning and pair
+ * kernel (no grid passes).  A following msm_eval_backward returns
+ * NO_FORWARD. */
+int msm_cutoff_eval(msm_handle h, int64_t n, const double* pos, const double* q, double* energy,
+                    double* phi, double* force, void* cuda_stream);
+
 /* Adjoint of the last msm_eval on this plan: given the upstream gradient
  * grad_energy = dL/dE ([1] double, device), writes grad_pos = dL/dr ([n][3])
  * and grad_q = dL/dq ([n]); either output may be NULL.  The long-range part

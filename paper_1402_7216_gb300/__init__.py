@@ -118,6 +118,25 @@ class MSM:
         self._last_io = io
         return E, phi, F
 
+    def cutoff_eval(self, pos, q, want_phi=True, want_force=True, stream=None, out=None):
+        """msm_cutoff_eval: the cutoff method (Coulomb law within this plan's
+        cutoff only; the parareal coarse propagator) on float64 device
+        inputs; returns (E, phi or None, F or None)."""
+        pos, q = self._check_inputs(pos, q)
+        if pos.dtype != torch.float64:
+            raise ValueError("cutoff_eval takes float64 pos and q")
+        n = pos.shape[0]
+        if out is None:
+            E = torch.empty((), dtype=torch.float64, device=pos.device)
+            phi = torch.empty(n, dtype=torch.float64, device=pos.device) if want_phi else None
+            F = torch.empty((n, 3), dtype=torch.float64, device=pos.device) if want_force else None
+        else:
+            E, phi, F = out
+        rc = lib().msm_cutoff_eval(self._h, n, _ptr(pos), _ptr(q), _ptr(E), _ptr(phi), _ptr(F), _stream(stream))
+        _capi.check(rc, "msm_cutoff_eval")
+        self._last_n = None
+        return E, phi, F
+
     def eval_f32io(self, pos, q, want_phi=True, want_force=True, stream=None, out=None):
         """msm_eval_f32io: eval with float32 positions, charges and outputs."""
         if pos.dtype != torch.float32 or q.dtype != torch.float32:

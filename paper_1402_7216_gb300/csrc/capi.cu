@@ -341,6 +341,23 @@ int msm_eval(msm_handle h, int64_t n, const double* pos, const double* q, double
   return forward(P, n, pos, q, energy, phi, force, (cudaStream_t)stream);
 }
 
+int msm_cutoff_eval(msm_handle h, int64_t n, const double* pos, const double* q, double* energy, double* phi,
+                    double* force, void* stream) {
+  if (!h || n < 0 || !energy || (n > 0 && (!pos || !q))) return MSM_ERR_INVALID_ARG;
+  Plan& P = h->p;
+  if (n > P.cap) return MSM_ERR_TOO_MANY_ATOMS;
+  cudaStream_t st = (cudaStream_t)stream;
+  P.last_n = -1;  // the per-atom buffers no longer hold an MSM forward pass
+  cudaError_t e = stage(P, MSM_STAGE_BINNING, st, [&] { return launch_binning(P, n, pos, q, st); });
+  if (e == cudaSuccess) e = stage(P, MSM_STAGE_SHORT_RANGE, st, [&] { return launch_cutoff_pairs(P, n, st); });
+  if (e == cudaSuccess)
+    e = stage(P, MSM_STAGE_INTERPOLATION, st, [&] { return launch_cutoff_assemble(P, n, energy, phi, force, st); });
+  if (e != cudaSuccess) return MSM_ERR_CUDA;
+  P.last_stream = st;
+  P.evals += 1;
+  return MSM_OK;
+}
+
 int msm_eval_backward(msm_handle h, const double* grad_energy, double* grad_pos, double* grad_q,
                       void* stream) {
   if (!h || !grad_energy) return MSM_ERR_INVALID_ARG;

@@ -1586,6 +1586,52 @@ cudaError_t launch_grid_to_double(Plan& P, const void* src, double* dst, int64_t
 }
 
 
+// ---- the cutoff method: assembly of phi, F and E from the pair sums ----
+// phi_i = k_c u_i, F_i = k_c (pair forces), E = 1/2 k_c sum_i q_i u_i; per-block
+// FP64 partials (grid-stride over the sorted atoms) and k_energy_final.
+template <typename T, typename OUT>
+__global__ void __launch_bounds__(256) k_cutoff_assemble(int64_t n, const int* __restrict__ perm,
+                                                         const R4<T>* __restrict__ atoms, const T* __restrict__ phis,
+                                                         const R4<T>* __restrict__ fs, T kc, OUT* __restrict__ phi_out,
+                                                         OUT* __restrict__ force_out, double* __restrict__ partial) {
+  double e = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+    const T p = phis[i];
+    const R4<T> f = fs[i];
+    const int o = perm[i];
+    if (phi_out) phi_out[o] = (OUT)(kc * p);
+    if (force_out) {
+      force_out[3 * (size_t)o + 0] = (OUT)(kc * f.x);
+      force_out[3 * (size_t)o + 1] = (OUT)(kc * f.y);
+      force_out[3 * (size_t)o + 2] = (OUT)(kc * f.z);
+    }
+    e += (double)(atoms[i].w * (kc * p));
+  }
+  const double bsum = block_sum<256>(e);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bsum;
+}
+
+template <typename OUT>
+cudaError_t launch_cutoff_assemble(Plan& P, int64_t n, double* energy, OUT* phi, OUT* force, cudaStream_t st) {
+  const int nb = (int)std::max<int64_t>(0, std::min<int64_t>(P.nblk_partial, (n + 255) / 256));
+  if (nb > 0) {
+    if (P.fp64)
+      k_cutoff_assemble<double, OUT><<<nb, 256, 0, st>>>(n, P.d.perm, (const R4<double>*)P.d.atoms,
+                                                        (const double*)P.d.phis, (const R4<double>*)P.d.fs,
+                                                        P.P.coulomb_k, phi, force, P.d.partial);
+    else
+      k_cutoff_assemble<float, OUT><<<nb, 256, 0, st>>>(n, P.d.perm, (const R4<float>*)P.d.atoms,
+                                                       (const float*)P.d.phis, (const R4<float>*)P.d.fs,
+                                                       (float)P.P.coulomb_k, phi, force, P.d.partial);
+  }
+  k_energy_final<<<1, 1024, 0, st>>>(P.d.partial, nb, energy);
+  P.launches += 1 + (nb > 0 ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_cutoff_assemble<double>(Plan&, int64_t, double*, double*, double*, cudaStream_t);
+template cudaError_t launch_cutoff_assemble<float>(Plan&, int64_t, double*, float*, float*, cudaStream_t);
+
 // ---- batches: every grid pass as one launch over all replicas ----
 namespace {
 

@@ -109,8 +109,14 @@ __device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
 template <typename T>
 __device__ __forceinline__ T far_away() { return T(1e18); }
 
+// Pair functions: K = 0 is MSM's short-range kernel g*(r) = 1/r - gamma(r/a)/a
+// (zero with its derivative at r = a); K = 1 is the plain Coulomb law 1/r of
+// the cutoff method (the parareal section's coarse propagator G), which is
+// not zero at a, so sources beyond the cutoff are masked.
+constexpr int kPairMSM = 0, kPairCutoff = 1;
+
 // One batch: the lane's target atom against the kBatch queued sources.
-template <typename T, int M, bool COMP>
+template <typename T, int M, bool COMP, int K = kPairMSM>
 __device__ __forceinline__ void pair_batch(const R4<T>* __restrict__ Q, const R4<T>& ai, T a2, T inv_a,
                                            T inv_a2, T two_inv_a3, T& phi, T& fx, T& fy, T& fz, T& cphi,
                                            T& cfx, T& cfy, T& cfz) {
@@ -124,9 +130,15 @@ __device__ __forceinline__ void pair_batch(const R4<T>* __restrict__ Q, const R4
     const T r2s = ok ? r2 : a2;
     const T qj = ok ? b.w : T(0);
     const T rinv = fast_rsqrt(r2s);
-    const T s = r2s * inv_a2;
-    pphi += qj * (rinv - Smooth<T, M>::g(s) * inv_a);
-    const T f = qj * (-(rinv * rinv * rinv) - two_inv_a3 * Smooth<T, M>::gs(s));
+    T f;
+    if (K == kPairMSM) {
+      const T s = r2s * inv_a2;
+      pphi += qj * (rinv - Smooth<T, M>::g(s) * inv_a);
+      f = qj * (-(rinv * rinv * rinv) - two_inv_a3 * Smooth<T, M>::gs(s));
+    } else {
+      pphi += qj * rinv;
+      f = -qj * (rinv * rinv * rinv);
+    }
     px += f * dx;
     py += f * dy;
     pz += f * dz;
@@ -149,7 +161,7 @@ __device__ __forceinline__ void pair_batch(const R4<T>* __restrict__ Q, const R4
 // farther than a from the bounding box of its target atoms, and appends the
 // rest to a per-warp queue in shared memory; each full queue of kBatch
 // sources is one fully unrolled batch of pair evaluations.
-template <typename T, int M, bool COMP>
+template <typename T, int M, bool COMP, int K>
 __global__ void __launch_bounds__(32 * kWarps) k_short_range(
     const R4<T>* __restrict__ atoms, const int* __restrict__ cell_start,
     const int4* __restrict__ offs, const R4<T>* __restrict__ shifts, PairArgs A, int ncell,
@@ -213,7 +225,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_short_range(
         qn += __popc(bal);
         __syncwarp();
         if (qn >= kBatch) {
-          pair_batch<T, M, COMP>(Q, ai, a2, inv_a, inv_a2, two_inv_a3, phi, fx, fy, fz, cphi, cfx, cfy, cfz);
+          pair_batch<T, M, COMP, K>(Q, ai, a2, inv_a, inv_a2, two_inv_a3, phi, fx, fy, fz, cphi, cfx, cfy, cfz);
           __syncwarp();
           if (lane < qn - kBatch) Q[lane] = Q[kBatch + lane];
           qn -= kBatch;
@@ -224,7 +236,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_short_range(
     if (qn > 0) {  // last partial batch, padded with far-away zero charges
       if (lane >= qn) Q[lane] = dummy;
       __syncwarp();
-      pair_batch<T, M, COMP>(Q, ai, a2, inv_a, inv_a2, two_inv_a3, phi, fx, fy, fz, cphi, cfx, cfy, cfz);
+      pair_batch<T, M, COMP, K>(Q, ai, a2, inv_a, inv_a2, two_inv_a3, phi, fx, fy, fz, cphi, cfx, cfy, cfz);
       __syncwarp();
     }
     if (iv) {
@@ -273,7 +285,7 @@ __device__ __forceinline__ float2 poly_d(const PairCoef& C, float2 r2) {
   return t;
 }
 
-template <int M>
+template <int M, int K>
 __device__ __forceinline__ void pair_batch_f2(const QueueF& Q, float2 nax, float2 nay, float2 naz, float a2,
                                               const PairCoef& C, float& phi, float& px, float& py, float& pz,
                                               float& cphi, float& cpx, float& cpy, float& cpz) {
@@ -295,14 +307,22 @@ __device__ __forceinline__ void pair_batch_f2(const QueueF& Q, float2 nax, float
       float2 r2 = __fmul2_rn(dx, dx);
       r2 = __ffma2_rn(dy, dy, r2);
       r2 = __ffma2_rn(dz, dz, r2);
-      // a source beyond the cutoff is evaluated at r = a, where g* and its
-      // derivative vanish (C1 smoothing): no select on q_j is needed
-      r2 = make_float2(fminf(r2.x, a2), fminf(r2.y, a2));
-      const float2 qj = bq;
-      const float2 rinv = make_float2(fast_rsqrt(r2.x), fast_rsqrt(r2.y));
-      const float2 pot = __fadd2_rn(rinv, poly_g<M>(C, r2));  // G holds -gamma coefficients
-      sphi = __ffma2_rn(qj, pot, sphi);
-      const float2 fp = __fmul2_rn(__ffma2_rn(__fmul2_rn(rinv, rinv), rinv, poly_d<M>(C, r2)), qj);
+      float2 fp;
+      if (K == kPairMSM) {
+        // a source beyond the cutoff is evaluated at r = a, where g* and its
+        // derivative vanish (C1 smoothing): no select on q_j is needed
+        r2 = make_float2(fminf(r2.x, a2), fminf(r2.y, a2));
+        const float2 qj = bq;
+        const float2 rinv = make_float2(fast_rsqrt(r2.x), fast_rsqrt(r2.y));
+        const float2 pot = __fadd2_rn(rinv, poly_g<M>(C, r2));  // G holds -gamma coefficients
+        sphi = __ffma2_rn(qj, pot, sphi);
+        fp = __fmul2_rn(__ffma2_rn(__fmul2_rn(rinv, rinv), rinv, poly_d<M>(C, r2)), qj);
+      } else {  // plain Coulomb within the cutoff (sources are never at r = 0 outside the home cell)
+        const float2 qj = make_float2(r2.x < a2 ? bq.x : 0.f, r2.y < a2 ? bq.y : 0.f);
+        const float2 rinv = make_float2(fast_rsqrt(r2.x), fast_rsqrt(r2.y));
+        sphi = __ffma2_rn(qj, rinv, sphi);
+        fp = __fmul2_rn(__fmul2_rn(__fmul2_rn(rinv, rinv), rinv), qj);
+      }
       sx = __ffma2_rn(fp, dx, sx);
       sy = __ffma2_rn(fp, dy, sy);
       sz = __ffma2_rn(fp, dz, sz);
@@ -346,7 +366,7 @@ struct PairKArgs {
   R4<float>* fs;
 };
 
-template <int M>
+template <int M, int KIND>
 __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk) {
   const R4<float>* __restrict__ atoms = K.atoms;
   const int* __restrict__ cell_start = K.cell_start;
@@ -467,8 +487,8 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
       home[warp][lane] = (j < i1) ? atoms[j] : R4<float>{FAR, FAR, FAR, 0.f};
       __syncwarp();
       float hphi = 0.f, hx_ = 0.f, hy_ = 0.f, hz_ = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-      pair_batch<float, M, true>(home[warp], ai, a2, inv_a, inv_a2s, two_inv_a3, hphi, hx_, hy_, hz_, c0, c1, c2,
-                                 c3);
+      pair_batch<float, M, true, KIND>(home[warp], ai, a2, inv_a, inv_a2s, two_inv_a3, hphi, hx_, hy_, hz_, c0, c1,
+                                       c2, c3);
       two_sum_add(phi, cphi, hphi + c0);
       two_sum_add(px, cpx, hx_ + c1);
       two_sum_add(py, cpy, hy_ + c2);
@@ -523,7 +543,7 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
       qn += __popc(bal);
       __syncwarp();
       if (qn >= kBatch) {
-        pair_batch_f2<M>(Q, nax, nay, naz, a2, C, phi, px, py, pz, cphi, cpx, cpy, cpz);
+        pair_batch_f2<M, KIND>(Q, nax, nay, naz, a2, C, phi, px, py, pz, cphi, cpx, cpy, cpz);
         __syncwarp();
         if (lane < qn - kBatch) {
           Q.x[lane] = Q.x[kBatch + lane];
@@ -543,7 +563,7 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
         Q.q[lane] = 0.f;
       }
       __syncwarp();
-      pair_batch_f2<M>(Q, nax, nay, naz, a2, C, phi, px, py, pz, cphi, cpx, cpy, cpz);
+      pair_batch_f2<M, KIND>(Q, nax, nay, naz, a2, C, phi, px, py, pz, cphi, cpx, cpy, cpz);
       __syncwarp();
     }
     if (iv) {
@@ -554,19 +574,19 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
   }
 }
 
-template <int M>
+template <int M, int KIND>
 __global__ void __launch_bounds__(32 * kWarps, 6) k_short_range_f2(PairKArgs a) {
-  short_range_f2_body<M>(a, blockIdx.x);
+  short_range_f2_body<M, KIND>(a, blockIdx.x);
 }
 
 template <int M>
 __global__ void __launch_bounds__(32 * kWarps, 6) kb_short_range_f2(const PairKArgs* __restrict__ tab,
                                                                    const int* __restrict__ first, int nrep) {
   const int r = batch_rep(first, nrep, blockIdx.x);
-  short_range_f2_body<M>(tab[r], blockIdx.x - first[r]);
+  short_range_f2_body<M, kPairMSM>(tab[r], blockIdx.x - first[r]);
 }
 
-template <typename T, bool COMP>
+template <typename T, bool COMP, int K>
 void launch_t(Plan& P, cudaStream_t st) {
   PairArgs A = pair_args(P);
   int blocks = (P.ncell + kWarps - 1) / kWarps;
@@ -576,15 +596,15 @@ void launch_t(Plan& P, cudaStream_t st) {
   auto* fs = (R4<T>*)P.d.fs;
   switch (P.P.splitting) {
     case 1:
-      k_short_range<T, 1, COMP><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A,
+      k_short_range<T, 1, COMP, K><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A,
                                                                P.ncell, ph, fs);
       break;
     case 2:
-      k_short_range<T, 2, COMP><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A,
+      k_short_range<T, 2, COMP, K><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A,
                                                                P.ncell, ph, fs);
       break;
     default:
-      k_short_range<T, 3, COMP><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A,
+      k_short_range<T, 3, COMP, K><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A,
                                                                P.ncell, ph, fs);
       break;
   }
@@ -621,18 +641,28 @@ PairKArgs pair_kargs(const Plan& P) {
   return K;
 }
 
+template <int KIND>
 void launch_f2(Plan& P, cudaStream_t st) {
   const PairKArgs K = pair_kargs(P);
   const int blocks = (P.ncell + kWarps - 1) / kWarps;
-  if (P.P.splitting == 1) k_short_range_f2<1><<<blocks, 32 * kWarps, 0, st>>>(K);
-  else if (P.P.splitting == 2) k_short_range_f2<2><<<blocks, 32 * kWarps, 0, st>>>(K);
-  else k_short_range_f2<3><<<blocks, 32 * kWarps, 0, st>>>(K);
+  if (KIND == kPairCutoff) k_short_range_f2<2, kPairCutoff><<<blocks, 32 * kWarps, 0, st>>>(K);  // M unused
+  else if (P.P.splitting == 1) k_short_range_f2<1, kPairMSM><<<blocks, 32 * kWarps, 0, st>>>(K);
+  else if (P.P.splitting == 2) k_short_range_f2<2, kPairMSM><<<blocks, 32 * kWarps, 0, st>>>(K);
+  else k_short_range_f2<3, kPairMSM><<<blocks, 32 * kWarps, 0, st>>>(K);
 }
 
 cudaError_t launch_short_range(Plan& P, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  if (P.fp64) launch_t<double, false>(P, st);
-  else launch_f2(P, st);
+  if (P.fp64) launch_t<double, false, kPairMSM>(P, st);
+  else launch_f2<kPairMSM>(P, st);
+  P.launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cutoff_pairs(Plan& P, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (P.fp64) launch_t<double, false, kPairCutoff>(P, st);
+  else launch_f2<kPairCutoff>(P, st);
   P.launches += 1;
   return cudaGetLastError();
 }

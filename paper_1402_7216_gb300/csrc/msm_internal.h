@@ -238,6 +238,11 @@ template <typename IO>  // IO = double or float (caller's position and charge ty
 cudaError_t launch_binning(Plan& P, int64_t n, const IO* pos, const IO* q, cudaStream_t s);
 // short-range pair sums (phis, fs.xyz)
 cudaError_t launch_short_range(Plan& P, int64_t n, cudaStream_t s);
+// the cutoff method: Coulomb pair sums within the cutoff (phis, fs.xyz), and
+// the assembly of phi, F and E from them
+cudaError_t launch_cutoff_pairs(Plan& P, int64_t n, cudaStream_t s);
+template <typename OUT>
+cudaError_t launch_cutoff_assemble(Plan& P, int64_t n, double* energy, OUT* phi, OUT* force, cudaStream_t s);
 // grid passes: anterpolation (charges q_i * scale, scale from device or 1)
 cudaError_t launch_anterpolate(Plan& P, int64_t n, void* grid0, const double* dscale, double factor,
                                cudaStream_t s);
