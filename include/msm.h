@@ -75,7 +75,7 @@ typedef struct {
 /* Tile shapes of a plan (0 in a field keeps its default).  They change
  * speed, never results beyond floating-point summation order.
  *   cell_fill     target atoms per short-range cell at the plan's capacity
- *                 density (default 24; cells stay between a/2 and 3a/4 wide)
+ *                 density (default 24; cells are at least a/2 wide)
  *   patch_cells   short-range cells per side of the shared-memory patch blocks
  *                 of anterpolation and interpolation (default: the largest of
  *                 4, 3, 2, 1 whose patch fits)

@@ -265,7 +265,8 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   // candidate volume)
   double vol = p.box[0] * p.box[1] * p.box[2];
   double wfill = std::cbrt(fill * vol / (double)p.max_atoms);
-  double wmin = std::max(0.5 * p.cutoff, std::min(wfill, 0.75 * p.cutoff));
+  // (cells may be wider than a: the neighbour rows then shrink to +-1 cell)
+  double wmin = std::max(0.5 * p.cutoff, wfill);
   for (int d = 0; d < 3; ++d) {
     // the cell count nearest to the target width, but cells at least a/2 wide
     int c = std::min((int)std::lround(p.box[d] / wmin), (int)std::floor(p.box[d] / (0.5 * p.cutoff)));
