@@ -86,13 +86,16 @@ int forward(Plan& P, int64_t n, const IO* pos, const IO* q, double* energy, IO* 
               [&] { return launch_anterpolate(P, n, P.d.gq[0], nullptr, 1.0, gs); });
   if (e == cudaSuccess) e = stage(P, MSM_STAGE_SHORT_RANGE, st, [&] { return launch_short_range(P, n, st); });
   if (e == cudaSuccess) e = grid_sweep(P, P.d.gq, P.d.gu, gs);
+  // the grid gather needs only u^0, so it runs on the grid's stream, under
+  // the pair sums; the assembly waits for both
+  if (e == cudaSuccess) e = stage(P, MSM_STAGE_INTERPOLATION, gs, [&] { return launch_interp_gather(P, n, gs); });
   if (e == cudaSuccess && gs != st) {
     e = cudaEventRecord(P.ev_join, gs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P.ev_join, 0);
   }
   if (e == cudaSuccess)
     e = stage(P, MSM_STAGE_INTERPOLATION, st,
-              [&] { return launch_interp_forward(P, n, energy, phi, force, st); });
+              [&] { return launch_interp_assemble(P, n, energy, phi, force, st); });
   if (e != cudaSuccess) return MSM_ERR_CUDA;
   P.last_stream = st;
   P.last_n = n;

@@ -959,7 +959,7 @@ struct Assemble<float> {
                                   const R4<float>& gl, float v, const float gv[3], int o, OUT* grad_pos,
                                   OUT* grad_q) {
     const float hg = 0.5f * gg;
-    if (grad_q) grad_q[o] = (OUT)(A.kcf * (gg * (phis - q * A.self_cf) + hg * s.w + v));
+    if (grad_q) grad_q[o] = (OUT)(A.kcf * (gg * (phis - q * A.self_cf) + hg * gl.w + v));
     if (grad_pos) {
       grad_pos[3 * (size_t)o + 0] = (OUT)(A.kcf * (-gg * s.x + hg * q * gl.x + q * gv[0]));
       grad_pos[3 * (size_t)o + 1] = (OUT)(A.kcf * (-gg * s.y + hg * q * gl.y + q * gv[1]));
@@ -985,7 +985,7 @@ struct Assemble<double> {
   __device__ static void backward(const AssembleArgs& A, double gg, double q, double phis, const R4<double>& s,
                                   const R4<double>& gl, double v, const double gv[3], int o, OUT* grad_pos,
                                   OUT* grad_q) {
-    if (grad_q) grad_q[o] = (OUT)(A.kc * (gg * (phis - q * A.self_c) + 0.5 * gg * s.w + v));
+    if (grad_q) grad_q[o] = (OUT)(A.kc * (gg * (phis - q * A.self_c) + 0.5 * gg * gl.w + v));
     if (grad_pos) {
       grad_pos[3 * (size_t)o + 0] = (OUT)(A.kc * (-gg * s.x + 0.5 * gg * q * gl.x + q * gv[0]));
       grad_pos[3 * (size_t)o + 1] = (OUT)(A.kc * (-gg * s.y + 0.5 * gg * q * gl.y + q * gv[1]));
@@ -1102,7 +1102,10 @@ struct InterpKArgs {
   int nbx, nby;  // blocks along x and y
 };
 
-template <typename T, int ORDER, typename OUT>
+// GATHER: interpolate only (u_long and its gradient into glong; no pair
+// results needed, so this runs while the pair sums are still being computed),
+// else also assemble phi, F and the energy partials.
+template <typename T, int ORDER, typename OUT, bool GATHER = false>
 __device__ __forceinline__ void interp_fwd_body(
     const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm,
     const int* __restrict__ cell_start, const AnterpArgs& AA, const T* __restrict__ u0, const GridDims& G,
@@ -1140,14 +1143,13 @@ __device__ __forceinline__ void interp_fwd_body(
     const R4<T> f = gfrac[i];
     T p, g[3];
     interp_patch_atom<T, ORDER>(f, gbase[i], patch, AA.pd, lo0, lo1, lo2, u0, G, ih, p, g);
-    R4<T> s = fs[i];
-    e += Assemble<T>::forward(A, f.w, phis[i], p, s, g, perm[i], phi_out, force_out);
-    s.w = p;
-    fs[i] = s;
-    glong[i] = R4<T>{g[0], g[1], g[2], T(0)};
+    if (!GATHER) e += Assemble<T>::forward(A, f.w, phis[i], p, fs[i], g, perm[i], phi_out, force_out);
+    glong[i] = R4<T>{g[0], g[1], g[2], p};
   }
-  double bsum = block_sum<256>(e);
-  if (threadIdx.x == 0) partial[lin] = bsum;
+  if (!GATHER) {
+    double bsum = block_sum<256>(e);
+    if (threadIdx.x == 0) partial[lin] = bsum;
+  }
 }
 
 template <typename T, int ORDER, typename OUT>
@@ -1156,15 +1158,33 @@ __device__ __forceinline__ void interp_fwd_call(const InterpKArgs<T, OUT>& K, in
                                  K.phi_out, K.force_out, K.partial, bx, by, bz, lin);
 }
 
-template <typename T, int ORDER, typename OUT>
-__global__ void __launch_bounds__(256, 3) k_interp_fwd(
-    const R4<T>* __restrict__ gfrac, const int4* __restrict__ gbase, const int* __restrict__ perm,
-    const int* __restrict__ cell_start, AnterpArgs AA, const T* __restrict__ u0, GridDims G, AssembleArgs A,
-    const T* __restrict__ phis, R4<T>* __restrict__ fs, R4<T>* __restrict__ glong, OUT* __restrict__ phi_out,
-    OUT* __restrict__ force_out, double* __restrict__ partial) {
-  interp_fwd_body<T, ORDER, OUT>(gfrac, gbase, perm, cell_start, AA, u0, G, A, phis, fs, glong, phi_out, force_out,
-                                 partial, blockIdx.x, blockIdx.y, blockIdx.z,
-                                 (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+template <typename T, int ORDER>
+__global__ void __launch_bounds__(256, 3) k_interp_gather(const R4<T>* __restrict__ gfrac,
+                                                          const int4* __restrict__ gbase,
+                                                          const int* __restrict__ cell_start, AnterpArgs AA,
+                                                          const T* __restrict__ u0, GridDims G, AssembleArgs A,
+                                                          R4<T>* __restrict__ glong) {
+  interp_fwd_body<T, ORDER, double, true>(gfrac, gbase, nullptr, cell_start, AA, u0, G, A, nullptr, nullptr, glong,
+                                          nullptr, nullptr, nullptr, blockIdx.x, blockIdx.y, blockIdx.z, 0);
+}
+
+// Assembly after the pair sums and the gather: phi_i, F_i in the caller's
+// order and the per-block energy partials (grid-stride over sorted atoms).
+template <typename T, typename OUT>
+__global__ void __launch_bounds__(256) k_interp_assemble(int64_t n, const int* __restrict__ perm,
+                                                         const R4<T>* __restrict__ gfrac, const T* __restrict__ phis,
+                                                         const R4<T>* __restrict__ fs,
+                                                         const R4<T>* __restrict__ glong, AssembleArgs A,
+                                                         OUT* __restrict__ phi_out, OUT* __restrict__ force_out,
+                                                         double* __restrict__ partial) {
+  double e = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+    const R4<T> gl = glong[i];
+    const T g[3] = {gl.x, gl.y, gl.z};
+    e += Assemble<T>::forward(A, gfrac[i].w, phis[i], gl.w, fs[i], g, perm[i], phi_out, force_out);
+  }
+  const double bsum = block_sum<256>(e);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bsum;
 }
 
 __device__ __forceinline__ void energy_final_body(const double* __restrict__ partial, int nb,
@@ -1528,27 +1548,49 @@ InterpKArgs<T, OUT> interp_kargs(Plan& P, bool backward, OUT* phi, OUT* force, c
   return K;
 }
 
-template <typename OUT>
-cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, OUT* phi, OUT* force, cudaStream_t st) {
+cudaError_t launch_interp_gather(Plan& P, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
   AnterpArgs AA = patch_args(P);
   dim3 grid(blocks_for(P.nc[0], AA.B), blocks_for(P.nc[1], AA.B), blocks_for(P.nc[2], AA.B));
-  int nb = (int)(grid.x * grid.y * grid.z);
-  if (n > 0) {
-    size_t sm = (P.fp64 ? 8 : 4) * (size_t)AA.pd * AA.pd * AA.pd;
-    if (P.fp64) {
-      auto K = interp_kargs<double, OUT>(P, false, phi, force, nullptr, nullptr, nullptr, P.d.partial);
-      if (P.P.order == 3) k_interp_fwd<double, 3, OUT><<<grid, 256, sm, st>>>(INTERP_FWD_ARGS(K));
-      else k_interp_fwd<double, 5, OUT><<<grid, 256, sm, st>>>(INTERP_FWD_ARGS(K));
-    } else {
-      auto K = interp_kargs<float, OUT>(P, false, phi, force, nullptr, nullptr, nullptr, P.d.partial);
-      if (P.P.order == 3) k_interp_fwd<float, 3, OUT><<<grid, 256, sm, st>>>(INTERP_FWD_ARGS(K));
-      else k_interp_fwd<float, 5, OUT><<<grid, 256, sm, st>>>(INTERP_FWD_ARGS(K));
-    }
+  size_t sm = (P.fp64 ? 8 : 4) * (size_t)AA.pd * AA.pd * AA.pd;
+  const GridDims G = dims_of(P, 0);
+  const AssembleArgs A = assemble_args(P);
+#define MSM_GATHER(T, O)                                                                                          \
+  k_interp_gather<T, O><<<grid, 256, sm, st>>>((const R4<T>*)P.d.gfrac, P.d.gbase, P.d.cell_start, AA,            \
+                                               (const T*)P.d.gu[0], G, A, (R4<T>*)P.d.glong)
+  if (P.fp64) {
+    if (P.P.order == 3) MSM_GATHER(double, 3);
+    else MSM_GATHER(double, 5);
+  } else {
+    if (P.P.order == 3) MSM_GATHER(float, 3);
+    else MSM_GATHER(float, 5);
   }
-  k_energy_final<<<1, 1024, 0, st>>>(P.d.partial, n > 0 ? nb : 0, energy);
-  P.launches += 1 + (n > 0 ? 1 : 0);
+#undef MSM_GATHER
+  P.launches += 1;
   return cudaGetLastError();
 }
+
+template <typename OUT>
+cudaError_t launch_interp_assemble(Plan& P, int64_t n, double* energy, OUT* phi, OUT* force, cudaStream_t st) {
+  const int nb = (int)std::max<int64_t>(0, std::min<int64_t>(P.nblk_partial, (n + 255) / 256));
+  const AssembleArgs A = assemble_args(P);
+  if (nb > 0) {
+    if (P.fp64)
+      k_interp_assemble<double, OUT><<<nb, 256, 0, st>>>(n, P.d.perm, (const R4<double>*)P.d.gfrac,
+                                                        (const double*)P.d.phis, (const R4<double>*)P.d.fs,
+                                                        (const R4<double>*)P.d.glong, A, phi, force, P.d.partial);
+    else
+      k_interp_assemble<float, OUT><<<nb, 256, 0, st>>>(n, P.d.perm, (const R4<float>*)P.d.gfrac,
+                                                       (const float*)P.d.phis, (const R4<float>*)P.d.fs,
+                                                       (const R4<float>*)P.d.glong, A, phi, force, P.d.partial);
+  }
+  k_energy_final<<<1, 1024, 0, st>>>(P.d.partial, nb, energy);
+  P.launches += 1 + (nb > 0 ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_interp_assemble<double>(Plan&, int64_t, double*, double*, double*, cudaStream_t);
+template cudaError_t launch_interp_assemble<float>(Plan&, int64_t, double*, float*, float*, cudaStream_t);
 
 template <typename OUT>
 cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, OUT* grad_pos, OUT* grad_q,
@@ -1571,8 +1613,6 @@ cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, OUT* gr
 }
 
 
-template cudaError_t launch_interp_forward<double>(Plan&, int64_t, double*, double*, double*, cudaStream_t);
-template cudaError_t launch_interp_forward<float>(Plan&, int64_t, double*, float*, float*, cudaStream_t);
 template cudaError_t launch_interp_backward<double>(Plan&, int64_t, const double*, double*, double*, cudaStream_t);
 template cudaError_t launch_interp_backward<float>(Plan&, int64_t, const double*, float*, float*, cudaStream_t);
 
@@ -2090,6 +2130,10 @@ cudaError_t configure_kernels() {
     cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (r != cudaSuccess) e = r;
   };
+  set((const void*)k_interp_gather<float, 3>);
+  set((const void*)k_interp_gather<float, 5>);
+  set((const void*)k_interp_gather<double, 3>);
+  set((const void*)k_interp_gather<double, 5>);
   set((const void*)k_lattice_f2<kLatticeLP, 4, 8>);
   set((const void*)k_lattice_f2<kLatticeLP, 0, 0>);
   set((const void*)kb_lattice_f2);
@@ -2103,14 +2147,6 @@ cudaError_t configure_kernels() {
   set((const void*)k_anterp_fx<5>);
   set((const void*)k_anterp_patch<double, double, 3>);
   set((const void*)k_anterp_patch<double, double, 5>);
-  set((const void*)k_interp_fwd<float, 3, double>);
-  set((const void*)k_interp_fwd<float, 3, float>);
-  set((const void*)k_interp_fwd<float, 5, double>);
-  set((const void*)k_interp_fwd<float, 5, float>);
-  set((const void*)k_interp_fwd<double, 3, double>);
-  set((const void*)k_interp_fwd<double, 3, float>);
-  set((const void*)k_interp_fwd<double, 5, double>);
-  set((const void*)k_interp_fwd<double, 5, float>);
   set((const void*)k_interp_bwd<float, 3, double>);
   set((const void*)k_interp_bwd<float, 3, float>);
   set((const void*)k_interp_bwd<float, 5, double>);

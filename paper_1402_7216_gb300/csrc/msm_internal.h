@@ -54,8 +54,8 @@ struct DeviceBuffers {
   int4* gbase = nullptr;       // [cap]: first level-0 index of the basis support per dim
   // per-atom results in sorted order
   void* phis = nullptr;        // T[cap]  short-range potential
-  void* fs = nullptr;          // R4<T>[cap] short-range force (x, y, z) and long-range potential (w)
-  void* glong = nullptr;       // R4<T>[cap] long-range gradient (x, y, z), spare (w)
+  void* fs = nullptr;          // R4<T>[cap] short-range force (x, y, z), spare (w)
+  void* glong = nullptr;       // R4<T>[cap] long-range gradient (x, y, z) and long-range potential (w)
   // grids, one per level: charges q^k in FP64, potentials u^k in T
   void* gq[kMaxLevels] = {};
   void* gu[kMaxLevels] = {};
@@ -250,9 +250,12 @@ cudaError_t launch_restrict(Plan& P, int k, const void* fine, void* coarse, cuda
 cudaError_t launch_lattice(Plan& P, int k, const void* qk, void* uk, cudaStream_t s);
 cudaError_t launch_top(Plan& P, const void* qt, void* ut, cudaStream_t s);
 cudaError_t launch_prolong(Plan& P, int k, const void* coarse, void* fine, cudaStream_t s);
-// interpolation of u^0 at the atoms and assembly of E, phi, F (forward)
-template <typename OUT>  // OUT = caller's output type (double or float)
-cudaError_t launch_interp_forward(Plan& P, int64_t n, double* energy, OUT* phi, OUT* force, cudaStream_t s);
+// interpolation of u^0 at the atoms and assembly of E, phi, F (forward) in two
+// launches: the grid gather (u_long and its gradient per atom, needs only
+// u^0) and the assembly with the pair sums (phi, F, E; OUT = caller's type)
+cudaError_t launch_interp_gather(Plan& P, int64_t n, cudaStream_t s);
+template <typename OUT>
+cudaError_t launch_interp_assemble(Plan& P, int64_t n, double* energy, OUT* phi, OUT* force, cudaStream_t s);
 // adjoint: interpolation of the adjoint grid and assembly of dL/dq, dL/dr
 template <typename OUT>
 cudaError_t launch_interp_backward(Plan& P, int64_t n, const double* gE, OUT* grad_pos, OUT* grad_q,
