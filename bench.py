@@ -97,7 +97,7 @@ class ClockSampler:
 
 
 def work_model(plan, n, box, cutoff, order):
-    """Algorithmic work per evaluation ('Work and traffic model')."""
+    """Algorithmic work per evaluation: each stage's flops and the fewest bytes it must move."""
     V = box ** 3
     rho = n / V
     pairs = n * (4.0 / 3.0) * math.pi * cutoff ** 3 * rho       # ordered pairs within a
@@ -259,6 +259,73 @@ def bench_batch(dev, args, n_rep=64):
                       "autotuned tile shapes, L2 flushed between steps"}
 
 
+def parareal_timings(args, w, plan, pos, q, n, dev, stream, flush, f_ms, E_mix, F_mix):
+    """The parareal section's coarse propagators G on the same system: the
+    cutoff method (Coulomb law within a) and MSM with a shorter cutoff or a
+    coarser grid, each timed against the MSM evaluation (F, f_ms per eval)."""
+    import torch
+    from paper_1402_7216_gb300 import MSM
+    # the cutoff method on the same system and cutoff (the parareal section's
+    # coarse propagator G): its evaluation time against MSM's (F)
+    E_c = torch.empty((), dtype=torch.float64, device=dev)
+    phi_c = torch.empty(n, dtype=torch.float64, device=dev)
+    F_c = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    for _ in range(3):
+        plan.cutoff_eval(pos, q, out=(E_c, phi_c, F_c))
+    torch.cuda.synchronize()
+    ms_g = []
+    for _ in range(max(3, args.steps // 4)):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.cutoff_eval(pos, q, out=(E_c, phi_c, F_c))
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_g.append(a.elapsed_time(b))
+    plan.check_status()
+    g_ms = sorted(ms_g)[len(ms_g) // 2]
+    cutoff_G = {"metric": "cutoff-method energy+force evals/sec on the same system (Coulomb law within a = %g A)"
+                          % w.cutoff, "value": 1e3 / g_ms, "unit": "evals/s", "ms_per_eval": g_ms,
+                "msm_ms_per_eval": f_ms, "ratio_F_over_G": f_ms / g_ms,
+                "paper_ratio_estimate": {"value": 60, "basis": "operation counts, MSM a=12, h=2, h*=1 A, C2, "
+                                                              "cubic against a 12 A cutoff (no hardware)"},
+                "energy_cutoff_vs_msm_rel": abs(E_c.item() - E_mix) / abs(E_mix)}
+    plan.eval(pos, q)  # leave the plan holding an MSM forward pass
+
+    # MSM itself as the coarse propagator (the parareal section's "shorter
+    # cutoff" and "coarse grid" options): time, F/G and the force error
+    # against the fine configuration
+    def g_variant(cutoff, spacing):
+        pg = MSM(box=w.box, periodic=w.periodic, cutoff=cutoff, spacing=spacing, levels=0, order=w.order,
+                 splitting=w.split, precision="mixed", max_atoms=n)
+        Eg, _, Fg = pg.eval(pos, q)
+        for _ in range(2):
+            pg.eval(pos, q)
+        torch.cuda.synchronize()
+        tg = []
+        for _ in range(max(3, args.steps // 4)):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pg.eval(pos, q, out=(Eg, None, Fg))
+            b.record(stream)
+            torch.cuda.synchronize()
+            tg.append(a.elapsed_time(b))
+        pg.check_status()
+        gm = sorted(tg)[len(tg) // 2]
+        dF = float(torch.sqrt(((Fg - F_mix) ** 2).sum() / (F_mix ** 2).sum()))
+        out = {"cutoff_A": cutoff, "spacing_A": spacing, "h_eff_A": pg.h_eff[0], "grid0": pg.dims[0],
+               "ms_per_eval": gm, "ratio_F_over_G": f_ms / gm, "force_rel_rms_vs_F": dF,
+               "energy_rel_vs_F": abs(Eg.item() - E_mix) / abs(E_mix)}
+        pg.close()
+        return out
+    msm_G = {"shorter_cutoff": g_variant(0.5 * w.cutoff, w.spacing),
+             "coarser_grid": g_variant(w.cutoff, 4.0 * w.spacing),
+             "paper_estimates": "shorter cutoff (6 vs 12 A): at most 7x theoretical speed-up, force error "
+                                "1-5 % from 8 A (Hardy); coarser grid: little gain, the work depends mainly on a"}
+    return cutoff_G, msm_G
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -269,6 +336,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-parareal", action="store_true", help="skip the coarse-propagator timings")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -346,65 +414,10 @@ def main():
     ms_iso, (stage_iso, _, evals_iso), _ = timed(plan, max(3, args.steps // 4), 2, True)
     plan.set_overlap(True)
 
-    # the cutoff method on the same system and cutoff (the parareal section's
-    # coarse propagator G): its evaluation time against MSM's (F)
-    E_c = torch.empty((), dtype=torch.float64, device=dev)
-    phi_c = torch.empty(n, dtype=torch.float64, device=dev)
-    F_c = torch.empty((n, 3), dtype=torch.float64, device=dev)
-    for _ in range(3):
-        plan.cutoff_eval(pos, q, out=(E_c, phi_c, F_c))
-    torch.cuda.synchronize()
-    ms_g = []
-    for _ in range(max(3, args.steps // 4)):
-        flush.fill_(1.0)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        plan.cutoff_eval(pos, q, out=(E_c, phi_c, F_c))
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms_g.append(a.elapsed_time(b))
-    plan.check_status()
-    g_ms = sorted(ms_g)[len(ms_g) // 2]
+    cutoff_G = msm_G = None
     f_ms = sorted(ms)[len(ms) // 2]
-    cutoff_G = {"metric": "cutoff-method energy+force evals/sec on the same system (Coulomb law within a = %g A)"
-                          % w.cutoff, "value": 1e3 / g_ms, "unit": "evals/s", "ms_per_eval": g_ms,
-                "msm_ms_per_eval": f_ms, "ratio_F_over_G": f_ms / g_ms,
-                "paper_ratio_estimate": {"value": 60, "basis": "operation counts, MSM a=12, h=2, h*=1 A, C2, "
-                                                              "cubic against a 12 A cutoff (no hardware)"},
-                "energy_cutoff_vs_msm_rel": abs(E_c.item() - E_mix) / abs(E_mix)}
-    plan.eval(pos, q)  # leave the plan holding an MSM forward pass
-
-    # MSM itself as the coarse propagator (the parareal section's "shorter
-    # cutoff" and "coarse grid" options): time, F/G and the force error
-    # against the fine configuration
-    def g_variant(cutoff, spacing):
-        pg = MSM(box=w.box, periodic=w.periodic, cutoff=cutoff, spacing=spacing, levels=0, order=w.order,
-                 splitting=w.split, precision="mixed", max_atoms=n)
-        Eg, _, Fg = pg.eval(pos, q)
-        for _ in range(2):
-            pg.eval(pos, q)
-        torch.cuda.synchronize()
-        tg = []
-        for _ in range(max(3, args.steps // 4)):
-            flush.fill_(1.0)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            pg.eval(pos, q, out=(Eg, None, Fg))
-            b.record(stream)
-            torch.cuda.synchronize()
-            tg.append(a.elapsed_time(b))
-        pg.check_status()
-        gm = sorted(tg)[len(tg) // 2]
-        dF = float(torch.sqrt(((Fg - F_mix) ** 2).sum() / (F_mix ** 2).sum()))
-        out = {"cutoff_A": cutoff, "spacing_A": spacing, "h_eff_A": pg.h_eff[0], "grid0": pg.dims[0],
-               "ms_per_eval": gm, "ratio_F_over_G": f_ms / gm, "force_rel_rms_vs_F": dF,
-               "energy_rel_vs_F": abs(Eg.item() - E_mix) / abs(E_mix)}
-        pg.close()
-        return out
-    msm_G = {"shorter_cutoff": g_variant(0.5 * w.cutoff, w.spacing),
-             "coarser_grid": g_variant(w.cutoff, 4.0 * w.spacing),
-             "paper_estimates": "shorter cutoff (6 vs 12 A): at most 7x theoretical speed-up, force error "
-                                "1-5 % from 8 A (Hardy); coarser grid: little gain, the work depends mainly on a"}
+    if not args.no_parareal:
+        cutoff_G, msm_G = parareal_timings(args, w, plan, pos, q, n, dev, stream, flush, f_ms, E_mix, F_mix)
 
     # end to end through the host-buffer entry point (pinned host memory)
     pos_pin = torch.tensor(pos_h).pin_memory()

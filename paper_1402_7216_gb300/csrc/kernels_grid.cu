@@ -574,6 +574,7 @@ __global__ void k_prolong_axis(const T* __restrict__ in, T* __restrict__ out, Ax
 constexpr int LBX = 32, LBZ = 4, LPX = 8;
 constexpr int kLatticeLP = 8;   // x outputs per lane of the FP32 lattice kernel (8 or 16)
 constexpr int kLatticeZ = 4;    // warps (output planes) per block of the FP32 lattice kernel
+constexpr size_t kLatticeSmemMax = 200 * 1024;  // dynamic shared memory the FP32 lattice kernels may use
 
 template <typename T>
 __device__ __forceinline__ void two_sum_add(T& s, T& c, T x) {
@@ -701,7 +702,10 @@ __device__ __forceinline__ void window_offsets(const GridDims& G, int x0, int y0
 // Asynchronous staging of one plane (cp.async: global -> shared without
 // registers); points outside an open grid are zero-filled (source size 0).
 // Each thread walks the window with a fixed stride of blockDim.x elements,
-// stepping its (row, column) incrementally.
+// stepping its (row, column) incrementally.  Window rows are stored even rows
+// first, then odd rows (row yy at yy / 2 + (yy odd) * SY / 2): lanes reading
+// rows 2 ty + c then read rows ty apart, one odd row stride SX apart, which
+// keeps the lanes of a warp on distinct banks.
 __device__ __forceinline__ void stage_plane_async(float* plane, const float* __restrict__ q, const GridDims& G,
                                                   int zi, const int* col, const int* row, int SXw, int SX, int SY) {
   int gz;
@@ -721,7 +725,7 @@ __device__ __forceinline__ void stage_plane_async(float* plane, const float* __r
     const int gx = col[xx], go = row[yy];
     const bool ok = zok && gx >= 0 && go >= 0;
     const float* src = ok ? qz + go + gx : q;
-    unsigned dst = (unsigned)__cvta_generic_to_shared(plane + yy * SX + xx);
+    unsigned dst = (unsigned)__cvta_generic_to_shared(plane + ((yy >> 1) + (yy & 1) * (SY >> 1)) * SX + xx);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0));
     xx += dxx;
     yy += dyy;
@@ -732,14 +736,22 @@ __device__ __forceinline__ void stage_plane_async(float* plane, const float* __r
   }
 }
 
-// FP32: each lane owns LP consecutive x outputs of two rows TYN apart, packed
-// into float2 (one FFMA2 per two outputs); a warp covers 32 (x) x 2 TYN (y)
-// of one plane (TYN = 32 LP / 32 rows of lanes).  Coefficients are stored
-// pre-duplicated as float2 pairs; the next input plane is staged by cp.async
-// while the current one is applied (double buffer).  A segment of 8 taps is
-// applied as a sliding window: input column k feeds the outputs j = k - t of
-// every tap t, so one pair of shared loads serves up to 8 FFMA2 (LP + 7 loads
-// per 8 LP FFMA2).  Taps accumulate straight into the outputs (summing each
+// FP32: each lane owns LP consecutive x outputs of two adjacent rows (y,
+// y + 1), packed into float2 (one FFMA2 per two outputs); a warp covers TXN LP
+// (x) x 2 TYN (y) of one plane.  An input row y + e feeds both outputs, row y
+// through the taps of stencil row e and row y + 1 through those of row e - 1,
+// so the table holds those coefficient pairs and one shared load serves both
+// rows (against two rows TYN apart with one coefficient each: 5% faster on
+// the 1.07M-atom system, 9% on the 64-replica batch).  The next input plane
+// is staged by cp.async while the current one is applied (double buffer).  A
+// segment of 8 taps is applied as a sliding window: input column k feeds the
+// outputs j = k - t of every tap t, so one shared load serves up to 8 FFMA2
+// (LP + 7 loads per 8 LP FFMA2); the row pairing costs 2 Ey + 2 input rows per
+// output pair instead of 2 Ey + 1.  The block's warps share each input plane
+// and apply to it different stencil planes dz, of unequal size, so a warp
+// may wait at the plane's barrier; stepping the warps through dz together
+// (each on its own input plane, a ring of kLatticeZ + 1 buffers) removes the
+// wait but measured 15-20% slower, the larger ring costing resident blocks.  Taps accumulate straight into the outputs (summing each
 // plane first measured no different on the 1.07M-atom system: mixed-vs-FP64
 // energy 4.4e-8, force 4.9e-7).
 // TXC, TYC: the warp tile fixed at compile time (the common 32 x 16 tile),
@@ -762,7 +774,7 @@ __device__ __forceinline__ void lattice_f2_body(const float* __restrict__ q, flo
   const int x0 = bx * TW, y0 = by * LBY, z0 = bz * kLatticeZ, zo = z0 + warp;
   const int nplanes = kLatticeZ + 2 * Ez, per = (nplanes + L.nsplit - 1) / L.nsplit;
   const int zbeg = z0 - Ez + part * per, zend = min(z0 - Ez + nplanes, zbeg + per);
-  float2 acc[LP];  // (row ty, row ty + TYN) of the LP x outputs
+  float2 acc[LP];  // (row 2 ty, row 2 ty + 1) of the LP x outputs
 #pragma unroll
   for (int j = 0; j < LP; ++j) acc[j] = make_float2(0.f, 0.f);
   window_offsets(G, x0, y0, Ex, Ey, SXw, SY, col, row);
@@ -781,11 +793,12 @@ __device__ __forceinline__ void lattice_f2_body(const float* __restrict__ q, flo
       const int s1 = seg_start[dz + Ez + 1];
       for (int s = seg_start[dz + Ez]; s < s1; ++s) {
         const Segment2 sg = seg[s];
-        const float* r0 = cur + (ty + Ey + sg.dy) * SX + tx * LP + Ex + sg.dx0;
-        const float* r1 = r0 + TYN * SX;
+        const int c = Ey + sg.dy;  // window row 2 ty + c, stored at ty + c / 2 (+ SY / 2 when c is odd)
+        const float* r0 = cur + (ty + (c >> 1) + (c & 1) * (SY >> 1)) * SX + tx * LP + Ex + sg.dx0;
 #pragma unroll
         for (int k = 0; k < LP + kSeg - 1; ++k) {
-          const float2 w = make_float2(r0[k], r1[k]);
+          const float v = r0[k];
+          const float2 w = make_float2(v, v);
 #pragma unroll
           for (int t = 0; t < kSeg; ++t)
             if (k - t >= 0 && k - t < LP) acc[k - t] = __ffma2_rn(sg.g[t], w, acc[k - t]);
@@ -798,7 +811,7 @@ __device__ __forceinline__ void lattice_f2_body(const float* __restrict__ q, flo
   if (zo >= G.n[2] || !active) return;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
-    const int y = y0 + ty + TYN * r;
+    const int y = y0 + 2 * ty + r;
     if (y >= G.n[1]) continue;
 #pragma unroll
     for (int j = 0; j < LP; ++j) {
@@ -1422,12 +1435,15 @@ __global__ void k_f64_to_f32(const double* __restrict__ src, float* __restrict__
 // the staging of its input window; the cost counts both (a warp's stencil
 // pass at a plane is ~14,000 instructions, staging ~1/3 instruction per
 // window element), so ragged small grids get tiles that fit them.
+static size_t lattice_smem(int txn, int tyn, const int E[3]);
+
 static void lattice_tile(int n0, int n1, const int E[3], int& txn, int& tyn) {
   double best = -1.0;
   txn = 4;
   tyn = 8;
   for (int a = 1; a <= 32; ++a)
     for (int b = 1; a * b <= 32; ++b) {
+      if (lattice_smem(a, b, E) > kLatticeSmemMax) continue;
       const double tiles = (double)((n0 + kLatticeLP * a - 1) / (kLatticeLP * a)) * ((n1 + 2 * b - 1) / (2 * b));
       const double window = (double)(kLatticeLP * a + 2 * E[0] + kSeg) * (2 * b + 2 * E[1]);
       const double cost = tiles * (14000.0 + window / 3.0);
@@ -1491,6 +1507,14 @@ void lattice_t(Plan& P, int k, const double* qk64, T* uk, cudaStream_t st) {
   } else {
     k_lattice<T, false><<<grid, 128, sm, st>>>(qk, uk, G, (const Segment<T>*)P.d.seg, P.d.seg_start, L, scale);
   }
+}
+
+bool lattice_fits(const Plan& P) {
+  if (P.fp64) {
+    const int SX = (LBX + 2 * P.E[0] + kSeg) | 1, SY = 8 + 2 * P.E[1];
+    return sizeof(double) * SX * SY <= 48 * 1024;
+  }
+  return lattice_smem(4, 8, P.E) <= kLatticeSmemMax;
 }
 
 cudaError_t launch_lattice(Plan& P, int k, const void* qk, void* uk, cudaStream_t st) {
@@ -1783,7 +1807,7 @@ __global__ void __launch_bounds__(256, 2) kb_anterp_fx(const AntKArgs* __restric
                         b / (a.nbx * a.nby));
 }
 
-__global__ void __launch_bounds__(32 * kLatticeZ) kb_lattice_f2(const LatKArgs* __restrict__ tab,
+__global__ void __launch_bounds__(32 * kLatticeZ, 7) kb_lattice_f2(const LatKArgs* __restrict__ tab,
                                                                    const int* __restrict__ first, int nrep) {
   const int r = batch_rep(first, nrep, blockIdx.x);
   const LatKArgs& a = tab[r];
@@ -2127,7 +2151,7 @@ cudaError_t grid_batch_interp(GridBatch* B, bool backward, cudaStream_t st) {
 cudaError_t configure_kernels() {
   cudaError_t e = cudaSuccess;
   auto set = [&](const void* f) {
-    cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLatticeSmemMax);
     if (r != cudaSuccess) e = r;
   };
   set((const void*)k_interp_gather<float, 3>);

@@ -33,7 +33,9 @@ struct Segment {
   T g[kSeg];
 };
 
-// The same run with each coefficient duplicated, for packed FP32x2 FMAs.
+// A run over two adjacent stencil rows, for packed FP32x2 FMAs: g[j] =
+// (tap (dx0 + j, dy, dz), tap (dx0 + j, dy - 1, dz)), the coefficients that
+// one input row applies to the two output rows y and y + 1 it feeds.
 struct alignas(16) Segment2 {
   float2 g[kSeg];  // first, so that it loads as four 16-byte words
   int dy, dx0;
@@ -70,7 +72,7 @@ struct DeviceBuffers {
   double* topu = nullptr;
   // level stencil
   void* seg = nullptr;         // Segment<T>[nseg]
-  void* seg2 = nullptr;        // Segment2[nseg] (mixed precision only)
+  void* seg2 = nullptr;        // Segment2[nseg] (mixed precision only, instead of seg)
   int* seg_start = nullptr;    // [2*Ez+2]: segments of plane dz live in [start[dz+Ez], start[dz+Ez+1])
   // neighbour cell offsets (x, y, z) of the pair kernel
   int4* cell_off = nullptr;    // [noff]
@@ -247,6 +249,9 @@ cudaError_t launch_cutoff_assemble(Plan& P, int64_t n, double* energy, OUT* phi,
 cudaError_t launch_anterpolate(Plan& P, int64_t n, void* grid0, const double* dscale, double factor,
                                cudaStream_t s);
 cudaError_t launch_restrict(Plan& P, int k, const void* fine, void* coarse, cudaStream_t s);
+// Whether the level stencil's window fits the lattice kernel's shared memory
+// (a stencil of half-width E holds about (2 E)^2 window points per plane).
+bool lattice_fits(const Plan& P);
 cudaError_t launch_lattice(Plan& P, int k, const void* qk, void* uk, cudaStream_t s);
 cudaError_t launch_top(Plan& P, const void* qt, void* ut, cudaStream_t s);
 cudaError_t launch_prolong(Plan& P, int k, const void* coarse, void* fine, cudaStream_t s);

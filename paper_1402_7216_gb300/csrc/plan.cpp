@@ -194,6 +194,46 @@ void build_segments(const Plan& P, const std::vector<double>& G, const int E[3],
   (void)P;
 }
 
+// Row pairs of the stencil for the packed FP32 kernel, whose lanes own two
+// adjacent output rows (y, y + 1): input row y + e feeds row y through the
+// taps of row e and row y + 1 through those of row e - 1, so one window load
+// serves both.  Entry (dz, e, dx0), e = -Ey..Ey+1, holds the pairs
+// (G(dx0 + j, e, dz), G(dx0 + j, e - 1, dz)) over the union of the two rows'
+// x extents (zero where a row has no tap).
+void build_row_pairs(const std::vector<double>& G, const int E[3], std::vector<Segment2>& segs,
+                     std::vector<int>& start) {
+  const int nx = 2 * E[0] + 1, ny = 2 * E[1] + 1;
+  auto at = [&](int dx, int dy, int dz) -> double {
+    if (dy < -E[1] || dy > E[1] || dx < -E[0] || dx > E[0]) return 0.0;
+    return G[((size_t)(dz + E[2]) * ny + (dy + E[1])) * nx + (dx + E[0])];
+  };
+  auto extent = [&](int dy, int dz) {  // largest |dx| with a nonzero tap, -1 for an empty row
+    int X = -1;
+    for (int dx = 0; dx <= E[0]; ++dx)
+      if (at(dx, dy, dz) != 0.0) X = dx;
+    return X;
+  };
+  start.assign(2 * E[2] + 2, 0);
+  for (int dz = -E[2]; dz <= E[2]; ++dz) {
+    start[dz + E[2]] = (int)segs.size();
+    for (int e = -E[1]; e <= E[1] + 1; ++e) {
+      const int X = std::max(extent(e, dz), extent(e - 1, dz));
+      if (X < 0) continue;
+      for (int dx0 = -X; dx0 <= X; dx0 += kSeg) {
+        Segment2 s;
+        s.dy = e;
+        s.dx0 = dx0;
+        for (int j = 0; j < kSeg; ++j) {
+          const int dx = dx0 + j;
+          s.g[j] = dx <= X ? make_float2((float)at(dx, e, dz), (float)at(dx, e - 1, dz)) : make_float2(0.f, 0.f);
+        }
+        segs.push_back(s);
+      }
+    }
+  }
+  start[2 * E[2] + 1] = (int)segs.size();
+}
+
 }  // namespace
 
 int64_t grid_points(const Plan& P, int k) { return (int64_t)P.n[k][0] * P.n[k][1] * P.n[k][2]; }
@@ -339,6 +379,7 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
     P->E[d] = (int)std::ceil(R / P->h[d]);
     while (P->E[d] > 0 && P->E[d] * P->h[d] >= R) --P->E[d];
   }
+  if (!lattice_fits(*P)) return MSM_ERR_UNSUPPORTED;  // cutoff too many grid spacings wide
   std::vector<double> G((size_t)(2 * P->E[0] + 1) * (2 * P->E[1] + 1) * (2 * P->E[2] + 1), 0.0);
   double taps = 0;
   for (int dz = -P->E[2]; dz <= P->E[2]; ++dz)
@@ -471,16 +512,9 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
     P->nseg = (int)segs.size();
     if (upload(&D.seg, segs) != cudaSuccess) return MSM_ERR_OOM;
   } else {
-    std::vector<Segment<float>> segs;
-    build_segments<float>(*P, G, P->E, segs, start);
-    P->nseg = (int)segs.size();
-    if (upload(&D.seg, segs) != cudaSuccess) return MSM_ERR_OOM;
-    std::vector<Segment2> segs2(segs.size());
-    for (size_t i = 0; i < segs.size(); ++i) {
-      segs2[i].dy = segs[i].dy;
-      segs2[i].dx0 = segs[i].dx0;
-      for (int j = 0; j < kSeg; ++j) segs2[i].g[j] = make_float2(segs[i].g[j], segs[i].g[j]);
-    }
+    std::vector<Segment2> segs2;
+    build_row_pairs(G, P->E, segs2, start);
+    P->nseg = (int)segs2.size();
     if (upload(&D.seg2, segs2) != cudaSuccess) return MSM_ERR_OOM;
   }
   if (upload((void**)&D.seg_start, start) != cudaSuccess) return MSM_ERR_OOM;

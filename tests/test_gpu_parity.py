@@ -304,3 +304,22 @@ def test_overlap_on_and_off_agree(dev):
         assert abs(a[0] - b[0]) <= tol * abs(a[0])
         assert rel_rms(a[2], b[2]) <= tol and rel_rms(a[1], b[1]) <= tol
         assert_close(b, ref, precision, precision)
+
+
+def test_stencil_wider_than_the_lattice_window_is_unsupported(dev):
+    """2a/h beyond the lattice kernel's shared-memory window is refused at
+    plan creation (UNSUPPORTED), not at the first evaluation."""
+    from paper_1402_7216_gb300 import MSMError
+    # capacity for cells a/2 wide, so that the anterpolation patch fits and
+    # the stencil is what decides
+    wide = dict(box=40.0, periodic=False, cutoff=12.0, order=3, split=2)
+    cap = 10000
+    for precision, h in [("mixed", 0.35), ("fp64", 0.85)]:   # 2a/h = 68.6 and 28.2
+        with pytest.raises(MSMError) as e:
+            plan_for(dict(wide, spacing=h), precision, cap)
+        assert e.value.code == -2
+    plan = plan_for(dict(wide, spacing=0.85), "mixed", cap)  # fits the FP32 window
+    pos = torch.tensor([[10.0, 10.0, 10.0], [13.0, 10.0, 10.0]], dtype=torch.float64, device=dev)
+    q = torch.tensor([1.0, -1.0], dtype=torch.float64, device=dev)
+    E = plan.eval(pos, q)[0]
+    assert abs(E + 1.0 / 3.0) < 1e-3 * (1.0 / 3.0)   # two opposite charges 3 A apart
