@@ -136,6 +136,30 @@ int msm_eval(msm_handle h, int64_t n, const double* pos, const double* q, double
 int msm_cutoff_eval(msm_handle h, int64_t n, const double* pos, const double* q, double* energy,
                     double* phi, double* force, void* cuda_stream);
 
+/* Molecular dynamics around the MSM force: nsteps steps of the velocity
+ * Verlet scheme (Sec. "Molecular Dynamics", the velocity Verlet equations),
+ * each one
+ *   v += (dt/2) F inv_mass;  r += dt v  (periodic boxes wrap r into [0, L));
+ *   F = MSM force at the new r (one msm_eval);  v += (dt/2) F inv_mass.
+ *   pos      [n][3] double, device, in/out: r(t0) in, r(t0 + nsteps dt) out.
+ *   vel      [n][3] double, device, in/out.
+ *   force    [n][3] double, device, in/out: must hold F(r(t0)) on entry (from
+ *            msm_eval, or from the previous call); holds F at the final r.
+ *   inv_mass [n] double, device: 1/m_i; 0 fixes the atom (no kick, and it
+ *            carries no kinetic energy or momentum).
+ *   q        [n] double, device.
+ *   records  [nsteps][6] double, device or NULL: per step, after its second
+ *            half kick, {potential E, kinetic 1/2 sum m v^2, total, and the
+ *            momentum sum m v (x, y, z)}, each reduced in a fixed order.
+ * Units are the caller's: the kick is F * inv_mass * dt, so coulomb_k, the
+ * masses and dt must be consistent.  Asynchronous on cuda_stream and
+ * capturable in a CUDA graph (3 + one evaluation's launches per step).
+ * Errors: INVALID_ARG (n < 0, nsteps < 0, non-finite dt, missing buffers),
+ * TOO_MANY_ATOMS, CUDA; ATOM_OUTSIDE_BOX (an atom left an open box) and
+ * NONFINITE later through msm_status. */
+int msm_md_run(msm_handle h, int64_t n, double* pos, double* vel, double* force, const double* inv_mass,
+               const double* q, double dt, int nsteps, double* records, void* cuda_stream);
+
 /* Adjoint of the last msm_eval on this plan: given the upstream gradient
  * grad_energy = dL/dE ([1] double, device), writes grad_pos = dL/dr ([n][3])
  * and grad_q = dL/dq ([n]); either output may be NULL.  The long-range part

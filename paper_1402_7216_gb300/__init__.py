@@ -137,6 +137,36 @@ class MSM:
         self._last_n = None
         return E, phi, F
 
+    def md_run(self, pos, vel, inv_mass, q, dt, nsteps, force=None, records=True, stream=None):
+        """msm_md_run: nsteps velocity Verlet steps around the MSM force, in
+        place on float64 device tensors pos [N,3], vel [N,3] and force [N,3]
+        (F at pos; None evaluates it first).  Returns (force, records) with
+        records [nsteps, 6] = (potential, kinetic, total, momentum x, y, z)
+        per step, or None when records is False."""
+        if not pos.is_contiguous():
+            raise ValueError("md_run updates pos in place: it must be contiguous")
+        pos, q = self._check_inputs(pos, q)
+        if pos.dtype != torch.float64:
+            raise ValueError("md_run takes float64 pos and q")
+        checks = [("vel", vel, pos.shape), ("inv_mass", inv_mass, q.shape)]
+        if force is not None:
+            checks.append(("force", force, pos.shape))
+        for name, t, shape in checks:
+            if t.dtype != torch.float64 or t.device != pos.device or tuple(t.shape) != tuple(shape) \
+                    or not t.is_contiguous():
+                raise ValueError("%s must be a contiguous float64 tensor of shape %s on %s"
+                                 % (name, tuple(shape), pos.device))
+        n = pos.shape[0]
+        if force is None:
+            _, _, force = self.eval(pos, q, want_phi=False, stream=stream)
+        rec = torch.empty((max(int(nsteps), 0), 6), dtype=torch.float64, device=pos.device) if records else None
+        rc = lib().msm_md_run(self._h, n, _ptr(pos), _ptr(vel), _ptr(force), _ptr(inv_mass), _ptr(q), float(dt),
+                              int(nsteps), _ptr(rec), _stream(stream))
+        _capi.check(rc, "msm_md_run")
+        self._last_n = n if nsteps > 0 else self._last_n
+        self._last_io = torch.float64
+        return force, rec
+
     def eval_f32io(self, pos, q, want_phi=True, want_force=True, stream=None, out=None):
         """msm_eval_f32io: eval with float32 positions, charges and outputs."""
         if pos.dtype != torch.float32 or q.dtype != torch.float32:

@@ -4,6 +4,7 @@
 // short-range pairs, anterpolation, restriction and lattice cutoff per level,
 // top level, prolongation, interpolation and assembly.  The grid passes may
 // run on a plan-owned stream forked from and joined back onto the caller's.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -358,6 +359,27 @@ int msm_cutoff_eval(msm_handle h, int64_t n, const double* pos, const double* q,
   if (e != cudaSuccess) return MSM_ERR_CUDA;
   P.last_stream = st;
   P.evals += 1;
+  return MSM_OK;
+}
+
+int msm_md_run(msm_handle h, int64_t n, double* pos, double* vel, double* force, const double* inv_mass,
+               const double* q, double dt, int nsteps, double* records, void* stream) {
+  if (!h || n < 0 || nsteps < 0 || !std::isfinite(dt)) return MSM_ERR_INVALID_ARG;
+  if (n > 0 && (!pos || !vel || !force || !inv_mass || !q)) return MSM_ERR_INVALID_ARG;
+  Plan& P = h->p;
+  if (n > P.cap) return MSM_ERR_TOO_MANY_ATOMS;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* potential = P.d.scalars + 1;  // the step's energy when no record is kept
+  for (int s = 0; s < nsteps; ++s) {
+    double* rec = records ? records + 6 * (size_t)s : nullptr;
+    double* u = rec ? rec : potential;
+    if (launch_md_drift(P, n, pos, vel, force, inv_mass, dt, st) != cudaSuccess) return MSM_ERR_CUDA;
+    int rc = forward(P, n, (const double*)pos, q, u, (double*)nullptr, force, st);
+    if (rc != MSM_OK) return rc;
+    if (launch_md_kick(P, n, vel, force, inv_mass, dt, u, rec ? rec : P.d.scalars + 2, st) != cudaSuccess)
+      return MSM_ERR_CUDA;
+  }
+  P.last_stream = st;
   return MSM_OK;
 }
 

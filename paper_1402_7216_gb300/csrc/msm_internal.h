@@ -80,7 +80,8 @@ struct DeviceBuffers {
   int4* cell_rows = nullptr;   // [nrows]: (dy, dz, xlo, xhi) rows of neighbour cell offsets
   // reductions and status
   double* partial = nullptr;   // per-block energy partials
-  double* scalars = nullptr;   // [8] scratch scalars (0: backward scale)
+  double* scalars = nullptr;   // [8] scratch scalars (0: backward scale; 1, 2..7: MD energy and record when none is kept)
+  double* md_partial = nullptr;  // [4 * kMdBlocks] per-block kinetic energy and momentum of the MD loop
   int* status = nullptr;
   // host-path staging (msm_eval_host)
   double* hpos = nullptr;
@@ -249,6 +250,14 @@ cudaError_t launch_cutoff_assemble(Plan& P, int64_t n, double* energy, OUT* phi,
 cudaError_t launch_anterpolate(Plan& P, int64_t n, void* grid0, const double* dscale, double factor,
                                cudaStream_t s);
 cudaError_t launch_restrict(Plan& P, int k, const void* fine, void* coarse, cudaStream_t s);
+// Velocity Verlet around the MSM force: the two half steps of one MD step
+// and the per-step record (potential, kinetic, total energy, momentum).
+constexpr int kMdBlocks = 1024;  // blocks (and partials) of the MD kernels
+cudaError_t launch_md_drift(Plan& P, int64_t n, double* pos, double* vel, const double* force,
+                            const double* inv_mass, double dt, cudaStream_t s);
+cudaError_t launch_md_kick(Plan& P, int64_t n, double* vel, const double* force, const double* inv_mass, double dt,
+                           const double* potential, double* record, cudaStream_t s);
+
 // Whether the level stencil's window fits the lattice kernel's shared memory
 // (a stencil of half-width E holds about (2 E)^2 window points per plane).
 bool lattice_fits(const Plan& P);
