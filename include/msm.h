@@ -136,15 +136,20 @@ int msm_eval(msm_handle h, int64_t n, const double* pos, const double* q, double
 int msm_cutoff_eval(msm_handle h, int64_t n, const double* pos, const double* q, double* energy,
                     double* phi, double* force, void* cuda_stream);
 
-/* Molecular dynamics around the MSM force: nsteps steps of the velocity
- * Verlet scheme (Sec. "Molecular Dynamics", the velocity Verlet equations),
- * each one
+/* Force methods of the MD entry points. */
+#define MSM_MD_MSM 0    /* the MSM evaluation (msm_eval) */
+#define MSM_MD_CUTOFF 1 /* the cutoff method (msm_cutoff_eval) */
+
+/* Molecular dynamics: nsteps steps of the velocity Verlet scheme (Sec.
+ * "Molecular Dynamics", the velocity Verlet equations), each one
  *   v += (dt/2) F inv_mass;  r += dt v  (periodic boxes wrap r into [0, L));
- *   F = MSM force at the new r (one msm_eval);  v += (dt/2) F inv_mass.
+ *   F = force at the new r (method: MSM_MD_MSM, one msm_eval; MSM_MD_CUTOFF,
+ *   one msm_cutoff_eval);  v += (dt/2) F inv_mass.
  *   pos      [n][3] double, device, in/out: r(t0) in, r(t0 + nsteps dt) out.
  *   vel      [n][3] double, device, in/out.
- *   force    [n][3] double, device, in/out: must hold F(r(t0)) on entry (from
- *            msm_eval, or from the previous call); holds F at the final r.
+ *   force    [n][3] double, device, in/out: must hold F(r(t0)) of the same
+ *            method on entry (from msm_eval / msm_cutoff_eval, or from the
+ *            previous call); holds F at the final r.
  *   inv_mass [n] double, device: 1/m_i; 0 fixes the atom (no kick, and it
  *            carries no kinetic energy or momentum).
  *   q        [n] double, device.
@@ -154,11 +159,50 @@ int msm_cutoff_eval(msm_handle h, int64_t n, const double* pos, const double* q,
  * Units are the caller's: the kick is F * inv_mass * dt, so coulomb_k, the
  * masses and dt must be consistent.  Asynchronous on cuda_stream and
  * capturable in a CUDA graph (3 + one evaluation's launches per step).
- * Errors: INVALID_ARG (n < 0, nsteps < 0, non-finite dt, missing buffers),
- * TOO_MANY_ATOMS, CUDA; ATOM_OUTSIDE_BOX (an atom left an open box) and
- * NONFINITE later through msm_status. */
+ * Errors: INVALID_ARG (n < 0, nsteps < 0, non-finite dt, unknown method,
+ * missing buffers), TOO_MANY_ATOMS, CUDA; ATOM_OUTSIDE_BOX (an atom left an
+ * open box) and NONFINITE later through msm_status. */
 int msm_md_run(msm_handle h, int64_t n, double* pos, double* vel, double* force, const double* inv_mass,
-               const double* q, double dt, int nsteps, double* records, void* cuda_stream);
+               const double* q, double dt, int nsteps, int method, double* records, void* cuda_stream);
+
+/* msm_md_run for nrep independent systems, replica r holding atoms
+ * offsets[r] .. offsets[r+1]-1 of every per-atom array and evaluated by
+ * plans[r] (distinct plans); records, when given, is [nrep][nsteps][6].  The
+ * replicas run concurrently on a pool of streams forked from cuda_stream
+ * and joined back (events only; capturable).  Errors as msm_eval_batch and
+ * msm_md_run. */
+int msm_md_run_batch(const msm_handle* plans, int nrep, const int64_t* offsets, double* pos, double* vel,
+                     double* force, const double* inv_mass, const double* q, double dt, int nsteps, int method,
+                     double* records, void* cuda_stream);
+
+/* Parareal integration of one window (Sec. "Parareal Method", Eq. parareal):
+ * time points T_k = T_0 + k dT, k = 0..window, with dT = steps_fine dt_fine;
+ * the fine propagator F is steps_fine velocity Verlet steps of dt_fine with
+ * the MSM force (fine[k] evaluates the propagation from T_k; the window's
+ * propagations run concurrently, one plan each), the coarse propagator G
+ * steps_coarse steps of dt_coarse with the cutoff method (plan coarse, which
+ * may be one of fine[]); each propagation starts by evaluating the force at
+ * its starting positions.  Iteration 0 is the coarse sweep lambda_{k+1} =
+ * G(lambda_k); each further iteration computes F(lambda_k) for every k, then
+ * sweeps lambda_{k+1} = G(lambda_k new) + F(lambda_k old) - G(lambda_k old),
+ * positions through the minimum image of F - G and wrapped when periodic.
+ * It stops after max_iter iterations or once the largest change of a
+ * position, and of a velocity times dT, is at most tol (A).  After
+ * `window` iterations the result is the sequential fine trajectory.
+ *   pos0, vel0 [n][3], inv_mass [n], q [n]: device, the state at T_0.
+ *   lam_pos, lam_vel [window+1][n][3] double, device, out: lambda_0..window.
+ *   workspace  device, msm_parareal_workspace(n, window) bytes.
+ *   iterations host int or NULL: iterations run (not counting the sweep).
+ *   change     host double [max_iter][2] or NULL: per iteration the largest
+ *              position change (A) and velocity change.
+ * Synchronous: reads the change back after each iteration.  window is 1 to
+ * MSM_PARAREAL_MAX_WINDOW.  Errors: INVALID_ARG, TOO_MANY_ATOMS, CUDA. */
+#define MSM_PARAREAL_MAX_WINDOW 64
+int64_t msm_parareal_workspace(int64_t n, int window);
+int msm_parareal(const msm_handle* fine, msm_handle coarse, int64_t n, const double* pos0, const double* vel0,
+                 const double* inv_mass, const double* q, int window, double dt_fine, int steps_fine,
+                 double dt_coarse, int steps_coarse, int max_iter, double tol, double* lam_pos, double* lam_vel,
+                 void* workspace, int* iterations, double* change, void* cuda_stream);
 
 /* Adjoint of the last msm_eval on this plan: given the upstream gradient
  * grad_energy = dL/dE ([1] double, device), writes grad_pos = dL/dr ([n][3])

@@ -17,7 +17,10 @@ import torch
 from . import _capi
 from ._capi import MSMError, MSM_FP64, MSM_MIXED  # noqa: F401
 
-__all__ = ["MSM", "MSMBatch", "BatchGraph", "MSMEnergy", "MSMError", "MSM_FP64", "MSM_MIXED", "lib"]
+__all__ = ["MSM", "MSMBatch", "BatchGraph", "MSMEnergy", "MSMError", "MSM_FP64", "MSM_MIXED", "lib", "parareal",
+           "MD_METHODS"]
+
+MD_METHODS = {"msm": 0, "cutoff": 1}  # MSM_MD_MSM, MSM_MD_CUTOFF
 
 
 def lib():
@@ -137,12 +140,15 @@ class MSM:
         self._last_n = None
         return E, phi, F
 
-    def md_run(self, pos, vel, inv_mass, q, dt, nsteps, force=None, records=True, stream=None):
-        """msm_md_run: nsteps velocity Verlet steps around the MSM force, in
-        place on float64 device tensors pos [N,3], vel [N,3] and force [N,3]
-        (F at pos; None evaluates it first).  Returns (force, records) with
+    def md_run(self, pos, vel, inv_mass, q, dt, nsteps, force=None, records=True, stream=None, method="msm"):
+        """msm_md_run: nsteps velocity Verlet steps around the MSM force
+        (method "msm") or the cutoff method's ("cutoff"), in place on float64
+        device tensors pos [N,3], vel [N,3] and force [N,3] (F at pos by the
+        same method; None evaluates it first).  Returns (force, records) with
         records [nsteps, 6] = (potential, kinetic, total, momentum x, y, z)
         per step, or None when records is False."""
+        if method not in MD_METHODS:
+            raise ValueError("method must be one of %s" % sorted(MD_METHODS))
         if not pos.is_contiguous():
             raise ValueError("md_run updates pos in place: it must be contiguous")
         pos, q = self._check_inputs(pos, q)
@@ -158,13 +164,15 @@ class MSM:
                                  % (name, tuple(shape), pos.device))
         n = pos.shape[0]
         if force is None:
-            _, _, force = self.eval(pos, q, want_phi=False, stream=stream)
+            ev = self.eval if method == "msm" else self.cutoff_eval
+            _, _, force = ev(pos, q, want_phi=False, stream=stream)
         rec = torch.empty((max(int(nsteps), 0), 6), dtype=torch.float64, device=pos.device) if records else None
         rc = lib().msm_md_run(self._h, n, _ptr(pos), _ptr(vel), _ptr(force), _ptr(inv_mass), _ptr(q), float(dt),
-                              int(nsteps), _ptr(rec), _stream(stream))
+                              int(nsteps), MD_METHODS[method], _ptr(rec), _stream(stream))
         _capi.check(rc, "msm_md_run")
-        self._last_n = n if nsteps > 0 else self._last_n
-        self._last_io = torch.float64
+        if nsteps > 0 or force is None:
+            self._last_n = n if method == "msm" else None
+            self._last_io = torch.float64
         return force, rec
 
     def eval_f32io(self, pos, q, want_phi=True, want_force=True, stream=None, out=None):
@@ -283,6 +291,22 @@ class MSMBatch:
         _capi.check(rc, "msm_eval_backward_batch")
         return gp, gq
 
+    def md_run(self, pos, vel, force, inv_mass, q, counts, dt, nsteps, method="msm", records=True, stream=None):
+        """msm_md_run_batch: nsteps velocity Verlet steps of every replica, in
+        place on the concatenated float64 device tensors pos, vel and force
+        (force: F at pos of each replica by the same method).  Returns the
+        records [nrep, nsteps, 6] or None."""
+        offs, n = self._offsets(counts)
+        rec = (torch.empty((len(self.plans), max(int(nsteps), 0), 6), dtype=torch.float64, device=pos.device)
+               if records else None)
+        rc = lib().msm_md_run_batch(self._arr, len(self.plans), offs, _ptr(pos), _ptr(vel), _ptr(force),
+                                    _ptr(inv_mass), _ptr(q), float(dt), int(nsteps), MD_METHODS[method], _ptr(rec),
+                                    _stream(stream))
+        _capi.check(rc, "msm_md_run_batch")
+        for p, c in zip(self.plans, counts):
+            p._last_n = int(c) if method == "msm" else None
+        return rec
+
     def graph(self, pos, q, counts, energies, phi=None, force=None, grad_energies=None, grad_pos=None,
               grad_q=None):
         """Captures the batched forward (+ adjoint when grad_energies is given)
@@ -316,6 +340,44 @@ class BatchGraph:
             self.close()
         except Exception:
             pass
+
+
+def parareal(fine, coarse, pos0, vel0, inv_mass, q, window, dt_fine, steps_fine, dt_coarse, steps_coarse,
+             max_iter, tol, stream=None):
+    """msm_parareal: one parareal window (Eq. parareal) with F = steps_fine
+    velocity Verlet steps of dt_fine on the MSM force (fine: `window`
+    distinct plans, run concurrently) and G = steps_coarse steps of dt_coarse
+    on the cutoff method (plan coarse).  Returns (lam_pos [window+1, N, 3],
+    lam_vel [window+1, N, 3], iterations, change [iterations, 2]) with the
+    largest position and velocity change of each iteration."""
+    import numpy as np
+    fine = list(fine)
+    if len(fine) != window:
+        raise ValueError("one fine plan per time point of the window")
+    n = pos0.shape[0]
+    dev = pos0.device
+    for name, t, shape in (("pos0", pos0, (n, 3)), ("vel0", vel0, (n, 3)), ("inv_mass", inv_mass, (n,)),
+                           ("q", q, (n,))):
+        if t.dtype != torch.float64 or t.device != dev or tuple(t.shape) != shape or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous float64 tensor of shape %s on %s" % (name, shape, dev))
+    nbytes = lib().msm_parareal_workspace(n, int(window))
+    if nbytes < 0:
+        raise ValueError("window must be 1..64")
+    ws = torch.empty(max(nbytes, 8), dtype=torch.uint8, device=dev)
+    lam_pos = torch.empty((window + 1, n, 3), dtype=torch.float64, device=dev)
+    lam_vel = torch.empty_like(lam_pos)
+    arr = (C.c_void_p * window)(*[p._h.value for p in fine])
+    iters = C.c_int(0)
+    change = np.zeros((max(int(max_iter), 1), 2))
+    rc = lib().msm_parareal(arr, coarse._h, n, _ptr(pos0), _ptr(vel0), _ptr(inv_mass), _ptr(q), int(window),
+                            float(dt_fine), int(steps_fine), float(dt_coarse), int(steps_coarse), int(max_iter),
+                            float(tol), _ptr(lam_pos), _ptr(lam_vel), _ptr(ws), C.byref(iters),
+                            change.ctypes.data_as(C.c_void_p), _stream(stream))
+    _capi.check(rc, "msm_parareal")
+    for p in fine:
+        p._last_n = n
+    coarse._last_n = None
+    return lam_pos, lam_vel, iters.value, change[:iters.value]
 
 
 class MSMEnergy(torch.autograd.Function):

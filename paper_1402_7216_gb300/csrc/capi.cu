@@ -4,6 +4,7 @@
 // short-range pairs, anterpolation, restriction and lattice cutoff per level,
 // top level, prolongation, interpolation and assembly.  The grid passes may
 // run on a plan-owned stream forked from and joined back onto the caller's.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -207,6 +208,50 @@ int batch_backward(const msm_handle* plans, int nrep, const int64_t* off, const 
   });
 }
 
+// The cutoff method's evaluation (binning, the pair kernel with the Coulomb
+// pair function, assembly): no grid passes.
+int cutoff_forward(Plan& P, int64_t n, const double* pos, const double* q, double* energy, double* phi, double* force,
+                   cudaStream_t st) {
+  P.last_n = -1;  // the per-atom buffers no longer hold an MSM forward pass
+  cudaError_t e = stage(P, MSM_STAGE_BINNING, st, [&] { return launch_binning(P, n, pos, q, st); });
+  if (e == cudaSuccess) e = stage(P, MSM_STAGE_SHORT_RANGE, st, [&] { return launch_cutoff_pairs(P, n, st); });
+  if (e == cudaSuccess)
+    e = stage(P, MSM_STAGE_INTERPOLATION, st, [&] { return launch_cutoff_assemble(P, n, energy, phi, force, st); });
+  if (e != cudaSuccess) return MSM_ERR_CUDA;
+  P.last_stream = st;
+  P.evals += 1;
+  return MSM_OK;
+}
+
+// Energy and force at pos by MSM or by the cutoff method.
+int md_force(Plan& P, int method, int64_t n, const double* pos, const double* q, double* energy, double* force,
+             cudaStream_t st) {
+  if (method == MSM_MD_CUTOFF) return cutoff_forward(P, n, pos, q, energy, nullptr, force, st);
+  return forward(P, n, pos, q, energy, (double*)nullptr, force, st);
+}
+
+// nsteps of velocity Verlet (drift, force, kick); with init_force the force
+// at the starting positions is evaluated first.
+int md_loop(Plan& P, int method, int64_t n, double* pos, double* vel, double* force, const double* inv_mass,
+            const double* q, double dt, int nsteps, bool init_force, double* records, cudaStream_t st) {
+  double* potential = P.d.scalars + 1;  // the step's energy when no record is kept
+  if (init_force) {
+    int rc = md_force(P, method, n, pos, q, potential, force, st);
+    if (rc != MSM_OK) return rc;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    double* rec = records ? records + 6 * (size_t)s : nullptr;
+    double* u = rec ? rec : potential;
+    if (launch_md_drift(P, n, pos, vel, force, inv_mass, dt, st) != cudaSuccess) return MSM_ERR_CUDA;
+    int rc = md_force(P, method, n, pos, q, u, force, st);
+    if (rc != MSM_OK) return rc;
+    if (launch_md_kick(P, n, vel, force, inv_mass, dt, u, rec ? rec : P.d.scalars + 2, st) != cudaSuccess)
+      return MSM_ERR_CUDA;
+  }
+  P.last_stream = st;
+  return MSM_OK;
+}
+
 std::once_flag g_config_once;
 cudaError_t g_config_err = cudaSuccess;
 
@@ -350,36 +395,115 @@ int msm_cutoff_eval(msm_handle h, int64_t n, const double* pos, const double* q,
   if (!h || n < 0 || !energy || (n > 0 && (!pos || !q))) return MSM_ERR_INVALID_ARG;
   Plan& P = h->p;
   if (n > P.cap) return MSM_ERR_TOO_MANY_ATOMS;
-  cudaStream_t st = (cudaStream_t)stream;
-  P.last_n = -1;  // the per-atom buffers no longer hold an MSM forward pass
-  cudaError_t e = stage(P, MSM_STAGE_BINNING, st, [&] { return launch_binning(P, n, pos, q, st); });
-  if (e == cudaSuccess) e = stage(P, MSM_STAGE_SHORT_RANGE, st, [&] { return launch_cutoff_pairs(P, n, st); });
-  if (e == cudaSuccess)
-    e = stage(P, MSM_STAGE_INTERPOLATION, st, [&] { return launch_cutoff_assemble(P, n, energy, phi, force, st); });
-  if (e != cudaSuccess) return MSM_ERR_CUDA;
-  P.last_stream = st;
-  P.evals += 1;
-  return MSM_OK;
+  return cutoff_forward(P, n, pos, q, energy, phi, force, (cudaStream_t)stream);
 }
 
 int msm_md_run(msm_handle h, int64_t n, double* pos, double* vel, double* force, const double* inv_mass,
-               const double* q, double dt, int nsteps, double* records, void* stream) {
+               const double* q, double dt, int nsteps, int method, double* records, void* stream) {
   if (!h || n < 0 || nsteps < 0 || !std::isfinite(dt)) return MSM_ERR_INVALID_ARG;
+  if (method != MSM_MD_MSM && method != MSM_MD_CUTOFF) return MSM_ERR_INVALID_ARG;
   if (n > 0 && (!pos || !vel || !force || !inv_mass || !q)) return MSM_ERR_INVALID_ARG;
   Plan& P = h->p;
   if (n > P.cap) return MSM_ERR_TOO_MANY_ATOMS;
+  return md_loop(P, method, n, pos, vel, force, inv_mass, q, dt, nsteps, false, records, (cudaStream_t)stream);
+}
+
+int msm_md_run_batch(const msm_handle* plans, int nrep, const int64_t* offsets, double* pos, double* vel,
+                     double* force, const double* inv_mass, const double* q, double dt, int nsteps, int method,
+                     double* records, void* stream) {
+  int rc = check_batch(plans, nrep, offsets);
+  if (rc != MSM_OK) return rc;
+  if (nsteps < 0 || !std::isfinite(dt) || (method != MSM_MD_MSM && method != MSM_MD_CUTOFF))
+    return MSM_ERR_INVALID_ARG;
+  if (offsets[nrep] > 0 && (!pos || !vel || !force || !inv_mass || !q)) return MSM_ERR_INVALID_ARG;
+  return fork_join(nrep, (cudaStream_t)stream, [&](int r, cudaStream_t s) {
+    const int64_t o = offsets[r], n = offsets[r + 1] - offsets[r];
+    return md_loop(plans[r]->p, method, n, pos + 3 * o, vel + 3 * o, force + 3 * o, inv_mass + o, q + o, dt, nsteps,
+                   false, records ? records + 6 * (size_t)nsteps * r : nullptr, s);
+  });
+}
+
+int64_t msm_parareal_workspace(int64_t n, int window) {
+  if (n < 0 || window < 1 || window > MSM_PARAREAL_MAX_WINDOW) return -1;
+  return (int64_t)sizeof(double) * (3 * n * (5 * (int64_t)window + 3) + 2 * (int64_t)window);
+}
+
+int msm_parareal(const msm_handle* fine, msm_handle coarse, int64_t n, const double* pos0, const double* vel0,
+                 const double* inv_mass, const double* q, int window, double dt_fine, int steps_fine,
+                 double dt_coarse, int steps_coarse, int max_iter, double tol, double* lam_pos, double* lam_vel,
+                 void* workspace, int* iterations, double* change, void* stream) {
+  if (!fine || !coarse || n < 0 || window < 1 || window > MSM_PARAREAL_MAX_WINDOW) return MSM_ERR_INVALID_ARG;
+  if (!std::isfinite(dt_fine) || !std::isfinite(dt_coarse) || steps_fine < 0 || steps_coarse < 0 || max_iter < 0 ||
+      !(tol >= 0.0) || !std::isfinite(tol))
+    return MSM_ERR_INVALID_ARG;
+  if (!workspace || !lam_pos || !lam_vel || (n > 0 && (!pos0 || !vel0 || !inv_mass || !q))) return MSM_ERR_INVALID_ARG;
+  for (int r = 0; r < window; ++r) {
+    if (!fine[r]) return MSM_ERR_INVALID_ARG;
+    if (n > fine[r]->p.cap) return MSM_ERR_TOO_MANY_ATOMS;
+    for (int s = 0; s < r; ++s)
+      if (fine[s] == fine[r]) return MSM_ERR_INVALID_ARG;  // the fine propagations run concurrently
+  }
+  if (n > coarse->p.cap) return MSM_ERR_TOO_MANY_ATOMS;
+  if (iterations) *iterations = 0;
   cudaStream_t st = (cudaStream_t)stream;
-  double* potential = P.d.scalars + 1;  // the step's energy when no record is kept
-  for (int s = 0; s < nsteps; ++s) {
-    double* rec = records ? records + 6 * (size_t)s : nullptr;
-    double* u = rec ? rec : potential;
-    if (launch_md_drift(P, n, pos, vel, force, inv_mass, dt, st) != cudaSuccess) return MSM_ERR_CUDA;
-    int rc = forward(P, n, (const double*)pos, q, u, (double*)nullptr, force, st);
+  const size_t N3 = 3 * (size_t)n, B3 = sizeof(double) * N3;
+  double* ws = (double*)workspace;
+  double *fpos = ws, *fvel = fpos + window * N3, *gpos = fvel + window * N3, *gvel = gpos + window * N3;
+  double *fforce = gvel + window * N3, *cpos = fforce + window * N3, *cvel = cpos + N3, *cforce = cvel + N3;
+  double* chg = cforce + N3;  // [window][2]
+  Plan& C = coarse->p;
+  auto lp = [&](int k) { return lam_pos + k * N3; };
+  auto lv = [&](int k) { return lam_vel + k * N3; };
+  auto cp = [&](double* dst, const double* src, cudaStream_t s) {
+    return B3 == 0 || cudaMemcpyAsync(dst, src, B3, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+  };
+  // G from time point k: the coarse state (cpos, cvel) after steps_coarse steps of the cutoff method
+  auto coarse_from = [&](int k) {
+    if (!cp(cpos, lp(k), st) || !cp(cvel, lv(k), st)) return (int)MSM_ERR_CUDA;
+    return md_loop(C, MSM_MD_CUTOFF, n, cpos, cvel, cforce, inv_mass, q, dt_coarse, steps_coarse, true, nullptr, st);
+  };
+  // lambda_0 = the initial state; iteration 0 is one coarse sweep
+  if (!cp(lp(0), pos0, st) || !cp(lv(0), vel0, st)) return MSM_ERR_CUDA;
+  for (int k = 0; k < window; ++k) {
+    int rc = coarse_from(k);
     if (rc != MSM_OK) return rc;
-    if (launch_md_kick(P, n, vel, force, inv_mass, dt, u, rec ? rec : P.d.scalars + 2, st) != cudaSuccess)
+    if (!cp(gpos + k * N3, cpos, st) || !cp(gvel + k * N3, cvel, st) || !cp(lp(k + 1), cpos, st) ||
+        !cp(lv(k + 1), cvel, st))
       return MSM_ERR_CUDA;
   }
-  P.last_stream = st;
+  const double span = dt_fine * steps_fine;  // Delta T: velocity changes are weighed by it
+  std::vector<double> h(2 * (size_t)window);
+  for (int it = 0; it < max_iter; ++it) {
+    // F from every time point of the window, concurrently (one plan each)
+    int rc = fork_join(window, st, [&](int r, cudaStream_t s) {
+      if (!cp(fpos + r * N3, lp(r), s) || !cp(fvel + r * N3, lv(r), s)) return (int)MSM_ERR_CUDA;
+      return md_loop(fine[r]->p, MSM_MD_MSM, n, fpos + r * N3, fvel + r * N3, fforce + r * N3, inv_mass, q, dt_fine,
+                     steps_fine, true, nullptr, s);
+    });
+    if (rc != MSM_OK) return rc;
+    // the sequential coarse sweep with the correction
+    for (int k = 0; k < window; ++k) {
+      rc = coarse_from(k);
+      if (rc != MSM_OK) return rc;
+      if (launch_parareal_correct(C, n, cpos, cvel, fpos + k * N3, fvel + k * N3, gpos + k * N3, gvel + k * N3,
+                                  lp(k + 1), lv(k + 1), chg + 2 * k, st) != cudaSuccess)
+        return MSM_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(h.data(), chg, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return MSM_ERR_CUDA;
+    double dr = 0.0, dv = 0.0;
+    for (int k = 0; k < window; ++k) {
+      dr = std::max(dr, h[2 * k]);
+      dv = std::max(dv, h[2 * k + 1]);
+    }
+    if (change) {
+      change[2 * it] = dr;
+      change[2 * it + 1] = dv;
+    }
+    if (iterations) *iterations = it + 1;
+    if (dr <= tol && dv * std::fabs(span) <= tol) break;
+  }
   return MSM_OK;
 }
 

@@ -115,6 +115,97 @@ __global__ void __launch_bounds__(kMdThreads) k_md_record(const double* __restri
   }
 }
 
+// Fixed-order block maximum of two non-negative values (thread 0 returns them).
+__device__ __forceinline__ void block_max2(double v[2]) {
+  __shared__ double red[kMdThreads / 32][2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+    for (int o = 16; o > 0; o >>= 1) v[c] = fmax(v[c], __shfl_down_sync(0xffffffffu, v[c], o));
+  if (lane == 0) {
+    red[w][0] = v[0];
+    red[w][1] = v[1];
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      v[c] = lane < kMdThreads / 32 ? red[lane][c] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v[c] = fmax(v[c], __shfl_down_sync(0xffffffffu, v[c], o));
+    }
+  }
+}
+
+// The parareal correction (Eq. parareal) of one time point:
+//   lambda_{n+1}^{k+1} = G(lambda_n^{k+1}) + F(lambda_n^k) - G(lambda_n^k)
+// for positions and velocities.  In a periodic box the position difference
+// F - G is taken as its minimum image and the result is wrapped into [0, L)
+// (the two propagations may have wrapped an atom differently).  The kernel
+// also keeps G(lambda_n^{k+1}) for the next iteration and records the largest
+// change of the point against its previous iterate (positions, velocities).
+__global__ void __launch_bounds__(kMdThreads) k_parareal_correct(int64_t n, MdBox B, const double* __restrict__ gnew_pos,
+                                                                  const double* __restrict__ gnew_vel,
+                                                                  const double* __restrict__ f_pos,
+                                                                  const double* __restrict__ f_vel,
+                                                                  double* __restrict__ g_pos, double* __restrict__ g_vel,
+                                                                  double* __restrict__ lam_pos,
+                                                                  double* __restrict__ lam_vel,
+                                                                  double* __restrict__ partial) {
+  double ch[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int64_t k = 3 * i + d;
+      double df = f_pos[k] - g_pos[k];
+      if (B.periodic) df -= B.L[d] * rint(df * B.inv_L[d]);
+      double x = gnew_pos[k] + df;
+      if (B.periodic) {
+        x -= B.L[d] * floor(x * B.inv_L[d]);
+        if (x >= B.L[d]) x -= B.L[d];
+        if (x < 0.0) x = 0.0;
+      }
+      double dx = x - lam_pos[k];
+      if (B.periodic) dx -= B.L[d] * rint(dx * B.inv_L[d]);
+      const double v = gnew_vel[k] + (f_vel[k] - g_vel[k]);
+      ch[0] = fmax(ch[0], fabs(dx));
+      ch[1] = fmax(ch[1], fabs(v - lam_vel[k]));
+      lam_pos[k] = x;
+      lam_vel[k] = v;
+      g_pos[k] = gnew_pos[k];
+      g_vel[k] = gnew_vel[k];
+    }
+  }
+  block_max2(ch);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = ch[0];
+    partial[2 * blockIdx.x + 1] = ch[1];
+  }
+}
+
+__global__ void __launch_bounds__(kMdThreads) k_parareal_change(const double* __restrict__ partial, int nb,
+                                                                 double* __restrict__ change) {
+  double ch[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    ch[0] = fmax(ch[0], partial[2 * b]);
+    ch[1] = fmax(ch[1], partial[2 * b + 1]);
+  }
+  block_max2(ch);
+  if (threadIdx.x == 0) {
+    change[0] = ch[0];
+    change[1] = ch[1];
+  }
+}
+
+MdBox md_box(const Plan& P) {
+  MdBox B;
+  for (int d = 0; d < 3; ++d) {
+    B.L[d] = P.P.box[d];
+    B.inv_L[d] = 1.0 / P.P.box[d];
+  }
+  B.periodic = P.P.periodic;
+  return B;
+}
+
 int md_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(kMdBlocks, (n + kMdThreads - 1) / kMdThreads)); }
 
 }  // namespace
@@ -122,13 +213,7 @@ int md_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(kM
 cudaError_t launch_md_drift(Plan& P, int64_t n, double* pos, double* vel, const double* force,
                             const double* inv_mass, double dt, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  MdBox B;
-  for (int d = 0; d < 3; ++d) {
-    B.L[d] = P.P.box[d];
-    B.inv_L[d] = 1.0 / P.P.box[d];
-  }
-  B.periodic = P.P.periodic;
-  k_md_drift<<<md_blocks(n), kMdThreads, 0, st>>>(n, pos, vel, force, inv_mass, dt, B);
+  k_md_drift<<<md_blocks(n), kMdThreads, 0, st>>>(n, pos, vel, force, inv_mass, dt, md_box(P));
   P.launches += 1;
   return cudaGetLastError();
 }
@@ -139,6 +224,20 @@ cudaError_t launch_md_kick(Plan& P, int64_t n, double* vel, const double* force,
   if (n > 0) k_md_kick<<<nb, kMdThreads, 0, st>>>(n, vel, force, inv_mass, dt, P.d.md_partial);
   else cudaMemsetAsync(P.d.md_partial, 0, sizeof(double) * 4, st);
   k_md_record<<<1, kMdThreads, 0, st>>>(P.d.md_partial, nb, potential, record);
+  P.launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_parareal_correct(Plan& P, int64_t n, const double* gnew_pos, const double* gnew_vel,
+                                    const double* f_pos, const double* f_vel, double* g_pos, double* g_vel,
+                                    double* lam_pos, double* lam_vel, double* change, cudaStream_t st) {
+  const int nb = md_blocks(n);
+  if (n > 0)
+    k_parareal_correct<<<nb, kMdThreads, 0, st>>>(n, md_box(P), gnew_pos, gnew_vel, f_pos, f_vel, g_pos, g_vel, lam_pos,
+                                                  lam_vel, P.d.md_partial);
+  else
+    cudaMemsetAsync(P.d.md_partial, 0, sizeof(double) * 2, st);
+  k_parareal_change<<<1, kMdThreads, 0, st>>>(P.d.md_partial, nb, change);
   P.launches += 2;
   return cudaGetLastError();
 }

@@ -257,6 +257,12 @@ cudaError_t launch_md_drift(Plan& P, int64_t n, double* pos, double* vel, const 
                             const double* inv_mass, double dt, cudaStream_t s);
 cudaError_t launch_md_kick(Plan& P, int64_t n, double* vel, const double* force, const double* inv_mass, double dt,
                            const double* potential, double* record, cudaStream_t s);
+// The parareal correction of one time point (uses P's box and MD partials):
+// lam = gnew + (f - g), g = gnew, change[0..1] = largest position and
+// velocity change of lam against its previous value.
+cudaError_t launch_parareal_correct(Plan& P, int64_t n, const double* gnew_pos, const double* gnew_vel,
+                                    const double* f_pos, const double* f_vel, double* g_pos, double* g_vel,
+                                    double* lam_pos, double* lam_vel, double* change, cudaStream_t s);
 
 // Whether the level stencil's window fits the lattice kernel's shared memory
 // (a stencil of half-width E holds about (2 E)^2 window points per plane).

@@ -1,0 +1,143 @@
+"""Parareal (msm_parareal, Eq. parareal) with F = velocity Verlet on the MSM
+force and G = velocity Verlet on the cutoff method, against the oracle's
+parareal; the cutoff method's MD (msm_md_run, method "cutoff") and the
+batched MD (msm_md_run_batch) against single runs.
+
+Tolerances: FP64 plans 1e-9 A / 1e-9 on velocities after two iterations
+(same arithmetic, other summation order); mixed fine plans 1e-5 A."""
+import numpy as np
+import pytest
+import torch
+
+from synth import make_ion_system
+
+pytestmark = pytest.mark.gpu
+
+L, A, H = 16.0, 6.0, 2.0
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def make_plan(n, precision, L=L, periodic=True):
+    from paper_1402_7216_gb300 import MSM
+    return MSM(box=L, periodic=periodic, cutoff=A, spacing=H, order=3, splitting=2, precision=precision,
+               max_atoms=max(n, 1))
+
+
+def oparams(L=L, periodic=True):
+    import oracle as O
+    return O.Params(box=(L,) * 3, periodic=periodic, cutoff=A, spacing=H, order=3, split=2)
+
+
+def dev_tensors(dev, *arrays):
+    return [torch.tensor(a, device=dev) for a in arrays]
+
+
+def min_image(d, L=L):
+    return d - L * np.round(d / L)
+
+
+def system(n=48, seed=31):
+    return make_ion_system(L, n, seed=seed, kind="plasma")
+
+
+def test_md_cutoff_method_matches_oracle(dev):
+    from oracle import cutoff_sum
+    from oracle.md import velocity_verlet
+    pos, q, im, vel = system()
+    P = oparams()
+
+    def force(r):
+        out = cutoff_sum(P, r, q)
+        return out["F"], out["E"]
+    r_o, v_o, _, rec_o = velocity_verlet(force, pos, vel, im, 0.05, 15, wrap=lambda r: r - L * np.floor(r / L))
+    plan = make_plan(len(q), "fp64")
+    tp, tv, ti, tq = dev_tensors(dev, pos, vel, im, q)
+    _, rec = plan.md_run(tp, tv, ti, tq, 0.05, 15, method="cutoff")
+    torch.cuda.synchronize()
+    assert np.abs(min_image(tp.cpu().numpy() - r_o)).max() < 1e-10
+    assert np.abs(tv.cpu().numpy() - v_o).max() < 1e-10
+    np.testing.assert_allclose(rec.cpu().numpy()[:, :3], rec_o[:, :3], rtol=1e-10)
+
+
+def test_md_batch_matches_single_runs(dev):
+    """Three systems of different sizes stepped together equal each stepped
+    alone (FP64: same kernels, summation order aside)."""
+    from paper_1402_7216_gb300 import MSMBatch
+    systems = [system(n, seed) for n, seed in ((30, 41), (48, 42), (64, 43))]
+    single = []
+    for pos, q, im, vel in systems:
+        plan = make_plan(len(q), "fp64")
+        tp, tv, ti, tq = dev_tensors(dev, pos, vel, im, q)
+        _, rec = plan.md_run(tp, tv, ti, tq, 0.05, 8)
+        single.append((tp.cpu().numpy(), tv.cpu().numpy(), rec.cpu().numpy()))
+    plans = [make_plan(len(s[1]), "fp64") for s in systems]
+    cat = [np.concatenate([s[i] for s in systems]) for i in range(4)]
+    tp, tq, ti, tv = dev_tensors(dev, cat[0], cat[1], cat[2], cat[3])
+    counts = [len(s[1]) for s in systems]
+    B = MSMBatch(plans)
+    _, _, F = B.eval(tp, tq, counts, want_phi=False)
+    rec = B.md_run(tp, tv, F, ti, tq, counts, 0.05, 8)
+    torch.cuda.synchronize()
+    off = np.cumsum([0] + counts)
+    for r, (p1, v1, rec1) in enumerate(single):
+        assert np.abs(min_image(tp.cpu().numpy()[off[r]:off[r + 1]] - p1)).max() < 1e-11
+        assert np.abs(tv.cpu().numpy()[off[r]:off[r + 1]] - v1).max() < 1e-11
+        np.testing.assert_allclose(rec.cpu().numpy()[r], rec1, rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_parareal_matches_oracle(precision, dev):
+    from paper_1402_7216_gb300 import parareal
+    from oracle.parareal import md_parareal
+    pos, q, im, vel = system()
+    W, dtf, sf, dtc, sc = 4, 0.05, 5, 0.125, 2
+    lam_o, hist_o, ch_o = md_parareal(oparams(), oparams(), pos, vel, im, q, W, dtf, sf, dtc, sc, 2, 0.0)
+    fine = [make_plan(len(q), precision) for _ in range(W)]
+    coarse = make_plan(len(q), "fp64")
+    tp, tv, ti, tq = dev_tensors(dev, pos, vel, im, q)
+    lp, lv, iters, ch = parareal(fine, coarse, tp, tv, ti, tq, W, dtf, sf, dtc, sc, 2, 0.0)
+    assert iters == 2
+    tol = 1e-9 if precision == "fp64" else 1e-5
+    for k in range(W + 1):
+        assert np.abs(min_image(lp[k].cpu().numpy() - lam_o[k][0])).max() < tol
+        assert np.abs(lv[k].cpu().numpy() - lam_o[k][1]).max() < tol * 10
+    np.testing.assert_allclose(ch, np.array(ch_o), rtol=1e-3 if precision == "fp64" else 2e-2)
+
+
+def test_parareal_converges_to_the_sequential_fine_run(dev):
+    from paper_1402_7216_gb300 import parareal
+    pos, q, im, vel = system(60, 33)
+    W, dtf, sf = 5, 0.05, 4
+    fine = [make_plan(len(q), "fp64") for _ in range(W)]
+    tp, tv, ti, tq = dev_tensors(dev, pos, vel, im, q)
+    lp, lv, iters, ch = parareal(fine, fine[0], tp, tv, ti, tq, W, dtf, sf, 0.1, 2, 20, 1e-9)
+    assert iters <= W + 1
+    assert ch[-1][0] <= 1e-9
+    seq = make_plan(len(q), "fp64")
+    sp, sv, si, sq = dev_tensors(dev, pos, vel, im, q)
+    for k in range(1, W + 1):
+        seq.md_run(sp, sv, si, sq, dtf, sf)      # F from the new positions (its own first force)
+        assert np.abs(min_image(lp[k].cpu().numpy() - sp.cpu().numpy())).max() < 1e-8
+        assert np.abs(lv[k].cpu().numpy() - sv.cpu().numpy()).max() < 1e-8
+
+
+def test_parareal_argument_errors(dev):
+    from paper_1402_7216_gb300 import MSMError, parareal
+    pos, q, im, vel = system(20, 34)
+    tp, tv, ti, tq = dev_tensors(dev, pos, vel, im, q)
+    a = make_plan(len(q), "mixed")
+    with pytest.raises(MSMError) as e:
+        parareal([a, a], a, tp, tv, ti, tq, 2, 0.05, 2, 0.1, 1, 1, 0.0)    # one plan twice in the window
+    assert e.value.code == -1
+    small = make_plan(8, "mixed")
+    with pytest.raises(MSMError) as e:
+        parareal([a], small, tp, tv, ti, tq, 1, 0.05, 2, 0.1, 1, 1, 0.0)   # coarse plan too small
+    assert e.value.code == -9
+    with pytest.raises(ValueError):
+        parareal([a], a, tp, tv, ti, tq, 2, 0.05, 2, 0.1, 1, 1, 0.0)       # one plan per time point

@@ -103,3 +103,50 @@ def test_md_msm_energy_fluctuation_scales_as_dt2(oracle):
         spread.append(np.abs(E - E[0]).max() / rec[:, 1].mean())
     assert spread[0] < 1e-4
     assert 3.0 < spread[0] / spread[1] < 5.5
+
+
+# ------------------------------------------------------------- parareal ----
+def test_parareal_linear_closed_form(oracle):
+    """Linear propagators F(y) = f y, G(y) = g y: iterate k of the parareal
+    recursion is lambda_n^k = sum_{j <= min(k, n)} C(n, j) (f - g)^j g^(n-j)
+    y0 (the binomial expansion of (g + (f - g))^n truncated at order k), so
+    iterate k is exact for n <= k."""
+    from math import comb
+    from oracle.parareal import parareal
+    f, g, y0, W = 0.93, 0.71, 1.7, 7
+    lam, hist, ch = parareal(lambda y: f * y, lambda y: g * y, lambda gn, fo, go: gn + fo - go,
+                             lambda new, old: max(abs(a - b) for a, b in zip(new, old)), lambda c: False,
+                             y0, W, W + 1)
+    assert len(hist) == W + 2
+    for k, it in enumerate(hist):
+        for n in range(W + 1):
+            want = y0 * sum(comb(n, j) * (f - g) ** j * g ** (n - j) for j in range(min(k, n) + 1))
+            assert it[n] == pytest.approx(want, rel=1e-13)
+        for n in range(min(k, W) + 1):
+            assert it[n] == pytest.approx(y0 * f ** n, rel=1e-13)      # exact up to point k
+    assert ch[-1] == pytest.approx(0.0, abs=1e-15)        # iterate W + 1 repeats iterate W
+
+
+def test_md_parareal_reaches_the_sequential_fine_trajectory(oracle):
+    """After `window` iterations every time point equals the sequential fine
+    propagation (velocity Verlet on the MSM force) from the start; the
+    iterations before are exact up to their own index."""
+    from oracle.md import md_run
+    from oracle.parareal import md_parareal
+    P = oracle.Params(box=(16.0,) * 3, periodic=True, cutoff=6.0, spacing=2.0, order=3, split=2)
+    pos, q, im, vel = small_plasma()
+    W, dtf, sf = 3, 0.05, 4
+    lam, hist, ch = md_parareal(P, P, pos, vel, im, q, W, dtf, sf, 0.1, 2, W, 0.0)
+    r, v = pos, vel
+    for n in range(1, W + 1):
+        r, v, _, _ = md_run(P, r, v, im, q, dtf, sf)
+        d = lam[n][0] - r
+        d -= 16.0 * np.round(d / 16.0)
+        assert np.abs(d).max() < 1e-11
+        np.testing.assert_allclose(lam[n][1], v, atol=1e-11)
+        # iterate 0 (coarse only) is already off at n = 1; iterate n is exact at n
+        d0 = hist[0][n][0] - r
+        assert np.abs(d0 - 16.0 * np.round(d0 / 16.0)).max() > 1e-6
+        dn = hist[n][n][0] - r
+        assert np.abs(dn - 16.0 * np.round(dn / 16.0)).max() < 1e-11
+    assert ch[0][0] > ch[-1][0]
