@@ -350,6 +350,62 @@ def md_timing(args, plan, pos, q, n, stream, f_ms):
             "integrator_overhead_ms": ms - f_ms, "records_finite": bool(torch.isfinite(rec).all().item())}
 
 
+def parareal_window_timing(coarse_method="cutoff", coarse_cutoff=10.0, window=8, steps_fine=10, dt_fine=0.05,
+                           steps_coarse=2, dt_coarse=0.25, tol=1e-4):
+    """One parareal window (msm_parareal) on a 23,558-ion one-component
+    plasma in the 62.2 A periodic box of the 23,558-atom configuration (a =
+    10 A, h = 2 A, cubic, mixed precision; unit masses, kT = 0.05 in
+    e^2/A): its wall time against the sequential fine run over the same
+    time span, the iterations it needs to tol and each iteration's change.
+    The fine propagations of a window run concurrently, one plan each."""
+    import torch
+    from paper_1402_7216_gb300 import MSM, parareal
+    from synth import make_ion_system
+    L, n = 62.2, 23558
+    pos, q, im, vel = make_ion_system(L, n, seed=61, kind="plasma", dmin=2.0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tp, tv, ti, tq = (torch.tensor(a, device=dev) for a in (pos, vel, im, q))
+
+    def mk():
+        return MSM(box=L, periodic=True, cutoff=10.0, spacing=2.0, order=3, splitting=2, precision="mixed",
+                   max_atoms=n)
+    fine = [mk() for _ in range(window)]
+    coarse = MSM(box=L, periodic=True, cutoff=coarse_cutoff, spacing=2.0, order=3, splitting=2, precision="mixed",
+                 max_atoms=n)
+    stream = torch.cuda.current_stream()
+    # sequential fine run over window * steps_fine steps
+    sp, sv = tp.clone(), tv.clone()
+    fine[0].md_run(tp.clone(), tv.clone(), ti, tq, dt_fine, 2)   # warm-up
+    F, _ = fine[0].md_run(sp, sv, ti, tq, dt_fine, 0)            # the force at the start
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fine[0].md_run(sp, sv, ti, tq, dt_fine, window * steps_fine, force=F, records=False)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_seq = a.elapsed_time(b)
+    parareal(fine, coarse, tp, tv, ti, tq, window, dt_fine, steps_fine, dt_coarse, steps_coarse, 1, 0.0,
+             coarse_method=coarse_method)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lp, lv, iters, ch = parareal(fine, coarse, tp, tv, ti, tq, window, dt_fine, steps_fine, dt_coarse,
+                                 steps_coarse, window, tol, coarse_method=coarse_method)
+    t_par = 1e3 * (time.perf_counter() - t0)
+    d = lp[window] - sp
+    err = float((d - L * torch.round(d / L)).abs().max())
+    for p in fine + [coarse]:
+        p.close()
+    return {"workload": "plasma23k: 23,558 ions (+1 e, unit mass) in the 62.2 A periodic box, a=10, h=2, cubic, "
+                        "mixed; kT=0.05 e^2/A",
+            "window": window, "fine": "%d steps x dt %g (MSM)" % (steps_fine, dt_fine),
+            "coarse": "%d steps x dt %g (%s, a=%g A)" % (steps_coarse, dt_coarse, "cutoff method" if coarse_method ==
+                                                         "cutoff" else "MSM", coarse_cutoff),
+            "tol_A": tol, "iterations": iters, "change_per_iteration": [[float(x) for x in c] for c in ch],
+            "ms_parareal": t_par, "ms_sequential_fine": t_seq, "speedup": t_seq / t_par,
+            "final_point_vs_sequential_A": err,
+            "timing": "parareal: host wall clock of the synchronous call; sequential: CUDA events"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,6 +501,9 @@ def main():
         cutoff_G, msm_G = parareal_timings(args, w, plan, pos, q, n, dev, stream, flush, f_ms, E_mix, F_mix)
     if not args.no_md:
         md = md_timing(args, plan, pos, q, n, stream, f_ms)
+    pr_window = None
+    if not args.no_parareal:
+        pr_window = [parareal_window_timing("cutoff", 10.0), parareal_window_timing("msm", 5.0)]
 
     # end to end through the host-buffer entry point (pinned host memory)
     pos_pin = torch.tensor(pos_h).pin_memory()
@@ -549,6 +608,7 @@ def main():
         "parareal_G_cutoff": cutoff_G,
         "parareal_G_msm": msm_G,
         "md_velocity_verlet": md,
+        "parareal_window": pr_window,
         "clocks": clk,
         "energy": E_mix,
     }

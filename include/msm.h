@@ -180,9 +180,11 @@ int msm_md_run_batch(const msm_handle* plans, int nrep, const int64_t* offsets, 
  * the fine propagator F is steps_fine velocity Verlet steps of dt_fine with
  * the MSM force (fine[k] evaluates the propagation from T_k; the window's
  * propagations run concurrently, one plan each), the coarse propagator G
- * steps_coarse steps of dt_coarse with the cutoff method (plan coarse, which
- * may be one of fine[]); each propagation starts by evaluating the force at
- * its starting positions.  Iteration 0 is the coarse sweep lambda_{k+1} =
+ * steps_coarse steps of dt_coarse with the force coarse_method of plan
+ * coarse (MSM_MD_CUTOFF: the cutoff method, the section's "Cutoff Method";
+ * MSM_MD_MSM: MSM with the coarse plan's own cutoff and grid, the "shorter
+ * cutoff" and "coarse grid" options); coarse may be one of fine[].  Each
+ * propagation starts by evaluating the force at its starting positions.  Iteration 0 is the coarse sweep lambda_{k+1} =
  * G(lambda_k); each further iteration computes F(lambda_k) for every k, then
  * sweeps lambda_{k+1} = G(lambda_k new) + F(lambda_k old) - G(lambda_k old),
  * positions through the minimum image of F - G and wrapped when periodic.
@@ -196,13 +198,14 @@ int msm_md_run_batch(const msm_handle* plans, int nrep, const int64_t* offsets, 
  *   change     host double [max_iter][2] or NULL: per iteration the largest
  *              position change (A) and velocity change.
  * Synchronous: reads the change back after each iteration.  window is 1 to
- * MSM_PARAREAL_MAX_WINDOW.  Errors: INVALID_ARG, TOO_MANY_ATOMS, CUDA. */
+ * MSM_PARAREAL_MAX_WINDOW.  Errors: INVALID_ARG (also an unknown coarse_method),
+ * TOO_MANY_ATOMS, CUDA. */
 #define MSM_PARAREAL_MAX_WINDOW 64
 int64_t msm_parareal_workspace(int64_t n, int window);
 int msm_parareal(const msm_handle* fine, msm_handle coarse, int64_t n, const double* pos0, const double* vel0,
                  const double* inv_mass, const double* q, int window, double dt_fine, int steps_fine,
-                 double dt_coarse, int steps_coarse, int max_iter, double tol, double* lam_pos, double* lam_vel,
-                 void* workspace, int* iterations, double* change, void* cuda_stream);
+                 double dt_coarse, int steps_coarse, int coarse_method, int max_iter, double tol, double* lam_pos,
+                 double* lam_vel, void* workspace, int* iterations, double* change, void* cuda_stream);
 
 /* Adjoint of the last msm_eval on this plan: given the upstream gradient
  * grad_energy = dL/dE ([1] double, device), writes grad_pos = dL/dr ([n][3])

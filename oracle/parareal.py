@@ -12,7 +12,7 @@ from lambda_0 (fixed).  ``parareal`` is the generic driver (any state type
 with the given combine and change rules); ``md_parareal`` instantiates it for
 molecular dynamics with F = velocity Verlet on the oracle's MSM force and G =
 velocity Verlet on the cutoff method's force (the parareal section's
-simplest coarse propagator).
+simplest coarse propagator) or on MSM with coarser parameters.
 """
 import numpy as np
 
@@ -49,7 +49,7 @@ def parareal(fine, coarse, combine, change, converged, lam0, window, max_iter):
 
 
 def md_parareal(P_fine, P_coarse, pos0, vel0, inv_mass, q, window, dt_fine, steps_fine, dt_coarse, steps_coarse,
-                max_iter, tol):
+                max_iter, tol, coarse_method="cutoff"):
     """Parareal MD: states (r, v); positions combined through the minimum
     image of F - G and wrapped when periodic; an iteration has converged
     when no position moved more than tol and no velocity more than
@@ -72,7 +72,10 @@ def md_parareal(P_fine, P_coarse, pos0, vel0, inv_mass, q, window, dt_fine, step
     wrap = (lambda r: r - box * np.floor(r / box)) if periodic else None
 
     def coarse(state):
-        r, v, _, _ = velocity_verlet(cutoff_force, state[0], state[1], im, dt_coarse, steps_coarse, wrap=wrap)
+        if coarse_method == "msm":   # MSM with the coarse parameters (shorter cutoff, coarser grid)
+            r, v, _, _ = md_run(P_coarse, state[0], state[1], im, q, dt_coarse, steps_coarse)
+        else:
+            r, v, _, _ = velocity_verlet(cutoff_force, state[0], state[1], im, dt_coarse, steps_coarse, wrap=wrap)
         return (r, v)
 
     def min_image(d):

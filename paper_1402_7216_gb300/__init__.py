@@ -343,11 +343,12 @@ class BatchGraph:
 
 
 def parareal(fine, coarse, pos0, vel0, inv_mass, q, window, dt_fine, steps_fine, dt_coarse, steps_coarse,
-             max_iter, tol, stream=None):
+             max_iter, tol, stream=None, coarse_method="cutoff"):
     """msm_parareal: one parareal window (Eq. parareal) with F = steps_fine
     velocity Verlet steps of dt_fine on the MSM force (fine: `window`
     distinct plans, run concurrently) and G = steps_coarse steps of dt_coarse
-    on the cutoff method (plan coarse).  Returns (lam_pos [window+1, N, 3],
+    on plan coarse's cutoff method (coarse_method "cutoff") or its MSM
+    ("msm").  Returns (lam_pos [window+1, N, 3],
     lam_vel [window+1, N, 3], iterations, change [iterations, 2]) with the
     largest position and velocity change of each iteration."""
     import numpy as np
@@ -370,7 +371,8 @@ def parareal(fine, coarse, pos0, vel0, inv_mass, q, window, dt_fine, steps_fine,
     iters = C.c_int(0)
     change = np.zeros((max(int(max_iter), 1), 2))
     rc = lib().msm_parareal(arr, coarse._h, n, _ptr(pos0), _ptr(vel0), _ptr(inv_mass), _ptr(q), int(window),
-                            float(dt_fine), int(steps_fine), float(dt_coarse), int(steps_coarse), int(max_iter),
+                            float(dt_fine), int(steps_fine), float(dt_coarse), int(steps_coarse),
+                            MD_METHODS[coarse_method], int(max_iter),
                             float(tol), _ptr(lam_pos), _ptr(lam_vel), _ptr(ws), C.byref(iters),
                             change.ctypes.data_as(C.c_void_p), _stream(stream))
     _capi.check(rc, "msm_parareal")

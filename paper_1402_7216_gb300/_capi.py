@@ -77,7 +77,7 @@ def load(path=LIB_PATH):
     L.msm_parareal_workspace.argtypes = [C.c_int64, C.c_int]
     L.msm_parareal_workspace.restype = C.c_int64
     L.msm_parareal.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int, C.c_double, C.c_int, C.c_double, C.c_int,
-                               C.c_int, C.c_double, vp, vp, vp, vp, vp, vp]
+                               C.c_int, C.c_int, C.c_double, vp, vp, vp, vp, vp, vp]
     L.msm_parareal.restype = C.c_int
     L.msm_eval_backward.argtypes = [vp, vp, vp, vp, vp]
     L.msm_eval_backward.restype = C.c_int

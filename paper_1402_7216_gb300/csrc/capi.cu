@@ -430,9 +430,10 @@ int64_t msm_parareal_workspace(int64_t n, int window) {
 
 int msm_parareal(const msm_handle* fine, msm_handle coarse, int64_t n, const double* pos0, const double* vel0,
                  const double* inv_mass, const double* q, int window, double dt_fine, int steps_fine,
-                 double dt_coarse, int steps_coarse, int max_iter, double tol, double* lam_pos, double* lam_vel,
-                 void* workspace, int* iterations, double* change, void* stream) {
+                 double dt_coarse, int steps_coarse, int coarse_method, int max_iter, double tol, double* lam_pos,
+                 double* lam_vel, void* workspace, int* iterations, double* change, void* stream) {
   if (!fine || !coarse || n < 0 || window < 1 || window > MSM_PARAREAL_MAX_WINDOW) return MSM_ERR_INVALID_ARG;
+  if (coarse_method != MSM_MD_MSM && coarse_method != MSM_MD_CUTOFF) return MSM_ERR_INVALID_ARG;
   if (!std::isfinite(dt_fine) || !std::isfinite(dt_coarse) || steps_fine < 0 || steps_coarse < 0 || max_iter < 0 ||
       !(tol >= 0.0) || !std::isfinite(tol))
     return MSM_ERR_INVALID_ARG;
@@ -457,10 +458,10 @@ int msm_parareal(const msm_handle* fine, msm_handle coarse, int64_t n, const dou
   auto cp = [&](double* dst, const double* src, cudaStream_t s) {
     return B3 == 0 || cudaMemcpyAsync(dst, src, B3, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
   };
-  // G from time point k: the coarse state (cpos, cvel) after steps_coarse steps of the cutoff method
+  // G from time point k: the coarse state (cpos, cvel) after steps_coarse steps
   auto coarse_from = [&](int k) {
     if (!cp(cpos, lp(k), st) || !cp(cvel, lv(k), st)) return (int)MSM_ERR_CUDA;
-    return md_loop(C, MSM_MD_CUTOFF, n, cpos, cvel, cforce, inv_mass, q, dt_coarse, steps_coarse, true, nullptr, st);
+    return md_loop(C, coarse_method, n, cpos, cvel, cforce, inv_mass, q, dt_coarse, steps_coarse, true, nullptr, st);
   };
   // lambda_0 = the initial state; iteration 0 is one coarse sweep
   if (!cp(lp(0), pos0, st) || !cp(lv(0), vel0, st)) return MSM_ERR_CUDA;

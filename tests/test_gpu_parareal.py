@@ -23,15 +23,15 @@ def dev():
     return torch.device("cuda:0")
 
 
-def make_plan(n, precision, L=L, periodic=True):
+def make_plan(n, precision, L=L, periodic=True, cutoff=A):
     from paper_1402_7216_gb300 import MSM
-    return MSM(box=L, periodic=periodic, cutoff=A, spacing=H, order=3, splitting=2, precision=precision,
+    return MSM(box=L, periodic=periodic, cutoff=cutoff, spacing=H, order=3, splitting=2, precision=precision,
                max_atoms=max(n, 1))
 
 
-def oparams(L=L, periodic=True):
+def oparams(L=L, periodic=True, cutoff=A):
     import oracle as O
-    return O.Params(box=(L,) * 3, periodic=periodic, cutoff=A, spacing=H, order=3, split=2)
+    return O.Params(box=(L,) * 3, periodic=periodic, cutoff=cutoff, spacing=H, order=3, split=2)
 
 
 def dev_tensors(dev, *arrays):
@@ -91,17 +91,21 @@ def test_md_batch_matches_single_runs(dev):
         np.testing.assert_allclose(rec.cpu().numpy()[r], rec1, rtol=1e-11, atol=1e-12)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_parareal_matches_oracle(precision, dev):
+@pytest.mark.parametrize("precision,coarse_method", [("fp64", "cutoff"), ("mixed", "cutoff"), ("fp64", "msm")])
+def test_parareal_matches_oracle(precision, coarse_method, dev):
+    """G = the cutoff method (a = 6 A) or MSM with half the cutoff (a = 3 A)."""
     from paper_1402_7216_gb300 import parareal
     from oracle.parareal import md_parareal
     pos, q, im, vel = system()
     W, dtf, sf, dtc, sc = 4, 0.05, 5, 0.125, 2
-    lam_o, hist_o, ch_o = md_parareal(oparams(), oparams(), pos, vel, im, q, W, dtf, sf, dtc, sc, 2, 0.0)
+    ac = A if coarse_method == "cutoff" else A / 2
+    lam_o, hist_o, ch_o = md_parareal(oparams(), oparams(cutoff=ac), pos, vel, im, q, W, dtf, sf, dtc, sc, 2, 0.0,
+                                      coarse_method=coarse_method)
     fine = [make_plan(len(q), precision) for _ in range(W)]
-    coarse = make_plan(len(q), "fp64")
+    coarse = make_plan(len(q), "fp64", cutoff=ac)
     tp, tv, ti, tq = dev_tensors(dev, pos, vel, im, q)
-    lp, lv, iters, ch = parareal(fine, coarse, tp, tv, ti, tq, W, dtf, sf, dtc, sc, 2, 0.0)
+    lp, lv, iters, ch = parareal(fine, coarse, tp, tv, ti, tq, W, dtf, sf, dtc, sc, 2, 0.0,
+                                 coarse_method=coarse_method)
     assert iters == 2
     tol = 1e-9 if precision == "fp64" else 1e-5
     for k in range(W + 1):
