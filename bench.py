@@ -193,12 +193,22 @@ def cpu_baseline(w, budget_s=30.0):
 
 
 def bench_batch(dev, args, n_rep=64):
+    """The 64-replica batch; under torchrun each rank takes its share of the
+    replicas (balanced by atoms, no collective on the data path) and the
+    job's time per batch is the slowest rank's."""
     import numpy as np
     import torch
+    import torch.distributed as dist
     from paper_1402_7216_gb300 import MSM, MSMBatch
+    from paper_1402_7216_gb300.shard import max_over_ranks, shard_replicas
     from synth import replica_boxes
     from paper_1402_7216_gb300.autotune import autotune_batch
-    reps = replica_boxes(n_rep)
+    reps_all = replica_boxes(n_rep)
+    world = dist.get_world_size() if dist.is_initialized() else 1
+    rank = dist.get_rank() if dist.is_initialized() else 0
+    mine = shard_replicas([len(q) for (_, _, q) in reps_all], world)[rank]
+    reps = [reps_all[i] for i in mine]
+    n_rep_all, n_rep = n_rep, len(reps)
     counts = [len(q) for (_, _, q) in reps]
     n = sum(counts)
     pos = torch.tensor(np.vstack([p for (_, p, _) in reps]), device=dev)
@@ -223,12 +233,17 @@ def bench_batch(dev, args, n_rep=64):
     torch.cuda.synchronize()
     steps = max(5, args.steps // 5)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
     for a, b in ev:
         flush.fill_(1.0)
         a.record(stream)
         graph.launch()
         b.record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
     # the same work as separate calls on one stream (no graph, no fork)
     seq = []
@@ -248,10 +263,12 @@ def bench_batch(dev, args, n_rep=64):
     for p in plans:
         p.check_status()
     graph.close()
-    t = sum(ms) / len(ms)
+    t = max_over_ranks(sum(ms) / len(ms), device=dev)
     return {"metric": "replica energy+force+adjoint evaluations per second (one graph launch = all replicas)",
-            "value": n_rep / (t * 1e-3), "unit": "replica-evals/s", "replicas": n_rep, "atoms_total": n,
-            "atoms_min": min(counts), "atoms_max": max(counts), "ms_per_batch": t, "steps": steps,
+            "value": n_rep_all / (t * 1e-3), "unit": "replica-evals/s", "replicas": n_rep_all,
+            "replicas_per_rank": n_rep, "atoms_total": sum(len(q) for (_, _, q) in reps_all),
+            "atoms_min": min(len(q) for (_, _, q) in reps_all), "atoms_max": max(len(q) for (_, _, q) in reps_all),
+            "ms_per_batch": t, "steps": steps,
             "ms_per_batch_sequential_calls": min(seq), "tuning": tuning,
             "autotune_ms": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in tune_ms.items()},
             "config": "periodic water boxes at 0.1 atoms/A^3, a=10, h=2.0, cubic, C2, mixed precision, "
