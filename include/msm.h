@@ -349,6 +349,14 @@ const char* msm_stage_name(int stage);
  * Errors: INVALID_ARG, TOO_MANY_ATOMS, CUDA. */
 int msm_energy_noalloc(int64_t n, const double* q, const double* phi, double* energy, void* cuda_stream);
 
+/* FP32 fused multiply-add throughput probe (for roofline denominators):
+ * blocks x 256 threads each run iters iterations of 16 independent FMAs,
+ * as 8 packed two-lane FMAs (packed != 0) or 16 scalar ones, and write one
+ * float each to out [blocks * 256] (device), so that FLOP = blocks * 256 *
+ * iters * 32 per launch.  Asynchronous; time it with events on the stream.
+ * Errors: INVALID_ARG, CUDA. */
+int msm_fma_probe(int packed, int64_t iters, int blocks, float* out, void* cuda_stream);
+
 /* Human-readable name of an MSM_ERR_* code. */
 const char* msm_strerror(int code);
 

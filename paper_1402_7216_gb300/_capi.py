@@ -39,7 +39,7 @@ class MSMError(RuntimeError):
 _lib = None
 _D = C.POINTER(C.c_double)
 EXPORTS = ["msm_create", "msm_create_tuned", "msm_destroy", "msm_query", "msm_eval", "msm_cutoff_eval", "msm_md_run", "msm_md_run_batch",
-           "msm_parareal_workspace", "msm_parareal",
+           "msm_parareal_workspace", "msm_parareal", "msm_fma_probe",
            "msm_eval_backward",
            "msm_eval_f32io", "msm_eval_backward_f32io",
            "msm_eval_host", "msm_status", "msm_debug_grid", "msm_set_overlap", "msm_profile", "msm_profile_read",
@@ -79,6 +79,8 @@ def load(path=LIB_PATH):
     L.msm_parareal.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int, C.c_double, C.c_int, C.c_double, C.c_int,
                                C.c_int, C.c_int, C.c_double, vp, vp, vp, vp, vp, vp]
     L.msm_parareal.restype = C.c_int
+    L.msm_fma_probe.argtypes = [C.c_int, C.c_int64, C.c_int, vp, vp]
+    L.msm_fma_probe.restype = C.c_int
     L.msm_eval_backward.argtypes = [vp, vp, vp, vp, vp]
     L.msm_eval_backward.restype = C.c_int
     L.msm_eval_f32io.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp]
