@@ -69,6 +69,9 @@ SMALL = [
     dict(name="open-cubic-C2", box=24.0, periodic=False, cutoff=8.0, spacing=2.0, order=3, split=2),
     dict(name="open-quintic-C1", box=24.0, periodic=False, cutoff=7.0, spacing=1.7, order=5, split=1),
     dict(name="open-cubic-C3-l1", box=24.0, periodic=False, cutoff=6.0, spacing=2.0, order=3, split=3, levels=1),
+    # 2a/h >= 13, as on the 4.1M-atom box: wide stencils, few grid points per tile
+    dict(name="per-quintic-wide", box=30.0, periodic=True, cutoff=10.0, spacing=1.5, order=5, split=2),
+    dict(name="open-cubic-wide", box=24.0, periodic=False, cutoff=8.0, spacing=1.2, order=3, split=2),
 ]
 
 
