@@ -77,8 +77,11 @@ typedef struct {
  *   cell_fill     target atoms per short-range cell at the plan's capacity
  *                 density (default 24; cells are at least a/2 wide)
  *   patch_cells   short-range cells per side of the shared-memory patch blocks
- *                 of anterpolation and interpolation (default: the largest of
- *                 4, 3, 2, 1 whose patch fits)
+ *                 of anterpolation and interpolation (default: 4, lowered to
+ *                 3 or 2 on a mixed-precision plan evaluated alone while fewer
+ *                 than 152 patch blocks cover its box, and lower still where
+ *                 the patch would not fit shared memory; batched launches
+ *                 keep the largest patch that fits)
  *   lattice_waves blocks per SM the lattice cutoff aims for when it splits the
  *                 stencil planes of a small level over several blocks (default 8)
  * Ranges: cell_fill 0..256, patch_cells 0..4, lattice_waves 0..64; anything

@@ -1300,14 +1300,16 @@ unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
 
-AnterpArgs patch_args(const Plan& P) {
+// batch: the patch of the batched launches (replicas fill the GPU together,
+// so they keep the larger patch that a small system alone gives up)
+AnterpArgs patch_args(const Plan& P, bool batch = false) {
   AnterpArgs A;
   for (int d = 0; d < 3; ++d) {
     A.nc[d] = P.nc[d];
     A.cw_h[d] = P.cw[d] / P.h[d];
   }
-  A.B = P.ablk;
-  A.pd = P.apd;
+  A.B = batch ? P.ablk_batch : P.ablk;
+  A.pd = batch ? P.apd_batch : P.apd;
   return A;
 }
 
@@ -1548,13 +1550,13 @@ cudaError_t launch_top(Plan& P, const void* qt, void* ut, cudaStream_t st) {
 // Interpolation arguments of plan P (forward: grid u^0; backward: the adjoint grid).
 template <typename T, typename OUT>
 InterpKArgs<T, OUT> interp_kargs(Plan& P, bool backward, OUT* phi, OUT* force, const double* gE, OUT* grad_pos,
-                                 OUT* grad_q, double* partial) {
+                                 OUT* grad_q, double* partial, bool batch = false) {
   InterpKArgs<T, OUT> K;
   K.gfrac = (const R4<T>*)P.d.gfrac;
   K.gbase = P.d.gbase;
   K.perm = P.d.perm;
   K.cell_start = P.d.cell_start;
-  K.AA = patch_args(P);
+  K.AA = patch_args(P, batch);
   K.u0 = (const T*)(backward ? P.d.au[0] : P.d.gu[0]);
   K.G = dims_of(P, 0);
   K.A = assemble_args(P);
@@ -1913,7 +1915,7 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
       a.gfrac = (const R4<float>*)P.d.gfrac;
       a.gbase = P.d.gbase;
       a.cell_start = P.d.cell_start;
-      a.A = patch_args(P);
+      a.A = patch_args(P, true);
       a.G = dims_of(P, 0);
       a.gfx = (unsigned long long*)P.d.tmp[0];
       a.nbx = (int)blocks_for(P.nc[0], a.A.B);
@@ -2086,8 +2088,10 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
       size_t sm = 0;
       for (const BatchRep& r : reps) {
         Plan& P = *r.plan;
-        auto K = dir ? interp_kargs<float, double>(P, true, nullptr, nullptr, r.grad_energy, r.grad_pos, r.grad_q, nullptr)
-                     : interp_kargs<float, double>(P, false, r.phi, r.force, nullptr, nullptr, nullptr, P.d.partial);
+        auto K = dir ? interp_kargs<float, double>(P, true, nullptr, nullptr, r.grad_energy, r.grad_pos, r.grad_q,
+                                                   nullptr, true)
+                     : interp_kargs<float, double>(P, false, r.phi, r.force, nullptr, nullptr, nullptr, P.d.partial,
+                                                   true);
         const int nb = K.nbx * K.nby * (int)blocks_for(P.nc[2], K.AA.B);
         ia.push_back(K);
         ib.push_back(r.n > 0 ? nb : 0);

@@ -107,6 +107,7 @@ struct Plan {
   int nrows = 0;
   // anterpolation patches: blocks of ablk^3 cells, patches of apd^3 points
   int ablk = 1, apd = 1;
+  int ablk_batch = 1, apd_batch = 1;  // the same for the batched launches (at least as large)
   // lattice: blocks per SM to aim for when splitting a small level's planes
   int lattice_waves = 8;
   // smoothing constants
