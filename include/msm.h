@@ -271,11 +271,14 @@ int msm_eval_backward_batch(const msm_handle* plans, int nrep, const int64_t* of
 /* A batched forward (and, when grad_energies is not NULL, its adjoint)
  * captured once into an instantiated CUDA graph on the given buffers; every
  * msm_graph_launch replays all kernels of all replicas with one launch.  When
- * every plan is MSM_MIXED with one interpolation order and one splitting,
- * each stage is a single kernel launch over all replicas (a block finds its
- * replica in a table of per-replica arguments built here), the pair sums of
- * all replicas running concurrently with their grid passes; otherwise the
- * replicas' own launch sequences are forked over library streams.  The
+ * there are several replicas and every plan is MSM_MIXED with one
+ * interpolation order and one splitting, each stage is a single kernel launch
+ * over all replicas (a block finds its replica in a table of per-replica
+ * arguments built here), the pair sums of all replicas running concurrently
+ * with their grid passes; otherwise the replicas' own launch sequences are
+ * forked over library streams.  With nrep = 1 this is the graph form of one
+ * plan's msm_eval (small systems lose most of their launch overhead).  Kernel
+ * nodes keep the priority of the stream they were captured from.  The
  * buffers and plans must outlive the graph; inputs may change between
  * replays (same sizes).  Creating the graph uploads the tables (synchronous)
  * and runs no kernel.  Errors: INVALID_ARG, TOO_MANY_ATOMS, OOM, CUDA. */

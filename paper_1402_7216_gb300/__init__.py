@@ -175,6 +175,13 @@ class MSM:
             self._last_io = torch.float64
         return force, rec
 
+    def graph(self, pos, q, energy, phi=None, force=None, grad_energy=None, grad_pos=None, grad_q=None):
+        """msm_batch_graph_create with this plan alone: msm_eval (and, with
+        grad_energy, msm_eval_backward) on these float64 buffers captured into
+        a CUDA graph; energy and grad_energy are 1-element tensors.  Returns
+        a BatchGraph (launch() replays it)."""
+        return MSMBatch([self]).graph(pos, q, [pos.shape[0]], energy, phi, force, grad_energy, grad_pos, grad_q)
+
     def eval_f32io(self, pos, q, want_phi=True, want_force=True, stream=None, out=None):
         """msm_eval_f32io: eval with float32 positions, charges and outputs."""
         if pos.dtype != torch.float32 or q.dtype != torch.float32:

@@ -559,7 +559,9 @@ int msm_batch_graph_create(const msm_handle* plans, int nrep, const int64_t* off
     cudaStreamDestroy(cs);
     return MSM_ERR_OOM;
   }
-  const bool fused = batchable(plans, nrep);
+  // one replica gains nothing from the batched tables: it is captured on the
+  // single-system path (its compile-time lattice tile, its own patch size)
+  const bool fused = nrep > 1 && batchable(plans, nrep);
   rc = fused ? batch_tables(g, plans, nrep, offsets, pos, q, energies, phi, force, grad_energies, grad_pos, grad_q)
              : MSM_OK;
   if (rc == MSM_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = MSM_ERR_CUDA;
@@ -575,7 +577,11 @@ int msm_batch_graph_create(const msm_handle* plans, int nrep, const int64_t* off
     cudaError_t e = cudaStreamEndCapture(cs, &graph);  // always end the capture
     if (rc == MSM_OK && e != cudaSuccess) rc = MSM_ERR_CUDA;
     g->graph = graph;
-    if (rc == MSM_OK && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) rc = MSM_ERR_CUDA;
+    // node priorities: the grid passes keep the precedence of the plan's
+    // high-priority side stream they were captured from
+    if (rc == MSM_OK && cudaGraphInstantiateWithFlags(&g->exec, graph, cudaGraphInstantiateFlagUseNodePriority) !=
+                            cudaSuccess)
+      rc = MSM_ERR_CUDA;
   }
   cudaStreamDestroy(cs);
   if (rc != MSM_OK) {

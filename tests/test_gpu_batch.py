@@ -138,3 +138,35 @@ def test_batch_graph_fallback_fp64(dev):
     assert torch.allclose(E, E2, rtol=1e-12, atol=0)
     assert rel_rms(F.cpu().numpy(), F2.cpu().numpy()) <= 1e-12
     g.close()
+
+
+def test_single_plan_graph_matches_eager_calls(dev):
+    """A one-plan graph (forward + adjoint) replays the plan's own
+    msm_eval / msm_eval_backward, and picks up changed inputs."""
+    from paper_1402_7216_gb300 import MSM
+    from synth import make_water_box
+    L = 24.0
+    pos, q = make_water_box(L, 400, 2, 2, seed=91, periodic=True)
+    plan = MSM(box=L, periodic=True, cutoff=8.0, spacing=2.0, order=5, splitting=2, precision="mixed",
+               max_atoms=len(q))
+    tp, tq = torch.tensor(pos, device=dev), torch.tensor(q, device=dev)
+    n = len(q)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    phi = torch.zeros(n, dtype=torch.float64, device=dev)
+    F = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    gE = torch.ones(1, dtype=torch.float64, device=dev)
+    gp = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    gq = torch.zeros(n, dtype=torch.float64, device=dev)
+    g = plan.graph(tp, tq, E, phi, F, gE, gp, gq)
+    for shift in (0.0, 0.37):
+        tp.add_(shift)
+        g.launch()
+        torch.cuda.synchronize()
+        E0, phi0, F0 = plan.eval(tp, tq)
+        gp0, gq0 = plan.backward(torch.ones((), dtype=torch.float64, device=dev))
+        torch.cuda.synchronize()
+        plan.check_status()
+        assert abs(E.item() - E0.item()) <= 1e-7 * abs(E0.item())
+        for a, b in ((phi, phi0), (F, F0), (gp, gp0), (gq, gq0)):
+            assert float(((a - b) ** 2).sum().sqrt() / (b ** 2).sum().sqrt()) < 1e-6
+    g.close()
