@@ -158,3 +158,20 @@ def test_md_fixed_atoms_zero_steps_and_errors(dev):
     with pytest.raises(MSMError) as e:
         big.md_run(tp, tv, ti, tq, 0.05, 1, force=F)
     assert e.value.code == -9
+
+
+def test_md_atom_leaving_an_open_box_is_reported(dev):
+    """An open box has no wrap: an atom driven out of [0, L] is reported by
+    the next evaluation's device check through msm_status (no fault)."""
+    from paper_1402_7216_gb300 import MSMError
+    L, n = 16.0, 40
+    pos, q, im, vel = make_ion_system(L, n, seed=26, kind="plasma", periodic=False)
+    vel[0] = (40.0, 0.0, 0.0)                             # 2 A per step along +x
+    plan = make_plan(L, n, "mixed", periodic=False)
+    tp, tv, ti, tq = (torch.tensor(a, device=dev) for a in (pos, vel, im, q))
+    plan.md_run(tp, tv, ti, tq, 0.05, 10)
+    torch.cuda.synchronize()
+    with pytest.raises(MSMError) as e:
+        plan.check_status()
+    assert e.value.code == -4
+    assert plan.status() == 0                             # cleared once read

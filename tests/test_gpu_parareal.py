@@ -145,3 +145,44 @@ def test_parareal_argument_errors(dev):
     assert e.value.code == -9
     with pytest.raises(ValueError):
         parareal([a], a, tp, tv, ti, tq, 2, 0.05, 2, 0.1, 1, 1, 0.0)       # one plan per time point
+
+
+def test_parareal_window_of_one_is_one_fine_propagation(dev):
+    """W = 1: after one iteration lambda_1 = G + F - G = F(lambda_0)."""
+    from paper_1402_7216_gb300 import parareal
+    pos, q, im, vel = system(40, 35)
+    fine = [make_plan(len(q), "fp64")]
+    tp, tv, ti, tq = dev_tensors(dev, pos, vel, im, q)
+    lp, lv, iters, ch = parareal(fine, make_plan(len(q), "fp64"), tp, tv, ti, tq, 1, 0.05, 6, 0.1, 3, 1, 0.0)
+    assert iters == 1
+    seq = make_plan(len(q), "fp64")
+    sp, sv, si, sq = dev_tensors(dev, pos, vel, im, q)
+    seq.md_run(sp, sv, si, sq, 0.05, 6)
+    torch.cuda.synchronize()
+    assert np.abs(min_image(lp[1].cpu().numpy() - sp.cpu().numpy())).max() < 1e-11
+    assert np.abs(lv[1].cpu().numpy() - sv.cpu().numpy()).max() < 1e-11
+    np.testing.assert_array_equal(lp[0].cpu().numpy(), pos)
+
+
+def test_md_batch_mixed_with_records(dev):
+    """The batched MD on mixed plans: each replica's records and trajectory
+    match the same replica stepped alone (mixed tolerance)."""
+    from paper_1402_7216_gb300 import MSMBatch
+    systems = [system(n, seed) for n, seed in ((36, 51), (52, 52))]
+    single = []
+    for pos, q, im, vel in systems:
+        plan = make_plan(len(q), "mixed")
+        tp, tv, ti, tq = dev_tensors(dev, pos, vel, im, q)
+        _, rec = plan.md_run(tp, tv, ti, tq, 0.05, 6)
+        single.append((tp.cpu().numpy(), rec.cpu().numpy()))
+    plans = [make_plan(len(s[1]), "mixed") for s in systems]
+    cat = [np.concatenate([s[i] for s in systems]) for i in range(4)]
+    tp, tq, ti, tv = dev_tensors(dev, cat[0], cat[1], cat[2], cat[3])
+    counts = [len(s[1]) for s in systems]
+    B = MSMBatch(plans)
+    _, _, F = B.eval(tp, tq, counts, want_phi=False)
+    rec = B.md_run(tp, tv, F, ti, tq, counts, 0.05, 6).cpu().numpy()
+    off = np.cumsum([0] + counts)
+    for r, (p1, rec1) in enumerate(single):
+        assert np.abs(min_image(tp.cpu().numpy()[off[r]:off[r + 1]] - p1)).max() < 1e-6
+        np.testing.assert_allclose(rec[r][:, :3], rec1[:, :3], rtol=1e-6)
