@@ -623,6 +623,7 @@ int msm_eval_host(msm_handle h, int64_t n, const double* pos, const double* q, d
     if (e == cudaSuccess) e = cudaMalloc((void**)&D.hphi, sizeof(double) * P.cap);
     if (e == cudaSuccess) e = cudaMalloc((void**)&D.hforce, sizeof(double) * 3 * P.cap);
     if (e == cudaSuccess) e = cudaMalloc((void**)&D.henergy, sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&D.hstatus, sizeof(int));
     if (e != cudaSuccess) return MSM_ERR_OOM;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -640,8 +641,14 @@ int msm_eval_host(msm_handle h, int64_t n, const double* pos, const double* q, d
   if (force && n > 0 &&
       cudaMemcpyAsync(force, D.hforce, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return MSM_ERR_CUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return MSM_ERR_CUDA;
-  return msm_status(h);
+  // the status word comes back with the results: one synchronisation of the
+  // stream instead of a device-wide one and a blocking copy
+  if (cudaMemcpyAsync(D.hstatus, P.d.status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return MSM_ERR_CUDA;
+  const int bits = *D.hstatus;
+  if (bits && cudaMemset(P.d.status, 0, sizeof(int)) != cudaSuccess) return MSM_ERR_CUDA;
+  return decode_status(bits);
 }
 
 int msm_status(msm_handle h) {

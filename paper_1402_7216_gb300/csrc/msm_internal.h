@@ -89,6 +89,7 @@ struct DeviceBuffers {
   double* hphi = nullptr;
   double* hforce = nullptr;
   double* henergy = nullptr;
+  int* hstatus = nullptr;  // pinned host copy of the status word, read after the call's one sync
 };
 
 struct Plan {

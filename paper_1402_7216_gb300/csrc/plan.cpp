@@ -551,6 +551,7 @@ void free_plan(Plan* P) {
                   D.hphi, D.hforce, D.henergy};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (D.hstatus) cudaFreeHost(D.hstatus);
   for (int i = 0; i < 2; ++i)
     if (D.tmp[i]) cudaFree(D.tmp[i]);
   for (int k = 0; k < kMaxLevels; ++k) {

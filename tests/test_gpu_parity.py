@@ -248,6 +248,23 @@ def test_host_entry_point_matches_device(dev):
     assert rel_rms(Fh.numpy(), Fd) <= 1e-7
 
 
+def test_host_entry_point_reports_device_errors_once(dev):
+    """msm_eval_host returns the device status of its own call (an atom
+    outside an open box) and clears it: the next good call succeeds."""
+    from paper_1402_7216_gb300 import MSMError
+    ocfg = dict(box=20.0, periodic=False, cutoff=6.0, spacing=2.0, order=3, split=2)
+    plan = plan_for(ocfg, "mixed", 8)
+    pos = torch.tensor([[1.0, 2.0, 3.0], [25.0, 1.0, 1.0]], dtype=torch.float64).pin_memory()
+    q = torch.tensor([1.0, -1.0], dtype=torch.float64).pin_memory()
+    with pytest.raises(MSMError) as e:
+        plan.eval_host(pos, q)
+    assert e.value.code == -4
+    pos[1, 0] = 5.0
+    E = plan.eval_host(pos, q)[0]
+    assert E.item() < 0.0                                   # two opposite charges 4.6 A apart
+    assert plan.status() == 0
+
+
 def test_repeatable(dev):
     cfg = dict(box=24.0, periodic=True, cutoff=8.0, spacing=2.0, order=5, split=2)
     pos, q = make_water_box(24.0, 400, 2, 2, seed=26, periodic=True)
