@@ -200,6 +200,8 @@ int msm_md_run_batch(const msm_handle* plans, int nrep, const int64_t* offsets, 
  *   iterations host int or NULL: iterations run (not counting the sweep).
  *   change     host double [max_iter][2] or NULL: per iteration the largest
  *              position change (A) and velocity change.
+ * One iteration (the window's fine propagations and the corrected coarse
+ * sweep) is captured once into a CUDA graph and replayed.
  * Synchronous: reads the change back after each iteration.  window is 1 to
  * MSM_PARAREAL_MAX_WINDOW.  Errors: INVALID_ARG (also an unknown coarse_method),
  * TOO_MANY_ATOMS, CUDA. */

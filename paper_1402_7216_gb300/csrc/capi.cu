@@ -252,6 +252,29 @@ int md_loop(Plan& P, int method, int64_t n, double* pos, double* vel, double* fo
   return MSM_OK;
 }
 
+// Captures body(stream) on a private stream into an instantiated graph whose
+// kernel nodes keep the priorities of the streams they were captured from.
+template <typename F>
+int capture_graph(F&& body, cudaGraphExec_t* out) {
+  *out = nullptr;
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return MSM_ERR_CUDA;
+  int rc = MSM_OK;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    rc = MSM_ERR_CUDA;
+  } else {
+    rc = body(cs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &g);  // always end the capture
+    if (rc == MSM_OK && e != cudaSuccess) rc = MSM_ERR_CUDA;
+    if (rc == MSM_OK && cudaGraphInstantiateWithFlags(out, g, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess)
+      rc = MSM_ERR_CUDA;
+    if (g) cudaGraphDestroy(g);
+  }
+  cudaStreamDestroy(cs);
+  return rc;
+}
+
 std::once_flag g_config_once;
 cudaError_t g_config_err = cudaSuccess;
 
@@ -459,40 +482,50 @@ int msm_parareal(const msm_handle* fine, msm_handle coarse, int64_t n, const dou
     return B3 == 0 || cudaMemcpyAsync(dst, src, B3, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
   };
   // G from time point k: the coarse state (cpos, cvel) after steps_coarse steps
-  auto coarse_from = [&](int k) {
-    if (!cp(cpos, lp(k), st) || !cp(cvel, lv(k), st)) return (int)MSM_ERR_CUDA;
-    return md_loop(C, coarse_method, n, cpos, cvel, cforce, inv_mass, q, dt_coarse, steps_coarse, true, nullptr, st);
+  auto coarse_from = [&](int k, cudaStream_t s) {
+    if (!cp(cpos, lp(k), s) || !cp(cvel, lv(k), s)) return (int)MSM_ERR_CUDA;
+    return md_loop(C, coarse_method, n, cpos, cvel, cforce, inv_mass, q, dt_coarse, steps_coarse, true, nullptr, s);
   };
   // lambda_0 = the initial state; iteration 0 is one coarse sweep
   if (!cp(lp(0), pos0, st) || !cp(lv(0), vel0, st)) return MSM_ERR_CUDA;
   for (int k = 0; k < window; ++k) {
-    int rc = coarse_from(k);
+    int rc = coarse_from(k, st);
     if (rc != MSM_OK) return rc;
     if (!cp(gpos + k * N3, cpos, st) || !cp(gvel + k * N3, cvel, st) || !cp(lp(k + 1), cpos, st) ||
         !cp(lv(k + 1), cvel, st))
       return MSM_ERR_CUDA;
   }
   const double span = dt_fine * steps_fine;  // Delta T: velocity changes are weighed by it
-  std::vector<double> h(2 * (size_t)window);
-  for (int it = 0; it < max_iter; ++it) {
-    // F from every time point of the window, concurrently (one plan each)
-    int rc = fork_join(window, st, [&](int r, cudaStream_t s) {
-      if (!cp(fpos + r * N3, lp(r), s) || !cp(fvel + r * N3, lv(r), s)) return (int)MSM_ERR_CUDA;
+  // One iteration: F from every time point of the window, concurrently (one
+  // plan each), then the sequential coarse sweep with the correction.  On a
+  // small system that is thousands of short launches, so it is captured once
+  // into a CUDA graph and replayed.
+  auto iteration = [&](cudaStream_t s) {
+    int rc = fork_join(window, s, [&](int r, cudaStream_t fs) {
+      if (!cp(fpos + r * N3, lp(r), fs) || !cp(fvel + r * N3, lv(r), fs)) return (int)MSM_ERR_CUDA;
       return md_loop(fine[r]->p, MSM_MD_MSM, n, fpos + r * N3, fvel + r * N3, fforce + r * N3, inv_mass, q, dt_fine,
-                     steps_fine, true, nullptr, s);
+                     steps_fine, true, nullptr, fs);
     });
-    if (rc != MSM_OK) return rc;
-    // the sequential coarse sweep with the correction
-    for (int k = 0; k < window; ++k) {
-      rc = coarse_from(k);
-      if (rc != MSM_OK) return rc;
-      if (launch_parareal_correct(C, n, cpos, cvel, fpos + k * N3, fvel + k * N3, gpos + k * N3, gvel + k * N3,
-                                  lp(k + 1), lv(k + 1), chg + 2 * k, st) != cudaSuccess)
-        return MSM_ERR_CUDA;
+    for (int k = 0; k < window && rc == MSM_OK; ++k) {
+      rc = coarse_from(k, s);
+      if (rc == MSM_OK && launch_parareal_correct(C, n, cpos, cvel, fpos + k * N3, fvel + k * N3, gpos + k * N3,
+                                                  gvel + k * N3, lp(k + 1), lv(k + 1), chg + 2 * k, s) != cudaSuccess)
+        rc = MSM_ERR_CUDA;
     }
-    if (cudaMemcpyAsync(h.data(), chg, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-      return MSM_ERR_CUDA;
+    return rc;
+  };
+  cudaGraphExec_t graph = nullptr;
+  int rc = max_iter > 0 ? capture_graph(iteration, &graph) : MSM_OK;
+  for (int r = 0; r < window; ++r) fine[r]->p.last_stream = st;  // not the capture's streams
+  C.last_stream = st;
+  std::vector<double> h(2 * (size_t)window);
+  for (int it = 0; it < max_iter && rc == MSM_OK; ++it) {
+    if (cudaGraphLaunch(graph, st) != cudaSuccess ||
+        cudaMemcpyAsync(h.data(), chg, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = MSM_ERR_CUDA;
+      break;
+    }
     double dr = 0.0, dv = 0.0;
     for (int k = 0; k < window; ++k) {
       dr = std::max(dr, h[2 * k]);
@@ -505,7 +538,8 @@ int msm_parareal(const msm_handle* fine, msm_handle coarse, int64_t n, const dou
     if (iterations) *iterations = it + 1;
     if (dr <= tol && dv * std::fabs(span) <= tol) break;
   }
-  return MSM_OK;
+  if (graph) cudaGraphExecDestroy(graph);
+  return rc;
 }
 
 int msm_eval_backward(msm_handle h, const double* grad_energy, double* grad_pos, double* grad_q,
@@ -584,6 +618,7 @@ int msm_batch_graph_create(const msm_handle* plans, int nrep, const int64_t* off
       rc = MSM_ERR_CUDA;
   }
   cudaStreamDestroy(cs);
+  for (int r = 0; r < nrep; ++r) plans[r]->p.last_stream = nullptr;  // not the destroyed capture stream
   if (rc != MSM_OK) {
     msm_graph_destroy(g);
     return rc;
