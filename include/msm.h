@@ -161,7 +161,10 @@ int msm_cutoff_eval(msm_handle h, int64_t n, const double* pos, const double* q,
  *            momentum sum m v (x, y, z)}, each reduced in a fixed order.
  * Units are the caller's: the kick is F * inv_mass * dt, so coulomb_k, the
  * masses and dt must be consistent.  Asynchronous on cuda_stream and
- * capturable in a CUDA graph (3 + one evaluation's launches per step).
+ * capturable in a CUDA graph (3 + one evaluation's launches per step).  On
+ * systems of at most 262,144 atoms, with nsteps >= 4 and cuda_stream not
+ * being captured, one step is captured into a CUDA graph and replayed
+ * nsteps times (small systems' steps are bound by launch latency).
  * Errors: INVALID_ARG (n < 0, nsteps < 0, non-finite dt, unknown method,
  * missing buffers), TOO_MANY_ATOMS, CUDA; ATOM_OUTSIDE_BOX (an atom left an
  * open box) and NONFINITE later through msm_status. */

@@ -230,27 +230,43 @@ int md_force(Plan& P, int method, int64_t n, const double* pos, const double* q,
   return forward(P, n, pos, q, energy, (double*)nullptr, force, st);
 }
 
-// nsteps of velocity Verlet (drift, force, kick); with init_force the force
-// at the starting positions is evaluated first.
+// One velocity Verlet step (drift, force, kick).  rec: this step's record or
+// NULL; with a step counter rec is the base of the records and the kick's
+// record kernel places and advances (steps replayed from a graph).
+int md_step(Plan& P, int method, int64_t n, double* pos, double* vel, double* force, const double* inv_mass,
+            const double* q, double dt, double* rec, int* counter, cudaStream_t st) {
+  double* u = (rec && !counter) ? rec : P.d.scalars + 1;  // the step's energy
+  if (launch_md_drift(P, n, pos, vel, force, inv_mass, dt, st) != cudaSuccess) return MSM_ERR_CUDA;
+  int rc = md_force(P, method, n, pos, q, u, force, st);
+  if (rc != MSM_OK) return rc;
+  if (launch_md_kick(P, n, vel, force, inv_mass, dt, u, rec ? rec : P.d.scalars + 2, rec ? counter : nullptr, st) !=
+      cudaSuccess)
+    return MSM_ERR_CUDA;
+  return MSM_OK;
+}
+
+// nsteps of velocity Verlet; with init_force the force at the starting
+// positions is evaluated first.
 int md_loop(Plan& P, int method, int64_t n, double* pos, double* vel, double* force, const double* inv_mass,
             const double* q, double dt, int nsteps, bool init_force, double* records, cudaStream_t st) {
-  double* potential = P.d.scalars + 1;  // the step's energy when no record is kept
   if (init_force) {
-    int rc = md_force(P, method, n, pos, q, potential, force, st);
+    int rc = md_force(P, method, n, pos, q, P.d.scalars + 1, force, st);
     if (rc != MSM_OK) return rc;
   }
   for (int s = 0; s < nsteps; ++s) {
-    double* rec = records ? records + 6 * (size_t)s : nullptr;
-    double* u = rec ? rec : potential;
-    if (launch_md_drift(P, n, pos, vel, force, inv_mass, dt, st) != cudaSuccess) return MSM_ERR_CUDA;
-    int rc = md_force(P, method, n, pos, q, u, force, st);
+    int rc = md_step(P, method, n, pos, vel, force, inv_mass, q, dt, records ? records + 6 * (size_t)s : nullptr,
+                     nullptr, st);
     if (rc != MSM_OK) return rc;
-    if (launch_md_kick(P, n, vel, force, inv_mass, dt, u, rec ? rec : P.d.scalars + 2, st) != cudaSuccess)
-      return MSM_ERR_CUDA;
   }
   P.last_stream = st;
   return MSM_OK;
 }
+
+// msm_md_run replays one captured step from a CUDA graph on systems this
+// small (their steps are launch-bound), and launches eagerly otherwise or
+// when the caller's stream is itself being captured.
+constexpr int64_t kMdGraphMaxAtoms = 262144;
+constexpr int kMdGraphMinSteps = 4;
 
 // Captures body(stream) on a private stream into an instantiated graph whose
 // kernel nodes keep the priorities of the streams they were captured from.
@@ -428,7 +444,23 @@ int msm_md_run(msm_handle h, int64_t n, double* pos, double* vel, double* force,
   if (n > 0 && (!pos || !vel || !force || !inv_mass || !q)) return MSM_ERR_INVALID_ARG;
   Plan& P = h->p;
   if (n > P.cap) return MSM_ERR_TOO_MANY_ATOMS;
-  return md_loop(P, method, n, pos, vel, force, inv_mass, q, dt, nsteps, false, records, (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return MSM_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone || nsteps < kMdGraphMinSteps || n > kMdGraphMaxAtoms)
+    return md_loop(P, method, n, pos, vel, force, inv_mass, q, dt, nsteps, false, records, st);
+  if (records && cudaMemsetAsync(P.d.md_step, 0, sizeof(int), st) != cudaSuccess) return MSM_ERR_CUDA;
+  cudaGraphExec_t g = nullptr;
+  int rc = capture_graph(
+      [&](cudaStream_t cs) {
+        return md_step(P, method, n, pos, vel, force, inv_mass, q, dt, records, P.d.md_step, cs);
+      },
+      &g);
+  P.last_stream = st;
+  for (int s = 0; s < nsteps && rc == MSM_OK; ++s)
+    if (cudaGraphLaunch(g, st) != cudaSuccess) rc = MSM_ERR_CUDA;
+  if (g) cudaGraphExecDestroy(g);  // freed once its launches complete
+  return rc;
 }
 
 int msm_md_run_batch(const msm_handle* plans, int nrep, const int64_t* offsets, double* pos, double* vel,

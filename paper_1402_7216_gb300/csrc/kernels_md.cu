@@ -96,9 +96,11 @@ __global__ void __launch_bounds__(kMdThreads) k_md_kick(int64_t n, double* __res
 
 // The step's record {potential, kinetic, total, momentum x, y, z}: the
 // block partials summed in block order.
-// (potential may point at record[0]: the evaluation's energy output)
+// (potential may point at record[0]: the evaluation's energy output).  With
+// a step counter the record goes to record + 6 * counter, and the counter
+// advances: a step replayed from a CUDA graph writes the next record.
 __global__ void __launch_bounds__(kMdThreads) k_md_record(const double* __restrict__ partial, int nb,
-                                                           const double* potential, double* record) {
+                                                           const double* potential, double* record, int* counter) {
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int b = threadIdx.x; b < nb; b += blockDim.x)
 #pragma unroll
@@ -106,6 +108,7 @@ __global__ void __launch_bounds__(kMdThreads) k_md_record(const double* __restri
   block_sum4(acc);
   if (threadIdx.x == 0) {
     const double u = *potential;
+    if (counter) record += 6 * (size_t)(*counter)++;
     record[0] = u;
     record[1] = acc[0];
     record[2] = u + acc[0];
@@ -219,11 +222,11 @@ cudaError_t launch_md_drift(Plan& P, int64_t n, double* pos, double* vel, const 
 }
 
 cudaError_t launch_md_kick(Plan& P, int64_t n, double* vel, const double* force, const double* inv_mass, double dt,
-                           const double* potential, double* record, cudaStream_t st) {
+                           const double* potential, double* record, int* counter, cudaStream_t st) {
   const int nb = md_blocks(n);
   if (n > 0) k_md_kick<<<nb, kMdThreads, 0, st>>>(n, vel, force, inv_mass, dt, P.d.md_partial);
   else cudaMemsetAsync(P.d.md_partial, 0, sizeof(double) * 4, st);
-  k_md_record<<<1, kMdThreads, 0, st>>>(P.d.md_partial, nb, potential, record);
+  k_md_record<<<1, kMdThreads, 0, st>>>(P.d.md_partial, nb, potential, record, counter);
   P.launches += 2;
   return cudaGetLastError();
 }

@@ -82,6 +82,7 @@ struct DeviceBuffers {
   double* partial = nullptr;   // per-block energy partials
   double* scalars = nullptr;   // [8] scratch scalars (0: backward scale; 1, 2..7: MD energy and record when none is kept)
   double* md_partial = nullptr;  // [4 * kMdBlocks] per-block kinetic energy and momentum of the MD loop
+  int* md_step = nullptr;        // [1] record counter of MD steps replayed from a graph
   int* status = nullptr;
   // host-path staging (msm_eval_host)
   double* hpos = nullptr;
@@ -257,8 +258,10 @@ cudaError_t launch_restrict(Plan& P, int k, const void* fine, void* coarse, cuda
 constexpr int kMdBlocks = 1024;  // blocks (and partials) of the MD kernels
 cudaError_t launch_md_drift(Plan& P, int64_t n, double* pos, double* vel, const double* force,
                             const double* inv_mass, double dt, cudaStream_t s);
+// counter: NULL, or a device step counter that places the record at
+// record + 6 * counter and advances (steps replayed from a graph)
 cudaError_t launch_md_kick(Plan& P, int64_t n, double* vel, const double* force, const double* inv_mass, double dt,
-                           const double* potential, double* record, cudaStream_t s);
+                           const double* potential, double* record, int* counter, cudaStream_t s);
 // The parareal correction of one time point (uses P's box and MD partials):
 // lam = gnew + (f - g), g = gnew, change[0..1] = largest position and
 // velocity change of lam against its previous value.

@@ -505,6 +505,7 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   M((void**)&D.partial, sizeof(double) * P->nblk_partial);
   M((void**)&D.scalars, sizeof(double) * 8);
   M((void**)&D.md_partial, sizeof(double) * 4 * kMdBlocks);
+  M((void**)&D.md_step, sizeof(int));
   M((void**)&D.status, sizeof(int));
   if (e != cudaSuccess) return MSM_ERR_OOM;
   if (cudaMemset(D.status, 0, sizeof(int)) != cudaSuccess) return MSM_ERR_CUDA;
@@ -547,7 +548,7 @@ void free_plan(Plan* P) {
   DeviceBuffers& D = P->d;
   void* ptrs[] = {D.key, D.rank, D.perm, D.count, D.csum, D.cell_start, D.atoms,
                   D.gfrac, D.gbase, D.phis, D.fs, D.glong, D.topK, D.topq, D.topu, D.seg, D.seg2, D.cell_shift, D.cell_rows,
-                  D.seg_start, D.cell_off, D.partial, D.scalars, D.md_partial, D.status, D.hpos, D.hq,
+                  D.seg_start, D.cell_off, D.partial, D.scalars, D.md_partial, D.md_step, D.status, D.hpos, D.hq,
                   D.hphi, D.hforce, D.henergy};
   for (void* p : ptrs)
     if (p) cudaFree(p);

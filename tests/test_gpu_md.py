@@ -175,3 +175,15 @@ def test_md_atom_leaving_an_open_box_is_reported(dev):
         plan.check_status()
     assert e.value.code == -4
     assert plan.status() == 0                             # cleared once read
+
+
+def test_md_with_no_atoms(dev):
+    """n = 0: every step's record is zero and nothing is touched."""
+    plan = make_plan(16.0, 4, "mixed")
+    z3 = torch.zeros((0, 3), dtype=torch.float64, device=dev)
+    z1 = torch.zeros(0, dtype=torch.float64, device=dev)
+    F, rec = plan.md_run(z3, z3.clone(), z1, z1.clone(), 0.05, 3, force=z3.clone())
+    torch.cuda.synchronize()
+    plan.check_status()
+    assert rec.shape == (3, 6)
+    assert torch.all(rec == 0.0)
