@@ -175,8 +175,10 @@ int msm_md_run(msm_handle h, int64_t n, double* pos, double* vel, double* force,
  * offsets[r] .. offsets[r+1]-1 of every per-atom array and evaluated by
  * plans[r] (distinct plans); records, when given, is [nrep][nsteps][6].  The
  * replicas run concurrently on a pool of streams forked from cuda_stream
- * and joined back (events only; capturable).  Errors as msm_eval_batch and
- * msm_md_run. */
+ * and joined back (events only; capturable); when no replica exceeds
+ * 262,144 atoms (and nsteps >= 4, cuda_stream not being captured) one step
+ * of all replicas is captured into a CUDA graph and replayed, as in
+ * msm_md_run.  Errors as msm_eval_batch and msm_md_run. */
 int msm_md_run_batch(const msm_handle* plans, int nrep, const int64_t* offsets, double* pos, double* vel,
                      double* force, const double* inv_mass, const double* q, double dt, int nsteps, int method,
                      double* records, void* cuda_stream);

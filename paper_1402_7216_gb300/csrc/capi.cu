@@ -471,11 +471,36 @@ int msm_md_run_batch(const msm_handle* plans, int nrep, const int64_t* offsets, 
   if (nsteps < 0 || !std::isfinite(dt) || (method != MSM_MD_MSM && method != MSM_MD_CUTOFF))
     return MSM_ERR_INVALID_ARG;
   if (offsets[nrep] > 0 && (!pos || !vel || !force || !inv_mass || !q)) return MSM_ERR_INVALID_ARG;
-  return fork_join(nrep, (cudaStream_t)stream, [&](int r, cudaStream_t s) {
-    const int64_t o = offsets[r], n = offsets[r + 1] - offsets[r];
-    return md_loop(plans[r]->p, method, n, pos + 3 * o, vel + 3 * o, force + 3 * o, inv_mass + o, q + o, dt, nsteps,
-                   false, records ? records + 6 * (size_t)nsteps * r : nullptr, s);
-  });
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t nmax = 0;
+  for (int r = 0; r < nrep; ++r) nmax = std::max(nmax, offsets[r + 1] - offsets[r]);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return MSM_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone || nsteps < kMdGraphMinSteps || nmax > kMdGraphMaxAtoms)
+    return fork_join(nrep, st, [&](int r, cudaStream_t s) {
+      const int64_t o = offsets[r], n = offsets[r + 1] - offsets[r];
+      return md_loop(plans[r]->p, method, n, pos + 3 * o, vel + 3 * o, force + 3 * o, inv_mass + o, q + o, dt,
+                     nsteps, false, records ? records + 6 * (size_t)nsteps * r : nullptr, s);
+    });
+  // small replicas: one step of all of them captured into a graph and replayed
+  for (int r = 0; r < nrep && records; ++r)
+    if (cudaMemsetAsync(plans[r]->p.d.md_step, 0, sizeof(int), st) != cudaSuccess) return MSM_ERR_CUDA;
+  cudaGraphExec_t g = nullptr;
+  rc = capture_graph(
+      [&](cudaStream_t cs) {
+        return fork_join(nrep, cs, [&](int r, cudaStream_t s) {
+          const int64_t o = offsets[r], n = offsets[r + 1] - offsets[r];
+          Plan& P = plans[r]->p;
+          return md_step(P, method, n, pos + 3 * o, vel + 3 * o, force + 3 * o, inv_mass + o, q + o, dt,
+                         records ? records + 6 * (size_t)nsteps * r : nullptr, P.d.md_step, s);
+        });
+      },
+      &g);
+  for (int r = 0; r < nrep; ++r) plans[r]->p.last_stream = st;
+  for (int s = 0; s < nsteps && rc == MSM_OK; ++s)
+    if (cudaGraphLaunch(g, st) != cudaSuccess) rc = MSM_ERR_CUDA;
+  if (g) cudaGraphExecDestroy(g);
+  return rc;
 }
 
 int64_t msm_parareal_workspace(int64_t n, int window) {
