@@ -791,6 +791,7 @@ __device__ __forceinline__ void lattice_f2_body(const float* __restrict__ q, flo
     const int dz = zi - zo;
     if (active && dz >= -Ez && dz <= Ez && zo < G.n[2]) {
       const int s1 = seg_start[dz + Ez + 1];
+#pragma unroll 2  // the next segment's coefficients load under this one's FMAs
       for (int s = seg_start[dz + Ez]; s < s1; ++s) {
         const Segment2 sg = seg[s];
         const int c = Ey + sg.dy;  // window row 2 ty + c, stored at ty + c / 2 (+ SY / 2 when c is odd)
@@ -825,7 +826,7 @@ __device__ __forceinline__ void lattice_f2_body(const float* __restrict__ q, flo
 }
 
 template <int LP, int TXC, int TYC>
-__global__ void __launch_bounds__(32 * kLatticeZ, 7) k_lattice_f2(const float* __restrict__ q, float* __restrict__ u,
+__global__ void __launch_bounds__(32 * kLatticeZ, 6) k_lattice_f2(const float* __restrict__ q, float* __restrict__ u,
                                                                GridDims G, const Segment2* __restrict__ seg,
                                                                const int* __restrict__ seg_start, LatticeArgs L,
                                                                float scale) {
@@ -1809,7 +1810,7 @@ __global__ void __launch_bounds__(256, 2) kb_anterp_fx(const AntKArgs* __restric
                         b / (a.nbx * a.nby));
 }
 
-__global__ void __launch_bounds__(32 * kLatticeZ, 7) kb_lattice_f2(const LatKArgs* __restrict__ tab,
+__global__ void __launch_bounds__(32 * kLatticeZ, 6) kb_lattice_f2(const LatKArgs* __restrict__ tab,
                                                                    const int* __restrict__ first, int nrep) {
   const int r = batch_rep(first, nrep, blockIdx.x);
   const LatKArgs& a = tab[r];
