@@ -10,7 +10,9 @@
  * rest goes through anterpolation, restriction, a lattice cutoff per level,
  * an all-pairs top level, prolongation and interpolation; the potential is
  * U_i = k_c (u_i^short + u_i^long) and the forces are F_i = -dU/dr_i
- * (Sec. "Simulation loop").
+ * (Sec. "Simulation loop").  Around that evaluation: its adjoint, batches of
+ * independent systems, the cutoff method (the parareal section's coarse
+ * propagator), velocity Verlet molecular dynamics and one parareal window.
  *
  * Conventions shared by every entry point:
  *   - Units are the caller's: positions in the unit of box/cutoff/spacing
@@ -22,7 +24,8 @@
  *   - The caller owns every input and output buffer; the plan owns its
  *     workspace (sorted atoms, grids, tables) and frees it in msm_destroy.
  *   - Evaluation calls are asynchronous on the given CUDA stream (NULL = the
- *     legacy default stream) and never synchronise the host.  msm_eval may
+ *     legacy default stream) and never synchronise the host (msm_eval_host,
+ *     msm_parareal, msm_status and msm_debug_grid do, as documented).  msm_eval may
  *     fork part of its work onto a plan-owned stream and joins it back onto
  *     the given stream before returning control of the results (events
  *     only; see msm_set_overlap).  Errors that can
