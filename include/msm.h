@@ -165,7 +165,7 @@ int msm_cutoff_eval(msm_handle h, int64_t n, const double* pos, const double* q,
  * Units are the caller's: the kick is F * inv_mass * dt, so coulomb_k, the
  * masses and dt must be consistent.  Asynchronous on cuda_stream and
  * capturable in a CUDA graph (3 + one evaluation's launches per step).  On
- * systems of at most 262,144 atoms, with nsteps >= 4 and cuda_stream not
+ * systems of at most 262,144 atoms, with nsteps >= 16 and cuda_stream not
  * being captured, one step is captured into a CUDA graph and replayed
  * nsteps times (small systems' steps are bound by launch latency).
  * Errors: INVALID_ARG (n < 0, nsteps < 0, non-finite dt, unknown method,
@@ -179,7 +179,7 @@ int msm_md_run(msm_handle h, int64_t n, double* pos, double* vel, double* force,
  * plans[r] (distinct plans); records, when given, is [nrep][nsteps][6].  The
  * replicas run concurrently on a pool of streams forked from cuda_stream
  * and joined back (events only; capturable); when no replica exceeds
- * 262,144 atoms (and nsteps >= 4, cuda_stream not being captured) one step
+ * 262,144 atoms (and nsteps >= 16, cuda_stream not being captured) one step
  * of all replicas is captured into a CUDA graph and replayed, as in
  * msm_md_run.  Errors as msm_eval_batch and msm_md_run. */
 int msm_md_run_batch(const msm_handle* plans, int nrep, const int64_t* offsets, double* pos, double* vel,

@@ -266,7 +266,7 @@ int md_loop(Plan& P, int method, int64_t n, double* pos, double* vel, double* fo
 // small (their steps are launch-bound), and launches eagerly otherwise or
 // when the caller's stream is itself being captured.
 constexpr int64_t kMdGraphMaxAtoms = 262144;
-constexpr int kMdGraphMinSteps = 4;
+constexpr int kMdGraphMinSteps = 16;  // enough steps to repay capturing and instantiating the graph
 
 // Captures body(stream) on a private stream into an instantiated graph whose
 // kernel nodes keep the priorities of the streams they were captured from.

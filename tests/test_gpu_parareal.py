@@ -166,14 +166,15 @@ def test_parareal_window_of_one_is_one_fine_propagation(dev):
 
 def test_md_batch_mixed_with_records(dev):
     """The batched MD on mixed plans: each replica's records and trajectory
-    match the same replica stepped alone (mixed tolerance)."""
+    match the same replica stepped alone (mixed tolerance).  16 steps: both
+    run as one step replayed from a CUDA graph."""
     from paper_1402_7216_gb300 import MSMBatch
     systems = [system(n, seed) for n, seed in ((36, 51), (52, 52))]
     single = []
     for pos, q, im, vel in systems:
         plan = make_plan(len(q), "mixed")
         tp, tv, ti, tq = dev_tensors(dev, pos, vel, im, q)
-        _, rec = plan.md_run(tp, tv, ti, tq, 0.05, 6)
+        _, rec = plan.md_run(tp, tv, ti, tq, 0.05, 16)
         single.append((tp.cpu().numpy(), rec.cpu().numpy()))
     plans = [make_plan(len(s[1]), "mixed") for s in systems]
     cat = [np.concatenate([s[i] for s in systems]) for i in range(4)]
@@ -181,7 +182,7 @@ def test_md_batch_mixed_with_records(dev):
     counts = [len(s[1]) for s in systems]
     B = MSMBatch(plans)
     _, _, F = B.eval(tp, tq, counts, want_phi=False)
-    rec = B.md_run(tp, tv, F, ti, tq, counts, 0.05, 6).cpu().numpy()
+    rec = B.md_run(tp, tv, F, ti, tq, counts, 0.05, 16).cpu().numpy()
     off = np.cumsum([0] + counts)
     for r, (p1, rec1) in enumerate(single):
         assert np.abs(min_image(tp.cpu().numpy()[off[r]:off[r + 1]] - p1)).max() < 1e-6
