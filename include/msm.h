@@ -117,6 +117,11 @@ void msm_destroy(msm_handle h);
  * sits at i * 2^k * h_eff).  dims and lo may be NULL, else hold 3*levels ints. */
 int msm_query(msm_handle h, double h_eff[3], int* levels, int* dims, int* lo);
 
+/* The grid geometry msm_create would give these parameters, as msm_query
+ * reports it, computed on the host alone: no device call, no allocation (it
+ * runs without a GPU).  Errors: those of msm_create's parameter checks. */
+int msm_geometry(const msm_params* params, double h_eff[3], int* levels, int* dims, int* lo);
+
 /* One energy+force evaluation (the forward pass).
  *   pos    [n][3] double, device; periodic positions may lie anywhere (they are
  *          folded into the box), open ones must lie in [0, L].

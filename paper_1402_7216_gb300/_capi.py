@@ -38,7 +38,7 @@ class MSMError(RuntimeError):
 
 _lib = None
 _D = C.POINTER(C.c_double)
-EXPORTS = ["msm_create", "msm_create_tuned", "msm_destroy", "msm_query", "msm_eval", "msm_cutoff_eval", "msm_md_run", "msm_md_run_batch",
+EXPORTS = ["msm_create", "msm_create_tuned", "msm_destroy", "msm_query", "msm_geometry", "msm_eval", "msm_cutoff_eval", "msm_md_run", "msm_md_run_batch",
            "msm_parareal_workspace", "msm_parareal", "msm_fma_probe",
            "msm_eval_backward",
            "msm_eval_f32io", "msm_eval_backward_f32io",
@@ -66,6 +66,8 @@ def load(path=LIB_PATH):
     L.msm_destroy.restype = None
     L.msm_query.argtypes = [vp, _D, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.msm_query.restype = C.c_int
+    L.msm_geometry.argtypes = [C.POINTER(MSMParams), _D, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.msm_geometry.restype = C.c_int
     L.msm_eval.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp]
     L.msm_eval.restype = C.c_int
     L.msm_cutoff_eval.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp]

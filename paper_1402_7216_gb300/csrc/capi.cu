@@ -407,6 +407,22 @@ void msm_destroy(msm_handle h) {
   delete h;
 }
 
+int msm_geometry(const msm_params* params, double h_eff[3], int* levels, int* dims, int* lo) {
+  if (!params) return MSM_ERR_INVALID_ARG;
+  Plan P;  // host fields only: nothing is allocated
+  const int rc = plan_geometry(params, &P);
+  if (rc != MSM_OK) return rc;
+  if (h_eff)
+    for (int d = 0; d < 3; ++d) h_eff[d] = P.h[d];
+  if (levels) *levels = P.levels;
+  for (int k = 0; k < P.levels; ++k)
+    for (int d = 0; d < 3; ++d) {
+      if (dims) dims[3 * k + d] = P.n[k][d];
+      if (lo) lo[3 * k + d] = P.lo[k][d];
+    }
+  return MSM_OK;
+}
+
 int msm_query(msm_handle h, double h_eff[3], int* levels, int* dims, int* lo) {
   if (!h) return MSM_ERR_INVALID_ARG;
   const Plan& P = h->p;

@@ -233,6 +233,7 @@ void grid_batch_free(GridBatch* b);
 
 // ---- host helpers (plan.cpp) ----
 int validate_params(const msm_params* p);  // host only, no CUDA calls
+int plan_geometry(const msm_params* p, Plan* P);  // validation and grid geometry only (host, no CUDA calls)
 int validate_tuning(const msm_tuning* t);  // host only, no CUDA calls
 int build_plan(const msm_params* p, const msm_tuning* t, Plan* plan);
 void free_plan(Plan* plan);

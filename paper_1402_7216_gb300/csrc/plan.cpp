@@ -267,6 +267,16 @@ int validate_tuning(const msm_tuning* t) {
   return MSM_OK;
 }
 
+int plan_geometry(const msm_params* pp, Plan* P) {
+  const int vrc = validate_params(pp);
+  if (vrc != MSM_OK) return vrc;
+  P->P = *pp;
+  P->fp64 = (pp->precision == MSM_FP64);
+  P->S = (pp->order + 1) / 2;
+  P->W = 2 * P->S;
+  return geometry(*pp, P);
+}
+
 int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   const msm_params& p = *pp;
   int vrc = validate_params(pp);
