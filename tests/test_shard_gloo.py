@@ -68,3 +68,13 @@ def test_two_gloo_ranks_shard_gather_and_time():
     assert sorted(m0 + m1) == list(range(64)) and not set(m0) & set(m1)
     assert f0 == pytest.approx(want) and f1 == pytest.approx(want)
     assert t0 == t1 == 13.0                                  # the slower rank's time
+
+
+def test_single_process_helpers_without_a_process_group():
+    from paper_1402_7216_gb300.shard import gather_replica_values, max_over_ranks
+    assert max_over_ranks(3.5) == 3.5
+    out = gather_replica_values([10.0, 30.0], [1, 3], 4)
+    assert out[1].item() == 10.0 and out[3].item() == 30.0
+    assert out[0].isnan().item() and out[2].isnan().item()
+    with pytest.raises(ValueError):
+        gather_replica_values([1.0], [0, 1], 4)
