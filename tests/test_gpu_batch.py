@@ -170,3 +170,54 @@ def test_single_plan_graph_matches_eager_calls(dev):
         for a, b in ((phi, phi0), (F, F0), (gp, gp0), (gq, gq0)):
             assert float(((a - b) ** 2).sum().sqrt() / (b ** 2).sum().sqrt()) < 1e-6
     g.close()
+
+
+def test_replicas64_full_size_graph(dev):
+    """The benchmark's 64-replica batch at full size (5,352-49,767 atoms each,
+    a=10, h=2, cubic, mixed), replayed from its batch graph as the bench
+    times it: every replica's energy, forces and adjoint against that
+    replica's own msm_eval / msm_eval_backward, and three replicas (the
+    smallest, a middle one, the largest) against the oracle on a spatial
+    subsample of 256 atoms."""
+    from paper_1402_7216_gb300 import MSM, MSMBatch
+    from synth import replica_boxes, spatial_subsample
+    reps = replica_boxes(64)
+    counts = [len(q) for (_, _, q) in reps]
+    n = sum(counts)
+    plans = [MSM(box=L, periodic=True, cutoff=10.0, spacing=2.0, order=3, splitting=2, precision="mixed",
+                 max_atoms=len(q)) for (L, _, q) in reps]
+    pos = torch.tensor(np.vstack([p for (_, p, _) in reps]), device=dev)
+    q = torch.tensor(np.concatenate([qq for (_, _, qq) in reps]), device=dev)
+    E = torch.zeros(64, dtype=torch.float64, device=dev)
+    phi = torch.zeros(n, dtype=torch.float64, device=dev)
+    F = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    gE = torch.linspace(0.5, 2.0, 64, dtype=torch.float64, device=dev)
+    gp = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    gq = torch.zeros(n, dtype=torch.float64, device=dev)
+    g = MSMBatch(plans).graph(pos, q, counts, E, phi, F, gE, gp, gq)
+    g.launch()
+    g.launch()
+    torch.cuda.synchronize()
+    Eg, Fg, gpg, gqg = E.cpu().numpy(), F.cpu().numpy(), gp.cpu().numpy(), gq.cpu().numpy()
+    o = 0
+    for r, p in enumerate(plans):
+        c = counts[r]
+        E1, _, F1 = p.eval(pos[o:o + c], q[o:o + c])
+        gp1, gq1 = p.backward(gE[r])
+        torch.cuda.synchronize()
+        p.check_status()
+        assert abs(Eg[r] - E1.item()) <= 1e-6 * abs(E1.item()), r
+        assert rel_rms(Fg[o:o + c], F1.cpu().numpy()) <= 1e-5, r
+        assert rel_rms(gpg[o:o + c], gp1.cpu().numpy()) <= 1e-5, r
+        assert rel_rms(gqg[o:o + c], gq1.cpu().numpy()) <= 1e-5, r
+        o += c
+    off = np.cumsum([0] + counts)
+    order = np.argsort(counts)
+    for r in (order[0], order[32], order[-1]):
+        L, p_r, q_r = reps[r]
+        pick = spatial_subsample(p_r, L, 256, seed=int(r))
+        ref = O.msm(O.Params(box=(L,) * 3, periodic=True, cutoff=10.0, spacing=2.0, order=3, split=2), p_r, q_r,
+                    targets=pick)
+        assert rel_rms(Fg[off[r]:off[r + 1]][pick], ref["F"]) <= 1e-5, r
+        assert rel_rms(phi.cpu().numpy()[off[r]:off[r + 1]][pick], ref["phi"]) <= 1e-5, r
+    g.close()
