@@ -224,8 +224,12 @@ cudaError_t launch_md_drift(Plan& P, int64_t n, double* pos, double* vel, const 
 cudaError_t launch_md_kick(Plan& P, int64_t n, double* vel, const double* force, const double* inv_mass, double dt,
                            const double* potential, double* record, int* counter, cudaStream_t st) {
   const int nb = md_blocks(n);
-  if (n > 0) k_md_kick<<<nb, kMdThreads, 0, st>>>(n, vel, force, inv_mass, dt, P.d.md_partial);
-  else cudaMemsetAsync(P.d.md_partial, 0, sizeof(double) * 4, st);
+  if (n > 0) {
+    k_md_kick<<<nb, kMdThreads, 0, st>>>(n, vel, force, inv_mass, dt, P.d.md_partial);
+  } else {
+    const cudaError_t e = cudaMemsetAsync(P.d.md_partial, 0, sizeof(double) * 4, st);
+    if (e != cudaSuccess) return e;
+  }
   k_md_record<<<1, kMdThreads, 0, st>>>(P.d.md_partial, nb, potential, record, counter);
   P.launches += 2;
   return cudaGetLastError();
@@ -238,8 +242,8 @@ cudaError_t launch_parareal_correct(Plan& P, int64_t n, const double* gnew_pos, 
   if (n > 0)
     k_parareal_correct<<<nb, kMdThreads, 0, st>>>(n, md_box(P), gnew_pos, gnew_vel, f_pos, f_vel, g_pos, g_vel, lam_pos,
                                                   lam_vel, P.d.md_partial);
-  else
-    cudaMemsetAsync(P.d.md_partial, 0, sizeof(double) * 2, st);
+  else if (const cudaError_t e = cudaMemsetAsync(P.d.md_partial, 0, sizeof(double) * 2, st); e != cudaSuccess)
+    return e;
   k_parareal_change<<<1, kMdThreads, 0, st>>>(P.d.md_partial, nb, change);
   P.launches += 2;
   return cudaGetLastError();
