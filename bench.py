@@ -96,17 +96,31 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
+# FP32 flop of one evaluation of the short-range pair function with the C2
+# splitting (FMA = 2 flop, as in the measured peak): difference 3, r^2 5
+# (1 mul + 2 FMA), rsqrt 1, gamma polynomial in r^2 4 (2 FMA), 1/r - gamma/a
+# 1, potential accumulate 2, force factor 6 (1/r^2 1, the FMA to 1/r^3 plus
+# the derivative polynomial 2, that polynomial's FMA 2, times q_j 1), force
+# accumulate 6 (3 FMA): 28.  The clamp of r^2 at a^2 is not counted.
+PAIR_FLOP = 28.0
+
+
 def work_model(plan, n, box, cutoff, order):
-    """Algorithmic work per evaluation: each stage's flops and the fewest bytes it must move."""
+    """Algorithmic work per evaluation: each stage's flops and the fewest bytes
+    it must move.  The short range counts the method's pairs once (half
+    pairs, N (4/3) pi a^3 rho / 2 at the box's mean density) times one pair
+    evaluation; evaluating each pair from both atoms is the kernel's choice,
+    not the method's work."""
     V = box ** 3
     rho = n / V
-    pairs = n * (4.0 / 3.0) * math.pi * cutoff ** 3 * rho       # ordered pairs within a
+    pairs = 0.5 * n * (4.0 / 3.0) * math.pi * cutoff ** 3 * rho   # unordered pairs within a
     W3 = (order + 1) ** 3
     taps = plan_taps(plan)
     pts = [d[0] * d[1] * d[2] for d in plan.dims]
     lat_pts = sum(pts[:-1])
     return {
-        "short_range": {"flop": 31.0 * pairs, "bytes": 36.0 * n, "units": "%.4g ordered pairs" % pairs},
+        "short_range": {"flop": PAIR_FLOP * pairs, "bytes": 36.0 * n, "pairs": pairs,
+                        "units": "%.4g pairs within a (each counted once) x %g flop" % (pairs, PAIR_FLOP)},
         "lattice_cutoff": {"flop": 2.0 * taps * lat_pts, "bytes": 12.0 * lat_pts,
                            "units": "%d points x %d taps" % (lat_pts, taps)},
         "anterpolation": {"flop": 3.0 * W3 * n, "bytes": 32.0 * n + 8.0 * pts[0]},
@@ -179,17 +193,129 @@ def run_reference(args):
 
 
 def cpu_baseline(w, budget_s=30.0):
-    """One whole oracle evaluation of the same system on the host cores."""
+    """One whole oracle evaluation of the same system on the host cores;
+    returns (the baseline entry, the oracle's result)."""
     import oracle as O
     pos, q = w.make()
     P = O.Params(box=(w.box,) * 3, periodic=w.periodic, cutoff=w.cutoff, spacing=w.spacing,
                  levels=w.levels, order=w.order, split=w.split)
     O.lib()
     t0 = time.perf_counter()
-    O.msm(P, pos, q)
+    ref = O.msm(P, pos, q)
     t = time.perf_counter() - t0
-    return {"value": 1.0 / t, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "1 whole evaluation of the %d-atom system (%.1f s)" % (w.n_atoms, t)}
+    return ({"value": 1.0 / t, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+             "sample": "1 whole evaluation of the %d-atom system (%.1f s)" % (w.n_atoms, t)}, ref)
+
+
+def errors_vs(E, phi, F, ref):
+    """Energy relative error, force and potential rel-RMS, and the worst atom's
+    force error over the RMS force, against a reference (numpy arrays)."""
+    import numpy as np
+    dF = np.sqrt(((F - ref["F"]) ** 2).sum(1))
+    sF = float(np.sqrt((ref["F"] ** 2).sum(1).mean()))
+    return {"energy_rel": abs(E - ref["E"]) / abs(ref["E"]),
+            "force_rel_rms": float(np.sqrt(((F - ref["F"]) ** 2).sum() / (ref["F"] ** 2).sum())),
+            "phi_rel_rms": float(np.sqrt(((phi - ref["phi"]) ** 2).sum() / (ref["phi"] ** 2).sum())),
+            "force_worst_atom_over_rms": float(dF.max() / sF)}
+
+
+def config_errors(dev):
+    """The two small configurations against the FP64 oracle, every atom: the
+    3,000-atom open water box (cubic, C1; also against the direct Coulomb
+    sum, the method's own error) and the 23,558-atom periodic box (cubic,
+    C2, net +2 e), both GPU paths."""
+    import torch
+    import oracle as O
+    from paper_1402_7216_gb300 import MSM
+    out = {}
+    for name in ("water3k_open", "water23k"):
+        w = WORKLOADS[name]
+        pos, q = w.make()
+        P = O.Params(box=(w.box,) * 3, periodic=w.periodic, cutoff=w.cutoff, spacing=w.spacing,
+                     levels=w.levels, order=w.order, split=w.split)
+        ref = O.msm(P, pos, q)
+        e = {"atoms": len(q)}
+        for precision in ("mixed", "fp64"):
+            plan = MSM(box=w.box, periodic=w.periodic, cutoff=w.cutoff, spacing=w.spacing, levels=w.levels,
+                       order=w.order, splitting=w.split, precision=precision, max_atoms=len(q))
+            E, phi, F = plan.eval(torch.tensor(pos, device=dev), torch.tensor(q, device=dev))
+            torch.cuda.synchronize()
+            plan.check_status()
+            e[precision] = errors_vs(E.item(), phi.cpu().numpy(), F.cpu().numpy(), ref)
+            plan.close()
+        if not w.periodic:
+            d = O.direct_sum(pos, q)
+            e["oracle_vs_direct_sum"] = errors_vs(ref["E"], ref["phi"], ref["F"], d)
+        out[name] = e
+    return out
+
+
+def bench_large(dev, args):
+    """The 4.1M-atom box (340 A, a = 10, h = 1.5 -> 240^3, quintic, 5 levels),
+    mixed precision: forward (E, phi, F) and adjoint (dE/dr, dE/dq; the
+    adjoint rebuilds the level-0 potential instead of storing it) timed with
+    CUDA events, the device memory they hold, and both against the FP64 GPU
+    path (the host oracle cannot afford a full evaluation at this size)."""
+    import torch
+    from paper_1402_7216_gb300 import MSM
+    w = WORKLOADS["water4m"]
+    pos_h, q_h = w.make()
+    n = len(q_h)
+    pos, q = torch.tensor(pos_h, device=dev), torch.tensor(q_h, device=dev)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats(dev)
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    plan = MSM(box=w.box, periodic=True, cutoff=w.cutoff, spacing=w.spacing, levels=w.levels, order=w.order,
+               splitting=w.split, precision="mixed", max_atoms=n)
+    workspace = free0 - torch.cuda.mem_get_info(dev)[0]
+    E = torch.empty((), dtype=torch.float64, device=dev)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    gE = torch.ones((), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        plan.eval(pos, q, out=(E, phi, F))
+        gp, gq = plan.backward(gE)
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 5)
+    tf, tb = [], []
+    for _ in range(steps):
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        plan.eval(pos, q, out=(E, phi, F))
+        b.record(stream)
+        gp, gq = plan.backward(gE)
+        c.record(stream)
+        torch.cuda.synchronize()
+        tf.append(a.elapsed_time(b))
+        tb.append(b.elapsed_time(c))
+    plan.check_status()
+    peak_torch = torch.cuda.max_memory_allocated(dev)
+    Em, phim, Fm, gpm, gqm = E.item(), phi.cpu().numpy(), F.cpu().numpy(), gp.cpu().numpy(), gq.cpu().numpy()
+    plan.close()
+    plan64 = MSM(box=w.box, periodic=True, cutoff=w.cutoff, spacing=w.spacing, levels=w.levels, order=w.order,
+                 splitting=w.split, precision="fp64", max_atoms=n)
+    E64, phi64, F64 = plan64.eval(pos, q)
+    gp64, gq64 = plan64.backward(gE)
+    torch.cuda.synchronize()
+    plan64.check_status()
+    ref = {"E": E64.item(), "phi": phi64.cpu().numpy(), "F": F64.cpu().numpy()}
+    import numpy as np
+    err = errors_vs(Em, phim, Fm, ref)
+    err["adjoint_dE_dr_rel_rms"] = float(np.sqrt(((gpm - gp64.cpu().numpy()) ** 2).sum() /
+                                                 (gp64.cpu().numpy() ** 2).sum()))
+    err["adjoint_dE_dq_rel_rms"] = float(np.sqrt(((gqm - gq64.cpu().numpy()) ** 2).sum() /
+                                                 (gq64.cpu().numpy() ** 2).sum()))
+    plan64.close()
+    fm, bm = sorted(tf)[len(tf) // 2], sorted(tb)[len(tb) // 2]
+    return {"workload": "water4m: periodic 340 A, 1,364,300 waters + 3,550 Na+ + 3,550 Cl- (%d atoms); a=10, h=1.5 "
+                        "(240^3), quintic, C2, 5 levels, mixed" % n,
+            "metric": "energy+force+adjoint evaluations per second", "value": 1e3 / (fm + bm),
+            "unit": "evals/s", "forward_ms": fm, "backward_ms": bm, "steps": steps,
+            "device_memory_GB": {"plan_workspace": workspace / 1e9, "caller_tensors_peak": peak_torch / 1e9,
+                                 "budget": 180.0},
+            "mixed_vs_fp64_gpu": err,
+            "timing": "CUDA events around each forward and each adjoint (inputs and grids exceed L2)"}
 
 
 def bench_batch(dev, args, n_rep=64):
@@ -262,6 +388,20 @@ def bench_batch(dev, args, n_rep=64):
         seq.append(a.elapsed_time(b))
     for p in plans:
         p.check_status()
+    # three replicas (smallest, median, largest) of the last replay against
+    # the FP64 oracle, every atom
+    import oracle as O
+    graph.launch()
+    torch.cuda.synchronize()
+    Eh, phih, Fh = E.cpu().numpy(), phi.cpu().numpy(), F.cpu().numpy()
+    order = sorted(range(n_rep), key=lambda r: counts[r])
+    off = np.concatenate([[0], np.cumsum(counts)])
+    rep_err = {}
+    for r in (order[0], order[n_rep // 2], order[-1]):
+        L, p_r, q_r = reps[r]
+        ref = O.msm(O.Params(box=(L,) * 3, periodic=True, cutoff=10.0, spacing=2.0, order=3, split=2), p_r, q_r)
+        rep_err["replica_%d_%d_atoms" % (mine[r], counts[r])] = errors_vs(
+            float(Eh[r]), phih[off[r]:off[r + 1]], Fh[off[r]:off[r + 1]], ref)
     graph.close()
     t = max_over_ranks(sum(ms) / len(ms), device=dev)
     return {"metric": "replica energy+force+adjoint evaluations per second (one graph launch = all replicas)",
@@ -270,6 +410,7 @@ def bench_batch(dev, args, n_rep=64):
             "atoms_min": min(len(q) for (_, _, q) in reps_all), "atoms_max": max(len(q) for (_, _, q) in reps_all),
             "ms_per_batch": t, "steps": steps,
             "ms_per_batch_sequential_calls": min(seq), "tuning": tuning,
+            "errors_vs_oracle": rep_err,
             "autotune_ms": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in tune_ms.items()},
             "config": "periodic water boxes at 0.1 atoms/A^3, a=10, h=2.0, cubic, C2, mixed precision, "
                       "forward + adjoint, one CUDA graph (each stage one launch over all replicas), "
@@ -423,21 +564,31 @@ def parareal_window_timing(coarse_method="cutoff", coarse_cutoff=10.0, window=8,
             "timing": "parareal: host wall clock of the synchronous call; sequential: CUDA events"}
 
 
+def load_fma_probe():
+    """bench's FP32 FMA probe library (fma_probe.cu, built beside this file)."""
+    import ctypes
+    from __graft_entry__ import build_fma_probe
+    L = ctypes.CDLL(build_fma_probe())
+    L.fma_probe.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    L.fma_probe.restype = ctypes.c_int
+    return L
+
+
 def fma_probe(dev, iters=1 << 16, blocks=152 * 8):
-    """Measured FP32 FMA throughput (msm_fma_probe): packed two-lane and
+    """Measured FP32 FMA throughput (fma_probe.cu): packed two-lane and
     scalar FMA chains over every SM, median of 5 timed launches, TFLOP/s."""
     import ctypes
     import torch
-    from paper_1402_7216_gb300 import lib
+    L = load_fma_probe()
     out = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     res = {}
     for packed in (1, 0):
         def launch():
-            rc = lib().msm_fma_probe(packed, iters, blocks, ctypes.c_void_p(out.data_ptr()),
-                                     ctypes.c_void_p(stream.cuda_stream))
+            rc = L.fma_probe(packed, iters, blocks, ctypes.c_void_p(out.data_ptr()),
+                             ctypes.c_void_p(stream.cuda_stream))
             if rc != 0:
-                raise RuntimeError("msm_fma_probe failed: %d" % rc)
+                raise RuntimeError("fma_probe failed: %d" % rc)
         for _ in range(3):
             launch()
         ts = []
@@ -466,6 +617,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-parareal", action="store_true", help="skip the coarse-propagator timings")
     ap.add_argument("--no-md", action="store_true", help="skip the velocity Verlet timing")
+    ap.add_argument("--no-large", action="store_true", help="skip the 4.1M-atom forward + adjoint timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -553,18 +705,21 @@ def main():
     if not args.no_parareal:
         pr_window = [parareal_window_timing("cutoff", 10.0), parareal_window_timing("msm", 5.0)]
 
-    # end to end through the host-buffer entry point (pinned host memory)
+    # end to end through the host-buffer entry point (pinned host memory):
+    # positions and charges in, energy, potentials and forces out, every step
     pos_pin = torch.tensor(pos_h).pin_memory()
     q_pin = torch.tensor(q_h).pin_memory()
+    host_out = (torch.empty((), dtype=torch.float64).pin_memory(), torch.empty(n, dtype=torch.float64).pin_memory(),
+                torch.empty((n, 3), dtype=torch.float64).pin_memory())
     for _ in range(2):
-        plan.eval_host(pos_pin, q_pin)
+        plan.eval_host(pos_pin, q_pin, out=host_out)
     torch.cuda.synchronize()
     e2e_t = []
     for _ in range(max(3, args.steps // 3)):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        plan.eval_host(pos_pin, q_pin)
+        plan.eval_host(pos_pin, q_pin, out=host_out)
         e2e_t.append(time.perf_counter() - t0)
     e2e_tot = sum(e2e_t)
     if world > 1:
@@ -594,6 +749,12 @@ def main():
     batched = None
     if not args.no_batch:
         batched = bench_batch(dev, args)
+    large = None
+    if not args.no_large and world == 1:
+        large = bench_large(dev, args)
+    cfg_err = None
+    if not args.no_cpu_baseline and world == 1:
+        cfg_err = config_errors(dev)
 
     if rank != 0:
         return
@@ -626,7 +787,7 @@ def main():
             ach = model[dom]["flop"] / (stage_times[dom] * 1e-3) / 1e12
             return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": ach / fp32_peak, "traffic": traffic.get(dom),
-                    "peak_source": "FP32 FMA throughput measured by msm_fma_probe in this run (packed %.1f, "
+                    "peak_source": "FP32 FMA throughput measured by fma_probe.cu in this run (packed %.1f, "
                                    "scalar %.1f TFLOP/s); nominal %d SMs x %d lanes x 2 flop x %.0f MHz (%s "
                                    "sm_max_mhz) = %.1f" % (probe["packed"], probe["scalar"], N_SM, FP32_LANES,
                                                            sm_max, peak_kind, fp32_derived),
@@ -648,7 +809,9 @@ def main():
                    "precision": "mixed", "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 32 * n,
-                "d2h_bytes_per_step": 8, "api": "msm_eval_host (pinned host buffers)"},
+                "d2h_bytes_per_step": 32 * n + 8,
+                "api": "msm_eval_host (pinned host buffers): positions and charges in; energy, potentials and "
+                       "forces out"},
         "gpu_launches": launches,
         "roofline": roof,
         "roofline_isolated": roof_iso,
@@ -659,6 +822,7 @@ def main():
         "ms_per_step_serial": sum(ms_iso) / len(ms_iso),
         "fp64_gpu_path": fp64,
         "batched_replicas": batched,
+        "water4m_forward_adjoint": large,
         "parareal_G_cutoff": cutoff_G,
         "parareal_G_msm": msm_G,
         "md_velocity_verlet": md,
@@ -667,7 +831,13 @@ def main():
         "energy": E_mix,
     }
     if not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(w)
+        out["cpu_baseline"], ref = cpu_baseline(w)
+        # every atom of the headline system against the FP64 oracle (its
+        # whole evaluation above): the mixed path and the FP64 GPU path
+        out["errors_vs_oracle"] = {"mixed": errors_vs(E_mix, phi_mix.cpu().numpy(), F_mix.cpu().numpy(), ref),
+                                   "atoms_compared": n, "other_configs": cfg_err}
+        if fp64 is not None:
+            out["errors_vs_oracle"]["fp64_gpu"] = errors_vs(E64, phi64.cpu().numpy(), F64.cpu().numpy(), ref)
     print(json.dumps(out))
     plan.close()
     if world > 1:

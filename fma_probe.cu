@@ -1,10 +1,19 @@
-// probe.cu -- FP32 FMA throughput of this GPU, measured: the denominator of
-// the roofline fractions of the ALU-bound kernels (pair sums, lattice
+// fma_probe.cu -- FP32 FMA throughput of this GPU, measured: the denominator
+// of the roofline fractions of the ALU-bound kernels (pair sums, lattice
 // cutoff).  Each thread runs independent chains of packed (two-lane) or
 // scalar fused multiply-adds long enough that issue, not latency, limits it.
-#include "msm_internal.h"
+// Measurement support of bench.py, built as its own library (fma_probe.so),
+// not part of the MSM library or its C ABI.
+//
+//   int fma_probe(int packed, int64_t iters, int blocks, float* out, void* stream)
+// blocks x 256 threads each run iters iterations of 16 independent FMAs (8
+// packed two-lane FMAs when packed != 0, else 16 scalar ones) and write one
+// float each to out [blocks * 256] (device): FLOP = blocks * 256 * iters * 32
+// per launch.  Asynchronous on stream.  Returns 0, -1 for bad arguments, -7
+// when the launch fails.
+#include <cuda_runtime.h>
+#include <stdint.h>
 
-namespace msm {
 namespace {
 
 constexpr int kProbeChains = 8;  // independent accumulators per thread
@@ -37,15 +46,13 @@ __global__ void __launch_bounds__(256) k_fma_probe_scalar(int64_t iters, float a
 }
 
 }  // namespace
-}  // namespace msm
 
-extern "C" int msm_fma_probe(int packed, int64_t iters, int blocks, float* out, void* stream) {
-  using namespace msm;
-  if (iters < 0 || blocks < 1 || !out) return MSM_ERR_INVALID_ARG;
+extern "C" int fma_probe(int packed, int64_t iters, int blocks, float* out, void* stream) {
+  if (iters < 0 || blocks < 1 || !out) return -1;
   cudaStream_t st = (cudaStream_t)stream;
   // a = 1 - 2^-20 and b = 2^-10 keep every chain finite and away from denormals
   const float a = 0.99999904632568359375f, b = 0.0009765625f;
   if (packed) k_fma_probe_packed<<<blocks, 256, 0, st>>>(iters, a, b, out);
   else k_fma_probe_scalar<<<blocks, 256, 0, st>>>(iters, a, b, out);
-  return cudaGetLastError() == cudaSuccess ? MSM_OK : MSM_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? 0 : -7;
 }

@@ -52,9 +52,10 @@ extern "C" {
 #define MSM_ERR_NONFINITE (-5)          /* NaN/Inf position or charge (device-detected) */
 #define MSM_ERR_OOM (-6)                /* device allocation failed */
 #define MSM_ERR_CUDA (-7)               /* a CUDA runtime call failed */
-#define MSM_ERR_TIMEOUT (-8)            /* a bounded device wait gave up */
+#define MSM_ERR_TIMEOUT (-8)            /* reserved: no entry point waits on the device */
 #define MSM_ERR_TOO_MANY_ATOMS (-9)     /* n > max_atoms of the plan */
 #define MSM_ERR_NO_FORWARD (-10)        /* backward called before a forward on this plan */
+#define MSM_ERR_STALE_FORWARD (-11)     /* backward of a forward whose buffers a later forward reused */
 
 #define MSM_FP64 0  /* every step in double precision */
 #define MSM_MIXED 1 /* pairs and grids in FP32 with compensated sums; top level and energy in FP64 */
@@ -111,10 +112,14 @@ int msm_create_tuned(const msm_params* params, const msm_tuning* tuning, msm_han
 /* Frees the plan and its device workspace (synchronises the device). */
 void msm_destroy(msm_handle h);
 
-/* Grid geometry of the plan: h_eff[3] (finest spacing per dimension), the
- * level count, and for level k the point counts dims[3k..3k+2] and the first
- * absolute index lo[3k..3k+2] (0 for periodic grids; grid point i of level k
- * sits at i * 2^k * h_eff).  dims and lo may be NULL, else hold 3*levels ints. */
+/* Grid geometry of the plan (Sec. "Multilevel Summation Method": level k
+ * has spacing 2^k h and nodal basis functions Phi((x - x_mu^k) / (2^k h)) on
+ * its points; how many points and where the grids start is not printed and
+ * follows the plan's reading of it): h_eff[3] (finest spacing per
+ * dimension), the level count, and for level k the point counts
+ * dims[3k..3k+2] and the first absolute index lo[3k..3k+2] (0 for periodic
+ * grids; grid point i of level k sits at i * 2^k * h_eff).  dims and lo may
+ * be NULL, else hold 3*levels ints.  Host only; Errors: INVALID_ARG. */
 int msm_query(msm_handle h, double h_eff[3], int* levels, int* dims, int* lo);
 
 /* The grid geometry msm_create would give these parameters, as msm_query
@@ -122,7 +127,12 @@ int msm_query(msm_handle h, double h_eff[3], int* levels, int* dims, int* lo);
  * runs without a GPU).  Errors: those of msm_create's parameter checks. */
 int msm_geometry(const msm_params* params, double h_eff[3], int* levels, int* dims, int* lo);
 
-/* One energy+force evaluation (the forward pass).
+/* One energy+force evaluation (the forward pass): the short-range sum of
+ * g* over pairs within a (Eq. msmgrid) and the six steps of the long-range
+ * part in the order of Sec. "Multilevel Summation Method" (anterpolation;
+ * restriction and lattice cutoff per level; top level; prolongation;
+ * interpolation), U_i = k_c (u_i^short + u_i^long), and the forces
+ * F_i = -dU/dr_i of Sec. "Simulation loop".
  *   pos    [n][3] double, device; periodic positions may lie anywhere (they are
  *          folded into the box), open ones must lie in [0, L].
  *   q      [n] double, device.
@@ -225,16 +235,32 @@ int msm_parareal(const msm_handle* fine, msm_handle coarse, int64_t n, const dou
                  double dt_coarse, int steps_coarse, int coarse_method, int max_iter, double tol, double* lam_pos,
                  double* lam_vel, void* workspace, int* iterations, double* change, void* cuda_stream);
 
-/* Adjoint of the last msm_eval on this plan: given the upstream gradient
- * grad_energy = dL/dE ([1] double, device), writes grad_pos = dL/dr ([n][3])
- * and grad_q = dL/dq ([n]); either output may be NULL.  The long-range part
- * is evaluated by the transposed grid passes (interpolation^T =
- * anterpolation, prolongation^T = restriction, the symmetric lattice and top
- * kernels); the short-range part reuses the forward pair sums.  Positions
- * and charges must be those of the last msm_eval.
- * Errors: INVALID_ARG, NO_FORWARD, CUDA. */
-int msm_eval_backward(msm_handle h, const double* grad_energy, double* grad_pos, double* grad_q,
-                      void* cuda_stream);
+/* Adjoint of one forward pass (the reverse mode of the whole evaluation:
+ * Sec. "Multilevel Summation Method", the six steps of the algorithm taken
+ * backwards, with F_i = -dU/dr_i of Sec. "Simulation loop").
+ *   forward_id  the id msm_forward_id returned right after that forward
+ *               pass (msm_eval, msm_eval_f32io, msm_eval_host, a batch or
+ *               a graph replay); it must still be the plan's latest forward.
+ *   grad_energy dL/dE, [1] double, device.
+ *   grad_pos    dL/dr, [n][3] double, device or NULL.
+ *   grad_q      dL/dq, [n] double, device or NULL.
+ * The long-range part is evaluated by the transposed grid passes
+ * (interpolation^T = anterpolation, prolongation^T = restriction, the
+ * symmetric lattice and top kernels), rebuilding the adjoint level-0
+ * potential instead of storing any forward grid; the short-range part reuses
+ * the per-atom pair sums the forward pass kept.  Asynchronous on cuda_stream.
+ * Errors: INVALID_ARG (also forward_id <= 0), NO_FORWARD (no MSM forward on
+ * this plan, or the last evaluation was msm_cutoff_eval), STALE_FORWARD (a
+ * later forward has reused the buffers: run the forward again), CUDA. */
+int msm_eval_backward(msm_handle h, int64_t forward_id, const double* grad_energy, double* grad_pos,
+                      double* grad_q, void* cuda_stream);
+
+/* The id of the plan's latest forward pass (0 when there is none, or after
+ * msm_cutoff_eval): ids grow by one with every forward of the plan, and each
+ * msm_graph_launch gives every plan of the graph a new one.  Host only.
+ * Errors: INVALID_ARG.  (No counterpart in the paper: bookkeeping of the
+ * adjoint, above.) */
+int msm_forward_id(msm_handle h, int64_t* forward_id);
 
 /* msm_eval with FP32 positions, charges and per-atom outputs (device):
  *   pos [n][3] float, q [n] float, phi [n] float or NULL, force [n][3] float
@@ -251,8 +277,8 @@ int msm_eval_f32io(msm_handle h, int64_t n, const float* pos, const float* q, do
 /* msm_eval_backward with FP32 outputs grad_pos [n][3] and grad_q [n]
  * (grad_energy stays [1] double).  Follows either msm_eval or
  * msm_eval_f32io.  Errors as msm_eval_backward. */
-int msm_eval_backward_f32io(msm_handle h, const double* grad_energy, float* grad_pos, float* grad_q,
-                            void* cuda_stream);
+int msm_eval_backward_f32io(msm_handle h, int64_t forward_id, const double* grad_energy, float* grad_pos,
+                            float* grad_q, void* cuda_stream);
 
 /* Same as msm_eval with HOST buffers: copies pos and q to the device, runs
  * the evaluation on the stream, copies energy (and phi/force when non-NULL)
@@ -263,6 +289,10 @@ int msm_eval_host(msm_handle h, int64_t n, const double* pos, const double* q, d
                   double* phi, double* force, void* cuda_stream);
 
 /* ---- batches of independent systems (replicas) ----
+ * Each replica is one evaluation of Sec. "Multilevel Summation Method" as
+ * msm_eval; evaluating independent systems side by side is the sampling use
+ * of the method (no formula of its own in the paper; the parareal section
+ * likewise runs the propagations of a window concurrently).
  * Replica r uses plans[r] (its own box, geometry and workspace; a plan may
  * appear only once in a batch) and the atoms offsets[r] .. offsets[r+1]-1 of
  * the concatenated arrays pos [N][3] and q [N] (device), N = offsets[nrep]
@@ -276,9 +306,11 @@ int msm_eval_host(msm_handle h, int64_t n, const double* pos, const double* q, d
 int msm_eval_batch(const msm_handle* plans, int nrep, const int64_t* offsets, const double* pos, const double* q,
                    double* energies, double* phi, double* force, void* cuda_stream);
 
-/* Adjoint of the last msm_eval_batch (or of the last msm_eval of every plan):
- * grad_energies [nrep] (device) -> grad_pos [N][3], grad_q [N] (device, either
- * NULL), per replica as msm_eval_backward.
+/* Adjoint of the latest forward of every plan (msm_eval_batch, or each
+ * plan's own last msm_eval on these atoms): grad_energies [nrep] (device) ->
+ * grad_pos [N][3], grad_q [N] (device, either NULL), per replica as
+ * msm_eval_backward (Sec. "Multilevel Summation Method" taken backwards).
+ * No forward id is checked: the caller orders its batch calls.
  * Errors: INVALID_ARG, TOO_MANY_ATOMS, NO_FORWARD, CUDA. */
 int msm_eval_backward_batch(const msm_handle* plans, int nrep, const int64_t* offsets, const double* grad_energies,
                             double* grad_pos, double* grad_q, void* cuda_stream);
@@ -305,7 +337,9 @@ int msm_graph_launch(msm_graph_handle g, void* cuda_stream);
 void msm_graph_destroy(msm_graph_handle g);
 
 /* Synchronises the device and returns the first device-posted error of this
- * plan since the previous msm_status call (or MSM_OK), then clears it. */
+ * plan since the previous msm_status call (or MSM_OK), then clears it.
+ * Device-posted errors: ATOM_OUTSIDE_BOX, NONFINITE.  (No counterpart in the
+ * paper: error reporting of the asynchronous evaluation.) */
 int msm_status(msm_handle h);
 
 /* Copies one grid of the last evaluation to HOST memory, as doubles in the
@@ -369,14 +403,6 @@ const char* msm_stage_name(int stage);
  *   - Asynchronous on cuda_stream; no plan is needed.
  * Errors: INVALID_ARG, TOO_MANY_ATOMS, CUDA. */
 int msm_energy_noalloc(int64_t n, const double* q, const double* phi, double* energy, void* cuda_stream);
-
-/* FP32 fused multiply-add throughput probe (for roofline denominators):
- * blocks x 256 threads each run iters iterations of 16 independent FMAs,
- * as 8 packed two-lane FMAs (packed != 0) or 16 scalar ones, and write one
- * float each to out [blocks * 256] (device), so that FLOP = blocks * 256 *
- * iters * 32 per launch.  Asynchronous; time it with events on the stream.
- * Errors: INVALID_ARG, CUDA. */
-int msm_fma_probe(int packed, int64_t iters, int blocks, float* out, void* cuda_stream);
 
 /* Human-readable name of an MSM_ERR_* code. */
 const char* msm_strerror(int code);

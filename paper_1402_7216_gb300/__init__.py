@@ -188,12 +188,24 @@ class MSM:
             raise ValueError("eval_f32io takes float32 pos and q")
         return self.eval(pos, q, want_phi, want_force, stream, out)
 
-    def backward(self, grad_E, want_pos=True, want_q=True, stream=None, dtype=None):
-        """Adjoint of the last eval: returns (dL/dpos [N,3], dL/dq [N]) in the
+    def forward_id(self):
+        """msm_forward_id: the id of this plan's latest forward pass (0: none)."""
+        fid = C.c_int64()
+        _capi.check(lib().msm_forward_id(self._h, C.byref(fid)), "msm_forward_id")
+        return fid.value
+
+    def backward(self, grad_E, want_pos=True, want_q=True, stream=None, dtype=None, forward_id=None):
+        """Adjoint of a forward pass: returns (dL/dpos [N,3], dL/dq [N]) in the
         last eval's input type (or `dtype`: float64 -> msm_eval_backward,
-        float32 -> msm_eval_backward_f32io)."""
+        float32 -> msm_eval_backward_f32io).  forward_id names the forward
+        (its forward_id() right after it ran; default: the plan's latest);
+        MSMError STALE_FORWARD (-11) when a later forward reused the plan's
+        buffers."""
         n = self._last_n
         if n is None:
+            raise MSMError(-10, "msm_eval_backward")
+        fid = self.forward_id() if forward_id is None else int(forward_id)
+        if fid == 0:
             raise MSMError(-10, "msm_eval_backward")
         io = dtype or getattr(self, "_last_io", torch.float64)
         dev = grad_E.device
@@ -201,24 +213,34 @@ class MSM:
         gq = torch.empty(n, dtype=io, device=dev) if want_q else None
         g = grad_E.to(torch.float64).reshape(()).contiguous()
         fn = lib().msm_eval_backward if io == torch.float64 else lib().msm_eval_backward_f32io
-        rc = fn(self._h, _ptr(g), _ptr(gp), _ptr(gq), _stream(stream))
+        rc = fn(self._h, fid, _ptr(g), _ptr(gp), _ptr(gq), _stream(stream))
         _capi.check(rc, "msm_eval_backward" if io == torch.float64 else "msm_eval_backward_f32io")
         return gp, gq
 
-    def eval_host(self, pos, q, want_phi=False, want_force=False, stream=None):
+    def eval_host(self, pos, q, want_phi=False, want_force=False, stream=None, out=None):
         """End-to-end call with HOST (CPU) buffers: copies in, evaluates,
-        copies the energy (and phi/F when asked) out, synchronises."""
+        copies the energy (and phi/F when asked) out, synchronises.  out:
+        optional (E [0-d], phi [N] or None, F [N,3] or None) float64 CPU
+        tensors to fill (pinned ones make the copies asynchronous)."""
         if pos.is_cuda or q.is_cuda:
             raise ValueError("eval_host takes CPU tensors")
         pos = pos.to(torch.float64).contiguous()
         q = q.to(torch.float64).contiguous()
         n = pos.shape[0]
-        E = torch.empty((), dtype=torch.float64, pin_memory=pos.is_pinned())
-        phi = torch.empty(n, dtype=torch.float64, pin_memory=pos.is_pinned()) if want_phi else None
-        F = torch.empty((n, 3), dtype=torch.float64, pin_memory=pos.is_pinned()) if want_force else None
+        if out is None:
+            E = torch.empty((), dtype=torch.float64, pin_memory=pos.is_pinned())
+            phi = torch.empty(n, dtype=torch.float64, pin_memory=pos.is_pinned()) if want_phi else None
+            F = torch.empty((n, 3), dtype=torch.float64, pin_memory=pos.is_pinned()) if want_force else None
+        else:
+            E, phi, F = out
+            for t in (E, phi, F):
+                if t is not None and (t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous()):
+                    raise ValueError("eval_host outputs must be contiguous float64 CPU tensors")
         rc = lib().msm_eval_host(self._h, n, _ptr(pos), _ptr(q), _ptr(E), _ptr(phi), _ptr(F),
                                  _stream(stream))
         _capi.check(rc, "msm_eval_host")
+        self._last_n = n
+        self._last_io = torch.float64
         return E, phi, F
 
     def set_overlap(self, enable=True):
@@ -391,17 +413,31 @@ def parareal(fine, coarse, pos0, vel0, inv_mass, q, window, dt_fine, steps_fine,
 
 class MSMEnergy(torch.autograd.Function):
     """E(pos, q) with a hand-written adjoint: backward runs the transposed
-    grid passes of the library (msm_eval_backward)."""
+    grid passes of the library (msm_eval_backward).
+
+    The adjoint reuses the per-atom terms the plan's buffers keep from the
+    forward pass.  Each forward records its forward id; when a later forward
+    on the same plan (another apply, or any eval) has reused the buffers,
+    the backward re-runs this forward on its saved inputs first, so the
+    gradient is always that of this call's inputs."""
 
     @staticmethod
     def forward(ctx, pos, q, plan):
-        E, _, _ = plan.eval(pos.detach(), q.detach(), want_phi=False, want_force=False)
-        plan._last_n = pos.shape[0]
+        pos_d, q_d = pos.detach(), q.detach()
+        E, _, _ = plan.eval(pos_d, q_d, want_phi=False, want_force=False)
         ctx.plan = plan
+        ctx.forward_id = plan.forward_id()
+        ctx.save_for_backward(pos_d, q_d)
         return E
 
     @staticmethod
     def backward(ctx, grad_E):
-        gp, gq = ctx.plan.backward(grad_E, want_pos=ctx.needs_input_grad[0],
-                                   want_q=ctx.needs_input_grad[1])
+        plan = ctx.plan
+        pos, q = ctx.saved_tensors
+        kw = dict(want_pos=ctx.needs_input_grad[0], want_q=ctx.needs_input_grad[1])
+        if plan.forward_id() != ctx.forward_id:
+            # the buffers hold a later forward: recompute this one
+            plan.eval(pos, q, want_phi=False, want_force=False)
+            ctx.forward_id = plan.forward_id()
+        gp, gq = plan.backward(grad_E, forward_id=ctx.forward_id, **kw)
         return gp, gq, None

@@ -14,6 +14,7 @@ ERRORS = {
     -1: "MSM_ERR_INVALID_ARG", -2: "MSM_ERR_UNSUPPORTED", -3: "MSM_ERR_CUTOFF_GT_HALF_BOX",
     -4: "MSM_ERR_ATOM_OUTSIDE_BOX", -5: "MSM_ERR_NONFINITE", -6: "MSM_ERR_OOM", -7: "MSM_ERR_CUDA",
     -8: "MSM_ERR_TIMEOUT", -9: "MSM_ERR_TOO_MANY_ATOMS", -10: "MSM_ERR_NO_FORWARD",
+    -11: "MSM_ERR_STALE_FORWARD",
 }
 MSM_FP64, MSM_MIXED = 0, 1
 MAX_LEVELS = 16
@@ -39,8 +40,8 @@ class MSMError(RuntimeError):
 _lib = None
 _D = C.POINTER(C.c_double)
 EXPORTS = ["msm_create", "msm_create_tuned", "msm_destroy", "msm_query", "msm_geometry", "msm_eval", "msm_cutoff_eval", "msm_md_run", "msm_md_run_batch",
-           "msm_parareal_workspace", "msm_parareal", "msm_fma_probe",
-           "msm_eval_backward",
+           "msm_parareal_workspace", "msm_parareal",
+           "msm_eval_backward", "msm_forward_id",
            "msm_eval_f32io", "msm_eval_backward_f32io",
            "msm_eval_host", "msm_status", "msm_debug_grid", "msm_set_overlap", "msm_profile", "msm_profile_read",
            "msm_stage_name", "msm_energy_noalloc", "msm_eval_batch", "msm_eval_backward_batch",
@@ -81,13 +82,13 @@ def load(path=LIB_PATH):
     L.msm_parareal.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int, C.c_double, C.c_int, C.c_double, C.c_int,
                                C.c_int, C.c_int, C.c_double, vp, vp, vp, vp, vp, vp]
     L.msm_parareal.restype = C.c_int
-    L.msm_fma_probe.argtypes = [C.c_int, C.c_int64, C.c_int, vp, vp]
-    L.msm_fma_probe.restype = C.c_int
-    L.msm_eval_backward.argtypes = [vp, vp, vp, vp, vp]
+    L.msm_eval_backward.argtypes = [vp, C.c_int64, vp, vp, vp, vp]
     L.msm_eval_backward.restype = C.c_int
+    L.msm_forward_id.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.msm_forward_id.restype = C.c_int
     L.msm_eval_f32io.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp]
     L.msm_eval_f32io.restype = C.c_int
-    L.msm_eval_backward_f32io.argtypes = [vp, vp, vp, vp, vp]
+    L.msm_eval_backward_f32io.argtypes = [vp, C.c_int64, vp, vp, vp, vp]
     L.msm_eval_backward_f32io.restype = C.c_int
     L.msm_eval_host.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp]
     L.msm_eval_host.restype = C.c_int

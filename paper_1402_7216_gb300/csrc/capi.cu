@@ -101,13 +101,17 @@ int forward(Plan& P, int64_t n, const IO* pos, const IO* q, double* energy, IO* 
   if (e != cudaSuccess) return MSM_ERR_CUDA;
   P.last_stream = st;
   P.last_n = n;
+  P.forward_id = ++P.next_id;
   P.evals += 1;
   return MSM_OK;
 }
 
+// forward_id: the id the caller's forward pass was given (msm_forward_id);
+// 0 accepts whatever forward the plan holds (the batched adjoints).
 template <typename IO>
-int backward(Plan& P, const double* grad_energy, IO* grad_pos, IO* grad_q, cudaStream_t st) {
+int backward(Plan& P, int64_t forward_id, const double* grad_energy, IO* grad_pos, IO* grad_q, cudaStream_t st) {
   if (P.last_n < 0) return MSM_ERR_NO_FORWARD;
+  if (forward_id != 0 && forward_id != P.forward_id) return MSM_ERR_STALE_FORWARD;
   int64_t n = P.last_n;
   // adjoint of u_long = A^T M A q with respect to its inputs: anterpolate the
   // adjoint of u_long (1/2 dL/dE q_i), sweep the (symmetric) grid operator,
@@ -204,7 +208,8 @@ int batch_backward(const msm_handle* plans, int nrep, const int64_t* off, const 
     Plan& P = plans[r]->p;
     int64_t o = off[r];
     if (P.last_n != off[r + 1] - off[r]) return (int)MSM_ERR_NO_FORWARD;
-    return backward(P, grad_energies + r, grad_pos ? grad_pos + 3 * o : nullptr, grad_q ? grad_q + o : nullptr, s);
+    return backward(P, 0, grad_energies + r, grad_pos ? grad_pos + 3 * o : nullptr, grad_q ? grad_q + o : nullptr,
+                    s);
   });
 }
 
@@ -213,6 +218,7 @@ int batch_backward(const msm_handle* plans, int nrep, const int64_t* off, const 
 int cutoff_forward(Plan& P, int64_t n, const double* pos, const double* q, double* energy, double* phi, double* force,
                    cudaStream_t st) {
   P.last_n = -1;  // the per-atom buffers no longer hold an MSM forward pass
+  P.forward_id = 0;
   cudaError_t e = stage(P, MSM_STAGE_BINNING, st, [&] { return launch_binning(P, n, pos, q, st); });
   if (e == cudaSuccess) e = stage(P, MSM_STAGE_SHORT_RANGE, st, [&] { return launch_cutoff_pairs(P, n, st); });
   if (e == cudaSuccess)
@@ -306,6 +312,8 @@ struct msm_graph {
   GridBatch* grid = nullptr;
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  // the plans whose buffers a replay refills (each replay is a new forward)
+  std::vector<Plan*> plans;
 };
 
 namespace {
@@ -615,10 +623,16 @@ int msm_parareal(const msm_handle* fine, msm_handle coarse, int64_t n, const dou
   return rc;
 }
 
-int msm_eval_backward(msm_handle h, const double* grad_energy, double* grad_pos, double* grad_q,
+int msm_eval_backward(msm_handle h, int64_t forward_id, const double* grad_energy, double* grad_pos, double* grad_q,
                       void* stream) {
-  if (!h || !grad_energy) return MSM_ERR_INVALID_ARG;
-  return backward(h->p, grad_energy, grad_pos, grad_q, (cudaStream_t)stream);
+  if (!h || !grad_energy || forward_id <= 0) return MSM_ERR_INVALID_ARG;
+  return backward(h->p, forward_id, grad_energy, grad_pos, grad_q, (cudaStream_t)stream);
+}
+
+int msm_forward_id(msm_handle h, int64_t* forward_id) {
+  if (!h || !forward_id) return MSM_ERR_INVALID_ARG;
+  *forward_id = h->p.forward_id;
+  return MSM_OK;
 }
 
 int msm_eval_f32io(msm_handle h, int64_t n, const float* pos, const float* q, double* energy, float* phi,
@@ -629,10 +643,10 @@ int msm_eval_f32io(msm_handle h, int64_t n, const float* pos, const float* q, do
   return forward(P, n, pos, q, energy, phi, force, (cudaStream_t)stream);
 }
 
-int msm_eval_backward_f32io(msm_handle h, const double* grad_energy, float* grad_pos, float* grad_q,
-                            void* stream) {
-  if (!h || !grad_energy) return MSM_ERR_INVALID_ARG;
-  return backward(h->p, grad_energy, grad_pos, grad_q, (cudaStream_t)stream);
+int msm_eval_backward_f32io(msm_handle h, int64_t forward_id, const double* grad_energy, float* grad_pos,
+                            float* grad_q, void* stream) {
+  if (!h || !grad_energy || forward_id <= 0) return MSM_ERR_INVALID_ARG;
+  return backward(h->p, forward_id, grad_energy, grad_pos, grad_q, (cudaStream_t)stream);
 }
 
 int msm_eval_batch(const msm_handle* plans, int nrep, const int64_t* offsets, const double* pos, const double* q,
@@ -691,7 +705,10 @@ int msm_batch_graph_create(const msm_handle* plans, int nrep, const int64_t* off
       rc = MSM_ERR_CUDA;
   }
   cudaStreamDestroy(cs);
-  for (int r = 0; r < nrep; ++r) plans[r]->p.last_stream = nullptr;  // not the destroyed capture stream
+  for (int r = 0; r < nrep; ++r) {
+    plans[r]->p.last_stream = nullptr;  // not the destroyed capture stream
+    g->plans.push_back(&plans[r]->p);
+  }
   if (rc != MSM_OK) {
     msm_graph_destroy(g);
     return rc;
@@ -702,7 +719,11 @@ int msm_batch_graph_create(const msm_handle* plans, int nrep, const int64_t* off
 
 int msm_graph_launch(msm_graph_handle g, void* stream) {
   if (!g || !g->exec) return MSM_ERR_INVALID_ARG;
-  return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? MSM_OK : MSM_ERR_CUDA;
+  if (cudaGraphLaunch(g->exec, (cudaStream_t)stream) != cudaSuccess) return MSM_ERR_CUDA;
+  // the replay refilled every plan's buffers: a later adjoint of an earlier
+  // forward id must be refused
+  for (Plan* P : g->plans) P->forward_id = ++P->next_id;
+  return MSM_OK;
 }
 
 void msm_graph_destroy(msm_graph_handle g) {
@@ -835,9 +856,10 @@ const char* msm_strerror(int code) {
     case MSM_ERR_NONFINITE: return "non-finite position or charge";
     case MSM_ERR_OOM: return "device allocation failed";
     case MSM_ERR_CUDA: return "CUDA error";
-    case MSM_ERR_TIMEOUT: return "bounded device wait gave up";
+    case MSM_ERR_TIMEOUT: return "bounded device wait gave up (reserved)";
     case MSM_ERR_TOO_MANY_ATOMS: return "more atoms than the plan's capacity";
     case MSM_ERR_NO_FORWARD: return "backward before forward";
+    case MSM_ERR_STALE_FORWARD: return "the plan holds a later forward pass than the one named";
     default: return "unknown error";
   }
 }

@@ -1,20 +1,26 @@
 // kernels_bin.cu -- atom binning (link cells, Sec. "Short-range interactions":
 // atoms are binned into cells so that each atom only examines nearby cells).
 //
-// A counting sort over cells in four launches:
-//   k_bin_count    cell key of every atom; its rank inside the cell from one
-//                  warp-aggregated atomic per (warp, cell)
+// A counting sort over cells in five launches:
+//   k_bin_count    cell key of every atom; a provisional rank inside the cell
+//                  from one warp-aggregated atomic per (warp, cell)
 //   k_cell_sums    per-chunk sums of the cell counts
 //   k_cell_scan    exclusive scan -> cell_start; resets the counts to zero
 //                  for the next evaluation
-//   k_bin_scatter  writes each atom's sorted records at cell_start + rank:
-//                  cell-local coordinates for the pair sums, fractional
-//                  level-0 grid coordinates and the first support index for
-//                  the grid passes, and the permutation back to input order.
-// The order inside a cell is the order in which the atomics were served, so
-// it may change from one evaluation to the next; every later pass either
-// accumulates in whatever order the atoms come or goes through the
-// permutation, so only the rounding of sums depends on it.
+//   k_bin_perm     perm[cell_start + rank] = atom index
+//   k_cell_fill    one warp per cell: puts the cell's atoms in input-index
+//                  order (each atom's final rank is the number of the cell's
+//                  atoms with a smaller index) and writes their sorted
+//                  records: cell-local coordinates for the pair sums,
+//                  fractional level-0 grid coordinates and the first support
+//                  index for the grid passes, and the permutation back to
+//                  input order.
+// The provisional ranks follow the order in which the atomics were served;
+// the reordering makes the sorted order a function of the input alone, so
+// every later pass sums in the same order on every run and the results are
+// bit-reproducible.  A cell of more than kOrderMax atoms (over 40 times the
+// default cell fill) keeps the atomic order: still correct, only its
+// rounding may vary between runs.
 //
 // Precision.  The FP64 plan folds and bins in FP64.  The mixed plan takes no
 // FP64 arithmetic at all (this GPU issues FP64 at 1/64 of the FP32 rate): an
@@ -37,6 +43,8 @@ namespace msm {
 namespace {
 
 constexpr int kScanChunk = 4096;  // cells per block of the cell scan (1024 threads x 4)
+constexpr int kFillWarps = 8;     // cells per block of k_cell_fill
+constexpr int kOrderMax = 1024;   // largest cell that k_cell_fill puts in index order
 
 // Folds x into [0, L) (multiplying by the reciprocal: FP64 division is slow).
 __device__ __forceinline__ double fold(double x, double L, double inv_L) {
@@ -193,6 +201,7 @@ struct BinKArgs {
   void* gfrac;
   int4* gbase;
   int* perm;
+  int ncell;
 };
 
 template <typename IO, bool FP64>
@@ -339,16 +348,27 @@ __global__ void __launch_bounds__(1024) kb_cell_scan(const ScanKArgs* __restrict
   cell_scan_body(tab[r].count, tab[r].ncell, tab[r].sums, tab[r].cell_start, blockIdx.x - first[r]);
 }
 
-template <typename IO, bool FP64>
-__device__ __forceinline__ void bin_scatter_body(const IO* __restrict__ pos, const IO* __restrict__ q, int n,
-                                                 const BinArgs& A, const int* __restrict__ key_in,
-                                                 const int* __restrict__ rank_in, const int* __restrict__ cell_start,
-                                                 void* __restrict__ atoms_v, void* __restrict__ gfrac_v,
-                                                 int4* __restrict__ gbase, int* __restrict__ perm, int blk) {
+// perm[cell_start[key] + provisional rank] = i
+__device__ __forceinline__ void bin_perm_body(int n, const int* __restrict__ key_in, const int* __restrict__ rank_in,
+                                              const int* __restrict__ cell_start, int* __restrict__ perm, int blk) {
   const int i = blk * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int key = key_in[i];
-  const int s = cell_start[key] + rank_in[i];
+  perm[cell_start[key_in[i]] + rank_in[i]] = i;
+}
+
+__global__ void __launch_bounds__(256) k_bin_perm(int n, const int* __restrict__ key_in,
+                                                  const int* __restrict__ rank_in, const int* __restrict__ cell_start,
+                                                  int* __restrict__ perm) {
+  bin_perm_body(n, key_in, rank_in, cell_start, perm, blockIdx.x);
+}
+
+// The sorted records of atom i at slot s of cell `key` (the atom's cell as
+// k_bin_count found it: the same functions on the same input).
+template <typename IO, bool FP64>
+__device__ __forceinline__ void write_records(const IO* __restrict__ pos, const IO* __restrict__ q, const BinArgs& A,
+                                              int key, int i, int s, void* __restrict__ atoms_v,
+                                              void* __restrict__ gfrac_v, int4* __restrict__ gbase,
+                                              int* __restrict__ perm) {
   const int kc[3] = {key % A.nc[0], (key / A.nc[0]) % A.nc[1], key / (A.nc[0] * A.nc[1])};
   int bad = 0, bs[3];
   if (FP64) {
@@ -377,23 +397,64 @@ __device__ __forceinline__ void bin_scatter_body(const IO* __restrict__ pos, con
   perm[s] = i;
 }
 
+// One warp per cell: the cell's atoms (perm, in provisional order) are put in
+// index order and their records written.  idx: the warp's kOrderMax ints of
+// shared memory.
 template <typename IO, bool FP64>
-__global__ void __launch_bounds__(256) k_bin_scatter(const IO* __restrict__ pos, const IO* __restrict__ q, int n,
-                                                     BinArgs A, const int* __restrict__ key_in,
-                                                     const int* __restrict__ rank_in,
-                                                     const int* __restrict__ cell_start, void* __restrict__ atoms_v,
-                                                     void* __restrict__ gfrac_v, int4* __restrict__ gbase,
-                                                     int* __restrict__ perm) {
-  bin_scatter_body<IO, FP64>(pos, q, n, A, key_in, rank_in, cell_start, atoms_v, gfrac_v, gbase, perm, blockIdx.x);
+__device__ __forceinline__ void cell_fill_body(const IO* __restrict__ pos, const IO* __restrict__ q,
+                                               const BinArgs& A, const int* __restrict__ cell_start,
+                                               void* __restrict__ atoms_v, void* __restrict__ gfrac_v,
+                                               int4* __restrict__ gbase, int* __restrict__ perm, int ncell, int cell,
+                                               int* __restrict__ idx) {
+  if (cell >= ncell) return;  // warp-uniform
+  const int lane = threadIdx.x & 31;
+  const int s0 = cell_start[cell], m = cell_start[cell + 1] - s0;
+  if (m <= kOrderMax) {
+    for (int t = lane; t < m; t += 32) idx[t] = perm[s0 + t];
+    __syncwarp();
+    for (int t = lane; t < m; t += 32) {
+      const int i = idx[t];
+      int r = 0;
+      for (int j = 0; j < m; ++j) r += idx[j] < i;  // indices are distinct: r is a permutation of 0..m-1
+      write_records<IO, FP64>(pos, q, A, cell, i, s0 + r, atoms_v, gfrac_v, gbase, perm);
+    }
+    __syncwarp();
+  } else {
+    for (int t = lane; t < m; t += 32)
+      write_records<IO, FP64>(pos, q, A, cell, perm[s0 + t], s0 + t, atoms_v, gfrac_v, gbase, perm);
+  }
 }
 
 template <typename IO, bool FP64>
-__global__ void __launch_bounds__(256) kb_bin_scatter(const BinKArgs<IO>* __restrict__ tab,
-                                                      const int* __restrict__ first, int nrep) {
+__global__ void __launch_bounds__(32 * kFillWarps) k_cell_fill(const IO* __restrict__ pos, const IO* __restrict__ q,
+                                                               BinArgs A, const int* __restrict__ cell_start,
+                                                               void* __restrict__ atoms_v, void* __restrict__ gfrac_v,
+                                                               int4* __restrict__ gbase, int* __restrict__ perm,
+                                                               int ncell) {
+  __shared__ int idx[kFillWarps][kOrderMax];
+  const int w = threadIdx.x >> 5;
+  cell_fill_body<IO, FP64>(pos, q, A, cell_start, atoms_v, gfrac_v, gbase, perm, ncell, blockIdx.x * kFillWarps + w,
+                           idx[w]);
+}
+
+// Batched forms: the atom-indexed kernels take 256 atoms per block, the cell
+// fill kFillWarps cells per block (tables `atoms` and `cells`).
+__global__ void __launch_bounds__(256) kb_bin_perm(const BinKArgs<double>* __restrict__ tab,
+                                                   const int* __restrict__ first, int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  const BinKArgs<double>& a = tab[r];
+  bin_perm_body(a.n, a.key, a.rank, a.cell_start, a.perm, blockIdx.x - first[r]);
+}
+
+template <typename IO, bool FP64>
+__global__ void __launch_bounds__(32 * kFillWarps) kb_cell_fill(const BinKArgs<IO>* __restrict__ tab,
+                                                                const int* __restrict__ first, int nrep) {
+  __shared__ int idx[kFillWarps][kOrderMax];
   const int r = batch_rep(first, nrep, blockIdx.x);
   const BinKArgs<IO>& a = tab[r];
-  bin_scatter_body<IO, FP64>(a.pos, a.q, a.n, a.A, a.key, a.rank, a.cell_start, a.atoms, a.gfrac, a.gbase, a.perm,
-                             blockIdx.x - first[r]);
+  const int w = threadIdx.x >> 5;
+  cell_fill_body<IO, FP64>(a.pos, a.q, a.A, a.cell_start, a.atoms, a.gfrac, a.gbase, a.perm, a.ncell,
+                           (blockIdx.x - first[r]) * kFillWarps + w, idx[w]);
 }
 
 // Veltkamp-style split c = hi + lo with hi holding `hb` significant bits.
@@ -458,19 +519,22 @@ cudaError_t launch_binning(Plan& P, int64_t n64, const IO* pos, const IO* q, cud
   k_cell_sums<<<nsc, 1024, 0, st>>>(D.count, P.ncell, D.csum);
   k_cell_scan<<<nsc, 1024, 0, st>>>(D.count, P.ncell, D.csum, D.cell_start);
   if (n > 0) {
+    const unsigned nf = (unsigned)((P.ncell + kFillWarps - 1) / kFillWarps);
+    k_bin_perm<<<nb, 256, 0, st>>>(n, D.key, D.rank, D.cell_start, D.perm);
     if (P.fp64)
-      k_bin_scatter<IO, true><<<nb, 256, 0, st>>>(pos, q, n, A, D.key, D.rank, D.cell_start, D.atoms, D.gfrac,
-                                                  D.gbase, D.perm);
+      k_cell_fill<IO, true><<<nf, 32 * kFillWarps, 0, st>>>(pos, q, A, D.cell_start, D.atoms, D.gfrac, D.gbase,
+                                                            D.perm, P.ncell);
     else
-      k_bin_scatter<IO, false><<<nb, 256, 0, st>>>(pos, q, n, A, D.key, D.rank, D.cell_start, D.atoms, D.gfrac,
-                                                   D.gbase, D.perm);
+      k_cell_fill<IO, false><<<nf, 32 * kFillWarps, 0, st>>>(pos, q, A, D.cell_start, D.atoms, D.gfrac, D.gbase,
+                                                             D.perm, P.ncell);
   }
-  P.launches += 2 + (n > 0 ? 2 : 0);
+  P.launches += 2 + (n > 0 ? 3 : 0);
   return cudaGetLastError();
 }
 
 struct BinBatch {
-  BatchTable<BinKArgs<double>> atoms;  // count and scatter: 256 atoms per block
+  BatchTable<BinKArgs<double>> atoms;  // count and perm: 256 atoms per block
+  BatchTable<BinKArgs<double>> cells;  // cell fill: kFillWarps cells per block
   BatchTable<ScanKArgs> scan;          // cell sums and scan: kScanChunk cells per block
 };
 
@@ -480,7 +544,7 @@ cudaError_t bin_batch_build(const std::vector<BatchRep>& reps, BinBatch** out) {
   if (!b) return cudaErrorMemoryAllocation;
   std::vector<BinKArgs<double>> ka;
   std::vector<ScanKArgs> sa;
-  std::vector<int> kb, sb;
+  std::vector<int> kb, cb, sb;
   for (const BatchRep& r : reps) {
     Plan& P = *r.plan;
     DeviceBuffers& D = P.d;
@@ -498,12 +562,15 @@ cudaError_t bin_batch_build(const std::vector<BatchRep>& reps, BinBatch** out) {
     a.gfrac = D.gfrac;
     a.gbase = D.gbase;
     a.perm = D.perm;
+    a.ncell = P.ncell;
     ka.push_back(a);
     kb.push_back((int)((r.n + 255) / 256));
+    cb.push_back(r.n > 0 ? (P.ncell + kFillWarps - 1) / kFillWarps : 0);
     sa.push_back(ScanKArgs{D.count, P.ncell, D.csum, D.cell_start});
     sb.push_back((P.ncell + kScanChunk - 1) / kScanChunk);
   }
   cudaError_t e = make_table(b->atoms, ka, kb);
+  if (e == cudaSuccess) e = make_table(b->cells, ka, cb);
   if (e == cudaSuccess) e = make_table(b->scan, sa, sb);
   if (e != cudaSuccess) {
     bin_batch_free(b);
@@ -519,13 +586,17 @@ cudaError_t bin_batch_launch(BinBatch* b, cudaStream_t st) {
   kb_cell_sums<<<b->scan.total, 1024, 0, st>>>(b->scan.args, b->scan.first, b->scan.nrep);
   kb_cell_scan<<<b->scan.total, 1024, 0, st>>>(b->scan.args, b->scan.first, b->scan.nrep);
   if (b->atoms.total > 0)
-    kb_bin_scatter<double, false><<<b->atoms.total, 256, 0, st>>>(b->atoms.args, b->atoms.first, b->atoms.nrep);
+    kb_bin_perm<<<b->atoms.total, 256, 0, st>>>(b->atoms.args, b->atoms.first, b->atoms.nrep);
+  if (b->cells.total > 0)
+    kb_cell_fill<double, false><<<b->cells.total, 32 * kFillWarps, 0, st>>>(b->cells.args, b->cells.first,
+                                                                             b->cells.nrep);
   return cudaGetLastError();
 }
 
 void bin_batch_free(BinBatch* b) {
   if (!b) return;
   b->atoms.release();
+  b->cells.release();
   b->scan.release();
   delete b;
 }

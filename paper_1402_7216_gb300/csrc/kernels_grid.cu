@@ -622,9 +622,12 @@ struct LatticeArgs {
   int txn, tyn;  // FP32 kernel: lanes along x (LP outputs each) and along y (two rows each) of a warp's tile
 };
 
+// When several blocks share a brick's input planes (L.nsplit > 1), block
+// part writes its partial sums to up[part][point] and k_lattice_reduce adds
+// the parts in order: no atomics, so the sums are reproducible.
 template <typename T, bool COMP>
-__global__ void __launch_bounds__(128) k_lattice(const T* __restrict__ q, T* __restrict__ u, GridDims G,
-                                                 const Segment<T>* __restrict__ seg,
+__global__ void __launch_bounds__(128) k_lattice(const T* __restrict__ q, T* __restrict__ u, T* __restrict__ up,
+                                                 GridDims G, const Segment<T>* __restrict__ seg,
                                                  const int* __restrict__ seg_start, LatticeArgs L, T scale) {
   constexpr int LBY = 8;
   extern __shared__ unsigned char smem_raw[];
@@ -674,8 +677,9 @@ __global__ void __launch_bounds__(128) k_lattice(const T* __restrict__ q, T* __r
     int x = x0 + tx * LPX + j;
     if (x >= G.n[0]) continue;
     T v = scale * (acc[j] + cmp[j]);
-    if (L.nsplit > 1) atomicAdd(u + ((size_t)zo * G.n[1] + y) * G.n[0] + x, v);
-    else u[((size_t)zo * G.n[1] + y) * G.n[0] + x] = v;
+    const size_t o = ((size_t)zo * G.n[1] + y) * G.n[0] + x;
+    if (L.nsplit > 1) up[(size_t)part * G.n[0] * G.n[1] * G.n[2] + o] = v;
+    else u[o] = v;
   }
 }
 
@@ -757,7 +761,8 @@ __device__ __forceinline__ void stage_plane_async(float* plane, const float* __r
 // TXC, TYC: the warp tile fixed at compile time (the common 32 x 16 tile),
 // or 0 to take it from L (other shapes, batches of uneven grids).
 template <int LP, int TXC, int TYC>
-__device__ __forceinline__ void lattice_f2_body(const float* __restrict__ q, float* __restrict__ u, const GridDims G,
+__device__ __forceinline__ void lattice_f2_body(const float* __restrict__ q, float* __restrict__ u,
+                                                float* __restrict__ up, const GridDims G,
                                                 const Segment2* __restrict__ seg, const int* __restrict__ seg_start,
                                                 const LatticeArgs L, float scale, int bx, int by, int bzs) {
   const int TXN = TXC ? TXC : L.txn, TYN = TYC ? TYC : L.tyn, TW = LP * TXN, LBY = 2 * TYN;  // tile: TW (x) by LBY (y)
@@ -819,18 +824,36 @@ __device__ __forceinline__ void lattice_f2_body(const float* __restrict__ q, flo
       int x = x0 + tx * LP + j;
       if (x >= G.n[0]) continue;
       float v = scale * (r == 0 ? acc[j].x : acc[j].y);
-      if (L.nsplit > 1) atomicAdd(u + ((size_t)zo * G.n[1] + y) * G.n[0] + x, v);
-      else u[((size_t)zo * G.n[1] + y) * G.n[0] + x] = v;
+      const size_t o = ((size_t)zo * G.n[1] + y) * G.n[0] + x;
+      if (L.nsplit > 1) up[(size_t)part * G.n[0] * G.n[1] * G.n[2] + o] = v;  // summed in order by k_lattice_reduce
+      else u[o] = v;
     }
   }
 }
 
 template <int LP, int TXC, int TYC>
 __global__ void __launch_bounds__(32 * kLatticeZ, 6) k_lattice_f2(const float* __restrict__ q, float* __restrict__ u,
-                                                               GridDims G, const Segment2* __restrict__ seg,
+                                                               float* __restrict__ up, GridDims G,
+                                                               const Segment2* __restrict__ seg,
                                                                const int* __restrict__ seg_start, LatticeArgs L,
                                                                float scale) {
-  lattice_f2_body<LP, TXC, TYC>(q, u, G, seg, seg_start, L, scale, blockIdx.x, blockIdx.y, blockIdx.z);
+  lattice_f2_body<LP, TXC, TYC>(q, u, up, G, seg, seg_start, L, scale, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// u[i] = sum over the parts p = 0..nsplit-1 of up[p][i], in that order.
+template <typename T>
+__device__ __forceinline__ void lattice_reduce_body(const T* __restrict__ up, T* __restrict__ u, int64_t np,
+                                                    int nsplit, int64_t i) {
+  if (i >= np) return;
+  T v = up[i];
+  for (int p = 1; p < nsplit; ++p) v += up[(size_t)p * np + i];
+  u[i] = v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_lattice_reduce(const T* __restrict__ up, T* __restrict__ u, int64_t np,
+                                                        int nsplit) {
+  lattice_reduce_body<T>(up, u, np, nsplit, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---- top level: all pairs of the coarsest grid, FP64 ----
@@ -1486,13 +1509,8 @@ void lattice_t(Plan& P, int k, const double* qk64, T* uk, cudaStream_t st) {
   const int TW = f32 ? kLatticeLP * L.txn : LBX, LBY = f32 ? 2 * L.tyn : 8;
   const int LBZb = f32 ? kLatticeZ : LBZ;  // output planes (warps) per block
   L.nbz = (int)blocks_for(G.n[2], LBZb);
-  int64_t bricks = (int64_t)blocks_for(G.n[0], TW) * blocks_for(G.n[1], LBY) * L.nbz;
-  const int64_t target = (int64_t)P.lattice_waves * 152 * 4 / LBZb;
-  L.nsplit = (int)std::min<int64_t>(LBZb + 2 * L.Ez, std::max<int64_t>(1, (target + bricks - 1) / bricks));
-  if (L.nsplit > 1) {
-    cudaMemsetAsync(uk, 0, sizeof(T) * (size_t)grid_points(P, k), st);
-    P.launches += 1;
-  }
+  L.nsplit = lattice_nsplit(P, k);
+  T* up = (T*)P.d.lparts;
   dim3 grid(blocks_for(G.n[0], TW), blocks_for(G.n[1], LBY), L.nbz * L.nsplit);
   int SX = (LBX + 2 * P.E[0] + kSeg) | 1, SY = LBY + 2 * P.E[1];
   // FP32 double-buffers its planes and keeps the window offsets (SXw + SY ints)
@@ -1500,16 +1518,43 @@ void lattice_t(Plan& P, int k, const double* qk64, T* uk, cudaStream_t st) {
   T scale = (T)std::ldexp(1.0, -k);
   if (f32) {
     if (L.txn == 4 && L.tyn == 8)
-      k_lattice_f2<kLatticeLP, 4, 8><<<grid, 32 * kLatticeZ, sm, st>>>((const float*)qk, (float*)uk, G,
+      k_lattice_f2<kLatticeLP, 4, 8><<<grid, 32 * kLatticeZ, sm, st>>>((const float*)qk, (float*)uk, (float*)up, G,
                                                                       (const Segment2*)P.d.seg2, P.d.seg_start, L,
                                                                       (float)scale);
     else
-      k_lattice_f2<kLatticeLP, 0, 0><<<grid, 32 * kLatticeZ, sm, st>>>((const float*)qk, (float*)uk, G,
+      k_lattice_f2<kLatticeLP, 0, 0><<<grid, 32 * kLatticeZ, sm, st>>>((const float*)qk, (float*)uk, (float*)up, G,
                                                                       (const Segment2*)P.d.seg2, P.d.seg_start, L,
                                                                       (float)scale);
   } else {
-    k_lattice<T, false><<<grid, 128, sm, st>>>(qk, uk, G, (const Segment<T>*)P.d.seg, P.d.seg_start, L, scale);
+    k_lattice<T, false><<<grid, 128, sm, st>>>(qk, uk, up, G, (const Segment<T>*)P.d.seg, P.d.seg_start, L, scale);
   }
+  if (L.nsplit > 1) {
+    const int64_t np = grid_points(P, k);
+    k_lattice_reduce<T><<<blocks_for(np, 256), 256, 0, st>>>(up, uk, np, L.nsplit);
+    P.launches += 1;
+  }
+}
+
+// Blocks that share one brick's input planes at level k (several on small
+// levels, so that the launch still fills the GPU: lattice_waves blocks per SM).
+int lattice_nsplit(const Plan& P, int k) {
+  GridDims G = dims_of(P, k);
+  const int TW = P.fp64 ? LBX : kLatticeLP * 4, LBY = P.fp64 ? 8 : 16;
+  const int LBZb = P.fp64 ? LBZ : kLatticeZ;
+  const int64_t bricks = (int64_t)blocks_for(G.n[0], TW) * blocks_for(G.n[1], LBY) * blocks_for(G.n[2], LBZb);
+  const int64_t target = (int64_t)P.lattice_waves * 152 * 4 / LBZb;
+  return (int)std::min<int64_t>(LBZb + 2 * P.E[2], std::max<int64_t>(1, (target + bricks - 1) / bricks));
+}
+
+// Elements of the plan's split-partial buffer: the largest nsplit x points of
+// any level whose lattice cutoff is split.
+int64_t lattice_parts_elems(const Plan& P) {
+  int64_t m = 0;
+  for (int k = 0; k + 1 < P.levels; ++k) {
+    const int ns = lattice_nsplit(P, k);
+    if (ns > 1) m = std::max<int64_t>(m, (int64_t)ns * grid_points(P, k));
+  }
+  return m;
 }
 
 bool lattice_fits(const Plan& P) {
@@ -1739,6 +1784,7 @@ struct AntKArgs {
 struct LatKArgs {
   const float* q;
   float* u;
+  float* up;  // split partials (nsplit > 1)
   GridDims G;
   const Segment2* seg;
   const int* seg_start;
@@ -1758,6 +1804,12 @@ struct EnergyKArgs {
   const double* partial;
   int nb;
   double* energy;
+};
+struct ReduceKArgs {
+  const float* up;
+  float* u;
+  int64_t np;
+  int nsplit;
 };
 
 __device__ __forceinline__ int64_t ew_index(const int* __restrict__ first, int r) {
@@ -1794,6 +1846,13 @@ __global__ void __launch_bounds__(kEw) kb_prolong_axis(const AxisKArgs<float>* _
   prolong_axis_body<float, ORDER>(a.in, a.out, a.A, a.acc, ew_index(first, r));
 }
 
+__global__ void __launch_bounds__(kEw) kb_lattice_reduce(const ReduceKArgs* __restrict__ tab,
+                                                         const int* __restrict__ first, int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  const ReduceKArgs& a = tab[r];
+  lattice_reduce_body<float>(a.up, a.u, a.np, a.nsplit, ew_index(first, r));
+}
+
 __global__ void __launch_bounds__(kEw) kb_f64_to_f32(const ConvKArgs* __restrict__ tab, const int* __restrict__ first,
                                                      int nrep) {
   const int r = batch_rep(first, nrep, blockIdx.x);
@@ -1815,8 +1874,8 @@ __global__ void __launch_bounds__(32 * kLatticeZ, 6) kb_lattice_f2(const LatKArg
   const int r = batch_rep(first, nrep, blockIdx.x);
   const LatKArgs& a = tab[r];
   const int b = blockIdx.x - first[r];
-  lattice_f2_body<kLatticeLP, 0, 0>(a.q, a.u, a.G, a.seg, a.seg_start, a.L, a.scale, b % a.nbx, (b / a.nbx) % a.nby,
-                                    b / (a.nbx * a.nby));
+  lattice_f2_body<kLatticeLP, 0, 0>(a.q, a.u, a.up, a.G, a.seg, a.seg_start, a.L, a.scale, b % a.nbx,
+                                    (b / a.nbx) % a.nby, b / (a.nbx * a.nby));
 }
 
 __global__ void __launch_bounds__(32 * kTopWarps) kb_top(const TopKArgs* __restrict__ tab,
@@ -1864,7 +1923,8 @@ struct GridBatch {
   BatchTable<FxKArgs> fx[2];
   std::vector<BatchTable<AxisKArgs<double>>> restr[2];  // [dir][3 k + axis]
   BatchTable<ConvKArgs> conv[2];
-  BatchTable<ZeroKArgs> zero_u[2];
+  BatchTable<ReduceKArgs> reduce_u[2];  // split lattice partials -> u, in part order
+  float* lparts[2] = {nullptr, nullptr};
   BatchTable<LatKArgs> lattice[2];
   BatchTable<TopKArgs> top[2];
   std::vector<BatchTable<AxisKArgs<float>>> prol[2];  // [dir][3 k + pass]
@@ -1880,7 +1940,8 @@ void grid_batch_free(GridBatch* b) {
     b->fx[d].release();
     for (auto& t : b->restr[d]) t.release();
     b->conv[d].release();
-    b->zero_u[d].release();
+    b->reduce_u[d].release();
+    if (b->lparts[d]) cudaFree(b->lparts[d]);
     b->lattice[d].release();
     b->top[d].release();
     for (auto& t : b->prol[d]) t.release();
@@ -1977,9 +2038,8 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
     // several blocks add into them
     {
       std::vector<ConvKArgs> ca;
-      std::vector<ZeroKArgs> za;
       std::vector<LatKArgs> la;
-      std::vector<int> cb, zb, lb;
+      std::vector<int> cb, lb;
       size_t sm = 0;
       for (const BatchRep& r : reps) {
         Plan& P = *r.plan;
@@ -2009,10 +2069,9 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
           a.nby = (int)blocks_for(G.n[1], LBY);
           a.L.nsplit = 1;  // set below, once the bricks of every replica and level are known
           a.scale = (float)std::ldexp(1.0, -k);
+          a.up = nullptr;
           la.push_back(a);
           lb.push_back(a.nbx * a.nby * a.L.nbz);
-          za.push_back(ZeroKArgs{(unsigned*)u[k], np});
-          zb.push_back(0);
           sm = std::max(sm, lattice_smem(a.L.txn, a.L.tyn, P.E));
         }
       }
@@ -2023,15 +2082,30 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
       for (int b : lb) bricks += b;
       const int64_t target = (int64_t)reps[0].plan->lattice_waves * 152 * 4 / kLatticeZ;
       const int nsplit = (int)std::max<int64_t>(1, (target + bricks - 1) / std::max<int64_t>(bricks, 1));
+      // split grids write their parts to one buffer of the graph, reduced in
+      // part order afterwards (reproducible sums)
+      int64_t elems = 0;
       for (size_t i = 0; i < la.size(); ++i) {
         la[i].L.nsplit = std::min(nsplit, kLatticeZ + 2 * la[i].L.Ez);
         lb[i] *= la[i].L.nsplit;
-        if (la[i].L.nsplit > 1) zb[i] = ew_blocks(za[i].words);
-        else za[i].words = 0;
+        if (la[i].L.nsplit > 1) elems += (int64_t)la[i].L.nsplit * la[i].G.n[0] * la[i].G.n[1] * la[i].G.n[2];
+      }
+      if (elems > 0) chk(cudaMalloc((void**)&B->lparts[dir], sizeof(float) * (size_t)elems));
+      std::vector<ReduceKArgs> ra;
+      std::vector<int> rb;
+      int64_t off = 0;
+      for (size_t i = 0; i < la.size(); ++i) {
+        const int64_t np = (int64_t)la[i].G.n[0] * la[i].G.n[1] * la[i].G.n[2];
+        if (la[i].L.nsplit > 1 && B->lparts[dir]) {
+          la[i].up = B->lparts[dir] + off;
+          ra.push_back(ReduceKArgs{la[i].up, la[i].u, np, la[i].L.nsplit});
+          rb.push_back(ew_blocks(np));
+          off += (int64_t)la[i].L.nsplit * np;
+        }
       }
       chk(make_table(B->conv[dir], ca, cb));
-      chk(make_table(B->zero_u[dir], za, zb));
       chk(make_table(B->lattice[dir], la, lb, sm));
+      chk(make_table(B->reduce_u[dir], ra, rb));
     }
     {  // top level of every replica
       std::vector<TopKArgs> ta;
@@ -2129,8 +2203,8 @@ cudaError_t grid_batch_sweep(GridBatch* B, bool backward, cudaStream_t st) {
     for (int ax = 0; ax < 3; ++ax)
       launch_table(B->restr[d][3 * k + ax], o3 ? kb_restrict_axis<3> : kb_restrict_axis<5>, kEw, st);
   launch_table(B->conv[d], kb_f64_to_f32, kEw, st);
-  launch_table(B->zero_u[d], kb_zero, kEw, st);
   launch_table(B->lattice[d], kb_lattice_f2, 32 * kLatticeZ, st);
+  launch_table(B->reduce_u[d], kb_lattice_reduce, kEw, st);
   launch_table(B->top[d], kb_top, 32 * kTopWarps, st);
   for (int k = B->maxlev - 2; k >= 0; --k)
     for (int i = 0; i < 3; ++i)

@@ -64,6 +64,8 @@ struct DeviceBuffers {
   // adjoint grids
   void* aq[kMaxLevels] = {};
   void* au[kMaxLevels] = {};
+  // lattice partial sums of levels split over several blocks: [nsplit][points] in T
+  void* lparts = nullptr;
   // separable restriction / prolongation temporaries (each as large as level 0, in doubles)
   void* tmp[2] = {nullptr, nullptr};
   // top level (always FP64)
@@ -133,6 +135,10 @@ struct Plan {
   // state
   cudaStream_t last_stream = nullptr;
   int64_t last_n = -1;
+  // id of the forward pass whose per-atom terms the buffers hold (0: none);
+  // every forward, and every replay of a captured forward, takes the next id
+  int64_t forward_id = 0;
+  int64_t next_id = 0;
   int host_status = 0;
   // diagnostics: stage event pairs (pool reused across reads), launch count
   struct StageRec {
@@ -273,6 +279,10 @@ cudaError_t launch_parareal_correct(Plan& P, int64_t n, const double* gnew_pos, 
 // Whether the level stencil's window fits the lattice kernel's shared memory
 // (a stencil of half-width E holds about (2 E)^2 window points per plane).
 bool lattice_fits(const Plan& P);
+// blocks sharing one brick's input planes at level k, and the elements of the
+// plan's split-partial buffer (largest nsplit x points over the split levels)
+int lattice_nsplit(const Plan& P, int k);
+int64_t lattice_parts_elems(const Plan& P);
 cudaError_t launch_lattice(Plan& P, int k, const void* qk, void* uk, cudaStream_t s);
 cudaError_t launch_top(Plan& P, const void* qt, void* ut, cudaStream_t s);
 cudaError_t launch_prolong(Plan& P, int k, const void* coarse, void* fine, cudaStream_t s);

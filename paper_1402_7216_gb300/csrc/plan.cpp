@@ -509,6 +509,7 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
     tsize = std::max(tsize, t);
   }
   for (int i = 0; i < 2; ++i) M(&D.tmp[i], sizeof(double) * tsize);
+  M(&D.lparts, T * (size_t)lattice_parts_elems(*P));
   size_t ntop = (size_t)grid_points(*P, top);
   M((void**)&D.topq, sizeof(double) * ntop);
   M((void**)&D.topu, sizeof(double) * ntop);
@@ -559,7 +560,7 @@ void free_plan(Plan* P) {
   void* ptrs[] = {D.key, D.rank, D.perm, D.count, D.csum, D.cell_start, D.atoms,
                   D.gfrac, D.gbase, D.phis, D.fs, D.glong, D.topK, D.topq, D.topu, D.seg, D.seg2, D.cell_shift, D.cell_rows,
                   D.seg_start, D.cell_off, D.partial, D.scalars, D.md_partial, D.md_step, D.status, D.hpos, D.hq,
-                  D.hphi, D.hforce, D.henergy};
+                  D.hphi, D.hforce, D.henergy, D.lparts};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (D.hstatus) cudaFreeHost(D.hstatus);

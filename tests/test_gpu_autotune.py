@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 import torch
 
-from conftest import rel_rms
+from conftest import assert_atoms, rel_rms
 from synth import make_water_box
 
 pytestmark = pytest.mark.gpu
@@ -35,8 +35,8 @@ def test_autotune_search_result_and_cache(tmp_path, monkeypatch):
         E1, phi1, F1 = tuned.eval(pos, q)
         torch.cuda.synchronize()
         assert abs(E1.item() - E0.item()) <= 1e-6 * abs(E0.item())
-        assert rel_rms(F1.cpu().numpy(), F0.cpu().numpy()) <= 1e-5
-        assert rel_rms(phi1.cpu().numpy(), phi0.cpu().numpy()) <= 1e-6
+        assert_atoms(F1.cpu().numpy(), F0.cpu().numpy(), 1e-5)
+        assert_atoms(phi1.cpu().numpy(), phi0.cpu().numpy(), 1e-6)
 
 
 def test_tuning_fields_are_checked():
@@ -81,4 +81,4 @@ def test_autotune_batch_search_and_cache(tmp_path, monkeypatch):
     E1, _, F1 = MSMBatch(mk(tuning)).eval(pos, q, counts)
     torch.cuda.synchronize()
     assert torch.allclose(E0, E1, rtol=1e-6, atol=0)
-    assert rel_rms(F1.cpu().numpy(), F0.cpu().numpy()) <= 1e-5
+    assert_atoms(F1.cpu().numpy(), F0.cpu().numpy(), 1e-5)

@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import oracle as O
-from conftest import rel_rms
+from conftest import assert_atoms, rel_rms
 from synth import make_water_box
 
 pytestmark = pytest.mark.gpu
@@ -59,17 +59,17 @@ def test_batch_equals_single_evaluations(precision, dev):
         Es, phis, Fs = singles[r].eval(torch.tensor(p, device=dev), torch.tensor(qq, device=dev))
         torch.cuda.synchronize()
         assert abs(E[r].item() - Es.item()) <= tol * abs(Es.item())
-        assert rel_rms(F[o:o + n].cpu().numpy(), Fs.cpu().numpy()) <= (1e-12 if precision == "fp64" else 1e-5)
+        assert_atoms(F[o:o + n].cpu().numpy(), Fs.cpu().numpy(), (1e-12 if precision == "fp64" else 1e-5))
         # adjoint: dL/dq = g phi, dL/dr = -g F
-        assert rel_rms(gq[o:o + n].cpu().numpy(), gE[r].item() * phis.cpu().numpy()) <= 1e-5
-        assert rel_rms(gp[o:o + n].cpu().numpy(), -gE[r].item() * Fs.cpu().numpy()) <= 1e-5
+        assert_atoms(gq[o:o + n].cpu().numpy(), gE[r].item() * phis.cpu().numpy(), 1e-5)
+        assert_atoms(gp[o:o + n].cpu().numpy(), -gE[r].item() * Fs.cpu().numpy(), 1e-5)
         o += n
     # one replica against the oracle
     L, p, qq = reps[2]
     ref = O.msm(O.Params(box=(L,) * 3, periodic=True, cutoff=6.0, spacing=1.5, order=3, split=2), p, qq)
     s = sum(counts[:2])
     assert abs(E[2].item() - ref["E"]) <= (1e-10 if precision == "fp64" else 1e-6) * abs(ref["E"])
-    assert rel_rms(F[s:s + counts[2]].cpu().numpy(), ref["F"]) <= (1e-9 if precision == "fp64" else 1e-5)
+    assert_atoms(F[s:s + counts[2]].cpu().numpy(), ref["F"], (1e-9 if precision == "fp64" else 1e-5))
 
 
 def test_batch_graph_replays(dev):
@@ -98,10 +98,10 @@ def test_batch_graph_replays(dev):
         g.launch()
         torch.cuda.synchronize()
         assert torch.allclose(E, E2, rtol=1e-6, atol=0)
-        assert rel_rms(F.cpu().numpy(), F2.cpu().numpy()) <= 1e-5
-        assert rel_rms(phi.cpu().numpy(), phi2.cpu().numpy()) <= 1e-6
-        assert rel_rms(gp.cpu().numpy(), (-gscale[:, None] * F2).cpu().numpy()) <= 1e-5
-        assert rel_rms(gq.cpu().numpy(), (gscale * phi2).cpu().numpy()) <= 1e-5
+        assert_atoms(F.cpu().numpy(), F2.cpu().numpy(), 1e-5)
+        assert_atoms(phi.cpu().numpy(), phi2.cpu().numpy(), 1e-6)
+        assert_atoms(gp.cpu().numpy(), (-gscale[:, None] * F2).cpu().numpy(), 1e-5)
+        assert_atoms(gq.cpu().numpy(), (gscale * phi2).cpu().numpy(), 1e-5)
         for p in plans:
             p.check_status()
     # one replica of the graph against the oracle
@@ -109,7 +109,7 @@ def test_batch_graph_replays(dev):
     ref = O.msm(O.Params(box=(L,) * 3, periodic=True, cutoff=6.0, spacing=1.5, order=3, split=2), p3, q3)
     s = sum(counts[:3])
     assert abs(E[3].item() - ref["E"]) <= 1e-6 * abs(ref["E"])
-    assert rel_rms(F[s:s + counts[3]].cpu().numpy(), ref["F"]) <= 1e-5
+    assert_atoms(F[s:s + counts[3]].cpu().numpy(), ref["F"], 1e-5)
     # new inputs in the same buffers are picked up by the next replay
     pos.add_(0.37)
     g.launch()
@@ -136,7 +136,7 @@ def test_batch_graph_fallback_fp64(dev):
     E2, _, F2 = MSMBatch(make_plans(reps, "fp64")).eval(pos, q, counts)
     torch.cuda.synchronize()
     assert torch.allclose(E, E2, rtol=1e-12, atol=0)
-    assert rel_rms(F.cpu().numpy(), F2.cpu().numpy()) <= 1e-12
+    assert_atoms(F.cpu().numpy(), F2.cpu().numpy(), 1e-12)
     g.close()
 
 
@@ -207,9 +207,9 @@ def test_replicas64_full_size_graph(dev):
         torch.cuda.synchronize()
         p.check_status()
         assert abs(Eg[r] - E1.item()) <= 1e-6 * abs(E1.item()), r
-        assert rel_rms(Fg[o:o + c], F1.cpu().numpy()) <= 1e-5, r
-        assert rel_rms(gpg[o:o + c], gp1.cpu().numpy()) <= 1e-5, r
-        assert rel_rms(gqg[o:o + c], gq1.cpu().numpy()) <= 1e-5, r
+        assert_atoms(Fg[o:o + c], F1.cpu().numpy(), 1e-5, r)
+        assert_atoms(gpg[o:o + c], gp1.cpu().numpy(), 1e-5, r)
+        assert_atoms(gqg[o:o + c], gq1.cpu().numpy(), 1e-5, r)
         o += c
     off = np.cumsum([0] + counts)
     order = np.argsort(counts)
@@ -218,6 +218,6 @@ def test_replicas64_full_size_graph(dev):
         pick = spatial_subsample(p_r, L, 256, seed=int(r))
         ref = O.msm(O.Params(box=(L,) * 3, periodic=True, cutoff=10.0, spacing=2.0, order=3, split=2), p_r, q_r,
                     targets=pick)
-        assert rel_rms(Fg[off[r]:off[r + 1]][pick], ref["F"]) <= 1e-5, r
-        assert rel_rms(phi.cpu().numpy()[off[r]:off[r + 1]][pick], ref["phi"]) <= 1e-5, r
+        assert_atoms(Fg[off[r]:off[r + 1]][pick], ref["F"], 1e-5, r)
+        assert_atoms(phi.cpu().numpy()[off[r]:off[r + 1]][pick], ref["phi"], 1e-5, r)
     g.close()

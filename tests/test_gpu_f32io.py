@@ -14,7 +14,7 @@ import pytest
 import torch
 
 import oracle as O
-from conftest import rel_rms
+from conftest import assert_atoms, rel_rms
 from synth import make_water_box
 
 pytestmark = pytest.mark.gpu
@@ -56,14 +56,14 @@ def test_f32io_matches_f64io_and_oracle(cfg, precision, dev):
     p.check_status()
     assert phi32.dtype == torch.float32 and F32.dtype == torch.float32 and E32.dtype == torch.float64
     assert abs(E32.item() - E64.item()) <= 1e-7 * abs(E64.item())
-    assert rel_rms(F32.double().cpu().numpy(), F64.cpu().numpy()) <= 1e-6
-    assert rel_rms(phi32.double().cpu().numpy(), phi64.cpu().numpy()) <= 1e-6
+    assert_atoms(F32.double().cpu().numpy(), F64.cpu().numpy(), 1e-6)
+    assert_atoms(phi32.double().cpu().numpy(), phi64.cpu().numpy(), 1e-6)
     b = cfg["box"]
     ref = O.msm(O.Params(box=(b, b, b), periodic=cfg["periodic"], cutoff=cfg["cutoff"], spacing=cfg["spacing"],
                          order=cfg["order"], split=cfg["split"]), pos, q)
     assert abs(E32.item() - ref["E"]) <= 1e-6 * abs(ref["E"])
-    assert rel_rms(F32.double().cpu().numpy(), ref["F"]) <= 1e-5
-    assert rel_rms(phi32.double().cpu().numpy(), ref["phi"]) <= 1e-6
+    assert_atoms(F32.double().cpu().numpy(), ref["F"], 1e-5)
+    assert_atoms(phi32.double().cpu().numpy(), ref["phi"], 1e-6)
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
@@ -79,8 +79,8 @@ def test_backward_f32io_matches_backward(precision, dev):
     gp32, gq32 = p.backward(g)
     torch.cuda.synchronize()
     assert gp32.dtype == torch.float32 and gq32.dtype == torch.float32
-    assert rel_rms(gp32.double().cpu().numpy(), gp64.cpu().numpy()) <= 1e-6
-    assert rel_rms(gq32.double().cpu().numpy(), gq64.cpu().numpy()) <= 1e-6
+    assert_atoms(gp32.double().cpu().numpy(), gp64.cpu().numpy(), 1e-6)
+    assert_atoms(gq32.double().cpu().numpy(), gq64.cpu().numpy(), 1e-6)
 
 
 def test_autograd_with_float32_tensors(dev):
@@ -95,8 +95,8 @@ def test_autograd_with_float32_tensors(dev):
     _, phi, F = p.eval(torch.tensor(pos, device=dev), torch.tensor(q, device=dev))
     torch.cuda.synchronize()
     assert x.grad.dtype == torch.float32 and c.grad.dtype == torch.float32
-    assert rel_rms(-x.grad.double().cpu().numpy(), F.cpu().numpy()) <= 1e-6
-    assert rel_rms(c.grad.double().cpu().numpy(), phi.cpu().numpy()) <= 1e-6
+    assert_atoms(-x.grad.double().cpu().numpy(), F.cpu().numpy(), 1e-6)
+    assert_atoms(c.grad.double().cpu().numpy(), phi.cpu().numpy(), 1e-6)
 
 
 def test_f32io_periodic_images_and_errors(dev):
@@ -117,7 +117,7 @@ def test_f32io_periodic_images_and_errors(dev):
     torch.cuda.synchronize()
     p.check_status()
     assert abs(E1.item() - E0.item()) <= 1e-6 * abs(E0.item())
-    assert rel_rms(F1.double().cpu().numpy(), F0.double().cpu().numpy()) <= 1e-5
+    assert_atoms(F1.double().cpu().numpy(), F0.double().cpu().numpy(), 1e-5)
     # device-detected errors through the FP32 entry point
     ocfg = CFGS[1]
     po = plan(ocfg, "mixed", 8)
