@@ -93,6 +93,9 @@ def lib():
             "orc_short_range_cells": (C.c_int, [P, C.c_int64, _D, _D, _D, _D]),
             "orc_direct_sum": (C.c_double, [C.c_int64, _D, _D, C.c_int64, _I64, _D, _D]),
             "orc_cutoff_sum": (C.c_double, [P, C.c_int64, _D, _D, C.c_int64, _I64, _D, _D]),
+            "orc_wolf_sum": (C.c_double, [P, C.c_double, C.c_int64, _D, _D, C.c_int64, _I64, _D, _D]),
+            "orc_wolf_pair": (C.c_double, [C.c_double, C.c_double, C.c_double, _D]),
+            "orc_wolf_self_coefficient": (C.c_double, [C.c_double, C.c_double]),
             "orc_ewald_sum": (C.c_double, [_D, C.c_double, C.c_int64, _D, _D, _D, _D]),
             "orc_ewald_psi_reg": (C.c_double, [_D, C.c_double, _D]),
             "orc_self_coefficient": (C.c_double, [P]),
@@ -337,6 +340,35 @@ def cutoff_sum(P: Params, pos, q, targets=None):
     if t is None:
         out["E"] = kc * E
     return out
+
+
+def wolf_sum(P: Params, pos, q, alpha, targets=None):
+    """Wolf summation in its damped, shifted-force form (Wolf et al. 1999;
+    force-shifted as in Fennell and Gezelter 2006), one of the coarse
+    functions of the parareal section: pair potential
+    v(r) = erfc(alpha r)/r - erfc(alpha R)/R + c1 (r - R) within R = P.cutoff,
+    self term -c_s q_i^2; returns phi = dE/dq, F = -dE/dr and E (no targets)."""
+    pos, q = _f64(pos, (-1, 3)), _f64(q)
+    t, nt, tp = _targets(targets)
+    cnt = nt if t is not None else len(q)
+    phi, F = np.zeros(cnt), np.zeros((cnt, 3))
+    E = lib().orc_wolf_sum(C.byref(P._c()), float(alpha), len(q), _dp(pos), _dp(q), nt, tp, _dp(phi), _dp(F))
+    kc = P.coulomb_k
+    out = {"phi": kc * phi, "F": kc * F}
+    if t is None:
+        out["E"] = kc * E
+    return out
+
+
+def wolf_pair(alpha, R, r):
+    """(v(r), v'(r)) of the Wolf pair potential above."""
+    d = C.c_double(0.0)
+    v = lib().orc_wolf_pair(float(alpha), float(R), float(r), C.byref(d))
+    return v, d.value
+
+
+def wolf_self_coefficient(alpha, R):
+    return lib().orc_wolf_self_coefficient(float(alpha), float(R))
 
 
 def ewald_sum(box, pos, q, eps_exp=6.0, coulomb_k=1.0):

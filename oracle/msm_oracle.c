@@ -842,6 +842,61 @@ double orc_cutoff_sum(const orc_params* P, int64_t n, const double* pos, const d
   return E;
 }
 
+/* Wolf summation (Wolf, Keblinski, Phillpot and Eggebrecht, J. Chem. Phys. */
+/* 110, 8254 (1999)), one of the coarse functions G the proposal lists for   */
+/* the parareal method (Sec. "Proposed Solutions"; the thesis gives no       */
+/* formula).  Reading taken: the damped, shifted-force form, whose pair      */
+/* potential and its derivative both vanish at the cutoff R = P->cutoff (the */
+/* force-shifted variant of Fennell and Gezelter, J. Chem. Phys. 124, 234104 */
+/* (2006)), so that the forces are the exact gradient of the energy:         */
+/*   v(r) = erfc(alpha r)/r - erfc(alpha R)/R + c1 (r - R),  r < R,          */
+/*   c1   = erfc(alpha R)/R^2 + (2 alpha/sqrt(pi)) exp(-alpha^2 R^2)/R,      */
+/*   E    = 1/2 sum_i sum_{j != i, r_ij < R} q_i q_j v(r_ij) - c_s sum q_i^2, */
+/*   c_s  = erfc(alpha R)/(2R) + alpha/sqrt(pi)   (charge-neutralising shell  */
+/*          and damping self terms of Wolf's sum),                            */
+/*   phi_i = dE/dq_i = sum_j q_j v(r_ij) - 2 c_s q_i,  E = 1/2 sum q_i phi_i, */
+/*   F_i  = -dE/dr_i = -q_i sum_j q_j v'(r_ij) (r_i - r_j)/r_ij.             */
+/* alpha = 0 is the shifted-force Coulomb cutoff.  Minimum image when        */
+/* periodic (R <= L/2).  Brute force over every pair; erfc from the C         */
+/* library.                                                                  */
+double orc_wolf_self_coefficient(double alpha, double R) { return erfc(alpha * R) / (2.0 * R) + alpha / sqrt(M_PI); }
+
+double orc_wolf_pair(double alpha, double R, double r, double* dvdr) {
+  const double two_a_sqrtpi = 2.0 * alpha / sqrt(M_PI);
+  const double c1 = erfc(alpha * R) / (R * R) + two_a_sqrtpi * exp(-alpha * alpha * R * R) / R;
+  if (dvdr) *dvdr = (r < R) ? -erfc(alpha * r) / (r * r) - two_a_sqrtpi * exp(-alpha * alpha * r * r) / r + c1 : 0.0;
+  if (r >= R) return 0.0;
+  return erfc(alpha * r) / r - erfc(alpha * R) / R + c1 * (r - R);
+}
+
+double orc_wolf_sum(const orc_params* P, double alpha, int64_t n, const double* pos, const double* q, int64_t nt,
+                    const int64_t* targets, double* phi, double* F) {
+  int64_t cnt = targets ? nt : n;
+  const double R = P->cutoff, cs = orc_wolf_self_coefficient(alpha, R);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t t = 0; t < cnt; ++t) {
+    int64_t i = targets ? targets[t] : t;
+    double p = 0.0, f[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double d[3] = {pos[3 * i] - pos[3 * j], pos[3 * i + 1] - pos[3 * j + 1],
+                     pos[3 * i + 2] - pos[3 * j + 2]};
+      min_image(P, d);
+      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      if (r >= R) continue;
+      double dv = 0.0;
+      p += q[j] * orc_wolf_pair(alpha, R, r, &dv);
+      for (int c = 0; c < 3; ++c) f[c] -= q[i] * q[j] * dv * d[c] / r;
+    }
+    phi[t] = p - 2.0 * cs * q[i];
+    for (int c = 0; c < 3; ++c) F[3 * t + c] = f[c];
+  }
+  double E = 0.0;
+  if (!targets)
+    for (int64_t i = 0; i < n; ++i) E += 0.5 * q[i] * phi[i];
+  return E;
+}
+
 /* Self term (reading): the grid part of u_i contains atom i's own charge     */
 /* through the smooth kernel, whose value at r = 0 is gamma(0)/a; that       */
 /* constant is removed from phi_i.  Exposed for the assembly step.           */

@@ -490,3 +490,100 @@ def test_cutoff_sum_forces_are_the_energy_gradient_and_scale(oracle):
         checked += 1
     assert checked >= 6
     assert oracle.cutoff_sum(P, pos, 1.7 * q)["E"] == pytest.approx(1.7 ** 2 * ref["E"], rel=1e-13)
+
+
+# ---- Wolf summation (damped, shifted-force form), a coarse function of the
+# parareal section: pinned by the rock-salt Madelung constant, by its alpha = 0
+# limit against the independently pinned cutoff method, by the continuity of
+# the pair potential and force at R, and by finite differences.
+
+def test_wolf_sum_reproduces_madelung_constant(oracle):
+    """Wolf's damped, charge-neutralised sum converges to the lattice sum: on
+    a periodic rock-salt crystal (nearest-neighbour distance 2.82 A, 4,096
+    ions) its energy per ion pair is -M/r0 to 1e-7 at alpha = 0.2/A,
+    R = 20 A and to 1e-6 at alpha = 0.25/A, R = 15 A (M: the textbook
+    Madelung constant)."""
+    pos, q, L = _rocksalt(8, 2.82)
+    M = TEXT["madelung_nacl"]["value"]
+    for alpha, R, tol in [(0.2, 20.0, 1e-7), (0.25, 15.0, 1e-6)]:
+        P = oracle.Params(box=(L,) * 3, periodic=True, cutoff=R, spacing=2.0)
+        out = oracle.wolf_sum(P, pos, q, alpha)
+        assert out["E"] / (len(q) / 2) == pytest.approx(-M / 2.82, rel=tol), (alpha, R)
+        # a perfect crystal: every ion feels no net force
+        assert np.abs(out["F"]).max() < 1e-9
+
+
+def test_wolf_sum_alpha_zero_is_the_shifted_force_cutoff(oracle):
+    """alpha = 0: v(r) = 1/r - 1/R + (r - R)/R^2 within R and the self term
+    q_i^2/(2R).  Built here from the cutoff method's potentials (an
+    independently pinned routine) plus per-pair sums of q_j and q_j r."""
+    pos, q = make_water_box(18.0, 120, 2, 2, seed=81, periodic=True)
+    R = 7.0
+    P = oracle.Params(box=(18.0,) * 3, periodic=True, cutoff=R, spacing=2.0)
+    w = oracle.wolf_sum(P, pos, q, 0.0)
+    c = oracle.cutoff_sum(P, pos, q)
+    d = pos[:, None, :] - pos[None, :, :]
+    d -= 18.0 * np.round(d / 18.0)
+    r = np.sqrt((d ** 2).sum(-1))
+    inside = (r < R) & ~np.eye(len(q), dtype=bool)
+    s0 = (inside * q[None, :]).sum(1)
+    s1 = (inside * q[None, :] * r).sum(1)
+    phi = c["phi"] - s0 / R + (s1 - R * s0) / R ** 2 - q / R
+    np.testing.assert_allclose(w["phi"], phi, rtol=1e-11, atol=1e-12)
+    assert w["E"] == pytest.approx(0.5 * float(np.dot(q, phi)), rel=1e-12)
+
+
+def test_wolf_pair_vanishes_with_its_derivative_at_the_cutoff(oracle):
+    """Shifted force: v(R) = 0 and v'(R) = 0, for several alpha; two charges
+    just inside and just outside R have the same energy (the self terms) and
+    no force; inside, E(r) = -integral_r^R F dr of the oracle's own force."""
+    R = 9.0
+    for alpha in [0.0, 0.15, 0.3]:
+        v, dv = oracle.wolf_pair(alpha, R, R * (1 - 1e-12))
+        assert abs(v) < 1e-12 and abs(dv) < 1e-11
+        P = oracle.Params(box=(40.0,) * 3, periodic=False, cutoff=R, spacing=2.0)
+        q = np.array([0.7, -1.1])
+        Es = []
+        for r in [R * (1 - 1e-9), R * (1 + 1e-9)]:
+            out = oracle.wolf_sum(P, np.array([[10.0, 10.0, 10.0], [10.0 + r, 10.0, 10.0]]), q, alpha)
+            Es.append(out["E"])
+            assert np.abs(out["F"]).max() < 1e-9
+        self_e = -oracle.wolf_self_coefficient(alpha, R) * float((q ** 2).sum())
+        assert Es[0] == pytest.approx(self_e, rel=1e-9) and Es[1] == pytest.approx(self_e, rel=1e-12)
+        # energy at r = 3 from the force integrated (Simpson) from r to R
+        s = np.linspace(3.0, R, 2001)
+        fx = [oracle.wolf_sum(P, np.array([[10.0, 10.0, 10.0], [10.0 + x, 10.0, 10.0]]), q, alpha)["F"][1, 0]
+              for x in s]
+        h = s[1] - s[0]
+        integral = h / 3 * (fx[0] + fx[-1] + 4 * sum(fx[1:-1:2]) + 2 * sum(fx[2:-1:2]))
+        E3 = oracle.wolf_sum(P, np.array([[10.0, 10.0, 10.0], [13.0, 10.0, 10.0]]), q, alpha)["E"]
+        assert E3 - self_e == pytest.approx(integral, rel=1e-9)
+
+
+def test_wolf_sum_gradients_and_accuracy_against_ewald(oracle):
+    """Central finite differences give F = -dE/dr and phi = dE/dq (step 1e-5 A;
+    a pair within the step of R limits the difference to O(step) there); on a neutral
+    periodic water box (alpha = 0.2/A, R = 11 A) the energy is within 1 % and
+    the forces within 5 % rel-RMS of the Ewald sum (the method's own accuracy
+    on a disordered system)."""
+    pos, q = make_water_box(24.0, 450, 3, 3, seed=5, periodic=True)
+    P = oracle.Params(box=(24.0,) * 3, periodic=True, cutoff=11.0, spacing=2.0)
+    ref = oracle.wolf_sum(P, pos, q, 0.2)
+    rng = np.random.default_rng(82)
+    h = 1e-5
+    for i in rng.choice(len(q), 6, replace=False):
+        for c in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, c] += h
+            pm[i, c] -= h
+            fd = -(oracle.wolf_sum(P, pp, q, 0.2)["E"] - oracle.wolf_sum(P, pm, q, 0.2)["E"]) / (2 * h)
+            # v is C1 at R (v'' jumps there): a pair within h of R costs O(h) in the difference
+            assert fd == pytest.approx(ref["F"][i, c], rel=1e-6, abs=1e-7)
+        qp, qm = q.copy(), q.copy()
+        qp[i] += h
+        qm[i] -= h
+        fd = (oracle.wolf_sum(P, pos, qp, 0.2)["E"] - oracle.wolf_sum(P, pos, qm, 0.2)["E"]) / (2 * h)
+        assert fd == pytest.approx(ref["phi"][i], rel=1e-7, abs=1e-9)
+    ew = oracle.ewald_sum((24.0,) * 3, pos, q)
+    assert ref["E"] == pytest.approx(ew["E"], rel=1e-2)
+    assert rel_rms(ref["F"], ew["F"]) < 0.05
