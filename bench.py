@@ -448,6 +448,28 @@ def parareal_timings(args, w, plan, pos, q, n, dev, stream, flush, f_ms, E_mix, 
                 "paper_ratio_estimate": {"value": 60, "basis": "operation counts, MSM a=12, h=2, h*=1 A, C2, "
                                                               "cubic against a 12 A cutoff (no hardware)"},
                 "energy_cutoff_vs_msm_rel": abs(E_c.item() - E_mix) / abs(E_mix)}
+    # Wolf summation (damped, shifted force, alpha = 0.2/A, R = a): the
+    # section's other coarse function, timed the same way
+    alpha_w = 0.2
+    for _ in range(3):
+        plan.wolf_eval(pos, q, alpha_w, out=(E_c, phi_c, F_c))
+    torch.cuda.synchronize()
+    ms_w = []
+    for _ in range(max(3, args.steps // 4)):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.wolf_eval(pos, q, alpha_w, out=(E_c, phi_c, F_c))
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_w.append(a.elapsed_time(b))
+    plan.check_status()
+    w_ms = sorted(ms_w)[len(ms_w) // 2]
+    dFw = float(torch.sqrt(((F_c - F_mix) ** 2).sum() / (F_mix ** 2).sum()))
+    wolf_G = {"metric": "Wolf-summation energy+force evals/sec on the same system (damped shifted force, "
+                                  "alpha = %g /A, R = a = %g A)" % (alpha_w, w.cutoff),
+                        "value": 1e3 / w_ms, "unit": "evals/s", "ms_per_eval": w_ms, "ratio_F_over_G": f_ms / w_ms,
+                        "energy_wolf_vs_msm_rel": abs(E_c.item() - E_mix) / abs(E_mix), "force_rel_rms_vs_F": dFw}
     plan.eval(pos, q)  # leave the plan holding an MSM forward pass
 
     # MSM itself as the coarse propagator (the parareal section's "shorter
@@ -481,7 +503,7 @@ def parareal_timings(args, w, plan, pos, q, n, dev, stream, flush, f_ms, E_mix, 
              "coarser_grid": g_variant(w.cutoff, 4.0 * w.spacing),
              "paper_estimates": "shorter cutoff (6 vs 12 A): at most 7x theoretical speed-up, force error "
                                 "1-5 % from 8 A (Hardy); coarser grid: little gain, the work depends mainly on a"}
-    return cutoff_G, msm_G
+    return cutoff_G, msm_G, wolf_G
 
 
 def md_timing(args, plan, pos, q, n, stream, f_ms):
@@ -556,8 +578,10 @@ def parareal_window_timing(coarse_method="cutoff", coarse_cutoff=10.0, window=8,
     return {"workload": "plasma23k: 23,558 ions (+1 e, unit mass) in the 62.2 A periodic box, a=10, h=2, cubic, "
                         "mixed; kT=0.05 e^2/A",
             "window": window, "fine": "%d steps x dt %g (MSM)" % (steps_fine, dt_fine),
-            "coarse": "%d steps x dt %g (%s, a=%g A)" % (steps_coarse, dt_coarse, "cutoff method" if coarse_method ==
-                                                         "cutoff" else "MSM", coarse_cutoff),
+            "coarse": "%d steps x dt %g (%s, a=%g A)" % (steps_coarse, dt_coarse,
+                                                         {"cutoff": "cutoff method", "msm": "MSM",
+                                                          "wolf": "Wolf summation, alpha = 2.4/a"}[coarse_method],
+                                                         coarse_cutoff),
             "tol_A": tol, "iterations": iters, "change_per_iteration": [[float(x) for x in c] for c in ch],
             "ms_parareal": t_par, "ms_sequential_fine": t_seq, "speedup": t_seq / t_par,
             "final_point_vs_sequential_A": err,
@@ -695,15 +719,16 @@ def main():
     ms_iso, (stage_iso, _, evals_iso), _ = timed(plan, max(3, args.steps // 4), 2, True)
     plan.set_overlap(True)
 
-    cutoff_G = msm_G = md = None
+    cutoff_G = msm_G = wolf_G = md = None
     f_ms = sorted(ms)[len(ms) // 2]
     if not args.no_parareal:
-        cutoff_G, msm_G = parareal_timings(args, w, plan, pos, q, n, dev, stream, flush, f_ms, E_mix, F_mix)
+        cutoff_G, msm_G, wolf_G = parareal_timings(args, w, plan, pos, q, n, dev, stream, flush, f_ms, E_mix, F_mix)
     if not args.no_md:
         md = md_timing(args, plan, pos, q, n, stream, f_ms)
     pr_window = None
     if not args.no_parareal:
-        pr_window = [parareal_window_timing("cutoff", 10.0), parareal_window_timing("msm", 5.0)]
+        pr_window = [parareal_window_timing("cutoff", 10.0), parareal_window_timing("msm", 5.0),
+                     parareal_window_timing("wolf", 10.0)]
 
     # end to end through the host-buffer entry point (pinned host memory):
     # positions and charges in, energy, potentials and forces out, every step
@@ -825,6 +850,7 @@ def main():
         "water4m_forward_adjoint": large,
         "parareal_G_cutoff": cutoff_G,
         "parareal_G_msm": msm_G,
+        "parareal_G_wolf": wolf_G,
         "md_velocity_verlet": md,
         "parareal_window": pr_window,
         "clocks": clk,

@@ -157,15 +157,42 @@ int msm_eval(msm_handle h, int64_t n, const double* pos, const double* q, double
 int msm_cutoff_eval(msm_handle h, int64_t n, const double* pos, const double* q, double* energy,
                     double* phi, double* force, void* cuda_stream);
 
+/* Wolf summation (Wolf, Keblinski, Phillpot and Eggebrecht, J. Chem. Phys.
+ * 110, 8254 (1999)), the other coarse function G the proposal lists for the
+ * parareal method (Sec. "Proposed Solutions"; the thesis prints no formula),
+ * in its damped, shifted-force form (pair potential and force both vanish at
+ * the cutoff; the force-shifted variant of Fennell and Gezelter, J. Chem.
+ * Phys. 124, 234104 (2006)), on this plan's box, cutoff R = a, precision and
+ * coulomb_k:
+ *   v(r)  = erfc(alpha r)/r - erfc(alpha R)/R + c1 (r - R) for r < R, else 0,
+ *           c1 = erfc(alpha R)/R^2 + (2 alpha/sqrt(pi)) exp(-alpha^2 R^2)/R;
+ *   phi_i = k_c [sum_{j != i} q_j v(r_ij) - 2 c_s q_i],
+ *           c_s = erfc(alpha R)/(2R) + alpha/sqrt(pi);
+ *   E = 1/2 sum_i q_i phi_i,  F_i = -dE/dr_i (minimum image when periodic).
+ * alpha >= 0 in inverse length units (alpha = 0: the shifted-force Coulomb
+ * cutoff; about 2.4/R is usual).  Arguments, layouts and errors as msm_eval,
+ * plus INVALID_ARG for a negative or non-finite alpha; uses the plan's
+ * binning and pair kernel (no grid passes).  A following msm_eval_backward
+ * returns NO_FORWARD. */
+int msm_wolf_eval(msm_handle h, double alpha, int64_t n, const double* pos, const double* q, double* energy,
+                  double* phi, double* force, void* cuda_stream);
+
+/* The damping alpha that the MSM_MD_WOLF force of the MD and parareal entry
+ * points uses on this plan (default 2.4 / cutoff).  Host only.
+ * Errors: INVALID_ARG (negative or non-finite alpha). */
+int msm_set_wolf_alpha(msm_handle h, double alpha);
+
 /* Force methods of the MD entry points. */
 #define MSM_MD_MSM 0    /* the MSM evaluation (msm_eval) */
 #define MSM_MD_CUTOFF 1 /* the cutoff method (msm_cutoff_eval) */
+#define MSM_MD_WOLF 2   /* Wolf summation (msm_wolf_eval with the plan's msm_set_wolf_alpha) */
 
 /* Molecular dynamics: nsteps steps of the velocity Verlet scheme (Sec.
  * "Molecular Dynamics", the velocity Verlet equations), each one
  *   v += (dt/2) F inv_mass;  r += dt v  (periodic boxes wrap r into [0, L));
  *   F = force at the new r (method: MSM_MD_MSM, one msm_eval; MSM_MD_CUTOFF,
- *   one msm_cutoff_eval);  v += (dt/2) F inv_mass.
+ *   one msm_cutoff_eval; MSM_MD_WOLF, one msm_wolf_eval with the plan's
+ *   damping);  v += (dt/2) F inv_mass.
  *   pos      [n][3] double, device, in/out: r(t0) in, r(t0 + nsteps dt) out.
  *   vel      [n][3] double, device, in/out.
  *   force    [n][3] double, device, in/out: must hold F(r(t0)) of the same
@@ -208,8 +235,8 @@ int msm_md_run_batch(const msm_handle* plans, int nrep, const int64_t* offsets, 
  * propagations run concurrently, one plan each), the coarse propagator G
  * steps_coarse steps of dt_coarse with the force coarse_method of plan
  * coarse (MSM_MD_CUTOFF: the cutoff method, the section's "Cutoff Method";
- * MSM_MD_MSM: MSM with the coarse plan's own cutoff and grid, the "shorter
- * cutoff" and "coarse grid" options); coarse may be one of fine[].  Each
+ * MSM_MD_WOLF: Wolf summation; MSM_MD_MSM: MSM with the coarse plan's own
+ * cutoff and grid, the "shorter cutoff" and "coarse grid" options); coarse may be one of fine[].  Each
  * propagation starts by evaluating the force at its starting positions.  Iteration 0 is the coarse sweep lambda_{k+1} =
  * G(lambda_k); each further iteration computes F(lambda_k) for every k, then
  * sweeps lambda_{k+1} = G(lambda_k new) + F(lambda_k old) - G(lambda_k old),

@@ -20,7 +20,7 @@ from ._capi import MSMError, MSM_FP64, MSM_MIXED  # noqa: F401
 __all__ = ["MSM", "MSMBatch", "BatchGraph", "MSMEnergy", "MSMError", "MSM_FP64", "MSM_MIXED", "lib", "parareal",
            "MD_METHODS"]
 
-MD_METHODS = {"msm": 0, "cutoff": 1}  # MSM_MD_MSM, MSM_MD_CUTOFF
+MD_METHODS = {"msm": 0, "cutoff": 1, "wolf": 2}  # MSM_MD_MSM, MSM_MD_CUTOFF, MSM_MD_WOLF
 
 
 def lib():
@@ -140,6 +140,30 @@ class MSM:
         self._last_n = None
         return E, phi, F
 
+    def wolf_eval(self, pos, q, alpha, want_phi=True, want_force=True, stream=None, out=None):
+        """msm_wolf_eval: Wolf summation (damped, shifted force, damping alpha,
+        cutoff = this plan's) on float64 device inputs; returns (E, phi or
+        None, F or None)."""
+        pos, q = self._check_inputs(pos, q)
+        if pos.dtype != torch.float64:
+            raise ValueError("wolf_eval takes float64 pos and q")
+        n = pos.shape[0]
+        if out is None:
+            E = torch.empty((), dtype=torch.float64, device=pos.device)
+            phi = torch.empty(n, dtype=torch.float64, device=pos.device) if want_phi else None
+            F = torch.empty((n, 3), dtype=torch.float64, device=pos.device) if want_force else None
+        else:
+            E, phi, F = out
+        rc = lib().msm_wolf_eval(self._h, float(alpha), n, _ptr(pos), _ptr(q), _ptr(E), _ptr(phi), _ptr(F),
+                                 _stream(stream))
+        _capi.check(rc, "msm_wolf_eval")
+        self._last_n = None
+        return E, phi, F
+
+    def set_wolf_alpha(self, alpha):
+        """msm_set_wolf_alpha: the damping of the "wolf" MD force on this plan."""
+        _capi.check(lib().msm_set_wolf_alpha(self._h, float(alpha)), "msm_set_wolf_alpha")
+
     def md_run(self, pos, vel, inv_mass, q, dt, nsteps, force=None, records=True, stream=None, method="msm"):
         """msm_md_run: nsteps velocity Verlet steps around the MSM force
         (method "msm") or the cutoff method's ("cutoff"), in place on float64
@@ -164,6 +188,8 @@ class MSM:
                                  % (name, tuple(shape), pos.device))
         n = pos.shape[0]
         if force is None:
+            if method == "wolf":
+                raise ValueError("md_run with method 'wolf' needs the starting force (wolf_eval with the plan's alpha)")
             ev = self.eval if method == "msm" else self.cutoff_eval
             _, _, force = ev(pos, q, want_phi=False, stream=stream)
         rec = torch.empty((max(int(nsteps), 0), 6), dtype=torch.float64, device=pos.device) if records else None

@@ -39,7 +39,8 @@ class MSMError(RuntimeError):
 
 _lib = None
 _D = C.POINTER(C.c_double)
-EXPORTS = ["msm_create", "msm_create_tuned", "msm_destroy", "msm_query", "msm_geometry", "msm_eval", "msm_cutoff_eval", "msm_md_run", "msm_md_run_batch",
+EXPORTS = ["msm_create", "msm_create_tuned", "msm_destroy", "msm_query", "msm_geometry", "msm_eval", "msm_cutoff_eval",
+           "msm_wolf_eval", "msm_set_wolf_alpha", "msm_md_run", "msm_md_run_batch",
            "msm_parareal_workspace", "msm_parareal",
            "msm_eval_backward", "msm_forward_id",
            "msm_eval_f32io", "msm_eval_backward_f32io",
@@ -73,6 +74,10 @@ def load(path=LIB_PATH):
     L.msm_eval.restype = C.c_int
     L.msm_cutoff_eval.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp]
     L.msm_cutoff_eval.restype = C.c_int
+    L.msm_wolf_eval.argtypes = [vp, C.c_double, C.c_int64, vp, vp, vp, vp, vp, vp]
+    L.msm_wolf_eval.restype = C.c_int
+    L.msm_set_wolf_alpha.argtypes = [vp, C.c_double]
+    L.msm_set_wolf_alpha.restype = C.c_int
     L.msm_md_run.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, C.c_double, C.c_int, C.c_int, vp, vp]
     L.msm_md_run.restype = C.c_int
     L.msm_md_run_batch.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, C.c_double, C.c_int, C.c_int, vp, vp]

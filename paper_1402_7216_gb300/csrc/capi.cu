@@ -229,12 +229,36 @@ int cutoff_forward(Plan& P, int64_t n, const double* pos, const double* q, doubl
   return MSM_OK;
 }
 
-// Energy and force at pos by MSM or by the cutoff method.
+// Wolf summation (damped, shifted force, damping alpha, cutoff a): the plan's
+// binning, the pair kernel with the Wolf pair function, and the assembly with
+// the self term phi_i -= 2 c_s q_i, c_s = erfc(alpha a)/(2a) + alpha/sqrt(pi).
+template <typename IO>
+int wolf_forward(Plan& P, double alpha, int64_t n, const IO* pos, const IO* q, double* energy, IO* phi, IO* force,
+                 cudaStream_t st) {
+  P.last_n = -1;  // the per-atom buffers no longer hold an MSM forward pass
+  P.forward_id = 0;
+  const double a = P.P.cutoff;
+  const double self_c = 2.0 * (std::erfc(alpha * a) / (2.0 * a) + alpha / std::sqrt(M_PI));
+  cudaError_t e = stage(P, MSM_STAGE_BINNING, st, [&] { return launch_binning(P, n, pos, q, st); });
+  if (e == cudaSuccess) e = stage(P, MSM_STAGE_SHORT_RANGE, st, [&] { return launch_wolf_pairs(P, n, alpha, st); });
+  if (e == cudaSuccess)
+    e = stage(P, MSM_STAGE_INTERPOLATION, st,
+              [&] { return launch_cutoff_assemble(P, n, energy, phi, force, st, self_c); });
+  if (e != cudaSuccess) return MSM_ERR_CUDA;
+  P.last_stream = st;
+  P.evals += 1;
+  return MSM_OK;
+}
+
+// Energy and force at pos by MSM, the cutoff method or Wolf summation.
 int md_force(Plan& P, int method, int64_t n, const double* pos, const double* q, double* energy, double* force,
              cudaStream_t st) {
   if (method == MSM_MD_CUTOFF) return cutoff_forward(P, n, pos, q, energy, nullptr, force, st);
+  if (method == MSM_MD_WOLF) return wolf_forward(P, P.wolf_alpha, n, pos, q, energy, (double*)nullptr, force, st);
   return forward(P, n, pos, q, energy, (double*)nullptr, force, st);
 }
+
+bool valid_method(int m) { return m == MSM_MD_MSM || m == MSM_MD_CUTOFF || m == MSM_MD_WOLF; }
 
 // One velocity Verlet step (drift, force, kick).  rec: this step's record or
 // NULL; with a step counter rec is the base of the records and the kick's
@@ -461,10 +485,25 @@ int msm_cutoff_eval(msm_handle h, int64_t n, const double* pos, const double* q,
   return cutoff_forward(P, n, pos, q, energy, phi, force, (cudaStream_t)stream);
 }
 
+int msm_wolf_eval(msm_handle h, double alpha, int64_t n, const double* pos, const double* q, double* energy,
+                  double* phi, double* force, void* stream) {
+  if (!h || n < 0 || !energy || (n > 0 && (!pos || !q)) || !(alpha >= 0.0) || !std::isfinite(alpha))
+    return MSM_ERR_INVALID_ARG;
+  Plan& P = h->p;
+  if (n > P.cap) return MSM_ERR_TOO_MANY_ATOMS;
+  return wolf_forward(P, alpha, n, pos, q, energy, phi, force, (cudaStream_t)stream);
+}
+
+int msm_set_wolf_alpha(msm_handle h, double alpha) {
+  if (!h || !(alpha >= 0.0) || !std::isfinite(alpha)) return MSM_ERR_INVALID_ARG;
+  h->p.wolf_alpha = alpha;
+  return MSM_OK;
+}
+
 int msm_md_run(msm_handle h, int64_t n, double* pos, double* vel, double* force, const double* inv_mass,
                const double* q, double dt, int nsteps, int method, double* records, void* stream) {
   if (!h || n < 0 || nsteps < 0 || !std::isfinite(dt)) return MSM_ERR_INVALID_ARG;
-  if (method != MSM_MD_MSM && method != MSM_MD_CUTOFF) return MSM_ERR_INVALID_ARG;
+  if (!valid_method(method)) return MSM_ERR_INVALID_ARG;
   if (n > 0 && (!pos || !vel || !force || !inv_mass || !q)) return MSM_ERR_INVALID_ARG;
   Plan& P = h->p;
   if (n > P.cap) return MSM_ERR_TOO_MANY_ATOMS;
@@ -492,7 +531,7 @@ int msm_md_run_batch(const msm_handle* plans, int nrep, const int64_t* offsets, 
                      double* records, void* stream) {
   int rc = check_batch(plans, nrep, offsets);
   if (rc != MSM_OK) return rc;
-  if (nsteps < 0 || !std::isfinite(dt) || (method != MSM_MD_MSM && method != MSM_MD_CUTOFF))
+  if (nsteps < 0 || !std::isfinite(dt) || !valid_method(method))
     return MSM_ERR_INVALID_ARG;
   if (offsets[nrep] > 0 && (!pos || !vel || !force || !inv_mass || !q)) return MSM_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -537,7 +576,7 @@ int msm_parareal(const msm_handle* fine, msm_handle coarse, int64_t n, const dou
                  double dt_coarse, int steps_coarse, int coarse_method, int max_iter, double tol, double* lam_pos,
                  double* lam_vel, void* workspace, int* iterations, double* change, void* stream) {
   if (!fine || !coarse || n < 0 || window < 1 || window > MSM_PARAREAL_MAX_WINDOW) return MSM_ERR_INVALID_ARG;
-  if (coarse_method != MSM_MD_MSM && coarse_method != MSM_MD_CUTOFF) return MSM_ERR_INVALID_ARG;
+  if (!valid_method(coarse_method)) return MSM_ERR_INVALID_ARG;
   if (!std::isfinite(dt_fine) || !std::isfinite(dt_coarse) || steps_fine < 0 || steps_coarse < 0 || max_iter < 0 ||
       !(tol >= 0.0) || !std::isfinite(tol))
     return MSM_ERR_INVALID_ARG;

@@ -1704,11 +1704,11 @@ cudaError_t launch_grid_to_double(Plan& P, const void* src, double* dst, int64_t
 template <typename T, typename OUT>
 __global__ void __launch_bounds__(256) k_cutoff_assemble(int64_t n, const int* __restrict__ perm,
                                                          const R4<T>* __restrict__ atoms, const T* __restrict__ phis,
-                                                         const R4<T>* __restrict__ fs, T kc, OUT* __restrict__ phi_out,
+                                                         const R4<T>* __restrict__ fs, T kc, T selfc, OUT* __restrict__ phi_out,
                                                          OUT* __restrict__ force_out, double* __restrict__ partial) {
   double e = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
-    const T p = phis[i];
+    const T p = phis[i] - selfc * atoms[i].w;  // selfc: the method's self term (0 for the cutoff method)
     const R4<T> f = fs[i];
     const int o = perm[i];
     if (phi_out) phi_out[o] = (OUT)(kc * p);
@@ -1724,25 +1724,27 @@ __global__ void __launch_bounds__(256) k_cutoff_assemble(int64_t n, const int* _
 }
 
 template <typename OUT>
-cudaError_t launch_cutoff_assemble(Plan& P, int64_t n, double* energy, OUT* phi, OUT* force, cudaStream_t st) {
+cudaError_t launch_cutoff_assemble(Plan& P, int64_t n, double* energy, OUT* phi, OUT* force, cudaStream_t st,
+                                   double self_c) {
   const int nb = (int)std::max<int64_t>(0, std::min<int64_t>(P.nblk_partial, (n + 255) / 256));
   if (nb > 0) {
     if (P.fp64)
       k_cutoff_assemble<double, OUT><<<nb, 256, 0, st>>>(n, P.d.perm, (const R4<double>*)P.d.atoms,
                                                         (const double*)P.d.phis, (const R4<double>*)P.d.fs,
-                                                        P.P.coulomb_k, phi, force, P.d.partial);
+                                                        P.P.coulomb_k, self_c, phi, force, P.d.partial);
     else
       k_cutoff_assemble<float, OUT><<<nb, 256, 0, st>>>(n, P.d.perm, (const R4<float>*)P.d.atoms,
                                                        (const float*)P.d.phis, (const R4<float>*)P.d.fs,
-                                                       (float)P.P.coulomb_k, phi, force, P.d.partial);
+                                                       (float)P.P.coulomb_k, (float)self_c, phi, force,
+                                                       P.d.partial);
   }
   k_energy_final<<<1, 1024, 0, st>>>(P.d.partial, nb, energy);
   P.launches += 1 + (nb > 0 ? 1 : 0);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_cutoff_assemble<double>(Plan&, int64_t, double*, double*, double*, cudaStream_t);
-template cudaError_t launch_cutoff_assemble<float>(Plan&, int64_t, double*, float*, float*, cudaStream_t);
+template cudaError_t launch_cutoff_assemble<double>(Plan&, int64_t, double*, double*, double*, cudaStream_t, double);
+template cudaError_t launch_cutoff_assemble<float>(Plan&, int64_t, double*, float*, float*, cudaStream_t, double);
 
 // ---- batches: every grid pass as one launch over all replicas ----
 namespace {

@@ -63,6 +63,28 @@ struct PairArgs {
   float a2f, inv_af, inv_a2f, two_inv_a3f;
 };
 
+// Constants of the Wolf pair function (damped, shifted force) with damping
+// alpha and cutoff R = a: v(r) = erfc(alpha r)/r - vR + c1 (r - R),
+// vR = erfc(alpha R)/R, c1 = erfc(alpha R)/R^2 + c2 exp(-alpha^2 R^2)/R,
+// c2 = 2 alpha/sqrt(pi).
+template <typename T>
+struct WolfC {
+  T alpha, alpha2, c2, vR, c1, R;
+};
+
+template <typename T>
+WolfC<T> wolf_consts(double alpha, double R) {
+  const double c2 = 2.0 * alpha / std::sqrt(M_PI);
+  const double vR = std::erfc(alpha * R) / R;
+  const double c1 = std::erfc(alpha * R) / (R * R) + c2 * std::exp(-alpha * alpha * R * R) / R;
+  return WolfC<T>{(T)alpha, (T)(alpha * alpha), (T)c2, (T)vR, (T)c1, (T)R};
+}
+
+__device__ __forceinline__ float d_erfc(float x) { return erfcf(x); }
+__device__ __forceinline__ double d_erfc(double x) { return erfc(x); }
+__device__ __forceinline__ float d_exp(float x) { return expf(x); }
+__device__ __forceinline__ double d_exp(double x) { return exp(x); }
+
 template <typename T>
 struct CutoffConsts;
 template <>
@@ -112,14 +134,16 @@ __device__ __forceinline__ T far_away() { return T(1e18); }
 // Pair functions: K = 0 is MSM's short-range kernel g*(r) = 1/r - gamma(r/a)/a
 // (zero with its derivative at r = a); K = 1 is the plain Coulomb law 1/r of
 // the cutoff method (the parareal section's coarse propagator G), which is
-// not zero at a, so sources beyond the cutoff are masked.
-constexpr int kPairMSM = 0, kPairCutoff = 1;
+// not zero at a, so sources beyond the cutoff are masked; K = 2 is Wolf
+// summation's damped, shifted-force pair potential (another coarse function
+// of that section), masked beyond a as well.
+constexpr int kPairMSM = 0, kPairCutoff = 1, kPairWolf = 2;
 
 // One batch: the lane's target atom against the kBatch queued sources.
 template <typename T, int M, bool COMP, int K = kPairMSM>
 __device__ __forceinline__ void pair_batch(const R4<T>* __restrict__ Q, const R4<T>& ai, T a2, T inv_a,
-                                           T inv_a2, T two_inv_a3, T& phi, T& fx, T& fy, T& fz, T& cphi,
-                                           T& cfx, T& cfy, T& cfz) {
+                                           T inv_a2, T two_inv_a3, const WolfC<T>& W, T& phi, T& fx, T& fy,
+                                           T& fz, T& cphi, T& cfx, T& cfy, T& cfz) {
   T pphi = 0, px = 0, py = 0, pz = 0;
 #pragma unroll 8
   for (int jj = 0; jj < kBatch; ++jj) {
@@ -135,6 +159,11 @@ __device__ __forceinline__ void pair_batch(const R4<T>* __restrict__ Q, const R4
       const T s = r2s * inv_a2;
       pphi += qj * (rinv - Smooth<T, M>::g(s) * inv_a);
       f = qj * (-(rinv * rinv * rinv) - two_inv_a3 * Smooth<T, M>::gs(s));
+    } else if (K == kPairWolf) {  // f = q_j v'(r) / r
+      const T r = r2s * rinv;
+      const T e = d_erfc(W.alpha * r), g = W.c2 * d_exp(-W.alpha2 * r2s);
+      pphi += qj * (e * rinv - W.vR + W.c1 * (r - W.R));
+      f = qj * (W.c1 * rinv - (e * rinv + g) * rinv * rinv);
     } else {
       pphi += qj * rinv;
       f = -qj * (rinv * rinv * rinv);
@@ -164,7 +193,7 @@ __device__ __forceinline__ void pair_batch(const R4<T>* __restrict__ Q, const R4
 template <typename T, int M, bool COMP, int K>
 __global__ void __launch_bounds__(32 * kWarps) k_short_range(
     const R4<T>* __restrict__ atoms, const int* __restrict__ cell_start,
-    const int4* __restrict__ offs, const R4<T>* __restrict__ shifts, PairArgs A, int ncell,
+    const int4* __restrict__ offs, const R4<T>* __restrict__ shifts, PairArgs A, WolfC<T> W, int ncell,
     T* __restrict__ phis, R4<T>* __restrict__ fs) {
   __shared__ R4<T> queue[kWarps][2 * kBatch];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -225,7 +254,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_short_range(
         qn += __popc(bal);
         __syncwarp();
         if (qn >= kBatch) {
-          pair_batch<T, M, COMP, K>(Q, ai, a2, inv_a, inv_a2, two_inv_a3, phi, fx, fy, fz, cphi, cfx, cfy, cfz);
+          pair_batch<T, M, COMP, K>(Q, ai, a2, inv_a, inv_a2, two_inv_a3, W, phi, fx, fy, fz, cphi, cfx, cfy, cfz);
           __syncwarp();
           if (lane < qn - kBatch) Q[lane] = Q[kBatch + lane];
           qn -= kBatch;
@@ -236,7 +265,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_short_range(
     if (qn > 0) {  // last partial batch, padded with far-away zero charges
       if (lane >= qn) Q[lane] = dummy;
       __syncwarp();
-      pair_batch<T, M, COMP, K>(Q, ai, a2, inv_a, inv_a2, two_inv_a3, phi, fx, fy, fz, cphi, cfx, cfy, cfz);
+      pair_batch<T, M, COMP, K>(Q, ai, a2, inv_a, inv_a2, two_inv_a3, W, phi, fx, fy, fz, cphi, cfx, cfy, cfz);
       __syncwarp();
     }
     if (iv) {
@@ -287,8 +316,9 @@ __device__ __forceinline__ float2 poly_d(const PairCoef& C, float2 r2) {
 
 template <int M, int K>
 __device__ __forceinline__ void pair_batch_f2(const QueueF& Q, float2 nax, float2 nay, float2 naz, float a2,
-                                              const PairCoef& C, float& phi, float& px, float& py, float& pz,
-                                              float& cphi, float& cpx, float& cpy, float& cpz) {
+                                              const PairCoef& C, const WolfC<float>& W, float& phi, float& px,
+                                              float& py, float& pz, float& cphi, float& cpx, float& cpy,
+                                              float& cpz) {
   float2 sphi = make_float2(0.f, 0.f), sx = sphi, sy = sphi, sz = sphi;
   // sources jj..jj+3 load as one float4 per coordinate (two packed halves)
 #pragma unroll
@@ -317,6 +347,20 @@ __device__ __forceinline__ void pair_batch_f2(const QueueF& Q, float2 nax, float
         const float2 pot = __fadd2_rn(rinv, poly_g<M>(C, r2));  // G holds -gamma coefficients
         sphi = __ffma2_rn(qj, pot, sphi);
         fp = __fmul2_rn(__ffma2_rn(__fmul2_rn(rinv, rinv), rinv, poly_d<M>(C, r2)), qj);
+      } else if (K == kPairWolf) {  // damped shifted force within the cutoff, one source at a time
+        float pv[2], fv[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float x2 = c ? r2.y : r2.x;
+          const bool ok = x2 < a2;
+          const float r2s = ok ? x2 : a2, q = ok ? (c ? bq.y : bq.x) : 0.f;
+          const float ri = fast_rsqrt(r2s), r = r2s * ri;
+          const float e = erfcf(W.alpha * r), g = W.c2 * expf(-W.alpha2 * r2s);
+          pv[c] = q * (e * ri - W.vR + W.c1 * (r - W.R));
+          fv[c] = q * ((e * ri + g) * ri * ri - W.c1 * ri);  // -v'(r)/r, the sign this kernel sums with
+        }
+        sphi = __fadd2_rn(sphi, make_float2(pv[0], pv[1]));
+        fp = make_float2(fv[0], fv[1]);
       } else {  // plain Coulomb within the cutoff (sources are never at r = 0 outside the home cell)
         const float2 qj = make_float2(r2.x < a2 ? bq.x : 0.f, r2.y < a2 ? bq.y : 0.f);
         const float2 rinv = make_float2(fast_rsqrt(r2.x), fast_rsqrt(r2.y));
@@ -360,6 +404,7 @@ struct PairKArgs {
   int nrows;
   PairArgs A;
   PairCoef C;
+  WolfC<float> W;
   float cwx, cwy, cwz;
   int ncell;
   float* phis;
@@ -374,6 +419,7 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
   const int nrows = K.nrows, ncell = K.ncell;
   const PairArgs& A = K.A;
   const PairCoef C = K.C;
+  const WolfC<float> W = K.W;
   const float cwx = K.cwx, cwy = K.cwy, cwz = K.cwz;
   float* __restrict__ phis = K.phis;
   R4<float>* __restrict__ fs = K.fs;
@@ -487,8 +533,8 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
       home[warp][lane] = (j < i1) ? atoms[j] : R4<float>{FAR, FAR, FAR, 0.f};
       __syncwarp();
       float hphi = 0.f, hx_ = 0.f, hy_ = 0.f, hz_ = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-      pair_batch<float, M, true, KIND>(home[warp], ai, a2, inv_a, inv_a2s, two_inv_a3, hphi, hx_, hy_, hz_, c0, c1,
-                                       c2, c3);
+      pair_batch<float, M, true, KIND>(home[warp], ai, a2, inv_a, inv_a2s, two_inv_a3, W, hphi, hx_, hy_, hz_, c0,
+                                       c1, c2, c3);
       two_sum_add(phi, cphi, hphi + c0);
       two_sum_add(px, cpx, hx_ + c1);
       two_sum_add(py, cpy, hy_ + c2);
@@ -543,7 +589,7 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
       qn += __popc(bal);
       __syncwarp();
       if (qn >= kBatch) {
-        pair_batch_f2<M, KIND>(Q, nax, nay, naz, a2, C, phi, px, py, pz, cphi, cpx, cpy, cpz);
+        pair_batch_f2<M, KIND>(Q, nax, nay, naz, a2, C, W, phi, px, py, pz, cphi, cpx, cpy, cpz);
         __syncwarp();
         if (lane < qn - kBatch) {
           Q.x[lane] = Q.x[kBatch + lane];
@@ -563,7 +609,7 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
         Q.q[lane] = 0.f;
       }
       __syncwarp();
-      pair_batch_f2<M, KIND>(Q, nax, nay, naz, a2, C, phi, px, py, pz, cphi, cpx, cpy, cpz);
+      pair_batch_f2<M, KIND>(Q, nax, nay, naz, a2, C, W, phi, px, py, pz, cphi, cpx, cpy, cpz);
       __syncwarp();
     }
     if (iv) {
@@ -587,8 +633,9 @@ __global__ void __launch_bounds__(32 * kWarps, 6) kb_short_range_f2(const PairKA
 }
 
 template <typename T, bool COMP, int K>
-void launch_t(Plan& P, cudaStream_t st) {
+void launch_t(Plan& P, cudaStream_t st, double alpha = 0.0) {
   PairArgs A = pair_args(P);
+  const WolfC<T> W = wolf_consts<T>(alpha, P.P.cutoff);
   int blocks = (P.ncell + kWarps - 1) / kWarps;
   auto* at = (const R4<T>*)P.d.atoms;
   auto* sh = (const R4<T>*)P.d.cell_shift;
@@ -596,15 +643,15 @@ void launch_t(Plan& P, cudaStream_t st) {
   auto* fs = (R4<T>*)P.d.fs;
   switch (P.P.splitting) {
     case 1:
-      k_short_range<T, 1, COMP, K><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A,
+      k_short_range<T, 1, COMP, K><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A, W,
                                                                P.ncell, ph, fs);
       break;
     case 2:
-      k_short_range<T, 2, COMP, K><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A,
+      k_short_range<T, 2, COMP, K><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A, W,
                                                                P.ncell, ph, fs);
       break;
     default:
-      k_short_range<T, 3, COMP, K><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A,
+      k_short_range<T, 3, COMP, K><<<blocks, 32 * kWarps, 0, st>>>(at, P.d.cell_start, P.d.cell_off, sh, A, W,
                                                                P.ncell, ph, fs);
       break;
   }
@@ -615,6 +662,7 @@ void launch_t(Plan& P, cudaStream_t st) {
 PairKArgs pair_kargs(const Plan& P) {
   PairKArgs K;
   K.A = pair_args(P);
+  K.W = wolf_consts<float>(0.0, P.P.cutoff);
   K.atoms = (const R4<float>*)P.d.atoms;
   K.cell_start = P.d.cell_start;
   K.rows = P.d.cell_rows;
@@ -642,10 +690,12 @@ PairKArgs pair_kargs(const Plan& P) {
 }
 
 template <int KIND>
-void launch_f2(Plan& P, cudaStream_t st) {
-  const PairKArgs K = pair_kargs(P);
+void launch_f2(Plan& P, cudaStream_t st, double alpha = 0.0) {
+  PairKArgs K = pair_kargs(P);
+  K.W = wolf_consts<float>(alpha, P.P.cutoff);
   const int blocks = (P.ncell + kWarps - 1) / kWarps;
   if (KIND == kPairCutoff) k_short_range_f2<2, kPairCutoff><<<blocks, 32 * kWarps, 0, st>>>(K);  // M unused
+  else if (KIND == kPairWolf) k_short_range_f2<2, kPairWolf><<<blocks, 32 * kWarps, 0, st>>>(K);
   else if (P.P.splitting == 1) k_short_range_f2<1, kPairMSM><<<blocks, 32 * kWarps, 0, st>>>(K);
   else if (P.P.splitting == 2) k_short_range_f2<2, kPairMSM><<<blocks, 32 * kWarps, 0, st>>>(K);
   else k_short_range_f2<3, kPairMSM><<<blocks, 32 * kWarps, 0, st>>>(K);
@@ -663,6 +713,14 @@ cudaError_t launch_cutoff_pairs(Plan& P, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (P.fp64) launch_t<double, false, kPairCutoff>(P, st);
   else launch_f2<kPairCutoff>(P, st);
+  P.launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wolf_pairs(Plan& P, int64_t n, double alpha, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (P.fp64) launch_t<double, false, kPairWolf>(P, st, alpha);
+  else launch_f2<kPairWolf>(P, st, alpha);
   P.launches += 1;
   return cudaGetLastError();
 }

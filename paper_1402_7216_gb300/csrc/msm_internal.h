@@ -139,6 +139,8 @@ struct Plan {
   // every forward, and every replay of a captured forward, takes the next id
   int64_t forward_id = 0;
   int64_t next_id = 0;
+  // damping of Wolf summation when it is the MD force (msm_set_wolf_alpha)
+  double wolf_alpha = 0.0;
   int host_status = 0;
   // diagnostics: stage event pairs (pool reused across reads), launch count
   struct StageRec {
@@ -251,11 +253,14 @@ template <typename IO>  // IO = double or float (caller's position and charge ty
 cudaError_t launch_binning(Plan& P, int64_t n, const IO* pos, const IO* q, cudaStream_t s);
 // short-range pair sums (phis, fs.xyz)
 cudaError_t launch_short_range(Plan& P, int64_t n, cudaStream_t s);
-// the cutoff method: Coulomb pair sums within the cutoff (phis, fs.xyz), and
-// the assembly of phi, F and E from them
+// the cutoff method: Coulomb pair sums within the cutoff (phis, fs.xyz); Wolf
+// summation: its damped shifted-force pair sums; and the assembly of phi
+// (minus self_c q_i: 0 for the cutoff method, 2 c_s for Wolf), F and E
 cudaError_t launch_cutoff_pairs(Plan& P, int64_t n, cudaStream_t s);
+cudaError_t launch_wolf_pairs(Plan& P, int64_t n, double alpha, cudaStream_t s);
 template <typename OUT>
-cudaError_t launch_cutoff_assemble(Plan& P, int64_t n, double* energy, OUT* phi, OUT* force, cudaStream_t s);
+cudaError_t launch_cutoff_assemble(Plan& P, int64_t n, double* energy, OUT* phi, OUT* force, cudaStream_t s,
+                                   double self_c = 0.0);
 // grid passes: anterpolation (charges q_i * scale, scale from device or 1)
 cudaError_t launch_anterpolate(Plan& P, int64_t n, void* grid0, const double* dscale, double factor,
                                cudaStream_t s);

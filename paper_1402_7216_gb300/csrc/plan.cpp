@@ -287,6 +287,7 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   if (tune) TU = *tune;
   const double fill = TU.cell_fill > 0 ? TU.cell_fill : 24.0;
   P->lattice_waves = TU.lattice_waves > 0 ? TU.lattice_waves : 8;
+  P->wolf_alpha = 2.4 / p.cutoff;  // alpha R = 2.4 (0.2 per length unit at R = 12) until msm_set_wolf_alpha
   for (int d = 0; d < 3; ++d)
     if (!(p.box[d] > 0.0) || !std::isfinite(p.box[d])) return MSM_ERR_INVALID_ARG;
   if (!(p.cutoff > 0.0) || !(p.spacing > 0.0) || !std::isfinite(p.cutoff) || !std::isfinite(p.spacing))
