@@ -266,8 +266,16 @@ def bench_large(dev, args):
     torch.cuda.synchronize()
     torch.cuda.reset_peak_memory_stats(dev)
     free0 = torch.cuda.mem_get_info(dev)[0]
+    # the lattice warp tile of the finest grid from the project's autotuner,
+    # timed on forward + adjoint (the lattice is most of both at this size)
+    from paper_1402_7216_gb300.autotune import TILES, autotune
+    tuning, tune_ms = autotune(pos, q, w.box, True, w.cutoff, w.spacing, levels=w.levels, order=w.order,
+                               splitting=w.split, precision="mixed", reps=3, search=[("lattice_tile", TILES)],
+                               backward=True)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(dev)[0]
     plan = MSM(box=w.box, periodic=True, cutoff=w.cutoff, spacing=w.spacing, levels=w.levels, order=w.order,
-               splitting=w.split, precision="mixed", max_atoms=n)
+               splitting=w.split, precision="mixed", max_atoms=n, tuning=tuning)
     workspace = free0 - torch.cuda.mem_get_info(dev)[0]
     E = torch.empty((), dtype=torch.float64, device=dev)
     phi = torch.empty(n, dtype=torch.float64, device=dev)
@@ -314,6 +322,8 @@ def bench_large(dev, args):
             "unit": "evals/s", "forward_ms": fm, "backward_ms": bm, "steps": steps,
             "device_memory_GB": {"plan_workspace": workspace / 1e9, "caller_tensors_peak": peak_torch / 1e9,
                                  "budget": 180.0},
+            "tuning": tuning, "autotune_ms": {k: (round(v, 3) if isinstance(v, float) else v)
+                                              for k, v in tune_ms.items()},
             "mixed_vs_fp64_gpu": err,
             "timing": "CUDA events around each forward and each adjoint (inputs and grids exceed L2)"}
 
@@ -339,11 +349,12 @@ def bench_batch(dev, args, n_rep=64):
     n = sum(counts)
     pos = torch.tensor(np.vstack([p for (_, p, _) in reps]), device=dev)
     q = torch.tensor(np.concatenate([qq for (_, _, qq) in reps]), device=dev)
-    # tile shapes shared by the replicas, from the project's autotuner (timed on the batch graph)
-    tuning, tune_ms = autotune_batch([L for (L, _, _) in reps], pos, q, counts, cutoff=10.0, spacing=2.0,
-                                     order=3, splitting=2, reps=3)
+    # tile shapes from the project's autotuner (timed on the batch graph): the
+    # fields every replica shares, and a lattice tile per finest-grid size
+    tunings, tuning, tune_ms = autotune_batch([L for (L, _, _) in reps], pos, q, counts, cutoff=10.0, spacing=2.0,
+                                              order=3, splitting=2, reps=3)
     plans = [MSM(box=L, periodic=True, cutoff=10.0, spacing=2.0, order=3, splitting=2, precision="mixed",
-                 max_atoms=len(q), tuning=tuning) for (L, _, q) in reps]
+                 max_atoms=len(q), tuning=t) for (L, _, q), t in zip(reps, tunings)]
     E = torch.zeros(n_rep, dtype=torch.float64, device=dev)
     F = torch.zeros((n, 3), dtype=torch.float64, device=dev)
     phi = torch.zeros(n, dtype=torch.float64, device=dev)

@@ -88,12 +88,27 @@ typedef struct {
  *                 keep the largest patch that fits)
  *   lattice_waves blocks per SM the lattice cutoff aims for when it splits the
  *                 stencil planes of a small level over several blocks (default 8)
- * Ranges: cell_fill 0..256, patch_cells 0..4, lattice_waves 0..64; anything
- * else is INVALID_ARG (checked on the host before any device call). */
+ *   pair_targets  mixed-precision pair kernel: 32 culls sources against
+ *                 the bounding box of up to 32 atoms of a cell, one target
+ *                 per lane (the default); 8 against clusters of 8 spatially
+ *                 consecutive atoms of a cell (fewer pairs, more culling
+ *                 work: measured slower on water)
+ *   lattice_txn, lattice_tyn  warp tile of the mixed-precision lattice
+ *                 kernel: txn lanes of 8 x outputs by tyn lanes of two rows,
+ *                 txn * tyn <= 32 (default 4 x 8 on a single system; batched
+ *                 launches pick a tile per level size); both 0 or both set
+ * Ranges: cell_fill 0..256, patch_cells 0..4, lattice_waves 0..64,
+ * pair_targets 0, 8 or 32, lattice_txn and lattice_tyn 0..32 with
+ * txn * tyn <= 32 and a staging window that fits shared memory; anything else
+ * is INVALID_ARG (checked on the host before any device call; the window
+ * check, which needs the plan's stencil, at msm_create_tuned). */
 typedef struct {
   int cell_fill;
   int patch_cells;
   int lattice_waves;
+  int pair_targets;
+  int lattice_txn;
+  int lattice_tyn;
 } msm_tuning;
 
 /* Builds a plan: validates params, fixes the grid geometry, builds the

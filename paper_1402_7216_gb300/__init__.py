@@ -43,7 +43,8 @@ class MSM:
     levels: l (0 = automatic); order: 3 cubic / 5 quintic; splitting: Taylor
     order m of gamma (1, 2, 3); precision: "fp64" or "mixed"; coulomb_k:
     prefactor; max_atoms: capacity of the workspace; tuning: optional tile
-    shapes {"cell_fill", "patch_cells", "lattice_waves"} (see autotune.py).
+    shapes {"cell_fill", "patch_cells", "lattice_waves", "pair_targets", "lattice_txn",
+    "lattice_tyn"} (see autotune.py and msm_tuning in include/msm.h).
     """
 
     def __init__(self, box, periodic, cutoff, spacing, levels=0, order=3, splitting=2,
@@ -67,8 +68,7 @@ class MSM:
         self._h = C.c_void_p()
         self._last_n = None
         self.tuning = dict(tuning or {})
-        t = _capi.MSMTuning(int(self.tuning.get("cell_fill", 0)), int(self.tuning.get("patch_cells", 0)),
-                            int(self.tuning.get("lattice_waves", 0)))
+        t = _capi.MSMTuning(*[int(self.tuning.get(k, 0)) for k, _ in _capi.MSMTuning._fields_])
         _capi.check(L.msm_create_tuned(C.byref(p), C.byref(t), C.byref(self._h)), "msm_create_tuned")
         heff = (C.c_double * 3)()
         nl = C.c_int()

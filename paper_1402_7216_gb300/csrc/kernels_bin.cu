@@ -8,17 +8,20 @@
 //   k_cell_scan    exclusive scan -> cell_start; resets the counts to zero
 //                  for the next evaluation
 //   k_bin_perm     perm[cell_start + rank] = atom index
-//   k_cell_fill    one warp per cell: puts the cell's atoms in input-index
-//                  order (each atom's final rank is the number of the cell's
-//                  atoms with a smaller index) and writes their sorted
-//                  records: cell-local coordinates for the pair sums,
-//                  fractional level-0 grid coordinates and the first support
-//                  index for the grid passes, and the permutation back to
-//                  input order.
+//   k_cell_fill    one warp per cell: orders the cell's atoms by the key
+//                  (sub-cell, input index) -- the sub-cell is the atom's
+//                  place on a 4 x 4 x 4 lattice inside the cell, taken in
+//                  Morton order, so that runs of consecutive atoms are
+//                  spatially compact (the pair kernel's target clusters);
+//                  each atom's final rank is the number of the cell's atoms
+//                  with a smaller key -- and writes their sorted records:
+//                  cell-local coordinates for the pair sums, fractional
+//                  level-0 grid coordinates and the first support index for
+//                  the grid passes, and the permutation back to input order.
 // The provisional ranks follow the order in which the atomics were served;
 // the reordering makes the sorted order a function of the input alone, so
 // every later pass sums in the same order on every run and the results are
-// bit-reproducible.  A cell of more than kOrderMax atoms (over 40 times the
+// bit-reproducible.  A cell of more than kOrderMax atoms (over 20 times the
 // default cell fill) keeps the atomic order: still correct, only its
 // rounding may vary between runs.
 //
@@ -44,7 +47,7 @@ namespace {
 
 constexpr int kScanChunk = 4096;  // cells per block of the cell scan (1024 threads x 4)
 constexpr int kFillWarps = 8;     // cells per block of k_cell_fill
-constexpr int kOrderMax = 1024;   // largest cell that k_cell_fill puts in index order
+constexpr int kOrderMax = 512;    // largest cell that k_cell_fill puts in key order
 
 // Folds x into [0, L) (multiplying by the reciprocal: FP64 division is slow).
 __device__ __forceinline__ double fold(double x, double L, double inv_L) {
@@ -362,6 +365,29 @@ __global__ void __launch_bounds__(256) k_bin_perm(int n, const int* __restrict__
   bin_perm_body(n, key_in, rank_in, cell_start, perm, blockIdx.x);
 }
 
+// Place of atom i on a 4 x 4 x 4 lattice inside its cell `key`, as a Morton
+// code (0..63), from its cell-local coordinates (the same arithmetic as the
+// records below).
+template <typename IO, bool FP64>
+__device__ __forceinline__ int subcell_code(const IO* __restrict__ pos, const BinArgs& A, int key, int i) {
+  const int kc[3] = {key % A.nc[0], (key / A.nc[0]) % A.nc[1], key / (A.nc[0] * A.nc[1])};
+  int code = 0, bad = 0;
+  for (int d = 0; d < 3; ++d) {
+    int sd;
+    if (FP64) {
+      const double v = prep_fp64(pos[3 * (size_t)i + d], A, d, bad);
+      sd = (int)((v - kc[d] * A.cw[d]) * (4.0 * A.inv_cw[d]));
+    } else {
+      float hi, lo;
+      prep_mixed(pos[3 * (size_t)i + d], A, d, bad, hi, lo);
+      sd = (int)(offset_from(hi, lo, kc[d], A.cw_hi[d], A.cw_lo[d]) * (4.f * A.inv_cwf[d]));
+    }
+    sd = min(max(sd, 0), 3);
+    code |= ((sd & 1) << d) | (((sd >> 1) & 1) << (3 + d));
+  }
+  return code;
+}
+
 // The sorted records of atom i at slot s of cell `key` (the atom's cell as
 // k_bin_count found it: the same functions on the same input).
 template <typename IO, bool FP64>
@@ -398,25 +424,28 @@ __device__ __forceinline__ void write_records(const IO* __restrict__ pos, const 
 }
 
 // One warp per cell: the cell's atoms (perm, in provisional order) are put in
-// index order and their records written.  idx: the warp's kOrderMax ints of
-// shared memory.
+// (sub-cell, index) order and their records written.  idx: the warp's
+// kOrderMax keys in shared memory.
 template <typename IO, bool FP64>
 __device__ __forceinline__ void cell_fill_body(const IO* __restrict__ pos, const IO* __restrict__ q,
                                                const BinArgs& A, const int* __restrict__ cell_start,
                                                void* __restrict__ atoms_v, void* __restrict__ gfrac_v,
                                                int4* __restrict__ gbase, int* __restrict__ perm, int ncell, int cell,
-                                               int* __restrict__ idx) {
+                                               long long* __restrict__ idx) {
   if (cell >= ncell) return;  // warp-uniform
   const int lane = threadIdx.x & 31;
   const int s0 = cell_start[cell], m = cell_start[cell + 1] - s0;
   if (m <= kOrderMax) {
-    for (int t = lane; t < m; t += 32) idx[t] = perm[s0 + t];
+    for (int t = lane; t < m; t += 32) {
+      const int i = perm[s0 + t];
+      idx[t] = ((long long)subcell_code<IO, FP64>(pos, A, cell, i) << 32) | (long long)i;
+    }
     __syncwarp();
     for (int t = lane; t < m; t += 32) {
-      const int i = idx[t];
+      const long long k = idx[t];
       int r = 0;
-      for (int j = 0; j < m; ++j) r += idx[j] < i;  // indices are distinct: r is a permutation of 0..m-1
-      write_records<IO, FP64>(pos, q, A, cell, i, s0 + r, atoms_v, gfrac_v, gbase, perm);
+      for (int j = 0; j < m; ++j) r += idx[j] < k;  // keys are distinct: r is a permutation of 0..m-1
+      write_records<IO, FP64>(pos, q, A, cell, (int)(k & 0xffffffffll), s0 + r, atoms_v, gfrac_v, gbase, perm);
     }
     __syncwarp();
   } else {
@@ -431,7 +460,7 @@ __global__ void __launch_bounds__(32 * kFillWarps) k_cell_fill(const IO* __restr
                                                                void* __restrict__ atoms_v, void* __restrict__ gfrac_v,
                                                                int4* __restrict__ gbase, int* __restrict__ perm,
                                                                int ncell) {
-  __shared__ int idx[kFillWarps][kOrderMax];
+  __shared__ long long idx[kFillWarps][kOrderMax];
   const int w = threadIdx.x >> 5;
   cell_fill_body<IO, FP64>(pos, q, A, cell_start, atoms_v, gfrac_v, gbase, perm, ncell, blockIdx.x * kFillWarps + w,
                            idx[w]);
@@ -449,7 +478,7 @@ __global__ void __launch_bounds__(256) kb_bin_perm(const BinKArgs<double>* __res
 template <typename IO, bool FP64>
 __global__ void __launch_bounds__(32 * kFillWarps) kb_cell_fill(const BinKArgs<IO>* __restrict__ tab,
                                                                 const int* __restrict__ first, int nrep) {
-  __shared__ int idx[kFillWarps][kOrderMax];
+  __shared__ long long idx[kFillWarps][kOrderMax];
   const int r = batch_rep(first, nrep, blockIdx.x);
   const BinKArgs<IO>& a = tab[r];
   const int w = threadIdx.x >> 5;

@@ -1504,8 +1504,10 @@ void lattice_t(Plan& P, int k, const double* qk64, T* uk, cudaStream_t st) {
   L.Ex = P.E[0];
   L.Ey = P.E[1];
   L.Ez = P.E[2];
-  L.txn = 4;  // one system: the 32 x 16 tile, fixed at compile time, on every level (the runtime-tile
-  L.tyn = 8;  // kernel is slower per tap than the saving on ragged coarse levels)
+  // one system: the 32 x 16 tile, fixed at compile time, on every level (the
+  // runtime-tile kernel is slower per tap than the saving on ragged coarse
+  // levels), unless the plan's tuning names another tile for level 0
+  lattice_tile_of(P, k, L.txn, L.tyn);
   const int TW = f32 ? kLatticeLP * L.txn : LBX, LBY = f32 ? 2 * L.tyn : 8;
   const int LBZb = f32 ? kLatticeZ : LBZ;  // output planes (warps) per block
   L.nbz = (int)blocks_for(G.n[2], LBZb);
@@ -1535,11 +1537,25 @@ void lattice_t(Plan& P, int k, const double* qk64, T* uk, cudaStream_t st) {
   }
 }
 
+// Warp tile of the FP32 lattice kernel at level k of a single system: the
+// plan's tuned tile on level 0, else 4 x 8 (32 x 16 outputs).
+void lattice_tile_of(const Plan& P, int k, int& txn, int& tyn) {
+  if (k == 0 && P.lattice_txn > 0) {
+    txn = P.lattice_txn;
+    tyn = P.lattice_tyn;
+  } else {
+    txn = 4;
+    tyn = 8;
+  }
+}
+
 // Blocks that share one brick's input planes at level k (several on small
 // levels, so that the launch still fills the GPU: lattice_waves blocks per SM).
 int lattice_nsplit(const Plan& P, int k) {
   GridDims G = dims_of(P, k);
-  const int TW = P.fp64 ? LBX : kLatticeLP * 4, LBY = P.fp64 ? 8 : 16;
+  int txn, tyn;
+  lattice_tile_of(P, k, txn, tyn);
+  const int TW = P.fp64 ? LBX : kLatticeLP * txn, LBY = P.fp64 ? 8 : 2 * tyn;
   const int LBZb = P.fp64 ? LBZ : kLatticeZ;
   const int64_t bricks = (int64_t)blocks_for(G.n[0], TW) * blocks_for(G.n[1], LBY) * blocks_for(G.n[2], LBZb);
   const int64_t target = (int64_t)P.lattice_waves * 152 * 4 / LBZb;
@@ -1563,6 +1579,10 @@ bool lattice_fits(const Plan& P) {
     return sizeof(double) * SX * SY <= 48 * 1024;
   }
   return lattice_smem(4, 8, P.E) <= kLatticeSmemMax;
+}
+
+bool lattice_tile_fits(const Plan& P, int txn, int tyn) {
+  return P.fp64 || lattice_smem(txn, tyn, P.E) <= kLatticeSmemMax;
 }
 
 cudaError_t launch_lattice(Plan& P, int k, const void* qk, void* uk, cudaStream_t st) {
@@ -2056,7 +2076,12 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
           cb.push_back(ew_blocks(np));
           GridDims G = dims_of(P, k);
           LatKArgs a;
-          lattice_tile(G.n[0], G.n[1], P.E, a.L.txn, a.L.tyn);
+          if (k == 0 && P.lattice_txn > 0) {  // the plan's tuned tile on its finest level
+            a.L.txn = P.lattice_txn;
+            a.L.tyn = P.lattice_tyn;
+          } else {
+            lattice_tile(G.n[0], G.n[1], P.E, a.L.txn, a.L.tyn);
+          }
           const int TW = kLatticeLP * a.L.txn, LBY = 2 * a.L.tyn;
           a.q = qf;
           a.u = (float*)u[k];

@@ -93,12 +93,6 @@ struct CutoffConsts<double> {
     a2 = A.a2; ia = A.inv_a; ia2 = A.inv_a2; t3 = A.two_inv_a3;
   }
 };
-template <>
-struct CutoffConsts<float> {
-  __device__ static void get(const PairArgs& A, float& a2, float& ia, float& ia2, float& t3) {
-    a2 = A.a2f; ia = A.inv_af; ia2 = A.inv_a2f; t3 = A.two_inv_a3f;
-  }
-};
 
 PairArgs pair_args(const Plan& P) {
   PairArgs A;
@@ -118,7 +112,14 @@ PairArgs pair_args(const Plan& P) {
 }
 
 constexpr int kWarps = 4;
-constexpr int kBatch = 32;       // pairs per lane per batch (one queue drain)
+#ifndef MSM_PAIR_BATCH
+#define MSM_PAIR_BATCH 64
+#endif
+#ifndef MSM_PAIR_MINB
+#define MSM_PAIR_MINB 6
+#endif
+constexpr int kBatch = MSM_PAIR_BATCH;  // sources per queue drain (pairs per lane per drain)
+constexpr int kHome = 32;               // home-cell sources per scalar batch (one per lane)
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float fast_rsqrt(float x) {  // one MUFU.RSQ; inputs are >= a^2/... never denormal
@@ -139,39 +140,45 @@ __device__ __forceinline__ T far_away() { return T(1e18); }
 // of that section), masked beyond a as well.
 constexpr int kPairMSM = 0, kPairCutoff = 1, kPairWolf = 2;
 
+// One pair, scalar: target ai against source b (skipped at r = 0, the atom
+// itself, and beyond the cutoff); adds q_j times the pair potential to pphi
+// and f (r_i - r_j) to (px, py, pz) with f = q_j v'(r)/r.
+template <typename T, int M, int K>
+__device__ __forceinline__ void pair1(const R4<T>& ai, const R4<T>& b, T a2, T inv_a, T inv_a2, T two_inv_a3,
+                                      const WolfC<T>& W, T& pphi, T& px, T& py, T& pz) {
+  const T dx = ai.x - b.x, dy = ai.y - b.y, dz = ai.z - b.z;
+  const T r2 = dx * dx + dy * dy + dz * dz;
+  const bool ok = (r2 < a2) && (r2 > T(0));  // inside the cutoff, not the atom itself
+  const T r2s = ok ? r2 : a2;
+  const T qj = ok ? b.w : T(0);
+  const T rinv = fast_rsqrt(r2s);
+  T f;
+  if (K == kPairMSM) {
+    const T s = r2s * inv_a2;
+    pphi += qj * (rinv - Smooth<T, M>::g(s) * inv_a);
+    f = qj * (-(rinv * rinv * rinv) - two_inv_a3 * Smooth<T, M>::gs(s));
+  } else if (K == kPairWolf) {  // f = q_j v'(r) / r
+    const T r = r2s * rinv;
+    const T e = d_erfc(W.alpha * r), g = W.c2 * d_exp(-W.alpha2 * r2s);
+    pphi += qj * (e * rinv - W.vR + W.c1 * (r - W.R));
+    f = qj * (W.c1 * rinv - (e * rinv + g) * rinv * rinv);
+  } else {
+    pphi += qj * rinv;
+    f = -qj * (rinv * rinv * rinv);
+  }
+  px += f * dx;
+  py += f * dy;
+  pz += f * dz;
+}
+
 // One batch: the lane's target atom against the kBatch queued sources.
-template <typename T, int M, bool COMP, int K = kPairMSM>
+template <typename T, int M, bool COMP, int K = kPairMSM, int NB = kBatch>
 __device__ __forceinline__ void pair_batch(const R4<T>* __restrict__ Q, const R4<T>& ai, T a2, T inv_a,
                                            T inv_a2, T two_inv_a3, const WolfC<T>& W, T& phi, T& fx, T& fy,
                                            T& fz, T& cphi, T& cfx, T& cfy, T& cfz) {
   T pphi = 0, px = 0, py = 0, pz = 0;
 #pragma unroll 8
-  for (int jj = 0; jj < kBatch; ++jj) {
-    const R4<T> b = Q[jj];
-    const T dx = ai.x - b.x, dy = ai.y - b.y, dz = ai.z - b.z;
-    const T r2 = dx * dx + dy * dy + dz * dz;
-    const bool ok = (r2 < a2) && (r2 > T(0));   // inside the cutoff, not the atom itself
-    const T r2s = ok ? r2 : a2;
-    const T qj = ok ? b.w : T(0);
-    const T rinv = fast_rsqrt(r2s);
-    T f;
-    if (K == kPairMSM) {
-      const T s = r2s * inv_a2;
-      pphi += qj * (rinv - Smooth<T, M>::g(s) * inv_a);
-      f = qj * (-(rinv * rinv * rinv) - two_inv_a3 * Smooth<T, M>::gs(s));
-    } else if (K == kPairWolf) {  // f = q_j v'(r) / r
-      const T r = r2s * rinv;
-      const T e = d_erfc(W.alpha * r), g = W.c2 * d_exp(-W.alpha2 * r2s);
-      pphi += qj * (e * rinv - W.vR + W.c1 * (r - W.R));
-      f = qj * (W.c1 * rinv - (e * rinv + g) * rinv * rinv);
-    } else {
-      pphi += qj * rinv;
-      f = -qj * (rinv * rinv * rinv);
-    }
-    px += f * dx;
-    py += f * dy;
-    pz += f * dz;
-  }
+  for (int jj = 0; jj < NB; ++jj) pair1<T, M, K>(ai, Q[jj], a2, inv_a, inv_a2, two_inv_a3, W, pphi, px, py, pz);
   if (COMP) {
     two_sum_add(phi, cphi, pphi);
     two_sum_add(fx, cfx, px);
@@ -263,7 +270,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_short_range(
       }
     }
     if (qn > 0) {  // last partial batch, padded with far-away zero charges
-      if (lane >= qn) Q[lane] = dummy;
+      for (int t = lane; t < kBatch; t += 32)
+        if (t >= qn) Q[t] = dummy;
       __syncwarp();
       pair_batch<T, M, COMP, K>(Q, ai, a2, inv_a, inv_a2, two_inv_a3, W, phi, fx, fy, fz, cphi, cfx, cfy, cfz);
       __syncwarp();
@@ -314,6 +322,54 @@ __device__ __forceinline__ float2 poly_d(const PairCoef& C, float2 r2) {
   return t;
 }
 
+// One packed step: the lane's target (negated coordinates nax, nay, naz)
+// against two sources (bx, by, bz, bq); adds q_j times the pair potential to
+// sphi and f' d to (sx, sy, sz) with d = r_j - r_i.  Sources are never at
+// r = 0 here (the home cell, the only one holding the target itself, goes
+// through the scalar path with the self test).
+template <int M, int K>
+__device__ __forceinline__ void pair2(float2 bx, float2 by, float2 bz, float2 bq, float2 nax, float2 nay, float2 naz,
+                                      float a2, const PairCoef& C, const WolfC<float>& W, float2& sphi, float2& sx,
+                                      float2& sy, float2& sz) {
+  const float2 dx = __fadd2_rn(bx, nax), dy = __fadd2_rn(by, nay), dz = __fadd2_rn(bz, naz);
+  float2 r2 = __fmul2_rn(dx, dx);
+  r2 = __ffma2_rn(dy, dy, r2);
+  r2 = __ffma2_rn(dz, dz, r2);
+  float2 fp;
+  if (K == kPairMSM) {
+    // a source beyond the cutoff is evaluated at r = a, where g* and its
+    // derivative vanish (C1 smoothing): no select on q_j is needed
+    r2 = make_float2(fminf(r2.x, a2), fminf(r2.y, a2));
+    const float2 qj = bq;
+    const float2 rinv = make_float2(fast_rsqrt(r2.x), fast_rsqrt(r2.y));
+    const float2 pot = __fadd2_rn(rinv, poly_g<M>(C, r2));  // G holds -gamma coefficients
+    sphi = __ffma2_rn(qj, pot, sphi);
+    fp = __fmul2_rn(__ffma2_rn(__fmul2_rn(rinv, rinv), rinv, poly_d<M>(C, r2)), qj);
+  } else if (K == kPairWolf) {  // damped shifted force within the cutoff, one source at a time
+    float pv[2], fv[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float x2 = c ? r2.y : r2.x;
+      const bool ok = x2 < a2;
+      const float r2s = ok ? x2 : a2, q = ok ? (c ? bq.y : bq.x) : 0.f;
+      const float ri = fast_rsqrt(r2s), r = r2s * ri;
+      const float e = erfcf(W.alpha * r), g = W.c2 * expf(-W.alpha2 * r2s);
+      pv[c] = q * (e * ri - W.vR + W.c1 * (r - W.R));
+      fv[c] = q * ((e * ri + g) * ri * ri - W.c1 * ri);  // -v'(r)/r, the sign this kernel sums with
+    }
+    sphi = __fadd2_rn(sphi, make_float2(pv[0], pv[1]));
+    fp = make_float2(fv[0], fv[1]);
+  } else {  // plain Coulomb within the cutoff
+    const float2 qj = make_float2(r2.x < a2 ? bq.x : 0.f, r2.y < a2 ? bq.y : 0.f);
+    const float2 rinv = make_float2(fast_rsqrt(r2.x), fast_rsqrt(r2.y));
+    sphi = __ffma2_rn(qj, rinv, sphi);
+    fp = __fmul2_rn(__fmul2_rn(__fmul2_rn(rinv, rinv), rinv), qj);
+  }
+  sx = __ffma2_rn(fp, dx, sx);
+  sy = __ffma2_rn(fp, dy, sy);
+  sz = __ffma2_rn(fp, dz, sz);
+}
+
 template <int M, int K>
 __device__ __forceinline__ void pair_batch_f2(const QueueF& Q, float2 nax, float2 nay, float2 naz, float a2,
                                               const PairCoef& C, const WolfC<float>& W, float& phi, float& px,
@@ -327,50 +383,10 @@ __device__ __forceinline__ void pair_batch_f2(const QueueF& Q, float2 nax, float
     const float4 y4 = *reinterpret_cast<const float4*>(&Q.y[jj]);
     const float4 z4 = *reinterpret_cast<const float4*>(&Q.z[jj]);
     const float4 q4 = *reinterpret_cast<const float4*>(&Q.q[jj]);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const float2 bx = h ? make_float2(x4.z, x4.w) : make_float2(x4.x, x4.y);
-      const float2 by = h ? make_float2(y4.z, y4.w) : make_float2(y4.x, y4.y);
-      const float2 bz = h ? make_float2(z4.z, z4.w) : make_float2(z4.x, z4.y);
-      const float2 bq = h ? make_float2(q4.z, q4.w) : make_float2(q4.x, q4.y);
-      const float2 dx = __fadd2_rn(bx, nax), dy = __fadd2_rn(by, nay), dz = __fadd2_rn(bz, naz);
-      float2 r2 = __fmul2_rn(dx, dx);
-      r2 = __ffma2_rn(dy, dy, r2);
-      r2 = __ffma2_rn(dz, dz, r2);
-      float2 fp;
-      if (K == kPairMSM) {
-        // a source beyond the cutoff is evaluated at r = a, where g* and its
-        // derivative vanish (C1 smoothing): no select on q_j is needed
-        r2 = make_float2(fminf(r2.x, a2), fminf(r2.y, a2));
-        const float2 qj = bq;
-        const float2 rinv = make_float2(fast_rsqrt(r2.x), fast_rsqrt(r2.y));
-        const float2 pot = __fadd2_rn(rinv, poly_g<M>(C, r2));  // G holds -gamma coefficients
-        sphi = __ffma2_rn(qj, pot, sphi);
-        fp = __fmul2_rn(__ffma2_rn(__fmul2_rn(rinv, rinv), rinv, poly_d<M>(C, r2)), qj);
-      } else if (K == kPairWolf) {  // damped shifted force within the cutoff, one source at a time
-        float pv[2], fv[2];
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const float x2 = c ? r2.y : r2.x;
-          const bool ok = x2 < a2;
-          const float r2s = ok ? x2 : a2, q = ok ? (c ? bq.y : bq.x) : 0.f;
-          const float ri = fast_rsqrt(r2s), r = r2s * ri;
-          const float e = erfcf(W.alpha * r), g = W.c2 * expf(-W.alpha2 * r2s);
-          pv[c] = q * (e * ri - W.vR + W.c1 * (r - W.R));
-          fv[c] = q * ((e * ri + g) * ri * ri - W.c1 * ri);  // -v'(r)/r, the sign this kernel sums with
-        }
-        sphi = __fadd2_rn(sphi, make_float2(pv[0], pv[1]));
-        fp = make_float2(fv[0], fv[1]);
-      } else {  // plain Coulomb within the cutoff (sources are never at r = 0 outside the home cell)
-        const float2 qj = make_float2(r2.x < a2 ? bq.x : 0.f, r2.y < a2 ? bq.y : 0.f);
-        const float2 rinv = make_float2(fast_rsqrt(r2.x), fast_rsqrt(r2.y));
-        sphi = __ffma2_rn(qj, rinv, sphi);
-        fp = __fmul2_rn(__fmul2_rn(__fmul2_rn(rinv, rinv), rinv), qj);
-      }
-      sx = __ffma2_rn(fp, dx, sx);
-      sy = __ffma2_rn(fp, dy, sy);
-      sz = __ffma2_rn(fp, dz, sz);
-    }
+    pair2<M, K>(make_float2(x4.x, x4.y), make_float2(y4.x, y4.y), make_float2(z4.x, z4.y), make_float2(q4.x, q4.y),
+                nax, nay, naz, a2, C, W, sphi, sx, sy, sz);
+    pair2<M, K>(make_float2(x4.z, x4.w), make_float2(y4.z, y4.w), make_float2(z4.z, z4.w), make_float2(q4.z, q4.w),
+                nax, nay, naz, a2, C, W, sphi, sx, sy, sz);
   }
   two_sum_add(phi, cphi, sphi.x + sphi.y);
   two_sum_add(px, cpx, sx.x + sx.y);
@@ -411,33 +427,15 @@ struct PairKArgs {
   R4<float>* fs;
 };
 
-template <int M, int KIND>
-__device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk) {
-  const R4<float>* __restrict__ atoms = K.atoms;
+// The segment table of cell (cx, cy, cz), built by the warp (lane r: row r);
+// returns the number of sources in the flat index space.
+__device__ __forceinline__ int build_seg_table(SegTable& T, const PairKArgs& K, int cx, int cy, int cz, int lane) {
   const int* __restrict__ cell_start = K.cell_start;
   const int4* __restrict__ rows = K.rows;
-  const int nrows = K.nrows, ncell = K.ncell;
+  const int nrows = K.nrows;
   const PairArgs& A = K.A;
-  const PairCoef C = K.C;
-  const WolfC<float> W = K.W;
-  const float cwx = K.cwx, cwy = K.cwy, cwz = K.cwz;
-  float* __restrict__ phis = K.phis;
-  R4<float>* __restrict__ fs = K.fs;
-  __shared__ QueueF queue[kWarps];
-  __shared__ R4<float> home[kWarps][kBatch];
-  __shared__ SegTable tables[kWarps];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  QueueF& Q = queue[warp];
-  SegTable& T = tables[warp];
-  const int cell = blk * kWarps + warp;
-  if (cell >= ncell) return;  // warp-uniform
   const int ncx = A.nc[0], ncy = A.nc[1], ncz = A.nc[2];
-  const int cx = cell % ncx, cy = (cell / ncx) % ncy, cz = cell / (ncx * ncy);
-  const float a2 = A.a2f, inv_a = A.inv_af, inv_a2s = A.inv_a2f, two_inv_a3 = A.two_inv_a3f;
-  const float FAR = 1e6f;
-  const int i0 = cell_start[cell], i1 = cell_start[cell + 1];
-
-  // ---- segment table of this cell (lane r: row r) ----
+  const float cwy = K.cwy, cwz = K.cwz;
   int len[2] = {0, 0}, j0s[2] = {0, 0}, ox0s[2] = {0, 0};
   int4 bnds[2] = {make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX), make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX)};
   float2 sh = make_float2(0.f, 0.f);
@@ -510,6 +508,35 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
     __syncwarp();
   }
 
+  return total;
+}
+
+template <int M, int KIND>
+__device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk) {
+  const R4<float>* __restrict__ atoms = K.atoms;
+  const int* __restrict__ cell_start = K.cell_start;
+  const int ncell = K.ncell;
+  const PairArgs& A = K.A;
+  const PairCoef C = K.C;
+  const WolfC<float> W = K.W;
+  const float cwx = K.cwx;
+  float* __restrict__ phis = K.phis;
+  R4<float>* __restrict__ fs = K.fs;
+  __shared__ QueueF queue[kWarps];
+  __shared__ R4<float> home[kWarps][kHome];
+  __shared__ SegTable tables[kWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  QueueF& Q = queue[warp];
+  SegTable& T = tables[warp];
+  const int cell = blk * kWarps + warp;
+  if (cell >= ncell) return;  // warp-uniform
+  const int ncx = A.nc[0], ncy = A.nc[1];
+  const int cx = cell % ncx, cy = (cell / ncx) % ncy, cz = cell / (ncx * ncy);
+  const float a2 = A.a2f, inv_a = A.inv_af, inv_a2s = A.inv_a2f, two_inv_a3 = A.two_inv_a3f;
+  const float FAR = 1e6f;
+  const int i0 = cell_start[cell], i1 = cell_start[cell + 1];
+  const int total = build_seg_table(T, K, cx, cy, cz, lane);
+
   for (int ib = i0; ib < i1; ib += 32) {
     const int i = ib + lane;
     const bool iv = i < i1;
@@ -533,8 +560,8 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
       home[warp][lane] = (j < i1) ? atoms[j] : R4<float>{FAR, FAR, FAR, 0.f};
       __syncwarp();
       float hphi = 0.f, hx_ = 0.f, hy_ = 0.f, hz_ = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-      pair_batch<float, M, true, KIND>(home[warp], ai, a2, inv_a, inv_a2s, two_inv_a3, W, hphi, hx_, hy_, hz_, c0,
-                                       c1, c2, c3);
+      pair_batch<float, M, true, KIND, kHome>(home[warp], ai, a2, inv_a, inv_a2s, two_inv_a3, W, hphi, hx_, hy_,
+                                              hz_, c0, c1, c2, c3);
       two_sum_add(phi, cphi, hphi + c0);
       two_sum_add(px, cpx, hx_ + c1);
       two_sum_add(py, cpy, hy_ + c2);
@@ -602,12 +629,13 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
       }
     }
     if (qn > 0) {  // last partial batch, padded with far-away zero charges
-      if (lane >= qn) {
-        Q.x[lane] = FAR;
-        Q.y[lane] = FAR;
-        Q.z[lane] = FAR;
-        Q.q[lane] = 0.f;
-      }
+      for (int t = lane; t < kBatch; t += 32)
+        if (t >= qn) {
+          Q.x[t] = FAR;
+          Q.y[t] = FAR;
+          Q.z[t] = FAR;
+          Q.q[t] = 0.f;
+        }
       __syncwarp();
       pair_batch_f2<M, KIND>(Q, nax, nay, naz, a2, C, W, phi, px, py, pz, cphi, cpx, cpy, cpz);
       __syncwarp();
@@ -620,13 +648,274 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
   }
 }
 
+// ---- target clusters (mixed precision) ----
+// The warp takes its cell's atoms 32 at a time (a pass) as up to kClPass
+// clusters of kCl consecutive atoms, spatially compact because binning orders
+// each cell by sub-cell, and culls every source against each cluster's own
+// bounding box: the box of 8 atoms admits ~1,650 sources per atom at water
+// density against ~2,200 for the box of a whole cell (the pairs inside the
+// cutoff are ~750).  Each cluster has its own queue; a full queue of kCD
+// sources is drained by the whole warp on that one cluster: lane 4 i + jl
+// evaluates target i of the cluster against sources 16 jl .. 16 jl + 15
+// (packed FP32x2), the four partial sums of a target are added across its
+// four lanes by two shuffles, and lane 4 i + c, which owns target (c, i),
+// folds them into its compensated totals.  The home cell goes through the
+// scalar pair with the self test.  Queue arrays leave 4 floats of padding
+// after every 16 sources, so that the four source lanes' float4 loads fall
+// on distinct banks.
+constexpr int kCl = 8, kClPass = 4, kCD = 64, kCQ = kCD + 32;
+constexpr int kCQP = kCQ + (kCQ / 16) * 4;
+__device__ __forceinline__ int cq_slot(int p) { return p + ((p >> 4) << 2); }
+struct alignas(16) ClQueue {
+  float x[kCQP], y[kCQP], z[kCQP], q[kCQP];
+};
+
 template <int M, int KIND>
-__global__ void __launch_bounds__(32 * kWarps, 6) k_short_range_f2(PairKArgs a) {
+__device__ __forceinline__ void cl_drain(const ClQueue& Q, float tx, float ty, float tz, int jl, float a2,
+                                         const PairCoef& C, const WolfC<float>& W, float& s0, float& s1, float& s2,
+                                         float& s3) {
+  const float2 nax = make_float2(-tx, -tx), nay = make_float2(-ty, -ty), naz = make_float2(-tz, -tz);
+  float2 sphi = make_float2(0.f, 0.f), sx = sphi, sy = sphi, sz = sphi;
+  const int b = cq_slot(16 * jl);
+#pragma unroll
+  for (int k = 0; k < 16; k += 4) {
+    const float4 x4 = *reinterpret_cast<const float4*>(&Q.x[b + k]);
+    const float4 y4 = *reinterpret_cast<const float4*>(&Q.y[b + k]);
+    const float4 z4 = *reinterpret_cast<const float4*>(&Q.z[b + k]);
+    const float4 q4 = *reinterpret_cast<const float4*>(&Q.q[b + k]);
+    pair2<M, KIND>(make_float2(x4.x, x4.y), make_float2(y4.x, y4.y), make_float2(z4.x, z4.y),
+                   make_float2(q4.x, q4.y), nax, nay, naz, a2, C, W, sphi, sx, sy, sz);
+    pair2<M, KIND>(make_float2(x4.z, x4.w), make_float2(y4.z, y4.w), make_float2(z4.z, z4.w),
+                   make_float2(q4.z, q4.w), nax, nay, naz, a2, C, W, sphi, sx, sy, sz);
+  }
+  s0 = sphi.x + sphi.y;
+  s1 = sx.x + sx.y;
+  s2 = sy.x + sy.y;
+  s3 = sz.x + sz.y;
+}
+
+// The four partial sums of target i, spread over lanes 4 i .. 4 i + 3, added
+// (every lane of the group gets the total).
+__device__ __forceinline__ void cl_reduce(float& s0, float& s1, float& s2, float& s3) {
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    s0 += __shfl_xor_sync(kFull, s0, o);
+    s1 += __shfl_xor_sync(kFull, s1, o);
+    s2 += __shfl_xor_sync(kFull, s2, o);
+    s3 += __shfl_xor_sync(kFull, s3, o);
+  }
+}
+
+template <int M, int KIND>
+__device__ __forceinline__ void short_range_c8_body(const PairKArgs& K, int blk) {
+  const R4<float>* __restrict__ atoms = K.atoms;
+  const int* __restrict__ cell_start = K.cell_start;
+  const int ncell = K.ncell;
+  const PairArgs& A = K.A;
+  const PairCoef C = K.C;
+  const WolfC<float> W = K.W;
+  const float cwx = K.cwx;
+  float* __restrict__ phis = K.phis;
+  R4<float>* __restrict__ fs = K.fs;
+  __shared__ ClQueue queues[kWarps][kClPass];
+  __shared__ R4<float> home[kWarps][32];
+  __shared__ SegTable tables[kWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cell = blk * kWarps + warp;
+  if (cell >= ncell) return;  // warp-uniform
+  const int ncx = A.nc[0], ncy = A.nc[1];
+  const int cx = cell % ncx, cy = (cell / ncx) % ncy, cz = cell / (ncx * ncy);
+  const float a2 = A.a2f, inv_a = A.inv_af, inv_a2s = A.inv_a2f, two_inv_a3 = A.two_inv_a3f;
+  const float FAR = 1e6f;
+  const int i0 = cell_start[cell], i1 = cell_start[cell + 1];
+  if (i0 == i1) return;  // warp-uniform
+  SegTable& T = tables[warp];
+  ClQueue* Q = queues[warp];
+  const int total = build_seg_table(T, K, cx, cy, cz, lane);
+  const int jl = lane & 3, ti = lane >> 2;
+  for (int base = i0; base < i1; base += kCl * kClPass) {
+    const int ncl = min(kClPass, (i1 - base + kCl - 1) / kCl);
+    // lane 4 i + c owns target (c, i), atom base + 8 c + i
+    const int t_atom = base + kCl * jl + ti;
+    const bool tv = t_atom < i1;
+    const R4<float> ai = tv ? atoms[t_atom] : R4<float>{FAR, FAR, FAR, 0.f};
+    // bounding box of each cluster (over the lanes with the same lane & 3),
+    // then every cluster's box in every lane
+    float lx = tv ? ai.x : FAR, ly = tv ? ai.y : FAR, lz = tv ? ai.z : FAR;
+    float hx = tv ? ai.x : -FAR, hy = tv ? ai.y : -FAR, hz = tv ? ai.z : -FAR;
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+      lx = fminf(lx, __shfl_xor_sync(kFull, lx, o));
+      ly = fminf(ly, __shfl_xor_sync(kFull, ly, o));
+      lz = fminf(lz, __shfl_xor_sync(kFull, lz, o));
+      hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, o));
+      hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, o));
+      hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, o));
+    }
+    float blx[kClPass], bly[kClPass], blz[kClPass], bhx[kClPass], bhy[kClPass], bhz[kClPass];
+#pragma unroll
+    for (int c = 0; c < kClPass; ++c) {
+      blx[c] = __shfl_sync(kFull, lx, c);
+      bly[c] = __shfl_sync(kFull, ly, c);
+      blz[c] = __shfl_sync(kFull, lz, c);
+      bhx[c] = __shfl_sync(kFull, hx, c);
+      bhy[c] = __shfl_sync(kFull, hy, c);
+      bhz[c] = __shfl_sync(kFull, hz, c);
+    }
+    float phi = 0.f, px = 0.f, py = 0.f, pz = 0.f, cphi = 0.f, cpx = 0.f, cpy = 0.f, cpz = 0.f;
+    // the home cell: cluster c's targets against all the cell's atoms, lane
+    // 4 i + jl taking sources jl, jl + 4, ... (scalar, with the self test)
+    for (int jb = i0; jb < i1; jb += 32) {
+      const int j = jb + lane;
+      home[warp][lane] = (j < i1) ? atoms[j] : R4<float>{FAR, FAR, FAR, 0.f};
+      __syncwarp();
+#pragma unroll 1
+      for (int c = 0; c < ncl; ++c) {
+        const int src = 4 * ti + c;
+        const R4<float> t = {__shfl_sync(kFull, ai.x, src), __shfl_sync(kFull, ai.y, src),
+                             __shfl_sync(kFull, ai.z, src), 0.f};
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          pair1<float, M, KIND>(t, home[warp][jl + 4 * k], a2, inv_a, inv_a2s, two_inv_a3, W, s0, s1, s2, s3);
+        cl_reduce(s0, s1, s2, s3);
+        if (jl == c) {  // both paths sum grad_i u_i (scalar: f (r_i - r_j); packed: f' (r_j - r_i), f' = -f)
+          two_sum_add(phi, cphi, s0);
+          two_sum_add(px, cpx, s1);
+          two_sum_add(py, cpy, s2);
+          two_sum_add(pz, cpz, s3);
+        }
+      }
+      __syncwarp();
+    }
+    // the neighbour rows: flat source index t in [0, total), 32 per step
+    int seg = 0;
+    auto locate = [&](int t, int& j, int& ox, float2& shv) {
+      while (T.rec[seg + 1].y <= t) ++seg;
+      const int4 r = T.rec[seg];
+      const int4 b = T.bnd[seg];
+      j = r.x + (t - r.y);
+      ox = r.z + (j >= b.x) + (j >= b.y) + (j >= b.z) + (j >= b.w);
+      shv = T.shift[seg];
+    };
+    R4<float> an = {FAR, FAR, FAR, 0.f};
+    int oxn = 0;
+    float2 shn = make_float2(0.f, 0.f);
+    if (lane < total) {
+      int j;
+      locate(lane, j, oxn, shn);
+      an = atoms[j];
+    }
+    int qn[kClPass];
+#pragma unroll
+    for (int c = 0; c < kClPass; ++c) qn[c] = 0;
+    auto drain = [&](int c) {
+      const int src = 4 * ti + c;
+      const float tx = __shfl_sync(kFull, ai.x, src), ty = __shfl_sync(kFull, ai.y, src),
+                  tz = __shfl_sync(kFull, ai.z, src);
+      float s0, s1, s2, s3;
+      cl_drain<M, KIND>(Q[c], tx, ty, tz, jl, a2, C, W, s0, s1, s2, s3);
+      cl_reduce(s0, s1, s2, s3);
+      if (jl == c) {
+        two_sum_add(phi, cphi, s0);
+        two_sum_add(px, cpx, s1);
+        two_sum_add(py, cpy, s2);
+        two_sum_add(pz, cpz, s3);
+      }
+    };
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const bool valid = t0 + lane < total;
+      R4<float> aj = an;
+      const int ox = oxn;
+      const float2 shv = shn;
+      if (t0 + 32 + lane < total) {  // next chunk's load goes out before this chunk's work
+        int j;
+        locate(t0 + 32 + lane, j, oxn, shn);
+        an = atoms[j];
+      }
+      aj.x += ox * cwx;
+      aj.y += shv.x;
+      aj.z += shv.y;
+      const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+      for (int c = 0; c < kClPass; ++c) {
+        if (c < ncl) {
+          const float ex = fmaxf(fmaxf(blx[c] - aj.x, aj.x - bhx[c]), 0.f);
+          const float ey = fmaxf(fmaxf(bly[c] - aj.y, aj.y - bhy[c]), 0.f);
+          const float ez = fmaxf(fmaxf(blz[c] - aj.z, aj.z - bhz[c]), 0.f);
+          const bool keep = valid && (ex * ex + ey * ey + ez * ez < a2);
+          const unsigned bal = __ballot_sync(kFull, keep);
+          if (keep) {
+            const int p = cq_slot(qn[c] + __popc(bal & lt));
+            Q[c].x[p] = aj.x;
+            Q[c].y[p] = aj.y;
+            Q[c].z[p] = aj.z;
+            Q[c].q[p] = aj.w;
+          }
+          qn[c] += __popc(bal);
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int c = 0; c < kClPass; ++c) {
+        if (c < ncl && qn[c] >= kCD) {
+          drain(c);
+          __syncwarp();
+          if (lane < qn[c] - kCD) {
+            const int from = cq_slot(kCD + lane), to = cq_slot(lane);
+            Q[c].x[to] = Q[c].x[from];
+            Q[c].y[to] = Q[c].y[from];
+            Q[c].z[to] = Q[c].z[from];
+            Q[c].q[to] = Q[c].q[from];
+          }
+          qn[c] -= kCD;
+          __syncwarp();
+        }
+      }
+    }
+    // last partial queues, padded with far-away zero charges
+#pragma unroll
+    for (int c = 0; c < kClPass; ++c) {
+      if (c < ncl && qn[c] > 0) {
+        for (int t = qn[c] + lane; t < kCD; t += 32) {
+          const int p = cq_slot(t);
+          Q[c].x[p] = FAR;
+          Q[c].y[p] = FAR;
+          Q[c].z[p] = FAR;
+          Q[c].q[p] = 0.f;
+        }
+        __syncwarp();
+        drain(c);
+        __syncwarp();
+      }
+    }
+    if (tv) {
+      phis[t_atom] = phi + cphi;
+      const float qi = ai.w;
+      fs[t_atom] = R4<float>{-qi * (px + cpx), -qi * (py + cpy), -qi * (pz + cpz), 0.f};
+    }
+  }
+}
+
+template <int M, int KIND>
+__global__ void __launch_bounds__(32 * kWarps, MSM_PAIR_MINB) k_short_range_f2(PairKArgs a) {
   short_range_f2_body<M, KIND>(a, blockIdx.x);
 }
 
+template <int M, int KIND>
+__global__ void __launch_bounds__(32 * kWarps, 4) k_short_range_c8(PairKArgs a) {
+  short_range_c8_body<M, KIND>(a, blockIdx.x);
+}
+
 template <int M>
-__global__ void __launch_bounds__(32 * kWarps, 6) kb_short_range_f2(const PairKArgs* __restrict__ tab,
+__global__ void __launch_bounds__(32 * kWarps, 4) kb_short_range_c8(const PairKArgs* __restrict__ tab,
+                                                                   const int* __restrict__ first, int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  short_range_c8_body<M, kPairMSM>(tab[r], blockIdx.x - first[r]);
+}
+
+template <int M>
+__global__ void __launch_bounds__(32 * kWarps, MSM_PAIR_MINB) kb_short_range_f2(const PairKArgs* __restrict__ tab,
                                                                    const int* __restrict__ first, int nrep) {
   const int r = batch_rep(first, nrep, blockIdx.x);
   short_range_f2_body<M, kPairMSM>(tab[r], blockIdx.x - first[r]);
@@ -694,6 +983,14 @@ void launch_f2(Plan& P, cudaStream_t st, double alpha = 0.0) {
   PairKArgs K = pair_kargs(P);
   K.W = wolf_consts<float>(alpha, P.P.cutoff);
   const int blocks = (P.ncell + kWarps - 1) / kWarps;
+  if (P.pair_targets == kCl) {  // clusters of 8 targets
+    if (KIND == kPairCutoff) k_short_range_c8<2, kPairCutoff><<<blocks, 32 * kWarps, 0, st>>>(K);  // M unused
+    else if (KIND == kPairWolf) k_short_range_c8<2, kPairWolf><<<blocks, 32 * kWarps, 0, st>>>(K);
+    else if (P.P.splitting == 1) k_short_range_c8<1, kPairMSM><<<blocks, 32 * kWarps, 0, st>>>(K);
+    else if (P.P.splitting == 2) k_short_range_c8<2, kPairMSM><<<blocks, 32 * kWarps, 0, st>>>(K);
+    else k_short_range_c8<3, kPairMSM><<<blocks, 32 * kWarps, 0, st>>>(K);
+    return;
+  }
   if (KIND == kPairCutoff) k_short_range_f2<2, kPairCutoff><<<blocks, 32 * kWarps, 0, st>>>(K);  // M unused
   else if (KIND == kPairWolf) k_short_range_f2<2, kPairWolf><<<blocks, 32 * kWarps, 0, st>>>(K);
   else if (P.P.splitting == 1) k_short_range_f2<1, kPairMSM><<<blocks, 32 * kWarps, 0, st>>>(K);
@@ -728,6 +1025,7 @@ cudaError_t launch_wolf_pairs(Plan& P, int64_t n, double alpha, cudaStream_t st)
 struct PairBatch {
   BatchTable<PairKArgs> cells;  // kWarps cells per block
   int splitting = 2;
+  int targets = 8;  // the first replica's pair_targets
 };
 
 cudaError_t pair_batch_build(const std::vector<BatchRep>& reps, PairBatch** out) {
@@ -741,6 +1039,7 @@ cudaError_t pair_batch_build(const std::vector<BatchRep>& reps, PairBatch** out)
     kb.push_back(r.n > 0 ? (r.plan->ncell + kWarps - 1) / kWarps : 0);
     b->splitting = r.plan->P.splitting;
   }
+  if (!reps.empty()) b->targets = reps[0].plan->pair_targets;
   cudaError_t e = make_table(b->cells, ka, kb);
   if (e != cudaSuccess) {
     pair_batch_free(b);
@@ -753,6 +1052,13 @@ cudaError_t pair_batch_build(const std::vector<BatchRep>& reps, PairBatch** out)
 cudaError_t pair_batch_launch(PairBatch* b, cudaStream_t st) {
   const int nb = b->cells.total;
   if (nb == 0) return cudaSuccess;
+  if (b->targets == kCl) {
+    if (b->splitting == 1) kb_short_range_c8<1><<<nb, 32 * kWarps, 0, st>>>(b->cells.args, b->cells.first, b->cells.nrep);
+    else if (b->splitting == 2)
+      kb_short_range_c8<2><<<nb, 32 * kWarps, 0, st>>>(b->cells.args, b->cells.first, b->cells.nrep);
+    else kb_short_range_c8<3><<<nb, 32 * kWarps, 0, st>>>(b->cells.args, b->cells.first, b->cells.nrep);
+    return cudaGetLastError();
+  }
   if (b->splitting == 1) kb_short_range_f2<1><<<nb, 32 * kWarps, 0, st>>>(b->cells.args, b->cells.first, b->cells.nrep);
   else if (b->splitting == 2) kb_short_range_f2<2><<<nb, 32 * kWarps, 0, st>>>(b->cells.args, b->cells.first, b->cells.nrep);
   else kb_short_range_f2<3><<<nb, 32 * kWarps, 0, st>>>(b->cells.args, b->cells.first, b->cells.nrep);

@@ -112,8 +112,12 @@ struct Plan {
   // anterpolation patches: blocks of ablk^3 cells, patches of apd^3 points
   int ablk = 1, apd = 1;
   int ablk_batch = 1, apd_batch = 1;  // the same for the batched launches (at least as large)
-  // lattice: blocks per SM to aim for when splitting a small level's planes
+  // lattice: blocks per SM to aim for when splitting a small level's planes,
+  // and the warp tile of the FP32 kernel (0 x 0: the default)
   int lattice_waves = 8;
+  int lattice_txn = 0, lattice_tyn = 0;
+  // mixed pair kernel: targets culled together (8: clusters; 32: a cell's warp)
+  int pair_targets = 32;
   // smoothing constants
   double gamma0 = 0.0;         // gamma(0)
   // level stencil
@@ -287,6 +291,8 @@ bool lattice_fits(const Plan& P);
 // blocks sharing one brick's input planes at level k, and the elements of the
 // plan's split-partial buffer (largest nsplit x points over the split levels)
 int lattice_nsplit(const Plan& P, int k);
+void lattice_tile_of(const Plan& P, int k, int& txn, int& tyn);
+bool lattice_tile_fits(const Plan& P, int txn, int tyn);  // the tile's staging window fits shared memory
 int64_t lattice_parts_elems(const Plan& P);
 cudaError_t launch_lattice(Plan& P, int k, const void* qk, void* uk, cudaStream_t s);
 cudaError_t launch_top(Plan& P, const void* qt, void* ut, cudaStream_t s);

@@ -264,6 +264,10 @@ int validate_tuning(const msm_tuning* t) {
   if (t->cell_fill < 0 || t->cell_fill > 256 || t->patch_cells < 0 || t->patch_cells > 4 || t->lattice_waves < 0 ||
       t->lattice_waves > 64)
     return MSM_ERR_INVALID_ARG;
+  if (t->pair_targets != 0 && t->pair_targets != 8 && t->pair_targets != 32) return MSM_ERR_INVALID_ARG;
+  if (t->lattice_txn < 0 || t->lattice_tyn < 0 || t->lattice_txn > 32 || t->lattice_tyn > 32 ||
+      (t->lattice_txn == 0) != (t->lattice_tyn == 0) || t->lattice_txn * t->lattice_tyn > 32)
+    return MSM_ERR_INVALID_ARG;
   return MSM_OK;
 }
 
@@ -283,10 +287,13 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   if (vrc != MSM_OK) return vrc;
   int trc = validate_tuning(tune);
   if (trc != MSM_OK) return trc;
-  msm_tuning TU = {0, 0, 0};
+  msm_tuning TU = {0, 0, 0, 0, 0, 0};
   if (tune) TU = *tune;
   const double fill = TU.cell_fill > 0 ? TU.cell_fill : 24.0;
   P->lattice_waves = TU.lattice_waves > 0 ? TU.lattice_waves : 8;
+  P->pair_targets = TU.pair_targets > 0 ? TU.pair_targets : 32;
+  P->lattice_txn = TU.lattice_txn;
+  P->lattice_tyn = TU.lattice_tyn;
   P->wolf_alpha = 2.4 / p.cutoff;  // alpha R = 2.4 (0.2 per length unit at R = 12) until msm_set_wolf_alpha
   for (int d = 0; d < 3; ++d)
     if (!(p.box[d] > 0.0) || !std::isfinite(p.box[d])) return MSM_ERR_INVALID_ARG;
@@ -406,6 +413,7 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
     while (P->E[d] > 0 && P->E[d] * P->h[d] >= R) --P->E[d];
   }
   if (!lattice_fits(*P)) return MSM_ERR_UNSUPPORTED;  // cutoff too many grid spacings wide
+  if (P->lattice_txn > 0 && !lattice_tile_fits(*P, P->lattice_txn, P->lattice_tyn)) return MSM_ERR_INVALID_ARG;
   std::vector<double> G((size_t)(2 * P->E[0] + 1) * (2 * P->E[1] + 1) * (2 * P->E[2] + 1), 0.0);
   double taps = 0;
   for (int dz = -P->E[2]; dz <= P->E[2]; ++dz)

@@ -23,13 +23,16 @@ def test_autotune_search_result_and_cache(tmp_path, monkeypatch):
     kw = dict(box=40.0, periodic=True, cutoff=9.0, spacing=2.0, order=5, splitting=2, precision="mixed")
     tuning, times = AT.autotune(pos, q, reps=3, **kw)
     space = dict(AT.SEARCH)
-    for k, v in tuning.items():
-        assert v in space[k]
-    assert "default" in times and len(times) > 3
+    for k, v in times["choice"].items():
+        assert tuple(v) in space[k] if k == "lattice_tile" else v in space[k]
+    assert "default" in times and len(times) > 8
+    assert any(k.startswith("lattice_tile=") for k in times)    # tiles were searched
+    assert any(k.startswith("pair_targets=8") for k in times)   # and the pair clusters
     t2, times2 = AT.autotune(pos, q, reps=3, **kw)
     assert t2 == tuning and "cached" in times2
     base = MSM(max_atoms=len(q_h), **kw)
-    for t in [tuning, {"cell_fill": 40, "patch_cells": 2, "lattice_waves": 8}]:
+    for t in [tuning, {"cell_fill": 40, "patch_cells": 2, "lattice_waves": 8},
+              {"pair_targets": 8, "lattice_txn": 2, "lattice_tyn": 16}]:
         tuned = MSM(max_atoms=len(q_h), tuning=t, **kw)
         E0, phi0, F0 = base.eval(pos, q)
         E1, phi1, F1 = tuned.eval(pos, q)
@@ -43,8 +46,11 @@ def test_tuning_fields_are_checked():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1402_7216_gb300 import MSM, MSMError
-    with pytest.raises(MSMError):
-        MSM(box=30.0, periodic=True, cutoff=9.0, spacing=2.0, max_atoms=100, tuning={"patch_cells": 7})
+    for bad in [{"patch_cells": 7}, {"pair_targets": 16}, {"lattice_txn": 4}, {"lattice_txn": 8, "lattice_tyn": 8},
+                {"lattice_txn": 32, "lattice_tyn": 1}]:   # the last: a 343 x 80 window, too wide for shared memory
+        with pytest.raises(MSMError) as e:
+            MSM(box=30.0, periodic=True, cutoff=9.0, spacing=0.45, max_atoms=100, tuning=bad)
+        assert e.value.code == -1, bad
 
 
 def test_autotune_batch_search_and_cache(tmp_path, monkeypatch):
@@ -68,17 +74,32 @@ def test_autotune_batch_search_and_cache(tmp_path, monkeypatch):
     pos = torch.tensor(np.vstack(ps), device=dev)
     q = torch.tensor(np.concatenate(qs), device=dev)
     kw = dict(cutoff=6.0, spacing=1.5, order=3, splitting=2)
-    tuning, times = AT.autotune_batch(boxes, pos, q, counts, reps=2, **kw)
+    tunings, summary, times = AT.autotune_batch(boxes, pos, q, counts, reps=2, **kw)
     space = dict(AT.SEARCH_BATCH)
-    for k, v in tuning.items():
+    for k, v in summary["shared"].items():
         assert v in space[k]
-    assert "default" in times and len(times) > 2
-    t2, times2 = AT.autotune_batch(boxes, pos, q, counts, reps=2, **kw)
-    assert t2 == tuning and "cached" in times2
-    mk = lambda t: [MSM(box=L, periodic=True, precision="mixed", max_atoms=c, tuning=t, **kw)
-                    for L, c in zip(boxes, counts)]
-    E0, _, F0 = MSMBatch(mk(None)).eval(pos, q, counts)
-    E1, _, F1 = MSMBatch(mk(tuning)).eval(pos, q, counts)
+    for g, tile in summary["lattice_tile_by_grid0"].items():
+        assert int(g) in summary["grid0_sizes"] and tuple(tile) in AT.TILES_BATCH
+    assert len(tunings) == len(counts)
+    assert "default" in times and any(k.startswith("grid0=") for k in times)   # per-grid tiles were timed
+    t2, s2, times2 = AT.autotune_batch(boxes, pos, q, counts, reps=2, **kw)
+    assert t2 == tunings and s2 == summary and "cached" in times2
+    mk = lambda ts: [MSM(box=L, periodic=True, precision="mixed", max_atoms=c, tuning=t, **kw)
+                     for L, c, t in zip(boxes, counts, ts)]
+    E0, _, F0 = MSMBatch(mk([None] * len(counts))).eval(pos, q, counts)
+    # the tuned tunings, and every replica on a non-default tile and the pair clusters
+    for ts in [tunings, [{"lattice_txn": 2, "lattice_tyn": 8, "pair_targets": 8}] * len(counts)]:
+        E1, _, F1 = MSMBatch(mk(ts)).eval(pos, q, counts)
+        torch.cuda.synchronize()
+        assert torch.allclose(E0, E1, rtol=1e-6, atol=0)
+        assert_atoms(F1.cpu().numpy(), F0.cpu().numpy(), 1e-5)
+    # the batch graph (one launch per stage) with those shapes
+    E = torch.zeros(len(counts), dtype=torch.float64, device=dev)
+    F = torch.zeros((len(q), 3), dtype=torch.float64, device=dev)
+    g = MSMBatch(mk([{"lattice_txn": 2, "lattice_tyn": 8, "pair_targets": 8}] * len(counts))).graph(
+        pos, q, counts, E, None, F)
+    g.launch()
     torch.cuda.synchronize()
-    assert torch.allclose(E0, E1, rtol=1e-6, atol=0)
-    assert_atoms(F1.cpu().numpy(), F0.cpu().numpy(), 1e-5)
+    g.close()
+    assert torch.allclose(E0, E, rtol=1e-6, atol=0)
+    assert_atoms(F.cpu().numpy(), F0.cpu().numpy(), 1e-5)
