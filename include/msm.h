@@ -52,7 +52,7 @@ extern "C" {
 #define MSM_ERR_NONFINITE (-5)          /* NaN/Inf position or charge (device-detected) */
 #define MSM_ERR_OOM (-6)                /* device allocation failed */
 #define MSM_ERR_CUDA (-7)               /* a CUDA runtime call failed */
-#define MSM_ERR_TIMEOUT (-8)            /* reserved: no entry point waits on the device */
+#define MSM_ERR_TIMEOUT (-8)            /* a bounded device wait gave up (the persistent batch chains) */
 #define MSM_ERR_TOO_MANY_ATOMS (-9)     /* n > max_atoms of the plan */
 #define MSM_ERR_NO_FORWARD (-10)        /* backward called before a forward on this plan */
 #define MSM_ERR_STALE_FORWARD (-11)     /* backward of a forward whose buffers a later forward reused */
@@ -97,8 +97,15 @@ typedef struct {
  *                 kernel: txn lanes of 8 x outputs by tyn lanes of two rows,
  *                 txn * tyn <= 32 (default 4 x 8 on a single system; batched
  *                 launches pick a tile per level size); both 0 or both set
+ *   batch_persistent  1: in a batched graph (msm_batch_graph_create, taken
+ *                 from the first replica's plan) the restriction and the
+ *                 prolongation of each grid sweep run as one cooperative
+ *                 launch each, the co-resident blocks meeting at a bounded
+ *                 grid barrier between passes (a wait that gives up posts
+ *                 MSM_ERR_TIMEOUT to that plan's status), instead of one
+ *                 launch per pass (0, the default)
  * Ranges: cell_fill 0..256, patch_cells 0..4, lattice_waves 0..64,
- * pair_targets 0, 8 or 32, lattice_txn and lattice_tyn 0..32 with
+ * pair_targets 0, 8 or 32, batch_persistent 0 or 1, lattice_txn and lattice_tyn 0..32 with
  * txn * tyn <= 32 and a staging window that fits shared memory; anything else
  * is INVALID_ARG (checked on the host before any device call; the window
  * check, which needs the plan's stencil, at msm_create_tuned). */
@@ -109,6 +116,7 @@ typedef struct {
   int pair_targets;
   int lattice_txn;
   int lattice_tyn;
+  int batch_persistent;
 } msm_tuning;
 
 /* Builds a plan: validates params, fixes the grid geometry, builds the

@@ -7,6 +7,8 @@ The tunables change speed, never results beyond summation order:
                  candidate volume)
   patch_cells    cells per side of the anterpolation/interpolation patch blocks
   lattice_waves  blocks per SM the lattice aims for on small levels
+  batch_persistent  batched graphs: restriction and prolongation chains as
+                 one cooperative launch each (1) or one launch per pass (0)
   lattice_tile   warp tile (txn, tyn) of the lattice kernel on the finest
                  level: txn lanes of 8 x outputs by tyn lanes of 2 rows
                  (msm_tuning.lattice_txn / lattice_tyn)
@@ -160,8 +162,8 @@ def tuned_plan(pos, q, box, periodic, cutoff, spacing, **kw):
 
 # Batches: timed on the captured batch graph (forward + adjoint), the form
 # msm_batch_graph_create runs.
-SEARCH_BATCH = [("pair_targets", [32, 8]), ("lattice_waves", [8, 16]), ("patch_cells", [3, 4]),
-                ("cell_fill", [20, 24])]
+SEARCH_BATCH = [("pair_targets", [32, 8]), ("batch_persistent", [0, 1]), ("lattice_waves", [8, 16]),
+                ("patch_cells", [3, 4]), ("cell_fill", [20, 24])]
 TILES_BATCH = [(4, 8), (2, 8), (4, 4), (8, 4), (2, 16), (1, 16)]
 
 

@@ -895,7 +895,7 @@ const char* msm_strerror(int code) {
     case MSM_ERR_NONFINITE: return "non-finite position or charge";
     case MSM_ERR_OOM: return "device allocation failed";
     case MSM_ERR_CUDA: return "CUDA error";
-    case MSM_ERR_TIMEOUT: return "bounded device wait gave up (reserved)";
+    case MSM_ERR_TIMEOUT: return "bounded device wait gave up";
     case MSM_ERR_TOO_MANY_ATOMS: return "more atoms than the plan's capacity";
     case MSM_ERR_NO_FORWARD: return "backward before forward";
     case MSM_ERR_STALE_FORWARD: return "the plan holds a later forward pass than the one named";

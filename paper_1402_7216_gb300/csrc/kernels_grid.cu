@@ -1936,6 +1936,82 @@ int ew_blocks(int64_t count) { return (int)((count + kEw - 1) / kEw); }
 
 }  // namespace
 
+// ---- persistent chains (a measured alternative to one launch per pass) ----
+// The restriction and the prolongation of a sweep are chains of small
+// dependent passes (three axes per level pair).  A persistent form runs a
+// whole chain in one cooperative launch: the co-resident blocks take the
+// virtual blocks of each pass in turn (the same tables and element bodies as
+// the per-pass launches) and meet at a grid barrier between passes.  The
+// barrier is a counter and a generation word in device memory; every wait is
+// bounded, and a wait that gives up posts kStatusTimeout and ends its block.
+struct PassDesc {
+  const void* args;   // the pass's table of per-replica arguments
+  const int* first;   // its block offsets
+  int nrep;
+  int total;          // virtual blocks of kEw elements over all replicas
+};
+constexpr int kGridSpin = 1 << 22;  // polls of the generation word before a barrier gives up
+
+// All blocks of the grid arrive, the last one releases the others.  bar[0]:
+// arrivals of the current barrier, bar[1]: generation.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) + 1u == nblocks) {
+      bar[0] = 0u;  // nobody arrives at the next barrier before the generation moves
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      for (int it = 0; *gen == g; ++it) {
+        if (it >= kGridSpin) {
+          ok = 0;
+          atomicOr(status, kStatusTimeout);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(kEw) kb_restrict_chain(const PassDesc* __restrict__ passes, int npass,
+                                                         unsigned* bar, int* status) {
+  for (int p = 0; p < npass; ++p) {
+    const PassDesc d = passes[p];
+    const AxisKArgs<double>* tab = reinterpret_cast<const AxisKArgs<double>*>(d.args);
+    for (int b = blockIdx.x; b < d.total; b += gridDim.x) {
+      const int r = batch_rep(d.first, d.nrep, b);
+      restrict_axis_body<double, ORDER>(tab[r].in, tab[r].out, tab[r].A, (int64_t)(b - d.first[r]) * kEw + threadIdx.x);
+    }
+    if (p + 1 < npass && !grid_barrier(bar, gridDim.x, status)) return;
+  }
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(kEw) kb_prolong_chain(const PassDesc* __restrict__ passes, int npass,
+                                                        unsigned* bar, int* status) {
+  for (int p = 0; p < npass; ++p) {
+    const PassDesc d = passes[p];
+    const AxisKArgs<float>* tab = reinterpret_cast<const AxisKArgs<float>*>(d.args);
+    for (int b = blockIdx.x; b < d.total; b += gridDim.x) {
+      const int r = batch_rep(d.first, d.nrep, b);
+      prolong_axis_body<float, ORDER>(tab[r].in, tab[r].out, tab[r].A, tab[r].acc,
+                                      (int64_t)(b - d.first[r]) * kEw + threadIdx.x);
+    }
+    if (p + 1 < npass && !grid_barrier(bar, gridDim.x, status)) return;
+  }
+}
+
 struct GridBatch {
   int order = 3;
   int maxlev = 1;
@@ -1952,6 +2028,15 @@ struct GridBatch {
   std::vector<BatchTable<AxisKArgs<float>>> prol[2];  // [dir][3 k + pass]
   BatchTable<InterpKArgs<float, double>> interp[2];
   BatchTable<EnergyKArgs> energy;
+  // persistent chains: pass descriptors of the restriction and prolongation
+  // of each direction, barrier words, the status word they post to
+  bool persistent = false;
+  PassDesc* chain_restr[2] = {nullptr, nullptr};
+  PassDesc* chain_prol[2] = {nullptr, nullptr};
+  int n_restr = 0, n_prol = 0;
+  unsigned* bar = nullptr;
+  int* status = nullptr;
+  int chain_blocks = 0;
 };
 
 void grid_batch_free(GridBatch* b) {
@@ -1970,6 +2055,11 @@ void grid_batch_free(GridBatch* b) {
     b->interp[d].release();
   }
   b->energy.release();
+  for (int d = 0; d < 2; ++d) {
+    if (b->chain_restr[d]) cudaFree(b->chain_restr[d]);
+    if (b->chain_prol[d]) cudaFree(b->chain_prol[d]);
+  }
+  if (b->bar) cudaFree(b->bar);
   delete b;
 }
 
@@ -2206,12 +2296,58 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
     }
   }
   (void)R;
+  // persistent chains (replica 0's plan asks for them): one cooperative launch
+  // per chain, as many blocks as are co-resident
+  if (e == cudaSuccess && !reps.empty() && reps[0].plan->batch_persistent) {
+    const bool o3 = B->order == 3;
+    int dev = 0, nsm = 0, per_r = 0, per_p = 0;
+    chk(cudaGetDevice(&dev));
+    chk(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    chk(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_r, (const void*)(o3 ? kb_restrict_chain<3> : kb_restrict_chain<5>), kEw, 0));
+    chk(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_p, (const void*)(o3 ? kb_prolong_chain<3> : kb_prolong_chain<5>), kEw, 0));
+    B->chain_blocks = nsm * std::max(1, std::min(per_r, per_p));
+    for (int dir = 0; dir < (backward ? 2 : 1) && e == cudaSuccess; ++dir) {
+      std::vector<PassDesc> rd, pd;
+      for (int k = 0; k + 1 < B->maxlev; ++k)
+        for (int ax = 0; ax < 3; ++ax) {
+          const auto& t = B->restr[dir][3 * k + ax];
+          if (t.total > 0) rd.push_back(PassDesc{t.args, t.first, t.nrep, t.total});
+        }
+      for (int k = B->maxlev - 2; k >= 0; --k)
+        for (int i = 0; i < 3; ++i) {
+          const auto& t = B->prol[dir][3 * k + i];
+          if (t.total > 0) pd.push_back(PassDesc{t.args, t.first, t.nrep, t.total});
+        }
+      B->n_restr = (int)rd.size();
+      B->n_prol = (int)pd.size();
+      chk(cudaMalloc((void**)&B->chain_restr[dir], sizeof(PassDesc) * std::max<size_t>(1, rd.size())));
+      chk(cudaMalloc((void**)&B->chain_prol[dir], sizeof(PassDesc) * std::max<size_t>(1, pd.size())));
+      if (e == cudaSuccess && !rd.empty())
+        chk(cudaMemcpy(B->chain_restr[dir], rd.data(), sizeof(PassDesc) * rd.size(), cudaMemcpyHostToDevice));
+      if (e == cudaSuccess && !pd.empty())
+        chk(cudaMemcpy(B->chain_prol[dir], pd.data(), sizeof(PassDesc) * pd.size(), cudaMemcpyHostToDevice));
+    }
+    chk(cudaMalloc((void**)&B->bar, 2 * sizeof(unsigned)));
+    if (e == cudaSuccess) chk(cudaMemset(B->bar, 0, 2 * sizeof(unsigned)));
+    B->status = reps[0].plan->d.status;
+    B->persistent = true;
+  }
   if (e != cudaSuccess) {
     grid_batch_free(B);
     return e;
   }
   *out = B;
   return cudaSuccess;
+}
+
+// One chain as a cooperative launch.
+template <typename K>
+cudaError_t launch_chain(GridBatch* B, K kernel, PassDesc* passes, int npass, cudaStream_t st) {
+  if (npass == 0) return cudaSuccess;
+  void* args[] = {(void*)&passes, (void*)&npass, (void*)&B->bar, (void*)&B->status};
+  return cudaLaunchCooperativeKernel((const void*)kernel, dim3(B->chain_blocks), dim3(kEw), args, 0, st);
 }
 
 template <typename A, typename K>
@@ -2226,16 +2362,26 @@ cudaError_t grid_batch_sweep(GridBatch* B, bool backward, cudaStream_t st) {
   launch_table(B->zero_fx, kb_zero, kEw, st);
   launch_table(B->anterp, o3 ? kb_anterp_fx<3> : kb_anterp_fx<5>, 256, st);
   launch_table(B->fx[d], kb_fx_to_f64, kEw, st);
-  for (int k = 0; k + 1 < B->maxlev; ++k)
-    for (int ax = 0; ax < 3; ++ax)
-      launch_table(B->restr[d][3 * k + ax], o3 ? kb_restrict_axis<3> : kb_restrict_axis<5>, kEw, st);
+  if (B->persistent) {
+    cudaError_t e = launch_chain(B, o3 ? kb_restrict_chain<3> : kb_restrict_chain<5>, B->chain_restr[d], B->n_restr, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    for (int k = 0; k + 1 < B->maxlev; ++k)
+      for (int ax = 0; ax < 3; ++ax)
+        launch_table(B->restr[d][3 * k + ax], o3 ? kb_restrict_axis<3> : kb_restrict_axis<5>, kEw, st);
+  }
   launch_table(B->conv[d], kb_f64_to_f32, kEw, st);
   launch_table(B->lattice[d], kb_lattice_f2, 32 * kLatticeZ, st);
   launch_table(B->reduce_u[d], kb_lattice_reduce, kEw, st);
   launch_table(B->top[d], kb_top, 32 * kTopWarps, st);
-  for (int k = B->maxlev - 2; k >= 0; --k)
-    for (int i = 0; i < 3; ++i)
-      launch_table(B->prol[d][3 * k + i], o3 ? kb_prolong_axis<3> : kb_prolong_axis<5>, kEw, st);
+  if (B->persistent) {
+    cudaError_t e = launch_chain(B, o3 ? kb_prolong_chain<3> : kb_prolong_chain<5>, B->chain_prol[d], B->n_prol, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    for (int k = B->maxlev - 2; k >= 0; --k)
+      for (int i = 0; i < 3; ++i)
+        launch_table(B->prol[d][3 * k + i], o3 ? kb_prolong_axis<3> : kb_prolong_axis<5>, kEw, st);
+  }
   return cudaGetLastError();
 }
 

@@ -118,6 +118,8 @@ struct Plan {
   int lattice_txn = 0, lattice_tyn = 0;
   // mixed pair kernel: targets culled together (8: clusters; 32: a cell's warp)
   int pair_targets = 32;
+  // batched graphs: restriction and prolongation chains as persistent launches
+  int batch_persistent = 0;
   // smoothing constants
   double gamma0 = 0.0;         // gamma(0)
   // level stencil
