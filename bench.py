@@ -223,7 +223,9 @@ def config_errors(dev):
     """The two small configurations against the FP64 oracle, every atom: the
     3,000-atom open water box (cubic, C1; also against the direct Coulomb
     sum, the method's own error) and the 23,558-atom periodic box (cubic,
-    C2, net +2 e), both GPU paths."""
+    C2, net +2 e), both GPU paths, with their evaluations per second (back
+    to back, eager and replayed from a one-plan graph; inputs stay in L2 at
+    this size)."""
     import torch
     import oracle as O
     from paper_1402_7216_gb300 import MSM
@@ -235,13 +237,34 @@ def config_errors(dev):
                      levels=w.levels, order=w.order, split=w.split)
         ref = O.msm(P, pos, q)
         e = {"atoms": len(q)}
+        tp, tq = torch.tensor(pos, device=dev), torch.tensor(q, device=dev)
+        stream = torch.cuda.current_stream()
+
+        def rate(fn, steps=50):
+            for _ in range(5):
+                fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(steps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return steps / (a.elapsed_time(b) * 1e-3)
         for precision in ("mixed", "fp64"):
             plan = MSM(box=w.box, periodic=w.periodic, cutoff=w.cutoff, spacing=w.spacing, levels=w.levels,
                        order=w.order, splitting=w.split, precision=precision, max_atoms=len(q))
-            E, phi, F = plan.eval(torch.tensor(pos, device=dev), torch.tensor(q, device=dev))
+            E, phi, F = plan.eval(tp, tq)
             torch.cuda.synchronize()
             plan.check_status()
             e[precision] = errors_vs(E.item(), phi.cpu().numpy(), F.cpu().numpy(), ref)
+            # evaluations per second on this small system: eager launches, and the
+            # one-plan CUDA graph (launch latency dominates at this size)
+            e[precision]["evals_per_s_eager"] = rate(lambda: plan.eval(tp, tq, out=(E, phi, F)))
+            g = plan.graph(tp, tq, E.reshape(1), phi, F)
+            e[precision]["evals_per_s_graph"] = rate(g.launch)
+            g.close()
+            plan.check_status()
             plan.close()
         if not w.periodic:
             d = O.direct_sum(pos, q)
@@ -711,8 +734,13 @@ def main():
         plan.check_status()
         return ms, prof, (E.item(), phi, F)
 
-    # mixed precision (the headline)
-    plan = make("mixed")
+    # mixed precision (the headline), with the tile shapes of the project's
+    # autotuner (each candidate timed on this system's own evaluations)
+    from paper_1402_7216_gb300.autotune import autotune
+    head_tuning, head_tune_ms = autotune(pos, q, w.box, w.periodic, w.cutoff, w.spacing, levels=w.levels,
+                                         order=w.order, splitting=w.split, precision="mixed", reps=5)
+    plan = MSM(box=w.box, periodic=w.periodic, cutoff=w.cutoff, spacing=w.spacing, levels=w.levels,
+               order=w.order, splitting=w.split, precision="mixed", max_atoms=n, tuning=head_tuning)
     clocks = ClockSampler(local)
     clocks.start()
     ms, (stage_ms, launches, evals), (E_mix, phi_mix, F_mix) = timed(plan, args.steps, max(3, args.warmup), True)
@@ -843,6 +871,7 @@ def main():
                    "spacing_A": w.spacing, "h_eff_A": plan.h_eff[0], "order": w.order,
                    "splitting": w.split, "levels": plan.levels, "grid0": plan.dims[0],
                    "precision": "mixed", "l2": "flushed between timed steps (512 MB write)",
+                   "tuning": head_tuning,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 32 * n,
                 "d2h_bytes_per_step": 32 * n + 8,
@@ -855,6 +884,7 @@ def main():
                       "nominal_tflops": fp32_derived, "probe_outputs_finite": probe["finite"]},
         "kernels_ms_per_eval": kernels,
         "kernels_ms_isolated": {k: round(v, 5) for k, v in per_iso.items()},
+        "autotune_ms": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in head_tune_ms.items()},
         "ms_per_step_serial": sum(ms_iso) / len(ms_iso),
         "fp64_gpu_path": fp64,
         "batched_replicas": batched,

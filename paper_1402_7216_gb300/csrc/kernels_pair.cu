@@ -119,7 +119,6 @@ constexpr int kWarps = 4;
 #define MSM_PAIR_MINB 6
 #endif
 constexpr int kBatch = MSM_PAIR_BATCH;  // sources per queue drain (pairs per lane per drain)
-constexpr int kHome = 32;               // home-cell sources per scalar batch (one per lane)
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float fast_rsqrt(float x) {  // one MUFU.RSQ; inputs are >= a^2/... never denormal
@@ -324,10 +323,10 @@ __device__ __forceinline__ float2 poly_d(const PairCoef& C, float2 r2) {
 
 // One packed step: the lane's target (negated coordinates nax, nay, naz)
 // against two sources (bx, by, bz, bq); adds q_j times the pair potential to
-// sphi and f' d to (sx, sy, sz) with d = r_j - r_i.  Sources are never at
-// r = 0 here (the home cell, the only one holding the target itself, goes
-// through the scalar path with the self test).
-template <int M, int K>
+// sphi and f' d to (sx, sy, sz) with d = r_j - r_i.  Outside the home cell a
+// source is never at r = 0; SELF (the home cell, which holds the target
+// itself) drops a source at r = 0: its charge becomes 0 and r^2 becomes a^2.
+template <int M, int K, bool SELF = false>
 __device__ __forceinline__ void pair2(float2 bx, float2 by, float2 bz, float2 bq, float2 nax, float2 nay, float2 naz,
                                       float a2, const PairCoef& C, const WolfC<float>& W, float2& sphi, float2& sx,
                                       float2& sy, float2& sz) {
@@ -335,6 +334,10 @@ __device__ __forceinline__ void pair2(float2 bx, float2 by, float2 bz, float2 bq
   float2 r2 = __fmul2_rn(dx, dx);
   r2 = __ffma2_rn(dy, dy, r2);
   r2 = __ffma2_rn(dz, dz, r2);
+  if (SELF) {
+    bq = make_float2(r2.x > 0.f ? bq.x : 0.f, r2.y > 0.f ? bq.y : 0.f);
+    r2 = make_float2(r2.x > 0.f ? r2.x : a2, r2.y > 0.f ? r2.y : a2);
+  }
   float2 fp;
   if (K == kPairMSM) {
     // a source beyond the cutoff is evaluated at r = a, where g* and its
@@ -370,23 +373,29 @@ __device__ __forceinline__ void pair2(float2 bx, float2 by, float2 bz, float2 bq
   sz = __ffma2_rn(fp, dz, sz);
 }
 
-template <int M, int K>
+template <int M, int K, int NB = kBatch, bool SELF = false>
 __device__ __forceinline__ void pair_batch_f2(const QueueF& Q, float2 nax, float2 nay, float2 naz, float a2,
                                               const PairCoef& C, const WolfC<float>& W, float& phi, float& px,
                                               float& py, float& pz, float& cphi, float& cpx, float& cpy,
                                               float& cpz) {
   float2 sphi = make_float2(0.f, 0.f), sx = sphi, sy = sphi, sz = sphi;
   // sources jj..jj+3 load as one float4 per coordinate (two packed halves)
-#pragma unroll
-  for (int jj = 0; jj < kBatch; jj += 4) {
+  auto four = [&](int jj) {
     const float4 x4 = *reinterpret_cast<const float4*>(&Q.x[jj]);
     const float4 y4 = *reinterpret_cast<const float4*>(&Q.y[jj]);
     const float4 z4 = *reinterpret_cast<const float4*>(&Q.z[jj]);
     const float4 q4 = *reinterpret_cast<const float4*>(&Q.q[jj]);
-    pair2<M, K>(make_float2(x4.x, x4.y), make_float2(y4.x, y4.y), make_float2(z4.x, z4.y), make_float2(q4.x, q4.y),
-                nax, nay, naz, a2, C, W, sphi, sx, sy, sz);
-    pair2<M, K>(make_float2(x4.z, x4.w), make_float2(y4.z, y4.w), make_float2(z4.z, z4.w), make_float2(q4.z, q4.w),
-                nax, nay, naz, a2, C, W, sphi, sx, sy, sz);
+    pair2<M, K, SELF>(make_float2(x4.x, x4.y), make_float2(y4.x, y4.y), make_float2(z4.x, z4.y),
+                      make_float2(q4.x, q4.y), nax, nay, naz, a2, C, W, sphi, sx, sy, sz);
+    pair2<M, K, SELF>(make_float2(x4.z, x4.w), make_float2(y4.z, y4.w), make_float2(z4.z, z4.w),
+                      make_float2(q4.z, q4.w), nax, nay, naz, a2, C, W, sphi, sx, sy, sz);
+  };
+  if (K == kPairWolf) {  // two library calls per source: a rolled loop keeps the code in the instruction cache
+#pragma unroll 1
+    for (int jj = 0; jj < NB; jj += 4) four(jj);
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < NB; jj += 4) four(jj);
   }
   two_sum_add(phi, cphi, sphi.x + sphi.y);
   two_sum_add(px, cpx, sx.x + sx.y);
@@ -523,7 +532,6 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
   float* __restrict__ phis = K.phis;
   R4<float>* __restrict__ fs = K.fs;
   __shared__ QueueF queue[kWarps];
-  __shared__ R4<float> home[kWarps][kHome];
   __shared__ SegTable tables[kWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   QueueF& Q = queue[warp];
@@ -532,7 +540,7 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
   if (cell >= ncell) return;  // warp-uniform
   const int ncx = A.nc[0], ncy = A.nc[1];
   const int cx = cell % ncx, cy = (cell / ncx) % ncy, cz = cell / (ncx * ncy);
-  const float a2 = A.a2f, inv_a = A.inv_af, inv_a2s = A.inv_a2f, two_inv_a3 = A.two_inv_a3f;
+  const float a2 = A.a2f;
   const float FAR = 1e6f;
   const int i0 = cell_start[cell], i1 = cell_start[cell + 1];
   const int total = build_seg_table(T, K, cx, cy, cz, lane);
@@ -554,18 +562,16 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
     }
     const float2 nax = make_float2(-ai.x, -ai.x), nay = make_float2(-ai.y, -ai.y), naz = make_float2(-ai.z, -ai.z);
     float phi = 0.f, px = 0.f, py = 0.f, pz = 0.f, cphi = 0.f, cpx = 0.f, cpy = 0.f, cpz = 0.f;
-    // home cell: scalar batches with the self test
+    // home cell: packed batches of 32 with the self test (the queue is empty here)
     for (int jb = i0; jb < i1; jb += 32) {
       const int j = jb + lane;
-      home[warp][lane] = (j < i1) ? atoms[j] : R4<float>{FAR, FAR, FAR, 0.f};
+      const R4<float> h = (j < i1) ? atoms[j] : R4<float>{FAR, FAR, FAR, 0.f};
+      Q.x[lane] = h.x;
+      Q.y[lane] = h.y;
+      Q.z[lane] = h.z;
+      Q.q[lane] = h.w;
       __syncwarp();
-      float hphi = 0.f, hx_ = 0.f, hy_ = 0.f, hz_ = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-      pair_batch<float, M, true, KIND, kHome>(home[warp], ai, a2, inv_a, inv_a2s, two_inv_a3, W, hphi, hx_, hy_,
-                                              hz_, c0, c1, c2, c3);
-      two_sum_add(phi, cphi, hphi + c0);
-      two_sum_add(px, cpx, hx_ + c1);
-      two_sum_add(py, cpy, hy_ + c2);
-      two_sum_add(pz, cpz, hz_ + c3);
+      pair_batch_f2<M, KIND, 32, true>(Q, nax, nay, naz, a2, C, W, phi, px, py, pz, cphi, cpx, cpy, cpz);
       __syncwarp();
     }
     // ---- the neighbour rows: flat source index t in [0, total), 32 per step ----
