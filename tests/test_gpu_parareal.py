@@ -131,6 +131,30 @@ def test_parareal_converges_to_the_sequential_fine_run(dev):
         assert np.abs(lv[k].cpu().numpy() - sv.cpu().numpy()).max() < 1e-8
 
 
+def test_mixed_parareal_reaches_the_sequential_fine_run_exactly(dev):
+    """Mixed precision, G = MSM with half the cutoff: the mixed path is
+    bit-reproducible, so the change per iteration falls to exactly 0 and
+    after W iterations every time point equals the sequential fine run to
+    the rounding of the correction g + (f - g) (1e-12; the noise floor of a
+    path whose sums vary between runs was 1e-5 A)."""
+    from paper_1402_7216_gb300 import MSM, parareal
+    pos, q, im, vel = system(60, 35)
+    W, dtf, sf = 4, 0.05, 4
+    fine = [make_plan(len(q), "mixed") for _ in range(W)]
+    coarse = MSM(box=L, periodic=True, cutoff=0.5 * A, spacing=H, order=3, splitting=2, precision="mixed",
+                 max_atoms=len(q))
+    tp, tv, ti, tq = dev_tensors(dev, pos, vel, im, q)
+    lp, lv, iters, ch = parareal(fine, coarse, tp, tv, ti, tq, W, dtf, sf, 0.1, 2, W + 1, 0.0,
+                                 coarse_method="msm")
+    assert iters == W + 1 and ch[-1][0] == 0.0 and ch[-1][1] == 0.0
+    seq = make_plan(len(q), "mixed")
+    sp, sv, si, sq = dev_tensors(dev, pos, vel, im, q)
+    for k in range(1, W + 1):
+        seq.md_run(sp, sv, si, sq, dtf, sf)
+        assert (lp[k] - sp).abs().max().item() <= 1e-12, k
+        assert (lv[k] - sv).abs().max().item() <= 1e-12, k
+
+
 def test_parareal_argument_errors(dev):
     from paper_1402_7216_gb300 import MSMError, parareal
     pos, q, im, vel = system(20, 34)
