@@ -104,8 +104,18 @@ typedef struct {
  *                 grid barrier between passes (a wait that gives up posts
  *                 MSM_ERR_TIMEOUT to that plan's status), instead of one
  *                 launch per pass (0, the default)
+ *   lattice_method  the lattice cutoff of a periodic plan evaluated alone:
+ *                 1 the direct stencil sum over staged shared-memory bricks,
+ *                 2 the same cyclic convolution by FFT (five passes over the
+ *                 level's grid; the kernel's transform computed in FP64 when
+ *                 the plan is built) where every lattice level's sizes are
+ *                 products of 2, 3, 5 and 7 up to 4096, the stencil
+ *                 elsewhere; 0 the default (1 until measured).  Open plans
+ *                 and batched graphs use the stencil; msm_lattice_method
+ *                 reports the form a plan took.
  * Ranges: cell_fill 0..256, patch_cells 0..4, lattice_waves 0..64,
- * pair_targets 0, 8 or 32, batch_persistent 0 or 1, lattice_txn and lattice_tyn 0..32 with
+ * pair_targets 0, 8 or 32, batch_persistent 0 or 1, lattice_method 0..2,
+ * lattice_txn and lattice_tyn 0..32 with
  * txn * tyn <= 32 and a staging window that fits shared memory; anything else
  * is INVALID_ARG (checked on the host before any device call; the window
  * check, which needs the plan's stencil, at msm_create_tuned). */
@@ -117,6 +127,7 @@ typedef struct {
   int lattice_txn;
   int lattice_tyn;
   int batch_persistent;
+  int lattice_method;
 } msm_tuning;
 
 /* Builds a plan: validates params, fixes the grid geometry, builds the
@@ -144,6 +155,11 @@ void msm_destroy(msm_handle h);
  * grids; grid point i of level k sits at i * 2^k * h_eff).  dims and lo may
  * be NULL, else hold 3*levels ints.  Host only; Errors: INVALID_ARG. */
 int msm_query(msm_handle h, double h_eff[3], int* levels, int* dims, int* lo);
+
+/* *method = the lattice-cutoff form plan h evaluates with: 1 the stencil
+ * sum, 2 the FFT convolution (msm_tuning.lattice_method).
+ * Errors: INVALID_ARG (null handle or pointer). */
+int msm_lattice_method(msm_handle h, int* method);
 
 /* The grid geometry msm_create would give these parameters, as msm_query
  * reports it, computed on the host alone: no device call, no allocation (it

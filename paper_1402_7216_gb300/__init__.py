@@ -43,8 +43,11 @@ class MSM:
     levels: l (0 = automatic); order: 3 cubic / 5 quintic; splitting: Taylor
     order m of gamma (1, 2, 3); precision: "fp64" or "mixed"; coulomb_k:
     prefactor; max_atoms: capacity of the workspace; tuning: optional tile
-    shapes {"cell_fill", "patch_cells", "lattice_waves", "pair_targets", "lattice_txn",
-    "lattice_tyn"} (see autotune.py and msm_tuning in include/msm.h).
+    shapes and methods, any of the fields of msm_tuning in include/msm.h
+    ({"cell_fill", "patch_cells", "lattice_waves", "pair_targets", "lattice_txn",
+    "lattice_tyn", "batch_persistent", "lattice_method"}; see autotune.py).
+    After construction, lattice_method says which lattice-cutoff form the
+    plan took ("stencil" or "fft").
     """
 
     def __init__(self, box, periodic, cutoff, spacing, levels=0, order=3, splitting=2,
@@ -79,6 +82,9 @@ class MSM:
         self.levels = nl.value
         self.dims = [tuple(dims[3 * k:3 * k + 3]) for k in range(self.levels)]
         self.lo = [tuple(lo[3 * k:3 * k + 3]) for k in range(self.levels)]
+        lm = C.c_int()
+        _capi.check(L.msm_lattice_method(self._h, C.byref(lm)), "msm_lattice_method")
+        self.lattice_method = {1: "stencil", 2: "fft"}[lm.value]
 
     def close(self):
         if self._h:

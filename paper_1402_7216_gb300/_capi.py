@@ -30,7 +30,7 @@ class MSMParams(C.Structure):
 class MSMTuning(C.Structure):
     _fields_ = [("cell_fill", C.c_int), ("patch_cells", C.c_int), ("lattice_waves", C.c_int),
                 ("pair_targets", C.c_int), ("lattice_txn", C.c_int), ("lattice_tyn", C.c_int),
-                ("batch_persistent", C.c_int)]
+                ("batch_persistent", C.c_int), ("lattice_method", C.c_int)]
 
 
 class MSMError(RuntimeError):
@@ -44,7 +44,7 @@ _D = C.POINTER(C.c_double)
 EXPORTS = ["msm_create", "msm_create_tuned", "msm_destroy", "msm_query", "msm_geometry", "msm_eval", "msm_cutoff_eval",
            "msm_wolf_eval", "msm_set_wolf_alpha", "msm_md_run", "msm_md_run_batch",
            "msm_parareal_workspace", "msm_parareal",
-           "msm_eval_backward", "msm_forward_id",
+           "msm_eval_backward", "msm_forward_id", "msm_lattice_method",
            "msm_eval_f32io", "msm_eval_backward_f32io",
            "msm_eval_host", "msm_status", "msm_debug_grid", "msm_set_overlap", "msm_profile", "msm_profile_read",
            "msm_stage_name", "msm_energy_noalloc", "msm_eval_batch", "msm_eval_backward_batch",
@@ -93,6 +93,8 @@ def load(path=LIB_PATH):
     L.msm_eval_backward.restype = C.c_int
     L.msm_forward_id.argtypes = [vp, C.POINTER(C.c_int64)]
     L.msm_forward_id.restype = C.c_int
+    L.msm_lattice_method.argtypes = [vp, C.POINTER(C.c_int)]
+    L.msm_lattice_method.restype = C.c_int
     L.msm_eval_f32io.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp]
     L.msm_eval_f32io.restype = C.c_int
     L.msm_eval_backward_f32io.argtypes = [vp, C.c_int64, vp, vp, vp, vp]

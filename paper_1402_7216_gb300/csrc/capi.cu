@@ -49,17 +49,26 @@ cudaError_t stage(Plan& P, int which, cudaStream_t st, F&& launch) {
   return e;
 }
 
-// The grid sweep shared by the forward pass and its adjoint: starting from
-// the level-0 charges in q[0], fills q[1..l-1] by restriction, u[k] by the
-// lattice cutoff and the top level, then prolongates u down to level 0.
-cudaError_t grid_sweep(Plan& P, void* const* q, void* const* u, cudaStream_t st) {
+// The grid sweep shared by the forward pass and its adjoint (dir 0: the
+// grids gq/gu, 1: aq/au): starting from the level-0 charges in q[0], fills
+// q[1..l-1] by restriction, u[k] by the lattice cutoff and the top level,
+// then prolongates u down to level 0.  The FFT form of the lattice cutoff
+// takes every level in one set of launches, after the last restriction.
+cudaError_t grid_sweep(Plan& P, int dir, cudaStream_t st) {
+  void* const* q = dir ? P.d.aq : P.d.gq;
+  void* const* u = dir ? P.d.au : P.d.gu;
   cudaError_t e = cudaSuccess;
   int l = P.levels;
   for (int k = 0; k + 1 < l && e == cudaSuccess; ++k) {
     e = stage(P, MSM_STAGE_RESTRICTION, st, [&] { return launch_restrict(P, k, q[k], q[k + 1], st); });
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !P.lattice_fft)
       e = stage(P, MSM_STAGE_LATTICE, st, [&] { return launch_lattice(P, k, q[k], u[k], st); });
   }
+  if (e == cudaSuccess && P.lattice_fft)
+    e = stage(P, MSM_STAGE_LATTICE, st, [&] {
+      P.launches += 5;
+      return fft_batch_launch(P.fftb[dir], st);
+    });
   if (e == cudaSuccess) e = stage(P, MSM_STAGE_TOP, st, [&] { return launch_top(P, q[l - 1], u[l - 1], st); });
   for (int k = l - 2; k >= 0 && e == cudaSuccess; --k)
     e = stage(P, MSM_STAGE_PROLONGATION, st, [&] { return launch_prolong(P, k, u[k + 1], u[k], st); });
@@ -87,7 +96,7 @@ int forward(Plan& P, int64_t n, const IO* pos, const IO* q, double* energy, IO* 
     e = stage(P, MSM_STAGE_ANTERPOLATION, gs,
               [&] { return launch_anterpolate(P, n, P.d.gq[0], nullptr, 1.0, gs); });
   if (e == cudaSuccess) e = stage(P, MSM_STAGE_SHORT_RANGE, st, [&] { return launch_short_range(P, n, st); });
-  if (e == cudaSuccess) e = grid_sweep(P, P.d.gq, P.d.gu, gs);
+  if (e == cudaSuccess) e = grid_sweep(P, 0, gs);
   // the grid gather needs only u^0, so it runs on the grid's stream, under
   // the pair sums; the assembly waits for both
   if (e == cudaSuccess) e = stage(P, MSM_STAGE_INTERPOLATION, gs, [&] { return launch_interp_gather(P, n, gs); });
@@ -118,7 +127,7 @@ int backward(Plan& P, int64_t forward_id, const double* grad_energy, IO* grad_po
   // and interpolate the result back to the atoms.
   cudaError_t e = stage(P, MSM_STAGE_ANTERPOLATION, st,
                         [&] { return launch_anterpolate(P, n, P.d.aq[0], grad_energy, 0.5, st); });
-  if (e == cudaSuccess) e = grid_sweep(P, P.d.aq, P.d.au, st);
+  if (e == cudaSuccess) e = grid_sweep(P, 1, st);
   if (e == cudaSuccess)
     e = stage(P, MSM_STAGE_INTERPOLATION, st,
               [&] { return launch_interp_backward(P, n, grad_energy, grad_pos, grad_q, st); });
@@ -466,6 +475,12 @@ int msm_query(msm_handle h, double h_eff[3], int* levels, int* dims, int* lo) {
       if (dims) dims[3 * k + d] = P.n[k][d];
       if (lo) lo[3 * k + d] = P.lo[k][d];
     }
+  return MSM_OK;
+}
+
+int msm_lattice_method(msm_handle h, int* method) {
+  if (!h || !method) return MSM_ERR_INVALID_ARG;
+  *method = h->p.lattice_fft ? 2 : 1;
   return MSM_OK;
 }
 

@@ -2024,6 +2024,7 @@ struct GridBatch {
   BatchTable<ReduceKArgs> reduce_u[2];  // split lattice partials -> u, in part order
   float* lparts[2] = {nullptr, nullptr};
   BatchTable<LatKArgs> lattice[2];
+  FftBatch* fft[2] = {nullptr, nullptr};  // the FFT form, when every replica's plan took it
   BatchTable<TopKArgs> top[2];
   std::vector<BatchTable<AxisKArgs<float>>> prol[2];  // [dir][3 k + pass]
   BatchTable<InterpKArgs<float, double>> interp[2];
@@ -2050,6 +2051,7 @@ void grid_batch_free(GridBatch* b) {
     b->reduce_u[d].release();
     if (b->lparts[d]) cudaFree(b->lparts[d]);
     b->lattice[d].release();
+    fft_batch_free(b->fft[d]);
     b->top[d].release();
     for (auto& t : b->prol[d]) t.release();
     b->interp[d].release();
@@ -2145,10 +2147,30 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
         }
         chk(make_table(B->restr[dir][3 * k + ax], ra, rb));
       }
-    // lattice cutoff of every level below the top, all in one launch: FP32
-    // copies of the charges at offsets of tmp[0], the outputs zeroed where
-    // several blocks add into them
-    {
+    // lattice cutoff of every level below the top.  FFT form (every plan
+    // periodic and built with it): five launches over all levels of all
+    // replicas, level k of a replica working at offset sum_{j<k} N_j of its
+    // plan's complex workspace
+    bool all_fft = true;
+    for (const BatchRep& r : reps) all_fft = all_fft && r.plan->lattice_fft;
+    if (all_fft) {
+      std::vector<FftBatchItem> items;
+      for (const BatchRep& r : reps) {
+        Plan& P = *r.plan;
+        void* const* q = dir ? P.d.aq : P.d.gq;
+        void* const* u = dir ? P.d.au : P.d.gu;
+        int64_t off = 0;
+        for (int k = 0; k + 1 < P.levels; ++k) {
+          items.push_back(FftBatchItem{&P.fftl[k], (const double*)q[k], u[k],
+                                       (char*)P.d.fft_work + 2 * sizeof(float) * (size_t)off});
+          off += grid_points(P, k);
+        }
+      }
+      chk(fft_batch_build(items, false, &B->fft[dir]));
+    }
+    // otherwise the stencil, all in one launch: FP32 copies of the charges at
+    // offsets of tmp[0], the outputs zeroed where several blocks add into them
+    if (!all_fft) {
       std::vector<ConvKArgs> ca;
       std::vector<LatKArgs> la;
       std::vector<int> cb, lb;
@@ -2370,9 +2392,14 @@ cudaError_t grid_batch_sweep(GridBatch* B, bool backward, cudaStream_t st) {
       for (int ax = 0; ax < 3; ++ax)
         launch_table(B->restr[d][3 * k + ax], o3 ? kb_restrict_axis<3> : kb_restrict_axis<5>, kEw, st);
   }
-  launch_table(B->conv[d], kb_f64_to_f32, kEw, st);
-  launch_table(B->lattice[d], kb_lattice_f2, 32 * kLatticeZ, st);
-  launch_table(B->reduce_u[d], kb_lattice_reduce, kEw, st);
+  if (B->fft[d]) {
+    cudaError_t e = fft_batch_launch(B->fft[d], st);
+    if (e != cudaSuccess) return e;
+  } else {
+    launch_table(B->conv[d], kb_f64_to_f32, kEw, st);
+    launch_table(B->lattice[d], kb_lattice_f2, 32 * kLatticeZ, st);
+    launch_table(B->reduce_u[d], kb_lattice_reduce, kEw, st);
+  }
   launch_table(B->top[d], kb_top, 32 * kTopWarps, st);
   if (B->persistent) {
     cudaError_t e = launch_chain(B, o3 ? kb_prolong_chain<3> : kb_prolong_chain<5>, B->chain_prol[d], B->n_prol, st);
@@ -2431,6 +2458,7 @@ cudaError_t configure_kernels() {
   set((const void*)k_interp_bwd<double, 3, float>);
   set((const void*)k_interp_bwd<double, 5, double>);
   set((const void*)k_interp_bwd<double, 5, float>);
+  if (e == cudaSuccess) e = configure_fft_kernels();
   return e;
 }
 

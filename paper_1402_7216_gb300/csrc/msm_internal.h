@@ -66,6 +66,8 @@ struct DeviceBuffers {
   void* au[kMaxLevels] = {};
   // lattice partial sums of levels split over several blocks: [nsplit][points] in T
   void* lparts = nullptr;
+  // complex work grid of the FFT lattice (the largest convolved level, FP64 complex)
+  void* fft_work = nullptr;
   // separable restriction / prolongation temporaries (each as large as level 0, in doubles)
   void* tmp[2] = {nullptr, nullptr};
   // top level (always FP64)
@@ -95,6 +97,18 @@ struct DeviceBuffers {
   int* hstatus = nullptr;  // pinned host copy of the status word, read after the call's one sync
 };
 
+// The lattice cutoff of one periodic level as an FFT convolution (fft.cu):
+// the level's dimensions, twiddle tables per axis and the kernel's transform
+// (real, with the level factor 2^-k and the inverse's 1/N), in the plan's
+// precision.
+struct FftLevel {
+  int n[3] = {0, 0, 0};
+  void* tw[3] = {nullptr, nullptr, nullptr};
+  void* khat = nullptr;
+};
+// The five passes' argument tables over a list of levels (fft.cu).
+struct FftBatch;
+
 struct Plan {
   msm_params P;
   bool fp64 = false;
@@ -120,6 +134,10 @@ struct Plan {
   int pair_targets = 32;
   // batched graphs: restriction and prolongation chains as persistent launches
   int batch_persistent = 0;
+  // lattice cutoff of periodic levels as an FFT convolution (fft.cu)
+  bool lattice_fft = false;
+  FftLevel fftl[kMaxLevels];
+  FftBatch* fftb[2] = {nullptr, nullptr};  // every lattice level: the forward sweep's grids, the adjoint's
   // smoothing constants
   double gamma0 = 0.0;         // gamma(0)
   // level stencil
@@ -297,6 +315,24 @@ void lattice_tile_of(const Plan& P, int k, int& txn, int& tyn);
 bool lattice_tile_fits(const Plan& P, int txn, int tyn);  // the tile's staging window fits shared memory
 int64_t lattice_parts_elems(const Plan& P);
 cudaError_t launch_lattice(Plan& P, int k, const void* qk, void* uk, cudaStream_t s);
+// the FFT form (fft.cu): tables per level, the convolution, one-time attributes
+bool fft_size_ok(int n);
+cudaError_t fft_build_level(Plan& P, int k, const std::vector<double>& K, void* work);
+void fft_free_level(FftLevel& F);
+cudaError_t configure_fft_kernels();
+// One launch per pass over every listed level (of one plan, or of every
+// replica of a batch).  Each item is one level: its tables, its FP64
+// charges, its potential (FP32, or FP64 with fp64) and a complex workspace
+// of its size in that precision.
+struct FftBatchItem {
+  const FftLevel* F;
+  const double* q;
+  void* u;
+  void* work;
+};
+cudaError_t fft_batch_build(const std::vector<FftBatchItem>& items, bool fp64, FftBatch** out);
+cudaError_t fft_batch_launch(const FftBatch* b, cudaStream_t s);
+void fft_batch_free(FftBatch* b);
 cudaError_t launch_top(Plan& P, const void* qt, void* ut, cudaStream_t s);
 cudaError_t launch_prolong(Plan& P, int k, const void* coarse, void* fine, cudaStream_t s);
 // interpolation of u^0 at the atoms and assembly of E, phi, F (forward) in two

@@ -266,6 +266,7 @@ int validate_tuning(const msm_tuning* t) {
     return MSM_ERR_INVALID_ARG;
   if (t->pair_targets != 0 && t->pair_targets != 8 && t->pair_targets != 32) return MSM_ERR_INVALID_ARG;
   if (t->batch_persistent != 0 && t->batch_persistent != 1) return MSM_ERR_INVALID_ARG;
+  if (t->lattice_method < 0 || t->lattice_method > 2) return MSM_ERR_INVALID_ARG;
   if (t->lattice_txn < 0 || t->lattice_tyn < 0 || t->lattice_txn > 32 || t->lattice_tyn > 32 ||
       (t->lattice_txn == 0) != (t->lattice_tyn == 0) || t->lattice_txn * t->lattice_tyn > 32)
     return MSM_ERR_INVALID_ARG;
@@ -288,13 +289,14 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   if (vrc != MSM_OK) return vrc;
   int trc = validate_tuning(tune);
   if (trc != MSM_OK) return trc;
-  msm_tuning TU = {0, 0, 0, 0, 0, 0, 0};
+  msm_tuning TU = {0, 0, 0, 0, 0, 0, 0, 0};
   if (tune) TU = *tune;
   const double fill = TU.cell_fill > 0 ? TU.cell_fill : 24.0;
   P->lattice_waves = TU.lattice_waves > 0 ? TU.lattice_waves : 8;
   P->pair_targets = TU.pair_targets > 0 ? TU.pair_targets : 32;
   P->lattice_txn = TU.lattice_txn;
   P->batch_persistent = TU.batch_persistent;
+  const int lattice_method = TU.lattice_method > 0 ? TU.lattice_method : 1;
   P->lattice_tyn = TU.lattice_tyn;
   P->wolf_alpha = 2.4 / p.cutoff;  // alpha R = 2.4 (0.2 per length unit at R = 12) until msm_set_wolf_alpha
   for (int d = 0; d < 3; ++d)
@@ -428,6 +430,12 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
         if (g != 0.0) taps += 1;
       }
   P->stencil_taps = taps;
+  // FFT form of the lattice cutoff (periodic levels whose sizes factor into
+  // radices 2, 3, 5, 7; built after the workspace below)
+  bool want_fft = p.periodic && lattice_method == 2 && P->levels > 1;
+  for (int k = 0; k + 1 < P->levels && want_fft; ++k)
+    for (int d = 0; d < 3; ++d)
+      if (!fft_size_ok(P->n[k][d])) want_fft = false;
 
   // top-level kernel table (FP64)
   int top = P->levels - 1;
@@ -529,8 +537,46 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   M((void**)&D.md_partial, sizeof(double) * 4 * kMdBlocks);
   M((void**)&D.md_step, sizeof(int));
   M((void**)&D.status, sizeof(int));
+  if (want_fft) {  // complex FP64 per point of every lattice level (the kernel's transforms use level 0's share)
+    size_t pts = 0;
+    for (int k = 0; k + 1 < P->levels; ++k) pts += (size_t)grid_points(*P, k);
+    M(&D.fft_work, 16 * pts);
+  }
   if (e != cudaSuccess) return MSM_ERR_OOM;
   if (cudaMemset(D.status, 0, sizeof(int)) != cudaSuccess) return MSM_ERR_CUDA;
+  if (want_fft) {
+    // the folded kernel of level k on its own grid: taps n wrapped modulo the
+    // level's dimensions (the images of the sphere where it is wider than the
+    // grid), values G0(n) (the level factor is applied with the transform)
+    for (int k = 0; k + 1 < P->levels; ++k) {
+      const int M0 = P->n[k][0], M1 = P->n[k][1], M2 = P->n[k][2];
+      std::vector<double> Kg((size_t)M0 * M1 * M2, 0.0);
+      for (int dz = -P->E[2]; dz <= P->E[2]; ++dz)
+        for (int dy = -P->E[1]; dy <= P->E[1]; ++dy)
+          for (int dx = -P->E[0]; dx <= P->E[0]; ++dx) {
+            const double g = G[((size_t)(dz + P->E[2]) * (2 * P->E[1] + 1) + (dy + P->E[1])) * (2 * P->E[0] + 1) +
+                               (dx + P->E[0])];
+            if (g == 0.0) continue;
+            const int x = ((dx % M0) + M0) % M0, y = ((dy % M1) + M1) % M1, z = ((dz % M2) + M2) % M2;
+            Kg[((size_t)z * M1 + y) * M0 + x] += g;
+          }
+      if (fft_build_level(*P, k, Kg, D.fft_work) != cudaSuccess) return MSM_ERR_CUDA;
+    }
+    // the pass tables of both sweeps: level k at offset sum_{j<k} N_j of the
+    // workspace, in complex elements of the plan's precision
+    const size_t cs = P->fp64 ? 2 * sizeof(double) : 2 * sizeof(float);
+    for (int dir = 0; dir < 2; ++dir) {
+      std::vector<FftBatchItem> items;
+      size_t off = 0;
+      for (int k = 0; k + 1 < P->levels; ++k) {
+        items.push_back(FftBatchItem{&P->fftl[k], (const double*)(dir ? D.aq[k] : D.gq[k]), dir ? D.au[k] : D.gu[k],
+                                     (char*)D.fft_work + cs * off});
+        off += (size_t)grid_points(*P, k);
+      }
+      if (fft_batch_build(items, P->fp64, &P->fftb[dir]) != cudaSuccess) return MSM_ERR_CUDA;
+    }
+    P->lattice_fft = true;
+  }
   if (upload((void**)&D.topK, K) != cudaSuccess) return MSM_ERR_OOM;
   if (upload((void**)&D.cell_off, offs) != cudaSuccess) return MSM_ERR_OOM;
   if (upload((void**)&D.cell_rows, rowv) != cudaSuccess) return MSM_ERR_OOM;
@@ -571,12 +617,17 @@ void free_plan(Plan* P) {
   void* ptrs[] = {D.key, D.rank, D.perm, D.count, D.csum, D.cell_start, D.atoms,
                   D.gfrac, D.gbase, D.phis, D.fs, D.glong, D.topK, D.topq, D.topu, D.seg, D.seg2, D.cell_shift, D.cell_rows,
                   D.seg_start, D.cell_off, D.partial, D.scalars, D.md_partial, D.md_step, D.status, D.hpos, D.hq,
-                  D.hphi, D.hforce, D.henergy, D.lparts};
+                  D.hphi, D.hforce, D.henergy, D.lparts, D.fft_work};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (D.hstatus) cudaFreeHost(D.hstatus);
   for (int i = 0; i < 2; ++i)
     if (D.tmp[i]) cudaFree(D.tmp[i]);
+  for (int k = 0; k < kMaxLevels; ++k) fft_free_level(P->fftl[k]);
+  for (int dir = 0; dir < 2; ++dir) {
+    fft_batch_free(P->fftb[dir]);
+    P->fftb[dir] = nullptr;
+  }
   for (int k = 0; k < kMaxLevels; ++k) {
     if (D.gq[k]) cudaFree(D.gq[k]);
     if (D.gu[k]) cudaFree(D.gu[k]);
