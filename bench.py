@@ -115,14 +115,25 @@ def work_model(plan, n, box, cutoff, order):
     rho = n / V
     pairs = 0.5 * n * (4.0 / 3.0) * math.pi * cutoff ** 3 * rho   # unordered pairs within a
     W3 = (order + 1) ** 3
-    taps = plan_taps(plan)
     pts = [d[0] * d[1] * d[2] for d in plan.dims]
     lat_pts = sum(pts[:-1])
+    if getattr(plan, "lattice_method", "stencil") == "fft":
+        # the same convolution by FFT: a complex 3-D transform each way (5 N log2 N
+        # flop each, the usual count) and the product by the real K^ (2 N); the
+        # fewest bytes are the FP64 charges in and the FP32 potential out (12 per
+        # point); the five passes move 80 bytes per point (FP32 complex grid read
+        # and written each pass, K^ once, q in, u out)
+        fft_flop = sum(10.0 * p * math.log2(p) + 2.0 * p for p in pts[:-1])
+        lattice = {"flop": fft_flop, "bytes": 12.0 * lat_pts, "pass_bytes": 80.0 * lat_pts,
+                   "units": "%d points, FFT convolution (10 N log2 N + 2 N flop per level)" % lat_pts}
+    else:
+        taps = plan_taps(plan)
+        lattice = {"flop": 2.0 * taps * lat_pts, "bytes": 12.0 * lat_pts,
+                   "units": "%d points x %d taps" % (lat_pts, taps)}
     return {
         "short_range": {"flop": PAIR_FLOP * pairs, "bytes": 36.0 * n, "pairs": pairs,
                         "units": "%.4g pairs within a (each counted once) x %g flop" % (pairs, PAIR_FLOP)},
-        "lattice_cutoff": {"flop": 2.0 * taps * lat_pts, "bytes": 12.0 * lat_pts,
-                           "units": "%d points x %d taps" % (lat_pts, taps)},
+        "lattice_cutoff": lattice,
         "anterpolation": {"flop": 3.0 * W3 * n, "bytes": 32.0 * n + 8.0 * pts[0]},
         "interpolation": {"flop": 8.0 * W3 * n, "bytes": 68.0 * n + 4.0 * pts[0]},
         "binning": {"flop": 0.0, "bytes": 32.0 * n + 4 * 8.0 * n * 2 + 64.0 * n},
@@ -289,12 +300,12 @@ def bench_large(dev, args):
     torch.cuda.synchronize()
     torch.cuda.reset_peak_memory_stats(dev)
     free0 = torch.cuda.mem_get_info(dev)[0]
-    # the lattice warp tile of the finest grid from the project's autotuner,
-    # timed on forward + adjoint (the lattice is most of both at this size)
+    # the lattice form (FFT or stencil) and, for the stencil, the warp tile of
+    # the finest grid from the project's autotuner, timed on forward + adjoint
     from paper_1402_7216_gb300.autotune import TILES, autotune
     tuning, tune_ms = autotune(pos, q, w.box, True, w.cutoff, w.spacing, levels=w.levels, order=w.order,
-                               splitting=w.split, precision="mixed", reps=3, search=[("lattice_tile", TILES)],
-                               backward=True)
+                               splitting=w.split, precision="mixed", reps=3,
+                               search=[("lattice_method", [1]), ("lattice_tile", TILES)], backward=True)
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info(dev)[0]
     plan = MSM(box=w.box, periodic=True, cutoff=w.cutoff, spacing=w.spacing, levels=w.levels, order=w.order,

@@ -104,15 +104,16 @@ typedef struct {
  *                 grid barrier between passes (a wait that gives up posts
  *                 MSM_ERR_TIMEOUT to that plan's status), instead of one
  *                 launch per pass (0, the default)
- *   lattice_method  the lattice cutoff of a periodic plan evaluated alone:
- *                 1 the direct stencil sum over staged shared-memory bricks,
- *                 2 the same cyclic convolution by FFT (five passes over the
- *                 level's grid; the kernel's transform computed in FP64 when
- *                 the plan is built) where every lattice level's sizes are
- *                 products of 2, 3, 5 and 7 up to 4096, the stencil
- *                 elsewhere; 0 the default (1 until measured).  Open plans
- *                 and batched graphs use the stencil; msm_lattice_method
- *                 reports the form a plan took.
+ *   lattice_method  the lattice cutoff of a periodic plan: 1 the direct
+ *                 stencil sum over staged shared-memory bricks, 2 the same
+ *                 cyclic convolution by FFT (five passes over the levels'
+ *                 grids; the kernel's transform computed in FP64 when the
+ *                 plan is built) where every lattice level's sizes are c 2^s
+ *                 with c a product of 3, 5 and 7, up to 4096; 0 the default,
+ *                 2 (measured faster on every periodic workload).  Open
+ *                 plans use the stencil; a batched graph takes the FFT when
+ *                 every replica's plan did; msm_lattice_method reports the
+ *                 form a plan took.
  * Ranges: cell_fill 0..256, patch_cells 0..4, lattice_waves 0..64,
  * pair_targets 0, 8 or 32, batch_persistent 0 or 1, lattice_method 0..2,
  * lattice_txn and lattice_tyn 0..32 with

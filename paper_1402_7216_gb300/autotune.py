@@ -9,13 +9,17 @@ The tunables change speed, never results beyond summation order:
   lattice_waves  blocks per SM the lattice aims for on small levels
   batch_persistent  batched graphs: restriction and prolongation chains as
                  one cooperative launch each (1) or one launch per pass (0)
+  lattice_method periodic plans: the lattice cutoff by FFT (the default) or
+                 by the direct stencil (1, the candidate); the stencil's own
+                 fields (lattice_waves, lattice_tile) are searched only when
+                 it wins
   lattice_tile   warp tile (txn, tyn) of the lattice kernel on the finest
                  level: txn lanes of 8 x outputs by tyn lanes of 2 rows
                  (msm_tuning.lattice_txn / lattice_tyn)
 A coordinate search times each candidate with CUDA events on the caller's own
 inputs (evaluations on the caller's stream, warm-up excluded) and keeps a
 change only when it is faster by MARGIN (1 %).  Batches search the shared fields on
-the captured batch graph, then one lattice tile per finest-grid size: the
+the captured batch graph, then, with the stencil, one lattice tile per finest-grid size: the
 replicas with the same level-0 grid share a tile, since the best tile
 depends on how the grid's rows and columns fill a warp.  Results are cached
 in a JSON file keyed by the plan parameters and the atom counts
@@ -35,8 +39,15 @@ MARGIN = 0.01
 # (txn, tyn) lattice warp tiles: 32 x 16 outputs (the default) and shapes that
 # fit small or flat grids better
 TILES = [(4, 8), (2, 8), (4, 4), (8, 4), (2, 16), (8, 2), (1, 16)]
-SEARCH = [("pair_targets", [32, 8]), ("cell_fill", [20, 24, 28, 32]), ("patch_cells", [2, 3, 4]),
-          ("lattice_waves", [4, 8, 16]), ("lattice_tile", TILES)]
+SEARCH = [("lattice_method", [1]), ("pair_targets", [32, 8]), ("cell_fill", [20, 24, 28, 32]),
+          ("patch_cells", [2, 3, 4]), ("lattice_waves", [4, 8, 16]), ("lattice_tile", TILES)]
+# fields that only the stencil form of the lattice cutoff reads
+STENCIL_ONLY = ("lattice_waves", "lattice_tile")
+
+
+def uses_stencil(cand, periodic=True):
+    """Whether a candidate runs the stencil lattice (open plans always do)."""
+    return (not periodic) or int(cand.get("lattice_method", 0)) == 1
 
 
 def tuning_fields(cand):
@@ -59,7 +70,7 @@ def cache_path():
 
 def cache_key(box, periodic, cutoff, spacing, levels, order, splitting, precision, n, backward=False):
     b = box if hasattr(box, "__len__") else (box, box, box)
-    return "box=%.4f,%.4f,%.4f|per=%d|a=%.4f|h=%.4f|l=%d|p=%d|m=%d|%s|n=%d|bwd=%d" % (
+    return "v2|box=%.4f,%.4f,%.4f|per=%d|a=%.4f|h=%.4f|l=%d|p=%d|m=%d|%s|n=%d|bwd=%d" % (
         b[0], b[1], b[2], int(bool(periodic)), cutoff, spacing, levels, order, splitting, precision, n,
         int(bool(backward)))
 
@@ -104,12 +115,16 @@ def time_plan(plan, pos, q, reps=5, warmup=2, backward=False):
     return ms[len(ms) // 2]
 
 
-def _coordinate_search(run, search, start=None, times=None):
+def _coordinate_search(run, search, start=None, times=None, skip=None):
+    """Tries each field's values in turn from the best so far; skip(field,
+    best) -> True leaves a field out (it cannot change the timing)."""
     best = dict(start or {})
     times = {} if times is None else times
     best_ms = run(best)
     times[_label(best) or "default"] = best_ms
     for field, values in search:
+        if skip is not None and skip(field, best):
+            continue
         for v in values:
             cand = dict(best)
             cand[field] = list(v) if isinstance(v, tuple) else v
@@ -147,7 +162,9 @@ def autotune(pos, q, box, periodic, cutoff, spacing, levels=0, order=3, splittin
         finally:
             plan.close()
 
-    best, best_ms, times = _coordinate_search(run, search)
+    best, best_ms, times = _coordinate_search(
+        run, search, skip=lambda field, b: (field in STENCIL_ONLY and not uses_stencil(b, periodic)) or
+        (field == "lattice_method" and not periodic))
     if use_cache:
         data = _load(path)
         data[key] = {"tuning": best, "ms": best_ms}
@@ -166,8 +183,8 @@ def tuned_plan(pos, q, box, periodic, cutoff, spacing, **kw):
 
 # Batches: timed on the captured batch graph (forward + adjoint), the form
 # msm_batch_graph_create runs.
-SEARCH_BATCH = [("pair_targets", [32, 8]), ("batch_persistent", [0, 1]), ("lattice_waves", [8, 16]),
-                ("patch_cells", [3, 4]), ("cell_fill", [20, 24])]
+SEARCH_BATCH = [("lattice_method", [1]), ("pair_targets", [32, 8]), ("batch_persistent", [0, 1]),
+                ("lattice_waves", [8, 16]), ("patch_cells", [3, 4]), ("cell_fill", [20, 24])]
 TILES_BATCH = [(4, 8), (2, 8), (4, 4), (8, 4), (2, 16), (1, 16)]
 
 
@@ -191,15 +208,15 @@ def time_graph(graph, reps=5, warmup=2):
 def batch_key(boxes, counts, cutoff, spacing, order, splitting, precision):
     import hashlib
     h = hashlib.sha1(repr((list(map(float, boxes)), list(map(int, counts)))).encode()).hexdigest()[:16]
-    return "batch2|%s|a=%.4f|h=%.4f|p=%d|m=%d|%s" % (h, cutoff, spacing, order, splitting, precision)
+    return "batch3|%s|a=%.4f|h=%.4f|p=%d|m=%d|%s" % (h, cutoff, spacing, order, splitting, precision)
 
 
 def autotune_batch(boxes, pos, q, counts, cutoff, spacing, order=3, splitting=2, precision="mixed", reps=5,
                    use_cache=True, search=SEARCH_BATCH, tiles=TILES_BATCH):
     """Tunes a batch of periodic boxes (edges `boxes`, atoms `counts`,
     concatenated `pos`, `q` on the device) on its batch graph with the
-    adjoint: first the fields every replica shares, then a lattice tile per
-    finest-grid size.  Returns (per-replica tuning dicts, summary
+    adjoint: first the fields every replica shares, then (when the stencil lattice
+    wins) a lattice tile per finest-grid size.  Returns (per-replica tuning dicts, summary
     {"shared": ..., "lattice_tile_by_grid0": {M0: [txn, tyn]}}, {candidate:
     ms}); cached like autotune()."""
     from . import MSMBatch
@@ -246,9 +263,12 @@ def autotune_batch(boxes, pos, q, counts, cutoff, spacing, order=3, splitting=2,
             for p in plans:
                 p.close()
 
-    shared, best_ms, times = _coordinate_search(lambda cand: run_all(per_replica(cand, {})), search)
+    shared, best_ms, times = _coordinate_search(
+        lambda cand: run_all(per_replica(cand, {})), search,
+        skip=lambda field, b: field in STENCIL_ONLY and not uses_stencil(b))
     by_grid = {}
-    for g in sorted(set(grid0), reverse=True):  # the largest grids first: they carry the most lattice work
+    tile_grids = sorted(set(grid0), reverse=True) if uses_stencil(shared) else []
+    for g in tile_grids:  # the largest grids first: they carry the most lattice work
         def run_tile(cand, g=g):
             trial = dict(by_grid)
             if "lattice_tile" in cand:

@@ -36,6 +36,7 @@ namespace msm {
 namespace {
 
 constexpr int kFftThreads = 256;
+constexpr int kFftBatch = 4;      // global loads a thread issues together
 constexpr int kRoots = 7;          // the seventh roots of unity after the stage tables (radix 7)
 constexpr size_t kFftSmem = 48 * 1024;  // line buffers per block, the budget lines_per_block aims for
 
@@ -67,17 +68,18 @@ __device__ __forceinline__ Cx<T> conj_if(Cx<T> z, T s) {
   return Cx<T>{z.x, s > 0 ? -z.y : z.y};
 }
 
-// Size of a line: n = c 2^s with c in {1, 3, 5, 7} (every periodic grid
-// size), so x / n = (x >> s) / c, a shift and a division by a constant.
+// Sizes are n = c 2^s with c odd and a product of 3, 5 and 7, so that
+// x / n = (x >> s) / c: a shift, then a division by a constant for the usual
+// c (1, 3, 5, 7: every periodic grid size m 2^j with m <= 8) and a plain
+// division otherwise.
 __device__ __forceinline__ int div_c(int x, int c) {
-  return c == 1 ? x : c == 3 ? x / 3 : c == 5 ? x / 5 : x / 7;
+  return c == 1 ? x : c == 3 ? x / 3 : c == 5 ? x / 5 : c == 7 ? x / 7 : x / c;
 }
 
 // One axis's line transform (host-built): length n = c 2^s, stages with
-// their radices (radix 4 and 2 first, then at most one of 3, 5, 7, so that
-// the sub-transform size Ns before any stage is a power of two).
+// their radices (radix 4 and 2 first, then 3, 5, 7).
 struct FftAxisDesc {
-  int n, c, s;                    // n = c 2^s
+  int n, c, s;                    // n = c 2^s, c odd
   int nst;                        // stages
   unsigned long long radix_code;  // radix of stage st in bits 4 st .. 4 st + 3
 };
@@ -145,19 +147,19 @@ __device__ __forceinline__ void dft_prime(Cx<T>* v, const Cx<T>* root, T s) {
 // butterfly j = g Ns + k of a line reads X[j + r m] (m = n / R), multiplies
 // element r by w^(r k) (w = exp(-2 pi i / (Ns R)), from the stage's table
 // ws[(r - 1) Ns + k]), applies the size-R DFT and writes Y[g Ns R + k + r Ns].
-// Ns = 2^sNs; m = cm 2^sm; the block's L = 2^sL lines.
+// Ns = cNs 2^sNs; m = cm 2^sm (cNs, cm odd); the block's L = 2^sL lines.
 template <typename T, int R>
-__device__ __forceinline__ void fft_stage(const Cx<T>* X, Cx<T>* Y, int sL, int n, int P, int sNs, int cm, int sm,
-                                          const Cx<T>* ws, const Cx<T>* root, T s) {
-  const int m = n / R, Ns = 1 << sNs;
+__device__ __forceinline__ void fft_stage(const Cx<T>* X, Cx<T>* Y, int sL, int n, int P, int sNs, int cNs, int cm,
+                                          int sm, const Cx<T>* ws, const Cx<T>* root, T s) {
+  const int m = n / R, Ns = cNs << sNs;
   for (int b = threadIdx.x; b < (m << sL); b += blockDim.x) {
     const int line = div_c(b >> sm, cm), j = b - line * m;
-    const int g = j >> sNs, k = j & (Ns - 1);
+    const int g = div_c(j >> sNs, cNs), k = j - g * Ns;
     const Cx<T>* x = X + line * P + j;
     Cx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = x[r * m];
-    if (sNs > 0) {
+    if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) v[r] = cmul(v[r], conj_if(ws[(r - 1) * Ns + k], s));
     }
@@ -179,18 +181,18 @@ template <typename T>
 __device__ __forceinline__ Cx<T>* fft_lines(Cx<T>* X, Cx<T>* Y, int sL, int P, int n, int c, int sn, int nst,
                                             unsigned long long radix_code, const Cx<T>* w, T s) {
   const Cx<T>* root = w + n - 1;
-  int sNs = 0;  // log2 of the sub-transform size Ns so far (a power of two before every stage)
+  int sNs = 0, cNs = 1;  // the sub-transform size so far, Ns = cNs 2^sNs
 #pragma unroll 1
   for (int st = 0; st < nst; ++st) {
     const int R = (int)((radix_code >> (4 * st)) & 15u);
-    const Cx<T>* ws = w + (1 << sNs) - 1;
-    // m = n / R = cm 2^sm: c 2^(sn-2), c 2^(sn-1), or 2^sn for the odd radix (R = c)
+    const Cx<T>* ws = w + (cNs << sNs) - 1;
+    // m = n / R = cm 2^sm: c 2^(sn-2), c 2^(sn-1), or (c / R) 2^sn for an odd radix
     switch (R) {
-      case 4: fft_stage<T, 4>(X, Y, sL, n, P, sNs, c, sn - 2, ws, root, s); sNs += 2; break;
-      case 2: fft_stage<T, 2>(X, Y, sL, n, P, sNs, c, sn - 1, ws, root, s); sNs += 1; break;
-      case 3: fft_stage<T, 3>(X, Y, sL, n, P, sNs, 1, sn, ws, root, s); break;
-      case 5: fft_stage<T, 5>(X, Y, sL, n, P, sNs, 1, sn, ws, root, s); break;
-      default: fft_stage<T, 7>(X, Y, sL, n, P, sNs, 1, sn, ws, root, s); break;
+      case 4: fft_stage<T, 4>(X, Y, sL, n, P, sNs, cNs, c, sn - 2, ws, root, s); sNs += 2; break;
+      case 2: fft_stage<T, 2>(X, Y, sL, n, P, sNs, cNs, c, sn - 1, ws, root, s); sNs += 1; break;
+      case 3: fft_stage<T, 3>(X, Y, sL, n, P, sNs, cNs, c / 3, sn, ws, root, s); cNs *= 3; break;
+      case 5: fft_stage<T, 5>(X, Y, sL, n, P, sNs, cNs, c / 5, sn, ws, root, s); cNs *= 5; break;
+      default: fft_stage<T, 7>(X, Y, sL, n, P, sNs, cNs, c / 7, sn, ws, root, s); cNs *= 7; break;
     }
     __syncthreads();
     Cx<T>* t = X;
@@ -258,42 +260,64 @@ __device__ __forceinline__ void fft_pass_body(const FftPassArgs<T>* __restrict__
     }
   }
   // load (consecutive threads on consecutive global addresses): axis 0 takes
-  // t = l n + e, the others t = e L + l
-  for (int t = threadIdx.x; t < (n << sL); t += blockDim.x) {
-    int l, e;
-    if (ax == 0) {
-      l = div_c(t >> sn, c);
-      e = t - l * n;
-    } else {
-      e = t >> sL;
-      l = t & (L - 1);
+  // t = l n + e, the others t = e L + l; kFftBatch loads per thread are issued
+  // before their shared-memory stores, so that they are in flight together
+  const int total = n << sL;
+  for (int t0 = threadIdx.x; t0 < total; t0 += kFftBatch * blockDim.x) {
+    Cx<T> v[kFftBatch];
+    int at[kFftBatch];
+#pragma unroll
+    for (int u = 0; u < kFftBatch; ++u) {
+      const int t = t0 + u * (int)blockDim.x;
+      v[u] = Cx<T>{T(0), T(0)};
+      at[u] = -1;
+      if (t < total) {
+        int l, e;
+        if (ax == 0) {
+          l = div_c(t >> sn, c);
+          e = t - l * n;
+        } else {
+          e = t >> sL;
+          l = t & (L - 1);
+        }
+        at[u] = l * P + e;
+        if (l < nl) {
+          const long long o = base + l * ls + e * es;
+          if (MODE == 0) v[u].x = (T)Ap->qin[o];
+          else v[u] = buf[o];
+        }
+      }
     }
-    Cx<T> v = Cx<T>{T(0), T(0)};
-    if (l < nl) {
-      const long long o = base + l * ls + e * es;
-      if (MODE == 0) v.x = (T)Ap->qin[o];
-      else v = buf[o];
-    }
-    X[l * P + e] = v;
+#pragma unroll
+    for (int u = 0; u < kFftBatch; ++u)
+      if (at[u] >= 0) X[at[u]] = v[u];
   }
   __syncthreads();
   const T s = (MODE == 3 || MODE == 4) ? T(1) : T(-1);
   Cx<T>* R = fft_lines(X, Y, sL, P, n, c, sn, nst, radix_code, w, s);
   if (MODE == 2) {  // product by K^ at this line's points, then the inverse along z
     const T* khat = Ap->khat;
-    for (int t = threadIdx.x; t < (n << sL); t += blockDim.x) {
-      const int e = t >> sL, l = t & (L - 1);
-      if (l < nl) {
-        const T kh = khat[base + l * ls + e * es];
-        R[l * P + e].x *= kh;
-        R[l * P + e].y *= kh;
+    for (int t0 = threadIdx.x; t0 < total; t0 += kFftBatch * blockDim.x) {
+      T kh[kFftBatch];
+#pragma unroll
+      for (int u = 0; u < kFftBatch; ++u) {
+        const int t = t0 + u * (int)blockDim.x, e = t >> sL, l = t & (L - 1);
+        kh[u] = (t < total && l < nl) ? khat[base + l * ls + e * es] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kFftBatch; ++u) {
+        const int t = t0 + u * (int)blockDim.x, e = t >> sL, l = t & (L - 1);
+        if (t < total && l < nl) {
+          R[l * P + e].x *= kh[u];
+          R[l * P + e].y *= kh[u];
+        }
       }
     }
     __syncthreads();
     R = fft_lines(R, R == X ? Y : X, sL, P, n, c, sn, nst, radix_code, w, T(1));
   }
   T* uout = Ap->uout;
-  for (int t = threadIdx.x; t < (n << sL); t += blockDim.x) {
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
     int l, e;
     if (ax == 0) {
       l = div_c(t >> sn, c);
@@ -319,9 +343,10 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass(const FftPassArgs<T>* 
   fft_pass_body<T, MODE>(tab + r, (int)blockIdx.x - __ldg(first + r));
 }
 
-// n = c 2^s with c in {1, 3, 5, 7}: stages radix 4 (while 4 divides the
-// power of two), one radix 2 if one factor 2 is left, then c if c > 1.
-// Returns false for any other n.
+// n = c 2^s with c a product of 3, 5 and 7: stages radix 4 (while 4
+// divides the power of two), one radix 2 if one factor 2 is left, then the
+// factors of c (3s, 5s, 7s).  Returns false for any other n or more than 16
+// stages.
 bool factorize(int n, FftAxisDesc& D) {
   D = FftAxisDesc{n, 1, 0, 0, 0ull};
   if (n < 1) return false;
@@ -330,14 +355,20 @@ bool factorize(int n, FftAxisDesc& D) {
     p >>= 1;
     D.s++;
   }
-  if (p != 1 && p != 3 && p != 5 && p != 7) return false;
   D.c = p;
   int s = D.s;
-  auto push = [&](int r) { D.radix_code |= (unsigned long long)r << (4 * D.nst++); };
+  auto push = [&](int r) {
+    if (D.nst < 16) D.radix_code |= (unsigned long long)r << (4 * D.nst);
+    D.nst++;
+  };
   for (; s >= 2; s -= 2) push(4);
   if (s == 1) push(2);
-  if (p > 1) push(p);
-  return D.nst <= 12;
+  for (int r : {3, 5, 7})
+    while (p % r == 0) {
+      push(r);
+      p /= r;
+    }
+  return p == 1 && D.nst <= 16;
 }
 
 // Lines per block: the largest power of two up to 16 whose two line buffers

@@ -296,7 +296,7 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   P->pair_targets = TU.pair_targets > 0 ? TU.pair_targets : 32;
   P->lattice_txn = TU.lattice_txn;
   P->batch_persistent = TU.batch_persistent;
-  const int lattice_method = TU.lattice_method > 0 ? TU.lattice_method : 1;
+  const int lattice_method = TU.lattice_method > 0 ? TU.lattice_method : 2;
   P->lattice_tyn = TU.lattice_tyn;
   P->wolf_alpha = 2.4 / p.cutoff;  // alpha R = 2.4 (0.2 per length unit at R = 12) until msm_set_wolf_alpha
   for (int d = 0; d < 3; ++d)

@@ -25,14 +25,16 @@ def test_autotune_search_result_and_cache(tmp_path, monkeypatch):
     space = dict(AT.SEARCH)
     for k, v in times["choice"].items():
         assert tuple(v) in space[k] if k == "lattice_tile" else v in space[k]
-    assert "default" in times and len(times) > 8
-    assert any(k.startswith("lattice_tile=") for k in times)    # tiles were searched
-    assert any(k.startswith("pair_targets=8") for k in times)   # and the pair clusters
+    assert "default" in times and len(times) > 6
+    assert any("lattice_method=1" in k for k in times)          # the stencil against the FFT default
+    # the stencil's tiles are searched exactly when the stencil won
+    assert any("lattice_tile=" in k for k in times) == AT.uses_stencil(times["choice"])
+    assert any("pair_targets=8" in k for k in times)            # and the pair clusters
     t2, times2 = AT.autotune(pos, q, reps=3, **kw)
     assert t2 == tuning and "cached" in times2
     base = MSM(max_atoms=len(q_h), **kw)
-    for t in [tuning, {"cell_fill": 40, "patch_cells": 2, "lattice_waves": 8},
-              {"pair_targets": 8, "lattice_txn": 2, "lattice_tyn": 16}]:
+    for t in [tuning, {"cell_fill": 40, "patch_cells": 2, "lattice_waves": 8, "lattice_method": 1},
+              {"pair_targets": 8, "lattice_txn": 2, "lattice_tyn": 16, "lattice_method": 1}]:
         tuned = MSM(max_atoms=len(q_h), tuning=t, **kw)
         E0, phi0, F0 = base.eval(pos, q)
         E1, phi1, F1 = tuned.eval(pos, q)
@@ -81,14 +83,16 @@ def test_autotune_batch_search_and_cache(tmp_path, monkeypatch):
     for g, tile in summary["lattice_tile_by_grid0"].items():
         assert int(g) in summary["grid0_sizes"] and tuple(tile) in AT.TILES_BATCH
     assert len(tunings) == len(counts)
-    assert "default" in times and any(k.startswith("grid0=") for k in times)   # per-grid tiles were timed
+    assert "default" in times and any("lattice_method=1" in k for k in times)
+    # per-grid tiles are timed exactly when the stencil won
+    assert any(k.startswith("grid0=") for k in times) == AT.uses_stencil(summary["shared"])
     t2, s2, times2 = AT.autotune_batch(boxes, pos, q, counts, reps=2, **kw)
     assert t2 == tunings and s2 == summary and "cached" in times2
     mk = lambda ts: [MSM(box=L, periodic=True, precision="mixed", max_atoms=c, tuning=t, **kw)
                      for L, c, t in zip(boxes, counts, ts)]
     E0, _, F0 = MSMBatch(mk([None] * len(counts))).eval(pos, q, counts)
     # the tuned tunings, and every replica on a non-default tile and the pair clusters
-    for ts in [tunings, [{"lattice_txn": 2, "lattice_tyn": 8, "pair_targets": 8}] * len(counts)]:
+    for ts in [tunings, [{"lattice_txn": 2, "lattice_tyn": 8, "pair_targets": 8, "lattice_method": 1}] * len(counts)]:
         E1, _, F1 = MSMBatch(mk(ts)).eval(pos, q, counts)
         torch.cuda.synchronize()
         assert torch.allclose(E0, E1, rtol=1e-6, atol=0)
@@ -96,7 +100,7 @@ def test_autotune_batch_search_and_cache(tmp_path, monkeypatch):
     # the batch graph (one launch per stage) with those shapes
     E = torch.zeros(len(counts), dtype=torch.float64, device=dev)
     F = torch.zeros((len(q), 3), dtype=torch.float64, device=dev)
-    g = MSMBatch(mk([{"lattice_txn": 2, "lattice_tyn": 8, "pair_targets": 8}] * len(counts))).graph(
+    g = MSMBatch(mk([{"lattice_txn": 2, "lattice_tyn": 8, "pair_targets": 8, "lattice_method": 1}] * len(counts))).graph(
         pos, q, counts, E, None, F)
     g.launch()
     torch.cuda.synchronize()

@@ -31,17 +31,18 @@ def dev():
     return torch.device("cuda:0")
 
 
-def make_plans(reps, precision):
+def make_plans(reps, precision, method=0):
     from paper_1402_7216_gb300 import MSM
     return [MSM(box=L, periodic=True, cutoff=6.0, spacing=1.5, order=3, splitting=2, precision=precision,
-                max_atoms=len(q)) for (L, _, q) in reps]
+                max_atoms=len(q), tuning={"lattice_method": method}) for (L, _, q) in reps]
 
 
+@pytest.mark.parametrize("method", [1, 2], ids=["stencil", "fft"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_equals_single_evaluations(precision, dev):
+def test_batch_equals_single_evaluations(precision, method, dev):
     from paper_1402_7216_gb300 import MSMBatch
     reps = replicas()
-    plans = make_plans(reps, precision)
+    plans = make_plans(reps, precision, method)
     assert len({p.dims[0] for p in plans}) > 1          # uneven grids
     counts = [len(q) for (_, _, q) in reps]
     pos = torch.tensor(np.vstack([p for (_, p, _) in reps]), device=dev)
@@ -53,7 +54,7 @@ def test_batch_equals_single_evaluations(precision, dev):
     torch.cuda.synchronize()
     tol = 1e-12 if precision == "fp64" else 1e-6
     o = 0
-    singles = make_plans(reps, precision)
+    singles = make_plans(reps, precision, method)
     for r, (L, p, qq) in enumerate(reps):
         n = len(qq)
         Es, phis, Fs = singles[r].eval(torch.tensor(p, device=dev), torch.tensor(qq, device=dev))
@@ -72,10 +73,11 @@ def test_batch_equals_single_evaluations(precision, dev):
     assert_atoms(F[s:s + counts[2]].cpu().numpy(), ref["F"], (1e-9 if precision == "fp64" else 1e-5))
 
 
-def test_batch_graph_replays(dev):
+@pytest.mark.parametrize("method", [1, 2], ids=["stencil", "fft"])
+def test_batch_graph_replays(method, dev):
     from paper_1402_7216_gb300 import MSMBatch
     reps = replicas(seed=41)
-    plans = make_plans(reps, "mixed")
+    plans = make_plans(reps, "mixed", method)
     counts = [len(q) for (_, _, q) in reps]
     n = sum(counts)
     pos = torch.tensor(np.vstack([p for (_, p, _) in reps]), device=dev)
@@ -91,7 +93,7 @@ def test_batch_graph_replays(dev):
     g = batch.graph(pos, q, counts, E, phi, F, gE, gp, gq)
     torch.cuda.synchronize()
     assert E.abs().sum().item() == 0.0                  # capturing runs nothing
-    direct = MSMBatch(make_plans(reps, "mixed"))
+    direct = MSMBatch(make_plans(reps, "mixed", method))
     E2, phi2, F2 = direct.eval(pos, q, counts)
     gscale = torch.cat([gE[r].expand(c) for r, c in enumerate(counts)])
     for _ in range(2):
@@ -184,8 +186,9 @@ def test_replicas64_full_size_graph(dev):
     reps = replica_boxes(64)
     counts = [len(q) for (_, _, q) in reps]
     n = sum(counts)
+    # the stencil lattice here; the FFT form of the same graph is in test_gpu_fft.py
     plans = [MSM(box=L, periodic=True, cutoff=10.0, spacing=2.0, order=3, splitting=2, precision="mixed",
-                 max_atoms=len(q)) for (L, _, q) in reps]
+                 max_atoms=len(q), tuning={"lattice_method": 1}) for (L, _, q) in reps]
     pos = torch.tensor(np.vstack([p for (_, p, _) in reps]), device=dev)
     q = torch.tensor(np.concatenate([qq for (_, _, qq) in reps]), device=dev)
     E = torch.zeros(64, dtype=torch.float64, device=dev)

@@ -7,7 +7,8 @@ path must give the oracle's grids and per-atom results within the same
 tolerances as the stencil path (FP64: grids 1e-11 of their largest value;
 mixed: the stencil path's FP32 tolerances), and agree with the stencil path
 of the same plan.  Grid sizes cover radices 2, 4 (16, 32, 96, 256), 3 (24,
-12, 6), 7 (14, 7) and a rectangular box.
+12, 6), 7 (14, 7), two odd stages (30 = 2 x 3 x 5, 18 = 2 x 3 x 3) and a
+rectangular box.
 """
 import numpy as np
 import pytest
@@ -31,6 +32,9 @@ PERIODIC = [
     dict(name="quintic-C3-l3", box=24.0, periodic=True, cutoff=6.0, spacing=1.5, order=5, split=3, levels=3),
     dict(name="rect-16x14x24", box=(24.0, 21.0, 36.0), periodic=True, cutoff=7.0, spacing=1.5, order=5,
          split=2),
+    # explicit level counts leave odd factors 15 = 3 x 5 and 9 = 3 x 3 in the grid sizes
+    dict(name="quintic-30-radix15-l2", box=45.0, periodic=True, cutoff=9.0, spacing=1.5, order=5, split=2, levels=2),
+    dict(name="cubic-18-radix9-l2", box=27.0, periodic=True, cutoff=7.0, spacing=1.5, order=3, split=2, levels=2),
 ]
 
 

@@ -1,6 +1,7 @@
 """The largest workload (4.1M atoms, 340 A periodic water box with 0.15 M
 NaCl, a = 10, h = 1.5 -> 240^3 finest grid, quintic, 5 levels) at full size,
-forward and adjoint: properties that hold at any size, and the mixed path
+forward and adjoint, with the stencil and with the FFT lattice (240 = 15 x
+16: radices 4, 4, 3, 5): properties that hold at any size, and the mixed path
 against the FP64 path (which the smaller systems pin to the oracle).  Oracle
 checks at this size would need the FP64 lattice sum on 13.8M points (~1.6e11
 taps) on the host, so they run on the 1.07M-atom system instead.
@@ -21,7 +22,8 @@ from synth import WORKLOADS
 pytestmark = pytest.mark.gpu
 
 
-def test_water4m_forward_adjoint_mixed_vs_fp64_and_invariants():
+@pytest.mark.parametrize("method", [1, 2], ids=["stencil", "fft"])
+def test_water4m_forward_adjoint_mixed_vs_fp64_and_invariants(method):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1402_7216_gb300 import MSM
@@ -37,8 +39,9 @@ def test_water4m_forward_adjoint_mixed_vs_fp64_and_invariants():
     held = {}
     for precision in ["mixed", "fp64"]:
         plan = MSM(box=w.box, periodic=True, cutoff=w.cutoff, spacing=w.spacing, levels=w.levels, order=w.order,
-                   splitting=w.split, precision=precision, max_atoms=len(q_h))
+                   splitting=w.split, precision=precision, max_atoms=len(q_h), tuning={"lattice_method": method})
         assert plan.dims[0] == (240, 240, 240) and plan.levels == 5
+        assert plan.lattice_method == {1: "stencil", 2: "fft"}[method]
         E, phi, F = plan.eval(pos, q)
         gp, gq = plan.backward(gE)
         torch.cuda.synchronize()

@@ -75,22 +75,28 @@ SMALL = [
 ]
 
 
+@pytest.mark.parametrize("method", [1, 2], ids=["stencil", "fft"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("cfg", SMALL, ids=[c["name"] for c in SMALL])
-def test_small_systems_match_oracle(cfg, precision, dev):
+def test_small_systems_match_oracle(cfg, precision, method, dev):
+    """Both forms of the lattice cutoff (the FFT applies to the periodic cases)."""
     pos, q = make_water_box(cfg["box"], 420, 3, 2, seed=21, periodic=cfg["periodic"])
     ref = O.msm(oparams(cfg), pos, q)
-    plan = plan_for(cfg, precision, len(q))
+    plan = plan_for(cfg, precision, len(q), tuning={"lattice_method": method})
+    # one level has no lattice cutoff at all (only the top level)
+    fft = method == 2 and cfg["periodic"] and cfg.get("levels", 0) != 1
+    assert plan.lattice_method == ("fft" if fft else "stencil")
     assert plan.levels == ref["geometry"].levels
     assert_close(gpu_eval(plan, pos, q, dev), ref, precision, cfg["name"])
 
 
-@pytest.mark.parametrize("periodic", [True, False])
-def test_staged_grids_match_oracle_fp64(periodic, dev):
+@pytest.mark.parametrize("periodic,method", [(True, 1), (True, 2), (False, 1)],
+                         ids=["periodic-stencil", "periodic-fft", "open"])
+def test_staged_grids_match_oracle_fp64(periodic, method, dev):
     cfg = dict(box=24.0, periodic=periodic, cutoff=6.0, spacing=1.5, order=5, split=2, levels=3)
     pos, q = make_water_box(24.0, 300, 1, 1, seed=22, periodic=periodic)
     ref = O.msm(oparams(cfg), pos, q, keep_grids=True)
-    plan = plan_for(cfg, "fp64", len(q))
+    plan = plan_for(cfg, "fp64", len(q), tuning={"lattice_method": method})
     gpu_eval(plan, pos, q, dev)
     G = ref["geometry"]
     for k in range(G.levels):
