@@ -169,8 +169,26 @@ __device__ __forceinline__ void fft_stage(const Cx<T>* X, Cx<T>* Y, int sL, int 
     else if (R == 5) dft5(v, s);
     else dft_prime<T, R>(v, root, s);
     Cx<T>* y = Y + line * P + g * Ns * R + k;
+    bool done = false;
+    if constexpr (R == 4) {
+      if (Ns <= 4) {
+        // a warp's writes y[r Ns] for one r fall on 4 of the 16 8-byte bank
+        // pairs when Ns is 1 or 4; writing output (r' + j / 4) mod 4 at step
+        // r' spreads them over all 16 (two lanes each, the least for 8-byte
+        // words)
+        const int rot = (j >> 2) & 3;
 #pragma unroll
-    for (int r = 0; r < R; ++r) y[r * Ns] = v[r];
+        for (int rr = 0; rr < 4; ++rr) {
+          const int r = (rr + rot) & 3;
+          y[r * Ns] = r == 0 ? v[0] : r == 1 ? v[1] : r == 2 ? v[2] : v[3];
+        }
+        done = true;
+      }
+    }
+    if (!done) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) y[r * Ns] = v[r];
+    }
   }
 }
 
@@ -337,7 +355,7 @@ __device__ __forceinline__ void fft_pass_body(const FftPassArgs<T>* __restrict__
 // One pass over a table of levels (one plan's, or every replica's): block b
 // belongs to the item whose range of blocks holds it.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kFftThreads) k_fft_pass(const FftPassArgs<T>* __restrict__ tab,
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 4 : 2) k_fft_pass(const FftPassArgs<T>* __restrict__ tab,
                                                           const int* __restrict__ first, int nitems) {
   const int r = batch_rep(first, nitems, blockIdx.x);
   fft_pass_body<T, MODE>(tab + r, (int)blockIdx.x - __ldg(first + r));
