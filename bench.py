@@ -674,6 +674,32 @@ def fma_probe(dev, iters=1 << 16, blocks=152 * 8):
     return res
 
 
+def run_profile_case(args):
+    """One section of the bench alone on cuda:0 (for ncu captures)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    if args.profile_case == "batch":
+        out = bench_batch(dev, args)
+    elif args.profile_case == "large":
+        out = bench_large(dev, args)
+    else:
+        from paper_1402_7216_gb300 import MSM
+        w = WORKLOADS[args.workload]
+        pos_h, q_h = w.make()
+        pos, q = torch.tensor(pos_h, device=dev), torch.tensor(q_h, device=dev)
+        plan = MSM(box=w.box, periodic=w.periodic, cutoff=w.cutoff, spacing=w.spacing, levels=w.levels,
+                   order=w.order, splitting=w.split, precision="mixed", max_atoms=len(q_h))
+        plan.set_overlap(False)
+        for _ in range(args.warmup + args.steps):
+            plan.eval(pos, q, want_phi=False, want_force=False)
+        torch.cuda.synchronize()
+        plan.check_status()
+        out = {"workload": args.workload, "evaluations": args.warmup + args.steps, "lattice": plan.lattice_method,
+               "levels": plan.levels, "dims": plan.dims}
+    print(json.dumps({"profile_case": args.profile_case, "result": out}, default=str))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -687,9 +713,15 @@ def main():
     ap.add_argument("--no-parareal", action="store_true", help="skip the coarse-propagator timings")
     ap.add_argument("--no-md", action="store_true", help="skip the velocity Verlet timing")
     ap.add_argument("--no-large", action="store_true", help="skip the 4.1M-atom forward + adjoint timing")
+    ap.add_argument("--profile-case", choices=["evals", "batch", "large"],
+                    help="run one section alone and print its JSON (the commands the ncu summaries in profiles/ "
+                         "use): 'evals' builds the benchmark system's default plan and runs --warmup then --steps "
+                         "plain evaluations; 'batch' the 64-replica batch; 'large' the 4.1M-atom box")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case(args)
 
     import numpy as np
     import torch
