@@ -134,9 +134,11 @@ typedef struct {
 /* Builds a plan: validates params, fixes the grid geometry, builds the
  * level stencil and the top-level kernel (FP64, host) and allocates device
  * workspace for max_atoms atoms on the current device.  Synchronous.
- * UNSUPPORTED also covers a level stencil too wide for the lattice kernel's
- * shared-memory window: 2a/h up to about 65 grid spacings (MSM_MIXED) or 27
- * (MSM_FP64), far beyond the usual 4 to 10.
+ * UNSUPPORTED also covers a level stencil too wide for the stencil lattice
+ * kernel's shared-memory window, 2a/h beyond about 65 grid spacings
+ * (MSM_MIXED) or 27 (MSM_FP64) (the usual range is 4 to 10), on a plan that
+ * would run that kernel: open plans, lattice_method = 1, or periodic sizes
+ * the FFT does not take.  A periodic plan in FFT form has no such limit.
  * Errors: INVALID_ARG, UNSUPPORTED, CUTOFF_GT_HALF_BOX, OOM, CUDA. */
 int msm_create(const msm_params* params, msm_handle* out);
 

@@ -352,13 +352,18 @@ struct msm_graph {
 namespace {
 
 // The batched form needs one kernel family for every replica: mixed
-// precision, one interpolation order, one splitting.
+// precision, one interpolation order, one splitting; and its lattice runs by
+// FFT when every plan took that form, else by the stencil, which every plan's
+// stencil must then fit.
 bool batchable(const msm_handle* plans, int nrep) {
+  bool all_fft = true, all_fit = true;
   for (int r = 0; r < nrep; ++r) {
     const Plan& P = plans[r]->p;
     if (P.fp64 || P.P.order != plans[0]->p.P.order || P.P.splitting != plans[0]->p.P.splitting) return false;
+    all_fft = all_fft && P.lattice_fft;
+    all_fit = all_fit && P.stencil_fits;
   }
-  return true;
+  return all_fft || all_fit;
 }
 
 // Builds the argument tables of the batched stages (synchronous; allocates).

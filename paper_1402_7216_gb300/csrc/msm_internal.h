@@ -136,6 +136,7 @@ struct Plan {
   int batch_persistent = 0;
   // lattice cutoff of periodic levels as an FFT convolution (fft.cu)
   bool lattice_fft = false;
+  bool stencil_fits = true;  // the stencil kernel's shared-memory window holds this plan's stencil
   FftLevel fftl[kMaxLevels];
   FftBatch* fftb[2] = {nullptr, nullptr};  // every lattice level: the forward sweep's grids, the adjoint's
   // smoothing constants

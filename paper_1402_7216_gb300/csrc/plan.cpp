@@ -416,8 +416,18 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
     P->E[d] = (int)std::ceil(R / P->h[d]);
     while (P->E[d] > 0 && P->E[d] * P->h[d] >= R) --P->E[d];
   }
-  if (!lattice_fits(*P)) return MSM_ERR_UNSUPPORTED;  // cutoff too many grid spacings wide
-  if (P->lattice_txn > 0 && !lattice_tile_fits(*P, P->lattice_txn, P->lattice_tyn)) return MSM_ERR_INVALID_ARG;
+  // FFT form of the lattice cutoff (periodic levels whose sizes factor into
+  // radices 2, 3, 5, 7; built after the workspace below).  It has no window
+  // to fit, so a stencil too many grid spacings wide for the stencil kernel's
+  // shared memory is refused only where the stencil would run.
+  bool want_fft = p.periodic && lattice_method == 2 && P->levels > 1;
+  for (int k = 0; k + 1 < P->levels && want_fft; ++k)
+    for (int d = 0; d < 3; ++d)
+      if (!fft_size_ok(P->n[k][d])) want_fft = false;
+  P->stencil_fits = lattice_fits(*P);
+  if (!P->stencil_fits && !want_fft) return MSM_ERR_UNSUPPORTED;  // cutoff too many grid spacings wide
+  if (P->lattice_txn > 0 && P->stencil_fits && !lattice_tile_fits(*P, P->lattice_txn, P->lattice_tyn))
+    return MSM_ERR_INVALID_ARG;
   std::vector<double> G((size_t)(2 * P->E[0] + 1) * (2 * P->E[1] + 1) * (2 * P->E[2] + 1), 0.0);
   double taps = 0;
   for (int dz = -P->E[2]; dz <= P->E[2]; ++dz)
@@ -430,12 +440,6 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
         if (g != 0.0) taps += 1;
       }
   P->stencil_taps = taps;
-  // FFT form of the lattice cutoff (periodic levels whose sizes factor into
-  // radices 2, 3, 5, 7; built after the workspace below)
-  bool want_fft = p.periodic && lattice_method == 2 && P->levels > 1;
-  for (int k = 0; k + 1 < P->levels && want_fft; ++k)
-    for (int d = 0; d < 3; ++d)
-      if (!fft_size_ok(P->n[k][d])) want_fft = false;
 
   // top-level kernel table (FP64)
   int top = P->levels - 1;
@@ -528,7 +532,7 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
     tsize = std::max(tsize, t);
   }
   for (int i = 0; i < 2; ++i) M(&D.tmp[i], sizeof(double) * tsize);
-  M(&D.lparts, T * (size_t)lattice_parts_elems(*P));
+  M(&D.lparts, T * (size_t)(P->stencil_fits ? lattice_parts_elems(*P) : 0));
   size_t ntop = (size_t)grid_points(*P, top);
   M((void**)&D.topq, sizeof(double) * ntop);
   M((void**)&D.topu, sizeof(double) * ntop);
@@ -590,19 +594,21 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
       sh.push_back({(float)(o.x * P->cw[0]), (float)(o.y * P->cw[1]), (float)(o.z * P->cw[2]), 0.f});
     if (upload(&D.cell_shift, sh) != cudaSuccess) return MSM_ERR_OOM;
   }
-  std::vector<int> start;
-  if (P->fp64) {
-    std::vector<Segment<double>> segs;
-    build_segments<double>(*P, G, P->E, segs, start);
-    P->nseg = (int)segs.size();
-    if (upload(&D.seg, segs) != cudaSuccess) return MSM_ERR_OOM;
-  } else {
-    std::vector<Segment2> segs2;
-    build_row_pairs(G, P->E, segs2, start);
-    P->nseg = (int)segs2.size();
-    if (upload(&D.seg2, segs2) != cudaSuccess) return MSM_ERR_OOM;
+  if (P->stencil_fits) {  // the stencil kernel's segment tables (unused, and not built, past its window)
+    std::vector<int> start;
+    if (P->fp64) {
+      std::vector<Segment<double>> segs;
+      build_segments<double>(*P, G, P->E, segs, start);
+      P->nseg = (int)segs.size();
+      if (upload(&D.seg, segs) != cudaSuccess) return MSM_ERR_OOM;
+    } else {
+      std::vector<Segment2> segs2;
+      build_row_pairs(G, P->E, segs2, start);
+      P->nseg = (int)segs2.size();
+      if (upload(&D.seg2, segs2) != cudaSuccess) return MSM_ERR_OOM;
+    }
+    if (upload((void**)&D.seg_start, start) != cudaSuccess) return MSM_ERR_OOM;
   }
-  if (upload((void**)&D.seg_start, start) != cudaSuccess) return MSM_ERR_OOM;
   int least = 0, greatest = 0;
   if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
       cudaStreamCreateWithPriority(&P->side, cudaStreamNonBlocking, greatest) != cudaSuccess ||

@@ -240,3 +240,20 @@ def test_fft_replicas64_full_size_graph(dev):
         assert_atoms(Fg[off[r]:off[r + 1]][pick], ref["F"], 1e-5, r)
         assert_atoms(phig[off[r]:off[r + 1]][pick], ref["phi"], 1e-5, r)
     g.close()
+
+
+def test_fft_takes_stencils_beyond_the_stencil_window(dev):
+    """FP64 with 2a/h = 31 (a stencil 30 grid spacings in radius) is past the
+    FP64 stencil kernel's shared-memory window (about 27): the periodic plan
+    evaluates it by FFT and matches the oracle; the stencil form and the open
+    box, which would need that kernel, stay UNSUPPORTED."""
+    from paper_1402_7216_gb300 import MSMError
+    cfg = dict(box=15.5, periodic=True, cutoff=6.0, spacing=0.4, order=3, split=2)
+    pos, q = water(cfg, 46, 0.03)
+    for bad in (dict(cfg, periodic=False), cfg):
+        with pytest.raises(MSMError) as e:
+            rect_plan(bad, "fp64", len(q), STENCIL)
+        assert e.value.code == -2
+    plan = rect_plan(cfg, "fp64", len(q), FFT)
+    assert plan.lattice_method == "fft" and plan.dims[0] == (40, 40, 40)
+    assert_close(gpu_eval(plan, pos, q, dev), O.msm(oparams(cfg), pos, q), "fp64", "wide stencil")
