@@ -81,7 +81,7 @@ __device__ __forceinline__ int div_c(int x, int c) {
 struct FftAxisDesc {
   int n, c, s;                    // n = c 2^s, c odd
   int nst;                        // stages
-  unsigned long long radix_code;  // radix of stage st in bits 4 st .. 4 st + 3
+  unsigned long long radix_code;  // radix of stage st in bits 5 st .. 5 st + 4
 };
 
 // Small DFTs in place on v[0..R-1]; s = -1 forward, +1 inverse.
@@ -127,6 +127,42 @@ __device__ __forceinline__ void dft5(Cx<T>* v, T s) {
   v[2] = cadd(m2, d2);
   v[3] = csub(m2, d2);
 }
+// 16 points as 4 x 4: for each r2 a size-4 DFT over r1 of v[4 r1 + r2],
+// times W16^(r2 k1), then for each k1 a size-4 DFT over r2; output k1 + 4 k2.
+// W16^q = exp(-2 pi i q / 16) for the q = r2 k1 that occur (conjugated for
+// the inverse).
+template <typename T>
+__device__ __forceinline__ void dft16(Cx<T>* v, T s) {
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;  // cos, sin (pi / 8)
+  const T h = (T)0.70710678118654752440;                                   // cos (pi / 4)
+  Cx<T> t[16];
+#pragma unroll
+  for (int r2 = 0; r2 < 4; ++r2) {
+    Cx<T> a[4] = {v[r2], v[4 + r2], v[8 + r2], v[12 + r2]};
+    dft4(a, s);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) t[4 * r2 + k1] = a[k1];
+  }
+  // W16^(r2 k1): (1), (r2 = 1) q = 1, 2, 3; (r2 = 2) q = 2, 4, 6; (r2 = 3) q = 3, 6, 9
+  const Cx<T> w1 = Cx<T>{c1, s * s1}, w2 = Cx<T>{h, s * h}, w3 = Cx<T>{s1, s * c1};
+  const Cx<T> w6 = Cx<T>{-h, s * h}, w9 = Cx<T>{-c1, -s * s1};
+  t[5] = cmul(t[5], w1);
+  t[6] = cmul(t[6], w2);
+  t[7] = cmul(t[7], w3);
+  t[9] = cmul(t[9], w2);
+  t[10] = cmuli(t[10], s);  // W16^4 = s i
+  t[11] = cmul(t[11], w6);
+  t[13] = cmul(t[13], w3);
+  t[14] = cmul(t[14], w6);
+  t[15] = cmul(t[15], w9);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    Cx<T> a[4] = {t[k1], t[4 + k1], t[8 + k1], t[12 + k1]};
+    dft4(a, s);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = a[k2];
+  }
+}
 // a prime radix R by the definition: V_k = sum_r v_r z^(r k mod R), z the
 // R-th roots of unity in root[0..R-1] (conjugated for the inverse)
 template <typename T, int R>
@@ -143,6 +179,12 @@ __device__ __forceinline__ void dft_prime(Cx<T>* v, const Cx<T>* root, T s) {
   for (int k = 0; k < R; ++k) v[k] = o[k];
 }
 
+// Element e of a line sits at e + e / 16 (one spare slot after every 16
+// complex values, 128 bytes): a warp's strided Stockham writes, 16 j + r for a
+// radix-16 stage or 4 j + r for a radix-4 one, then fall on distinct bank
+// pairs instead of one or four.
+__host__ __device__ __forceinline__ int pad(int e) { return e + (e >> 4); }
+
 // One Stockham stage of radix R over the L lines of X into Y (line pitch P):
 // butterfly j = g Ns + k of a line reads X[j + r m] (m = n / R), multiplies
 // element r by w^(r k) (w = exp(-2 pi i / (Ns R)), from the stage's table
@@ -155,40 +197,24 @@ __device__ __forceinline__ void fft_stage(const Cx<T>* X, Cx<T>* Y, int sL, int 
   for (int b = threadIdx.x; b < (m << sL); b += blockDim.x) {
     const int line = div_c(b >> sm, cm), j = b - line * m;
     const int g = div_c(j >> sNs, cNs), k = j - g * Ns;
-    const Cx<T>* x = X + line * P + j;
+    const Cx<T>* x = X + line * P;
     Cx<T> v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = x[r * m];
+    for (int r = 0; r < R; ++r) v[r] = x[pad(j + r * m)];
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) v[r] = cmul(v[r], conj_if(ws[(r - 1) * Ns + k], s));
     }
-    if (R == 4) dft4(v, s);
+    if (R == 16) dft16(v, s);
+    else if (R == 4) dft4(v, s);
     else if (R == 2) dft2(v);
     else if (R == 3) dft3(v, s);
     else if (R == 5) dft5(v, s);
     else dft_prime<T, R>(v, root, s);
-    Cx<T>* y = Y + line * P + g * Ns * R + k;
-    bool done = false;
-    if constexpr (R == 4) {
-      if (Ns <= 4) {
-        // a warp's writes y[r Ns] for one r fall on 4 of the 16 8-byte bank
-        // pairs when Ns is 1 or 4; writing output (r' + j / 4) mod 4 at step
-        // r' spreads them over all 16 (two lanes each, the least for 8-byte
-        // words)
-        const int rot = (j >> 2) & 3;
+    Cx<T>* y = Y + line * P;
+    const int o = g * Ns * R + k;
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-          const int r = (rr + rot) & 3;
-          y[r * Ns] = r == 0 ? v[0] : r == 1 ? v[1] : r == 2 ? v[2] : v[3];
-        }
-        done = true;
-      }
-    }
-    if (!done) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) y[r * Ns] = v[r];
-    }
+    for (int r = 0; r < R; ++r) y[pad(o + r * Ns)] = v[r];
   }
 }
 
@@ -202,10 +228,11 @@ __device__ __forceinline__ Cx<T>* fft_lines(Cx<T>* X, Cx<T>* Y, int sL, int P, i
   int sNs = 0, cNs = 1;  // the sub-transform size so far, Ns = cNs 2^sNs
 #pragma unroll 1
   for (int st = 0; st < nst; ++st) {
-    const int R = (int)((radix_code >> (4 * st)) & 15u);
+    const int R = (int)((radix_code >> (5 * st)) & 31u);
     const Cx<T>* ws = w + (cNs << sNs) - 1;
-    // m = n / R = cm 2^sm: c 2^(sn-2), c 2^(sn-1), or (c / R) 2^sn for an odd radix
+    // m = n / R = cm 2^sm: c 2^(sn-4), c 2^(sn-2), c 2^(sn-1), or (c / R) 2^sn for an odd radix
     switch (R) {
+      case 16: fft_stage<T, 16>(X, Y, sL, n, P, sNs, cNs, c, sn - 4, ws, root, s); sNs += 4; break;
       case 4: fft_stage<T, 4>(X, Y, sL, n, P, sNs, cNs, c, sn - 2, ws, root, s); sNs += 2; break;
       case 2: fft_stage<T, 2>(X, Y, sL, n, P, sNs, cNs, c, sn - 1, ws, root, s); sNs += 1; break;
       case 3: fft_stage<T, 3>(X, Y, sL, n, P, sNs, cNs, c / 3, sn, ws, root, s); cNs *= 3; break;
@@ -235,9 +262,10 @@ struct FftPassArgs {
   const T* khat;         // z pass: the kernel's transform (real), scaled
 };
 
-// Line pitch in shared memory: odd, so that the L lines of a y or z pass,
-// loaded one grid row segment at a time, fall in distinct banks.
-__host__ __device__ __forceinline__ int line_pitch(int n) { return n | 1; }
+// Line pitch in shared memory: the padded line, made odd, so that the L lines
+// of a y or z pass, loaded one grid row segment at a time, fall in distinct
+// banks.
+__host__ __device__ __forceinline__ int line_pitch(int n) { return (pad(n - 1) + 1) | 1; }
 
 // MODE: 0 x forward from real FP64 input, 1 forward (any axis), 2 z forward
 // x K^ x z inverse, 3 inverse (y), 4 x inverse to real output.  The block's
@@ -298,7 +326,7 @@ __device__ __forceinline__ void fft_pass_body(const FftPassArgs<T>* __restrict__
           e = t >> sL;
           l = t & (L - 1);
         }
-        at[u] = l * P + e;
+        at[u] = l * P + pad(e);
         if (l < nl) {
           const long long o = base + l * ls + e * es;
           if (MODE == 0) v[u].x = (T)Ap->qin[o];
@@ -326,8 +354,8 @@ __device__ __forceinline__ void fft_pass_body(const FftPassArgs<T>* __restrict__
       for (int u = 0; u < kFftBatch; ++u) {
         const int t = t0 + u * (int)blockDim.x, e = t >> sL, l = t & (L - 1);
         if (t < total && l < nl) {
-          R[l * P + e].x *= kh[u];
-          R[l * P + e].y *= kh[u];
+          R[l * P + pad(e)].x *= kh[u];
+          R[l * P + pad(e)].y *= kh[u];
         }
       }
     }
@@ -346,8 +374,8 @@ __device__ __forceinline__ void fft_pass_body(const FftPassArgs<T>* __restrict__
     }
     if (l < nl) {
       const long long o = base + l * ls + e * es;
-      if (MODE == 4) uout[o] = R[l * P + e].x;
-      else buf[o] = R[l * P + e];
+      if (MODE == 4) uout[o] = R[l * P + pad(e)].x;
+      else buf[o] = R[l * P + pad(e)];
     }
   }
 }
@@ -361,11 +389,12 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 4 : 2) k_fft_pas
   fft_pass_body<T, MODE>(tab + r, (int)blockIdx.x - __ldg(first + r));
 }
 
-// n = c 2^s with c a product of 3, 5 and 7: stages radix 4 (while 4
-// divides the power of two), one radix 2 if one factor 2 is left, then the
-// factors of c (3s, 5s, 7s).  Returns false for any other n or more than 16
-// stages.
-bool factorize(int n, FftAxisDesc& D) {
+// n = c 2^s with c a product of 3, 5 and 7: stages radix 16 (while 16
+// divides the power of two, with radix16: the FP32 form, whose 16 values a
+// thread keeps in registers), radix 4 (while 4 divides what is left), one
+// radix 2 if one factor 2 is left, then the factors of c (3s, 5s, 7s).
+// Returns false for any other n or more than 12 stages.
+bool factorize(int n, FftAxisDesc& D, bool radix16) {
   D = FftAxisDesc{n, 1, 0, 0, 0ull};
   if (n < 1) return false;
   int p = n;
@@ -376,9 +405,11 @@ bool factorize(int n, FftAxisDesc& D) {
   D.c = p;
   int s = D.s;
   auto push = [&](int r) {
-    if (D.nst < 16) D.radix_code |= (unsigned long long)r << (4 * D.nst);
+    if (D.nst < 12) D.radix_code |= (unsigned long long)r << (5 * D.nst);
     D.nst++;
   };
+  if (radix16)
+    for (; s >= 4; s -= 4) push(16);
   for (; s >= 2; s -= 2) push(4);
   if (s == 1) push(2);
   for (int r : {3, 5, 7})
@@ -386,7 +417,7 @@ bool factorize(int n, FftAxisDesc& D) {
       push(r);
       p /= r;
     }
-  return p == 1 && D.nst <= 16;
+  return p == 1 && D.nst <= 12;
 }
 
 // Lines per block: the largest power of two up to 16 whose two line buffers
@@ -412,7 +443,7 @@ FftPassArgs<T> pass_args(const int dims[3], int axis, const void* tw, void* buf,
   A.axis = axis;
   A.sL = lines_per_block_log2<T>(n);
   A.groups_per_row = (dims[0] + (1 << A.sL) - 1) >> A.sL;
-  factorize(n, A.D);
+  factorize(n, A.D, sizeof(T) == sizeof(float));
   A.tw = reinterpret_cast<const Cx<T>*>(tw);
   A.buf = reinterpret_cast<Cx<T>*>(buf);
   A.qin = nullptr;
@@ -436,13 +467,13 @@ void run_pass(const BatchTable<FftPassArgs<T>>& t, cudaStream_t st) {
 // The twiddle table of one axis of length n, FP64: the stage tables
 // exp(-2 pi i r k / (Ns R)) at (Ns - 1) + (r - 1) Ns + k, then the seventh
 // roots of unity exp(-2 pi i q / 7).
-std::vector<double> twiddles(int n) {
+std::vector<double> twiddles(int n, bool radix16) {
   FftAxisDesc D;
-  factorize(n, D);
+  factorize(n, D, radix16);
   std::vector<double> tw(2 * (size_t)(n - 1 + kRoots), 0.0);
   int Ns = 1;
   for (int st = 0; st < D.nst; ++st) {
-    const int R = (int)((D.radix_code >> (4 * st)) & 15u);
+    const int R = (int)((D.radix_code >> (5 * st)) & 31u);
     for (int r = 1; r < R; ++r)
       for (int k = 0; k < Ns; ++k) {
         const size_t i = (size_t)(Ns - 1) + (size_t)(r - 1) * Ns + k;
@@ -502,7 +533,7 @@ cudaError_t configure_fft_kernels() {
 
 bool fft_size_ok(int n) {
   FftAxisDesc D;
-  return n <= 4096 && factorize(n, D);
+  return n <= 4096 && factorize(n, D, false) && factorize(n, D, true);
 }
 
 // Builds level k's tables: twiddles per axis (in the plan's precision) and
@@ -515,7 +546,9 @@ cudaError_t fft_build_level(Plan& P, int k, const std::vector<double>& K, void* 
   cudaError_t e = cudaSuccess;
   void* tw64[3] = {nullptr, nullptr, nullptr};
   for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
-    const std::vector<double> tw = twiddles(F.n[d]);
+    // FP64 passes (K^ here, and the FP64 plan's) take radix 4 at most; the
+    // FP32 form also radix 16, with its own stage tables
+    const std::vector<double> tw = twiddles(F.n[d], false);
     e = cudaMalloc(&tw64[d], sizeof(double) * tw.size());
     if (e == cudaSuccess) e = cudaMemcpy(tw64[d], tw.data(), sizeof(double) * tw.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) break;
@@ -523,7 +556,8 @@ cudaError_t fft_build_level(Plan& P, int k, const std::vector<double>& K, void* 
       e = cudaMalloc(&F.tw[d], sizeof(double) * tw.size());
       if (e == cudaSuccess) e = cudaMemcpy(F.tw[d], tw.data(), sizeof(double) * tw.size(), cudaMemcpyHostToDevice);
     } else {
-      const std::vector<float> twf(tw.begin(), tw.end());
+      const std::vector<double> tw16 = twiddles(F.n[d], true);
+      const std::vector<float> twf(tw16.begin(), tw16.end());
       e = cudaMalloc(&F.tw[d], sizeof(float) * twf.size());
       if (e == cudaSuccess) e = cudaMemcpy(F.tw[d], twf.data(), sizeof(float) * twf.size(), cudaMemcpyHostToDevice);
     }
