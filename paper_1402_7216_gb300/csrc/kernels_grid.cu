@@ -487,6 +487,31 @@ struct AxisArgs {
   int periodic;
 };
 
+// The output point t of an axis pass as (x, y, z): 32-bit divisions while
+// the grid has fewer than 2^32 points (64-bit integer division is a long
+// software sequence on the GPU), 64-bit beyond.
+__device__ __forceinline__ void axis_point(int64_t t, const int nout[3], int64_t np, int c[3]) {
+  if (np <= 0xffffffffLL) {
+    const unsigned tu = (unsigned)t, n0 = (unsigned)nout[0], n1 = (unsigned)nout[1];
+    const unsigned q = tu / n0;
+    c[0] = (int)(tu - q * n0);
+    c[1] = (int)(q % n1);
+    c[2] = (int)(q / n1);
+  } else {
+    c[0] = (int)(t % nout[0]);
+    c[1] = (int)((t / nout[0]) % nout[1]);
+    c[2] = (int)(t / ((int64_t)nout[0] * nout[1]));
+  }
+}
+
+// index s into [0, n) on a periodic axis: s is at most a few taps outside,
+// so a wrap by additions replaces the integer modulo
+__device__ __forceinline__ int wrap_periodic(int s, int n) {
+  while (s < 0) s += n;
+  while (s >= n) s -= n;
+  return s;
+}
+
 // restriction along one axis: out[.., c, ..] = sum_d w(d) in[.., 2(lo_out + c) + d - lo_in, ..]
 template <typename T, int ORDER>
 __device__ __forceinline__ void restrict_axis_body(const T* __restrict__ in, T* __restrict__ out, const AxisArgs& A,
@@ -494,7 +519,8 @@ __device__ __forceinline__ void restrict_axis_body(const T* __restrict__ in, T* 
   constexpr int R = ORDER;  // taps reach |d| <= 2S - 1 = ORDER
   int64_t np = (int64_t)A.nout[0] * A.nout[1] * A.nout[2];
   if (t >= np) return;
-  int c[3] = {(int)(t % A.nout[0]), (int)((t / A.nout[0]) % A.nout[1]), (int)(t / ((int64_t)A.nout[0] * A.nout[1]))};
+  int c[3];
+  axis_point(t, A.nout, np, c);
   int64_t stride = A.axis == 0 ? 1 : (A.axis == 1 ? (int64_t)A.nin[0] : (int64_t)A.nin[0] * A.nin[1]);
   int cc = c[A.axis];
   c[A.axis] = 0;
@@ -507,8 +533,7 @@ __device__ __forceinline__ void restrict_axis_body(const T* __restrict__ in, T* 
     if (d != 0 && (d & 1) == 0) continue;
     int s = nu0 + d - A.lo_in;
     if (A.periodic) {
-      s %= n;
-      if (s < 0) s += n;
+      s = wrap_periodic(s, n);
     } else if (s < 0 || s >= n) {
       continue;
     }
@@ -529,7 +554,8 @@ __device__ __forceinline__ void prolong_axis_body(const T* __restrict__ in, T* _
   constexpr int R = ORDER;
   int64_t np = (int64_t)A.nout[0] * A.nout[1] * A.nout[2];
   if (t >= np) return;
-  int c[3] = {(int)(t % A.nout[0]), (int)((t / A.nout[0]) % A.nout[1]), (int)(t / ((int64_t)A.nout[0] * A.nout[1]))};
+  int c[3];
+  axis_point(t, A.nout, np, c);
   int64_t stride = A.axis == 0 ? 1 : (A.axis == 1 ? (int64_t)A.nin[0] : (int64_t)A.nin[0] * A.nin[1]);
   int f = c[A.axis];
   c[A.axis] = 0;
@@ -543,8 +569,7 @@ __device__ __forceinline__ void prolong_axis_body(const T* __restrict__ in, T* _
     if (((nu - d) & 1) != 0) continue;
     int s = (nu - d) / 2 - A.lo_in;
     if (A.periodic) {
-      s %= n;
-      if (s < 0) s += n;
+      s = wrap_periodic(s, n);
     } else if (s < 0 || s >= n) {
       continue;
     }
