@@ -348,20 +348,34 @@ __device__ __forceinline__ void pair2(float2 bx, float2 by, float2 bz, float2 bq
     const float2 pot = __fadd2_rn(rinv, poly_g<M>(C, r2));  // G holds -gamma coefficients
     sphi = __ffma2_rn(qj, pot, sphi);
     fp = __fmul2_rn(__ffma2_rn(__fmul2_rn(rinv, rinv), rinv, poly_d<M>(C, r2)), qj);
-  } else if (K == kPairWolf) {  // damped shifted force within the cutoff, one source at a time
-    float pv[2], fv[2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const float x2 = c ? r2.y : r2.x;
-      const bool ok = x2 < a2;
-      const float r2s = ok ? x2 : a2, q = ok ? (c ? bq.y : bq.x) : 0.f;
-      const float ri = fast_rsqrt(r2s), r = r2s * ri;
-      const float e = erfcf(W.alpha * r), g = W.c2 * expf(-W.alpha2 * r2s);
-      pv[c] = q * (e * ri - W.vR + W.c1 * (r - W.R));
-      fv[c] = q * ((e * ri + g) * ri * ri - W.c1 * ri);  // -v'(r)/r, the sign this kernel sums with
-    }
-    sphi = __fadd2_rn(sphi, make_float2(pv[0], pv[1]));
-    fp = make_float2(fv[0], fv[1]);
+  } else if (K == kPairWolf) {
+    // damped shifted force within the cutoff; erfc(x) by Abramowitz and
+    // Stegun 7.1.26, t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),
+    // t = 1 / (1 + p x), |error| < 1.5e-7 for x >= 0, whose exp(-x^2) is the
+    // force term's exp(-alpha^2 r^2) as well
+    const bool okx = r2.x < a2, oky = r2.y < a2;
+    const float2 r2s = make_float2(okx ? r2.x : a2, oky ? r2.y : a2);
+    const float2 q = make_float2(okx ? bq.x : 0.f, oky ? bq.y : 0.f);
+    const float2 ri = make_float2(fast_rsqrt(r2s.x), fast_rsqrt(r2s.y));
+    const float2 r = __fmul2_rn(r2s, ri);
+    const float2 al = make_float2(W.alpha, W.alpha);
+    const float2 x = __fmul2_rn(al, r);
+    const float2 den = __ffma2_rn(make_float2(0.3275911f, 0.3275911f), x, make_float2(1.f, 1.f));
+    const float2 t = make_float2(__fdividef(1.f, den.x), __fdividef(1.f, den.y));
+    float2 poly = make_float2(1.061405429f, 1.061405429f);
+    poly = __ffma2_rn(poly, t, make_float2(-1.453152027f, -1.453152027f));
+    poly = __ffma2_rn(poly, t, make_float2(1.421413741f, 1.421413741f));
+    poly = __ffma2_rn(poly, t, make_float2(-0.284496736f, -0.284496736f));
+    poly = __ffma2_rn(poly, t, make_float2(0.254829592f, 0.254829592f));
+    const float2 ex = make_float2(__expf(-W.alpha2 * r2s.x), __expf(-W.alpha2 * r2s.y));
+    const float2 e = __fmul2_rn(__fmul2_rn(poly, t), ex);  // erfc(alpha r)
+    const float2 er = __fmul2_rn(e, ri);
+    // q (erfc(alpha r) / r - v_R + c1 (r - R)) and -v'(r) / r = q ((e/r + c2 ex) / r^2 - c1 / r)
+    const float2 c1v = make_float2(W.c1, W.c1);
+    const float2 pot = __ffma2_rn(c1v, __fadd2_rn(r, make_float2(-W.R, -W.R)), __fadd2_rn(er, make_float2(-W.vR, -W.vR)));
+    sphi = __ffma2_rn(q, pot, sphi);
+    const float2 inner = __ffma2_rn(make_float2(W.c2, W.c2), ex, er);
+    fp = __fmul2_rn(q, __ffma2_rn(__fmul2_rn(inner, ri), ri, __fmul2_rn(make_float2(-W.c1, -W.c1), ri)));
   } else {  // plain Coulomb within the cutoff
     const float2 qj = make_float2(r2.x < a2 ? bq.x : 0.f, r2.y < a2 ? bq.y : 0.f);
     const float2 rinv = make_float2(fast_rsqrt(r2.x), fast_rsqrt(r2.y));
@@ -390,13 +404,8 @@ __device__ __forceinline__ void pair_batch_f2(const QueueF& Q, float2 nax, float
     pair2<M, K, SELF>(make_float2(x4.z, x4.w), make_float2(y4.z, y4.w), make_float2(z4.z, z4.w),
                       make_float2(q4.z, q4.w), nax, nay, naz, a2, C, W, sphi, sx, sy, sz);
   };
-  if (K == kPairWolf) {  // two library calls per source: a rolled loop keeps the code in the instruction cache
-#pragma unroll 1
-    for (int jj = 0; jj < NB; jj += 4) four(jj);
-  } else {
 #pragma unroll
-    for (int jj = 0; jj < NB; jj += 4) four(jj);
-  }
+  for (int jj = 0; jj < NB; jj += 4) four(jj);
   two_sum_add(phi, cphi, sphi.x + sphi.y);
   two_sum_add(px, cpx, sx.x + sx.y);
   two_sum_add(py, cpy, sy.x + sy.y);

@@ -6,8 +6,9 @@ compared.
 
 Tolerances: FP64 plan energy rel 1e-10, force/potential rel-RMS 1e-9 (same
 sum, other order); mixed plan energy rel 1e-6, force rel-RMS 1e-5, potential
-rel-RMS 1e-6 (FP32 pair sums with compensated accumulation; erfcf and expf
-from CUDA's math library), each with the per-atom bound of
+rel-RMS 1e-6 (FP32 pair sums with compensated accumulation; erfc by
+Abramowitz and Stegun 7.1.26, |error| < 1.5e-7, which moves the potential by
+~2e-7 rel-RMS on water), each with the per-atom bound of
 conftest.assert_atoms."""
 import numpy as np
 import pytest
