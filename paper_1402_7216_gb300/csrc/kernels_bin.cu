@@ -38,6 +38,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 
 #include "msm_internal.h"
 
@@ -423,9 +424,65 @@ __device__ __forceinline__ void write_records(const IO* __restrict__ pos, const 
   perm[s] = i;
 }
 
+// One atom's records in registers (computed once from one read of its
+// position) and its sub-cell code, from the same cell-local coordinates as
+// subcell_code and write_records above.
+template <bool FP64>
+struct CellRec {
+  using T = typename std::conditional<FP64, double, float>::type;
+  T loc[3], fr[3], q;
+  int bs[3];
+};
+
+template <typename IO, bool FP64>
+__device__ __forceinline__ int make_record(const IO* __restrict__ pos, const IO* __restrict__ q, const BinArgs& A,
+                                           int key, int i, CellRec<FP64>& R) {
+  const int kc[3] = {key % A.nc[0], (key / A.nc[0]) % A.nc[1], key / (A.nc[0] * A.nc[1])};
+  int bad = 0, code = 0;
+  for (int d = 0; d < 3; ++d) {
+    int sd;
+    if (FP64) {
+      const double v = prep_fp64(pos[3 * (size_t)i + d], A, d, bad);
+      R.loc[d] = v - kc[d] * A.cw[d];
+      sd = (int)((v - kc[d] * A.cw[d]) * (4.0 * A.inv_cw[d]));
+      double fr;
+      grid_fp64(v, A, d, R.bs[d], fr);
+      R.fr[d] = fr;
+    } else {
+      float hi, lo;
+      prep_mixed(pos[3 * (size_t)i + d], A, d, bad, hi, lo);
+      const float loc = offset_from(hi, lo, kc[d], A.cw_hi[d], A.cw_lo[d]);
+      R.loc[d] = loc;
+      sd = (int)(loc * (4.f * A.inv_cwf[d]));
+      float fr;
+      grid_mixed(hi, lo, A, d, R.bs[d], fr);
+      R.fr[d] = fr;
+    }
+    sd = min(max(sd, 0), 3);
+    code |= ((sd & 1) << d) | (((sd >> 1) & 1) << (3 + d));
+  }
+  R.q = finite_bits(q[i]) ? (typename CellRec<FP64>::T)q[i] : (typename CellRec<FP64>::T)0;
+  return code;
+}
+
+template <bool FP64>
+__device__ __forceinline__ void store_record(const CellRec<FP64>& R, const BinArgs& A, int i, int s,
+                                             void* __restrict__ atoms_v, void* __restrict__ gfrac_v,
+                                             int4* __restrict__ gbase, int* __restrict__ perm) {
+  using T = typename CellRec<FP64>::T;
+  reinterpret_cast<R4<T>*>(atoms_v)[s] = R4<T>{R.loc[0], R.loc[1], R.loc[2], R.q};
+  reinterpret_cast<R4<T>*>(gfrac_v)[s] = R4<T>{R.fr[0], R.fr[1], R.fr[2], R.q};
+  gbase[s] = make_int4(R.bs[0] - (A.S - 1), R.bs[1] - (A.S - 1), R.bs[2] - (A.S - 1), 0);
+  perm[s] = i;
+}
+
 // One warp per cell: the cell's atoms (perm, in provisional order) are put in
-// (sub-cell, index) order and their records written.  idx: the warp's
-// kOrderMax keys in shared memory.
+// (sub-cell, index) order and their records written.  A cell of at most 32
+// atoms (nearly every cell) takes one atom per lane: the lane reads its
+// atom's position once, keeps the records in registers, ranks its key among
+// the cell's keys and stores at that rank.  Larger cells go through the keys
+// in shared memory (idx: the warp's kOrderMax keys) and recompute the
+// records.
 template <typename IO, bool FP64>
 __device__ __forceinline__ void cell_fill_body(const IO* __restrict__ pos, const IO* __restrict__ q,
                                                const BinArgs& A, const int* __restrict__ cell_start,
@@ -435,7 +492,23 @@ __device__ __forceinline__ void cell_fill_body(const IO* __restrict__ pos, const
   if (cell >= ncell) return;  // warp-uniform
   const int lane = threadIdx.x & 31;
   const int s0 = cell_start[cell], m = cell_start[cell + 1] - s0;
-  if (m <= kOrderMax) {
+  if (m <= 32) {
+    CellRec<FP64> R;
+    long long k = 0x7fffffffffffffffll;  // lanes past the cell rank after every atom
+    int i = 0;
+    if (lane < m) {
+      i = perm[s0 + lane];
+      k = ((long long)make_record<IO, FP64>(pos, q, A, cell, i, R) << 32) | (long long)i;
+      idx[lane] = k;
+    }
+    __syncwarp();
+    if (lane < m) {
+      int r = 0;
+      for (int j = 0; j < m; ++j) r += idx[j] < k;  // keys are distinct: r is a permutation of 0..m-1
+      store_record<FP64>(R, A, i, s0 + r, atoms_v, gfrac_v, gbase, perm);
+    }
+    __syncwarp();
+  } else if (m <= kOrderMax) {
     for (int t = lane; t < m; t += 32) {
       const int i = perm[s0 + t];
       idx[t] = ((long long)subcell_code<IO, FP64>(pos, A, cell, i) << 32) | (long long)i;
