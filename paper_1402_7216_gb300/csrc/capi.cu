@@ -343,8 +343,8 @@ struct msm_graph {
   BinBatch* bin = nullptr;
   PairBatch* pair = nullptr;
   GridBatch* grid = nullptr;
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t side = nullptr, side2 = nullptr;  // the forward's and the adjoint's grid passes
+  cudaEvent_t fork = nullptr, join = nullptr, front = nullptr, join2 = nullptr;
   // the plans whose buffers a replay refills (each replay is a new forward)
   std::vector<Plan*> plans;
 };
@@ -391,8 +391,11 @@ int batch_tables(msm_graph* g, const msm_handle* plans, int nrep, const int64_t*
       grid_batch_build(reps, grad_energies != nullptr, &g->grid) != cudaSuccess ||
       cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
       cudaStreamCreateWithPriority(&g->side, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&g->side2, cudaStreamNonBlocking, greatest) != cudaSuccess ||
       cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&g->join, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&g->join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->front, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->join2, cudaEventDisableTiming) != cudaSuccess)
     return MSM_ERR_CUDA;
   for (int r = 0; r < nrep; ++r) plans[r]->p.last_n = off[r + 1] - off[r];
   return MSM_OK;
@@ -401,17 +404,33 @@ int batch_tables(msm_graph* g, const msm_handle* plans, int nrep, const int64_t*
 // The batched forward (and adjoint) on cs: binning of every replica, then the
 // pair sums of every replica on cs concurrently with the grid passes of every
 // replica on the high-priority side stream, then interpolation; each stage is
-// one launch over all replicas.
+// one launch over all replicas.  The adjoint's grid passes need only the
+// binned atoms and the anterpolated charges (not the forward's pair sums or
+// potentials), so after the shared anterpolation they run on a second side
+// stream beside the forward's (each direction has its own temporaries); the
+// adjoint's interpolation waits for them.  Persistent chains share one grid
+// barrier, so with them the adjoint's passes follow the forward's on cs.
 int batch_fused(msm_graph* g, cudaStream_t cs, bool backward) {
+  const bool side_adjoint = backward && !grid_batch_persistent(g->grid);
   cudaError_t e = bin_batch_launch(g->bin, cs);
   if (e == cudaSuccess) e = cudaEventRecord(g->fork, cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(g->side, g->fork, 0);
-  if (e == cudaSuccess) e = grid_batch_sweep(g->grid, false, g->side);
+  if (e == cudaSuccess) e = grid_batch_front(g->grid, backward, g->side);
+  if (e == cudaSuccess && side_adjoint) {
+    e = cudaEventRecord(g->front, g->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->side2, g->front, 0);
+    if (e == cudaSuccess) e = grid_batch_levels(g->grid, 1, g->side2);
+    if (e == cudaSuccess) e = cudaEventRecord(g->join2, g->side2);
+  }
+  if (e == cudaSuccess) e = grid_batch_levels(g->grid, 0, g->side);
   if (e == cudaSuccess) e = cudaEventRecord(g->join, g->side);
   if (e == cudaSuccess) e = pair_batch_launch(g->pair, cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, g->join, 0);
   if (e == cudaSuccess) e = grid_batch_interp(g->grid, false, cs);
-  if (e == cudaSuccess && backward) e = grid_batch_sweep(g->grid, true, cs);
+  if (e == cudaSuccess && backward) {
+    if (side_adjoint) e = cudaStreamWaitEvent(cs, g->join2, 0);
+    else e = grid_batch_levels(g->grid, 1, cs);
+  }
   if (e == cudaSuccess && backward) e = grid_batch_interp(g->grid, true, cs);
   return e == cudaSuccess ? MSM_OK : MSM_ERR_CUDA;
 }
@@ -794,8 +813,11 @@ void msm_graph_destroy(msm_graph_handle g) {
   pair_batch_free(g->pair);
   grid_batch_free(g->grid);
   if (g->side) cudaStreamDestroy(g->side);
+  if (g->side2) cudaStreamDestroy(g->side2);
   if (g->fork) cudaEventDestroy(g->fork);
   if (g->join) cudaEventDestroy(g->join);
+  if (g->front) cudaEventDestroy(g->front);
+  if (g->join2) cudaEventDestroy(g->join2);
   delete g;
 }
 

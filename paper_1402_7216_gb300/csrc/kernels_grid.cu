@@ -2063,6 +2063,8 @@ struct GridBatch {
   unsigned* bar = nullptr;
   int* status = nullptr;
   int chain_blocks = 0;
+  // the adjoint direction's temporaries, one block per replica
+  std::vector<void*> scratch1;
 };
 
 void grid_batch_free(GridBatch* b) {
@@ -2087,6 +2089,7 @@ void grid_batch_free(GridBatch* b) {
     if (b->chain_prol[d]) cudaFree(b->chain_prol[d]);
   }
   if (b->bar) cudaFree(b->bar);
+  for (void* p : b->scratch1) cudaFree(p);
   delete b;
 }
 
@@ -2128,7 +2131,36 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
     chk(make_table(B->zero_fx, za, zb));
     chk(make_table(B->anterp, aa, ab, sm));
   }
+  // the adjoint direction's own temporaries (restriction and prolongation,
+  // the FFT workspace or the stencil's FP32 charges, the top level's FP64
+  // values), so that its level chain can run beside the forward's
+  struct Scratch {
+    void* tmp[2] = {nullptr, nullptr};
+    void* fftw = nullptr;
+    double* topu = nullptr;
+  };
+  std::vector<Scratch> S1(reps.size());
+  if (backward)
+    for (size_t i = 0; i < reps.size() && e == cudaSuccess; ++i) {
+      Plan& P = *reps[i].plan;
+      size_t lat = 0;
+      for (int k = 0; k + 1 < P.levels; ++k) lat += (size_t)grid_points(P, k);
+      const size_t tmpb = sizeof(double) * (size_t)P.tmp_elems, fftb = P.lattice_fft ? 16 * lat : 0;
+      const size_t topb = sizeof(double) * (size_t)grid_points(P, P.levels - 1);
+      char* base = nullptr;
+      chk(cudaMalloc((void**)&base, 2 * tmpb + fftb + topb));
+      if (e != cudaSuccess) break;
+      B->scratch1.push_back(base);
+      S1[i].tmp[0] = base;
+      S1[i].tmp[1] = base + tmpb;
+      S1[i].fftw = base + 2 * tmpb;
+      S1[i].topu = reinterpret_cast<double*>(base + 2 * tmpb + fftb);
+    }
   for (int dir = 0; dir < (backward ? 2 : 1); ++dir) {
+    // this direction's temporaries of replica r
+    auto tmp_of = [&](const BatchRep& r, int i) -> void* {
+      return dir ? S1[&r - &reps[0]].tmp[i] : r.plan->d.tmp[i];
+    };
     std::vector<FxKArgs> fa;
     std::vector<int> fb;
     for (const BatchRep& r : reps) {
@@ -2151,8 +2183,8 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
           int nb = 0;
           if (k + 1 < P.levels) {
             void* const* q = dir ? P.d.aq : P.d.gq;
-            const double* src[3] = {(const double*)q[k], (const double*)P.d.tmp[0], (const double*)P.d.tmp[1]};
-            double* dst[3] = {(double*)P.d.tmp[0], (double*)P.d.tmp[1], (double*)q[k + 1]};
+            const double* src[3] = {(const double*)q[k], (const double*)tmp_of(r, 0), (const double*)tmp_of(r, 1)};
+            double* dst[3] = {(double*)tmp_of(r, 0), (double*)tmp_of(r, 1), (double*)q[k + 1]};
             int cur[3] = {P.n[k][0], P.n[k][1], P.n[k][2]};
             for (int a2 = 0; a2 < ax; ++a2) cur[a2] = P.n[k + 1][a2];
             for (int d = 0; d < 3; ++d) a.A.nin[d] = cur[d];
@@ -2186,8 +2218,9 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
         void* const* u = dir ? P.d.au : P.d.gu;
         int64_t off = 0;
         for (int k = 0; k + 1 < P.levels; ++k) {
+          void* work = dir ? S1[&r - &reps[0]].fftw : P.d.fft_work;
           items.push_back(FftBatchItem{&P.fftl[k], (const double*)q[k], u[k],
-                                       (char*)P.d.fft_work + 2 * sizeof(float) * (size_t)off});
+                                       (char*)work + 2 * sizeof(float) * (size_t)off});
           off += grid_points(P, k);
         }
       }
@@ -2207,7 +2240,7 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
         int64_t off = 0;
         for (int k = 0; k + 1 < P.levels; ++k) {
           const int64_t np = grid_points(P, k);
-          float* qf = (float*)P.d.tmp[0] + off;
+          float* qf = (float*)tmp_of(r, 0) + off;
           off += np;
           ca.push_back(ConvKArgs{(const double*)q[k], qf, np});
           cb.push_back(ew_blocks(np));
@@ -2279,7 +2312,8 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
         const int top = P.levels - 1;
         void* const* q = dir ? P.d.aq : P.d.gq;
         void* const* u = dir ? P.d.au : P.d.gu;
-        ta.push_back(TopKArgs{(const double*)q[top], (float*)u[top], P.d.topu, dims_of(P, top), P.d.topK,
+        ta.push_back(TopKArgs{(const double*)q[top], (float*)u[top], dir ? S1[&r - &reps[0]].topu : P.d.topu,
+                              dims_of(P, top), P.d.topK,
                               P.top_table_dims[0], P.top_table_dims[1]});
         tb.push_back((int)blocks_for(grid_points(P, top), kTopWarps));
       }
@@ -2297,8 +2331,8 @@ cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, G
           int nb = 0;
           if (k + 1 < P.levels) {
             void* const* u = dir ? P.d.au : P.d.gu;
-            const float* src[3] = {(const float*)u[k + 1], (const float*)P.d.tmp[0], (const float*)P.d.tmp[1]};
-            float* dst[3] = {(float*)P.d.tmp[0], (float*)P.d.tmp[1], (float*)u[k]};
+            const float* src[3] = {(const float*)u[k + 1], (const float*)tmp_of(r, 0), (const float*)tmp_of(r, 1)};
+            float* dst[3] = {(float*)tmp_of(r, 0), (float*)tmp_of(r, 1), (float*)u[k]};
             int cur[3] = {P.n[k + 1][0], P.n[k + 1][1], P.n[k + 1][2]};
             for (int j = 0; j < i; ++j) cur[2 - j] = P.n[k][2 - j];
             const int ax = 2 - i;  // z, then y, then x
@@ -2402,13 +2436,21 @@ void launch_table(const BatchTable<A>& t, K kernel, int threads, cudaStream_t st
   if (t.total > 0) kernel<<<t.total, threads, t.smem, st>>>(t.args, t.first, t.nrep);
 }
 
-cudaError_t grid_batch_sweep(GridBatch* B, bool backward, cudaStream_t st) {
-  const int d = backward ? 1 : 0;
+cudaError_t grid_batch_front(GridBatch* B, bool backward, cudaStream_t st) {
   if (backward && !B->has_backward) return cudaErrorInvalidValue;
   const bool o3 = B->order == 3;
   launch_table(B->zero_fx, kb_zero, kEw, st);
   launch_table(B->anterp, o3 ? kb_anterp_fx<3> : kb_anterp_fx<5>, 256, st);
-  launch_table(B->fx[d], kb_fx_to_f64, kEw, st);
+  launch_table(B->fx[0], kb_fx_to_f64, kEw, st);
+  if (backward) launch_table(B->fx[1], kb_fx_to_f64, kEw, st);
+  return cudaGetLastError();
+}
+
+bool grid_batch_persistent(const GridBatch* B) { return B->persistent; }
+
+cudaError_t grid_batch_levels(GridBatch* B, int d, cudaStream_t st) {
+  if (d == 1 && !B->has_backward) return cudaErrorInvalidValue;
+  const bool o3 = B->order == 3;
   if (B->persistent) {
     cudaError_t e = launch_chain(B, o3 ? kb_restrict_chain<3> : kb_restrict_chain<5>, B->chain_restr[d], B->n_restr, st);
     if (e != cudaSuccess) return e;

@@ -137,6 +137,7 @@ struct Plan {
   // lattice cutoff of periodic levels as an FFT convolution (fft.cu)
   bool lattice_fft = false;
   bool stencil_fits = true;  // the stencil kernel's shared-memory window holds this plan's stencil
+  int64_t tmp_elems = 0;     // FP64 elements of each of the two temporaries tmp[0], tmp[1]
   FftLevel fftl[kMaxLevels];
   FftBatch* fftb[2] = {nullptr, nullptr};  // every lattice level: the forward sweep's grids, the adjoint's
   // smoothing constants
@@ -260,7 +261,15 @@ void pair_batch_free(PairBatch* b);
 // interpolation with assembly (forward: phi, F and the energies; backward,
 // built only when every replica has grad_energy: dL/dq and dL/dr).
 cudaError_t grid_batch_build(const std::vector<BatchRep>& reps, bool backward, GridBatch** out);
-cudaError_t grid_batch_sweep(GridBatch* b, bool backward, cudaStream_t st);
+// The sweep in two parts: the front (anterpolation into the fixed-point
+// grids and their conversion to the level-0 charges of the forward and, with
+// backward, of the adjoint) and the level chain of one direction
+// (restriction, lattice cutoff, top level, prolongation).  The adjoint's
+// chain has its own temporaries, so it may run concurrently with the
+// forward's unless the chains are persistent (one grid barrier word).
+cudaError_t grid_batch_front(GridBatch* b, bool backward, cudaStream_t st);
+cudaError_t grid_batch_levels(GridBatch* b, int dir, cudaStream_t st);
+bool grid_batch_persistent(const GridBatch* b);
 cudaError_t grid_batch_interp(GridBatch* b, bool backward, cudaStream_t st);
 void grid_batch_free(GridBatch* b);
 

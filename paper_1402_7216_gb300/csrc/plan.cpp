@@ -532,6 +532,7 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
     tsize = std::max(tsize, t);
   }
   for (int i = 0; i < 2; ++i) M(&D.tmp[i], sizeof(double) * tsize);
+  P->tmp_elems = (int64_t)tsize;
   M(&D.lparts, T * (size_t)(P->stencil_fits ? lattice_parts_elems(*P) : 0));
   size_t ntop = (size_t)grid_points(*P, top);
   M((void**)&D.topq, sizeof(double) * ntop);
