@@ -315,12 +315,15 @@ int msm_parareal(const msm_handle* fine, msm_handle coarse, int64_t n, const dou
  *   grad_q      dL/dq, [n] double, device or NULL.
  * The long-range part is evaluated by the transposed grid passes
  * (interpolation^T = anterpolation, prolongation^T = restriction, the
- * symmetric lattice and top kernels), rebuilding the adjoint level-0
- * potential instead of storing any forward grid; the short-range part reuses
- * the per-atom pair sums the forward pass kept.  Asynchronous on cuda_stream.
+ * symmetric lattice and top kernels): the anterpolated adjoint charges are
+ * the forward's level-0 charge grid times dL/dE / 2 (the same atoms and
+ * weights), from which the sweep rebuilds the adjoint level-0 potential
+ * instead of storing any forward potential; the short-range part reuses the
+ * per-atom pair sums the forward pass kept.  Asynchronous on cuda_stream.
  * Errors: INVALID_ARG (also forward_id <= 0), NO_FORWARD (no MSM forward on
- * this plan, or the last evaluation was msm_cutoff_eval), STALE_FORWARD (a
- * later forward has reused the buffers: run the forward again), CUDA. */
+ * this plan, or the last evaluation was msm_cutoff_eval or msm_wolf_eval),
+ * STALE_FORWARD (a later forward has reused the buffers: run the forward
+ * again), CUDA. */
 int msm_eval_backward(msm_handle h, int64_t forward_id, const double* grad_energy, double* grad_pos,
                       double* grad_q, void* cuda_stream);
 

@@ -119,14 +119,19 @@ int forward(Plan& P, int64_t n, const IO* pos, const IO* q, double* energy, IO* 
 // 0 accepts whatever forward the plan holds (the batched adjoints).
 template <typename IO>
 int backward(Plan& P, int64_t forward_id, const double* grad_energy, IO* grad_pos, IO* grad_q, cudaStream_t st) {
-  if (P.last_n < 0) return MSM_ERR_NO_FORWARD;
+  if (P.last_n < 0 || P.forward_id == 0) return MSM_ERR_NO_FORWARD;  // no MSM forward in the plan's buffers
   if (forward_id != 0 && forward_id != P.forward_id) return MSM_ERR_STALE_FORWARD;
   int64_t n = P.last_n;
   // adjoint of u_long = A^T M A q with respect to its inputs: anterpolate the
   // adjoint of u_long (1/2 dL/dE q_i), sweep the (symmetric) grid operator,
-  // and interpolate the result back to the atoms.
+  // and interpolate the result back to the atoms.  The anterpolation of
+  // 1/2 dL/dE q_i is 1/2 dL/dE times the forward's level-0 charge grid (the
+  // same atoms and weights, kept in gq[0] until the next forward), so the
+  // adjoint's grid is that one scaled; the potential is recomputed by the
+  // sweep.  On the mixed path the result equals a fresh anterpolation bit
+  // for bit (the fixed-point sum and the power-of-two unit are exact).
   cudaError_t e = stage(P, MSM_STAGE_ANTERPOLATION, st,
-                        [&] { return launch_anterpolate(P, n, P.d.aq[0], grad_energy, 0.5, st); });
+                        [&] { return launch_scale_grid(P, P.d.gq[0], P.d.aq[0], grad_energy, 0.5, st); });
   if (e == cudaSuccess) e = grid_sweep(P, 1, st);
   if (e == cudaSuccess)
     e = stage(P, MSM_STAGE_INTERPOLATION, st,

@@ -1413,6 +1413,22 @@ cudaError_t launch_anterpolate(Plan& P, int64_t n, void* grid0, const double* ds
   return cudaGetLastError();
 }
 
+// dst = factor * dscale[0] * src over the level-0 grid (FP64)
+__global__ void k_scale_grid(const double* __restrict__ src, double* __restrict__ dst, int64_t count,
+                             const double* __restrict__ dscale, double factor) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  dst[i] = src[i] * (factor * *dscale);
+}
+
+cudaError_t launch_scale_grid(Plan& P, const void* src, void* dst, const double* dscale, double factor,
+                              cudaStream_t st) {
+  P.launches += 1;
+  const int64_t np = grid_points(P, 0);
+  k_scale_grid<<<blocks_for(np, 256), 256, 0, st>>>((const double*)src, (double*)dst, np, dscale, factor);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_restrict(Plan& P, int k, const void* fine, void* coarse, cudaStream_t st) {
   P.launches += 3;
   const int* nf = P.n[k];

@@ -298,6 +298,9 @@ cudaError_t launch_cutoff_assemble(Plan& P, int64_t n, double* energy, OUT* phi,
 // grid passes: anterpolation (charges q_i * scale, scale from device or 1)
 cudaError_t launch_anterpolate(Plan& P, int64_t n, void* grid0, const double* dscale, double factor,
                                cudaStream_t s);
+// the adjoint's level-0 charges: factor * dscale[0] times the forward's
+cudaError_t launch_scale_grid(Plan& P, const void* src, void* dst, const double* dscale, double factor,
+                              cudaStream_t s);
 cudaError_t launch_restrict(Plan& P, int k, const void* fine, void* coarse, cudaStream_t s);
 // Velocity Verlet around the MSM force: the two half steps of one MD step
 // and the per-step record (potential, kinetic, total energy, momentum).

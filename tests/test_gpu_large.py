@@ -7,7 +7,8 @@ checks at this size would need the FP64 lattice sum on 13.8M points (~1.6e11
 taps) on the host, so they run on the 1.07M-atom system instead.
 
 The adjoint rebuilds the level-0 potential from the anterpolated adjoint
-charges instead of storing any forward grid; its gradients must equal the
+charges (the forward's level-0 charges scaled) instead of storing any forward
+potential; its gradients must equal the
 forward's -F and phi (dE/dr = -F, dE/dq = phi) and agree between precisions.
 Tolerances: mixed vs FP64 energy 1e-6, force and dE/dr rel-RMS 1e-5,
 potential and dE/dq rel-RMS 1e-6, each with the per-atom bound of
