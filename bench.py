@@ -689,14 +689,15 @@ def run_profile_case(args):
         pos_h, q_h = w.make()
         pos, q = torch.tensor(pos_h, device=dev), torch.tensor(q_h, device=dev)
         plan = MSM(box=w.box, periodic=w.periodic, cutoff=w.cutoff, spacing=w.spacing, levels=w.levels,
-                   order=w.order, splitting=w.split, precision="mixed", max_atoms=len(q_h))
+                   order=w.order, splitting=w.split, precision="mixed", max_atoms=len(q_h),
+                   tuning=json.loads(args.tuning) if args.tuning else None)
         plan.set_overlap(False)
         for _ in range(args.warmup + args.steps):
             plan.eval(pos, q, want_phi=False, want_force=False)
         torch.cuda.synchronize()
         plan.check_status()
         out = {"workload": args.workload, "evaluations": args.warmup + args.steps, "lattice": plan.lattice_method,
-               "levels": plan.levels, "dims": plan.dims}
+               "levels": plan.levels, "dims": plan.dims, "tuning": plan.tuning}
     print(json.dumps({"profile_case": args.profile_case, "result": out}, default=str))
 
 
@@ -717,6 +718,8 @@ def main():
                     help="run one section alone and print its JSON (the commands the ncu summaries in profiles/ "
                          "use): 'evals' builds the benchmark system's default plan and runs --warmup then --steps "
                          "plain evaluations; 'batch' the 64-replica batch; 'large' the 4.1M-atom box")
+    ap.add_argument("--tuning", default=None,
+                    help="msm_tuning fields as JSON for --profile-case evals (e.g. the autotuner's choice)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -93,6 +93,12 @@ typedef struct {
  *                 per lane (the default); 8 against clusters of 8 spatially
  *                 consecutive atoms of a cell (fewer pairs, more culling
  *                 work: measured slower on water)
+ *   pair_runs     mixed-precision pair kernel with pair_targets 32: 1 a
+ *                 warp takes 32 consecutive atoms of the sorted order as its
+ *                 targets (runs across the cells of a row, which binning
+ *                 sorts by x), 2 a warp takes one cell's atoms; 0 the
+ *                 default, 2.  Runs need at least seven cells along x on a
+ *                 periodic plan and fall back to cells otherwise
  *   lattice_txn, lattice_tyn  warp tile of the mixed-precision lattice
  *                 kernel: txn lanes of 8 x outputs by tyn lanes of two rows,
  *                 txn * tyn <= 32 (default 4 x 8 on a single system; batched
@@ -115,7 +121,7 @@ typedef struct {
  *                 every replica's plan did; msm_lattice_method reports the
  *                 form a plan took.
  * Ranges: cell_fill 0..256, patch_cells 0..4, lattice_waves 0..64,
- * pair_targets 0, 8 or 32, batch_persistent 0 or 1, lattice_method 0..2,
+ * pair_targets 0, 8 or 32, batch_persistent 0 or 1, lattice_method 0..2, pair_runs 0..2,
  * lattice_txn and lattice_tyn 0..32 with
  * txn * tyn <= 32 and a staging window that fits shared memory; anything else
  * is INVALID_ARG (checked on the host before any device call; the window
@@ -129,6 +135,7 @@ typedef struct {
   int lattice_tyn;
   int batch_persistent;
   int lattice_method;
+  int pair_runs;
 } msm_tuning;
 
 /* Builds a plan: validates params, fixes the grid geometry, builds the

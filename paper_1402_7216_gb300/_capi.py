@@ -30,7 +30,7 @@ class MSMParams(C.Structure):
 class MSMTuning(C.Structure):
     _fields_ = [("cell_fill", C.c_int), ("patch_cells", C.c_int), ("lattice_waves", C.c_int),
                 ("pair_targets", C.c_int), ("lattice_txn", C.c_int), ("lattice_tyn", C.c_int),
-                ("batch_persistent", C.c_int), ("lattice_method", C.c_int)]
+                ("batch_persistent", C.c_int), ("lattice_method", C.c_int), ("pair_runs", C.c_int)]
 
 
 class MSMError(RuntimeError):

@@ -3,6 +3,8 @@
 The tunables change speed, never results beyond summation order:
   pair_targets   targets the pair kernel culls together: 32 (a cell's warp)
                  or 8 (clusters of 8 consecutive atoms)
+  pair_runs      with 32: a warp's targets are one cell's atoms (2, the
+                 default) or 32 consecutive atoms of an x-sorted cell row (1)
   cell_fill      target atoms per short-range cell (pair-kernel lane use vs
                  candidate volume)
   patch_cells    cells per side of the anterpolation/interpolation patch blocks
@@ -39,7 +41,7 @@ MARGIN = 0.01
 # (txn, tyn) lattice warp tiles: 32 x 16 outputs (the default) and shapes that
 # fit small or flat grids better
 TILES = [(4, 8), (2, 8), (4, 4), (8, 4), (2, 16), (8, 2), (1, 16)]
-SEARCH = [("lattice_method", [1]), ("pair_targets", [32, 8]), ("cell_fill", [20, 24, 28, 32]),
+SEARCH = [("lattice_method", [1]), ("pair_targets", [32, 8]), ("pair_runs", [1]), ("cell_fill", [20, 24, 28, 32]),
           ("patch_cells", [2, 3, 4]), ("lattice_waves", [4, 8, 16]), ("lattice_tile", TILES)]
 # fields that only the stencil form of the lattice cutoff reads
 STENCIL_ONLY = ("lattice_waves", "lattice_tile")
@@ -70,7 +72,7 @@ def cache_path():
 
 def cache_key(box, periodic, cutoff, spacing, levels, order, splitting, precision, n, backward=False):
     b = box if hasattr(box, "__len__") else (box, box, box)
-    return "v2|box=%.4f,%.4f,%.4f|per=%d|a=%.4f|h=%.4f|l=%d|p=%d|m=%d|%s|n=%d|bwd=%d" % (
+    return "v3|box=%.4f,%.4f,%.4f|per=%d|a=%.4f|h=%.4f|l=%d|p=%d|m=%d|%s|n=%d|bwd=%d" % (
         b[0], b[1], b[2], int(bool(periodic)), cutoff, spacing, levels, order, splitting, precision, n,
         int(bool(backward)))
 
@@ -183,7 +185,7 @@ def tuned_plan(pos, q, box, periodic, cutoff, spacing, **kw):
 
 # Batches: timed on the captured batch graph (forward + adjoint), the form
 # msm_batch_graph_create runs.
-SEARCH_BATCH = [("lattice_method", [1]), ("pair_targets", [32, 8]), ("batch_persistent", [0, 1]),
+SEARCH_BATCH = [("lattice_method", [1]), ("pair_targets", [32, 8]), ("pair_runs", [1]), ("batch_persistent", [0, 1]),
                 ("lattice_waves", [8, 16]), ("patch_cells", [3, 4]), ("cell_fill", [20, 24])]
 TILES_BATCH = [(4, 8), (2, 8), (4, 4), (8, 4), (2, 16), (1, 16)]
 
@@ -208,7 +210,7 @@ def time_graph(graph, reps=5, warmup=2):
 def batch_key(boxes, counts, cutoff, spacing, order, splitting, precision):
     import hashlib
     h = hashlib.sha1(repr((list(map(float, boxes)), list(map(int, counts)))).encode()).hexdigest()[:16]
-    return "batch3|%s|a=%.4f|h=%.4f|p=%d|m=%d|%s" % (h, cutoff, spacing, order, splitting, precision)
+    return "batch4|%s|a=%.4f|h=%.4f|p=%d|m=%d|%s" % (h, cutoff, spacing, order, splitting, precision)
 
 
 def autotune_batch(boxes, pos, q, counts, cutoff, spacing, order=3, splitting=2, precision="mixed", reps=5,

@@ -9,10 +9,11 @@
 //                  for the next evaluation
 //   k_bin_perm     perm[cell_start + rank] = atom index
 //   k_cell_fill    one warp per cell: orders the cell's atoms by the key
-//                  (sub-cell, input index) -- the sub-cell is the atom's
-//                  place on a 4 x 4 x 4 lattice inside the cell, taken in
-//                  Morton order, so that runs of consecutive atoms are
-//                  spatially compact (the pair kernel's target clusters);
+//                  (slab, input index) -- the slab is the atom's place on
+//                  256 slabs across the cell in x, so that a row of cells
+//                  (cells are numbered x fastest) is sorted by x and any
+//                  run of consecutive atoms of a row is a compact slab of it
+//                  (the pair kernel's 32-atom target runs);
 //                  each atom's final rank is the number of the cell's atoms
 //                  with a smaller key -- and writes their sorted records:
 //                  cell-local coordinates for the pair sums, fractional
@@ -366,27 +367,22 @@ __global__ void __launch_bounds__(256) k_bin_perm(int n, const int* __restrict__
   bin_perm_body(n, key_in, rank_in, cell_start, perm, blockIdx.x);
 }
 
-// Place of atom i on a 4 x 4 x 4 lattice inside its cell `key`, as a Morton
-// code (0..63), from its cell-local coordinates (the same arithmetic as the
-// records below).
+// Slab of atom i across its cell `key` in x (0..kSlabs-1), from its
+// cell-local x coordinate (the same arithmetic as the records below).
+constexpr int kSlabs = 256;
 template <typename IO, bool FP64>
-__device__ __forceinline__ int subcell_code(const IO* __restrict__ pos, const BinArgs& A, int key, int i) {
-  const int kc[3] = {key % A.nc[0], (key / A.nc[0]) % A.nc[1], key / (A.nc[0] * A.nc[1])};
-  int code = 0, bad = 0;
-  for (int d = 0; d < 3; ++d) {
-    int sd;
-    if (FP64) {
-      const double v = prep_fp64(pos[3 * (size_t)i + d], A, d, bad);
-      sd = (int)((v - kc[d] * A.cw[d]) * (4.0 * A.inv_cw[d]));
-    } else {
-      float hi, lo;
-      prep_mixed(pos[3 * (size_t)i + d], A, d, bad, hi, lo);
-      sd = (int)(offset_from(hi, lo, kc[d], A.cw_hi[d], A.cw_lo[d]) * (4.f * A.inv_cwf[d]));
-    }
-    sd = min(max(sd, 0), 3);
-    code |= ((sd & 1) << d) | (((sd >> 1) & 1) << (3 + d));
+__device__ __forceinline__ int slab_code(const IO* __restrict__ pos, const BinArgs& A, int key, int i) {
+  const int kx = key % A.nc[0];
+  int bad = 0, sx;
+  if (FP64) {
+    const double v = prep_fp64(pos[3 * (size_t)i], A, 0, bad);
+    sx = (int)((v - kx * A.cw[0]) * (kSlabs * A.inv_cw[0]));
+  } else {
+    float hi, lo;
+    prep_mixed(pos[3 * (size_t)i], A, 0, bad, hi, lo);
+    sx = (int)(offset_from(hi, lo, kx, A.cw_hi[0], A.cw_lo[0]) * (kSlabs * A.inv_cwf[0]));
   }
-  return code;
+  return min(max(sx, 0), kSlabs - 1);
 }
 
 // The sorted records of atom i at slot s of cell `key` (the atom's cell as
@@ -425,8 +421,8 @@ __device__ __forceinline__ void write_records(const IO* __restrict__ pos, const 
 }
 
 // One atom's records in registers (computed once from one read of its
-// position) and its sub-cell code, from the same cell-local coordinates as
-// subcell_code and write_records above.
+// position) and its slab, from the same cell-local coordinates as
+// slab_code and write_records above.
 template <bool FP64>
 struct CellRec {
   using T = typename std::conditional<FP64, double, float>::type;
@@ -440,11 +436,10 @@ __device__ __forceinline__ int make_record(const IO* __restrict__ pos, const IO*
   const int kc[3] = {key % A.nc[0], (key / A.nc[0]) % A.nc[1], key / (A.nc[0] * A.nc[1])};
   int bad = 0, code = 0;
   for (int d = 0; d < 3; ++d) {
-    int sd;
     if (FP64) {
       const double v = prep_fp64(pos[3 * (size_t)i + d], A, d, bad);
       R.loc[d] = v - kc[d] * A.cw[d];
-      sd = (int)((v - kc[d] * A.cw[d]) * (4.0 * A.inv_cw[d]));
+      if (d == 0) code = (int)((v - kc[d] * A.cw[d]) * (kSlabs * A.inv_cw[d]));
       double fr;
       grid_fp64(v, A, d, R.bs[d], fr);
       R.fr[d] = fr;
@@ -453,14 +448,13 @@ __device__ __forceinline__ int make_record(const IO* __restrict__ pos, const IO*
       prep_mixed(pos[3 * (size_t)i + d], A, d, bad, hi, lo);
       const float loc = offset_from(hi, lo, kc[d], A.cw_hi[d], A.cw_lo[d]);
       R.loc[d] = loc;
-      sd = (int)(loc * (4.f * A.inv_cwf[d]));
+      if (d == 0) code = (int)(loc * (kSlabs * A.inv_cwf[d]));
       float fr;
       grid_mixed(hi, lo, A, d, R.bs[d], fr);
       R.fr[d] = fr;
     }
-    sd = min(max(sd, 0), 3);
-    code |= ((sd & 1) << d) | (((sd >> 1) & 1) << (3 + d));
   }
+  code = min(max(code, 0), kSlabs - 1);
   R.q = finite_bits(q[i]) ? (typename CellRec<FP64>::T)q[i] : (typename CellRec<FP64>::T)0;
   return code;
 }
@@ -477,7 +471,7 @@ __device__ __forceinline__ void store_record(const CellRec<FP64>& R, const BinAr
 }
 
 // One warp per cell: the cell's atoms (perm, in provisional order) are put in
-// (sub-cell, index) order and their records written.  A cell of at most 32
+// (slab, index) order and their records written.  A cell of at most 32
 // atoms (nearly every cell) takes one atom per lane: the lane reads its
 // atom's position once, keeps the records in registers, ranks its key among
 // the cell's keys and stores at that rank.  Larger cells go through the keys
@@ -511,7 +505,7 @@ __device__ __forceinline__ void cell_fill_body(const IO* __restrict__ pos, const
   } else if (m <= kOrderMax) {
     for (int t = lane; t < m; t += 32) {
       const int i = perm[s0 + t];
-      idx[t] = ((long long)subcell_code<IO, FP64>(pos, A, cell, i) << 32) | (long long)i;
+      idx[t] = ((long long)slab_code<IO, FP64>(pos, A, cell, i) << 32) | (long long)i;
     }
     __syncwarp();
     for (int t = lane; t < m; t += 32) {

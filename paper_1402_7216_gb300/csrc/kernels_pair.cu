@@ -443,6 +443,11 @@ struct PairKArgs {
   int ncell;
   float* phis;
   R4<float>* fs;
+  // target runs (short_range_run_body): cell of every input atom, the sorted
+  // order's input indices and the atom count
+  const int* key;
+  const int* perm;
+  int natoms;
 };
 
 // The segment table of cell (cx, cy, cz), built by the warp (lane r: row r);
@@ -665,11 +670,9 @@ __device__ __forceinline__ void short_range_f2_body(const PairKArgs& K, int blk)
 
 // ---- target clusters (mixed precision) ----
 // The warp takes its cell's atoms 32 at a time (a pass) as up to kClPass
-// clusters of kCl consecutive atoms, spatially compact because binning orders
-// each cell by sub-cell, and culls every source against each cluster's own
-// bounding box: the box of 8 atoms admits ~1,650 sources per atom at water
-// density against ~2,200 for the box of a whole cell (the pairs inside the
-// cutoff are ~750).  Each cluster has its own queue; a full queue of kCD
+// clusters of kCl consecutive atoms (slabs of the cell across x, since
+// binning sorts each cell by x), and culls every source against each
+// cluster's own bounding box.  Each cluster has its own queue; a full queue of kCD
 // sources is drained by the whole warp on that one cluster: lane 4 i + jl
 // evaluates target i of the cluster against sources 16 jl .. 16 jl + 15
 // (packed FP32x2), the four partial sums of a target are added across its
@@ -912,6 +915,279 @@ __device__ __forceinline__ void short_range_c8_body(const PairKArgs& K, int blk)
   }
 }
 
+// ---- target runs (mixed precision) ----
+// Warp w takes the 32 consecutive sorted atoms 32 w .. 32 w + 31 as its
+// targets, whatever cells they belong to, so that no lane idles for want of
+// a cell's atoms (~25 per cell at the default fill).  Binning sorts each cell
+// by x and numbers cells x fastest, so a run of a cell row is a slab of it
+// 32 atoms thick.  The run is cut into pieces of one row and at most three
+// consecutive cells (nearly always one piece); a piece is a pass as in the
+// one-cell kernel, about its first cell c0 and span s = its last cell - c0:
+// the targets enter c0's frame shifted by whole cells, the home block is the
+// atoms of cells c0 .. c0 + s with the self test, and the neighbour rows are
+// the plan's rows widened by s cells in +x (the home row without the piece's
+// own cells), walked as one flat index space, culled against the piece's
+// bounding box and queued.  A periodic row then spans up to seven cells, so
+// the runs need at least seven cells in x.
+constexpr int kRunBnd = 6;  // boundaries inside a row segment of up to 7 cells
+struct SegTableR {
+  int4 rec[2 * kMaxRows + 1];         // (first atom, flat start, x offset of the first cell, -); sentinel at the end
+  int4 bnd[2 * kMaxRows];             // first atom of the segment's 2nd..5th cell (INT_MAX where absent)
+  int2 bnd2[2 * kMaxRows];            // ... of its 6th and 7th cell
+  float2 shift[2 * kMaxRows];         // (y, z) shift of the row
+};
+
+// The segment table of the rows about cells (cx .. cx + span, cy, cz): as
+// build_seg_table, each row widened by span cells in +x (the home row's
+// right part moved past the piece's cells).
+__device__ __forceinline__ int build_seg_table_run(SegTableR& T, const PairKArgs& K, int cx, int cy, int cz, int span,
+                                                   int lane) {
+  const int* __restrict__ cell_start = K.cell_start;
+  const PairArgs& A = K.A;
+  const int ncx = A.nc[0], ncy = A.nc[1], ncz = A.nc[2];
+  const int nrows = K.nrows;
+  const float cwy = K.cwy, cwz = K.cwz;
+  int len[2] = {0, 0}, j0s[2] = {0, 0}, ox0s[2] = {0, 0};
+  int bb[2][kRunBnd];
+#pragma unroll
+  for (int g = 0; g < 2; ++g)
+#pragma unroll
+    for (int t = 0; t < kRunBnd; ++t) bb[g][t] = INT_MAX;
+  float2 sh = make_float2(0.f, 0.f);
+  if (lane < nrows) {
+    int4 row = K.rows[lane];  // (dy, dz, xlo, xhi)
+    if (row.x == 0 && row.y == 0) {
+      if (row.z > 0) { row.z += span; row.w += span; }  // the home row's right part
+    } else {
+      row.w += span;
+    }
+    int ny = cy + row.x, nz = cz + row.y;
+    bool inside = true;
+    if (A.periodic) {
+      ny += (ny < 0) ? ncy : ((ny >= ncy) ? -ncy : 0);
+      nz += (nz < 0) ? ncz : ((nz >= ncz) ? -ncz : 0);
+    } else if (ny < 0 || nz < 0 || ny >= ncy || nz >= ncz) {
+      inside = false;
+    }
+    const int rbase = (nz * ncy + ny) * ncx;
+    sh = make_float2(row.x * cwy, row.y * cwz);
+#pragma unroll
+    for (int seg = 0; seg < 2; ++seg) {
+      int ox0 = 0, ox1 = -1;
+      if (!inside) {
+      } else if (A.periodic) {  // at most 7 <= ncx cells: the row wraps at one end at most
+        const int xa = cx + row.z, xb = cx + row.w;
+        if (xa < 0) {
+          if (seg == 0) { ox0 = row.z; ox1 = -cx - 1; } else { ox0 = -cx; ox1 = row.w; }
+        } else if (xb >= ncx) {
+          if (seg == 0) { ox0 = row.z; ox1 = ncx - 1 - cx; } else { ox0 = ncx - cx; ox1 = row.w; }
+        } else if (seg == 0) {
+          ox0 = row.z; ox1 = row.w;
+        }
+      } else if (seg == 0) {
+        ox0 = max(row.z, -cx);
+        ox1 = min(row.w, ncx - 1 - cx);
+      }
+      if (ox0 <= ox1) {
+        int x0 = cx + ox0, x1 = cx + ox1;
+        if (A.periodic) {
+          x0 += (x0 < 0) ? ncx : ((x0 >= ncx) ? -ncx : 0);
+          x1 += (x1 < 0) ? ncx : ((x1 >= ncx) ? -ncx : 0);
+        }
+        const int j0 = cell_start[rbase + x0], j1 = cell_start[rbase + x1 + 1];
+#pragma unroll
+        for (int t = 0; t < kRunBnd; ++t) bb[seg][t] = (x0 + 1 + t <= x1) ? cell_start[rbase + x0 + 1 + t] : INT_MAX;
+        len[seg] = j1 - j0;
+        j0s[seg] = j0;
+        ox0s[seg] = ox0;
+      }
+    }
+  }
+  const int mine = len[0] + len[1];
+  int incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  const int start = incl - mine;
+  if (lane < nrows) {
+#pragma unroll
+    for (int seg = 0; seg < 2; ++seg) {
+      T.rec[2 * lane + seg] = make_int4(j0s[seg], seg ? start + len[0] : start, ox0s[seg], 0);
+      T.bnd[2 * lane + seg] = make_int4(bb[seg][0], bb[seg][1], bb[seg][2], bb[seg][3]);
+      T.bnd2[2 * lane + seg] = make_int2(bb[seg][4], bb[seg][5]);
+      T.shift[2 * lane + seg] = sh;
+    }
+  }
+  if (lane == 0) T.rec[2 * nrows] = make_int4(0, INT_MAX, 0, 0);
+  __syncwarp();
+  return total;
+}
+
+template <int M, int KIND>
+__device__ __forceinline__ void short_range_run_body(const PairKArgs& K, int blk) {
+  const R4<float>* __restrict__ atoms = K.atoms;
+  const int* __restrict__ cell_start = K.cell_start;
+  const PairArgs& A = K.A;
+  const PairCoef C = K.C;
+  const WolfC<float> W = K.W;
+  const float cwx = K.cwx;
+  float* __restrict__ phis = K.phis;
+  R4<float>* __restrict__ fs = K.fs;
+  __shared__ QueueF queue[kWarps];
+  __shared__ SegTableR tables[kWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  QueueF& Q = queue[warp];
+  SegTableR& T = tables[warp];
+  const int s0 = 32 * (blk * kWarps + warp);
+  if (s0 >= K.natoms) return;  // warp-uniform
+  const int nval = min(32, K.natoms - s0);
+  const int ncx = A.nc[0], ncy = A.nc[1];
+  const float a2 = A.a2f;
+  const float FAR = 1e6f;
+  // the lane's target: its sorted record and its cell (cells ascend with the lane)
+  const bool sv = lane < nval;
+  const int mycell = sv ? K.key[K.perm[s0 + lane]] : INT_MAX;
+  const R4<float> me = sv ? atoms[s0 + lane] : R4<float>{0.f, 0.f, 0.f, 0.f};
+  for (int l0 = 0; l0 < nval;) {  // one piece per step (warp-uniform)
+    const int c0 = __shfl_sync(kFull, mycell, l0);
+    const int cx = c0 % ncx, cy = (c0 / ncx) % ncy, cz = c0 / (ncx * ncy);
+    const int climit = c0 + min(2, ncx - 1 - cx);  // the piece stays in the row, three cells at most
+    const bool inp = lane >= l0 && mycell <= climit;  // lanes l0 .. l1 - 1
+    const unsigned pb = __ballot_sync(kFull, inp);
+    const int l1 = 32 - __clz(pb);
+    const int span = __shfl_sync(kFull, mycell, l1 - 1) - c0;
+    // cell boundaries inside the piece: atoms of cell c0 + 1 and c0 + 2 begin here
+    const int h0 = cell_start[c0];
+    const int b1 = span >= 1 ? cell_start[c0 + 1] : INT_MAX;
+    const int b2 = span >= 2 ? cell_start[c0 + 2] : INT_MAX;
+    const int h1 = cell_start[c0 + span + 1];
+    // the target in c0's frame
+    R4<float> ai = me;
+    ai.x = __fmaf_rn((float)(inp ? mycell - c0 : 0), cwx, ai.x);  // the same rounding as the home block's
+    float lx = inp ? ai.x : FAR, ly = inp ? ai.y : FAR, lz = inp ? ai.z : FAR;
+    float hx = inp ? ai.x : -FAR, hy = inp ? ai.y : -FAR, hz = inp ? ai.z : -FAR;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lx = fminf(lx, __shfl_xor_sync(kFull, lx, o));
+      ly = fminf(ly, __shfl_xor_sync(kFull, ly, o));
+      lz = fminf(lz, __shfl_xor_sync(kFull, lz, o));
+      hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, o));
+      hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, o));
+      hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, o));
+    }
+    const float2 nax = make_float2(-ai.x, -ai.x), nay = make_float2(-ai.y, -ai.y), naz = make_float2(-ai.z, -ai.z);
+    float phi = 0.f, px = 0.f, py = 0.f, pz = 0.f, cphi = 0.f, cpx = 0.f, cpy = 0.f, cpz = 0.f;
+    // the home block: the atoms of the piece's cells, 32 at a time, with the self test
+    for (int jb = h0; jb < h1; jb += 32) {
+      const int j = jb + lane;
+      R4<float> h = (j < h1) ? atoms[j] : R4<float>{FAR, FAR, FAR, 0.f};
+      if (j < h1) h.x = __fmaf_rn((float)((j >= b1) + (j >= b2)), cwx, h.x);
+      Q.x[lane] = h.x;
+      Q.y[lane] = h.y;
+      Q.z[lane] = h.z;
+      Q.q[lane] = h.w;
+      __syncwarp();
+      pair_batch_f2<M, KIND, 32, true>(Q, nax, nay, naz, a2, C, W, phi, px, py, pz, cphi, cpx, cpy, cpz);
+      __syncwarp();
+    }
+    // the neighbour rows: flat source index t in [0, total), 32 per step
+    const int total = build_seg_table_run(T, K, cx, cy, cz, span, lane);
+    int seg = 0;
+    auto locate = [&](int t, int& j, int& ox, float2& shv) {
+      while (T.rec[seg + 1].y <= t) ++seg;
+      const int4 r = T.rec[seg];
+      const int4 b = T.bnd[seg];
+      const int2 b2 = T.bnd2[seg];
+      j = r.x + (t - r.y);
+      ox = r.z + (j >= b.x) + (j >= b.y) + (j >= b.z) + (j >= b.w) + (j >= b2.x) + (j >= b2.y);
+      shv = T.shift[seg];
+    };
+    R4<float> an = {FAR, FAR, FAR, 0.f};
+    int oxn = 0;
+    float2 shn = make_float2(0.f, 0.f);
+    if (lane < total) {
+      int j;
+      locate(lane, j, oxn, shn);
+      an = atoms[j];
+    }
+    int qn = 0;
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const bool valid = t0 + lane < total;
+      R4<float> aj = an;
+      const int ox = oxn;
+      const float2 shv = shn;
+      if (t0 + 32 + lane < total) {
+        int j;
+        locate(t0 + 32 + lane, j, oxn, shn);
+        an = atoms[j];
+      }
+      aj.x += ox * cwx;
+      aj.y += shv.x;
+      aj.z += shv.y;
+      const float ex = fmaxf(fmaxf(lx - aj.x, aj.x - hx), 0.f);
+      const float ey = fmaxf(fmaxf(ly - aj.y, aj.y - hy), 0.f);
+      const float ez = fmaxf(fmaxf(lz - aj.z, aj.z - hz), 0.f);
+      const bool keep = valid && (ex * ex + ey * ey + ez * ez < a2);
+      const unsigned bal = __ballot_sync(kFull, keep);
+      if (keep) {
+        const int p = qn + __popc(bal & ((1u << lane) - 1u));
+        Q.x[p] = aj.x;
+        Q.y[p] = aj.y;
+        Q.z[p] = aj.z;
+        Q.q[p] = aj.w;
+      }
+      qn += __popc(bal);
+      __syncwarp();
+      if (qn >= kBatch) {
+        pair_batch_f2<M, KIND>(Q, nax, nay, naz, a2, C, W, phi, px, py, pz, cphi, cpx, cpy, cpz);
+        __syncwarp();
+        if (lane < qn - kBatch) {
+          Q.x[lane] = Q.x[kBatch + lane];
+          Q.y[lane] = Q.y[kBatch + lane];
+          Q.z[lane] = Q.z[kBatch + lane];
+          Q.q[lane] = Q.q[kBatch + lane];
+        }
+        qn -= kBatch;
+        __syncwarp();
+      }
+    }
+    if (qn > 0) {  // last partial batch, padded with far-away zero charges
+      for (int t = lane; t < kBatch; t += 32)
+        if (t >= qn) {
+          Q.x[t] = FAR;
+          Q.y[t] = FAR;
+          Q.z[t] = FAR;
+          Q.q[t] = 0.f;
+        }
+      __syncwarp();
+      pair_batch_f2<M, KIND>(Q, nax, nay, naz, a2, C, W, phi, px, py, pz, cphi, cpx, cpy, cpz);
+      __syncwarp();
+    }
+    if (inp) {
+      const int i = s0 + lane;
+      phis[i] = phi + cphi;
+      const float qi = me.w;
+      fs[i] = R4<float>{-qi * (px + cpx), -qi * (py + cpy), -qi * (pz + cpz), 0.f};
+    }
+    l0 = l1;
+  }
+}
+
+template <int M, int KIND>
+__global__ void __launch_bounds__(32 * kWarps, MSM_PAIR_MINB) k_short_range_run(PairKArgs a) {
+  short_range_run_body<M, KIND>(a, blockIdx.x);
+}
+
+template <int M>
+__global__ void __launch_bounds__(32 * kWarps, MSM_PAIR_MINB) kb_short_range_run(const PairKArgs* __restrict__ tab,
+                                                                   const int* __restrict__ first, int nrep) {
+  const int r = batch_rep(first, nrep, blockIdx.x);
+  short_range_run_body<M, kPairMSM>(tab[r], blockIdx.x - first[r]);
+}
+
 template <int M, int KIND>
 __global__ void __launch_bounds__(32 * kWarps, MSM_PAIR_MINB) k_short_range_f2(PairKArgs a) {
   short_range_f2_body<M, KIND>(a, blockIdx.x);
@@ -990,14 +1266,33 @@ PairKArgs pair_kargs(const Plan& P) {
   K.cwx = (float)P.cw[0];
   K.cwy = (float)P.cw[1];
   K.cwz = (float)P.cw[2];
+  K.key = P.d.key;
+  K.perm = P.d.perm;
+  K.natoms = 0;
   return K;
 }
 
+// Target runs apply to a plan whose pair kernel takes a cell's targets
+// (pair_targets 32) and whose periodic rows hold at least seven cells.
+static bool use_runs(const Plan& P) {
+  return P.pair_runs && P.pair_targets != kCl && (!P.P.periodic || P.nc[0] >= 7);
+}
+
 template <int KIND>
-void launch_f2(Plan& P, cudaStream_t st, double alpha = 0.0) {
+void launch_f2(Plan& P, int64_t n, cudaStream_t st, double alpha = 0.0) {
   PairKArgs K = pair_kargs(P);
   K.W = wolf_consts<float>(alpha, P.P.cutoff);
+  K.natoms = (int)n;
   const int blocks = (P.ncell + kWarps - 1) / kWarps;
+  if (use_runs(P)) {  // runs of 32 consecutive atoms
+    const int br = (int)(((n + 31) / 32 + kWarps - 1) / kWarps);
+    if (KIND == kPairCutoff) k_short_range_run<2, kPairCutoff><<<br, 32 * kWarps, 0, st>>>(K);  // M unused
+    else if (KIND == kPairWolf) k_short_range_run<2, kPairWolf><<<br, 32 * kWarps, 0, st>>>(K);
+    else if (P.P.splitting == 1) k_short_range_run<1, kPairMSM><<<br, 32 * kWarps, 0, st>>>(K);
+    else if (P.P.splitting == 2) k_short_range_run<2, kPairMSM><<<br, 32 * kWarps, 0, st>>>(K);
+    else k_short_range_run<3, kPairMSM><<<br, 32 * kWarps, 0, st>>>(K);
+    return;
+  }
   if (P.pair_targets == kCl) {  // clusters of 8 targets
     if (KIND == kPairCutoff) k_short_range_c8<2, kPairCutoff><<<blocks, 32 * kWarps, 0, st>>>(K);  // M unused
     else if (KIND == kPairWolf) k_short_range_c8<2, kPairWolf><<<blocks, 32 * kWarps, 0, st>>>(K);
@@ -1016,7 +1311,7 @@ void launch_f2(Plan& P, cudaStream_t st, double alpha = 0.0) {
 cudaError_t launch_short_range(Plan& P, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (P.fp64) launch_t<double, false, kPairMSM>(P, st);
-  else launch_f2<kPairMSM>(P, st);
+  else launch_f2<kPairMSM>(P, n, st);
   P.launches += 1;
   return cudaGetLastError();
 }
@@ -1024,7 +1319,7 @@ cudaError_t launch_short_range(Plan& P, int64_t n, cudaStream_t st) {
 cudaError_t launch_cutoff_pairs(Plan& P, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (P.fp64) launch_t<double, false, kPairCutoff>(P, st);
-  else launch_f2<kPairCutoff>(P, st);
+  else launch_f2<kPairCutoff>(P, n, st);
   P.launches += 1;
   return cudaGetLastError();
 }
@@ -1032,15 +1327,16 @@ cudaError_t launch_cutoff_pairs(Plan& P, int64_t n, cudaStream_t st) {
 cudaError_t launch_wolf_pairs(Plan& P, int64_t n, double alpha, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (P.fp64) launch_t<double, false, kPairWolf>(P, st, alpha);
-  else launch_f2<kPairWolf>(P, st, alpha);
+  else launch_f2<kPairWolf>(P, n, st, alpha);
   P.launches += 1;
   return cudaGetLastError();
 }
 
 struct PairBatch {
-  BatchTable<PairKArgs> cells;  // kWarps cells per block
+  BatchTable<PairKArgs> cells;  // kWarps cells (or target runs) per block
   int splitting = 2;
   int targets = 8;  // the first replica's pair_targets
+  bool runs = false;  // every replica takes target runs
 };
 
 cudaError_t pair_batch_build(const std::vector<BatchRep>& reps, PairBatch** out) {
@@ -1049,9 +1345,14 @@ cudaError_t pair_batch_build(const std::vector<BatchRep>& reps, PairBatch** out)
   if (!b) return cudaErrorMemoryAllocation;
   std::vector<PairKArgs> ka;
   std::vector<int> kb;
+  b->runs = !reps.empty();
+  for (const BatchRep& r : reps) b->runs = b->runs && use_runs(*r.plan);
   for (const BatchRep& r : reps) {
-    ka.push_back(pair_kargs(*r.plan));
-    kb.push_back(r.n > 0 ? (r.plan->ncell + kWarps - 1) / kWarps : 0);
+    PairKArgs K = pair_kargs(*r.plan);
+    K.natoms = (int)r.n;
+    ka.push_back(K);
+    if (b->runs) kb.push_back(r.n > 0 ? (int)(((r.n + 31) / 32 + kWarps - 1) / kWarps) : 0);
+    else kb.push_back(r.n > 0 ? (r.plan->ncell + kWarps - 1) / kWarps : 0);
     b->splitting = r.plan->P.splitting;
   }
   if (!reps.empty()) b->targets = reps[0].plan->pair_targets;
@@ -1067,6 +1368,13 @@ cudaError_t pair_batch_build(const std::vector<BatchRep>& reps, PairBatch** out)
 cudaError_t pair_batch_launch(PairBatch* b, cudaStream_t st) {
   const int nb = b->cells.total;
   if (nb == 0) return cudaSuccess;
+  if (b->runs) {
+    if (b->splitting == 1) kb_short_range_run<1><<<nb, 32 * kWarps, 0, st>>>(b->cells.args, b->cells.first, b->cells.nrep);
+    else if (b->splitting == 2)
+      kb_short_range_run<2><<<nb, 32 * kWarps, 0, st>>>(b->cells.args, b->cells.first, b->cells.nrep);
+    else kb_short_range_run<3><<<nb, 32 * kWarps, 0, st>>>(b->cells.args, b->cells.first, b->cells.nrep);
+    return cudaGetLastError();
+  }
   if (b->targets == kCl) {
     if (b->splitting == 1) kb_short_range_c8<1><<<nb, 32 * kWarps, 0, st>>>(b->cells.args, b->cells.first, b->cells.nrep);
     else if (b->splitting == 2)

@@ -132,6 +132,8 @@ struct Plan {
   int lattice_txn = 0, lattice_tyn = 0;
   // mixed pair kernel: targets culled together (8: clusters; 32: a cell's warp)
   int pair_targets = 32;
+  // mixed pair kernel: targets in runs of 32 consecutive sorted atoms (true) or one cell per warp
+  bool pair_runs = false;
   // batched graphs: restriction and prolongation chains as persistent launches
   int batch_persistent = 0;
   // lattice cutoff of periodic levels as an FFT convolution (fft.cu)

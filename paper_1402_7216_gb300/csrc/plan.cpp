@@ -267,6 +267,7 @@ int validate_tuning(const msm_tuning* t) {
   if (t->pair_targets != 0 && t->pair_targets != 8 && t->pair_targets != 32) return MSM_ERR_INVALID_ARG;
   if (t->batch_persistent != 0 && t->batch_persistent != 1) return MSM_ERR_INVALID_ARG;
   if (t->lattice_method < 0 || t->lattice_method > 2) return MSM_ERR_INVALID_ARG;
+  if (t->pair_runs < 0 || t->pair_runs > 2) return MSM_ERR_INVALID_ARG;
   if (t->lattice_txn < 0 || t->lattice_tyn < 0 || t->lattice_txn > 32 || t->lattice_tyn > 32 ||
       (t->lattice_txn == 0) != (t->lattice_tyn == 0) || t->lattice_txn * t->lattice_tyn > 32)
     return MSM_ERR_INVALID_ARG;
@@ -289,11 +290,12 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   if (vrc != MSM_OK) return vrc;
   int trc = validate_tuning(tune);
   if (trc != MSM_OK) return trc;
-  msm_tuning TU = {0, 0, 0, 0, 0, 0, 0, 0};
+  msm_tuning TU = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (tune) TU = *tune;
   const double fill = TU.cell_fill > 0 ? TU.cell_fill : 24.0;
   P->lattice_waves = TU.lattice_waves > 0 ? TU.lattice_waves : 8;
   P->pair_targets = TU.pair_targets > 0 ? TU.pair_targets : 32;
+  P->pair_runs = TU.pair_runs == 1;
   P->lattice_txn = TU.lattice_txn;
   P->batch_persistent = TU.batch_persistent;
   const int lattice_method = TU.lattice_method > 0 ? TU.lattice_method : 2;

@@ -78,6 +78,10 @@ def test_create_tuned_rejects_bad_tuning_without_a_gpu(library):
     for bad in [(-1, 0, 0), (257, 0, 0), (0, 5, 0), (0, -2, 0), (0, 0, 65), (0, 0, -1)]:
         t = _capi.MSMTuning(*bad)
         assert L.msm_create_tuned(ctypes.byref(p), ctypes.byref(t), ctypes.byref(h)) == -1, bad
+    for field, bad in [("pair_runs", 3), ("pair_runs", -1), ("pair_targets", 16), ("lattice_method", 3)]:
+        t = _capi.MSMTuning()
+        setattr(t, field, bad)
+        assert L.msm_create_tuned(ctypes.byref(p), ctypes.byref(t), ctypes.byref(h)) == -1, (field, bad)
     p.order = 4  # bad params are still reported with a valid tuning
     t = _capi.MSMTuning(26, 4, 4)
     assert L.msm_create_tuned(ctypes.byref(p), ctypes.byref(t), ctypes.byref(h)) == -1
