@@ -939,8 +939,13 @@ struct SegTableR {
 
 // The segment table of the rows about cells (cx .. cx + span, cy, cz): as
 // build_seg_table, each row widened by span cells in +x (the home row's
-// right part moved past the piece's cells).
+// right part moved past the piece's cells), then narrowed to the cells a
+// source within a of the targets' bounding box (lx..hx, ly..hy, lz..hz, in
+// the frame of cell cx) can lie in: a row at y gap gy and z gap gz from the
+// box reaches sqrt(a^2 - gy^2 - gz^2) beyond it in x (with a margin for
+// rounding; the culling tests each source exactly).
 __device__ __forceinline__ int build_seg_table_run(SegTableR& T, const PairKArgs& K, int cx, int cy, int cz, int span,
+                                                   float lx, float ly, float lz, float hx, float hy, float hz,
                                                    int lane) {
   const int* __restrict__ cell_start = K.cell_start;
   const PairArgs& A = K.A;
@@ -961,8 +966,17 @@ __device__ __forceinline__ int build_seg_table_run(SegTableR& T, const PairKArgs
     } else {
       row.w += span;
     }
+    const float gy = fmaxf(fmaxf(row.x * cwy - hy, ly - (row.x + 1) * cwy), 0.f);
+    const float gz = fmaxf(fmaxf(row.y * cwz - hz, lz - (row.y + 1) * cwz), 0.f);
+    const float r2 = A.a2f - gy * gy - gz * gz;
+    bool inside = r2 > 0.f;
+    if (inside) {
+      const float reach = sqrtf(r2) * 1.0001f + 1e-3f;
+      row.z = max(row.z, (int)floorf((lx - reach) / K.cwx));
+      row.w = min(row.w, (int)floorf((hx + reach) / K.cwx));
+      inside = row.z <= row.w;
+    }
     int ny = cy + row.x, nz = cz + row.y;
-    bool inside = true;
     if (A.periodic) {
       ny += (ny < 0) ? ncy : ((ny >= ncy) ? -ncy : 0);
       nz += (nz < 0) ? ncz : ((nz >= ncz) ? -ncz : 0);
@@ -1094,7 +1108,7 @@ __device__ __forceinline__ void short_range_run_body(const PairKArgs& K, int blk
       __syncwarp();
     }
     // the neighbour rows: flat source index t in [0, total), 32 per step
-    const int total = build_seg_table_run(T, K, cx, cy, cz, span, lane);
+    const int total = build_seg_table_run(T, K, cx, cy, cz, span, lx, ly, lz, hx, hy, hz, lane);
     int seg = 0;
     auto locate = [&](int t, int& j, int& ox, float2& shv) {
       while (T.rec[seg + 1].y <= t) ++seg;
