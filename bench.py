@@ -301,11 +301,13 @@ def bench_large(dev, args):
     torch.cuda.reset_peak_memory_stats(dev)
     free0 = torch.cuda.mem_get_info(dev)[0]
     # the lattice form (FFT or stencil) and, for the stencil, the warp tile of
-    # the finest grid from the project's autotuner, timed on forward + adjoint
+    # the finest grid, and the pair kernel's target grouping, from the
+    # project's autotuner, timed on forward + adjoint
     from paper_1402_7216_gb300.autotune import TILES, autotune
     tuning, tune_ms = autotune(pos, q, w.box, True, w.cutoff, w.spacing, levels=w.levels, order=w.order,
                                splitting=w.split, precision="mixed", reps=3,
-                               search=[("lattice_method", [1]), ("lattice_tile", TILES)], backward=True)
+                               search=[("lattice_method", [1]), ("pair_runs", [1, 2]), ("lattice_tile", TILES)],
+                               backward=True)
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info(dev)[0]
     plan = MSM(box=w.box, periodic=True, cutoff=w.cutoff, spacing=w.spacing, levels=w.levels, order=w.order,

@@ -97,8 +97,9 @@ typedef struct {
  *                 warp takes 32 consecutive atoms of the sorted order as its
  *                 targets (runs across the cells of a row, which binning
  *                 sorts by x), 2 a warp takes one cell's atoms; 0 the
- *                 default, 2.  Runs need at least seven cells along x on a
- *                 periodic plan and fall back to cells otherwise
+ *                 default, 1 on plans of at least 16,384 cells and 2 below.
+ *                 Runs need at least seven cells along x on a periodic plan
+ *                 and fall back to cells otherwise
  *   lattice_txn, lattice_tyn  warp tile of the mixed-precision lattice
  *                 kernel: txn lanes of 8 x outputs by tyn lanes of two rows,
  *                 txn * tyn <= 32 (default 4 x 8 on a single system; batched

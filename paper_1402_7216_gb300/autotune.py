@@ -3,8 +3,9 @@
 The tunables change speed, never results beyond summation order:
   pair_targets   targets the pair kernel culls together: 32 (a cell's warp)
                  or 8 (clusters of 8 consecutive atoms)
-  pair_runs      with 32: a warp's targets are one cell's atoms (2, the
-                 default) or 32 consecutive atoms of an x-sorted cell row (1)
+  pair_runs      with 32: a warp's targets are one cell's atoms (2) or 32
+                 consecutive atoms of an x-sorted cell row (1); the default
+                 takes runs on plans of at least 16,384 cells
   cell_fill      target atoms per short-range cell (pair-kernel lane use vs
                  candidate volume)
   patch_cells    cells per side of the anterpolation/interpolation patch blocks
@@ -41,7 +42,7 @@ MARGIN = 0.01
 # (txn, tyn) lattice warp tiles: 32 x 16 outputs (the default) and shapes that
 # fit small or flat grids better
 TILES = [(4, 8), (2, 8), (4, 4), (8, 4), (2, 16), (8, 2), (1, 16)]
-SEARCH = [("lattice_method", [1]), ("pair_targets", [32, 8]), ("pair_runs", [1]), ("cell_fill", [20, 24, 28, 32]),
+SEARCH = [("lattice_method", [1]), ("pair_targets", [32, 8]), ("pair_runs", [1, 2]), ("cell_fill", [20, 24, 28, 32]),
           ("patch_cells", [2, 3, 4]), ("lattice_waves", [4, 8, 16]), ("lattice_tile", TILES)]
 # fields that only the stencil form of the lattice cutoff reads
 STENCIL_ONLY = ("lattice_waves", "lattice_tile")
@@ -185,7 +186,7 @@ def tuned_plan(pos, q, box, periodic, cutoff, spacing, **kw):
 
 # Batches: timed on the captured batch graph (forward + adjoint), the form
 # msm_batch_graph_create runs.
-SEARCH_BATCH = [("lattice_method", [1]), ("pair_targets", [32, 8]), ("pair_runs", [1]), ("batch_persistent", [0, 1]),
+SEARCH_BATCH = [("lattice_method", [1]), ("pair_targets", [32, 8]), ("pair_runs", [1, 2]), ("batch_persistent", [0, 1]),
                 ("lattice_waves", [8, 16]), ("patch_cells", [3, 4]), ("cell_fill", [20, 24])]
 TILES_BATCH = [(4, 8), (2, 8), (4, 4), (8, 4), (2, 16), (1, 16)]
 
