@@ -343,7 +343,7 @@ int build_plan(const msm_params* pp, const msm_tuning* tune, Plan* P) {
   P->ncell = P->nc[0] * P->nc[1] * P->nc[2];
   // target runs by default on large boxes, where they were measured faster
   // (1.63 against 1.72 ms at 42,875 cells); small boxes run too few warps
-  // for the longer row walks of a run (1.1-2x slower at 300-1,000 cells)
+  // for the longer row walks of a run (1.15-1.9x slower at 343-1,000 cells)
   P->pair_runs = TU.pair_runs == 1 || (TU.pair_runs == 0 && P->ncell >= 16384);
   std::vector<int4> offs;
   for (int oz = -2; oz <= 2; ++oz)
